@@ -1,0 +1,382 @@
+"""Pins of the FP64 oracle against what the physics and the paper fix
+(arXiv:1307.3711 Sec. II), independent of the oracle's own formulas.
+
+Each test names the law it checks.  None calls the CUDA path.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import constants as sc
+from scipy import integrate, optimize, stats
+
+import oracle
+from paper_1307_3711_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+KC = oracle.coulomb_constant(0.8)
+
+
+# ----------------------------------------------------------------- units ---
+
+def test_coulomb_constant_from_si_coulomb_law():
+    """a = eE/(m_e omega c) with E = e/(4 pi eps0 r^2), r = r'/k and omega = c k
+    gives K_C = e^2 k / (4 pi eps0 m_e c^2): computed here from SI constants,
+    not from the classical electron radius the oracle uses."""
+    lam = 0.8e-6
+    k = 2 * math.pi / lam
+    kc_si = sc.e ** 2 * k / (4 * math.pi * sc.epsilon_0 * sc.m_e * sc.c ** 2)
+    assert oracle.coulomb_constant(0.8) == pytest.approx(kc_si, rel=1e-9)
+    assert oracle.coulomb_constant(0.4) == pytest.approx(2 * kc_si, rel=1e-9)
+
+
+def test_paper_worked_values():
+    """Sec. II / Sec. III numbers: R_W table and Ar_40000 -> R0 about 82 A
+    (Eq. 1); Eq. 2 against the field amplitude of an SI plane wave."""
+    with open(os.path.join(GOLDEN, "paper_values.json")) as f:
+        g = json.load(f)
+    ar = g["ar40000_radius"]
+    r0 = ar["r_w_angstrom"] * ar["n_atoms"] ** (1 / 3)
+    assert abs(r0 - ar["r0_angstrom_about"]) < ar["rounding_angstrom"]
+    assert oracle.n_atoms(r0, ar["r_w_angstrom"]) == pytest.approx(ar["n_atoms"], rel=1e-12)
+    # Eq. 2 vs a = eE/(m_e omega c) with I = (1/2) c eps0 E^2 (linear polarisation)
+    for lam_um, inten in [(0.8, 1e16), (0.857, 5e16), (0.806, 8e15), (0.79, 4e15)]:
+        e_si = math.sqrt(2 * inten * 1e4 / (sc.c * sc.epsilon_0))
+        omega = 2 * math.pi * sc.c / (lam_um * 1e-6)
+        a_si = sc.e * e_si / (sc.m_e * omega * sc.c)
+        # 1.366e18 is a rounded constant: agreement to 0.1 %
+        assert oracle.a0_from_intensity(inten, lam_um) == pytest.approx(a_si, rel=2e-3)
+    for sp, rw in g["wigner_seitz_angstrom"].items():
+        if not sp.startswith("_"):
+            assert synth.R_W_ANGSTROM[sp] == rw
+
+
+# ----------------------------------------------------------------- laser ---
+
+@pytest.mark.parametrize("pol", [0, 1])
+def test_laser_is_a_plane_wave_along_z(pol):
+    """Eqs. 4-9 with b0 = a0: E and B of a plane wave travelling along +z,
+    B = z_hat x E, |B| = |E|, E.B = 0; circular: |E| constant."""
+    a0, tau = 0.3, 40 * math.pi
+    for t in np.linspace(0.1, tau - 0.1, 37):
+        a, b = oracle.laser_fields(t, a0, pol, oracle.ENV_SIN2, tau)
+        zx = np.cross([0, 0, 1.0], a)
+        np.testing.assert_allclose(b, zx, atol=1e-15)
+        assert a[2] == 0 and b[2] == 0
+        f = oracle.envelope(t, oracle.ENV_SIN2, tau)
+        if pol == 1:
+            assert np.linalg.norm(a) == pytest.approx(a0 * f, rel=1e-12)
+        else:
+            assert a[1] == 0 and b[0] == 0
+            assert a[0] == pytest.approx(a0 * f * math.sin(t), rel=1e-12, abs=1e-300)
+
+
+def _fwhm_of_intensity(env, tau, lo, hi):
+    g = lambda t: oracle.envelope(t, env, tau) ** 2
+    tpk = optimize.minimize_scalar(lambda t: -g(t), bounds=(lo, hi), method="bounded",
+                                   options={"xatol": 1e-10}).x
+    left = optimize.brentq(lambda t: g(t) - 0.5, lo, tpk, xtol=1e-12)
+    right = optimize.brentq(lambda t: g(t) - 0.5, tpk, hi, xtol=1e-12)
+    return tpk, right - left
+
+
+def test_envelope_fwhm_readings():
+    """Eq. 3 reading: intensity FWHM = tau, peak at 2 tau (Gaussian);
+    sin^2 field envelope with T from the FWHM has intensity FWHM = tau."""
+    tau = 235.0
+    tpk, w = _fwhm_of_intensity(oracle.ENV_GAUSS, tau, 0.0, 4 * tau)
+    assert tpk == pytest.approx(2 * tau, rel=1e-6)
+    assert w == pytest.approx(tau, rel=1e-8)
+    T = synth.sin2_length_from_fwhm(tau)
+    tpk, w = _fwhm_of_intensity(oracle.ENV_SIN2, T, 0.0, T)
+    assert tpk == pytest.approx(T / 2, rel=1e-6)
+    assert w == pytest.approx(tau, rel=1e-8)
+    assert oracle.envelope(-1.0, oracle.ENV_SIN2, T) == 0.0
+    assert oracle.envelope(T + 1.0, oracle.ENV_SIN2, T) == 0.0
+    # literal Eq. 3 constant 2.77 ~ 4 ln 2: its field envelope has FWHM ~ tau
+    tpk, w = _fwhm_of_intensity(oracle.ENV_LITERAL_EQ3, tau, 0.0, 4 * tau)
+    assert w == pytest.approx(tau / math.sqrt(2), rel=2e-3)
+
+
+# ------------------------------------------------------------ direct sum ---
+
+def _mp_field_from_potential(x, q, eps, kc, i):
+    """Brute force in 50-digit arithmetic: E_i = -grad_i U / q_i with
+    U = sum_{j<k} K q_j q_k / sqrt(r^2 + eps^2), by central differences."""
+    import mpmath as mp
+    mp.mp.dps = 50
+    X = [[mp.mpf(float(v)) for v in row] for row in x]
+    Q = [mp.mpf(float(v)) for v in q]
+    K, E2 = mp.mpf(kc), mp.mpf(eps) ** 2
+
+    def U(Xi):
+        s = mp.mpf(0)
+        for j in range(len(X)):
+            if j == i:
+                continue
+            d2 = sum((Xi[c] - X[j][c]) ** 2 for c in range(3)) + E2
+            s += K * Q[i] * Q[j] / mp.sqrt(d2)
+        return s
+
+    h = mp.mpf("1e-20")
+    out = []
+    for c in range(3):
+        xp = list(X[i]); xm = list(X[i])
+        xp[c] += h; xm[c] -= h
+        out.append(-(U(xp) - U(xm)) / (2 * h) / Q[i])
+    return np.array([float(v) for v in out])
+
+
+@pytest.mark.parametrize("eps", [0.0, 3e-3])
+def test_field_is_minus_gradient_of_pair_potential_bruteforce(eps):
+    """Tiny N: the field equals -grad U / q of the softened pair potential,
+    evaluated in 50-digit arithmetic (catches sign, index and power errors)."""
+    rng = np.random.default_rng(7)
+    n = 9
+    x = rng.normal(size=(n, 3)) * 0.01
+    q = rng.choice([-1.0, 1.0, 2.0, 3.0], size=n) * rng.uniform(0.5, 2.0, size=n)
+    e = oracle.self_field(x, q, eps, KC)
+    for i in range(n):
+        ref = _mp_field_from_potential(x, q, eps, KC, i)
+        np.testing.assert_allclose(e[i], ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+def test_newton_third_law():
+    """sum_i Q_i E_i = 0 for internal forces (exact up to FP64 rounding)."""
+    c = synth.make_cluster(3, 300, 500, 0.02, 2, 1000.0)
+    q = c.w * c.z
+    e = oracle.self_field(c.x, q, 1e-4, KC)
+    f = q[:, None] * e
+    scale = np.abs(f).sum()
+    assert np.abs(f.sum(axis=0)).max() < 1e-13 * scale
+
+
+def test_far_field_of_symmetric_cluster_is_point_charge():
+    """Far from a point-symmetric charge set (dipole zero) the field is
+    K Q r_hat / r^2 up to (R/r)^2: the 1/r^2 law and the constant."""
+    pts = np.array([[sx, sy, sz] for sx in (-1, 1) for sy in (-1, 1) for sz in (-1, 1)],
+                   float) * 0.01
+    pts = np.concatenate([pts, -pts * 0.5])
+    q = np.concatenate([np.full(8, 2.0), np.full(8, -0.5)])
+    Q = q.sum()
+    for r in [10.0, 30.0]:
+        for d in [np.array([1.0, 0, 0]), np.array([0.3, -0.4, 0.866])]:
+            d = d / np.linalg.norm(d)
+            e = oracle.coulomb_field(d[None, :] * r, pts, q, 0.0, KC)[0]
+            np.testing.assert_allclose(e, KC * Q * d / r ** 2, rtol=1e-7)
+
+
+def test_gauss_law_inside_uniform_sphere():
+    """Inside a uniformly charged ball E(r) = K Q r / R0^3 (statistical: the
+    mean over many interior targets; a softening of 0.02 R0 bounds the
+    variance of the nearest-neighbour term); outside E = K Q / r^2."""
+    rng = np.random.default_rng(11)
+    n, r0 = 60000, 0.05
+    x = synth.uniform_sphere(rng, n, r0)
+    q = np.ones(n)
+    d = rng.normal(size=(600, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    rad = rng.uniform(0.2, 0.7, size=600) * r0
+    tgt = d * rad[:, None]
+    e = oracle.coulomb_field(tgt, x, q, 0.02 * r0, KC, nthreads=4)
+    er = (e * d).sum(1)
+    ratio = er / (KC * n * rad / r0 ** 3)
+    assert ratio.mean() == pytest.approx(1.0, abs=0.01)
+    out = np.array([[0, 0, 3 * r0]])
+    eo = oracle.coulomb_field(out, x, q, 0.0, KC)[0]
+    assert eo[2] == pytest.approx(KC * n / (3 * r0) ** 2, rel=2e-3)
+
+
+def test_uniform_sphere_potential_energy_three_fifths():
+    """Independent uniform points in a ball: <1/r> = 6/(5 R0), so the expected
+    pair energy is (3/5) K q^2 N(N-1)/R0 (the 3/5 of Sec. III)."""
+    vals = []
+    n, r0 = 3000, 0.02
+    for seed in range(6):
+        rng = np.random.default_rng(100 + seed)
+        x = synth.uniform_sphere(rng, n, r0)
+        q = np.ones(n)
+        _, phi = oracle.self_field(x, q, 0.0, KC, potential=True, nthreads=4)
+        vals.append(0.5 * (q * phi).sum() / (0.6 * KC * n * (n - 1) / r0))
+    assert np.mean(vals) == pytest.approx(1.0, abs=0.01)
+
+
+# ----------------------------------------------------------------- Boris ---
+
+def test_boris_uniform_electric_field_exact():
+    """E only: u grows linearly, exactly (the two half kicks are exact)."""
+    u = np.array([0.01, -0.2, 0.3])
+    e = np.array([0.5, -0.25, 0.125])
+    qm, dt = -1.0, 0.05
+    for n in range(1, 200):
+        u = oracle.boris_kick(u, e, np.zeros(3), qm, dt)
+    np.testing.assert_allclose(u, np.array([0.01, -0.2, 0.3]) + 199 * qm * e * dt,
+                               rtol=1e-13, atol=1e-13)
+
+
+def test_boris_uniform_magnetic_field_rotation():
+    """B only: |u| conserved; rotation angle per step 2 atan(omega_c dt / 2 gamma)
+    about B, in the sense of q u x B."""
+    u0 = np.array([0.4, 0.0, 0.1])
+    b = np.array([0.0, 0.0, 0.7])
+    qm, dt = -1.0, 0.1
+    g = math.sqrt(1 + u0 @ u0)
+    theta = 2 * math.atan(abs(qm) * 0.7 * dt / (2 * g))
+    u = u0.copy()
+    for n in range(1, 51):
+        u = oracle.boris_kick(u, np.zeros(3), b, qm, dt)
+        assert np.linalg.norm(u) == pytest.approx(np.linalg.norm(u0), rel=1e-14)
+        ang = -n * theta * np.sign(qm)  # electron turns counter-clockwise about +z
+        expect = np.array([0.4 * math.cos(ang) - 0.0, 0.4 * math.sin(ang), 0.1])
+        # q u x B for q<0 and B along +z turns u_perp counter-clockwise
+        np.testing.assert_allclose(u, expect, atol=1e-13)
+
+
+def test_hyperbolic_motion_positions_second_order():
+    """Uniform E from rest (relativistic): x(t) = (1/g)(sqrt(1 + (g t)^2) - 1)
+    with g = (q/m)E; leap-frog positions converge at second order."""
+    gacc = 0.8
+    errs = []
+    for dt in [0.04, 0.02, 0.01]:
+        n = int(round(4.0 / dt))
+        u = np.array([-0.5 * gacc * dt, 0.0, 0.0])  # u^{-1/2}
+        x = np.zeros(3)
+        for _ in range(n):
+            u = oracle.boris_kick(u, np.array([gacc, 0, 0]), np.zeros(3), 1.0, dt)
+            x = oracle.drift(x, u, dt)
+        t = n * dt
+        errs.append(abs(x[0] - (math.sqrt(1 + (gacc * t) ** 2) - 1) / gacc))
+    assert errs[0] / errs[1] == pytest.approx(4.0, rel=0.1)
+    assert errs[1] / errs[2] == pytest.approx(4.0, rel=0.1)
+
+
+# ---------------------------------------------------- laser + free electron ---
+
+@pytest.mark.parametrize("a0,pol", [(0.05, 0), (1.0, 0), (0.5, 1)])
+def test_free_electron_light_cone_invariant(a0, pol):
+    """Sec. II b0 = a0: for a plane wave along z, gamma - u_z = 1 and
+    u_z = u_perp^2 / 2 for an electron starting at rest (Boris: O(dt^2))."""
+    T = 40 * math.pi
+    dt = 0.02
+    nsteps = int(T / dt) + 50
+    st = oracle.State(np.zeros((1, 3)), np.zeros((1, 3)), [-1], [1.0], [1.0])
+    p = oracle.make_params(a0=a0, tau=T, dt=dt, eps=1e-3, pol=pol, env=oracle.ENV_SIN2)
+    worst = 0.0
+    for chunk in range(0, nsteps, 250):
+        oracle.md_steps(st, p, 250)
+        u = st.u[0]
+        g = math.sqrt(1 + u @ u)
+        worst = max(worst, abs(g - u[2] - 1.0))
+        assert u[2] == pytest.approx(0.5 * (u[0] ** 2 + u[1] ** 2), abs=5e-4 * a0 ** 2 + 1e-12)
+    assert worst < 5e-4 * a0 ** 2
+
+
+def test_free_electron_quiver_nonrelativistic():
+    """a0 << 1: u_x(t) = -integral_0^t a_x (electron, q/m = -1), quadrature of
+    Eqs. 4 and 3 by scipy; after an integer number of cycles under the sin^2
+    envelope the drift returns to zero."""
+    a0, T, dt = 1e-4, 16 * math.pi, 0.01
+    st = oracle.State(np.zeros((1, 3)), np.zeros((1, 3)), [-1], [1.0], [1.0])
+    p = oracle.make_params(a0=a0, tau=T, dt=dt, eps=1e-3, env=oracle.ENV_SIN2)
+    ax = lambda s: a0 * math.sin(math.pi * s / T) ** 2 * math.sin(s)
+    n_done = 0
+    for n_target in [400, 1300, 2513]:
+        oracle.md_steps(st, p, n_target - n_done)
+        n_done = n_target
+        t_half = (n_done - 0.5) * dt  # u lives at half steps
+        ref = -integrate.quad(ax, 0, t_half, limit=200)[0]
+        assert st.u[0, 0] == pytest.approx(ref, rel=1e-3, abs=1e-3 * a0)
+    oracle.md_steps(st, p, int(T / dt) + 10 - n_done)
+    assert abs(st.u[0, 0]) < 1e-3 * a0
+
+
+# ------------------------------------------------------------ dynamics ---
+
+def test_two_ion_coulomb_explosion_closed_form():
+    """Two ions from rest at separation d, eps = 0, non-relativistic:
+    t(r) = sqrt(mu d^3 / (2 K q1 q2)) [sqrt(x(x-1)) + ln(sqrt(x) + sqrt(x-1))],
+    x = r/d; the kinetic energy tends to K q1 q2 / d."""
+    q1, q2, m1, m2, d = 2, 3, 5000.0, 9000.0, 0.01
+    mu = m1 * m2 / (m1 + m2)
+    tc = math.sqrt(mu * d ** 3 / (2 * KC * q1 * q2))
+    dt = tc / 2000
+    x = np.array([[0.0, 0, 0], [d, 0, 0]])
+    # leap-frog start: u^{-1/2} = -h E(x^0) (closed-form two-body field)
+    f = KC * q1 * q2 / d ** 2
+    u = np.array([[+0.5 * dt * f / m1, 0, 0], [-0.5 * dt * f / m2, 0, 0]])
+    st = oracle.State(x, u, [q1, q2], [m1, m2], [1.0, 1.0])
+    p = oracle.make_params(a0=0.0, dt=dt, eps=0.0, env=oracle.ENV_FLAT)
+    for k in range(1, 5):
+        oracle.md_steps(st, p, 3000)
+        r = st.x[1, 0] - st.x[0, 0]
+        xr = r / d
+        t_pred = tc * (math.sqrt(xr * (xr - 1)) + math.log(math.sqrt(xr) + math.sqrt(xr - 1)))
+        assert t_pred == pytest.approx(st.step * dt, rel=2e-6)
+    dg = oracle.diagnostics(st, p)
+    assert dg["total"] == pytest.approx(KC * q1 * q2 / d, rel=1e-6)
+    np.testing.assert_allclose(dg["p"], 0.0, atol=1e-12 * m1 * abs(st.u[0, 0]))
+
+
+def test_momentum_and_energy_conservation_laser_off():
+    """Laser off: total momentum is conserved to rounding (pairwise forces);
+    the total-energy error of leap-frog is second order in dt.  Measured for
+    the 2k-particle, 2 nm, 0.1 nm-softening case over t = 4 (200 steps at
+    dt = 0.02): |dE| = 8.5e-4 of the final kinetic energy, 2.1e-4 at
+    dt = 0.01 (the electrons fall into the softened ion wells and gain ten
+    times the initial |PE|)."""
+    w = synth.plain_fp64_2k(0)
+    c = w.cluster
+    errs = []
+    for dt in (0.02, 0.01):
+        st = oracle.State(c.x, c.u, c.z, c.mass, c.w)
+        p = oracle.make_params(a0=0.0, dt=dt, eps=w.eps, env=oracle.ENV_FLAT)
+        d0 = oracle.diagnostics(st, p, nthreads=4)
+        oracle.md_steps(st, p, int(round(4.0 / dt)), nthreads=4)
+        d1 = oracle.diagnostics(st, p, nthreads=4)
+        pscale = np.abs((c.w * c.mass)[:, None] * st.u).sum()
+        assert np.abs(d1["p"] - d0["p"]).max() < 1e-12 * pscale
+        assert d1["ke"] > 5 * abs(d0["pe"])  # the electrons did move
+        errs.append(abs(d1["total"] - d0["total"]) / d1["ke"])
+    assert errs[0] < 1.5e-3
+    assert errs[0] / errs[1] == pytest.approx(4.0, rel=0.15)
+
+
+def _asymptotic_energy(x, u, q, m, kc):
+    """Spherical symmetry with no shell crossing: E_inf = KE + K q Q_in(r)/r."""
+    r = np.linalg.norm(x, axis=1)
+    order = np.argsort(r)
+    qin = np.empty_like(q)
+    qin[order] = np.cumsum(q[order]) - q[order]
+    ke = m * (u * u).sum(1) / (np.sqrt(1 + (u * u).sum(1)) + 1)
+    return ke + kc * q * qin / r
+
+
+def test_coulomb_explosion_spectrum_of_uniform_ion_sphere():
+    """Ions only, uniform ball, from rest, laser off (Sec. III: <E> = 3/5 E_max):
+    dN/dE ~ sqrt(E) on [0, E_max], E_max = K q Q / R0; CDF (E/E_max)^{3/2},
+    <E>/E_max = 3/5, <E^2>/E_max^2 = 3/7."""
+    n, r0, m, qv = 1200, synth.nm_to_len(2.0), synth.MASS_40AMU, 1
+    c = synth.make_cluster(5, n, 0, r0, qv, m)
+    q = c.w * c.z
+    e_max = KC * qv * q.sum() / r0
+    tau = math.sqrt(m * r0 ** 3 / (KC * qv * q.sum()))
+    st = oracle.State(c.x, c.u, c.z, c.mass, c.w)
+    p = oracle.make_params(a0=0.0, dt=tau / 40, eps=0.0, env=oracle.ENV_FLAT)
+    d0 = oracle.diagnostics(st, p, nthreads=4)
+    oracle.md_steps(st, p, 120, nthreads=4)  # t = 3 tau
+    e_mid = _asymptotic_energy(st.x, st.u, q, m, KC)
+    oracle.md_steps(st, p, 120, nthreads=4)  # t = 6 tau
+    e_inf = _asymptotic_energy(st.x, st.u, q, m, KC)
+    d1 = oracle.diagnostics(st, p, nthreads=4)
+    assert d1["total"] == pytest.approx(d0["total"], rel=1e-4)
+    # the asymptotic estimate has settled (no shell crossing after the start)
+    assert e_inf.mean() == pytest.approx(e_mid.mean(), rel=2e-3)
+    # the spectrum: moments and shape (finite-N edge: E_max uses N not N-1)
+    s = np.sort(e_inf / e_max)
+    # sampling std of the mean is 0.26/sqrt(N) = 0.008
+    assert s.mean() == pytest.approx(3 / 5, abs=0.02)
+    assert (s ** 2).mean() == pytest.approx(3 / 7, abs=0.02)
+    ks = stats.kstest(np.clip(s, 0, 1), lambda v: np.clip(v, 0, 1) ** 1.5)
+    assert ks.pvalue > 1e-3
