@@ -1,0 +1,229 @@
+/*
+ * md.h -- C ABI of the GB300 laser-cluster molecular-dynamics hot path.
+ *
+ * Method: Holkundkar, "Parallel Implementation of 3D Molecular Dynamic
+ * Simulation for Laser-Cluster Interaction", arXiv:1307.3711, Sec. II.
+ * Each step advances every particle of every cluster under
+ *   - the Coulomb field of all other charged particles (Sec. II, particle
+ *     mover paragraph), a softened O(N^2) direct sum computed in FP32 with
+ *     compensated (Kahan) accumulation per tile of sources,
+ *   - the spatially uniform laser field of Eqs. 3-9 (dipole approximation,
+ *     b0 = a0),
+ *   - a relativistic Boris kick and an FP64 position update ("standard Boris
+ *     leap frog", Sec. II).
+ *
+ * Units are the paper's (Sec. II): time in 1/omega, length in 1/k, velocity
+ * in c, u = gamma*beta, fields a = eE/(m_e omega c), b = eB/(m_e omega),
+ * charge in e, mass in m_e, energy in m_e c^2.  The Coulomb constant in these
+ * units is K_C = 2 pi r_e / lambda (the field of charge Q at distance r is
+ * K_C Q / r^2), computed from md_config.lambda_um.
+ *
+ * Conventions for every call:
+ *   - Every call returns md_status; nothing is thrown across the ABI.
+ *     md_last_error() gives a thread-local message for the last failure.
+ *   - The library owns the device memory of a context (allocated in md_init,
+ *     freed in md_destroy).  Host pointers passed in are read or written only
+ *     during the call.
+ *   - Calls that launch work are asynchronous on the context's stream;
+ *     md_diagnostics, md_get_particles, md_get_fields and md_sync
+ *     synchronise that stream and report device-side errors (an mbarrier wait
+ *     that ran out of its time budget: MD_ERR_TIMEOUT).
+ *   - A context is not thread-safe; use one per host thread.
+ */
+#ifndef MD_H
+#define MD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct md_ctx md_ctx;
+
+typedef enum {
+    MD_OK = 0,
+    MD_ERR_ARG = -1,        /* invalid argument (message says which) */
+    MD_ERR_OOM = -2,        /* device or pinned-host allocation failed */
+    MD_ERR_CUDA = -3,       /* a CUDA runtime call failed */
+    MD_ERR_TIMEOUT = -4,    /* a device-side wait exceeded its budget */
+    MD_ERR_NONFINITE = -5,  /* diagnostics found NaN/Inf in the state */
+    MD_ERR_STATE = -6,      /* call not valid in the current state */
+    MD_ERR_UNSUPPORTED = -7 /* feature not available in this build */
+} md_status;
+
+/* Temporal envelope of the laser (Eq. 3 and its readings). */
+enum {
+    MD_ENV_GAUSS = 0,       /* field exp[-2 ln2 (t-2tau)^2/tau^2]: intensity FWHM tau, peak at 2 tau */
+    MD_ENV_SIN2 = 1,        /* field sin^2(pi t / tau) on [0, tau] (tau = total length T), 0 outside */
+    MD_ENV_LITERAL_EQ3 = 2, /* field exp[-2.77 (t-2tau)^2/tau^2], Eq. 3 as printed */
+    MD_ENV_FLAT = 3         /* constant amplitude (continuous wave) */
+};
+
+/* Boundary of the simulation box (Sec. II, first paragraph). */
+enum {
+    MD_BOUNDARY_OPEN = 0,
+    MD_BOUNDARY_PERIODIC = 1, /* positions wrapped into the cube [-box/2, box/2)^3, no image forces */
+    MD_BOUNDARY_MIXED = 2     /* periodic while t < t_switch, open afterwards */
+};
+
+/* Particle kinds. */
+enum {
+    MD_KIND_ION = 0,      /* ion or neutral atom (charge z >= 0) */
+    MD_KIND_ELECTRON = 1, /* electron (z = -1) */
+    MD_KIND_INACTIVE = 2  /* unused slot: no charge, never moves */
+};
+
+/* Physics of one cluster, all in the paper's units. */
+typedef struct {
+    double a0;          /* peak field amplitude (Eq. 2 gives it from I0, lambda); b0 = a0 */
+    double tau;         /* envelope time: FWHM (GAUSS, LITERAL_EQ3) or total length T (SIN2) */
+    double t0;          /* time of step 0 */
+    double dt;          /* time step, > 0 */
+    double softening;   /* Plummer softening length eps, > 0 */
+    double box;         /* side of the periodic cube (PERIODIC / MIXED), e.g. 20 R0 */
+    double t_switch;    /* MIXED: time at which the boundary becomes open */
+    double lambda_um;   /* laser wavelength in micron (sets K_C); > 0 */
+    int32_t polarization; /* 0 linear (E along x, B along y), 1 circular (Eqs. 4-9) */
+    int32_t envelope;     /* MD_ENV_* */
+    int32_t boundary;     /* MD_BOUNDARY_* */
+    int32_t reserved;     /* must be 0 */
+} md_config;
+
+/* Host-side particle records of one cluster (structure of arrays, n records).
+ * For md_init / md_set_particles the arrays are read; md_get_particles writes
+ * the arrays whose pointer is non-NULL.  u is the momentum at the half step
+ * before the current step (leap-frog), i.e. u^{n-1/2} at step n; the first
+ * step uses the given u as u^{-1/2}. */
+typedef struct {
+    int64_t n;
+    double *x;       /* [n][3] positions */
+    double *u;       /* [n][3] u = gamma beta */
+    int32_t *z;      /* [n] charge number (electron -1, neutral 0) */
+    double *mass;    /* [n] mass of one real particle, m_e */
+    double *w;       /* [n] macro weight (real particles per record) */
+    uint8_t *kind;   /* [n] MD_KIND_* ; NULL on input: electron if z < 0, else ion */
+} md_particles;
+
+/* FP64 diagnostics at integer time t_n for the state (x^n, u^{n-1/2}):
+ * u^n = (u^{n-1/2} + u^{n+1/2})/2 with u^{n+1/2} the kick of step n (not
+ * applied to the state).  Energies in m_e c^2, momentum in m_e c. */
+typedef struct {
+    int64_t step;
+    double t;
+    double ke;            /* sum over active records of w m (gamma - 1) */
+    double ke_ions;       /* kind ION */
+    double ke_electrons;  /* kind ELECTRON */
+    double pe;            /* 1/2 sum_i Q_i phi_i, softened */
+    double total;         /* ke + pe */
+    double p[3];          /* sum of w m u */
+    int64_t n_active;
+    int64_t n_nonfinite;  /* records with a NaN/Inf position or momentum */
+    int64_t charge_count[16];   /* ION records by charge state z (z >= 15 in the last bin) */
+    double charge_weight[16];   /* the same, weighted by w */
+} md_diag;
+
+/* Kernel configuration of the fused Coulomb/push kernel.  md_autotune picks
+ * one by timing; md_set_tuning forces one (must be an entry of
+ * md_tuning_list). */
+typedef struct {
+    int32_t threads;    /* threads per CTA */
+    int32_t r;          /* i-particles per thread (register blocking) */
+    int32_t tile;       /* sources per shared-memory stage */
+    int32_t ctas_per_sm;/* persistent CTAs per SM (0: as many as fit) */
+    int32_t jsplit;     /* source segments per i-block (0: chosen for load balance); the
+                           partial fields of the segments go to a library scratch buffer
+                           and the last segment to finish sums them and pushes */
+} md_tuning;
+
+/* ---- context life cycle -------------------------------------------------
+ * md_init: creates a context holding n_clusters independent clusters (a
+ * batched parameter scan when > 1), uploads their particles and returns it
+ * in *out.  cfgs[c] and parts[c] describe cluster c.  stream: a cudaStream_t
+ * to launch on (NULL: the library creates its own).  The device must be an
+ * sm_103 GPU.  Errors: MD_ERR_ARG (n_clusters < 1, n < 1, dt/softening/
+ * lambda <= 0, bad enum, kind/z mismatch), MD_ERR_OOM, MD_ERR_CUDA. */
+md_status md_init(md_ctx **out, const md_config *cfgs, int32_t n_clusters,
+                  const md_particles *parts, void *stream);
+void md_destroy(md_ctx *ctx);
+const char *md_last_error(void);
+
+/* md_step: advances every cluster by nsteps full steps (Sec. II): softened
+ * Coulomb field at x^n + laser at t_n, relativistic Boris kick, FP64 drift,
+ * boundary.  One fused kernel per step; runs of steps are replayed from a
+ * captured CUDA graph.  Asynchronous.  nsteps >= 0. */
+md_status md_step(md_ctx *ctx, int32_t nsteps);
+
+/* md_sync: waits for the context's stream and reports device-side errors. */
+md_status md_sync(md_ctx *ctx);
+
+/* md_diagnostics: FP64 energies, momentum and charge-state counts of cluster
+ * `cluster` at the current step (synchronous; out is caller-owned). */
+md_status md_diagnostics(md_ctx *ctx, int32_t cluster, md_diag *out);
+
+/* md_get_particles / md_set_particles: copy cluster `cluster`'s records to /
+ * from host arrays (n must equal the cluster's record count).  get is
+ * synchronous; set is asynchronous with respect to the caller's later calls
+ * but reads the host arrays before it returns (staged through pinned memory). */
+md_status md_get_particles(md_ctx *ctx, int32_t cluster, md_particles *out);
+md_status md_set_particles(md_ctx *ctx, int32_t cluster, const md_particles *in);
+
+/* md_get_fields: the Coulomb field (without the laser) and, if phi != NULL,
+ * the potential K_C sum_{j!=i} Q_j / sqrt(r^2+eps^2) at the current positions
+ * of cluster `cluster`, computed by the same FP32/Kahan sum as md_step.
+ * e: host [n][3], phi: host [n] or NULL.  Synchronous. */
+md_status md_get_fields(md_ctx *ctx, int32_t cluster, double *e, double *phi);
+
+/* Step counter of the context (steps taken since md_init). Synchronous. */
+md_status md_get_step(md_ctx *ctx, int64_t *step);
+
+/* ---- tuning -------------------------------------------------------------
+ * md_tuning_list: writes up to cap entries of the compiled kernel
+ * configurations into list (may be NULL) and returns their number.
+ * md_set_tuning: uses the given configuration from now on.
+ * md_get_tuning: the configuration in use.
+ * md_autotune: times every configuration over `steps` steps on the
+ * context's own state (restored afterwards) and keeps the fastest; the
+ * per-configuration mean step times in ms go to times_ms (cap entries, may be
+ * NULL). */
+int32_t md_tuning_list(md_tuning *list, int32_t cap);
+md_status md_set_tuning(md_ctx *ctx, const md_tuning *t);
+md_status md_get_tuning(md_ctx *ctx, md_tuning *t);
+md_status md_autotune(md_ctx *ctx, int32_t steps, double *times_ms, int32_t cap);
+
+/* ---- stateless field evaluation on caller device buffers -----------------
+ * md_coulomb_field_device: field (and potential) at nt targets from ns
+ * sources, the FP32/Kahan direct sum of Sec. II on device memory the caller
+ * owns.
+ *   src:  device float4[ns] = (x, y, z, K_C * Q) per source (16-byte aligned)
+ *   tgt:  device float4[nt] = (x, y, z, unused) per target
+ *   eps2: softening squared
+ *   self_offset: target i is source i + self_offset (its potential self term
+ *         is removed), or -1 if targets are not sources
+ *   e:    device double[nt][3] output field; phi: device double[nt] or NULL
+ *   stream: cudaStream_t (NULL = legacy default stream).  Asynchronous.
+ * Errors: MD_ERR_ARG for NULL/unaligned pointers, ns < 0, nt < 0. */
+md_status md_coulomb_field_device(const void *src, int64_t ns, const void *tgt,
+                                  int64_t nt, float eps2, int64_t self_offset,
+                                  double *e, double *phi, void *stream);
+
+/* ---- helpers for SI inputs (Sec. II) ------------------------------------ */
+double md_coulomb_constant(double lambda_um);                  /* K_C = 2 pi r_e / lambda */
+double md_a0_from_intensity(double intensity_wcm2, double lambda_um); /* Eq. 2 */
+double md_n_atoms(double r0, double r_wigner_seitz);           /* Eq. 1 */
+
+/* Measurement helper: FP32 fused multiply-adds per second (lane operations)
+ * of the current device, from kernels of 8 independent FMA chains per thread
+ * on 8 x SMs CTAs of 256 threads: *ffma_per_s with scalar fma.rn.f32,
+ * *packed_fma_per_s (may be NULL) with packed fma.rn.f32x2.  Synchronous on
+ * `stream`.  The denominators of the FP32 roofline fraction. */
+md_status md_measure_fp32_peak(double *ffma_per_s, double *packed_fma_per_s, void *stream);
+
+/* Number of SMs and the device name of the current device (for reports). */
+md_status md_device_info(int32_t *sm_count, char *name, int32_t name_cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MD_H */

@@ -1,0 +1,670 @@
+// md_device.cuh -- device code of the laser-cluster MD hot path for sm_103a.
+//
+// Method (Holkundkar, arXiv:1307.3711, Sec. II): every particle moves under the
+// Coulomb field of all other charged particles plus the spatially uniform laser
+// field of Eqs. 3-9 (b0 = a0), advanced by a relativistic Boris leap-frog.
+//
+// Design for GB300 (not the paper's OpenMP decomposition):
+//   * the j-stream is an SoA float4 array (x, y, z, K_C*Q) double-buffered
+//     across steps; tiles of it are staged into shared memory by 1-D TMA bulk
+//     copies (cp.async.bulk) completing on an mbarrier, STAGES deep;
+//   * each thread keeps R i-particles in registers (register blocking), every
+//     source is one broadcast LDS.128 shared by R pair evaluations;
+//   * one pair is 12 FP32-pipe instructions (3 FADD, 3 FFMA, 3 FMUL, 3 FFMA)
+//     plus one MUFU.RSQ (rsqrt.approx.ftz.f32);
+//   * FP32 partial sums are folded into Kahan-compensated FP32 sums once per
+//     tile, so the compensation costs ~12/TILE instructions per pair;
+//   * the laser field and the Boris kick are fused into the epilogue: the
+//     kick increment is evaluated in FP32, the integrator state (x, u) and the
+//     drift are FP64;
+//   * work units (cluster, i-block) are handed out by an atomic ticket to a
+//     persistent grid, so uneven clusters of a parameter scan share one launch;
+//     the last CTA to finish resets the ticket and advances the step counter,
+//     so a captured CUDA graph of many steps replays without host work.
+// Every mbarrier wait is bounded by a clock64 budget; on expiry the kernel sets
+// an error bit, drains its own copies (again bounded) and returns.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "md_types.cuh"
+
+namespace md {
+
+// ------------------------------------------------------------------ PTX --
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// 1-D TMA bulk copy global -> shared, completion counted on `bar` in bytes.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for phase `parity` of `bar`: false after kWaitBudget cycles.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > kWaitBudget) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ float rsqrt_mufu(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// --------------------------------------------------------------- laser --
+
+// Field-amplitude envelope (Eq. 3 and its readings): 0 Gaussian with
+// intensity FWHM tau peaking at 2 tau; 1 sin^2(pi t/tau) on [0, tau];
+// 2 exp[-2.77 (t-2tau)^2/tau^2] as printed; 3 flat.
+__device__ __forceinline__ double envelope(double t, int kind, double tau) {
+  if (kind == 0) {
+    const double s = (t - 2.0 * tau) / tau;
+    return exp(-1.3862943611198906 * s * s);  // 2 ln 2
+  }
+  if (kind == 1) {
+    if (t < 0.0 || t > tau) return 0.0;
+    const double s = sinpi(t / tau);
+    return s * s;
+  }
+  if (kind == 2) {
+    const double s = (t - 2.0 * tau) / tau;
+    return exp(-2.77 * s * s);
+  }
+  return 1.0;
+}
+
+// Eqs. 4-9 at time t: linear E = A sin t x, B = A sin t y; circular adds
+// E_y = A sin(t + 3pi/2) = -A cos t and B_x = A sin(t + pi/2) = A cos t.
+// out = (a_x, a_y, a_z, b_x, b_y, b_z).
+__device__ __forceinline__ void laser_field(const ClusterDev& c, double t, float* out) {
+  const double amp = c.a0 * envelope(t, c.env, c.tau);
+  double sn, cs;
+  sincos(t, &sn, &cs);
+  const double circ = c.pol ? 1.0 : 0.0;
+  out[0] = static_cast<float>(amp * sn);
+  out[1] = static_cast<float>(-circ * amp * cs);
+  out[2] = 0.0f;
+  out[3] = static_cast<float>(circ * amp * cs);
+  out[4] = static_cast<float>(amp * sn);
+  out[5] = 0.0f;
+}
+
+// ---------------------------------------------------------------- Boris --
+
+// Increment du = u^{n+1/2} - u^{n-1/2} of one relativistic Boris kick
+// (half electric kick, rotation with tan(theta/2) = h|b|/gamma, half
+// electric kick), h = (q/m) dt / 2, evaluated in FP32.
+__device__ __forceinline__ void boris_increment(float ux, float uy, float uz, float ex, float ey,
+                                                float ez, float bx, float by, float bz, float h,
+                                                float& dux, float& duy, float& duz) {
+  const float hex = h * ex, hey = h * ey, hez = h * ez;
+  const float mx = ux + hex, my = uy + hey, mz = uz + hez;
+  const float ginv = rsqrtf(1.0f + mx * mx + my * my + mz * mz);
+  const float tx = h * bx * ginv, ty = h * by * ginv, tz = h * bz * ginv;
+  const float f = 2.0f / (1.0f + tx * tx + ty * ty + tz * tz);
+  const float sx = f * tx, sy = f * ty, sz = f * tz;
+  const float px = mx + (my * tz - mz * ty);
+  const float py = my + (mz * tx - mx * tz);
+  const float pz = mz + (mx * ty - my * tx);
+  // u+ - u- = u' x s ; total increment = 2 h E + u' x s
+  dux = 2.0f * hex + (py * sz - pz * sy);
+  duy = 2.0f * hey + (pz * sx - px * sz);
+  duz = 2.0f * hez + (px * sy - py * sx);
+}
+
+__device__ __forceinline__ double wrap_periodic(double v, double box) {
+  return v - box * floor((v + 0.5 * box) / box);
+}
+
+// ------------------------------------------------------- pair kernel body --
+
+template <int R, bool POT>
+struct Acc {
+  float ax[R], ay[R], az[R], ap[R];  // FP32 partial over the current tile
+  float sx[R], sy[R], sz[R], sp[R];  // Kahan sums
+  float cx[R], cy[R], cz[R], cp[R];  // Kahan compensations
+
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      ax[r] = ay[r] = az[r] = ap[r] = 0.0f;
+      sx[r] = sy[r] = sz[r] = sp[r] = 0.0f;
+      cx[r] = cy[r] = cz[r] = cp[r] = 0.0f;
+    }
+  }
+};
+
+__device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
+  const float y = v - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+// One source against R targets: acc += Q_j (x_j - x_i) / (r^2 + eps^2)^{3/2}
+// (and phi += Q_j / sqrt(r^2 + eps^2)); Q_j already carries K_C.
+template <int R, bool POT>
+__device__ __forceinline__ void pair(const float4 p, const float (&xi)[R], const float (&yi)[R],
+                                     const float (&zi)[R], float eps2, Acc<R, POT>& a) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const float dx = p.x - xi[r];
+    const float dy = p.y - yi[r];
+    const float dz = p.z - zi[r];
+    float r2 = fmaf(dx, dx, eps2);
+    r2 = fmaf(dy, dy, r2);
+    r2 = fmaf(dz, dz, r2);
+    const float ri = rsqrt_mufu(r2);
+    const float qr = p.w * ri;
+    const float ri2 = ri * ri;
+    const float s = qr * ri2;
+    a.ax[r] = fmaf(dx, s, a.ax[r]);
+    a.ay[r] = fmaf(dy, s, a.ay[r]);
+    a.az[r] = fmaf(dz, s, a.az[r]);
+    if (POT) a.ap[r] += qr;
+  }
+}
+
+template <int R, bool POT>
+__device__ __forceinline__ void fold(Acc<R, POT>& a) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    kahan_add(a.sx[r], a.cx[r], a.ax[r]);
+    kahan_add(a.sy[r], a.cy[r], a.ay[r]);
+    kahan_add(a.sz[r], a.cz[r], a.az[r]);
+    a.ax[r] = a.ay[r] = a.az[r] = 0.0f;
+    if (POT) {
+      kahan_add(a.sp[r], a.cp[r], a.ap[r]);
+      a.ap[r] = 0.0f;
+    }
+  }
+}
+
+// Shared-memory staging of the j-stream.
+template <int TILE, int STAGES>
+struct Stage {
+  alignas(128) float4 tile[STAGES][TILE];
+  alignas(8) uint64_t full[STAGES];
+};
+
+template <int TILE, int STAGES>
+__device__ __forceinline__ void issue_tile(Stage<TILE, STAGES>& sm, unsigned g, const float4* src,
+                                           long long ns, int t) {
+  const int s = static_cast<int>(g % STAGES);
+  const long long j0 = static_cast<long long>(t) * TILE;
+  const long long rem = ns - j0;
+  const uint32_t cnt = static_cast<uint32_t>(rem < TILE ? rem : TILE);
+  fence_proxy_async_smem();
+  mbar_arrive_expect_tx(&sm.full[s], cnt * 16u);
+  bulk_g2s(&sm.tile[s][0], src + j0, cnt * 16u, &sm.full[s]);
+}
+
+// Sum over all ns sources for the R targets held by this thread, streaming the
+// sources through the STAGES-deep TMA ring.  `it` counts tiles this CTA has
+// consumed so far (sets the barrier phases).  Returns false (uniformly across
+// the CTA) if a wait ran out of budget; the error bit is then set and this
+// CTA's copies in flight have been waited for (bounded).
+template <int THREADS, int R, int TILE, int STAGES, bool POT>
+__device__ __forceinline__ bool sum_sources(Stage<TILE, STAGES>& sm, unsigned& it,
+                                            const float4* __restrict__ src, long long ns,
+                                            const float (&xi)[R], const float (&yi)[R],
+                                            const float (&zi)[R], float eps2, Acc<R, POT>& acc,
+                                            int* err, int* s_abort) {
+  const int ntiles = static_cast<int>((ns + TILE - 1) / TILE);
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < STAGES && k < ntiles; ++k) issue_tile<TILE, STAGES>(sm, it + k, src, ns, k);
+  }
+  for (int t = 0; t < ntiles; ++t) {
+    const unsigned g = it + t;
+    const int s = static_cast<int>(g % STAGES);
+    const uint32_t parity = (g / STAGES) & 1u;
+    if (!mbar_wait(&sm.full[s], parity)) {
+      atomicOr(err, kErrTimeout);
+      *s_abort = 1;
+    }
+    if (!*reinterpret_cast<volatile int*>(s_abort)) {
+      const float4* tile = sm.tile[s];
+      const long long rem = ns - static_cast<long long>(t) * TILE;
+      const int cnt = static_cast<int>(rem < TILE ? rem : TILE);
+      int j = 0;
+      for (; j + 8 <= cnt; j += 8) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) pair<R, POT>(tile[j + k], xi, yi, zi, eps2, acc);
+        if (POT) {
+          // potential terms of one species share a sign: fold them often so
+          // the FP32 partial stays small against a cancelling total
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            kahan_add(acc.sp[r], acc.cp[r], acc.ap[r]);
+            acc.ap[r] = 0.0f;
+          }
+        }
+      }
+      for (; j < cnt; ++j) pair<R, POT>(tile[j], xi, yi, zi, eps2, acc);
+      fold<R, POT>(acc);
+    }
+    __syncthreads();
+    if (*reinterpret_cast<volatile int*>(s_abort)) {
+      if (threadIdx.x == 0) {
+        const int last = (t + STAGES < ntiles) ? t + STAGES : ntiles;
+        for (int k = t + 1; k < last; ++k) {
+          const unsigned gk = it + k;
+          mbar_wait(&sm.full[gk % STAGES], (gk / STAGES) & 1u);
+        }
+      }
+      __syncthreads();
+      return false;
+    }
+    if (threadIdx.x == 0 && t + STAGES < ntiles)
+      issue_tile<TILE, STAGES>(sm, it + t + STAGES, src, ns, t + STAGES);
+  }
+  it += static_cast<unsigned>(ntiles);
+  return true;
+}
+
+// ------------------------------------------------------------ step kernel --
+
+// Laser + Boris kick (FP32 increment) + FP64 drift + boundary for record i
+// with Coulomb field (ex, ey, ez); writes x, u and the next j-stream entry.
+__device__ __forceinline__ void push_record(const StepArgs& a, const ClusterDev& c, long long i,
+                                            double ex, double ey, double ez, const float* las,
+                                            double t_next, const float4* cur, float4* nxt) {
+  double X = a.x[i], Y = a.y[i], Z = a.z[i];
+  double Ux = a.ux[i], Uy = a.uy[i], Uz = a.uz[i];
+  const float h = 0.5f * static_cast<float>(c.dt) * a.qm[i];
+  float dux, duy, duz;
+  boris_increment(static_cast<float>(Ux), static_cast<float>(Uy), static_cast<float>(Uz),
+                  static_cast<float>(ex) + las[0], static_cast<float>(ey) + las[1],
+                  static_cast<float>(ez) + las[2], las[3], las[4], las[5], h, dux, duy, duz);
+  Ux += static_cast<double>(dux);
+  Uy += static_cast<double>(duy);
+  Uz += static_cast<double>(duz);
+  const double ginv = rsqrt(1.0 + (Ux * Ux + Uy * Uy + Uz * Uz));
+  X += c.dt * Ux * ginv;
+  Y += c.dt * Uy * ginv;
+  Z += c.dt * Uz * ginv;
+  const bool wrap = (c.boundary == 1) || (c.boundary == 2 && t_next < c.t_switch);
+  if (wrap) {
+    X = wrap_periodic(X, c.box);
+    Y = wrap_periodic(Y, c.box);
+    Z = wrap_periodic(Z, c.box);
+  }
+  a.x[i] = X;
+  a.y[i] = Y;
+  a.z[i] = Z;
+  a.ux[i] = Ux;
+  a.uy[i] = Uy;
+  a.uz[i] = Uz;
+  nxt[i] = make_float4(static_cast<float>(X), static_cast<float>(Y), static_cast<float>(Z),
+                       cur[i].w);
+}
+
+// One full MD step for every work unit (cluster, i-block): field at x^n from
+// all sources of the cluster, laser at t_n, Boris kick, FP64 drift, boundary,
+// new j-stream entry.  Persistent: CTAs take units from an atomic ticket.
+template <int THREADS, int R, int TILE, int STAGES>
+__global__ void __launch_bounds__(THREADS) k_step(const StepArgs a) {
+  __shared__ Stage<TILE, STAGES> sm;
+  __shared__ int s_unit, s_abort, s_last;
+  __shared__ float s_las[6];
+
+  const long long step = __ldcg(a.step);
+  const float4* __restrict__ cur = (step & 1) ? a.posq1 : a.posq0;
+  float4* __restrict__ nxt = (step & 1) ? a.posq0 : a.posq1;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) mbar_init(&sm.full[s], 1);
+    fence_mbar_init();
+    s_abort = 0;
+  }
+  __syncthreads();
+
+  unsigned it = 0;
+  for (;;) {
+    if (threadIdx.x == 0) s_unit = static_cast<int>(atomicAdd(a.ticket, 1u));
+    __syncthreads();
+    const int u = s_unit;
+    if (u >= a.n_units) break;
+    const Unit un = a.units[u];
+    const ClusterDev c = a.cl[un.cluster];
+    const double t_n = c.t0 + static_cast<double>(step) * c.dt;
+    if (threadIdx.x == 0) laser_field(c, t_n, s_las);
+
+    const long long i0 = c.off + static_cast<long long>(un.block) * (THREADS * R);
+    const long long iend = c.off + c.n_pad;
+    const long long j0 = static_cast<long long>(un.seg) * c.seg_len;
+    const long long jrem = c.n_pad - j0;
+    const long long jn = jrem < c.seg_len ? jrem : c.seg_len;
+    float xi[R], yi[R], zi[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const long long i = i0 + threadIdx.x + r * THREADS;
+      const float4 p = (i < iend) ? cur[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+      xi[r] = p.x;
+      yi[r] = p.y;
+      zi[r] = p.z;
+    }
+    Acc<R, false> acc;
+    acc.zero();
+    if (!sum_sources<THREADS, R, TILE, STAGES, false>(sm, it, cur + c.off + j0, jn, xi, yi, zi,
+                                                      c.eps2, acc, a.err, &s_abort))
+      return;
+
+    const double t_next = t_n + c.dt;
+    if (c.nseg == 1) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const long long i = i0 + threadIdx.x + r * THREADS;
+        if (i >= iend) continue;
+        // field at i is -(sum of Q (x_j - x_i)/r^3); the Kahan total is s - c
+        push_record(a, c, i, -(static_cast<double>(acc.sx[r]) - acc.cx[r]),
+                    -(static_cast<double>(acc.sy[r]) - acc.cy[r]),
+                    -(static_cast<double>(acc.sz[r]) - acc.cz[r]), s_las, t_next, cur, nxt);
+      }
+    } else {
+      // this unit covers one segment of the sources: publish the partial
+      // field; the last of the nseg units of this i-block sums the partials
+      // in segment order (deterministic) and pushes
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const long long i = i0 + threadIdx.x + r * THREADS;
+        if (i >= iend) continue;
+        double* p = a.part + 3 * (static_cast<long long>(un.seg) * a.n_total + i);
+        __stcg(p + 0, -(static_cast<double>(acc.sx[r]) - acc.cx[r]));
+        __stcg(p + 1, -(static_cast<double>(acc.sy[r]) - acc.cy[r]));
+        __stcg(p + 2, -(static_cast<double>(acc.sz[r]) - acc.cz[r]));
+      }
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const unsigned prev = atomicAdd(a.iblk_cnt + un.ib, 1u);
+        s_last = (prev == static_cast<unsigned>(c.nseg - 1));
+        if (s_last) atomicExch(a.iblk_cnt + un.ib, 0u);
+      }
+      __syncthreads();
+      if (s_last) {
+        __threadfence();
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const long long i = i0 + threadIdx.x + r * THREADS;
+          if (i >= iend) continue;
+          double ex = 0.0, ey = 0.0, ez = 0.0;
+          for (int sg = 0; sg < c.nseg; ++sg) {
+            const double* p = a.part + 3 * (static_cast<long long>(sg) * a.n_total + i);
+            ex += __ldcg(p + 0);
+            ey += __ldcg(p + 1);
+            ez += __ldcg(p + 2);
+          }
+          push_record(a, c, i, ex, ey, ez, s_las, t_next, cur, nxt);
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  // last CTA out: reset the ticket, advance the step counter
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(a.done, 1u);
+    if (prev == gridDim.x - 1) {
+      atomicExch(a.ticket, 0u);
+      atomicExch(a.done, 0u);
+      __threadfence();
+      *reinterpret_cast<volatile long long*>(a.step) = step + 1;
+    }
+  }
+}
+
+// ----------------------------------------------------------- field kernel --
+
+// Field (and potential) at targets from sources; one target block per CTA.
+template <int THREADS, int R, int TILE, int STAGES, bool POT>
+__global__ void __launch_bounds__(THREADS) k_field(const FieldArgs a) {
+  __shared__ Stage<TILE, STAGES> sm;
+  __shared__ int s_abort;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) mbar_init(&sm.full[s], 1);
+    fence_mbar_init();
+    s_abort = 0;
+  }
+  __syncthreads();
+  const long long i0 = static_cast<long long>(blockIdx.x) * (THREADS * R);
+  float xi[R], yi[R], zi[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const long long i = i0 + threadIdx.x + r * THREADS;
+    const float4 p = (i < a.nt) ? a.tgt[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    xi[r] = p.x;
+    yi[r] = p.y;
+    zi[r] = p.z;
+  }
+  Acc<R, POT> acc;
+  acc.zero();
+  unsigned it = 0;
+  if (!sum_sources<THREADS, R, TILE, STAGES, POT>(sm, it, a.src, a.ns, xi, yi, zi, a.eps2, acc,
+                                                   a.err, &s_abort))
+    return;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const long long i = i0 + threadIdx.x + r * THREADS;
+    if (i >= a.nt) continue;
+    a.e[3 * i + 0] = -(static_cast<double>(acc.sx[r]) - acc.cx[r]);
+    a.e[3 * i + 1] = -(static_cast<double>(acc.sy[r]) - acc.cy[r]);
+    a.e[3 * i + 2] = -(static_cast<double>(acc.sz[r]) - acc.cz[r]);
+    if (POT && a.phi) {
+      double ph = static_cast<double>(acc.sp[r]) - acc.cp[r];
+      if (a.self_offset >= 0) {
+        const long long js = i + a.self_offset;
+        if (js < a.ns) ph -= static_cast<double>(a.src[js].w * rsqrt_mufu(a.eps2));
+      }
+      a.phi[i] = ph;
+    }
+  }
+}
+
+// ------------------------------------------------------- diagnostics (K4) --
+
+template <int THREADS>
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < THREADS / 32; ++k) s += red[k];
+  return s;  // valid in thread 0
+}
+
+// Per-block FP64 partial sums of the diagnostics of one cluster.
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) k_diag_partial(const DiagArgs a) {
+  __shared__ double red[THREADS / 32];
+  const long long step = __ldcg(a.step);
+  const double t_n = a.c.t0 + static_cast<double>(step) * a.c.dt;
+  float las[6];
+  laser_field(a.c, t_n, las);
+  const float hq = 0.5f * static_cast<float>(a.c.dt);
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  long long na = 0, nbad = 0;
+  long long hist[kHistBins];
+  double histw[kHistBins];
+#pragma unroll
+  for (int k = 0; k < kHistBins; ++k) {
+    hist[k] = 0;
+    histw[k] = 0.0;
+  }
+  for (long long k = static_cast<long long>(blockIdx.x) * THREADS + threadIdx.x; k < a.c.n;
+       k += static_cast<long long>(gridDim.x) * THREADS) {
+    const long long i = a.c.off + k;
+    const unsigned char kd = a.kind[i];
+    if (kd == 2) continue;
+    ++na;
+    const double X = a.x[i], Y = a.y[i], Z = a.z[i];
+    const double Ux = a.ux[i], Uy = a.uy[i], Uz = a.uz[i];
+    if (!(isfinite(X) && isfinite(Y) && isfinite(Z) && isfinite(Ux) && isfinite(Uy) &&
+          isfinite(Uz))) {
+      ++nbad;
+      continue;
+    }
+    float dux, duy, duz;
+    boris_increment(static_cast<float>(Ux), static_cast<float>(Uy), static_cast<float>(Uz),
+                    static_cast<float>(a.e[3 * k]) + las[0],
+                    static_cast<float>(a.e[3 * k + 1]) + las[1],
+                    static_cast<float>(a.e[3 * k + 2]) + las[2], las[3], las[4], las[5],
+                    hq * a.qm[i], dux, duy, duz);
+    const double mx = Ux + 0.5 * dux, my = Uy + 0.5 * duy, mz = Uz + 0.5 * duz;
+    const double uu = mx * mx + my * my + mz * mz;
+    const double wm = a.w[i] * a.mass[i];
+    const double ke = wm * uu / (sqrt(1.0 + uu) + 1.0);
+    acc[0] += ke;
+    if (kd == 1) acc[2] += ke; else acc[1] += ke;
+    acc[3] += 0.5 * a.w[i] * a.zq[i] * a.phi[k];
+    acc[4] += wm * mx;
+    acc[5] += wm * my;
+    acc[6] += wm * mz;
+    if (kd == 0) {
+      int zb = a.zq[i];
+      zb = zb < 0 ? 0 : (zb >= kHistBins ? kHistBins - 1 : zb);
+      hist[zb] += 1;
+      histw[zb] += a.w[i];
+    }
+  }
+  DiagPartial* out = a.part + blockIdx.x;
+  for (int k = 0; k < 8; ++k) {
+    const double s = block_sum<THREADS>(acc[k], red);
+    if (threadIdx.x == 0) out->v[k] = s;
+  }
+  {
+    double s = block_sum<THREADS>(static_cast<double>(na), red);
+    if (threadIdx.x == 0) out->cnt[0] = static_cast<long long>(s);
+    s = block_sum<THREADS>(static_cast<double>(nbad), red);
+    if (threadIdx.x == 0) out->cnt[1] = static_cast<long long>(s);
+  }
+  for (int k = 0; k < kHistBins; ++k) {
+    double s = block_sum<THREADS>(static_cast<double>(hist[k]), red);
+    if (threadIdx.x == 0) out->hist[k] = static_cast<long long>(s);
+    s = block_sum<THREADS>(histw[k], red);
+    if (threadIdx.x == 0) out->histw[k] = s;
+  }
+}
+
+// Sums the per-block partials in block order (deterministic); one thread per
+// component.
+__global__ void k_diag_final(const DiagPartial* __restrict__ part, int nblocks,
+                             DiagPartial* __restrict__ out) {
+  const int k = threadIdx.x;
+  if (k < 8) {
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += part[b].v[k];
+    out->v[k] = s;
+  } else if (k < 10) {
+    long long s = 0;
+    for (int b = 0; b < nblocks; ++b) s += part[b].cnt[k - 8];
+    out->cnt[k - 8] = s;
+  } else if (k < 10 + kHistBins) {
+    long long s = 0;
+    for (int b = 0; b < nblocks; ++b) s += part[b].hist[k - 10];
+    out->hist[k - 10] = s;
+  } else if (k < 10 + 2 * kHistBins) {
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += part[b].histw[k - 10 - kHistBins];
+    out->histw[k - 10 - kHistBins] = s;
+  }
+}
+
+// ------------------------------------------------------------ layout glue --
+
+// Scatter host-layout records ([n][3] x/u, z, mass, w, kind) into the SoA
+// device state of one cluster starting at record `off`; writes the current
+// j-stream entry (x, y, z, K_C w z).
+
+__global__ void k_upload(const UploadArgs a) {
+  const long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= a.n) return;
+  const long long i = a.off + k;
+  const unsigned char kd = a.hkind[k];
+  const double X = a.hx[3 * k], Y = a.hx[3 * k + 1], Z = a.hx[3 * k + 2];
+  a.x[i] = X;
+  a.y[i] = Y;
+  a.z[i] = Z;
+  a.ux[i] = a.hu[3 * k];
+  a.uy[i] = a.hu[3 * k + 1];
+  a.uz[i] = a.hu[3 * k + 2];
+  const int zq = a.hz[k];
+  a.zq[i] = zq;
+  a.mass[i] = a.hmass[k];
+  a.w[i] = a.hw[k];
+  a.kind[i] = kd;
+  const bool live = (kd != 2);
+  a.qm[i] = live ? static_cast<float>(zq / a.hmass[k]) : 0.0f;
+  const float q = live ? static_cast<float>(a.kc * a.hw[k] * zq) : 0.0f;
+  const float4 p = make_float4(static_cast<float>(X), static_cast<float>(Y), static_cast<float>(Z), q);
+  const long long step = __ldcg(a.step);
+  if (step & 1) a.posq1[i] = p; else a.posq0[i] = p;
+}
+
+__global__ void k_download(const DownloadArgs a) {
+  const long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= a.n) return;
+  const long long i = a.off + k;
+  a.hx[3 * k] = a.x[i];
+  a.hx[3 * k + 1] = a.y[i];
+  a.hx[3 * k + 2] = a.z[i];
+  a.hu[3 * k] = a.ux[i];
+  a.hu[3 * k + 1] = a.uy[i];
+  a.hu[3 * k + 2] = a.uz[i];
+  a.hz[k] = a.zq[i];
+  a.hmass[k] = a.mass[i];
+  a.hw[k] = a.w[i];
+  a.hkind[k] = a.kind[i];
+}
+
+}  // namespace md

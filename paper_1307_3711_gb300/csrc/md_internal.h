@@ -1,0 +1,37 @@
+// md_internal.h -- interface between the kernel instantiations (md_kernels.cu)
+// and the host runtime (md_runtime.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "md_types.cuh"
+
+namespace md {
+
+// One compiled configuration of the fused step kernel.
+struct KernelConfig {
+  int threads;
+  int r;
+  int tile;
+  int stages;
+  cudaError_t (*launch_step)(const StepArgs& a, int grid, cudaStream_t s);
+  cudaError_t (*max_blocks_per_sm)(int* out);
+};
+
+const KernelConfig* step_configs(int* count);
+
+// Field (and potential) at nt targets from ns sources (FP32/Kahan direct sum).
+cudaError_t launch_field(const FieldArgs& a, bool potential, cudaStream_t s);
+
+// Diagnostics: per-block partials then a deterministic final sum.
+constexpr int kDiagThreads = 256;
+cudaError_t launch_diag(const DiagArgs& a, int blocks, DiagPartial* out, cudaStream_t s);
+
+// FP32 peak probe: blocks x 256 threads x iters x 128 FFMA each (scalar
+// fma.rn.f32, or packed fma.rn.f32x2 doing two lanes per instruction).
+cudaError_t launch_ffma_probe(int blocks, int iters, bool packed, float* sink, cudaStream_t s);
+
+cudaError_t launch_upload(const UploadArgs& a, cudaStream_t s);
+cudaError_t launch_download(const DownloadArgs& a, cudaStream_t s);
+
+}  // namespace md

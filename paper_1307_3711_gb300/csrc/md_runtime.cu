@@ -1,0 +1,971 @@
+// md_runtime.cu -- host runtime behind the C ABI of include/md.h: context
+// life cycle, device layout, graph-replayed stepping, autotuner, diagnostics.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "md.h"
+#include "md_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+md_status fail(md_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+md_status cuda_fail(cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation)
+    return fail(MD_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+  return fail(MD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define MD_CUDA(call)                                  \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kClassicalElectronRadius = 2.8179403262e-15;  // m, CODATA 2018
+constexpr int kGraphSteps = 16;
+
+template <class T>
+cudaError_t dev_alloc(T** p, size_t count) {
+  return cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(count, 1) * sizeof(T));
+}
+
+}  // namespace
+
+struct md_ctx {
+  int device = 0;
+  int sm_count = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+
+  int n_clusters = 0;
+  std::vector<md::ClusterDev> cl;
+  std::vector<double> kc;  // K_C of each cluster
+  long long n_total = 0;   // padded records of all clusters
+  long long max_n = 0;     // largest real record count of a cluster
+
+  md::ClusterDev* d_cl = nullptr;
+  float4* d_posq[2] = {nullptr, nullptr};
+  double* d_x[3] = {nullptr, nullptr, nullptr};
+  double* d_u[3] = {nullptr, nullptr, nullptr};
+  float* d_qm = nullptr;
+  double* d_w = nullptr;
+  double* d_mass = nullptr;
+  int* d_z = nullptr;
+  unsigned char* d_kind = nullptr;
+  long long* d_step = nullptr;
+  unsigned* d_ticket = nullptr;
+  unsigned* d_done = nullptr;
+  int* d_err = nullptr;
+
+  // field / diagnostics scratch (sized for the largest cluster)
+  double* d_e = nullptr;
+  double* d_phi = nullptr;
+  md::DiagPartial* d_part = nullptr;
+  md::DiagPartial* d_diag = nullptr;
+  int diag_blocks = 0;
+
+  // host <-> device staging for set/get (device raw buffer + pinned host)
+  unsigned char* d_raw = nullptr;
+  unsigned char* h_raw = nullptr;
+  size_t raw_bytes = 0;
+  md::DiagPartial* h_diag = nullptr;
+
+  // kernel configuration
+  int cfg = -1;
+  int ctas_per_sm = 0;
+  int jsplit = 0;          // requested source segments (0: chosen by balance)
+  int nseg_used = 1;       // largest segment count of any cluster
+  md::Unit* d_units = nullptr;
+  int n_units = 0;
+  int grid = 0;
+  double* d_fpart = nullptr;       // partial fields [nseg][n_total][3]
+  size_t part_cap = 0;             // doubles allocated
+  unsigned* d_iblk_cnt = nullptr;  // completion counter per i-block
+  int iblk_cap = 0;
+
+  cudaGraphExec_t graph = nullptr;
+};
+
+namespace {
+
+size_t raw_record_bytes() {
+  return 3 * sizeof(double) * 2 + sizeof(int) + 2 * sizeof(double) + 1;
+}
+
+// Host-layout staging: x[n][3], u[n][3], z[n], mass[n], w[n], kind[n].
+struct RawView {
+  double* x;
+  double* u;
+  int* z;
+  double* mass;
+  double* w;
+  unsigned char* kind;
+};
+
+RawView raw_view(unsigned char* base, long long n) {
+  RawView v;
+  size_t o = 0;
+  v.x = reinterpret_cast<double*>(base + o);
+  o += sizeof(double) * 3 * n;
+  v.u = reinterpret_cast<double*>(base + o);
+  o += sizeof(double) * 3 * n;
+  v.mass = reinterpret_cast<double*>(base + o);
+  o += sizeof(double) * n;
+  v.w = reinterpret_cast<double*>(base + o);
+  o += sizeof(double) * n;
+  v.z = reinterpret_cast<int*>(base + o);
+  o += sizeof(int) * n;
+  v.kind = base + o;
+  return v;
+}
+
+md_status validate_config(const md_config& c, int idx) {
+  if (!(c.dt > 0.0) || !std::isfinite(c.dt))
+    return fail(MD_ERR_ARG, "cluster %d: dt must be > 0", idx);
+  if (!(c.softening > 0.0) || !std::isfinite(c.softening))
+    return fail(MD_ERR_ARG, "cluster %d: softening must be > 0 (the GPU sum keeps the self pair)", idx);
+  if (!(c.lambda_um > 0.0)) return fail(MD_ERR_ARG, "cluster %d: lambda_um must be > 0", idx);
+  if (c.polarization != 0 && c.polarization != 1)
+    return fail(MD_ERR_ARG, "cluster %d: polarization must be 0 or 1", idx);
+  if (c.envelope < 0 || c.envelope > 3) return fail(MD_ERR_ARG, "cluster %d: bad envelope", idx);
+  if (c.boundary < 0 || c.boundary > 2) return fail(MD_ERR_ARG, "cluster %d: bad boundary", idx);
+  if (c.boundary != 0 && !(c.box > 0.0))
+    return fail(MD_ERR_ARG, "cluster %d: periodic/mixed boundary needs box > 0", idx);
+  if (c.envelope != MD_ENV_FLAT && !(c.tau > 0.0))
+    return fail(MD_ERR_ARG, "cluster %d: tau must be > 0", idx);
+  if (c.reserved != 0) return fail(MD_ERR_ARG, "cluster %d: reserved must be 0", idx);
+  return MD_OK;
+}
+
+md_status validate_particles(const md_particles& p, int idx, long long expect_n) {
+  if (p.n < 1) return fail(MD_ERR_ARG, "cluster %d: n must be >= 1", idx);
+  if (expect_n >= 0 && p.n != expect_n)
+    return fail(MD_ERR_ARG, "cluster %d: n = %lld, context holds %lld", idx, (long long)p.n,
+                expect_n);
+  if (p.n > (1LL << 30)) return fail(MD_ERR_ARG, "cluster %d: n too large", idx);
+  if (!p.x || !p.u || !p.z || !p.mass || !p.w)
+    return fail(MD_ERR_ARG, "cluster %d: x, u, z, mass and w are required", idx);
+  for (long long i = 0; i < p.n; ++i) {
+    const int kd = p.kind ? p.kind[i] : (p.z[i] < 0 ? MD_KIND_ELECTRON : MD_KIND_ION);
+    if (kd < 0 || kd > 2) return fail(MD_ERR_ARG, "cluster %d: record %lld: bad kind", idx, i);
+    if (kd != MD_KIND_INACTIVE && !(p.mass[i] > 0.0))
+      return fail(MD_ERR_ARG, "cluster %d: record %lld: mass must be > 0", idx, i);
+    if (kd == MD_KIND_ELECTRON && p.z[i] >= 0)
+      return fail(MD_ERR_ARG, "cluster %d: record %lld: electron with z >= 0", idx, i);
+    if (kd == MD_KIND_ION && p.z[i] < 0)
+      return fail(MD_ERR_ARG, "cluster %d: record %lld: ion with z < 0", idx, i);
+  }
+  return MD_OK;
+}
+
+void destroy_graph(md_ctx* c) {
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+}
+
+md::StepArgs step_args(md_ctx* c) {
+  md::StepArgs a;
+  a.cl = c->d_cl;
+  a.units = c->d_units;
+  a.n_units = c->n_units;
+  a.posq0 = c->d_posq[0];
+  a.posq1 = c->d_posq[1];
+  a.x = c->d_x[0];
+  a.y = c->d_x[1];
+  a.z = c->d_x[2];
+  a.ux = c->d_u[0];
+  a.uy = c->d_u[1];
+  a.uz = c->d_u[2];
+  a.qm = c->d_qm;
+  a.step = c->d_step;
+  a.ticket = c->d_ticket;
+  a.done = c->d_done;
+  a.err = c->d_err;
+  a.part = c->d_fpart;
+  a.iblk_cnt = c->d_iblk_cnt;
+  a.n_total = c->n_total;
+  return a;
+}
+
+// Segments per i-block for a requested split S: each segment holds at least
+// one shared-memory tile of sources.
+void segments_for(const md::ClusterDev& cl, int S, int tile, int* nseg, int* seg_len) {
+  int n = std::max(1, std::min(S, cl.n_pad / tile));
+  int len = (cl.n_pad + n - 1) / n;
+  len = (len + md::kPad - 1) / md::kPad * md::kPad;
+  *seg_len = len;
+  *nseg = (cl.n_pad + len - 1) / len;
+}
+
+long long units_for(const md_ctx* c, long long per, int S, int tile) {
+  long long u = 0;
+  for (auto& cl : c->cl) {
+    int ns, len;
+    segments_for(cl, S, tile, &ns, &len);
+    u += (cl.n_pad + per - 1) / per * ns;
+  }
+  return u;
+}
+
+// Source split chosen for balance: equal units handed out by the ticket finish
+// in ceil(units / slots) rounds; take the smallest split whose last round is
+// at least 95 % full (or the best one up to 32).
+int choose_split(const md_ctx* c, long long per, int tile, long long slots) {
+  int best = 1;
+  double best_eff = -1.0;
+  for (int S = 1; S <= 32; ++S) {
+    const long long u = units_for(c, per, S, tile);
+    const long long rounds = (u + slots - 1) / slots;
+    const double eff = static_cast<double>(u) / static_cast<double>(rounds * slots);
+    if (eff >= 0.95) return S;
+    if (eff > best_eff + 1e-9) {
+      best_eff = eff;
+      best = S;
+    }
+  }
+  return best;
+}
+
+// Work units (cluster, i-block, source segment) ordered by decreasing cost,
+// so the ticket hands the largest blocks out first.
+md_status configure(md_ctx* c, int cfg, int ctas_per_sm, int jsplit) {
+  int ncfg = 0;
+  const md::KernelConfig* cfgs = md::step_configs(&ncfg);
+  if (cfg < 0 || cfg >= ncfg) return fail(MD_ERR_ARG, "tuning index %d out of range", cfg);
+  if (jsplit < 0 || jsplit > 64) return fail(MD_ERR_ARG, "jsplit must be in [0, 64]");
+  const md::KernelConfig& k = cfgs[cfg];
+  const long long per = static_cast<long long>(k.threads) * k.r;
+  int bps = 0;
+  MD_CUDA(k.max_blocks_per_sm(&bps));
+  if (bps < 1) return fail(MD_ERR_CUDA, "kernel configuration %d does not fit on an SM", cfg);
+  const int cps = ctas_per_sm > 0 ? std::min(ctas_per_sm, bps) : bps;
+  const long long slots = static_cast<long long>(cps) * c->sm_count;
+  const int S = jsplit > 0 ? jsplit : choose_split(c, per, k.tile, slots);
+
+  struct Work {
+    long long cost;
+    md::Unit u;
+  };
+  std::vector<Work> work;
+  int ib = 0, max_seg = 1;
+  for (int ci = 0; ci < c->n_clusters; ++ci) {
+    md::ClusterDev& cl = c->cl[ci];
+    segments_for(cl, S, k.tile, &cl.nseg, &cl.seg_len);
+    max_seg = std::max(max_seg, cl.nseg);
+    const long long nb = (cl.n_pad + per - 1) / per;
+    for (long long b = 0; b < nb; ++b, ++ib)
+      for (int sg = 0; sg < cl.nseg; ++sg) {
+        const long long len = std::min<long long>(cl.seg_len, cl.n_pad - static_cast<long long>(sg) * cl.seg_len);
+        work.push_back({per * len, {ci, static_cast<int>(b), sg, ib}});
+      }
+  }
+  std::stable_sort(work.begin(), work.end(),
+                   [](const Work& a, const Work& b) { return a.cost > b.cost; });
+  std::vector<md::Unit> units;
+  units.reserve(work.size());
+  for (auto& w : work) units.push_back(w.u);
+
+  MD_CUDA(cudaStreamSynchronize(c->stream));
+  if (c->d_units) cudaFree(c->d_units);
+  c->d_units = nullptr;
+  MD_CUDA(dev_alloc(&c->d_units, units.size()));
+  MD_CUDA(cudaMemcpyAsync(c->d_units, units.data(), units.size() * sizeof(md::Unit),
+                          cudaMemcpyHostToDevice, c->stream));
+  MD_CUDA(cudaMemcpyAsync(c->d_cl, c->cl.data(), sizeof(md::ClusterDev) * c->n_clusters,
+                          cudaMemcpyHostToDevice, c->stream));
+  if (max_seg > 1) {
+    const size_t need = static_cast<size_t>(max_seg) * static_cast<size_t>(c->n_total) * 3;
+    if (need > c->part_cap) {
+      cudaFree(c->d_fpart);
+      c->d_fpart = nullptr;
+      c->part_cap = 0;
+      MD_CUDA(dev_alloc(&c->d_fpart, need));
+      c->part_cap = need;
+    }
+    if (ib > c->iblk_cap) {
+      cudaFree(c->d_iblk_cnt);
+      c->d_iblk_cnt = nullptr;
+      c->iblk_cap = 0;
+      MD_CUDA(dev_alloc(&c->d_iblk_cnt, ib));
+      c->iblk_cap = ib;
+    }
+    MD_CUDA(cudaMemsetAsync(c->d_iblk_cnt, 0, sizeof(unsigned) * ib, c->stream));
+  }
+  MD_CUDA(cudaStreamSynchronize(c->stream));
+  c->n_units = static_cast<int>(units.size());
+  c->grid = static_cast<int>(std::max<long long>(1, std::min<long long>(c->n_units, slots)));
+  c->cfg = cfg;
+  c->ctas_per_sm = ctas_per_sm;
+  c->jsplit = jsplit;
+  c->nseg_used = max_seg;
+  destroy_graph(c);
+  return MD_OK;
+}
+
+// Default before autotuning: 256 threads x 4 i-particles per thread.
+int default_config(md_ctx* c) {
+  (void)c;
+  int ncfg = 0;
+  const md::KernelConfig* cfgs = md::step_configs(&ncfg);
+  for (int i = 0; i < ncfg; ++i)
+    if (cfgs[i].threads == 256 && cfgs[i].r == 4) return i;
+  return 0;
+}
+
+md_status ensure_scratch(md_ctx* c) {
+  if (c->d_e) return MD_OK;
+  MD_CUDA(dev_alloc(&c->d_e, 3 * static_cast<size_t>(c->max_n + md::kPad)));
+  MD_CUDA(dev_alloc(&c->d_phi, static_cast<size_t>(c->max_n + md::kPad)));
+  c->diag_blocks = std::max(1, std::min(4 * c->sm_count,
+                                        static_cast<int>((c->max_n + md::kDiagThreads - 1) /
+                                                         md::kDiagThreads)));
+  MD_CUDA(dev_alloc(&c->d_part, c->diag_blocks));
+  MD_CUDA(dev_alloc(&c->d_diag, 1));
+  MD_CUDA(cudaMallocHost(reinterpret_cast<void**>(&c->h_diag), sizeof(md::DiagPartial)));
+  return MD_OK;
+}
+
+md_status check_device_error(md_ctx* c) {
+  int err = 0;
+  MD_CUDA(cudaMemcpyAsync(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  MD_CUDA(cudaStreamSynchronize(c->stream));
+  if (err & md::kErrTimeout) {
+    MD_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+    MD_CUDA(cudaMemsetAsync(c->d_ticket, 0, sizeof(unsigned), c->stream));
+    MD_CUDA(cudaMemsetAsync(c->d_done, 0, sizeof(unsigned), c->stream));
+    if (c->d_iblk_cnt)
+      MD_CUDA(cudaMemsetAsync(c->d_iblk_cnt, 0, sizeof(unsigned) * c->iblk_cap, c->stream));
+    return fail(MD_ERR_TIMEOUT, "a device-side wait exceeded its time budget");
+  }
+  return MD_OK;
+}
+
+md_status launch_steps_direct(md_ctx* c, int n) {
+  int ncfg = 0;
+  const md::KernelConfig* cfgs = md::step_configs(&ncfg);
+  const md::StepArgs a = step_args(c);
+  for (int s = 0; s < n; ++s) {
+    cudaError_t e = cfgs[c->cfg].launch_step(a, c->grid, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
+  }
+  return MD_OK;
+}
+
+md_status build_graph(md_ctx* c) {
+  cudaStream_t cs = nullptr;
+  MD_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    int ncfg = 0;
+    const md::KernelConfig* cfgs = md::step_configs(&ncfg);
+    const md::StepArgs a = step_args(c);
+    for (int s = 0; s < kGraphSteps && e == cudaSuccess; ++s)
+      e = cfgs[c->cfg].launch_step(a, c->grid, cs);
+    cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph, g, 0);
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) {
+    c->graph = nullptr;
+    return cuda_fail(e, "capturing the step graph");
+  }
+  return MD_OK;
+}
+
+void free_ctx(md_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  destroy_graph(c);
+  cudaFree(c->d_cl);
+  for (auto p : c->d_posq) cudaFree(p);
+  for (auto p : c->d_x) cudaFree(p);
+  for (auto p : c->d_u) cudaFree(p);
+  cudaFree(c->d_qm);
+  cudaFree(c->d_w);
+  cudaFree(c->d_mass);
+  cudaFree(c->d_z);
+  cudaFree(c->d_kind);
+  cudaFree(c->d_step);
+  cudaFree(c->d_ticket);
+  cudaFree(c->d_done);
+  cudaFree(c->d_err);
+  cudaFree(c->d_e);
+  cudaFree(c->d_phi);
+  cudaFree(c->d_part);
+  cudaFree(c->d_diag);
+  cudaFree(c->d_units);
+  cudaFree(c->d_fpart);
+  cudaFree(c->d_iblk_cnt);
+  cudaFree(c->d_raw);
+  if (c->h_raw) cudaFreeHost(c->h_raw);
+  if (c->h_diag) cudaFreeHost(c->h_diag);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+md_status upload_cluster(md_ctx* c, int ci, const md_particles& p) {
+  const long long n = p.n;
+  RawView h = raw_view(c->h_raw, n);
+  std::memcpy(h.x, p.x, sizeof(double) * 3 * n);
+  std::memcpy(h.u, p.u, sizeof(double) * 3 * n);
+  std::memcpy(h.mass, p.mass, sizeof(double) * n);
+  std::memcpy(h.w, p.w, sizeof(double) * n);
+  std::memcpy(h.z, p.z, sizeof(int) * n);
+  for (long long i = 0; i < n; ++i)
+    h.kind[i] = p.kind ? p.kind[i] : static_cast<unsigned char>(p.z[i] < 0 ? 1 : 0);
+  MD_CUDA(cudaMemcpyAsync(c->d_raw, c->h_raw, raw_record_bytes() * n, cudaMemcpyHostToDevice,
+                          c->stream));
+  RawView d = raw_view(c->d_raw, n);
+  md::UploadArgs a;
+  a.hx = d.x;
+  a.hu = d.u;
+  a.hz = d.z;
+  a.hmass = d.mass;
+  a.hw = d.w;
+  a.hkind = d.kind;
+  a.n = n;
+  a.off = c->cl[ci].off;
+  a.kc = c->kc[ci];
+  a.posq0 = c->d_posq[0];
+  a.posq1 = c->d_posq[1];
+  a.x = c->d_x[0];
+  a.y = c->d_x[1];
+  a.z = c->d_x[2];
+  a.ux = c->d_u[0];
+  a.uy = c->d_u[1];
+  a.uz = c->d_u[2];
+  a.qm = c->d_qm;
+  a.w = c->d_w;
+  a.mass = c->d_mass;
+  a.zq = c->d_z;
+  a.kind = c->d_kind;
+  a.step = c->d_step;
+  MD_CUDA(md::launch_upload(a, c->stream));
+  // the pinned staging buffer is reused by the next call: wait for the copy
+  MD_CUDA(cudaStreamSynchronize(c->stream));
+  return MD_OK;
+}
+
+}  // namespace
+
+// ===================================================================== ABI
+
+extern "C" {
+
+const char* md_last_error(void) { return g_last_error.c_str(); }
+
+double md_coulomb_constant(double lambda_um) {
+  return 2.0 * kPi * kClassicalElectronRadius / (lambda_um * 1e-6);
+}
+
+double md_a0_from_intensity(double intensity_wcm2, double lambda_um) {
+  return std::sqrt(intensity_wcm2 * lambda_um * lambda_um / 1.366e18);
+}
+
+double md_n_atoms(double r0, double r_wigner_seitz) {
+  const double q = r0 / r_wigner_seitz;
+  return q * q * q;
+}
+
+md_status md_device_info(int32_t* sm_count, char* name, int32_t name_cap) {
+  int dev = 0;
+  MD_CUDA(cudaGetDevice(&dev));
+  cudaDeviceProp prop;
+  MD_CUDA(cudaGetDeviceProperties(&prop, dev));
+  if (sm_count) *sm_count = prop.multiProcessorCount;
+  if (name && name_cap > 0) {
+    std::strncpy(name, prop.name, name_cap - 1);
+    name[name_cap - 1] = 0;
+  }
+  return MD_OK;
+}
+
+md_status md_init(md_ctx** out, const md_config* cfgs, int32_t n_clusters,
+                  const md_particles* parts, void* stream) {
+  if (!out) return fail(MD_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (n_clusters < 1 || !cfgs || !parts) return fail(MD_ERR_ARG, "need >= 1 cluster");
+  for (int i = 0; i < n_clusters; ++i) {
+    md_status st = validate_config(cfgs[i], i);
+    if (st != MD_OK) return st;
+    st = validate_particles(parts[i], i, -1);
+    if (st != MD_OK) return st;
+  }
+  md_ctx* c = new md_ctx();
+  auto bail = [&](md_status st) {
+    free_ctx(c);
+    return st;
+  };
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "cudaGetDevice"));
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, c->device);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "cudaGetDeviceProperties"));
+  if (prop.major != 10 || prop.minor != 3)
+    return bail(fail(MD_ERR_UNSUPPORTED, "device %s is sm_%d%d; this library is built for sm_103a",
+                     prop.name, prop.major, prop.minor));
+  c->sm_count = prop.multiProcessorCount;
+  if (stream) {
+    c->stream = static_cast<cudaStream_t>(stream);
+  } else {
+    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamCreate"));
+    c->own_stream = true;
+  }
+
+  c->n_clusters = n_clusters;
+  long long off = 0;
+  for (int i = 0; i < n_clusters; ++i) {
+    const md_config& f = cfgs[i];
+    md::ClusterDev d;
+    d.off = off;
+    d.n = static_cast<int>(parts[i].n);
+    d.n_pad = static_cast<int>((parts[i].n + md::kPad - 1) / md::kPad * md::kPad);
+    d.a0 = f.a0;
+    d.tau = f.tau;
+    d.t0 = f.t0;
+    d.dt = f.dt;
+    d.box = f.box;
+    d.t_switch = f.t_switch;
+    d.eps2 = static_cast<float>(f.softening * f.softening);
+    d.pol = f.polarization;
+    d.env = f.envelope;
+    d.boundary = f.boundary;
+    c->cl.push_back(d);
+    c->kc.push_back(md_coulomb_constant(f.lambda_um));
+    off += d.n_pad;
+    c->max_n = std::max<long long>(c->max_n, parts[i].n);
+  }
+  c->n_total = off;
+  const size_t N = static_cast<size_t>(c->n_total);
+
+  md_status st = MD_OK;
+#define MD_ALLOC(ptr, cnt)                                        \
+  do {                                                            \
+    cudaError_t e_ = dev_alloc(&(ptr), (cnt));                    \
+    if (e_ != cudaSuccess) return bail(cuda_fail(e_, "cudaMalloc")); \
+  } while (0)
+  MD_ALLOC(c->d_cl, n_clusters);
+  MD_ALLOC(c->d_posq[0], N);
+  MD_ALLOC(c->d_posq[1], N);
+  for (int k = 0; k < 3; ++k) {
+    MD_ALLOC(c->d_x[k], N);
+    MD_ALLOC(c->d_u[k], N);
+  }
+  MD_ALLOC(c->d_qm, N);
+  MD_ALLOC(c->d_w, N);
+  MD_ALLOC(c->d_mass, N);
+  MD_ALLOC(c->d_z, N);
+  MD_ALLOC(c->d_kind, N);
+  MD_ALLOC(c->d_step, 1);
+  MD_ALLOC(c->d_ticket, 1);
+  MD_ALLOC(c->d_done, 1);
+  MD_ALLOC(c->d_err, 1);
+#undef MD_ALLOC
+  c->raw_bytes = raw_record_bytes() * static_cast<size_t>(c->max_n) + 64;
+  e = cudaMalloc(reinterpret_cast<void**>(&c->d_raw), c->raw_bytes);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
+  e = cudaMallocHost(reinterpret_cast<void**>(&c->h_raw), c->raw_bytes);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMallocHost"));
+
+  // zero state; padding records are INACTIVE with zero charge at the origin
+  cudaStream_t s = c->stream;
+  bool ok = true;
+  ok &= cudaMemcpyAsync(c->d_cl, c->cl.data(), sizeof(md::ClusterDev) * n_clusters,
+                        cudaMemcpyHostToDevice, s) == cudaSuccess;
+  for (int k = 0; k < 2; ++k) ok &= cudaMemsetAsync(c->d_posq[k], 0, N * sizeof(float4), s) == cudaSuccess;
+  for (int k = 0; k < 3; ++k) {
+    ok &= cudaMemsetAsync(c->d_x[k], 0, N * sizeof(double), s) == cudaSuccess;
+    ok &= cudaMemsetAsync(c->d_u[k], 0, N * sizeof(double), s) == cudaSuccess;
+  }
+  ok &= cudaMemsetAsync(c->d_qm, 0, N * sizeof(float), s) == cudaSuccess;
+  ok &= cudaMemsetAsync(c->d_w, 0, N * sizeof(double), s) == cudaSuccess;
+  ok &= cudaMemsetAsync(c->d_mass, 0, N * sizeof(double), s) == cudaSuccess;
+  ok &= cudaMemsetAsync(c->d_z, 0, N * sizeof(int), s) == cudaSuccess;
+  ok &= cudaMemsetAsync(c->d_kind, MD_KIND_INACTIVE, N, s) == cudaSuccess;
+  ok &= cudaMemsetAsync(c->d_step, 0, sizeof(long long), s) == cudaSuccess;
+  ok &= cudaMemsetAsync(c->d_ticket, 0, sizeof(unsigned), s) == cudaSuccess;
+  ok &= cudaMemsetAsync(c->d_done, 0, sizeof(unsigned), s) == cudaSuccess;
+  ok &= cudaMemsetAsync(c->d_err, 0, sizeof(int), s) == cudaSuccess;
+  if (!ok) return bail(cuda_fail(cudaGetLastError(), "initialising device state"));
+  for (int i = 0; i < n_clusters; ++i) {
+    st = upload_cluster(c, i, parts[i]);
+    if (st != MD_OK) return bail(st);
+  }
+  st = configure(c, default_config(c), 0, 0);
+  if (st != MD_OK) return bail(st);
+  *out = c;
+  return MD_OK;
+}
+
+void md_destroy(md_ctx* ctx) { free_ctx(ctx); }
+
+md_status md_step(md_ctx* c, int32_t nsteps) {
+  if (!c) return fail(MD_ERR_ARG, "ctx is NULL");
+  if (nsteps < 0) return fail(MD_ERR_ARG, "nsteps < 0");
+  if (nsteps == 0) return MD_OK;
+  if (nsteps >= kGraphSteps) {
+    if (!c->graph) {
+      md_status st = build_graph(c);
+      if (st != MD_OK) return st;
+    }
+    for (int k = 0; k + kGraphSteps <= nsteps; k += kGraphSteps) {
+      cudaError_t e = cudaGraphLaunch(c->graph, c->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    }
+  }
+  return launch_steps_direct(c, nsteps % kGraphSteps);
+}
+
+md_status md_sync(md_ctx* c) {
+  if (!c) return fail(MD_ERR_ARG, "ctx is NULL");
+  MD_CUDA(cudaStreamSynchronize(c->stream));
+  return check_device_error(c);
+}
+
+md_status md_get_step(md_ctx* c, int64_t* step) {
+  if (!c || !step) return fail(MD_ERR_ARG, "NULL argument");
+  long long v = 0;
+  MD_CUDA(cudaMemcpyAsync(&v, c->d_step, sizeof(v), cudaMemcpyDeviceToHost, c->stream));
+  MD_CUDA(cudaStreamSynchronize(c->stream));
+  *step = v;
+  return MD_OK;
+}
+
+static md_status run_fields(md_ctx* c, int ci, bool potential) {
+  md_status st = ensure_scratch(c);
+  if (st != MD_OK) return st;
+  long long step = 0;
+  MD_CUDA(cudaMemcpyAsync(&step, c->d_step, sizeof(step), cudaMemcpyDeviceToHost, c->stream));
+  MD_CUDA(cudaStreamSynchronize(c->stream));
+  const md::ClusterDev& cl = c->cl[ci];
+  const float4* cur = c->d_posq[step & 1] + cl.off;
+  md::FieldArgs a;
+  a.src = cur;
+  a.ns = cl.n_pad;
+  a.tgt = cur;
+  a.nt = cl.n_pad;
+  a.eps2 = cl.eps2;
+  a.self_offset = 0;
+  a.e = c->d_e;
+  a.phi = potential ? c->d_phi : nullptr;
+  a.err = c->d_err;
+  MD_CUDA(md::launch_field(a, potential, c->stream));
+  return MD_OK;
+}
+
+md_status md_get_fields(md_ctx* c, int32_t cluster, double* e, double* phi) {
+  if (!c || !e) return fail(MD_ERR_ARG, "NULL argument");
+  if (cluster < 0 || cluster >= c->n_clusters) return fail(MD_ERR_ARG, "bad cluster index");
+  md_status st = run_fields(c, cluster, phi != nullptr);
+  if (st != MD_OK) return st;
+  const long long n = c->cl[cluster].n;
+  MD_CUDA(cudaMemcpyAsync(e, c->d_e, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
+  if (phi)
+    MD_CUDA(cudaMemcpyAsync(phi, c->d_phi, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+  MD_CUDA(cudaStreamSynchronize(c->stream));
+  return check_device_error(c);
+}
+
+md_status md_diagnostics(md_ctx* c, int32_t cluster, md_diag* out) {
+  if (!c || !out) return fail(MD_ERR_ARG, "NULL argument");
+  if (cluster < 0 || cluster >= c->n_clusters) return fail(MD_ERR_ARG, "bad cluster index");
+  md_status st = run_fields(c, cluster, true);
+  if (st != MD_OK) return st;
+  md::DiagArgs a;
+  a.c = c->cl[cluster];
+  a.x = c->d_x[0];
+  a.y = c->d_x[1];
+  a.z = c->d_x[2];
+  a.ux = c->d_u[0];
+  a.uy = c->d_u[1];
+  a.uz = c->d_u[2];
+  a.qm = c->d_qm;
+  a.w = c->d_w;
+  a.mass = c->d_mass;
+  a.zq = c->d_z;
+  a.kind = c->d_kind;
+  a.e = c->d_e;
+  a.phi = c->d_phi;
+  a.step = c->d_step;
+  a.part = c->d_part;
+  MD_CUDA(md::launch_diag(a, c->diag_blocks, c->d_diag, c->stream));
+  MD_CUDA(cudaMemcpyAsync(c->h_diag, c->d_diag, sizeof(md::DiagPartial), cudaMemcpyDeviceToHost,
+                          c->stream));
+  long long step = 0;
+  MD_CUDA(cudaMemcpyAsync(&step, c->d_step, sizeof(step), cudaMemcpyDeviceToHost, c->stream));
+  MD_CUDA(cudaStreamSynchronize(c->stream));
+  st = check_device_error(c);
+  if (st != MD_OK) return st;
+  const md::DiagPartial& d = *c->h_diag;
+  std::memset(out, 0, sizeof(*out));
+  out->step = step;
+  out->t = a.c.t0 + static_cast<double>(step) * a.c.dt;
+  out->ke = d.v[0];
+  out->ke_ions = d.v[1];
+  out->ke_electrons = d.v[2];
+  out->pe = d.v[3];
+  out->total = d.v[0] + d.v[3];
+  out->p[0] = d.v[4];
+  out->p[1] = d.v[5];
+  out->p[2] = d.v[6];
+  out->n_active = d.cnt[0];
+  out->n_nonfinite = d.cnt[1];
+  for (int k = 0; k < md::kHistBins; ++k) {
+    out->charge_count[k] = d.hist[k];
+    out->charge_weight[k] = d.histw[k];
+  }
+  if (out->n_nonfinite > 0)
+    return fail(MD_ERR_NONFINITE, "%lld records hold NaN/Inf", (long long)out->n_nonfinite);
+  return MD_OK;
+}
+
+md_status md_get_particles(md_ctx* c, int32_t cluster, md_particles* out) {
+  if (!c || !out) return fail(MD_ERR_ARG, "NULL argument");
+  if (cluster < 0 || cluster >= c->n_clusters) return fail(MD_ERR_ARG, "bad cluster index");
+  const long long n = c->cl[cluster].n;
+  if (out->n != n) return fail(MD_ERR_ARG, "out->n = %lld, cluster holds %lld", (long long)out->n, n);
+  RawView d = raw_view(c->d_raw, n);
+  md::DownloadArgs a;
+  a.hx = d.x;
+  a.hu = d.u;
+  a.hz = d.z;
+  a.hmass = d.mass;
+  a.hw = d.w;
+  a.hkind = d.kind;
+  a.n = n;
+  a.off = c->cl[cluster].off;
+  a.x = c->d_x[0];
+  a.y = c->d_x[1];
+  a.z = c->d_x[2];
+  a.ux = c->d_u[0];
+  a.uy = c->d_u[1];
+  a.uz = c->d_u[2];
+  a.w = c->d_w;
+  a.mass = c->d_mass;
+  a.zq = c->d_z;
+  a.kind = c->d_kind;
+  MD_CUDA(md::launch_download(a, c->stream));
+  MD_CUDA(cudaMemcpyAsync(c->h_raw, c->d_raw, raw_record_bytes() * n, cudaMemcpyDeviceToHost,
+                          c->stream));
+  MD_CUDA(cudaStreamSynchronize(c->stream));
+  RawView h = raw_view(c->h_raw, n);
+  if (out->x) std::memcpy(out->x, h.x, sizeof(double) * 3 * n);
+  if (out->u) std::memcpy(out->u, h.u, sizeof(double) * 3 * n);
+  if (out->z) std::memcpy(out->z, h.z, sizeof(int) * n);
+  if (out->mass) std::memcpy(out->mass, h.mass, sizeof(double) * n);
+  if (out->w) std::memcpy(out->w, h.w, sizeof(double) * n);
+  if (out->kind) std::memcpy(out->kind, h.kind, n);
+  return check_device_error(c);
+}
+
+md_status md_set_particles(md_ctx* c, int32_t cluster, const md_particles* in) {
+  if (!c || !in) return fail(MD_ERR_ARG, "NULL argument");
+  if (cluster < 0 || cluster >= c->n_clusters) return fail(MD_ERR_ARG, "bad cluster index");
+  md_status st = validate_particles(*in, cluster, c->cl[cluster].n);
+  if (st != MD_OK) return st;
+  return upload_cluster(c, cluster, *in);
+}
+
+int32_t md_tuning_list(md_tuning* list, int32_t cap) {
+  int n = 0;
+  const md::KernelConfig* cfgs = md::step_configs(&n);
+  for (int i = 0; list && i < n && i < cap; ++i) {
+    list[i].threads = cfgs[i].threads;
+    list[i].r = cfgs[i].r;
+    list[i].tile = cfgs[i].tile;
+    list[i].ctas_per_sm = 0;
+    list[i].jsplit = 0;
+  }
+  return n;
+}
+
+md_status md_set_tuning(md_ctx* c, const md_tuning* t) {
+  if (!c || !t) return fail(MD_ERR_ARG, "NULL argument");
+  int n = 0;
+  const md::KernelConfig* cfgs = md::step_configs(&n);
+  for (int i = 0; i < n; ++i) {
+    if (cfgs[i].threads == t->threads && cfgs[i].r == t->r && cfgs[i].tile == t->tile) {
+      if (t->ctas_per_sm < 0) return fail(MD_ERR_ARG, "ctas_per_sm < 0");
+      MD_CUDA(cudaStreamSynchronize(c->stream));
+      return configure(c, i, t->ctas_per_sm, t->jsplit);
+    }
+  }
+  return fail(MD_ERR_ARG, "no compiled configuration threads=%d r=%d tile=%d", t->threads, t->r,
+              t->tile);
+}
+
+md_status md_get_tuning(md_ctx* c, md_tuning* t) {
+  if (!c || !t) return fail(MD_ERR_ARG, "NULL argument");
+  int n = 0;
+  const md::KernelConfig* cfgs = md::step_configs(&n);
+  t->threads = cfgs[c->cfg].threads;
+  t->r = cfgs[c->cfg].r;
+  t->tile = cfgs[c->cfg].tile;
+  t->ctas_per_sm = c->ctas_per_sm;
+  t->jsplit = c->nseg_used;
+  return MD_OK;
+}
+
+md_status md_autotune(md_ctx* c, int32_t steps, double* times_ms, int32_t cap) {
+  if (!c) return fail(MD_ERR_ARG, "ctx is NULL");
+  if (steps < 1) return fail(MD_ERR_ARG, "steps < 1");
+  const size_t N = static_cast<size_t>(c->n_total);
+  // back up the mutable state, time each configuration, restore
+  float4* bq[2] = {nullptr, nullptr};
+  double* bx[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  long long step0 = 0;
+  md_status st = MD_OK;
+  auto release = [&]() {
+    for (auto p : bq) cudaFree(p);
+    for (auto p : bx) cudaFree(p);
+  };
+  bool ok = true;
+  for (int k = 0; k < 2; ++k) ok &= dev_alloc(&bq[k], N) == cudaSuccess;
+  for (int k = 0; k < 6; ++k) ok &= dev_alloc(&bx[k], N) == cudaSuccess;
+  if (!ok) {
+    release();
+    return fail(MD_ERR_OOM, "autotune backup allocation failed");
+  }
+  cudaStream_t s = c->stream;
+  for (int k = 0; k < 2; ++k)
+    cudaMemcpyAsync(bq[k], c->d_posq[k], N * sizeof(float4), cudaMemcpyDeviceToDevice, s);
+  for (int k = 0; k < 3; ++k) {
+    cudaMemcpyAsync(bx[k], c->d_x[k], N * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(bx[3 + k], c->d_u[k], N * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  }
+  cudaMemcpyAsync(&step0, c->d_step, sizeof(step0), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  const int cfg0 = c->cfg, cps0 = c->ctas_per_sm, js0 = c->jsplit;
+  int n = 0;
+  md::step_configs(&n);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best = 1e300;
+  int best_cfg = cfg0;
+  for (int i = 0; i < n && st == MD_OK; ++i) {
+    st = configure(c, i, 0, 0);
+    if (st != MD_OK) break;
+    st = launch_steps_direct(c, 1);  // warm-up
+    if (st != MD_OK) break;
+    cudaEventRecord(e0, s);
+    st = launch_steps_direct(c, steps);
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) st = fail(MD_ERR_CUDA, "autotune timing");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double per = ms / steps;
+    if (times_ms && i < cap) times_ms[i] = per;
+    if (per < best) {
+      best = per;
+      best_cfg = i;
+    }
+    if (st == MD_OK) st = check_device_error(c);
+    // restore the state before the next configuration
+    for (int k = 0; k < 2; ++k)
+      cudaMemcpyAsync(c->d_posq[k], bq[k], N * sizeof(float4), cudaMemcpyDeviceToDevice, s);
+    for (int k = 0; k < 3; ++k) {
+      cudaMemcpyAsync(c->d_x[k], bx[k], N * sizeof(double), cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(c->d_u[k], bx[3 + k], N * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    }
+    cudaMemcpyAsync(c->d_step, &step0, sizeof(step0), cudaMemcpyHostToDevice, s);
+    cudaStreamSynchronize(s);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  release();
+  if (st != MD_OK) {
+    configure(c, cfg0, cps0, js0);
+    return st;
+  }
+  return configure(c, best_cfg, 0, 0);
+}
+
+md_status md_coulomb_field_device(const void* src, int64_t ns, const void* tgt, int64_t nt,
+                                  float eps2, int64_t self_offset, double* e, double* phi,
+                                  void* stream) {
+  if (ns < 0 || nt < 0) return fail(MD_ERR_ARG, "negative size");
+  if (nt == 0) return MD_OK;
+  if (!src || !tgt || !e) return fail(MD_ERR_ARG, "NULL pointer");
+  if ((reinterpret_cast<uintptr_t>(src) & 15) || (reinterpret_cast<uintptr_t>(tgt) & 15))
+    return fail(MD_ERR_ARG, "src and tgt must be 16-byte aligned");
+  if (!(eps2 > 0.0f)) return fail(MD_ERR_ARG, "eps2 must be > 0");
+  static int* d_err = nullptr;  // per-process error word of the stateless call
+  if (!d_err) {
+    cudaError_t ce = cudaMalloc(reinterpret_cast<void**>(&d_err), sizeof(int));
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaMalloc");
+    cudaMemset(d_err, 0, sizeof(int));
+  }
+  md::FieldArgs a;
+  a.src = static_cast<const float4*>(src);
+  a.ns = ns;
+  a.tgt = static_cast<const float4*>(tgt);
+  a.nt = nt;
+  a.eps2 = eps2;
+  a.self_offset = self_offset;
+  a.e = e;
+  a.phi = phi;
+  a.err = d_err;
+  MD_CUDA(md::launch_field(a, phi != nullptr, static_cast<cudaStream_t>(stream)));
+  return MD_OK;
+}
+
+md_status md_measure_fp32_peak(double* ffma_per_s, double* packed_fma_per_s, void* stream) {
+  if (!ffma_per_s) return fail(MD_ERR_ARG, "NULL argument");
+  int dev = 0, sms = 0;
+  MD_CUDA(cudaGetDevice(&dev));
+  MD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  float* sink = nullptr;
+  MD_CUDA(cudaMalloc(reinterpret_cast<void**>(&sink), sizeof(float) * 8 * sms));
+  const int blocks = 8 * sms, iters = 20000;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double rate[2] = {0.0, 0.0};
+  cudaError_t e = cudaSuccess;
+  for (int packed = 0; packed < 2 && e == cudaSuccess; ++packed) {
+    e = md::launch_ffma_probe(blocks, iters / 10, packed != 0, sink, s);  // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess) e = md::launch_ffma_probe(blocks, iters, packed != 0, sink, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    // lane FMAs: 256 threads x iters x 16 x 8 chains (x 2 lanes when packed)
+    const double fma = static_cast<double>(blocks) * 256.0 * iters * 128.0 * (packed ? 2.0 : 1.0);
+    rate[packed] = fma / (ms * 1e-3);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  if (e != cudaSuccess) return cuda_fail(e, "FP32 peak probe");
+  *ffma_per_s = rate[0];
+  if (packed_fma_per_s) *packed_fma_per_s = rate[1];
+  return MD_OK;
+}
+
+}  // extern "C"

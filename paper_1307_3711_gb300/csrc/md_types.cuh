@@ -1,0 +1,141 @@
+// md_types.cuh -- plain data shared by the kernels and the host runtime.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace md {
+
+constexpr int kPad = 16;                          // records per cluster padded to a multiple of this
+constexpr long long kWaitBudget = 4000000000LL;   // clock64 cycles (about 2 s)
+constexpr int kErrTimeout = 1;
+constexpr int kHistBins = 16;
+
+struct ClusterDev {
+  long long off;   // first record of the cluster
+  int n;           // real records
+  int n_pad;       // records incl. zero-charge padding (multiple of kPad)
+  int nseg;        // sources split into nseg segments (work units) per i-block
+  int seg_len;     // sources per segment (last one shorter)
+  double a0, tau, t0, dt, box, t_switch;
+  float eps2;
+  int pol, env, boundary;
+};
+
+struct Unit {
+  int cluster;
+  int block;  // i-block within the cluster
+  int seg;    // source segment
+  int ib;     // i-block index over all clusters (completion counter)
+};
+
+struct StepArgs {
+  const ClusterDev* cl;
+  const Unit* units;
+  int n_units;
+  float4* posq0;
+  float4* posq1;
+  double* x;
+  double* y;
+  double* z;
+  double* ux;
+  double* uy;
+  double* uz;
+  const float* qm;
+  long long* step;
+  unsigned* ticket;
+  unsigned* done;
+  int* err;
+  // split sources: partial fields [seg][n_total][3] and per-i-block counters
+  double* part;
+  unsigned* iblk_cnt;
+  long long n_total;
+};
+
+struct FieldArgs {
+  const float4* src;
+  long long ns;
+  const float4* tgt;
+  long long nt;
+  float eps2;
+  long long self_offset;  // target i is source i + self_offset, or -1
+  double* e;              // [nt][3]
+  double* phi;            // [nt] or nullptr
+  int* err;
+};
+
+struct DiagPartial {
+  double v[8];  // ke, ke_ions, ke_electrons, pe, px, py, pz, unused
+  long long cnt[2];  // n_active, n_nonfinite
+  long long hist[kHistBins];
+  double histw[kHistBins];
+};
+constexpr int kDiagVals = 8 + 2 + 2 * kHistBins;
+
+struct DiagArgs {
+  ClusterDev c;
+  const double* x;
+  const double* y;
+  const double* z;
+  const double* ux;
+  const double* uy;
+  const double* uz;
+  const float* qm;
+  const double* w;
+  const double* mass;
+  const int* zq;
+  const unsigned char* kind;
+  const double* e;    // Coulomb field [n_pad][3] of this cluster
+  const double* phi;  // potential [n_pad]
+  const long long* step;
+  DiagPartial* part;  // [gridDim.x]
+};
+
+struct UploadArgs {
+  const double* hx;
+  const double* hu;
+  const int* hz;
+  const double* hmass;
+  const double* hw;
+  const unsigned char* hkind;
+  long long n;
+  long long off;
+  double kc;
+  float4* posq0;
+  float4* posq1;
+  double* x;
+  double* y;
+  double* z;
+  double* ux;
+  double* uy;
+  double* uz;
+  float* qm;
+  double* w;
+  double* mass;
+  int* zq;
+  unsigned char* kind;
+  const long long* step;
+};
+
+struct DownloadArgs {
+  double* hx;
+  double* hu;
+  int* hz;
+  double* hmass;
+  double* hw;
+  unsigned char* hkind;
+  long long n;
+  long long off;
+  const double* x;
+  const double* y;
+  const double* z;
+  const double* ux;
+  const double* uy;
+  const double* uz;
+  const double* w;
+  const double* mass;
+  const int* zq;
+  const unsigned char* kind;
+};
+
+}  // namespace md

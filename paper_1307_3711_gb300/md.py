@@ -1,0 +1,281 @@
+"""Thin ctypes binding of the C ABI in ``include/md.h`` (libmd.so).
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  Importing this module loads ``_build/libmd.so`` and raises
+``ImportError`` if it is missing (build it with ``paper_1307_3711_gb300.build``
+or ``__graft_entry__.build()``); there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_LIB_PATH = _build.LIB
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"libmd.so not built ({_LIB_PATH}); run paper_1307_3711_gb300.build.build()")
+_lib = C.CDLL(_LIB_PATH)
+
+MD_OK, MD_ERR_ARG, MD_ERR_OOM, MD_ERR_CUDA, MD_ERR_TIMEOUT, MD_ERR_NONFINITE, MD_ERR_STATE, \
+    MD_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
+ENV_GAUSS, ENV_SIN2, ENV_LITERAL_EQ3, ENV_FLAT = 0, 1, 2, 3
+BOUNDARY_OPEN, BOUNDARY_PERIODIC, BOUNDARY_MIXED = 0, 1, 2
+KIND_ION, KIND_ELECTRON, KIND_INACTIVE = 0, 1, 2
+
+
+class MDError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"md status {status}: {msg}")
+        self.status = status
+
+
+class Config(C.Structure):
+    _fields_ = [("a0", C.c_double), ("tau", C.c_double), ("t0", C.c_double),
+                ("dt", C.c_double), ("softening", C.c_double), ("box", C.c_double),
+                ("t_switch", C.c_double), ("lambda_um", C.c_double),
+                ("polarization", C.c_int32), ("envelope", C.c_int32),
+                ("boundary", C.c_int32), ("reserved", C.c_int32)]
+
+
+class Particles(C.Structure):
+    _fields_ = [("n", C.c_int64), ("x", C.c_void_p), ("u", C.c_void_p), ("z", C.c_void_p),
+                ("mass", C.c_void_p), ("w", C.c_void_p), ("kind", C.c_void_p)]
+
+
+class Diag(C.Structure):
+    _fields_ = [("step", C.c_int64), ("t", C.c_double), ("ke", C.c_double),
+                ("ke_ions", C.c_double), ("ke_electrons", C.c_double), ("pe", C.c_double),
+                ("total", C.c_double), ("p", C.c_double * 3), ("n_active", C.c_int64),
+                ("n_nonfinite", C.c_int64), ("charge_count", C.c_int64 * 16),
+                ("charge_weight", C.c_double * 16)]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("threads", C.c_int32), ("r", C.c_int32), ("tile", C.c_int32),
+                ("ctas_per_sm", C.c_int32), ("jsplit", C.c_int32)]
+
+    def as_tuple(self):
+        return (self.threads, self.r, self.tile, self.ctas_per_sm, self.jsplit)
+
+
+_ctx_p = C.c_void_p
+_st = C.c_int
+_p = C.c_void_p
+_SIGS = {
+    "md_init": (_st, [C.POINTER(_ctx_p), C.POINTER(Config), C.c_int32, C.POINTER(Particles), _p]),
+    "md_destroy": (None, [_ctx_p]),
+    "md_last_error": (C.c_char_p, []),
+    "md_step": (_st, [_ctx_p, C.c_int32]),
+    "md_sync": (_st, [_ctx_p]),
+    "md_diagnostics": (_st, [_ctx_p, C.c_int32, C.POINTER(Diag)]),
+    "md_get_particles": (_st, [_ctx_p, C.c_int32, C.POINTER(Particles)]),
+    "md_set_particles": (_st, [_ctx_p, C.c_int32, C.POINTER(Particles)]),
+    "md_get_fields": (_st, [_ctx_p, C.c_int32, _p, _p]),
+    "md_get_step": (_st, [_ctx_p, C.POINTER(C.c_int64)]),
+    "md_tuning_list": (C.c_int32, [C.POINTER(Tuning), C.c_int32]),
+    "md_set_tuning": (_st, [_ctx_p, C.POINTER(Tuning)]),
+    "md_get_tuning": (_st, [_ctx_p, C.POINTER(Tuning)]),
+    "md_autotune": (_st, [_ctx_p, C.c_int32, _p, C.c_int32]),
+    "md_coulomb_field_device": (_st, [_p, C.c_int64, _p, C.c_int64, C.c_float, C.c_int64, _p,
+                                      _p, _p]),
+    "md_coulomb_constant": (C.c_double, [C.c_double]),
+    "md_a0_from_intensity": (C.c_double, [C.c_double, C.c_double]),
+    "md_n_atoms": (C.c_double, [C.c_double, C.c_double]),
+    "md_device_info": (_st, [C.POINTER(C.c_int32), C.c_char_p, C.c_int32]),
+    "md_measure_fp32_peak": (_st, [C.POINTER(C.c_double), C.POINTER(C.c_double), _p]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _fn = getattr(_lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+# every symbol include/md.h declares
+EXPORTED = tuple(_SIGS)
+
+
+def _check(st: int):
+    if st != MD_OK:
+        raise MDError(st, _lib.md_last_error().decode())
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def coulomb_constant(lambda_um: float = 0.8) -> float:
+    return _lib.md_coulomb_constant(lambda_um)
+
+
+def a0_from_intensity(intensity_wcm2: float, lambda_um: float) -> float:
+    return _lib.md_a0_from_intensity(intensity_wcm2, lambda_um)
+
+
+def n_atoms(r0: float, r_w: float) -> float:
+    return _lib.md_n_atoms(r0, r_w)
+
+
+def device_info():
+    n = C.c_int32(0)
+    buf = C.create_string_buffer(256)
+    _check(_lib.md_device_info(C.byref(n), buf, 256))
+    return int(n.value), buf.value.decode()
+
+
+def measure_fp32_peak(stream=None):
+    """(scalar FFMA, packed f32x2 FMA) lane operations per second of the GPU."""
+    v = C.c_double(0)
+    t = C.c_double(0)
+    _check(_lib.md_measure_fp32_peak(C.byref(v), C.byref(t),
+                                     C.c_void_p(stream) if stream else None))
+    return float(v.value), float(t.value)
+
+
+def tuning_list():
+    n = _lib.md_tuning_list(None, 0)
+    arr = (Tuning * n)()
+    _lib.md_tuning_list(arr, n)
+    return [t.as_tuple() for t in arr]
+
+
+class HostParticles:
+    """Host arrays of one cluster in the layout md_particles expects; keeps the
+    numpy arrays alive while a C struct points at them."""
+
+    def __init__(self, x, u, z, mass, w, kind=None):
+        self.x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+        self.u = np.ascontiguousarray(u, dtype=np.float64).reshape(-1, 3)
+        self.z = np.ascontiguousarray(z, dtype=np.int32).ravel()
+        self.mass = np.ascontiguousarray(mass, dtype=np.float64).ravel()
+        self.w = np.ascontiguousarray(w, dtype=np.float64).ravel()
+        if kind is None:
+            kind = np.where(self.z < 0, KIND_ELECTRON, KIND_ION)
+        self.kind = np.ascontiguousarray(kind, dtype=np.uint8).ravel()
+
+    @classmethod
+    def empty(cls, n):
+        return cls(np.zeros((n, 3)), np.zeros((n, 3)), np.zeros(n, np.int32), np.zeros(n),
+                   np.zeros(n), np.zeros(n, np.uint8))
+
+    @classmethod
+    def from_cluster(cls, c):
+        kind = np.where(c.active == 0, KIND_INACTIVE, np.where(c.z < 0, KIND_ELECTRON, KIND_ION))
+        return cls(c.x, c.u, c.z, c.mass, c.w, kind)
+
+    @property
+    def n(self):
+        return self.x.shape[0]
+
+    def struct(self) -> Particles:
+        return Particles(self.n, _ptr(self.x), _ptr(self.u), _ptr(self.z), _ptr(self.mass),
+                         _ptr(self.w), _ptr(self.kind))
+
+
+def make_config(a0=0.0, tau=1.0, t0=0.0, dt=0.02, softening=1e-3, box=0.0, t_switch=0.0,
+                lambda_um=0.8, polarization=0, envelope=ENV_SIN2,
+                boundary=BOUNDARY_OPEN) -> Config:
+    return Config(a0, tau, t0, dt, softening, box, t_switch, lambda_um, polarization, envelope,
+                  boundary, 0)
+
+
+def config_from_workload(w) -> Config:
+    """Config of a ``synth.Workload``."""
+    return make_config(a0=w.a0, tau=w.tau, t0=w.t0, dt=w.dt, softening=w.eps, box=w.box,
+                       t_switch=w.t_switch, lambda_um=w.lambda_um, polarization=w.pol,
+                       envelope=w.env, boundary=w.boundary)
+
+
+class Context:
+    """An md_ctx: one or more clusters resident on the GPU."""
+
+    def __init__(self, configs, particles, stream=None):
+        configs = list(configs)
+        particles = list(particles)
+        assert len(configs) == len(particles) and configs
+        self._cfgs = (Config * len(configs))(*configs)
+        self._parts = (Particles * len(particles))(*[p.struct() for p in particles])
+        self._keep = particles
+        self.sizes = [p.n for p in particles]
+        h = _ctx_p()
+        _check(_lib.md_init(C.byref(h), self._cfgs, len(configs), self._parts,
+                            C.c_void_p(stream) if stream else None))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.md_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def step(self, nsteps: int = 1):
+        _check(_lib.md_step(self._h, int(nsteps)))
+
+    def sync(self):
+        _check(_lib.md_sync(self._h))
+
+    def step_index(self) -> int:
+        v = C.c_int64(0)
+        _check(_lib.md_get_step(self._h, C.byref(v)))
+        return int(v.value)
+
+    def diagnostics(self, cluster: int = 0) -> dict:
+        d = Diag()
+        _check(_lib.md_diagnostics(self._h, cluster, C.byref(d)))
+        return {"step": d.step, "t": d.t, "ke": d.ke, "ke_ions": d.ke_ions,
+                "ke_electrons": d.ke_electrons, "pe": d.pe, "total": d.total,
+                "p": np.array(d.p[:]), "n_active": d.n_active, "n_nonfinite": d.n_nonfinite,
+                "charge_count": np.array(d.charge_count[:]),
+                "charge_weight": np.array(d.charge_weight[:])}
+
+    def get_particles(self, cluster: int = 0, out: HostParticles | None = None) -> HostParticles:
+        out = out or HostParticles.empty(self.sizes[cluster])
+        s = out.struct()
+        _check(_lib.md_get_particles(self._h, cluster, C.byref(s)))
+        return out
+
+    def set_particles(self, cluster: int, p: HostParticles):
+        s = p.struct()
+        _check(_lib.md_set_particles(self._h, cluster, C.byref(s)))
+
+    def fields(self, cluster: int = 0, potential: bool = False):
+        n = self.sizes[cluster]
+        e = np.zeros((n, 3))
+        phi = np.zeros(n) if potential else None
+        _check(_lib.md_get_fields(self._h, cluster, _ptr(e), _ptr(phi)))
+        return (e, phi) if potential else e
+
+    def tuning(self):
+        t = Tuning()
+        _check(_lib.md_get_tuning(self._h, C.byref(t)))
+        return t.as_tuple()
+
+    def set_tuning(self, threads, r, tile, ctas_per_sm=0, jsplit=0):
+        t = Tuning(threads, r, tile, ctas_per_sm, jsplit)
+        _check(_lib.md_set_tuning(self._h, C.byref(t)))
+
+    def autotune(self, steps: int = 3):
+        n = len(tuning_list())
+        times = np.zeros(n)
+        _check(_lib.md_autotune(self._h, int(steps), _ptr(times), n))
+        return times
+
+
+def coulomb_field_device(src_ptr: int, ns: int, tgt_ptr: int, nt: int, eps2: float,
+                         self_offset: int, e_ptr: int, phi_ptr: int | None, stream: int | None):
+    """Stateless field evaluation on caller-owned device buffers (raw device
+    addresses, e.g. ``tensor.data_ptr()``)."""
+    _check(_lib.md_coulomb_field_device(C.c_void_p(src_ptr), int(ns), C.c_void_p(tgt_ptr),
+                                        int(nt), float(eps2), int(self_offset),
+                                        C.c_void_p(e_ptr),
+                                        C.c_void_p(phi_ptr) if phi_ptr else None,
+                                        C.c_void_p(stream) if stream else None))

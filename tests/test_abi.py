@@ -1,0 +1,93 @@
+"""The C ABI library builds for sm_103a, loads, exports every symbol
+include/md.h declares, and rejects bad arguments on the host (no GPU needed:
+no compute call is made here)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1307_3711_gb300 import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def md():
+    build.build()
+    from paper_1307_3711_gb300 import md as m
+    return m
+
+
+def header_symbols():
+    txt = open(os.path.join(ROOT, "include", "md.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(md_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol(md):
+    lib = C.CDLL(build.LIB)
+    syms = header_symbols()
+    assert len(syms) >= 15
+    for s in syms:
+        assert hasattr(lib, s), s
+    assert set(syms) == set(md.EXPORTED)
+
+
+def test_si_helpers_match_oracle(md):
+    """Eqs. 1-2 and K_C on the library side agree with the oracle's own code."""
+    for lam in (0.4, 0.8, 1.06):
+        assert md.coulomb_constant(lam) == pytest.approx(oracle.coulomb_constant(lam), rel=1e-15)
+    assert md.a0_from_intensity(1e16, 0.8) == pytest.approx(oracle.a0_from_intensity(1e16, 0.8),
+                                                            rel=1e-15)
+    assert md.n_atoms(82.0, 2.4) == pytest.approx(oracle.n_atoms(82.0, 2.4), rel=1e-15)
+
+
+def test_tuning_list(md):
+    lst = md.tuning_list()
+    assert len(lst) >= 4
+    for threads, r, tile, _, _ in lst:
+        assert threads % 32 == 0 and r >= 1 and tile % 16 == 0
+
+
+def _one(md, **kw):
+    p = md.HostParticles(np.zeros((2, 3)), np.zeros((2, 3)), [1, -1], [1000.0, 1.0], [1.0, 1.0])
+    return md.make_config(**kw), p
+
+
+@pytest.mark.parametrize("kw,what", [
+    ({"dt": 0.0}, "dt"), ({"softening": 0.0}, "softening"), ({"lambda_um": -1.0}, "lambda"),
+    ({"polarization": 2}, "polarization"), ({"envelope": 9}, "envelope"),
+    ({"boundary": 1, "box": 0.0}, "box"), ({"tau": 0.0, "envelope": 1}, "tau"),
+])
+def test_init_rejects_bad_config_on_host(md, kw, what):
+    cfg, p = _one(md, **kw)
+    with pytest.raises(md.MDError) as ei:
+        md.Context([cfg], [p])
+    assert ei.value.status == md.MD_ERR_ARG
+    assert what in str(ei.value)
+
+
+def test_init_rejects_inconsistent_particles(md):
+    cfg = md.make_config()
+    p = md.HostParticles(np.zeros((2, 3)), np.zeros((2, 3)), [1, 1], [1000.0, 1.0], [1.0, 1.0],
+                         kind=[0, 1])
+    with pytest.raises(md.MDError) as ei:
+        md.Context([cfg], [p])
+    assert ei.value.status == md.MD_ERR_ARG
+    p = md.HostParticles(np.zeros((2, 3)), np.zeros((2, 3)), [1, -1], [0.0, 1.0], [1.0, 1.0])
+    with pytest.raises(md.MDError):
+        md.Context([cfg], [p])
+
+
+def test_init_without_gpu_fails_cleanly(md):
+    """Valid arguments but no usable GPU: a CUDA error status, not a crash."""
+    from tests.helpers import has_gpu
+    if has_gpu():
+        pytest.skip("a GPU is present")
+    cfg, p = _one(md)
+    with pytest.raises(md.MDError) as ei:
+        md.Context([cfg], [p])
+    assert ei.value.status in (md.MD_ERR_CUDA, md.MD_ERR_UNSUPPORTED)

@@ -1,0 +1,324 @@
+"""GPU parity of the CUDA hot path (through the C ABI) against the FP64 oracle.
+
+Field: floored relative error (per target, |E - E64| / max(|E64|, rms|E64|))
+with p99 <= 2e-5 for the FP32/Kahan sum.  Trajectories: compared over a few
+steps only (chaotic beyond); long runs by energy and momentum.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1307_3711_gb300 import synth
+from tests.helpers import force_error, summary
+
+pytestmark = pytest.mark.gpu
+
+FORCE_P99 = 2e-5
+
+
+@pytest.fixture(scope="module")
+def md():
+    from paper_1307_3711_gb300 import build
+    build.build()
+    from paper_1307_3711_gb300 import md as m
+    return m
+
+
+def ctx_for(md, w, **kw):
+    return md.Context([md.config_from_workload(w)], [md.HostParticles.from_cluster(w.cluster)],
+                      **kw)
+
+
+def oracle_state(c):
+    return oracle.State(c.x, c.u, c.z, c.mass, c.w, c.active)
+
+
+def oracle_params(w, nthreads=1):
+    return oracle.make_params(a0=w.a0, tau=w.tau, t0=w.t0, dt=w.dt, eps=w.eps,
+                              box=w.box, t_switch=w.t_switch, pol=w.pol, env=w.env,
+                              boundary=w.boundary, lambda_um=w.lambda_um)
+
+
+# ------------------------------------------------------------------ field --
+
+@pytest.mark.parametrize("n_ions,n_el", [(700, 2100), (1, 1), (5, 0), (1500, 1517)])
+def test_field_parity_small(md, n_ions, n_el):
+    """Several 512-source tiles plus a ragged tail, and degenerate sizes."""
+    c = synth.make_cluster(3, n_ions, n_el, synth.nm_to_len(3.0), 3, synth.MASS_XE, kT_e_ev=10)
+    w = synth.Workload("t", c, a0=0.07, pol=0, env=1, tau=300.0, eps=synth.nm_to_len(0.1),
+                       dt=0.02, nsteps=1)
+    with ctx_for(md, w) as ctx:
+        e, phi = ctx.fields(0, potential=True)
+    kc = oracle.coulomb_constant(0.8)
+    e64, phi64 = oracle.self_field(c.x, c.w * c.z, w.eps, kc, potential=True)
+    if c.n == 1:
+        assert np.all(e == 0) and np.all(np.abs(phi) < 1e-12)
+        return
+    err = force_error(e, e64)
+    s = summary(err)
+    assert s["p99"] <= FORCE_P99, s
+    perr = np.abs(phi - phi64) / np.sqrt(np.mean(phi64 ** 2))
+    assert np.percentile(perr, 99) < 2e-5
+
+
+def test_field_parity_headline_sampled(md):
+    """The 200k-particle workload in its benchmarked launch configuration:
+    400 sampled targets against the oracle."""
+    w = synth.headline_200k(0)
+    c = w.cluster
+    with ctx_for(md, w) as ctx:
+        e = ctx.fields(0)
+    rng = np.random.default_rng(5)
+    idx = rng.choice(c.n, 400, replace=False)
+    kc = oracle.coulomb_constant(0.8)
+    e64 = oracle.coulomb_field(c.x[idx], c.x, c.w * c.z, w.eps, kc, self_idx=idx, nthreads=8)
+    s = summary(force_error(e[idx], e64))
+    assert s["p99"] <= FORCE_P99, s
+
+
+def test_stateless_field_entry_point(md):
+    """md_coulomb_field_device on caller (torch) device buffers; targets that
+    are not sources, ragged sizes, and the self term removed from phi."""
+    import torch
+    rng = np.random.default_rng(9)
+    kc = oracle.coulomb_constant(0.8)
+    ns, nt = 1237, 777
+    xs = rng.normal(size=(ns, 3)) * 0.02
+    qs = rng.choice([-1.0, 1.0, 3.0], size=ns)
+    xt = rng.normal(size=(nt, 3)) * 0.02
+    eps = 1e-3
+    src = torch.tensor(np.c_[xs, kc * qs], dtype=torch.float32, device="cuda")
+    tgt = torch.tensor(np.c_[xt, np.zeros(nt)], dtype=torch.float32, device="cuda")
+    e = torch.zeros((nt, 3), dtype=torch.float64, device="cuda")
+    phi = torch.zeros(nt, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    md.coulomb_field_device(src.data_ptr(), ns, tgt.data_ptr(), nt, eps * eps, -1, e.data_ptr(),
+                            phi.data_ptr(), stream)
+    torch.cuda.synchronize()
+    e64, phi64 = oracle.coulomb_field(xt, xs, qs, eps, kc, potential=True)
+    assert summary(force_error(e.cpu().numpy(), e64))["p99"] <= FORCE_P99
+    np.testing.assert_allclose(phi.cpu().numpy(), phi64, rtol=1e-5,
+                               atol=1e-5 * np.abs(phi64).max())
+    # targets = sources: self term excluded from phi, zero self force
+    e2 = torch.zeros((ns, 3), dtype=torch.float64, device="cuda")
+    phi2 = torch.zeros(ns, dtype=torch.float64, device="cuda")
+    md.coulomb_field_device(src.data_ptr(), ns, src.data_ptr(), ns, eps * eps, 0, e2.data_ptr(),
+                            phi2.data_ptr(), stream)
+    torch.cuda.synchronize()
+    e64, phi64 = oracle.self_field(xs, qs, eps, kc, potential=True)
+    assert summary(force_error(e2.cpu().numpy(), e64))["p99"] <= FORCE_P99
+    np.testing.assert_allclose(phi2.cpu().numpy(), phi64, rtol=1e-4,
+                               atol=2e-5 * np.abs(phi64).max())
+    with pytest.raises(md.MDError):
+        md.coulomb_field_device(src.data_ptr() + 4, ns, tgt.data_ptr(), nt, eps * eps, -1,
+                                e.data_ptr(), 0, stream)
+
+
+# ------------------------------------------------------------------ steps --
+
+def test_step_parity_short_2k(md):
+    """2k-particle 2 nm case: positions and momenta after 10 steps agree with
+    the FP64 oracle (before chaos amplifies the FP32 field error)."""
+    w = synth.plain_fp64_2k(0)
+    with ctx_for(md, w) as ctx:
+        ctx.step(10)
+        g = ctx.get_particles(0)
+    st = oracle_state(w.cluster)
+    oracle.md_steps(st, oracle_params(w), 10, nthreads=4)
+    r0 = synth.nm_to_len(2.0)
+    assert np.abs(g.x - st.x).max() < 1e-6 * r0
+    uscale = np.abs(st.u).max()
+    assert np.percentile(np.abs(g.u - st.u).max(1), 99) < 2e-4 * uscale
+    assert g.z.tolist() == w.cluster.z.tolist()
+
+
+def test_diagnostics_parity_and_energy_conservation_2k(md):
+    """FP64 diagnostics match the oracle's at step 0; over the 200 steps of the
+    2k case with the laser off the GPU conserves energy like the oracle."""
+    w = synth.plain_fp64_2k(0)
+    w.a0 = 0.0
+    with ctx_for(md, w) as ctx:
+        d0 = ctx.diagnostics(0)
+        st = oracle_state(w.cluster)
+        p = oracle_params(w)
+        o0 = oracle.diagnostics(st, p)
+        scale = abs(o0["pe"])
+        assert d0["pe"] == pytest.approx(o0["pe"], rel=1e-5)
+        assert abs(d0["ke"] - o0["ke"]) < 1e-5 * scale
+        ctx.step(w.nsteps)
+        d1 = ctx.diagnostics(0)
+        g = ctx.get_particles(0)
+    oracle.md_steps(st, p, w.nsteps, nthreads=4)
+    o1 = oracle.diagnostics(st, p)
+    drift_gpu = abs(d1["total"] - d0["total"]) / d1["ke"]
+    drift_cpu = abs(o1["total"] - o0["total"]) / o1["ke"]
+    assert drift_gpu < 1.5e-3
+    assert drift_gpu < 2 * drift_cpu + 1e-5
+    # Newton's third law holds only to FP32 rounding in the per-target sums
+    pscale = np.sum(g.w * g.mass * np.linalg.norm(g.u, axis=1))
+    assert np.abs(d1["p"] - d0["p"]).max() < 1e-5 * pscale
+    assert d1["n_active"] == w.cluster.n and d1["n_nonfinite"] == 0
+    assert d1["charge_count"][1] == 1000
+
+
+@pytest.mark.parametrize("pol", [0, 1])
+def test_free_electron_light_cone_invariant_gpu(md, pol):
+    """One electron in the laser of Eqs. 4-9 (b0 = a0): gamma - u_z = 1 and
+    final drift ~ 0 after the sin^2 pulse, as in the oracle."""
+    a0, T = 0.5, 40 * math.pi
+    c = synth.Cluster(np.zeros((1, 3)), np.zeros((1, 3)), np.array([-1], np.int32), np.ones(1),
+                      np.ones(1), np.ones(1, np.uint8))
+    w = synth.Workload("e", c, a0=a0, pol=pol, env=1, tau=T, eps=1e-3, dt=0.02, nsteps=0)
+    nsteps = int(T / 0.02) + 20
+    with ctx_for(md, w) as ctx:
+        for k in range(0, nsteps, 500):
+            ctx.step(min(500, nsteps - k))
+            u = ctx.get_particles(0).u[0]
+            g = math.sqrt(1 + u @ u)
+            assert abs(g - u[2] - 1) < 5e-4 * a0 ** 2
+    st = oracle_state(c)
+    oracle.md_steps(st, oracle_params(w), nsteps)
+    np.testing.assert_allclose(u, st.u[0], atol=2e-5 * a0)
+
+
+def test_two_ion_closed_form_gpu(md):
+    """Two ions from rest (softening 1e-7 of the separation): t(r) closed form."""
+    kc = oracle.coulomb_constant(0.8)
+    q1, q2, m1, m2, d = 2, 3, 5000.0, 9000.0, 0.01
+    mu = m1 * m2 / (m1 + m2)
+    tc = math.sqrt(mu * d ** 3 / (2 * kc * q1 * q2))
+    dt = tc / 2000
+    f = kc * q1 * q2 / d ** 2
+    x = np.array([[0.0, 0, 0], [d, 0, 0]])
+    u = np.array([[+0.5 * dt * f / m1, 0, 0], [-0.5 * dt * f / m2, 0, 0]])
+    c = synth.Cluster(x, u, np.array([q1, q2], np.int32), np.array([m1, m2]), np.ones(2),
+                      np.ones(2, np.uint8))
+    w = synth.Workload("2ion", c, a0=0.0, pol=0, env=3, tau=1.0, eps=1e-7 * d, dt=dt, nsteps=0)
+    with ctx_for(md, w) as ctx:
+        ctx.step(9000)
+        g = ctx.get_particles(0)
+    xr = (g.x[1, 0] - g.x[0, 0]) / d
+    t_pred = tc * (math.sqrt(xr * (xr - 1)) + math.log(math.sqrt(xr) + math.sqrt(xr - 1)))
+    assert t_pred == pytest.approx(9000 * dt, rel=1e-5)
+
+
+# ------------------------------------------------- batching / determinism --
+
+@pytest.mark.parametrize("jsplit", [1, 3])
+def test_batched_clusters_equal_single_runs_bitwise(md, jsplit):
+    """A parameter scan of uneven clusters in one persistent launch gives
+    exactly the per-cluster results of separate contexts (same kernel
+    configuration and source split)."""
+    scan = synth.batched_scan(6, seed=3, n_min=200, n_max=3000)
+    cfgs, parts = [], []
+    for e in scan:
+        cl = synth.scan_cluster(e)
+        cfgs.append(md.make_config(a0=e.a0, tau=e.tau, dt=0.02, softening=synth.nm_to_len(0.1),
+                                   envelope=md.ENV_SIN2))
+        parts.append(md.HostParticles.from_cluster(cl))
+    with md.Context(cfgs, parts) as ctx:
+        ctx.set_tuning(128, 2, 512, 0, jsplit)
+        ctx.step(20)
+        batched = [ctx.get_particles(k) for k in range(len(scan))]
+    for k in range(len(scan)):
+        with md.Context([cfgs[k]], [parts[k]]) as one:
+            one.set_tuning(128, 2, 512, 0, jsplit)
+            one.step(20)
+            g = one.get_particles(0)
+        assert np.array_equal(g.x, batched[k].x)
+        assert np.array_equal(g.u, batched[k].u)
+
+
+def test_graph_replay_equals_direct_launches_and_tunings_agree(md):
+    """md_step(n) through the captured graph equals n single-step calls; every
+    kernel configuration with the same tile and source split gives identical
+    bits, and every configuration agrees with the others to FP32 level."""
+    w = synth.xe3_cluster(6000, seed=2)
+    with ctx_for(md, w) as a:
+        a.step(35)
+        ga = a.get_particles(0)
+        assert a.step_index() == 35
+    with ctx_for(md, w) as b:
+        for _ in range(35):
+            b.step(1)
+        gb = b.get_particles(0)
+    assert np.array_equal(ga.x, gb.x) and np.array_equal(ga.u, gb.u)
+    r0 = np.abs(w.cluster.x).max()
+    ref = None
+    for threads, r, tile, _, _ in md.tuning_list():
+        for jsplit in (1, 0):
+            with ctx_for(md, w) as c:
+                c.set_tuning(threads, r, tile, 0, jsplit)
+                c.step(17)
+                g = c.get_particles(0)
+            if ref is None:
+                ref = g
+            if tile == 512 and jsplit == 1:
+                assert np.array_equal(g.x, ref.x) and np.array_equal(g.u, ref.u)
+            else:
+                assert np.abs(g.x - ref.x).max() < 1e-6 * r0
+
+
+def test_split_sources_parity_and_determinism(md):
+    """Splitting the sources into segments (partial fields in scratch, summed
+    by the last segment's CTA) matches the oracle after a few steps and is
+    bitwise reproducible."""
+    w = synth.xe3_cluster(20000, seed=7)
+    outs = []
+    for _ in range(2):
+        with ctx_for(md, w) as c:
+            c.set_tuning(256, 4, 512, 0, 5)
+            assert c.tuning()[4] == 5
+            c.step(6)
+            outs.append(c.get_particles(0))
+    assert np.array_equal(outs[0].x, outs[1].x) and np.array_equal(outs[0].u, outs[1].u)
+    st = oracle_state(w.cluster)
+    oracle.md_steps(st, oracle_params(w), 6, nthreads=8)
+    r0 = np.abs(w.cluster.x).max()
+    assert np.abs(outs[0].x - st.x).max() < 1e-6 * r0
+    du = np.abs(outs[0].u - st.u).max(1)
+    assert np.percentile(du, 99) < 1e-4 * np.abs(st.u).max()
+
+
+def test_autotune_restores_state(md):
+    w = synth.xe3_cluster(8000, seed=4)
+    with ctx_for(md, w) as ctx:
+        ctx.step(3)
+        before = ctx.get_particles(0)
+        times = ctx.autotune(2)
+        after = ctx.get_particles(0)
+        assert ctx.step_index() == 3
+        assert np.all(times > 0)
+        assert np.array_equal(before.x, after.x) and np.array_equal(before.u, after.u)
+
+
+def test_set_particles_round_trip(md):
+    w = synth.xe3_cluster(3000, seed=6)
+    with ctx_for(md, w) as ctx:
+        ctx.step(4)
+        g = ctx.get_particles(0)
+        g.x[:] += 0.001
+        ctx.set_particles(0, g)
+        h = ctx.get_particles(0)
+        assert np.array_equal(g.x, h.x) and np.array_equal(g.u, h.u)
+        assert np.array_equal(g.kind, h.kind)
+
+
+def test_periodic_boundary_wraps_into_box(md):
+    """Sec. II periodic box: positions stay in [-L/2, L/2) and match the oracle
+    over a few steps of a hot electron gas."""
+    c = synth.make_cluster(8, 200, 600, 0.01, 3, synth.MASS_XE, kT_e_ev=5000.0)
+    L = 0.02
+    w = synth.Workload("box", c, a0=0.0, pol=0, env=3, tau=1.0, eps=1e-3, dt=0.05, nsteps=0,
+                       boundary=1, box=L)
+    with ctx_for(md, w) as ctx:
+        ctx.step(40)
+        g = ctx.get_particles(0)
+    assert g.x.min() >= -L / 2 and g.x.max() <= L / 2
+    st = oracle_state(c)
+    oracle.md_steps(st, oracle_params(w), 40)
+    d = np.abs(g.x - st.x)
+    d = np.minimum(d, L - d)
+    assert np.percentile(d.max(1), 90) < 1e-5 * L
