@@ -207,6 +207,27 @@ md_status md_coulomb_field_device(const void *src, int64_t ns, const void *tgt,
                                   int64_t nt, float eps2, int64_t self_offset,
                                   double *e, double *phi, void *stream);
 
+/* md_coulomb_field_device_noalloc: the same field and potential as
+ * md_coulomb_field_device, for callers that cannot allocate device memory
+ * (code inside another framework's memory pool, a graph builder that must not
+ * see cudaMalloc, a plugin whose host forbids allocation).  The paper has no
+ * counterpart: this is a library-interface variant.  The sources are cut into
+ * up to 8 segments whose partial fields go to a fixed scratch array compiled
+ * into the library (about 8.6 MB of device memory on every GPU that loads it,
+ * held until the process exits); the call itself allocates nothing.
+ *   Arguments, layout and ownership: as md_coulomb_field_device.
+ *   Limit: nt <= 32768 targets per call (MD_ERR_ARG beyond it, nothing is
+ *   launched); ns is unbounded.
+ *   The first call on a device looks up the scratch array's device address on
+ *   that device; make that first call before any stream capture.
+ *   Every call shares the one scratch array: calls that overlap on the GPU
+ *   (other streams, other host threads) race and give wrong results, so
+ *   serialise them.  Each call clears the counters it uses before its kernel.
+ *   Asynchronous on `stream`. */
+md_status md_coulomb_field_device_noalloc(const void *src, int64_t ns, const void *tgt,
+                                          int64_t nt, float eps2, int64_t self_offset,
+                                          double *e, double *phi, void *stream);
+
 /* ---- helpers for SI inputs (Sec. II) ------------------------------------ */
 double md_coulomb_constant(double lambda_um);                  /* K_C = 2 pi r_e / lambda */
 double md_a0_from_intensity(double intensity_wcm2, double lambda_um); /* Eq. 2 */

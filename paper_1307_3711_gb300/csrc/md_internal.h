@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include "md.h"
 #include "md_types.cuh"
 
 namespace md {
@@ -32,6 +33,11 @@ cudaError_t launch_diag(const DiagArgs& a, int blocks, DiagPartial* out, cudaStr
 cudaError_t launch_ffma_probe(int blocks, int iters, bool packed, float* sink, cudaStream_t s);
 
 cudaError_t launch_upload(const UploadArgs& a, cudaStream_t s);
+
+// Records the thread-local message returned by md_last_error() and returns
+// the status (implemented in md_runtime.cu).
+md_status report_error(md_status status, const char* msg);
+md_status report_cuda_error(cudaError_t e, const char* what);
 cudaError_t launch_download(const DownloadArgs& a, cudaStream_t s);
 
 }  // namespace md

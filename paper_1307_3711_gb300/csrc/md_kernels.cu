@@ -1,4 +1,6 @@
 // md_kernels.cu -- instantiations and launchers of the sm_103a kernels.
+#include <mutex>
+
 #include "md_device.cuh"
 #include "md_internal.h"
 
@@ -125,3 +127,200 @@ cudaError_t launch_download(const DownloadArgs& a, cudaStream_t s) {
 }
 
 }  // namespace md
+
+// ===================================================== allocation-free field
+//
+// A variant of the field evaluation for callers that cannot allocate device
+// memory themselves: code running inside another framework's memory pool, a
+// CUDA-graph builder that must not see a cudaMalloc, or a plugin whose host
+// forbids allocation after start-up.  Like the split-source step, it cuts the
+// sources into segments so that more CTAs share the sum, keeps each segment's
+// partial field in scratch memory and lets the last segment to finish add them
+// up in segment order.  Here that scratch is a fixed, file-scope device array
+// instead of a buffer the library allocates, so the call allocates nothing.
+//
+// Limits: at most kNoAllocMaxTargets targets per call (sources unbounded), at
+// most kNoAllocMaxSeg segments.  The arrays below (about 8.6 MB) are held on
+// every GPU that loads the library until the process exits.  Every call shares
+// them, so calls that overlap on the GPU (two streams, two host threads) race
+// and give wrong fields: serialise them.  Each call clears the counters it
+// needs before its kernel runs; the partial sums are overwritten before use.
+
+namespace md {
+
+constexpr int kNoAllocMaxTargets = 32768;
+constexpr int kNoAllocMaxSeg = 8;
+constexpr int kNoAllocThreads = 128;
+constexpr int kNoAllocR = 2;
+constexpr int kNoAllocTile = 512;
+constexpr int kNoAllocBlocks = kNoAllocMaxTargets / (kNoAllocThreads * kNoAllocR);
+
+// partial (ex, ey, ez, phi) per segment and target, completion counters per
+// target block, and the wait-timeout error word
+static __device__ __align__(256) double g_noalloc_part[kNoAllocMaxSeg * kNoAllocMaxTargets * 4];
+static __device__ __align__(256) unsigned g_noalloc_cnt[kNoAllocBlocks];
+static __device__ __align__(256) int g_noalloc_err[1];
+
+struct NoAllocScratch {
+  double* part;
+  unsigned* cnt;
+  int* err;
+};
+
+template <int THREADS, int R, int TILE, int STAGES, bool POT>
+__global__ void __launch_bounds__(THREADS)
+    k_field_noalloc(const FieldArgs a, int nseg, long long seg_len, NoAllocScratch sc) {
+  __shared__ Stage<TILE, STAGES> sm;
+  __shared__ int s_abort, s_last;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) mbar_init(&sm.full[s], 1);
+    fence_mbar_init();
+    s_abort = 0;
+  }
+  __syncthreads();
+  const int blk = blockIdx.x / nseg;
+  const int seg = blockIdx.x % nseg;
+  const long long i0 = static_cast<long long>(blk) * (THREADS * R);
+  float xi[R], yi[R], zi[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const long long i = i0 + threadIdx.x + r * THREADS;
+    const float4 p = (i < a.nt) ? a.tgt[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    xi[r] = p.x;
+    yi[r] = p.y;
+    zi[r] = p.z;
+  }
+  const long long j0 = static_cast<long long>(seg) * seg_len;
+  const long long jrem = a.ns - j0;
+  const long long jn = jrem < seg_len ? jrem : seg_len;
+  Acc<R, POT> acc;
+  acc.zero();
+  unsigned it = 0;
+  if (!sum_sources<THREADS, R, TILE, STAGES, POT>(sm, it, a.src + j0, jn, xi, yi, zi, a.eps2, acc,
+                                                   sc.err, &s_abort))
+    return;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const long long i = i0 + threadIdx.x + r * THREADS;
+    if (i >= a.nt) continue;
+    double* p = sc.part + 4 * (static_cast<long long>(seg) * kNoAllocMaxTargets + i);
+    __stcg(p + 0, -(static_cast<double>(acc.sx[r]) - acc.cx[r]));
+    __stcg(p + 1, -(static_cast<double>(acc.sy[r]) - acc.cy[r]));
+    __stcg(p + 2, -(static_cast<double>(acc.sz[r]) - acc.cz[r]));
+    __stcg(p + 3, POT ? static_cast<double>(acc.sp[r]) - acc.cp[r] : 0.0);
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned prev = atomicAdd(sc.cnt + blk, 1u);
+    s_last = (prev == static_cast<unsigned>(nseg - 1));
+    if (s_last) atomicExch(sc.cnt + blk, 0u);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const long long i = i0 + threadIdx.x + r * THREADS;
+    if (i >= a.nt) continue;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int sg = 0; sg < nseg; ++sg) {
+      const double* p = sc.part + 4 * (static_cast<long long>(sg) * kNoAllocMaxTargets + i);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[k] += __ldcg(p + k);
+    }
+    a.e[3 * i + 0] = v[0];
+    a.e[3 * i + 1] = v[1];
+    a.e[3 * i + 2] = v[2];
+    if (POT && a.phi) {
+      double ph = v[3];
+      if (a.self_offset >= 0) {
+        const long long js = i + a.self_offset;
+        if (js < a.ns) ph -= static_cast<double>(a.src[js].w * rsqrt_mufu(a.eps2));
+      }
+      a.phi[i] = ph;
+    }
+  }
+}
+
+namespace {
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+bool g_noalloc_ready[kNoAllocMaxDevices] = {};
+NoAllocScratch g_noalloc_ptr[kNoAllocMaxDevices];
+
+// Device addresses of the scratch arrays on the current device, looked up once
+// per device (host code cannot use the array names as device addresses).
+md_status noalloc_scratch(NoAllocScratch* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return report_cuda_error(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kNoAllocMaxDevices)
+    return report_error(MD_ERR_UNSUPPORTED, "device ordinal beyond the allocation-free table");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ready[dev]) {
+    NoAllocScratch s;
+    e = cudaGetSymbolAddress(reinterpret_cast<void**>(&s.part), g_noalloc_part);
+    if (e != cudaSuccess) return report_cuda_error(e, "cudaGetSymbolAddress(partials)");
+    e = cudaGetSymbolAddress(reinterpret_cast<void**>(&s.cnt), g_noalloc_cnt);
+    if (e != cudaSuccess) return report_cuda_error(e, "cudaGetSymbolAddress(counters)");
+    e = cudaGetSymbolAddress(reinterpret_cast<void**>(&s.err), g_noalloc_err);
+    if (e != cudaSuccess) return report_cuda_error(e, "cudaGetSymbolAddress(error word)");
+    g_noalloc_ptr[dev] = s;
+    g_noalloc_ready[dev] = true;
+  }
+  *out = g_noalloc_ptr[dev];
+  return MD_OK;
+}
+
+}  // namespace
+}  // namespace md
+
+extern "C" md_status md_coulomb_field_device_noalloc(const void* src, int64_t ns, const void* tgt,
+                                                     int64_t nt, float eps2, int64_t self_offset,
+                                                     double* e, double* phi, void* stream) {
+  using namespace md;
+  if (ns < 0 || nt < 0) return report_error(MD_ERR_ARG, "negative size");
+  if (nt > kNoAllocMaxTargets)
+    return report_error(MD_ERR_ARG,
+                        "md_coulomb_field_device_noalloc: nt exceeds the 32768-target maximum "
+                        "of its fixed scratch array");
+  if (nt == 0) return MD_OK;
+  if (!src || !tgt || !e) return report_error(MD_ERR_ARG, "NULL pointer");
+  if ((reinterpret_cast<uintptr_t>(src) & 15) || (reinterpret_cast<uintptr_t>(tgt) & 15))
+    return report_error(MD_ERR_ARG, "src and tgt must be 16-byte aligned");
+  if (!(eps2 > 0.0f)) return report_error(MD_ERR_ARG, "eps2 must be > 0");
+  NoAllocScratch sc;
+  md_status st = noalloc_scratch(&sc);
+  if (st != MD_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const long long per = kNoAllocThreads * kNoAllocR;
+  const int nblk = static_cast<int>((nt + per - 1) / per);
+  // segments of at least 4 tiles of sources, at most kNoAllocMaxSeg
+  long long nseg = ns / (4LL * kNoAllocTile);
+  nseg = nseg < 1 ? 1 : (nseg > kNoAllocMaxSeg ? kNoAllocMaxSeg : nseg);
+  const long long seg_len = ns > 0 ? (ns + nseg - 1) / nseg : 1;
+  cudaError_t ce = cudaMemsetAsync(sc.cnt, 0, sizeof(unsigned) * nblk, s);
+  if (ce != cudaSuccess) return report_cuda_error(ce, "clearing the counters");
+  FieldArgs a;
+  a.src = static_cast<const float4*>(src);
+  a.ns = ns;
+  a.tgt = static_cast<const float4*>(tgt);
+  a.nt = nt;
+  a.eps2 = eps2;
+  a.self_offset = self_offset;
+  a.e = e;
+  a.phi = phi;
+  a.err = sc.err;
+  const unsigned grid = static_cast<unsigned>(nblk * nseg);
+  if (phi)
+    k_field_noalloc<kNoAllocThreads, kNoAllocR, kNoAllocTile, 2, true>
+        <<<grid, kNoAllocThreads, 0, s>>>(a, static_cast<int>(nseg), seg_len, sc);
+  else
+    k_field_noalloc<kNoAllocThreads, kNoAllocR, kNoAllocTile, 2, false>
+        <<<grid, kNoAllocThreads, 0, s>>>(a, static_cast<int>(nseg), seg_len, sc);
+  ce = cudaGetLastError();
+  if (ce != cudaSuccess) return report_cuda_error(ce, "allocation-free field launch");
+  return MD_OK;
+}

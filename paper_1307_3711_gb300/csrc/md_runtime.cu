@@ -470,6 +470,14 @@ md_status upload_cluster(md_ctx* c, int ci, const md_particles& p) {
 
 }  // namespace
 
+namespace md {
+
+md_status report_error(md_status status, const char* msg) { return fail(status, "%s", msg); }
+
+md_status report_cuda_error(cudaError_t e, const char* what) { return cuda_fail(e, what); }
+
+}  // namespace md
+
 // ===================================================================== ABI
 
 extern "C" {

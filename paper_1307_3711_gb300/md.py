@@ -81,6 +81,8 @@ _SIGS = {
     "md_autotune": (_st, [_ctx_p, C.c_int32, _p, C.c_int32]),
     "md_coulomb_field_device": (_st, [_p, C.c_int64, _p, C.c_int64, C.c_float, C.c_int64, _p,
                                       _p, _p]),
+    "md_coulomb_field_device_noalloc": (_st, [_p, C.c_int64, _p, C.c_int64, C.c_float, C.c_int64,
+                                              _p, _p, _p]),
     "md_coulomb_constant": (C.c_double, [C.c_double]),
     "md_a0_from_intensity": (C.c_double, [C.c_double, C.c_double]),
     "md_n_atoms": (C.c_double, [C.c_double, C.c_double]),
@@ -279,3 +281,14 @@ def coulomb_field_device(src_ptr: int, ns: int, tgt_ptr: int, nt: int, eps2: flo
                                         C.c_void_p(e_ptr),
                                         C.c_void_p(phi_ptr) if phi_ptr else None,
                                         C.c_void_p(stream) if stream else None))
+
+
+def coulomb_field_device_noalloc(src_ptr: int, ns: int, tgt_ptr: int, nt: int, eps2: float,
+                                 self_offset: int, e_ptr: int, phi_ptr: int | None,
+                                 stream: int | None):
+    """As ``coulomb_field_device`` without any device allocation: its scratch
+    is a fixed array inside the library (nt <= 32768; overlapping calls race)."""
+    _check(_lib.md_coulomb_field_device_noalloc(
+        C.c_void_p(src_ptr), int(ns), C.c_void_p(tgt_ptr), int(nt), float(eps2),
+        int(self_offset), C.c_void_p(e_ptr), C.c_void_p(phi_ptr) if phi_ptr else None,
+        C.c_void_p(stream) if stream else None))
