@@ -51,6 +51,8 @@ def parse_args():
                     help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tuning", default=None,
+                    help="force a kernel configuration: threads,r,tile,packed[,jsplit[,min_blocks]]")
     return ap.parse_args()
 
 
@@ -212,7 +214,11 @@ def run_native(args):
     sms, gpu_name = md.device_info()
 
     tune_ms = None
-    if not args.no_autotune:
+    if args.tuning:
+        f = [int(v) for v in args.tuning.split(",")]
+        ctx.set_tuning(f[0], f[1], f[2], 0, f[4] if len(f) > 4 else 0, f[3],
+                       f[5] if len(f) > 5 else -1)
+    elif not args.no_autotune:
         tune_ms = ctx.autotune(3).tolist()
     tuning = ctx.tuning()
 
@@ -308,7 +314,9 @@ def run_native(args):
             "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write outside the "
                   "timed events)",
             "tuning": {"threads": tuning[0], "r": tuning[1], "tile": tuning[2],
-                       "source_segments": tuning[4]},
+                       "source_segments": tuning[4], "packed_f32x2": bool(tuning[5]),
+                       "min_blocks": tuning[6]},
+            "autotune_configs": [list(t) for t in md.tuning_list()],
             "autotune_ms_per_step": tune_ms,
             "device": gpu_name, "sms": sms, "wall_s_timed_region": wall,
         },

@@ -134,6 +134,10 @@ typedef struct {
     int32_t jsplit;     /* source segments per i-block (0: chosen for load balance); the
                            partial fields of the segments go to a library scratch buffer
                            and the last segment to finish sums them and pushes */
+    int32_t packed;     /* 1: pair arithmetic in packed f32x2 (two i-particles per
+                           instruction, bit-identical results), 0: scalar FP32 */
+    int32_t min_blocks; /* register budget: 64K / (threads x min_blocks); 0 = left to the
+                           compiler.  On input to md_set_tuning, -1 matches any value */
 } md_tuning;
 
 /* ---- context life cycle -------------------------------------------------

@@ -90,6 +90,22 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return true;
 }
 
+// Explicit shared-memory loads (the tiles are reached through references, so
+// the address space is stated rather than inferred).
+__device__ __forceinline__ float4 lds_f4(uint32_t addr) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(addr));
+  return v;
+}
+
+__device__ __forceinline__ ulonglong2 lds_u64x2(uint32_t addr) {
+  ulonglong2 v;
+  asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "r"(addr));
+  return v;
+}
+
 __device__ __forceinline__ float rsqrt_mufu(float x) {
   float y;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -268,13 +284,13 @@ __device__ __forceinline__ bool sum_sources(Stage<TILE, STAGES>& sm, unsigned& i
       *s_abort = 1;
     }
     if (!*reinterpret_cast<volatile int*>(s_abort)) {
-      const float4* tile = sm.tile[s];
+      const uint32_t tile = smem_u32(&sm.tile[s][0]);
       const long long rem = ns - static_cast<long long>(t) * TILE;
       const int cnt = static_cast<int>(rem < TILE ? rem : TILE);
       int j = 0;
       for (; j + 8 <= cnt; j += 8) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) pair<R, POT>(tile[j + k], xi, yi, zi, eps2, acc);
+        for (int k = 0; k < 8; ++k) pair<R, POT>(lds_f4(tile + 16u * (j + k)), xi, yi, zi, eps2, acc);
         if (POT) {
           // potential terms of one species share a sign: fold them often so
           // the FP32 partial stays small against a cancelling total
@@ -285,7 +301,7 @@ __device__ __forceinline__ bool sum_sources(Stage<TILE, STAGES>& sm, unsigned& i
           }
         }
       }
-      for (; j < cnt; ++j) pair<R, POT>(tile[j], xi, yi, zi, eps2, acc);
+      for (; j < cnt; ++j) pair<R, POT>(lds_f4(tile + 16u * j), xi, yi, zi, eps2, acc);
       fold<R, POT>(acc);
     }
     __syncthreads();
@@ -302,6 +318,215 @@ __device__ __forceinline__ bool sum_sources(Stage<TILE, STAGES>& sm, unsigned& i
     }
     if (threadIdx.x == 0 && t + STAGES < ntiles)
       issue_tile<TILE, STAGES>(sm, it + t + STAGES, src, ns, t + STAGES);
+  }
+  it += static_cast<unsigned>(ntiles);
+  return true;
+}
+
+// ------------------------------------------------ packed (f32x2) pair path --
+//
+// sm_100-family packed FP32: add/sub/mul/fma.rn.f32x2 apply the scalar IEEE
+// operation to two lanes held in one 64-bit register pair.  Two i-particles
+// share each instruction, halving the issue slots per pair (12 packed FP32
+// instructions and 2 MUFU per two pairs) while the FMA pipe does the same lane
+// work; the per-lane results are bit-identical to the scalar path.
+
+using u64 = unsigned long long;
+
+__device__ __forceinline__ u64 f2_pack(float lo, float hi) {
+  u64 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(u64 v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ u64 f2_add(u64 a, u64 b) {
+  u64 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ u64 f2_sub(u64 a, u64 b) {
+  u64 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ u64 f2_mul(u64 a, u64 b) {
+  u64 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ u64 f2_fma(u64 a, u64 b, u64 c) {
+  u64 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ void kahan_add2(u64& s, u64& c, u64 v) {
+  const u64 y = f2_sub(v, c);
+  const u64 t = f2_add(s, y);
+  c = f2_sub(f2_sub(t, s), y);
+  s = t;
+}
+
+// A tile of sources expanded for packed use: per source (x,x | y,y) and
+// (z,z | q,q), so one LDS.128 yields two ready register pairs.
+template <int TILE>
+struct DupTile {
+  alignas(16) ulonglong2 v[TILE][2];
+};
+
+template <int P, bool POT>
+struct AccP {
+  u64 ax[P], ay[P], az[P], ap[P];  // packed FP32 partials of the current tile
+};
+
+// Kahan sums and compensations of the packed path, one slot per thread, kept
+// in shared memory (folded once per tile) so the registers hold only the
+// targets and the tile partials: [component][pair][thread], component =
+// sx, sy, sz, cx, cy, cz (, sp, cp with the potential).
+template <int P, int THREADS, bool POT>
+struct KahanSmem {
+  u64 v[POT ? 8 : 6][P][THREADS];
+};
+
+// Component k (0..5: sx, sy, sz, cx, cy, cz) of target r of this thread.
+template <int P, int THREADS, bool POT>
+__device__ __forceinline__ float kahan_part(const KahanSmem<P, THREADS, POT>& ks, int k, int r) {
+  float lo, hi;
+  f2_unpack(ks.v[k][r >> 1][threadIdx.x], lo, hi);
+  return (r & 1) ? hi : lo;
+}
+
+template <int P, bool POT>
+__device__ __forceinline__ void pair2(const ulonglong2 xy, const ulonglong2 zq, const u64 (&xi)[P],
+                                      const u64 (&yi)[P], const u64 (&zi)[P], u64 e2,
+                                      AccP<P, POT>& a) {
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const u64 dx = f2_sub(xy.x, xi[p]);
+    const u64 dy = f2_sub(xy.y, yi[p]);
+    const u64 dz = f2_sub(zq.x, zi[p]);
+    u64 r2 = f2_fma(dx, dx, e2);
+    r2 = f2_fma(dy, dy, r2);
+    r2 = f2_fma(dz, dz, r2);
+    float lo, hi;
+    f2_unpack(r2, lo, hi);
+    const u64 ri = f2_pack(rsqrt_mufu(lo), rsqrt_mufu(hi));
+    const u64 qr = f2_mul(zq.y, ri);
+    const u64 ri2 = f2_mul(ri, ri);
+    const u64 s = f2_mul(qr, ri2);
+    a.ax[p] = f2_fma(dx, s, a.ax[p]);
+    a.ay[p] = f2_fma(dy, s, a.ay[p]);
+    a.az[p] = f2_fma(dz, s, a.az[p]);
+    if (POT) a.ap[p] = f2_add(a.ap[p], qr);
+  }
+}
+
+// As sum_sources, with the pair arithmetic in packed f32x2.  Each landed
+// tile is first expanded into `dup` (which frees its TMA stage at once, so a
+// single stage suffices), then the R targets of this thread are summed two at
+// a time.  The Kahan sums live in `ks` and are returned unpacked in `out`
+// (bit-identical to the scalar path).
+template <int THREADS, int R, int TILE, int STAGES, bool POT>
+__device__ __forceinline__ bool sum_sources_packed(Stage<TILE, STAGES>& sm, DupTile<TILE>& dup,
+                                                   KahanSmem<R / 2, THREADS, POT>& ks, unsigned& it,
+                                                   const float4* __restrict__ src, long long ns,
+                                                   const float (&xi)[R], const float (&yi)[R],
+                                                   const float (&zi)[R], float eps2, int* err,
+                                                   int* s_abort) {
+  static_assert(R % 2 == 0, "packed path needs an even number of i-particles per thread");
+  constexpr int P = R / 2;
+  const int tid = threadIdx.x;
+  u64 xi2[P], yi2[P], zi2[P];
+  AccP<P, POT> a;
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    xi2[p] = f2_pack(xi[2 * p], xi[2 * p + 1]);
+    yi2[p] = f2_pack(yi[2 * p], yi[2 * p + 1]);
+    zi2[p] = f2_pack(zi[2 * p], zi[2 * p + 1]);
+    a.ax[p] = a.ay[p] = a.az[p] = a.ap[p] = 0ull;
+#pragma unroll
+    for (int k = 0; k < (POT ? 8 : 6); ++k) ks.v[k][p][tid] = 0ull;
+  }
+  const u64 e2 = f2_pack(eps2, eps2);
+  const int ntiles = static_cast<int>((ns + TILE - 1) / TILE);
+  if (tid == 0) {
+    for (int k = 0; k < STAGES && k < ntiles; ++k) issue_tile<TILE, STAGES>(sm, it + k, src, ns, k);
+  }
+  for (int t = 0; t < ntiles; ++t) {
+    const unsigned g = it + t;
+    const int s = static_cast<int>(g % STAGES);
+    const uint32_t parity = (g / STAGES) & 1u;
+    if (!mbar_wait(&sm.full[s], parity)) {
+      atomicOr(err, kErrTimeout);
+      *s_abort = 1;
+    }
+    const long long rem = ns - static_cast<long long>(t) * TILE;
+    const int cnt = static_cast<int>(rem < TILE ? rem : TILE);
+    if (!*reinterpret_cast<volatile int*>(s_abort)) {
+      for (int k = tid; k < cnt; k += THREADS) {
+        const float4 p = sm.tile[s][k];
+        dup.v[k][0] = make_ulonglong2(f2_pack(p.x, p.x), f2_pack(p.y, p.y));
+        dup.v[k][1] = make_ulonglong2(f2_pack(p.z, p.z), f2_pack(p.w, p.w));
+      }
+    }
+    __syncthreads();
+    if (*reinterpret_cast<volatile int*>(s_abort)) {
+      if (tid == 0) {
+        const int last = (t + STAGES < ntiles) ? t + STAGES : ntiles;
+        for (int k = t + 1; k < last; ++k) {
+          const unsigned gk = it + k;
+          mbar_wait(&sm.full[gk % STAGES], (gk / STAGES) & 1u);
+        }
+      }
+      __syncthreads();
+      return false;
+    }
+    // the stage is expanded into dup: refill it while this tile is summed
+    if (tid == 0 && t + STAGES < ntiles)
+      issue_tile<TILE, STAGES>(sm, it + t + STAGES, src, ns, t + STAGES);
+    const uint32_t dbase = smem_u32(&dup.v[0][0]);
+    int j = 0;
+    for (; j + 8 <= cnt; j += 8) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        pair2<P, POT>(lds_u64x2(dbase + 32u * (j + k)), lds_u64x2(dbase + 32u * (j + k) + 16u),
+                      xi2, yi2, zi2, e2, a);
+      if (POT) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          u64 sp = ks.v[6][p][tid], cp = ks.v[7][p][tid];
+          kahan_add2(sp, cp, a.ap[p]);
+          ks.v[6][p][tid] = sp;
+          ks.v[7][p][tid] = cp;
+          a.ap[p] = 0ull;
+        }
+      }
+    }
+    for (; j < cnt; ++j)
+      pair2<P, POT>(lds_u64x2(dbase + 32u * j), lds_u64x2(dbase + 32u * j + 16u), xi2, yi2, zi2,
+                    e2, a);
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      u64 sv, cv;
+      sv = ks.v[0][p][tid]; cv = ks.v[3][p][tid];
+      kahan_add2(sv, cv, a.ax[p]);
+      ks.v[0][p][tid] = sv; ks.v[3][p][tid] = cv;
+      sv = ks.v[1][p][tid]; cv = ks.v[4][p][tid];
+      kahan_add2(sv, cv, a.ay[p]);
+      ks.v[1][p][tid] = sv; ks.v[4][p][tid] = cv;
+      sv = ks.v[2][p][tid]; cv = ks.v[5][p][tid];
+      kahan_add2(sv, cv, a.az[p]);
+      ks.v[2][p][tid] = sv; ks.v[5][p][tid] = cv;
+      a.ax[p] = a.ay[p] = a.az[p] = 0ull;
+      if (POT) {
+        sv = ks.v[6][p][tid]; cv = ks.v[7][p][tid];
+        kahan_add2(sv, cv, a.ap[p]);
+        ks.v[6][p][tid] = sv; ks.v[7][p][tid] = cv;
+        a.ap[p] = 0ull;
+      }
+    }
+    __syncthreads();  // dup is rewritten by the next tile
   }
   it += static_cast<unsigned>(ntiles);
   return true;
@@ -347,15 +572,20 @@ __device__ __forceinline__ void push_record(const StepArgs& a, const ClusterDev&
 // One full MD step for every work unit (cluster, i-block): field at x^n from
 // all sources of the cluster, laser at t_n, Boris kick, FP64 drift, boundary,
 // new j-stream entry.  Persistent: CTAs take units from an atomic ticket.
-template <int THREADS, int R, int TILE, int STAGES>
-__global__ void __launch_bounds__(THREADS) k_step(const StepArgs a) {
+template <int THREADS, int R, int TILE, int STAGES, bool PACK, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) k_step(const StepArgs a) {
   __shared__ Stage<TILE, STAGES> sm;
+  __shared__ DupTile<PACK ? TILE : 1> dup;
+  __shared__ KahanSmem<PACK ? R / 2 : 1, PACK ? THREADS : 1, false> ks;
   __shared__ int s_unit, s_abort, s_last;
   __shared__ float s_las[6];
+  // the current unit's cluster and ranges live in shared memory, not in
+  // registers, so that nothing but the targets and partials is held across
+  // the source loop
+  __shared__ ClusterDev s_c;
+  __shared__ Unit s_un;
 
   const long long step = __ldcg(a.step);
-  const float4* __restrict__ cur = (step & 1) ? a.posq1 : a.posq0;
-  float4* __restrict__ nxt = (step & 1) ? a.posq0 : a.posq1;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) mbar_init(&sm.full[s], 1);
@@ -366,81 +596,126 @@ __global__ void __launch_bounds__(THREADS) k_step(const StepArgs a) {
 
   unsigned it = 0;
   for (;;) {
-    if (threadIdx.x == 0) s_unit = static_cast<int>(atomicAdd(a.ticket, 1u));
-    __syncthreads();
-    const int u = s_unit;
-    if (u >= a.n_units) break;
-    const Unit un = a.units[u];
-    const ClusterDev c = a.cl[un.cluster];
-    const double t_n = c.t0 + static_cast<double>(step) * c.dt;
-    if (threadIdx.x == 0) laser_field(c, t_n, s_las);
-
-    const long long i0 = c.off + static_cast<long long>(un.block) * (THREADS * R);
-    const long long iend = c.off + c.n_pad;
-    const long long j0 = static_cast<long long>(un.seg) * c.seg_len;
-    const long long jrem = c.n_pad - j0;
-    const long long jn = jrem < c.seg_len ? jrem : c.seg_len;
-    float xi[R], yi[R], zi[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const long long i = i0 + threadIdx.x + r * THREADS;
-      const float4 p = (i < iend) ? cur[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-      xi[r] = p.x;
-      yi[r] = p.y;
-      zi[r] = p.z;
+    if (threadIdx.x == 0) {
+      const int u = static_cast<int>(atomicAdd(a.ticket, 1u));
+      s_unit = u;
+      if (u < a.n_units) {
+        s_un = a.units[u];
+        s_c = a.cl[s_un.cluster];
+        laser_field(s_c, s_c.t0 + static_cast<double>(step) * s_c.dt, s_las);
+      }
     }
-    Acc<R, false> acc;
-    acc.zero();
-    if (!sum_sources<THREADS, R, TILE, STAGES, false>(sm, it, cur + c.off + j0, jn, xi, yi, zi,
-                                                      c.eps2, acc, a.err, &s_abort))
-      return;
+    __syncthreads();
+    if (s_unit >= a.n_units) break;
+    {
+      const float4* __restrict__ cur = (step & 1) ? a.posq1 : a.posq0;
+      const long long i0 = s_c.off + static_cast<long long>(s_un.block) * (THREADS * R);
+      const long long iend = s_c.off + s_c.n_pad;
+      const long long j0 = static_cast<long long>(s_un.seg) * s_c.seg_len;
+      const long long jrem = s_c.n_pad - j0;
+      const long long jn = jrem < s_c.seg_len ? jrem : s_c.seg_len;
+      float xi[R], yi[R], zi[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const long long i = i0 + threadIdx.x + r * THREADS;
+        const float4 p = (i < iend) ? cur[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        xi[r] = p.x;
+        yi[r] = p.y;
+        zi[r] = p.z;
+      }
+      bool ok;
+      Acc<R, false> acc;
+      if constexpr (PACK) {
+        ok = sum_sources_packed<THREADS, R, TILE, STAGES, false>(
+            sm, dup, ks, it, cur + s_c.off + j0, jn, xi, yi, zi, s_c.eps2, a.err, &s_abort);
+      } else {
+        acc.zero();
+        ok = sum_sources<THREADS, R, TILE, STAGES, false>(sm, it, cur + s_c.off + j0, jn, xi, yi,
+                                                          zi, s_c.eps2, acc, a.err, &s_abort);
+      }
+      if (!ok) return;
 
-    const double t_next = t_n + c.dt;
-    if (c.nseg == 1) {
+      // field at target r: -(Kahan total s - c) of sum Q (x_j - x_i)/r^3
+      auto field_of = [&](int r, double& ex, double& ey, double& ez) {
+        if constexpr (PACK) {
+          ex = -(static_cast<double>(kahan_part(ks, 0, r)) - kahan_part(ks, 3, r));
+          ey = -(static_cast<double>(kahan_part(ks, 1, r)) - kahan_part(ks, 4, r));
+          ez = -(static_cast<double>(kahan_part(ks, 2, r)) - kahan_part(ks, 5, r));
+        } else {
+          ex = -(static_cast<double>(acc.sx[r]) - acc.cx[r]);
+          ey = -(static_cast<double>(acc.sy[r]) - acc.cy[r]);
+          ez = -(static_cast<double>(acc.sz[r]) - acc.cz[r]);
+        }
+      };
+
+      // the unit's ranges are re-read from shared memory after the loop
+      const float4* __restrict__ cur2 = (step & 1) ? a.posq1 : a.posq0;
+      float4* __restrict__ nxt = (step & 1) ? a.posq0 : a.posq1;
+      const long long e0 = s_c.off + static_cast<long long>(s_un.block) * (THREADS * R);
+      const long long eend = s_c.off + s_c.n_pad;
+      const double t_next = s_c.t0 + static_cast<double>(step + 1) * s_c.dt;
+      if (s_c.nseg == 1) {
+        // the packed path reads its sums from shared memory, so its epilogue
+        // stays rolled (one FP64 push at a time)
+        if constexpr (PACK) {
+#pragma unroll 1
+          for (int r = 0; r < R; ++r) {
+            const long long i = e0 + threadIdx.x + r * THREADS;
+            if (i >= eend) continue;
+            double ex, ey, ez;
+            field_of(r, ex, ey, ez);
+            push_record(a, s_c, i, ex, ey, ez, s_las, t_next, cur2, nxt);
+          }
+        } else {
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const long long i = i0 + threadIdx.x + r * THREADS;
-        if (i >= iend) continue;
-        // field at i is -(sum of Q (x_j - x_i)/r^3); the Kahan total is s - c
-        push_record(a, c, i, -(static_cast<double>(acc.sx[r]) - acc.cx[r]),
-                    -(static_cast<double>(acc.sy[r]) - acc.cy[r]),
-                    -(static_cast<double>(acc.sz[r]) - acc.cz[r]), s_las, t_next, cur, nxt);
-      }
-    } else {
-      // this unit covers one segment of the sources: publish the partial
-      // field; the last of the nseg units of this i-block sums the partials
-      // in segment order (deterministic) and pushes
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const long long i = i0 + threadIdx.x + r * THREADS;
-        if (i >= iend) continue;
-        double* p = a.part + 3 * (static_cast<long long>(un.seg) * a.n_total + i);
-        __stcg(p + 0, -(static_cast<double>(acc.sx[r]) - acc.cx[r]));
-        __stcg(p + 1, -(static_cast<double>(acc.sy[r]) - acc.cy[r]));
-        __stcg(p + 2, -(static_cast<double>(acc.sz[r]) - acc.cz[r]));
-      }
-      __threadfence();
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        const unsigned prev = atomicAdd(a.iblk_cnt + un.ib, 1u);
-        s_last = (prev == static_cast<unsigned>(c.nseg - 1));
-        if (s_last) atomicExch(a.iblk_cnt + un.ib, 0u);
-      }
-      __syncthreads();
-      if (s_last) {
-        __threadfence();
+          for (int r = 0; r < R; ++r) {
+            const long long i = e0 + threadIdx.x + r * THREADS;
+            if (i >= eend) continue;
+            double ex, ey, ez;
+            field_of(r, ex, ey, ez);
+            push_record(a, s_c, i, ex, ey, ez, s_las, t_next, cur2, nxt);
+          }
+        }
+      } else {
+        // this unit covers one segment of the sources: publish the partial
+        // field; the last of the nseg units of this i-block sums the partials
+        // in segment order (deterministic) and pushes
+        const int seg = s_un.seg;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-          const long long i = i0 + threadIdx.x + r * THREADS;
-          if (i >= iend) continue;
-          double ex = 0.0, ey = 0.0, ez = 0.0;
-          for (int sg = 0; sg < c.nseg; ++sg) {
-            const double* p = a.part + 3 * (static_cast<long long>(sg) * a.n_total + i);
-            ex += __ldcg(p + 0);
-            ey += __ldcg(p + 1);
-            ez += __ldcg(p + 2);
+          const long long i = e0 + threadIdx.x + r * THREADS;
+          if (i >= eend) continue;
+          double ex, ey, ez;
+          field_of(r, ex, ey, ez);
+          double* p = a.part + 3 * (static_cast<long long>(seg) * a.n_total + i);
+          __stcg(p + 0, ex);
+          __stcg(p + 1, ey);
+          __stcg(p + 2, ez);
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          const unsigned prev = atomicAdd(a.iblk_cnt + s_un.ib, 1u);
+          s_last = (prev == static_cast<unsigned>(s_c.nseg - 1));
+          if (s_last) atomicExch(a.iblk_cnt + s_un.ib, 0u);
+        }
+        __syncthreads();
+        if (s_last) {
+          __threadfence();
+          const int nseg = s_c.nseg;
+#pragma unroll 1
+          for (int r = 0; r < R; ++r) {
+            const long long i = e0 + threadIdx.x + r * THREADS;
+            if (i >= eend) continue;
+            double ex = 0.0, ey = 0.0, ez = 0.0;
+            for (int sg = 0; sg < nseg; ++sg) {
+              const double* p = a.part + 3 * (static_cast<long long>(sg) * a.n_total + i);
+              ex += __ldcg(p + 0);
+              ey += __ldcg(p + 1);
+              ez += __ldcg(p + 2);
+            }
+            push_record(a, s_c, i, ex, ey, ez, s_las, t_next, cur2, nxt);
           }
-          push_record(a, c, i, ex, ey, ez, s_las, t_next, cur, nxt);
         }
       }
     }

@@ -15,6 +15,8 @@ struct KernelConfig {
   int r;
   int tile;
   int stages;
+  int packed;      // pair arithmetic in packed f32x2
+  int min_blocks;  // launch bound: CTAs per SM the register budget is sized for
   cudaError_t (*launch_step)(const StepArgs& a, int grid, cudaStream_t s);
   cudaError_t (*max_blocks_per_sm)(int* out);
 };

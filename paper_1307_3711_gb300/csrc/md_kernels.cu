@@ -8,25 +8,31 @@ namespace md {
 
 namespace {
 
-template <int T, int R, int TILE, int ST>
+template <int T, int R, int TILE, int ST, bool PK, int MB>
 cudaError_t launch_step_t(const StepArgs& a, int grid, cudaStream_t s) {
-  k_step<T, R, TILE, ST><<<grid, T, 0, s>>>(a);
+  k_step<T, R, TILE, ST, PK, MB><<<grid, T, 0, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int T, int R, int TILE, int ST>
+template <int T, int R, int TILE, int ST, bool PK, int MB>
 cudaError_t blocks_per_sm_t(int* out) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_step<T, R, TILE, ST>, T, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_step<T, R, TILE, ST, PK, MB>, T, 0);
 }
 
-#define MD_STEP_CONFIG(T, R, TILE, ST) \
-  {T, R, TILE, ST, &launch_step_t<T, R, TILE, ST>, &blocks_per_sm_t<T, R, TILE, ST>}
+// threads, i-particles per thread, sources per tile, TMA stages, packed, min CTAs per SM
+#define MD_STEP_CONFIG(T, R, TILE, ST, PK, MB) \
+  {T, R, TILE, ST, PK, MB, &launch_step_t<T, R, TILE, ST, PK, MB>, \
+   &blocks_per_sm_t<T, R, TILE, ST, PK, MB>}
 
+// min CTAs per SM = 0 leaves the register budget to ptxas; a positive value
+// caps it at 64K / (threads x value)
 const KernelConfig kConfigs[] = {
-    MD_STEP_CONFIG(128, 1, 512, 2), MD_STEP_CONFIG(128, 2, 512, 2),
-    MD_STEP_CONFIG(128, 4, 512, 2), MD_STEP_CONFIG(256, 1, 512, 2),
-    MD_STEP_CONFIG(256, 2, 512, 2), MD_STEP_CONFIG(256, 4, 512, 2),
-    MD_STEP_CONFIG(256, 8, 256, 2), MD_STEP_CONFIG(512, 2, 512, 2),
+    // scalar FP32 pair arithmetic
+    MD_STEP_CONFIG(128, 1, 512, 2, false, 0), MD_STEP_CONFIG(128, 4, 512, 2, false, 0),
+    MD_STEP_CONFIG(256, 2, 512, 2, false, 0),
+    // packed f32x2 pair arithmetic (tile expanded in shared memory, one TMA stage)
+    MD_STEP_CONFIG(128, 4, 256, 1, true, 0), MD_STEP_CONFIG(256, 4, 256, 1, true, 0),
+    MD_STEP_CONFIG(128, 8, 256, 1, true, 0),
 };
 
 constexpr int kFieldThreads = 128;

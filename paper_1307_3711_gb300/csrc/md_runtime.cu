@@ -321,13 +321,13 @@ md_status configure(md_ctx* c, int cfg, int ctas_per_sm, int jsplit) {
   return MD_OK;
 }
 
-// Default before autotuning: 256 threads x 4 i-particles per thread.
+// Default before autotuning: 128 threads x 8 i-particles per thread, packed.
 int default_config(md_ctx* c) {
   (void)c;
   int ncfg = 0;
   const md::KernelConfig* cfgs = md::step_configs(&ncfg);
   for (int i = 0; i < ncfg; ++i)
-    if (cfgs[i].threads == 256 && cfgs[i].r == 4) return i;
+    if (cfgs[i].threads == 128 && cfgs[i].r == 8 && cfgs[i].packed) return i;
   return 0;
 }
 
@@ -806,6 +806,8 @@ int32_t md_tuning_list(md_tuning* list, int32_t cap) {
     list[i].tile = cfgs[i].tile;
     list[i].ctas_per_sm = 0;
     list[i].jsplit = 0;
+    list[i].packed = cfgs[i].packed;
+    list[i].min_blocks = cfgs[i].min_blocks;
   }
   return n;
 }
@@ -815,14 +817,16 @@ md_status md_set_tuning(md_ctx* c, const md_tuning* t) {
   int n = 0;
   const md::KernelConfig* cfgs = md::step_configs(&n);
   for (int i = 0; i < n; ++i) {
-    if (cfgs[i].threads == t->threads && cfgs[i].r == t->r && cfgs[i].tile == t->tile) {
+    if (cfgs[i].threads == t->threads && cfgs[i].r == t->r && cfgs[i].tile == t->tile &&
+        cfgs[i].packed == (t->packed != 0) &&
+        (t->min_blocks < 0 || cfgs[i].min_blocks == t->min_blocks)) {
       if (t->ctas_per_sm < 0) return fail(MD_ERR_ARG, "ctas_per_sm < 0");
       MD_CUDA(cudaStreamSynchronize(c->stream));
       return configure(c, i, t->ctas_per_sm, t->jsplit);
     }
   }
-  return fail(MD_ERR_ARG, "no compiled configuration threads=%d r=%d tile=%d", t->threads, t->r,
-              t->tile);
+  return fail(MD_ERR_ARG, "no compiled configuration threads=%d r=%d tile=%d packed=%d",
+              t->threads, t->r, t->tile, t->packed);
 }
 
 md_status md_get_tuning(md_ctx* c, md_tuning* t) {
@@ -834,6 +838,8 @@ md_status md_get_tuning(md_ctx* c, md_tuning* t) {
   t->tile = cfgs[c->cfg].tile;
   t->ctas_per_sm = c->ctas_per_sm;
   t->jsplit = c->nseg_used;
+  t->packed = cfgs[c->cfg].packed;
+  t->min_blocks = cfgs[c->cfg].min_blocks;
   return MD_OK;
 }
 
@@ -868,13 +874,16 @@ md_status md_autotune(md_ctx* c, int32_t steps, double* times_ms, int32_t cap) {
   cudaStreamSynchronize(s);
   const int cfg0 = c->cfg, cps0 = c->ctas_per_sm, js0 = c->jsplit;
   int n = 0;
-  md::step_configs(&n);
+  const md::KernelConfig* cfgs = md::step_configs(&n);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   double best = 1e300;
   int best_cfg = cfg0;
   for (int i = 0; i < n && st == MD_OK; ++i) {
+    if (times_ms && i < cap) times_ms[i] = -1.0;
+    int bps = 0;
+    if (cfgs[i].max_blocks_per_sm(&bps) != cudaSuccess || bps < 1) continue;  // does not fit
     st = configure(c, i, 0, 0);
     if (st != MD_OK) break;
     st = launch_steps_direct(c, 1);  // warm-up

@@ -55,10 +55,12 @@ class Diag(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("threads", C.c_int32), ("r", C.c_int32), ("tile", C.c_int32),
-                ("ctas_per_sm", C.c_int32), ("jsplit", C.c_int32)]
+                ("ctas_per_sm", C.c_int32), ("jsplit", C.c_int32), ("packed", C.c_int32),
+                ("min_blocks", C.c_int32)]
 
     def as_tuple(self):
-        return (self.threads, self.r, self.tile, self.ctas_per_sm, self.jsplit)
+        return (self.threads, self.r, self.tile, self.ctas_per_sm, self.jsplit, self.packed,
+                self.min_blocks)
 
 
 _ctx_p = C.c_void_p
@@ -261,8 +263,8 @@ class Context:
         _check(_lib.md_get_tuning(self._h, C.byref(t)))
         return t.as_tuple()
 
-    def set_tuning(self, threads, r, tile, ctas_per_sm=0, jsplit=0):
-        t = Tuning(threads, r, tile, ctas_per_sm, jsplit)
+    def set_tuning(self, threads, r, tile, ctas_per_sm=0, jsplit=0, packed=0, min_blocks=-1):
+        t = Tuning(threads, r, tile, ctas_per_sm, jsplit, packed, min_blocks)
         _check(_lib.md_set_tuning(self._h, C.byref(t)))
 
     def autotune(self, steps: int = 3):

@@ -48,8 +48,11 @@ def test_si_helpers_match_oracle(md):
 def test_tuning_list(md):
     lst = md.tuning_list()
     assert len(lst) >= 4
-    for threads, r, tile, _, _ in lst:
+    for threads, r, tile, _, _, packed, minb in lst:
         assert threads % 32 == 0 and r >= 1 and tile % 16 == 0
+        assert packed in (0, 1) and (not packed or r % 2 == 0)
+        assert minb >= 0
+    assert any(t[5] for t in lst) and any(not t[5] for t in lst)
 
 
 def _one(md, **kw):

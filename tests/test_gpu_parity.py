@@ -219,12 +219,12 @@ def test_batched_clusters_equal_single_runs_bitwise(md, jsplit):
                                    envelope=md.ENV_SIN2))
         parts.append(md.HostParticles.from_cluster(cl))
     with md.Context(cfgs, parts) as ctx:
-        ctx.set_tuning(128, 2, 512, 0, jsplit)
+        ctx.set_tuning(128, 4, 256, 0, jsplit, 1)
         ctx.step(20)
         batched = [ctx.get_particles(k) for k in range(len(scan))]
     for k in range(len(scan)):
         with md.Context([cfgs[k]], [parts[k]]) as one:
-            one.set_tuning(128, 2, 512, 0, jsplit)
+            one.set_tuning(128, 4, 256, 0, jsplit, 1)
             one.step(20)
             g = one.get_particles(0)
         assert np.array_equal(g.x, batched[k].x)
@@ -246,19 +246,22 @@ def test_graph_replay_equals_direct_launches_and_tunings_agree(md):
         gb = b.get_particles(0)
     assert np.array_equal(ga.x, gb.x) and np.array_equal(ga.u, gb.u)
     r0 = np.abs(w.cluster.x).max()
-    ref = None
-    for threads, r, tile, _, _ in md.tuning_list():
+    first, by_tile = None, {}
+    for threads, r, tile, _, _, packed, minb in md.tuning_list():
         for jsplit in (1, 0):
             with ctx_for(md, w) as c:
-                c.set_tuning(threads, r, tile, 0, jsplit)
+                c.set_tuning(threads, r, tile, 0, jsplit, packed, minb)
+                assert c.tuning()[5] == packed
                 c.step(17)
                 g = c.get_particles(0)
-            if ref is None:
-                ref = g
-            if tile == 512 and jsplit == 1:
-                assert np.array_equal(g.x, ref.x) and np.array_equal(g.u, ref.u)
-            else:
-                assert np.abs(g.x - ref.x).max() < 1e-6 * r0
+            first = first or g
+            if jsplit == 1:
+                # same tile and split: the same sums in the same order, so every
+                # configuration (scalar or packed f32x2) gives identical bits
+                ref = by_tile.setdefault(tile, g)
+                assert np.array_equal(g.x, ref.x) and np.array_equal(g.u, ref.u), \
+                    (threads, r, tile, packed, minb)
+            assert np.abs(g.x - first.x).max() < 1e-6 * r0
 
 
 def test_split_sources_parity_and_determinism(md):
@@ -269,7 +272,7 @@ def test_split_sources_parity_and_determinism(md):
     outs = []
     for _ in range(2):
         with ctx_for(md, w) as c:
-            c.set_tuning(256, 4, 512, 0, 5)
+            c.set_tuning(256, 4, 256, 0, 5, 1)
             assert c.tuning()[4] == 5
             c.step(6)
             outs.append(c.get_particles(0))
@@ -290,7 +293,7 @@ def test_autotune_restores_state(md):
         times = ctx.autotune(2)
         after = ctx.get_particles(0)
         assert ctx.step_index() == 3
-        assert np.all(times > 0)
+        assert np.all((times > 0) | (times == -1.0)) and np.any(times > 0)
         assert np.array_equal(before.x, after.x) and np.array_equal(before.u, after.u)
 
 
