@@ -23,7 +23,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libmd_oracle.so")
 # a planted-mistake test compiles a mutant elsewhere and points here
 _LIB_OVERRIDE = os.environ.get("MD_ORACLE_LIB")
-_SOURCES = ["md_oracle.c"]
+_SOURCES = ["md_oracle.c", "ionize_oracle.c"]
 _lock = threading.Lock()
 _lib = None
 
@@ -88,6 +88,23 @@ def lib():
             L.or_diagnostics.restype = None
             L.or_diagnostics.argtypes = [i, p, p, p, p, p, p, p, C.POINTER(Params), i64,
                                          p, p, p, p, i]
+            L.io_philox4x32_10.restype = None
+            L.io_philox4x32_10.argtypes = [p, p, p]
+            L.io_uniform_open0.restype = d
+            L.io_uniform_open0.argtypes = [C.c_uint32]
+            L.io_e1.restype = d
+            L.io_e1.argtypes = [d]
+            L.io_adk_rate_au.restype = d
+            L.io_adk_rate_au.argtypes = [d, d, d]
+            L.io_lotz_rate_cgs.restype = d
+            L.io_lotz_rate_cgs.argtypes = [d, d, d]
+            L.io_rate_total.restype = d
+            L.io_rate_total.argtypes = [d, i, d, d, p, p, d]
+            L.io_local_moments.restype = None
+            L.io_local_moments.argtypes = [i, p, i, p, p, p, p, p, d, d, p, p]
+            L.io_decide.restype = None
+            L.io_decide.argtypes = [i, p, p, p, p, p, p, p, i, d, d, C.c_uint64, i64, d, p, p,
+                                    p]
             _lib = L
     return _lib
 
@@ -251,3 +268,105 @@ def diagnostics(state: State, params: Params, nthreads: int = 1) -> dict:
     return {"ke": out[0], "ke_ions": out[1], "ke_electrons": out[2], "pe": out[3],
             "p": out[4:7].copy(), "n_active": int(out[7]),
             "total": out[0] + out[3]}
+
+
+# ------------------------------------------------------------- ionization ---
+# Sec. II ionization paragraph; arithmetic in ionize_oracle.c.
+
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 block: four counter words, two key words -> four words."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, np.uint32)
+    lib().io_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def uniform_open0(w):
+    return lib().io_uniform_open0(int(w))
+
+
+def e1(x):
+    return lib().io_e1(float(x))
+
+
+def adk_rate_au(field_au, ip_au, z_residual):
+    return lib().io_adk_rate_au(float(field_au), float(ip_au), float(z_residual))
+
+
+def lotz_rate_cgs(p_ev, t_ev, q):
+    return lib().io_lotz_rate_cgs(float(p_ev), float(t_ev), float(q))
+
+
+def _species(species):
+    ip = np.ascontiguousarray(species["ip_ev"], dtype=np.float64)
+    q = np.ascontiguousarray(species["q_outer"], dtype=np.float64)
+    return ip, q
+
+
+def rate_total(a_mag, z, ne, te, species, lambda_um=0.8):
+    ip, q = _species(species)
+    return lib().io_rate_total(float(a_mag), int(z), float(ne), float(te), _ptr(ip), _ptr(q),
+                               float(lambda_um))
+
+
+def local_moments(x_targets, state: "State", r_loc, lambda_um=0.8):
+    """(ne [cm^-3], Te [eV]) of the active electrons within r_loc of each target."""
+    xt = _f64(x_targets, (-1, 3))
+    ne = np.zeros(xt.shape[0])
+    te = np.zeros(xt.shape[0])
+    lib().io_local_moments(xt.shape[0], _ptr(xt), state.n, _ptr(state.x), _ptr(state.u),
+                           _ptr(state.w), _ptr(state.z), _ptr(state.active), float(r_loc),
+                           float(lambda_um), _ptr(ne), _ptr(te))
+    return ne, te
+
+
+def decide(ids, z, a_mag, ne, te, species, zmax, seed, step, dt_ion, r_create,
+           lambda_um=0.8):
+    """Monte-Carlo decision (Sec. II): returns (new z, fired, offsets, P)."""
+    ids = np.ascontiguousarray(ids, dtype=np.int64)
+    z = np.ascontiguousarray(z, dtype=np.int32).copy()
+    a = np.ascontiguousarray(a_mag, dtype=np.float64)
+    ne = np.ascontiguousarray(ne, dtype=np.float64)
+    te = np.ascontiguousarray(te, dtype=np.float64)
+    ip, q = _species(species)
+    n = ids.shape[0]
+    fired = np.zeros(n, np.uint8)
+    off = np.zeros((n, 3))
+    prob = np.zeros(n)
+    lib().io_decide(n, _ptr(ids), _ptr(z), _ptr(a), _ptr(ne), _ptr(te), _ptr(ip), _ptr(q),
+                    int(zmax), float(lambda_um), float(dt_ion), int(seed) & (2 ** 64 - 1),
+                    int(step), float(r_create), _ptr(fired), _ptr(off), _ptr(prob))
+    return z, fired, off, prob
+
+
+def ionize_pass(state: "State", params: Params, species, n_ion, slot_base, zmax, seed, dt_ion,
+                r_loc, r_create, lambda_um=0.8, nthreads=1):
+    """One ionization pass at step state.step (Sec. II): for each ion record
+    i < n_ion (id = i) of charge z < zmax, the field |E_coulomb + a(t_n)| at
+    x_i, the local electron moments, the Philox decision; an ionizing ion gets
+    z + 1 and activates electron slot slot_base + z_old * n_ion + i at
+    x_i + offset with the ion's u and weight.  Returns (fired, field_mag, ne,
+    te) of the ions; modifies state."""
+    ions = np.arange(n_ion, dtype=np.int64)
+    q = state.q()
+    e = coulomb_field(state.x[:n_ion], state.x, q, params.eps, params.kc, self_idx=ions,
+                      nthreads=nthreads)
+    t = params.t0 + state.step * params.dt
+    a, _ = laser_fields(t, params.a0, params.pol, params.env, params.tau)
+    amag = np.linalg.norm(e + a[None, :], axis=1)
+    ne, te = local_moments(state.x[:n_ion], state, r_loc, lambda_um)
+    z_old = state.z[:n_ion].copy()
+    z_new, fired, off, _ = decide(ions, z_old, amag, ne, te, species, zmax, seed, state.step,
+                                  dt_ion, r_create, lambda_um)
+    for i in np.nonzero(fired)[0]:
+        slot = slot_base + z_old[i] * n_ion + i
+        assert state.active[slot] == 0
+        state.x[slot] = state.x[i] + off[i]
+        state.u[slot] = state.u[i]
+        state.z[slot] = -1
+        state.mass[slot] = 1.0
+        state.w[slot] = state.w[i]
+        state.active[slot] = 1
+    state.z[:n_ion] = z_new
+    return fired, amag, ne, te

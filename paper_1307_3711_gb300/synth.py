@@ -28,6 +28,18 @@ R_W_ANGSTROM = {"D": 1.70, "Ne": 2.02, "Ar": 2.40, "Xe": 2.73}
 
 ENV_GAUSS, ENV_SIN2, ENV_LITERAL_EQ3, ENV_FLAT = 0, 1, 2, 3
 
+# Argon ionization data used as input by the ionization runs: ionization
+# energies of Ar^z -> Ar^(z+1), z = 0..7 (eV, NIST Atomic Spectra Database,
+# rounded), and the number of electrons in the outermost occupied subshell of
+# Ar^z (3p^6 ... 3p^1, then 3s^2, 3s^1).
+ARGON = {
+    "name": "Ar",
+    "ip_ev": [15.7596, 27.62967, 40.735, 59.58, 74.84, 91.290, 124.41, 143.4567],
+    "q_outer": [6.0, 5.0, 4.0, 3.0, 2.0, 1.0, 2.0, 1.0],
+    "mass": MASS_AR,
+    "r_w_nm": 0.240,
+}
+
 
 def nm_to_len(nm: float, lambda_um: float = 0.8) -> float:
     """Length in nm -> units of 1/k (k = 2 pi / lambda)."""

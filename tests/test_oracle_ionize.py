@@ -1,0 +1,199 @@
+"""Pins of the ionization oracle (Sec. II, ionization paragraph) against
+closed forms, library routines and exact invariants."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import constants as sc
+from scipy import integrate, special, stats
+
+import oracle
+from paper_1307_3711_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+AR = synth.ARGON
+
+
+def test_philox_known_answers():
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.json")) as f:
+        kat = json.load(f)
+    for v in kat["vectors"]:
+        ctr = [int(x, 16) for x in v["ctr"]]
+        key = [int(x, 16) for x in v["key"]]
+        out = [int(x, 16) for x in v["out"]]
+        assert oracle.philox4x32_10(ctr, key).tolist() == out
+
+
+def test_philox_uniform_and_decorrelated():
+    """Words of consecutive counters are uniform (KS) and a one-bit change of
+    the counter flips about half of the output bits."""
+    ws = np.array([oracle.philox4x32_10([i, 7, 0, 0], [11, 13]) for i in range(4000)])
+    u = ws.astype(np.float64) / 2 ** 32
+    for k in range(4):
+        assert stats.kstest(u[:, k], "uniform").pvalue > 1e-3
+    flips = []
+    for i in range(200):
+        a = oracle.philox4x32_10([i, 3, 5, 0], [1, 2])
+        b = oracle.philox4x32_10([i ^ 1, 3, 5, 0], [1, 2])
+        flips.append(sum(bin(int(x) ^ int(y)).count("1") for x, y in zip(a, b)))
+    assert np.mean(flips) == pytest.approx(64, abs=2)
+    assert oracle.uniform_open0(0) == 2.0 ** -32 and oracle.uniform_open0(2 ** 32 - 1) == 1.0
+
+
+@pytest.mark.parametrize("x", [1e-8, 1e-3, 0.3, 0.999, 1.0, 1.001, 2.5, 10.0, 50.0, 300.0])
+def test_e1_matches_library(x):
+    assert oracle.e1(x) == pytest.approx(special.exp1(x), rel=1e-13)
+
+
+@pytest.mark.parametrize("F", [0.02, 0.05, 0.1, 0.3, 1.0])
+def test_adk_reduces_to_landau_hydrogen_rate(F):
+    """For hydrogen (Ip = 1/2 a.u., Z = 1: n* = 1, l* = 0) the static ADK
+    rate is the exact weak-field tunnelling rate of the ground state,
+    w = (4/F) exp(-2/(3F)) (Landau & Lifshitz, QM, Sec. 77)."""
+    assert oracle.adk_rate_au(F, 0.5, 1.0) == pytest.approx(4.0 / F * math.exp(-2.0 / (3 * F)),
+                                                            rel=1e-12)
+
+
+def test_adk_structure():
+    """Monotone in the field, vanishing as F -> 0, and suppressed for higher
+    potentials at the same field."""
+    ip = AR["ip_ev"][0] / 27.211386245988
+    f = np.logspace(-3, 0, 40)
+    w = np.array([oracle.adk_rate_au(x, ip, 1.0) for x in f])
+    assert np.all(np.diff(w) > 0) and w[0] < 1e-100
+    assert oracle.adk_rate_au(0.0, ip, 1.0) == 0.0
+    ip2 = AR["ip_ev"][1] / 27.211386245988
+    assert oracle.adk_rate_au(0.05, ip2, 2.0) < oracle.adk_rate_au(0.05, ip, 1.0)
+
+
+@pytest.mark.parametrize("P,T,q", [(15.76, 5.0, 6), (15.76, 40.0, 6), (143.46, 30.0, 1),
+                                   (59.58, 200.0, 3)])
+def test_lotz_rate_is_maxwell_average_of_cross_section(P, T, q):
+    """<sigma v> of the Lotz cross section sigma = a q ln(E/P)/(E P) over a
+    Maxwellian, integrated numerically in SI units, equals the closed form."""
+    a = 4.5e-14 * 1e-4 * sc.e ** 2            # m^2 J^2
+    Pj, Tj = P * sc.e, T * sc.e
+
+    def integrand(E):  # energy in J
+        sigma = a * q * math.log(E / Pj) / (E * Pj)
+        v = math.sqrt(2 * E / sc.m_e)
+        f = 2 * math.sqrt(E / math.pi) * Tj ** -1.5 * math.exp(-E / Tj)  # Maxwell energy pdf
+        return sigma * v * f
+
+    val, _ = integrate.quad(integrand, Pj, Pj + 60 * Tj, limit=400, epsabs=0, epsrel=1e-11)
+    assert oracle.lotz_rate_cgs(P, T, q) == pytest.approx(val * 1e6, rel=1e-8)  # m^3 -> cm^3
+    assert oracle.lotz_rate_cgs(P, 0.0, q) == 0.0
+
+
+def test_rate_total_units():
+    """nu_total in 1/omega: field a -> E = a m_e c omega / e, ADK in a.u.
+    converted with the atomic unit of time; collisions n_e <sigma v>."""
+    lam = 0.8e-6
+    omega = 2 * math.pi * sc.c / lam
+    amag = 0.05
+    e_si = amag * sc.m_e * sc.c * omega / sc.e
+    F = e_si / (sc.physical_constants["atomic unit of electric field"][0])
+    ip = AR["ip_ev"][0] / (sc.physical_constants["Hartree energy in eV"][0])
+    t_au = sc.physical_constants["atomic unit of time"][0]
+    nu_ofi = oracle.adk_rate_au(F, ip, 1.0) / t_au / omega
+    assert oracle.rate_total(amag, 0, 0.0, 0.0, AR) == pytest.approx(nu_ofi, rel=1e-8)
+    ne, te = 1e22, 30.0
+    nu_ci = ne * oracle.lotz_rate_cgs(AR["ip_ev"][0], te, 6) / omega
+    assert oracle.rate_total(amag, 0, ne, te, AR) == pytest.approx(nu_ofi + nu_ci, rel=1e-8)
+
+
+def test_local_moments_constructed_case():
+    """Six electrons at 0.5 r_loc along +-x, +-y, +-z with u = +-v along the
+    same axis (mean zero, <u^2> = v^2): ne = 6 w / volume, Te = m c^2 v^2 / 3;
+    an ion, an inactive slot and a far electron do not count."""
+    r_loc, v, w = 0.01, 0.003, 2.0
+    pos = []
+    vel = []
+    for ax in range(3):
+        for s in (1, -1):
+            p = np.zeros(3); p[ax] = 0.5 * s * r_loc
+            q = np.zeros(3); q[ax] = s * v
+            pos.append(p); vel.append(q)
+    x = np.array(pos + [[0.001, 0, 0], [0, 0.002, 0], [2 * r_loc, 0, 0]])
+    u = np.array(vel + [[0, 0, 0], [0, 0, 0], [0.5, 0, 0]])
+    z = np.array([-1] * 6 + [3, 0, -1])
+    active = np.array([1] * 6 + [1, 0, 1], np.uint8)
+    st = oracle.State(x, u, z, np.ones(9), np.full(9, w), active)
+    ne, te = oracle.local_moments(np.zeros((1, 3)), st, r_loc)
+    k = 2 * math.pi / 0.8e-6
+    vol_cm3 = 4 / 3 * math.pi * (r_loc / k) ** 3 * 1e6
+    assert ne[0] == pytest.approx(6 * w / vol_cm3, rel=1e-12)
+    assert te[0] == pytest.approx(510998.95 * v * v / 3, rel=1e-12)
+    ne, te = oracle.local_moments(np.array([[10.0, 0, 0]]), st, r_loc)
+    assert ne[0] == 0 and te[0] == 0
+
+
+def test_decision_statistics_constant_rate():
+    """With a fixed probability per pass, the ionized fraction after one pass
+    is binomial(P), independent of the ion id and step."""
+    n = 20000
+    ids = np.arange(n)
+    z = np.zeros(n, np.int32)
+    amag = np.full(n, 0.012)
+    P = None
+    frac = []
+    for step in range(3):
+        z1, fired, off, prob = oracle.decide(ids, z, amag, np.zeros(n), np.zeros(n), AR, 8,
+                                             seed=5, step=step, dt_ion=2.0, r_create=0.001)
+        P = prob[0]
+        assert np.all(prob == P) and 0.05 < P < 0.95
+        frac.append(fired.mean())
+        assert np.array_equal(z1, z + fired)
+    for f in frac:
+        assert abs(f - P) < 4 * math.sqrt(P * (1 - P) / n)
+    # the decision is a pure function of (seed, id, step)
+    a = oracle.decide(ids[:50], z[:50], amag[:50], np.zeros(50), np.zeros(50), AR, 8, 5, 1, 2.0,
+                      0.001)
+    b = oracle.decide(ids[:50], z[:50], amag[:50], np.zeros(50), np.zeros(50), AR, 8, 5, 1, 2.0,
+                      0.001)
+    assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+    # zmax caps the charge
+    zc = np.full(5, 8, np.int32)
+    z2, f2, _, p2 = oracle.decide(ids[:5], zc, np.full(5, 10.0), np.zeros(5), np.zeros(5), AR, 8,
+                                  5, 1, 2.0, 0.001)
+    assert np.all(f2 == 0) and np.all(z2 == 8) and np.all(p2 == 0)
+
+
+def test_electron_placement_uniform_in_ball():
+    n = 20000
+    rc = 0.004
+    _, fired, off, _ = oracle.decide(np.arange(n), np.zeros(n, np.int32), np.full(n, 0.2),
+                                     np.zeros(n), np.zeros(n), AR, 8, 9, 0, 100.0, rc)
+    assert fired.mean() > 0.99
+    r = np.linalg.norm(off[fired > 0], axis=1)
+    assert r.max() <= rc
+    assert stats.kstest(r / rc, lambda s: np.clip(s, 0, 1) ** 3).pvalue > 1e-3
+    assert np.abs(off[fired > 0].mean(axis=0)).max() < 0.03 * rc
+
+
+def test_ionize_pass_conserves_charge_and_uses_slots():
+    """Neutral Ar atoms in a strong field: every pass conserves the total
+    charge exactly; slot slot_base + z_old n_ion + i is the new electron."""
+    n_ion, zmax = 300, 8
+    c = synth.make_cluster(4, n_ion, 0, synth.nm_to_len(2.0), 0, AR["mass"],
+                           n_electron_slots=n_ion * zmax)
+    st = oracle.State(c.x, c.u, c.z, c.mass, c.w, c.active)
+    p = oracle.make_params(a0=0.3, tau=1.0, dt=0.05, eps=synth.nm_to_len(0.1),
+                           env=oracle.ENV_FLAT)
+    r_loc = 3 * synth.nm_to_len(AR["r_w_nm"])
+    total = []
+    for k in range(4):
+        st.step = 10 + k
+        z_before = st.z[:n_ion].copy()
+        fired, amag, ne, te = oracle.ionize_pass(st, p, AR, n_ion, n_ion, zmax, seed=3,
+                                                 dt_ion=5.0, r_loc=r_loc,
+                                                 r_create=synth.nm_to_len(AR["r_w_nm"]))
+        total.append(int(np.sum(st.w * st.z * st.active)))
+        for i in np.nonzero(fired)[0]:
+            slot = n_ion + z_before[i] * n_ion + i
+            assert st.active[slot] == 1 and st.z[slot] == -1
+    assert total == [0, 0, 0, 0]
+    assert st.z[:n_ion].max() >= 2
+    assert st.active[n_ion:].sum() == st.z[:n_ion].sum()
