@@ -87,8 +87,28 @@ typedef struct {
     int32_t polarization; /* 0 linear (E along x, B along y), 1 circular (Eqs. 4-9) */
     int32_t envelope;     /* MD_ENV_* */
     int32_t boundary;     /* MD_BOUNDARY_* */
+    /* ---- Monte-Carlo ionization (Sec. II, ionization paragraph) ---- */
+    int32_t rate_model;   /* MD_RATES_*: 0 none */
+    int32_t ionize_every; /* k >= 1: one pass before every k-th step, dt_ion = k dt;
+                             0: passes only through md_ionize (dt_ion = dt) */
+    int32_t zmax;         /* highest charge state, 1..16 */
+    int32_t n_ions;       /* records [0, n_ions) are the atoms/ions that can ionize */
     int32_t reserved;     /* must be 0 */
+    int64_t slot_base;    /* the electron freed from ion i at charge z becomes record
+                             slot_base + z * n_ions + i (INACTIVE until then) */
+    uint64_t seed;        /* Philox key */
+    double r_loc;         /* local electron moments from electrons within r_loc of the ion */
+    double r_create;      /* new electron uniform in the ball of this radius around the ion */
+    double ip_ev[16];     /* ionization energy of charge state z -> z+1 (eV), z < zmax */
+    double q_outer[16];   /* electrons in the outermost subshell of charge state z (Lotz) */
 } md_config;
+
+/* Rate models of the ionization pass. */
+enum {
+    MD_RATES_NONE = 0,
+    MD_RATES_PLAIN = 1, /* static ADK tunnelling + Lotz electron impact */
+    MD_RATES_MLP = 2    /* learned surrogate of the plain total rate (md_set_rate_mlp) */
+};
 
 /* Host-side particle records of one cluster (structure of arrays, n records).
  * For md_init / md_set_particles the arrays are read; md_get_particles writes
@@ -177,6 +197,26 @@ md_status md_set_particles(md_ctx *ctx, int32_t cluster, const md_particles *in)
  * of cluster `cluster`, computed by the same FP32/Kahan sum as md_step.
  * e: host [n][3], phi: host [n] or NULL.  Synchronous. */
 md_status md_get_fields(md_ctx *ctx, int32_t cluster, double *e, double *phi);
+
+/* md_ionize: one Monte-Carlo ionization pass (Sec. II) of every cluster with
+ * rate_model != 0 at the current step, whatever ionize_every says (dt_ion =
+ * ionize_every dt, or dt if it is 0).  For each ion/atom record i < n_ions of
+ * charge z < zmax: the Coulomb field at x_i from all other particles plus the
+ * laser at t_n, the weight, mean and spread of u of the electrons within
+ * r_loc (density in cm^-3, temperature in eV), the total rate (static ADK +
+ * Lotz, or the surrogate), P = 1 - exp(-nu dt_ion), alpha from
+ * Philox4x32-10(counter = (i, step lo, step hi, 0), key = seed); if
+ * alpha < P the ion's charge rises by one and slot_base + z n_ions + i
+ * becomes an electron at x_i + r (r uniform in the ball of radius r_create,
+ * from Philox words 1-3) with the ion's u and weight.  Asynchronous. */
+md_status md_ionize(md_ctx *ctx);
+
+/* md_get_ionization: per-ion results of the last pass of cluster `cluster`
+ * (host arrays of n_ions entries, any may be NULL): field magnitude |E| (paper
+ * units), local electron density (cm^-3) and temperature (eV), probability P
+ * and whether the ion ionized.  Synchronous. */
+md_status md_get_ionization(md_ctx *ctx, int32_t cluster, double *emag, double *ne, double *te,
+                            double *prob, uint8_t *fired);
 
 /* Step counter of the context (steps taken since md_init). Synchronous. */
 md_status md_get_step(md_ctx *ctx, int64_t *step);

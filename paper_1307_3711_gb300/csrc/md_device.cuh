@@ -112,6 +112,24 @@ __device__ __forceinline__ float rsqrt_mufu(float x) {
   return y;
 }
 
+// ------------------------------------------------------------- Philox ----
+// Philox4x32-10 block function (Salmon et al., SC'11): per round, the 32x32
+// products of words 0 and 2 with 0xD2511F53 / 0xCD9E8D57, high halves mixed
+// with words 1 / 3 and the key; the key advances by 0x9E3779B9, 0xBB67AE85.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    if (r < 9) {
+      k.x += 0x9E3779B9u;
+      k.y += 0xBB67AE85u;
+    }
+  }
+  return c;
+}
+
 // --------------------------------------------------------------- laser --
 
 // Field-amplitude envelope (Eq. 3 and its readings): 0 Gaussian with
@@ -869,77 +887,6 @@ __global__ void __launch_bounds__(THREADS) k_diag_partial(const DiagArgs a) {
     s = block_sum<THREADS>(histw[k], red);
     if (threadIdx.x == 0) out->histw[k] = s;
   }
-}
-
-// Sums the per-block partials in block order (deterministic); one thread per
-// component.
-__global__ void k_diag_final(const DiagPartial* __restrict__ part, int nblocks,
-                             DiagPartial* __restrict__ out) {
-  const int k = threadIdx.x;
-  if (k < 8) {
-    double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += part[b].v[k];
-    out->v[k] = s;
-  } else if (k < 10) {
-    long long s = 0;
-    for (int b = 0; b < nblocks; ++b) s += part[b].cnt[k - 8];
-    out->cnt[k - 8] = s;
-  } else if (k < 10 + kHistBins) {
-    long long s = 0;
-    for (int b = 0; b < nblocks; ++b) s += part[b].hist[k - 10];
-    out->hist[k - 10] = s;
-  } else if (k < 10 + 2 * kHistBins) {
-    double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += part[b].histw[k - 10 - kHistBins];
-    out->histw[k - 10 - kHistBins] = s;
-  }
-}
-
-// ------------------------------------------------------------ layout glue --
-
-// Scatter host-layout records ([n][3] x/u, z, mass, w, kind) into the SoA
-// device state of one cluster starting at record `off`; writes the current
-// j-stream entry (x, y, z, K_C w z).
-
-__global__ void k_upload(const UploadArgs a) {
-  const long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (k >= a.n) return;
-  const long long i = a.off + k;
-  const unsigned char kd = a.hkind[k];
-  const double X = a.hx[3 * k], Y = a.hx[3 * k + 1], Z = a.hx[3 * k + 2];
-  a.x[i] = X;
-  a.y[i] = Y;
-  a.z[i] = Z;
-  a.ux[i] = a.hu[3 * k];
-  a.uy[i] = a.hu[3 * k + 1];
-  a.uz[i] = a.hu[3 * k + 2];
-  const int zq = a.hz[k];
-  a.zq[i] = zq;
-  a.mass[i] = a.hmass[k];
-  a.w[i] = a.hw[k];
-  a.kind[i] = kd;
-  const bool live = (kd != 2);
-  a.qm[i] = live ? static_cast<float>(zq / a.hmass[k]) : 0.0f;
-  const float q = live ? static_cast<float>(a.kc * a.hw[k] * zq) : 0.0f;
-  const float4 p = make_float4(static_cast<float>(X), static_cast<float>(Y), static_cast<float>(Z), q);
-  const long long step = __ldcg(a.step);
-  if (step & 1) a.posq1[i] = p; else a.posq0[i] = p;
-}
-
-__global__ void k_download(const DownloadArgs a) {
-  const long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (k >= a.n) return;
-  const long long i = a.off + k;
-  a.hx[3 * k] = a.x[i];
-  a.hx[3 * k + 1] = a.y[i];
-  a.hx[3 * k + 2] = a.z[i];
-  a.hu[3 * k] = a.ux[i];
-  a.hu[3 * k + 1] = a.uy[i];
-  a.hu[3 * k + 2] = a.uz[i];
-  a.hz[k] = a.zq[i];
-  a.hmass[k] = a.mass[i];
-  a.hw[k] = a.w[i];
-  a.hkind[k] = a.kind[i];
 }
 
 }  // namespace md

@@ -1,0 +1,290 @@
+// md_ionize.cu -- Monte-Carlo ionization pass on the GPU (Holkundkar,
+// arXiv:1307.3711, Sec. II, ionization paragraph).
+//
+// Two kernels per cluster and pass:
+//   k_ion_field   for every ion/atom record: the Coulomb field of all other
+//                 particles (the TMA-staged FP32/Kahan direct sum of the step
+//                 kernel) and the weight, momentum and momentum-square sums of
+//                 the electrons within r_loc (gathered from the FP64 state);
+//   k_ion_decide  per ion: laser field at t_n, |E|, local density and
+//                 temperature, total rate (static ADK + Lotz, or the learned
+//                 surrogate), P = 1 - exp(-nu dt_ion), a Philox4x32-10 draw and
+//                 the charge update with activation of its electron slot.
+// The decision runs after the whole field pass, so no charge changes while
+// any other ion's field is being summed.  Rates are FP64, as on the host.
+#include <cmath>
+
+#include "md_device.cuh"
+#include "md_internal.h"
+
+namespace md {
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kEulerGamma = 0.57721566490153286061;
+constexpr double kHartreeEv = 27.211386245988;
+constexpr double kFieldAu = 5.14220674763e11;   // V/m
+constexpr double kTimeAu = 2.4188843265857e-17;  // s
+constexpr double kMeC2Ev = 510998.95;
+constexpr double kElemCharge = 1.602176634e-19;  // C
+constexpr double kElectronMass = 9.1093837015e-31;  // kg
+constexpr double kLotzA = 4.5e-14;               // cm^2 eV^2
+
+// ---------------------------------------------------------------- rates ---
+
+// E1(x) = int_x^inf e^-t/t dt: power series up to 1, even continued fraction
+// (modified Lentz) beyond.
+__device__ double expint_e1(double x) {
+  if (!(x > 0.0)) return __longlong_as_double(0x7ff0000000000000LL);  // +inf
+  if (x <= 1.0) {
+    double sum = 0.0, term = 1.0;
+    for (int k = 1; k < 60; ++k) {
+      term *= -x / k;
+      const double add = -term / k;
+      sum += add;
+      if (fabs(add) < 1e-18 * fabs(sum)) break;
+    }
+    return -kEulerGamma - log(x) + sum;
+  }
+  const double tiny = 1e-300;
+  double b = x + 1.0, c = 1.0 / tiny, d = 1.0 / b, h = d;
+  for (int i = 1; i < 300; ++i) {
+    const double an = -static_cast<double>(i) * i;
+    b += 2.0;
+    d = 1.0 / (an * d + b);
+    c = b + an / c;
+    const double del = c * d;
+    h *= del;
+    if (fabs(del - 1.0) < 1e-16) break;
+  }
+  return h * exp(-x);
+}
+
+// Static ADK rate (a.u.) at field F (a.u.), potential ip (a.u.), residual
+// charge Z: n* = Z/sqrt(2 ip), l* = n* - 1, l = m = 0.
+__device__ double adk_rate_au(double F, double ip, double Z) {
+  if (!(F > 0.0)) return 0.0;
+  const double ns = Z / sqrt(2.0 * ip);
+  const double ls = ns - 1.0;
+  const double c2 = pow(2.0, 2.0 * ns) / (ns * tgamma(ns + ls + 1.0) * tgamma(ns - ls));
+  const double f0 = pow(2.0 * ip, 1.5);
+  return c2 * ip * pow(2.0 * f0 / F, 2.0 * ns - 1.0) * exp(-2.0 * f0 / (3.0 * F));
+}
+
+// Lotz rate coefficient (cm^3/s): sqrt(8/(pi m_e)) a q E1(P/T) / (P sqrt(T)).
+__device__ double lotz_rate_cgs(double P, double T, double q) {
+  if (!(T > 0.0) || !(q > 0.0)) return 0.0;
+  const double v_th = sqrt(8.0 * kElemCharge / (kPi * kElectronMass)) * 100.0;
+  return v_th * kLotzA * q * expint_e1(P / T) / (P * sqrt(T));
+}
+
+// Total rate per unit time 1/omega of charge state z at |a| (paper units),
+// ne (cm^-3), te (eV).
+__device__ double rate_plain(const IonDev& io, double a_mag, int z, double ne, double te) {
+  const double F = a_mag * kMeC2Ev * io.k_si / kFieldAu;
+  const double w_ofi = adk_rate_au(F, io.ip_ev[z] / kHartreeEv, static_cast<double>(z + 1)) /
+                       kTimeAu;
+  const double w_ci = ne > 0.0 ? ne * lotz_rate_cgs(io.ip_ev[z], te, io.q_outer[z]) : 0.0;
+  return (w_ofi + w_ci) / io.omega;
+}
+
+__device__ __forceinline__ bool pass_active(const IonArgs& a, long long step) {
+  if (a.ion.rate_model == 0) return false;
+  if (a.force) return true;
+  return a.ion.ionize_every > 0 && (step % a.ion.ionize_every) == 0;
+}
+
+// --------------------------------------------------------- field + moments
+
+// Field (FP32/Kahan) and local electron moments at R ion targets per thread.
+template <int THREADS, int R, int TILE, int STAGES>
+__global__ void __launch_bounds__(THREADS) k_ion_field(const IonArgs a) {
+  __shared__ Stage<TILE, STAGES> sm;
+  __shared__ int s_abort;
+  const long long step = __ldcg(a.step);
+  if (!pass_active(a, step)) return;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) mbar_init(&sm.full[s], 1);
+    fence_mbar_init();
+    s_abort = 0;
+  }
+  __syncthreads();
+  const float4* __restrict__ cur = (step & 1) ? a.posq1 : a.posq0;
+  const float4* src = cur + a.c.off;
+  const long long ns = a.c.n_pad;
+  const long long t0 = static_cast<long long>(blockIdx.x) * (THREADS * R);
+  const float rloc2 = static_cast<float>(a.ion.r_loc * a.ion.r_loc);
+  float xi[R], yi[R], zi[R];
+  Acc<R, false> acc;
+  acc.zero();
+  double mom[R][5];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const long long t = t0 + threadIdx.x + r * THREADS;
+    const float4 p = (t < a.ion.n_ions) ? cur[a.c.off + t] : make_float4(0.f, 0.f, 0.f, 0.f);
+    xi[r] = p.x;
+    yi[r] = p.y;
+    zi[r] = p.z;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) mom[r][k] = 0.0;
+  }
+  const int ntiles = static_cast<int>((ns + TILE - 1) / TILE);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < STAGES && k < ntiles; ++k) issue_tile<TILE, STAGES>(sm, k, src, ns, k);
+  for (int t = 0; t < ntiles; ++t) {
+    const int s = t % STAGES;
+    if (!mbar_wait(&sm.full[s], (t / STAGES) & 1u)) {
+      atomicOr(a.err, kErrTimeout);
+      s_abort = 1;
+    }
+    if (!*reinterpret_cast<volatile int*>(&s_abort)) {
+      const long long jb = static_cast<long long>(t) * TILE;
+      const long long rem = ns - jb;
+      const int cnt = static_cast<int>(rem < TILE ? rem : TILE);
+      for (int j = 0; j < cnt; ++j) {
+        const float4 p = sm.tile[s][j];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const float dx = p.x - xi[r], dy = p.y - yi[r], dz = p.z - zi[r];
+          const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          const float ri = rsqrt_mufu(d2 + a.c.eps2);
+          const float s3 = p.w * ri * ri * ri;
+          acc.ax[r] = fmaf(dx, s3, acc.ax[r]);
+          acc.ay[r] = fmaf(dy, s3, acc.ay[r]);
+          acc.az[r] = fmaf(dz, s3, acc.az[r]);
+          if (p.w < 0.0f && d2 < rloc2) {  // an electron within r_loc
+            const long long jg = a.c.off + jb + j;
+            const double w = a.w[jg], ux = a.ux[jg], uy = a.uy[jg], uz = a.uz[jg];
+            mom[r][0] += w;
+            mom[r][1] += w * ux;
+            mom[r][2] += w * uy;
+            mom[r][3] += w * uz;
+            mom[r][4] += w * (ux * ux + uy * uy + uz * uz);
+          }
+        }
+      }
+      fold<R, false>(acc);
+    }
+    __syncthreads();
+    if (*reinterpret_cast<volatile int*>(&s_abort)) {
+      if (threadIdx.x == 0) {
+        const int last = (t + STAGES < ntiles) ? t + STAGES : ntiles;
+        for (int k = t + 1; k < last; ++k) mbar_wait(&sm.full[k % STAGES], (k / STAGES) & 1u);
+      }
+      return;
+    }
+    if (threadIdx.x == 0 && t + STAGES < ntiles)
+      issue_tile<TILE, STAGES>(sm, t + STAGES, src, ns, t + STAGES);
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const long long t = t0 + threadIdx.x + r * THREADS;
+    if (t >= a.ion.n_ions) continue;
+    double* o = a.scratch + 8 * t;
+    o[0] = -(static_cast<double>(acc.sx[r]) - acc.cx[r]);
+    o[1] = -(static_cast<double>(acc.sy[r]) - acc.cy[r]);
+    o[2] = -(static_cast<double>(acc.sz[r]) - acc.cz[r]);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) o[3 + k] = mom[r][k];
+  }
+}
+
+// ------------------------------------------------------------- decision --
+
+__device__ __forceinline__ double laser_ax(const ClusterDev& c, double t, double* ay) {
+  const double amp = c.a0 * envelope(t, c.env, c.tau);
+  double sn, cs;
+  sincos(t, &sn, &cs);
+  *ay = c.pol ? -amp * cs : 0.0;
+  return amp * sn;
+}
+
+__global__ void __launch_bounds__(256) k_ion_decide(const IonArgs a) {
+  const long long step = __ldcg(a.step);
+  if (!pass_active(a, step)) return;
+  const long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= a.ion.n_ions) return;
+  const long long i = a.c.off + t;
+  const double* sc = a.scratch + 8 * t;
+  const double tn = a.c.t0 + static_cast<double>(step) * a.c.dt;
+  double lay;
+  const double lax = laser_ax(a.c, tn, &lay);
+  const double ex = sc[0] + lax, ey = sc[1] + lay, ez = sc[2];
+  const double emag = sqrt(ex * ex + ey * ey + ez * ez);
+  double ne = 0.0, te = 0.0;
+  if (sc[3] > 0.0) {
+    const double lk = a.ion.r_loc / a.ion.k_si;  // r_loc in metres
+    const double vol_cm3 = (4.0 / 3.0) * kPi * lk * lk * lk * 1e6;
+    const double mx = sc[4] / sc[3], my = sc[5] / sc[3], mz = sc[6] / sc[3];
+    const double var = sc[7] / sc[3] - (mx * mx + my * my + mz * mz);
+    ne = sc[3] / vol_cm3;
+    te = var > 0.0 ? kMeC2Ev * var / 3.0 : 0.0;
+  }
+  double* o = a.out + 4 * t;
+  o[0] = emag;
+  o[1] = ne;
+  o[2] = te;
+  o[3] = 0.0;
+  a.fired[t] = 0;
+  const int z = a.zq[i];
+  if (a.kind[i] != 0 || z < 0 || z >= a.ion.zmax) return;
+  double nu = rate_plain(a.ion, emag, z, ne, te);
+  const double dt_ion = (a.ion.ionize_every > 0 ? a.ion.ionize_every : 1) * a.c.dt;
+  const double P = -expm1(-nu * dt_ion);
+  o[3] = P;
+  const uint4 wv = philox4x32_10(
+      make_uint4(static_cast<uint32_t>(t), static_cast<uint32_t>(step),
+                 static_cast<uint32_t>(static_cast<unsigned long long>(step) >> 32), 0u),
+      make_uint2(static_cast<uint32_t>(a.ion.seed), static_cast<uint32_t>(a.ion.seed >> 32)));
+  const double alpha = (static_cast<double>(wv.x) + 1.0) * (1.0 / 4294967296.0);
+  if (!(alpha < P)) return;
+  a.fired[t] = 1;
+  const int z1 = z + 1;
+  const double kc_w = a.ion.kc * a.w[i];
+  float4* cur = (step & 1) ? a.posq1 : a.posq0;
+  a.zq[i] = z1;
+  a.qm[i] = static_cast<float>(z1 / a.mass[i]);
+  cur[i].w = static_cast<float>(kc_w * z1);
+  // the freed electron: uniform in the ball of radius r_create around the ion
+  const double u1 = (static_cast<double>(wv.y) + 0.5) * (1.0 / 4294967296.0);
+  const double u2 = (static_cast<double>(wv.z) + 0.5) * (1.0 / 4294967296.0);
+  const double u3 = (static_cast<double>(wv.w) + 0.5) * (1.0 / 4294967296.0);
+  const double ct = 2.0 * u1 - 1.0, st = sqrt(fmax(0.0, 1.0 - ct * ct));
+  const double ph = 2.0 * kPi * u2, rr = a.ion.r_create * cbrt(u3);
+  const long long e = a.c.off + a.ion.slot_base + static_cast<long long>(z) * a.ion.n_ions + t;
+  const double X = a.x[i] + rr * st * cos(ph), Y = a.y[i] + rr * st * sin(ph), Z = a.z[i] + rr * ct;
+  a.x[e] = X;
+  a.y[e] = Y;
+  a.z[e] = Z;
+  a.ux[e] = a.ux[i];
+  a.uy[e] = a.uy[i];
+  a.uz[e] = a.uz[i];
+  a.zq[e] = -1;
+  a.qm[e] = -1.0f;
+  a.w[e] = a.w[i];
+  a.mass[e] = 1.0;
+  a.kind[e] = 1;
+  cur[e] = make_float4(static_cast<float>(X), static_cast<float>(Y), static_cast<float>(Z),
+                       static_cast<float>(-kc_w));
+}
+
+constexpr int kIonThreads = 128;
+constexpr int kIonR = 2;
+constexpr int kIonTile = 512;
+
+}  // namespace
+
+cudaError_t launch_ion_pass(const IonArgs& a, cudaStream_t s) {
+  if (a.ion.n_ions <= 0) return cudaSuccess;
+  const long long per = kIonThreads * kIonR;
+  const unsigned g1 = static_cast<unsigned>((a.ion.n_ions + per - 1) / per);
+  k_ion_field<kIonThreads, kIonR, kIonTile, 2><<<g1, kIonThreads, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const unsigned g2 = static_cast<unsigned>((a.ion.n_ions + 255) / 256);
+  k_ion_decide<<<g2, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace md

@@ -6,6 +6,76 @@
 
 namespace md {
 
+// Sums the per-block partials in block order (deterministic); one thread per
+// component.
+__global__ void k_diag_final(const DiagPartial* __restrict__ part, int nblocks,
+                             DiagPartial* __restrict__ out) {
+  const int k = threadIdx.x;
+  if (k < 8) {
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += part[b].v[k];
+    out->v[k] = s;
+  } else if (k < 10) {
+    long long s = 0;
+    for (int b = 0; b < nblocks; ++b) s += part[b].cnt[k - 8];
+    out->cnt[k - 8] = s;
+  } else if (k < 10 + kHistBins) {
+    long long s = 0;
+    for (int b = 0; b < nblocks; ++b) s += part[b].hist[k - 10];
+    out->hist[k - 10] = s;
+  } else if (k < 10 + 2 * kHistBins) {
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += part[b].histw[k - 10 - kHistBins];
+    out->histw[k - 10 - kHistBins] = s;
+  }
+}
+
+// ------------------------------------------------------------ layout glue --
+
+// Scatter host-layout records ([n][3] x/u, z, mass, w, kind) into the SoA
+// device state of one cluster starting at record `off`; writes the current
+// j-stream entry (x, y, z, K_C w z).
+
+__global__ void k_upload(const UploadArgs a) {
+  const long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= a.n) return;
+  const long long i = a.off + k;
+  const unsigned char kd = a.hkind[k];
+  const double X = a.hx[3 * k], Y = a.hx[3 * k + 1], Z = a.hx[3 * k + 2];
+  a.x[i] = X;
+  a.y[i] = Y;
+  a.z[i] = Z;
+  a.ux[i] = a.hu[3 * k];
+  a.uy[i] = a.hu[3 * k + 1];
+  a.uz[i] = a.hu[3 * k + 2];
+  const int zq = a.hz[k];
+  a.zq[i] = zq;
+  a.mass[i] = a.hmass[k];
+  a.w[i] = a.hw[k];
+  a.kind[i] = kd;
+  const bool live = (kd != 2);
+  a.qm[i] = live ? static_cast<float>(zq / a.hmass[k]) : 0.0f;
+  const float q = live ? static_cast<float>(a.kc * a.hw[k] * zq) : 0.0f;
+  const float4 p = make_float4(static_cast<float>(X), static_cast<float>(Y), static_cast<float>(Z), q);
+  const long long step = __ldcg(a.step);
+  if (step & 1) a.posq1[i] = p; else a.posq0[i] = p;
+}
+
+__global__ void k_download(const DownloadArgs a) {  const long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= a.n) return;
+  const long long i = a.off + k;
+  a.hx[3 * k] = a.x[i];
+  a.hx[3 * k + 1] = a.y[i];
+  a.hx[3 * k + 2] = a.z[i];
+  a.hu[3 * k] = a.ux[i];
+  a.hu[3 * k + 1] = a.uy[i];
+  a.hu[3 * k + 2] = a.uz[i];
+  a.hz[k] = a.zq[i];
+  a.hmass[k] = a.mass[i];
+  a.hw[k] = a.w[i];
+  a.hkind[k] = a.kind[i];
+}
+
 namespace {
 
 template <int T, int R, int TILE, int ST, bool PK, int MB>

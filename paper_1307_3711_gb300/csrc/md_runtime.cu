@@ -101,6 +101,15 @@ struct md_ctx {
   int iblk_cap = 0;
 
   cudaGraphExec_t graph = nullptr;
+
+  // ionization
+  std::vector<md::IonDev> ion;
+  std::vector<long long> ion_out_off;  // per cluster, into d_ion_out / d_ion_fired
+  bool any_ion = false;
+  double* d_ion_scratch = nullptr;     // [max n_ions][8]
+  double* d_ion_out = nullptr;         // [sum n_ions][4]
+  unsigned char* d_ion_fired = nullptr;
+  const float* d_mlp = nullptr;        // surrogate weights (device), if set
 };
 
 namespace {
@@ -151,6 +160,31 @@ md_status validate_config(const md_config& c, int idx) {
   if (c.envelope != MD_ENV_FLAT && !(c.tau > 0.0))
     return fail(MD_ERR_ARG, "cluster %d: tau must be > 0", idx);
   if (c.reserved != 0) return fail(MD_ERR_ARG, "cluster %d: reserved must be 0", idx);
+  if (c.rate_model < 0 || c.rate_model > 2)
+    return fail(MD_ERR_ARG, "cluster %d: rate_model must be 0, 1 or 2", idx);
+  return MD_OK;
+}
+
+md_status validate_ionization(const md_config& c, const md_particles& p, int idx) {
+  if (c.rate_model == 0) return MD_OK;
+  if (c.zmax < 1 || c.zmax > md::kMaxZ)
+    return fail(MD_ERR_ARG, "cluster %d: zmax must be in [1, 16]", idx);
+  if (c.n_ions < 1 || c.n_ions > p.n) return fail(MD_ERR_ARG, "cluster %d: bad n_ions", idx);
+  if (c.slot_base < c.n_ions ||
+      c.slot_base + static_cast<long long>(c.zmax) * c.n_ions > p.n)
+    return fail(MD_ERR_ARG,
+                "cluster %d: electron slots [slot_base, slot_base + zmax n_ions) must lie "
+                "after the ions and inside the records", idx);
+  if (c.ionize_every < 0) return fail(MD_ERR_ARG, "cluster %d: ionize_every < 0", idx);
+  if (!(c.r_loc > 0.0) || !(c.r_create >= 0.0))
+    return fail(MD_ERR_ARG, "cluster %d: r_loc must be > 0 and r_create >= 0", idx);
+  for (int z = 0; z < c.zmax; ++z)
+    if (!(c.ip_ev[z] > 0.0) || !(c.q_outer[z] >= 0.0))
+      return fail(MD_ERR_ARG, "cluster %d: ip_ev[%d] must be > 0, q_outer >= 0", idx, z);
+  for (long long i = 0; i < c.n_ions; ++i) {
+    const int kd = p.kind ? p.kind[i] : (p.z[i] < 0 ? MD_KIND_ELECTRON : MD_KIND_ION);
+    if (kd != MD_KIND_ION) return fail(MD_ERR_ARG, "cluster %d: record %lld < n_ions is not an ion", idx, i);
+  }
   return MD_OK;
 }
 
@@ -359,11 +393,54 @@ md_status check_device_error(md_ctx* c) {
   return MD_OK;
 }
 
+md::IonArgs ion_args(md_ctx* c, int ci, int force) {
+  md::IonArgs a;
+  a.c = c->cl[ci];
+  a.ion = c->ion[ci];
+  a.posq0 = c->d_posq[0];
+  a.posq1 = c->d_posq[1];
+  a.x = c->d_x[0];
+  a.y = c->d_x[1];
+  a.z = c->d_x[2];
+  a.ux = c->d_u[0];
+  a.uy = c->d_u[1];
+  a.uz = c->d_u[2];
+  a.qm = c->d_qm;
+  a.w = c->d_w;
+  a.mass = c->d_mass;
+  a.zq = c->d_z;
+  a.kind = c->d_kind;
+  a.step = c->d_step;
+  a.err = c->d_err;
+  a.force = force;
+  a.scratch = c->d_ion_scratch;
+  a.out = c->d_ion_out + 4 * c->ion_out_off[ci];
+  a.fired = c->d_ion_fired + c->ion_out_off[ci];
+  a.mlp = c->d_mlp;
+  return a;
+}
+
+// Ionization passes of all clusters (the kernels skip themselves unless the
+// device step is due or `force` is set).
+cudaError_t launch_ion_all(md_ctx* c, int force, cudaStream_t s) {
+  for (int ci = 0; ci < c->n_clusters; ++ci) {
+    if (!c->ion[ci].rate_model) continue;
+    if (!force && c->ion[ci].ionize_every <= 0) continue;
+    cudaError_t e = md::launch_ion_pass(ion_args(c, ci, force), s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 md_status launch_steps_direct(md_ctx* c, int n) {
   int ncfg = 0;
   const md::KernelConfig* cfgs = md::step_configs(&ncfg);
   const md::StepArgs a = step_args(c);
   for (int s = 0; s < n; ++s) {
+    if (c->any_ion) {
+      cudaError_t e = launch_ion_all(c, 0, c->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "ionization launch");
+    }
     cudaError_t e = cfgs[c->cfg].launch_step(a, c->grid, c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
   }
@@ -379,8 +456,10 @@ md_status build_graph(md_ctx* c) {
     int ncfg = 0;
     const md::KernelConfig* cfgs = md::step_configs(&ncfg);
     const md::StepArgs a = step_args(c);
-    for (int s = 0; s < kGraphSteps && e == cudaSuccess; ++s)
-      e = cfgs[c->cfg].launch_step(a, c->grid, cs);
+    for (int s = 0; s < kGraphSteps && e == cudaSuccess; ++s) {
+      if (c->any_ion) e = launch_ion_all(c, 0, cs);
+      if (e == cudaSuccess) e = cfgs[c->cfg].launch_step(a, c->grid, cs);
+    }
     cudaError_t e2 = cudaStreamEndCapture(cs, &g);
     if (e == cudaSuccess) e = e2;
   }
@@ -419,6 +498,9 @@ void free_ctx(md_ctx* c) {
   cudaFree(c->d_fpart);
   cudaFree(c->d_iblk_cnt);
   cudaFree(c->d_raw);
+  cudaFree(c->d_ion_scratch);
+  cudaFree(c->d_ion_out);
+  cudaFree(c->d_ion_fired);
   if (c->h_raw) cudaFreeHost(c->h_raw);
   if (c->h_diag) cudaFreeHost(c->h_diag);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -520,6 +602,8 @@ md_status md_init(md_ctx** out, const md_config* cfgs, int32_t n_clusters,
     if (st != MD_OK) return st;
     st = validate_particles(parts[i], i, -1);
     if (st != MD_OK) return st;
+    st = validate_ionization(cfgs[i], parts[i], i);
+    if (st != MD_OK) return st;
   }
   md_ctx* c = new md_ctx();
   auto bail = [&](md_status st) {
@@ -563,6 +647,26 @@ md_status md_init(md_ctx** out, const md_config* cfgs, int32_t n_clusters,
     d.boundary = f.boundary;
     c->cl.push_back(d);
     c->kc.push_back(md_coulomb_constant(f.lambda_um));
+    md::IonDev io;
+    std::memset(&io, 0, sizeof(io));
+    io.rate_model = f.rate_model;
+    io.ionize_every = f.ionize_every;
+    io.zmax = f.zmax;
+    io.n_ions = f.rate_model ? f.n_ions : 0;
+    io.slot_base = f.slot_base;
+    io.seed = f.seed;
+    io.r_loc = f.r_loc;
+    io.r_create = f.r_create;
+    io.kc = md_coulomb_constant(f.lambda_um);
+    io.k_si = 2.0 * kPi / (f.lambda_um * 1e-6);
+    io.omega = 299792458.0 * io.k_si;
+    for (int z = 0; z < md::kMaxZ; ++z) {
+      io.ip_ev[z] = f.ip_ev[z];
+      io.q_outer[z] = f.q_outer[z];
+    }
+    c->ion_out_off.push_back(c->ion.empty() ? 0 : c->ion_out_off.back() + c->ion.back().n_ions);
+    c->ion.push_back(io);
+    if (f.rate_model) c->any_ion = true;
     off += d.n_pad;
     c->max_n = std::max<long long>(c->max_n, parts[i].n);
   }
@@ -597,6 +701,19 @@ md_status md_init(md_ctx** out, const md_config* cfgs, int32_t n_clusters,
   if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
   e = cudaMallocHost(reinterpret_cast<void**>(&c->h_raw), c->raw_bytes);
   if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMallocHost"));
+  if (c->any_ion) {
+    long long max_ion = 0, sum_ion = 0;
+    for (auto& io : c->ion) {
+      max_ion = std::max<long long>(max_ion, io.n_ions);
+      sum_ion += io.n_ions;
+    }
+    if (dev_alloc(&c->d_ion_scratch, 8 * static_cast<size_t>(max_ion)) != cudaSuccess ||
+        dev_alloc(&c->d_ion_out, 4 * static_cast<size_t>(sum_ion)) != cudaSuccess ||
+        dev_alloc(&c->d_ion_fired, static_cast<size_t>(sum_ion)) != cudaSuccess)
+      return bail(fail(MD_ERR_OOM, "ionization buffers"));
+    cudaMemsetAsync(c->d_ion_out, 0, sizeof(double) * 4 * sum_ion, c->stream);
+    cudaMemsetAsync(c->d_ion_fired, 0, sum_ion, c->stream);
+  }
 
   // zero state; padding records are INACTIVE with zero charge at the origin
   cudaStream_t s = c->stream;
@@ -650,6 +767,36 @@ md_status md_step(md_ctx* c, int32_t nsteps) {
 md_status md_sync(md_ctx* c) {
   if (!c) return fail(MD_ERR_ARG, "ctx is NULL");
   MD_CUDA(cudaStreamSynchronize(c->stream));
+  return check_device_error(c);
+}
+
+md_status md_ionize(md_ctx* c) {
+  if (!c) return fail(MD_ERR_ARG, "ctx is NULL");
+  if (!c->any_ion) return MD_OK;
+  cudaError_t e = launch_ion_all(c, 1, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "ionization launch");
+  return MD_OK;
+}
+
+md_status md_get_ionization(md_ctx* c, int32_t cluster, double* emag, double* ne, double* te,
+                            double* prob, uint8_t* fired) {
+  if (!c) return fail(MD_ERR_ARG, "ctx is NULL");
+  if (cluster < 0 || cluster >= c->n_clusters) return fail(MD_ERR_ARG, "bad cluster index");
+  const long long n = c->ion[cluster].n_ions;
+  if (!c->ion[cluster].rate_model || n == 0) return fail(MD_ERR_STATE, "cluster has no ionization");
+  std::vector<double> out(4 * n);
+  MD_CUDA(cudaMemcpyAsync(out.data(), c->d_ion_out + 4 * c->ion_out_off[cluster],
+                          sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, c->stream));
+  if (fired)
+    MD_CUDA(cudaMemcpyAsync(fired, c->d_ion_fired + c->ion_out_off[cluster], n,
+                            cudaMemcpyDeviceToHost, c->stream));
+  MD_CUDA(cudaStreamSynchronize(c->stream));
+  for (long long i = 0; i < n; ++i) {
+    if (emag) emag[i] = out[4 * i];
+    if (ne) ne[i] = out[4 * i + 1];
+    if (te) te[i] = out[4 * i + 2];
+    if (prob) prob[i] = out[4 * i + 3];
+  }
   return check_device_error(c);
 }
 

@@ -22,6 +22,24 @@ struct ClusterDev {
   int pol, env, boundary;
 };
 
+constexpr int kMaxZ = 16;
+
+// Ionization parameters of one cluster (Sec. II, ionization paragraph).
+struct IonDev {
+  int rate_model;     // 0 off, 1 ADK + Lotz, 2 MLP surrogate (1 outside its range)
+  int ionize_every;   // pass before every k-th step (0: explicit calls only)
+  int zmax;
+  int n_ions;         // records [off, off + n_ions) can ionize
+  long long slot_base;  // cluster-relative first electron slot (z-major)
+  unsigned long long seed;
+  double r_loc, r_create;
+  double kc;          // K_C of the cluster: Q = kc w z
+  double k_si;        // laser wave number, 1/m
+  double omega;       // laser angular frequency, rad/s
+  double ip_ev[kMaxZ];
+  double q_outer[kMaxZ];
+};
+
 struct Unit {
   int cluster;
   int block;  // i-block within the cluster
@@ -50,6 +68,32 @@ struct StepArgs {
   double* part;
   unsigned* iblk_cnt;
   long long n_total;
+};
+
+// Arguments of the ionization kernels of one cluster.
+struct IonArgs {
+  ClusterDev c;
+  IonDev ion;
+  float4* posq0;
+  float4* posq1;
+  double* x;
+  double* y;
+  double* z;
+  double* ux;
+  double* uy;
+  double* uz;
+  float* qm;
+  double* w;
+  double* mass;
+  int* zq;
+  unsigned char* kind;
+  const long long* step;
+  int* err;
+  int force;          // 1: run regardless of ionize_every
+  double* scratch;    // [n_ions][8]: ex, ey, ez, sw, swux, swuy, swuz, swu2
+  double* out;        // [n_ions][4]: |E|, ne (cm^-3), Te (eV), P
+  unsigned char* fired;  // [n_ions]
+  const float* mlp;   // surrogate weights (rate_model 2) or nullptr
 };
 
 struct FieldArgs {

@@ -37,7 +37,11 @@ class Config(C.Structure):
                 ("dt", C.c_double), ("softening", C.c_double), ("box", C.c_double),
                 ("t_switch", C.c_double), ("lambda_um", C.c_double),
                 ("polarization", C.c_int32), ("envelope", C.c_int32),
-                ("boundary", C.c_int32), ("reserved", C.c_int32)]
+                ("boundary", C.c_int32), ("rate_model", C.c_int32),
+                ("ionize_every", C.c_int32), ("zmax", C.c_int32), ("n_ions", C.c_int32),
+                ("reserved", C.c_int32), ("slot_base", C.c_int64), ("seed", C.c_uint64),
+                ("r_loc", C.c_double), ("r_create", C.c_double),
+                ("ip_ev", C.c_double * 16), ("q_outer", C.c_double * 16)]
 
 
 class Particles(C.Structure):
@@ -77,6 +81,8 @@ _SIGS = {
     "md_set_particles": (_st, [_ctx_p, C.c_int32, C.POINTER(Particles)]),
     "md_get_fields": (_st, [_ctx_p, C.c_int32, _p, _p]),
     "md_get_step": (_st, [_ctx_p, C.POINTER(C.c_int64)]),
+    "md_ionize": (_st, [_ctx_p]),
+    "md_get_ionization": (_st, [_ctx_p, C.c_int32, _p, _p, _p, _p, _p]),
     "md_tuning_list": (C.c_int32, [C.POINTER(Tuning), C.c_int32]),
     "md_set_tuning": (_st, [_ctx_p, C.POINTER(Tuning)]),
     "md_get_tuning": (_st, [_ctx_p, C.POINTER(Tuning)]),
@@ -177,11 +183,26 @@ class HostParticles:
                          _ptr(self.w), _ptr(self.kind))
 
 
+RATES_NONE, RATES_PLAIN, RATES_MLP = 0, 1, 2
+
+
 def make_config(a0=0.0, tau=1.0, t0=0.0, dt=0.02, softening=1e-3, box=0.0, t_switch=0.0,
                 lambda_um=0.8, polarization=0, envelope=ENV_SIN2,
-                boundary=BOUNDARY_OPEN) -> Config:
-    return Config(a0, tau, t0, dt, softening, box, t_switch, lambda_um, polarization, envelope,
-                  boundary, 0)
+                boundary=BOUNDARY_OPEN, rate_model=RATES_NONE, ionize_every=0, zmax=0,
+                n_ions=0, slot_base=0, seed=0, r_loc=0.0, r_create=0.0, species=None) -> Config:
+    c = Config()
+    c.a0, c.tau, c.t0, c.dt, c.softening = a0, tau, t0, dt, softening
+    c.box, c.t_switch, c.lambda_um = box, t_switch, lambda_um
+    c.polarization, c.envelope, c.boundary = polarization, envelope, boundary
+    c.rate_model, c.ionize_every, c.zmax, c.n_ions = rate_model, ionize_every, zmax, n_ions
+    c.reserved, c.slot_base, c.seed = 0, slot_base, seed & (2 ** 64 - 1)
+    c.r_loc, c.r_create = r_loc, r_create
+    if species is not None:
+        for k, v in enumerate(species["ip_ev"]):
+            c.ip_ev[k] = v
+        for k, v in enumerate(species["q_outer"]):
+            c.q_outer[k] = v
+    return c
 
 
 def config_from_workload(w) -> Config:
@@ -257,6 +278,17 @@ class Context:
         phi = np.zeros(n) if potential else None
         _check(_lib.md_get_fields(self._h, cluster, _ptr(e), _ptr(phi)))
         return (e, phi) if potential else e
+
+    def ionize(self):
+        _check(_lib.md_ionize(self._h))
+
+    def ionization(self, cluster: int = 0, n_ions: int | None = None) -> dict:
+        n = int(n_ions if n_ions is not None else self._cfgs[cluster].n_ions)
+        emag, ne, te, prob = (np.zeros(n) for _ in range(4))
+        fired = np.zeros(n, np.uint8)
+        _check(_lib.md_get_ionization(self._h, cluster, _ptr(emag), _ptr(ne), _ptr(te),
+                                      _ptr(prob), _ptr(fired)))
+        return {"emag": emag, "ne": ne, "te": te, "prob": prob, "fired": fired}
 
     def tuning(self):
         t = Tuning()
