@@ -23,7 +23,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libmd_oracle.so")
 # a planted-mistake test compiles a mutant elsewhere and points here
 _LIB_OVERRIDE = os.environ.get("MD_ORACLE_LIB")
-_SOURCES = ["md_oracle.c", "ionize_oracle.c"]
+_SOURCES = ["md_oracle.c", "ionize_oracle.c", "mlp_oracle.c"]
 _lock = threading.Lock()
 _lib = None
 
@@ -102,6 +102,18 @@ def lib():
             L.io_rate_total.argtypes = [d, i, d, d, p, p, d]
             L.io_local_moments.restype = None
             L.io_local_moments.argtypes = [i, p, i, p, p, p, p, p, d, d, p, p]
+            L.mo_nparam.restype = i
+            L.mo_nparam.argtypes = []
+            L.mo_features.restype = None
+            L.mo_features.argtypes = [d, i, d, d, p]
+            L.mo_target.restype = d
+            L.mo_target.argtypes = [d]
+            L.mo_rate_from_output.restype = d
+            L.mo_rate_from_output.argtypes = [d]
+            L.mo_forward.restype = None
+            L.mo_forward.argtypes = [p, i, p, p]
+            L.mo_loss_grad.restype = d
+            L.mo_loss_grad.argtypes = [p, i, p, p, p, p]
             L.io_decide.restype = None
             L.io_decide.argtypes = [i, p, p, p, p, p, p, p, i, d, d, C.c_uint64, i64, d, p, p,
                                     p]
@@ -370,3 +382,42 @@ def ionize_pass(state: "State", params: Params, species, n_ion, slot_base, zmax,
         state.active[slot] = 1
     state.z[:n_ion] = z_new
     return fired, amag, ne, te
+
+
+# ------------------------------------------------------------ rate surrogate
+# Learned stand-in for the rate evaluation; definition in mlp_oracle.c.
+
+def mlp_nparam():
+    return lib().mo_nparam()
+
+
+def mlp_features(e_mag, z, ne, te):
+    f = np.zeros(4)
+    lib().mo_features(float(e_mag), int(z), float(ne), float(te), _ptr(f))
+    return f
+
+
+def mlp_target(nu):
+    return lib().mo_target(float(nu))
+
+
+def mlp_rate_from_output(y):
+    return lib().mo_rate_from_output(float(y))
+
+
+def mlp_forward(params, feats):
+    p = _f64(params).ravel()
+    f = _f64(feats, (-1, 4))
+    y = np.zeros((f.shape[0], 8))
+    lib().mo_forward(_ptr(p), f.shape[0], _ptr(f), _ptr(y))
+    return y
+
+
+def mlp_loss_grad(params, feats, z, target):
+    p = _f64(params).ravel()
+    f = _f64(feats, (-1, 4))
+    zz = np.ascontiguousarray(z, dtype=np.int32)
+    t = _f64(target).ravel()
+    g = np.zeros(mlp_nparam())
+    loss = lib().mo_loss_grad(_ptr(p), f.shape[0], _ptr(f), _ptr(zz), _ptr(t), _ptr(g))
+    return loss, g

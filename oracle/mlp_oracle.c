@@ -1,0 +1,138 @@
+/*
+ * mlp_oracle.c -- FP64 reference of the learned ionization-rate surrogate.
+ * TEST INFRASTRUCTURE ONLY (see md_oracle.c).
+ *
+ * The surrogate is not from the paper: it stands in for the per-ion rate
+ * evaluation of Sec. II (nu_total = nu_ofi + nu_ci).  Definition:
+ *   features  f = ((log10 max(|E|, 1e-6) + 1.5) / 1.5,  z / 8,
+ *                  (log10 max(n_e, 1e15) - 19.5) / 4.5,
+ *                  (log10 max(T_e, 0.1) - 1.5) / 2.5)
+ *   network   h1 = silu(W1 f + b1)    (64)
+ *             h2 = silu(W2 h1 + b2)   (64)
+ *             y  = W3 h2 + b3          (8)
+ *   output    y_k approximates (log10 max(nu_k, 1e-30) + 15) / 15 for the
+ *             transition k -> k+1; the ion of charge z uses y_z.
+ *   loss      mean over samples of (y_{z_s} - target_s)^2.
+ * Parameters, one flat array: W1[64][4], b1[64], W2[64][64], b2[64],
+ * W3[8][64], b3[8] (5000 values, rows = outputs).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#define NI 4
+#define NH 64
+#define NO 8
+#define OFF_W1 0
+#define OFF_B1 (OFF_W1 + NH * NI)
+#define OFF_W2 (OFF_B1 + NH)
+#define OFF_B2 (OFF_W2 + NH * NH)
+#define OFF_W3 (OFF_B2 + NH)
+#define OFF_B3 (OFF_W3 + NO * NH)
+#define NPARAM (OFF_B3 + NO)
+
+int mo_nparam(void) { return NPARAM; }
+
+void mo_features(double e_mag, int z, double ne, double te, double f[4])
+{
+    f[0] = (log10(fmax(e_mag, 1e-6)) + 1.5) / 1.5;
+    f[1] = z / 8.0;
+    f[2] = (log10(fmax(ne, 1e15)) - 19.5) / 4.5;
+    f[3] = (log10(fmax(te, 0.1)) - 1.5) / 2.5;
+}
+
+double mo_target(double nu) { return (log10(fmax(nu, 1e-30)) + 15.0) / 15.0; }
+
+double mo_rate_from_output(double y) { return pow(10.0, 15.0 * y - 15.0); }
+
+static double silu(double a) { return a / (1.0 + exp(-a)); }
+
+/* d silu / da = s (1 + a (1 - s)), s = sigmoid(a) */
+static double dsilu(double a)
+{
+    double s = 1.0 / (1.0 + exp(-a));
+    return s * (1.0 + a * (1.0 - s));
+}
+
+/* Forward pass of n samples f[n][4] -> y[n][8]. */
+void mo_forward(const double *p, int n, const double *f, double *y)
+{
+    for (int s = 0; s < n; ++s) {
+        double h1[NH], h2[NH];
+        for (int j = 0; j < NH; ++j) {
+            double a = p[OFF_B1 + j];
+            for (int k = 0; k < NI; ++k) a += p[OFF_W1 + j * NI + k] * f[s * NI + k];
+            h1[j] = silu(a);
+        }
+        for (int j = 0; j < NH; ++j) {
+            double a = p[OFF_B2 + j];
+            for (int k = 0; k < NH; ++k) a += p[OFF_W2 + j * NH + k] * h1[k];
+            h2[j] = silu(a);
+        }
+        for (int j = 0; j < NO; ++j) {
+            double a = p[OFF_B3 + j];
+            for (int k = 0; k < NH; ++k) a += p[OFF_W3 + j * NH + k] * h2[k];
+            y[s * NO + j] = a;
+        }
+    }
+}
+
+/* Loss (mean squared error of the selected outputs) and its gradient with
+ * respect to every parameter, by reverse-mode differentiation of the forward
+ * pass (chain rule written out layer by layer).  grad has NPARAM entries. */
+double mo_loss_grad(const double *p, int n, const double *f, const int32_t *z,
+                    const double *target, double *grad)
+{
+    memset(grad, 0, sizeof(double) * NPARAM);
+    double loss = 0.0;
+    for (int s = 0; s < n; ++s) {
+        double a1[NH], h1[NH], a2[NH], h2[NH], y[NO];
+        const double *x = f + s * NI;
+        for (int j = 0; j < NH; ++j) {
+            double a = p[OFF_B1 + j];
+            for (int k = 0; k < NI; ++k) a += p[OFF_W1 + j * NI + k] * x[k];
+            a1[j] = a;
+            h1[j] = silu(a);
+        }
+        for (int j = 0; j < NH; ++j) {
+            double a = p[OFF_B2 + j];
+            for (int k = 0; k < NH; ++k) a += p[OFF_W2 + j * NH + k] * h1[k];
+            a2[j] = a;
+            h2[j] = silu(a);
+        }
+        for (int j = 0; j < NO; ++j) {
+            double a = p[OFF_B3 + j];
+            for (int k = 0; k < NH; ++k) a += p[OFF_W3 + j * NH + k] * h2[k];
+            y[j] = a;
+        }
+        int zs = z[s];
+        double r = y[zs] - target[s];
+        loss += r * r;
+        double dy[NO] = {0};
+        dy[zs] = 2.0 * r / n;
+        double dh2[NH] = {0};
+        for (int j = 0; j < NO; ++j) {
+            if (dy[j] == 0.0) continue;
+            grad[OFF_B3 + j] += dy[j];
+            for (int k = 0; k < NH; ++k) {
+                grad[OFF_W3 + j * NH + k] += dy[j] * h2[k];
+                dh2[k] += dy[j] * p[OFF_W3 + j * NH + k];
+            }
+        }
+        double da2[NH], dh1[NH] = {0};
+        for (int j = 0; j < NH; ++j) da2[j] = dh2[j] * dsilu(a2[j]);
+        for (int j = 0; j < NH; ++j) {
+            grad[OFF_B2 + j] += da2[j];
+            for (int k = 0; k < NH; ++k) {
+                grad[OFF_W2 + j * NH + k] += da2[j] * h1[k];
+                dh1[k] += da2[j] * p[OFF_W2 + j * NH + k];
+            }
+        }
+        for (int j = 0; j < NH; ++j) {
+            double da1 = dh1[j] * dsilu(a1[j]);
+            grad[OFF_B1 + j] += da1;
+            for (int k = 0; k < NI; ++k) grad[OFF_W1 + j * NI + k] += da1 * x[k];
+        }
+    }
+    return loss / n;
+}

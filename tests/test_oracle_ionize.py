@@ -105,16 +105,18 @@ def test_rate_total_units():
 
 
 def test_local_moments_constructed_case():
-    """Six electrons at 0.5 r_loc along +-x, +-y, +-z with u = +-v along the
-    same axis (mean zero, <u^2> = v^2): ne = 6 w / volume, Te = m c^2 v^2 / 3;
-    an ion, an inactive slot and a far electron do not count."""
+    """Six electrons at 0.5 r_loc along +-x, +-y, +-z with u = drift +- v
+    along the same axis (spread about the mean: <|u - <u>|^2> = v^2):
+    ne = 6 w / volume, Te = m c^2 v^2 / 3 in the local mean frame; an ion,
+    an inactive slot and a far electron do not count."""
     r_loc, v, w = 0.01, 0.003, 2.0
+    drift = np.array([0.002, -0.001, 0.0005])
     pos = []
     vel = []
     for ax in range(3):
         for s in (1, -1):
             p = np.zeros(3); p[ax] = 0.5 * s * r_loc
-            q = np.zeros(3); q[ax] = s * v
+            q = drift.copy(); q[ax] += s * v
             pos.append(p); vel.append(q)
     x = np.array(pos + [[0.001, 0, 0], [0, 0.002, 0], [2 * r_loc, 0, 0]])
     u = np.array(vel + [[0, 0, 0], [0, 0, 0], [0.5, 0, 0]])
@@ -125,7 +127,7 @@ def test_local_moments_constructed_case():
     k = 2 * math.pi / 0.8e-6
     vol_cm3 = 4 / 3 * math.pi * (r_loc / k) ** 3 * 1e6
     assert ne[0] == pytest.approx(6 * w / vol_cm3, rel=1e-12)
-    assert te[0] == pytest.approx(510998.95 * v * v / 3, rel=1e-12)
+    assert te[0] == pytest.approx(510998.95 * v * v / 3, rel=1e-9)
     ne, te = oracle.local_moments(np.array([[10.0, 0, 0]]), st, r_loc)
     assert ne[0] == 0 and te[0] == 0
 

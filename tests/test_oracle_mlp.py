@@ -1,0 +1,58 @@
+"""Pins of the FP64 surrogate oracle: the analytic gradient equals central
+finite differences of the loss; the output map inverts the target map."""
+import numpy as np
+import pytest
+
+import oracle
+
+
+def random_params(seed, scale=0.4):
+    rng = np.random.default_rng(seed)
+    return rng.normal(size=oracle.mlp_nparam()) * scale
+
+
+def test_parameter_count():
+    assert oracle.mlp_nparam() == 64 * 4 + 64 + 64 * 64 + 64 + 8 * 64 + 8 == 5000
+
+
+def test_gradient_equals_finite_differences():
+    rng = np.random.default_rng(3)
+    p = random_params(1)
+    f = rng.normal(size=(7, 4))
+    z = rng.integers(0, 8, size=7)
+    t = rng.normal(size=7)
+    loss, g = oracle.mlp_loss_grad(p, f, z, t)
+    idx = np.concatenate([np.arange(0, 256, 17), np.arange(256, 320, 9),
+                          np.arange(320, 4416, 97), np.arange(4416, 4480, 7),
+                          np.arange(4480, 4992, 23), np.arange(4992, 5000)])
+    h = 1e-6
+    for i in idx:
+        pp = p.copy(); pp[i] += h
+        pm = p.copy(); pm[i] -= h
+        fd = (oracle.mlp_loss_grad(pp, f, z, t)[0] - oracle.mlp_loss_grad(pm, f, z, t)[0]) / (2 * h)
+        assert g[i] == pytest.approx(fd, rel=1e-6, abs=1e-9), i
+
+
+def test_forward_consistent_with_loss():
+    rng = np.random.default_rng(4)
+    p = random_params(2)
+    f = rng.normal(size=(11, 4))
+    z = rng.integers(0, 8, size=11)
+    t = rng.normal(size=11)
+    y = oracle.mlp_forward(p, f)
+    loss, _ = oracle.mlp_loss_grad(p, f, z, t)
+    assert loss == pytest.approx(np.mean((y[np.arange(11), z] - t) ** 2), rel=1e-12)
+
+
+@pytest.mark.parametrize("nu", [1e-30, 3.7e-12, 1e-3, 0.5, 7.0])
+def test_output_map_inverts_target(nu):
+    assert oracle.mlp_rate_from_output(oracle.mlp_target(nu)) == pytest.approx(nu, rel=1e-12)
+    assert oracle.mlp_target(0.0) == oracle.mlp_target(1e-40) == -1.0  # floored at 1e-30
+
+
+def test_features_definition_points():
+    f = oracle.mlp_features(10 ** -1.5, 8, 10 ** 19.5, 10 ** 1.5)
+    np.testing.assert_allclose(f, [0.0, 1.0, 0.0, 0.0], atol=1e-15)
+    f = oracle.mlp_features(0.0, 0, 0.0, 0.0)  # floors: 1e-6, 1e15 cm^-3, 0.1 eV
+    np.testing.assert_allclose(f, [(-6 + 1.5) / 1.5, 0.0, (15 - 19.5) / 4.5, (-1 - 1.5) / 2.5],
+                               atol=1e-15)

@@ -1,6 +1,6 @@
 """Planted mistakes in the oracle, on the CPU: each plausible slip (dropped
 term, wrong sign, wrong power, transposed operand, missing factor) compiled
-into a mutant of md_oracle.c must make at least one physics pin fail.  This
+into a mutant of the oracle's C sources must make at least one pin fail.  This
 shows that the pins constrain every part of the FP64 oracle."""
 import os
 import subprocess
@@ -9,7 +9,8 @@ import sys
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-SRC = os.path.join(ROOT, "oracle", "md_oracle.c")
+ORACLE = os.path.join(ROOT, "oracle")
+SOURCES = ["md_oracle.c", "ionize_oracle.c", "mlp_oracle.c"]
 
 # (name, exact text in md_oracle.c, replacement)
 MUTANTS = [
@@ -47,18 +48,69 @@ MUTANTS = [
      "if (qs[j] == 0.0) continue;"),
 ]
 
+# (name, file, exact text, replacement, pin file) for the ionization and
+# surrogate oracles
+MUTANTS_OTHER = [
+    ("philox_multiplier", "ionize_oracle.c", "uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;",
+     "uint64_t p1 = (uint64_t)0xCD9E8D55u * c2;", "test_oracle_ionize.py"),
+    ("philox_key_bump", "ionize_oracle.c", "k1 += 0xBB67AE85u;", "k1 += 0xBB67AE86u;",
+     "test_oracle_ionize.py"),
+    ("philox_word_order", "ionize_oracle.c", "uint32_t n2 = hi0 ^ c3 ^ k1;",
+     "uint32_t n2 = hi0 ^ c1 ^ k1;", "test_oracle_ionize.py"),
+    ("alpha_closed_at_zero", "ionize_oracle.c", "return ((double)w + 1.0) * (1.0 / 4294967296.0);",
+     "return ((double)w) * (1.0 / 4294967296.0);", "test_oracle_ionize.py"),
+    ("e1_series_sign", "ionize_oracle.c", "return -IO_EULER_GAMMA - log(x) + sum;",
+     "return -IO_EULER_GAMMA - log(x) - sum;", "test_oracle_ionize.py"),
+    ("adk_exponent", "ionize_oracle.c",
+     "return c2 * ip * pow(2.0 * F0 / F, 2.0 * ns - 1.0) * exp(-2.0 * F0 / (3.0 * F));",
+     "return c2 * ip * pow(2.0 * F0 / F, 2.0 * ns) * exp(-2.0 * F0 / (3.0 * F));",
+     "test_oracle_ionize.py"),
+    ("lotz_sqrt_t", "ionize_oracle.c",
+     "return v_th * IO_LOTZ_A * q * io_e1(P / T) / (P * sqrt(T));",
+     "return v_th * IO_LOTZ_A * q * io_e1(P / T) / (P * T);", "test_oracle_ionize.py"),
+    ("moments_no_mean_frame", "ionize_oracle.c",
+     "double var = su2 / sw - (mx * mx + my * my + mz * mz);", "double var = su2 / sw;",
+     "test_oracle_ionize.py"),
+    ("decision_le", "ionize_oracle.c", "if (alpha < P) {", "if (alpha > P) {",
+     "test_oracle_ionize.py"),
+    ("placement_radius", "ionize_oracle.c", "double ph = 2.0 * IO_PI * u2, r = r_create * cbrt(u3);",
+     "double ph = 2.0 * IO_PI * u2, r = r_create * u3;", "test_oracle_ionize.py"),
+    ("mlp_dsilu", "mlp_oracle.c", "return s * (1.0 + a * (1.0 - s));", "return s * (1.0 + a * s);",
+     "test_oracle_mlp.py"),
+    ("mlp_grad_w2_index", "mlp_oracle.c", "grad[OFF_W2 + j * NH + k] += da2[j] * h1[k];",
+     "grad[OFF_W2 + k * NH + j] += da2[j] * h1[k];", "test_oracle_mlp.py"),
+    ("mlp_loss_scale", "mlp_oracle.c", "dy[zs] = 2.0 * r / n;", "dy[zs] = r / n;",
+     "test_oracle_mlp.py"),
+]
+
+
+def _run_mutant(tmp_path, fname, old, new, pin_file):
+    sources = {f: open(os.path.join(ORACLE, f)).read() for f in SOURCES}
+    assert sources[fname].count(old) == 1, f"mutation anchor not unique in {fname}: {old}"
+    sources[fname] = sources[fname].replace(old, new)
+    paths = []
+    for f, txt in sources.items():
+        pth = tmp_path / f
+        pth.write_text(txt)
+        paths.append(str(pth))
+    so = tmp_path / "libmut.so"
+    subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+                    "-std=c11", "-o", str(so)] + paths + ["-lm"], check=True)
+    env = dict(os.environ, MD_ORACLE_LIB=str(so))
+    return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                           os.path.join(ROOT, "tests", pin_file)],
+                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+
 
 @pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
 def test_pins_catch_planted_mistake(name, old, new, tmp_path):
-    src = open(SRC).read()
-    assert src.count(old) == 1, f"mutation anchor for {name} not unique"
-    mut = tmp_path / "md_oracle_mutant.c"
-    mut.write_text(src.replace(old, new))
-    so = tmp_path / "libmut.so"
-    subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-                    "-std=c11", "-o", str(so), str(mut), "-lm"], check=True)
-    env = dict(os.environ, MD_ORACLE_LIB=str(so))
-    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
-                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    r = _run_mutant(tmp_path, "md_oracle.c", old, new, "test_oracle_pins.py")
+    assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
+
+
+@pytest.mark.parametrize("name,fname,old,new,pins", MUTANTS_OTHER,
+                         ids=[m[0] for m in MUTANTS_OTHER])
+def test_ionization_and_surrogate_pins_catch_planted_mistake(name, fname, old, new, pins,
+                                                             tmp_path):
+    r = _run_mutant(tmp_path, fname, old, new, pins)
     assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
