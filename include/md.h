@@ -272,6 +272,77 @@ md_status md_coulomb_field_device_noalloc(const void *src, int64_t ns, const voi
                                           int64_t nt, float eps2, int64_t self_offset,
                                           double *e, double *phi, void *stream);
 
+/* ---- learned rate surrogate ------------------------------------------------
+ * Not from the paper: a 4 -> 64 -> 64 -> 8 MLP (SiLU) standing in for the
+ * per-ion rate evaluation of the ionization pass, with BF16 weights and FP32
+ * accumulation on the tensor cores.  Features: ((log10 max(|E|,1e-6)+1.5)/1.5,
+ * z/8, (log10 max(n_e,1e15)-19.5)/4.5, (log10 max(T_e,0.1)-1.5)/2.5); output
+ * y_k ~ (log10(nu_k + 1e-12)+6)/6 for the step k -> k+1, inverted as
+ * nu = max(10^(6y-6) - 1e-12, 0) (rates below 1e-12 per unit time never
+ * ionize: P < 1e-13 per pass).  Parameters:
+ * 5000 FP32 values W1[64][4] b1[64] W2[64][64] b2[64] W3[8][64] b3[8]. */
+typedef struct {
+    double ip_ev[16];       /* species data as in md_config (z < zmax) */
+    double q_outer[16];
+    int32_t zmax;           /* 1..8 */
+    int32_t epochs;
+    double lambda_um;       /* laser wavelength of the unit conversion */
+    int64_t n_samples;      /* training samples; a held-out set of max(4096, n/20) is added */
+    int32_t batch;          /* minibatch size */
+    int32_t reserved;       /* must be 0 */
+    double lr;              /* Adam learning rate, cosine-decayed to 1 % */
+    uint64_t seed;          /* Philox key of the samples and of the initial weights */
+    double e_min, e_max;    /* training domain: |E| (paper units) */
+    double ne_min, ne_max;  /* n_e (cm^-3) */
+    double te_min, te_max;  /* T_e (eV) */
+} md_mlp_train_config;
+
+typedef struct {
+    double loss_first, loss_last;  /* mean minibatch loss of the first and last step */
+    double holdout_median_dlog10;  /* |log10 nu_surrogate - log10 nu_plain| on held-out samples */
+    double holdout_p99_dlog10;
+    double holdout_max_dlog10;
+    double train_ms;               /* device time of sample generation + training */
+    int64_t n_holdout;
+    int64_t steps;
+} md_mlp_report;
+
+/* md_mlp_train: draws n_samples of (|E|, z, n_e, T_e) log-uniform over the
+ * domain with Philox, labels them with the library's FP64 plain rate (static
+ * ADK + Lotz), trains the surrogate on the GPU (BF16 forward/backward kernels,
+ * deterministic gradient reduction, Adam) and writes the FP32 parameters to
+ * params_out (host, 5000 floats).  Allocates and frees its own device
+ * buffers.  Synchronous on `stream`. */
+md_status md_mlp_train(const md_mlp_train_config *cfg, float *params_out, md_mlp_report *rep,
+                       void *stream);
+
+/* md_set_rate_mlp: installs surrogate parameters (host, 5000 floats) in the
+ * context; clusters with rate_model MD_RATES_MLP then use it for ions inside
+ * the domain of `domain` and the plain rates outside. */
+md_status md_set_rate_mlp(md_ctx *ctx, const float *params, const md_mlp_train_config *domain);
+
+/* Device-buffer entry points of the surrogate (all pointers device memory):
+ *   md_mlp_forward_device: y[n][8] from features feats[n][4].
+ *   md_mlp_loss_grad_device: loss (mean squared error of y[z]) and its
+ *     gradient grad[5000] for samples feats[n][4], z[n], target[n];
+ *     allocates per-call scratch; synchronous.
+ *   md_mlp_samples_device: the training samples of md_mlp_train (features,
+ *     z, target, and raw[n][3] = |E|, n_e, T_e if raw != NULL).
+ *   md_ion_rates_device: total rate per unit time nu[n] from |E|, z, n_e,
+ *     T_e with model 1 (plain) or 2 (surrogate inside the domain of cfg,
+ *     plain outside; params = device surrogate parameters). */
+md_status md_mlp_forward_device(const float *params, const float *feats, int64_t n, float *y,
+                                void *stream);
+md_status md_mlp_loss_grad_device(const float *params, const float *feats, const int32_t *z,
+                                  const float *target, int64_t n, float *grad, float *loss,
+                                  void *stream);
+md_status md_mlp_samples_device(const md_mlp_train_config *cfg, int64_t n, uint64_t seed,
+                                float *feats, int32_t *z, float *target, double *raw,
+                                void *stream);
+md_status md_ion_rates_device(const md_mlp_train_config *cfg, int32_t model, const float *params,
+                              const double *emag, const int32_t *z, const double *ne,
+                              const double *te, int64_t n, double *nu, void *stream);
+
 /* ---- helpers for SI inputs (Sec. II) ------------------------------------ */
 double md_coulomb_constant(double lambda_um);                  /* K_C = 2 pi r_e / lambda */
 double md_a0_from_intensity(double intensity_wcm2, double lambda_um); /* Eq. 2 */

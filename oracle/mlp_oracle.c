@@ -10,8 +10,12 @@
  *   network   h1 = silu(W1 f + b1)    (64)
  *             h2 = silu(W2 h1 + b2)   (64)
  *             y  = W3 h2 + b3          (8)
- *   output    y_k approximates (log10 max(nu_k, 1e-30) + 15) / 15 for the
- *             transition k -> k+1; the ion of charge z uses y_z.
+ *   output    y_k approximates (log10(nu_k + 1e-12) + 6) / 6 for the
+ *             transition k -> k+1; the ion of charge z uses y_z and
+ *             nu = max(10^(6 y - 6) - 1e-12, 0).  The 1e-12 per unit time
+ *             floor (P < 1e-13 per pass: such rates never ionize) keeps the
+ *             fitted range to 13 decades, and adding it rather than clipping
+ *             keeps the target smooth.
  *   loss      mean over samples of (y_{z_s} - target_s)^2.
  * Parameters, one flat array: W1[64][4], b1[64], W2[64][64], b2[64],
  * W3[8][64], b3[8] (5000 values, rows = outputs).
@@ -41,9 +45,9 @@ void mo_features(double e_mag, int z, double ne, double te, double f[4])
     f[3] = (log10(fmax(te, 0.1)) - 1.5) / 2.5;
 }
 
-double mo_target(double nu) { return (log10(fmax(nu, 1e-30)) + 15.0) / 15.0; }
+double mo_target(double nu) { return (log10(fmax(nu, 0.0) + 1e-12) + 6.0) / 6.0; }
 
-double mo_rate_from_output(double y) { return pow(10.0, 15.0 * y - 15.0); }
+double mo_rate_from_output(double y) { return fmax(pow(10.0, 6.0 * y - 6.0) - 1e-12, 0.0); }
 
 static double silu(double a) { return a / (1.0 + exp(-a)); }
 

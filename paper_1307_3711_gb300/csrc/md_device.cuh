@@ -130,6 +130,81 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
   return c;
 }
 
+// ------------------------------------------------- ionization rates (FP64) --
+// Static ADK tunnelling and Lotz electron-impact rates of Sec. II's ionization
+// paragraph, shared by the ionization pass and the surrogate's training data.
+
+namespace rate {
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kEulerGamma = 0.57721566490153286061;
+constexpr double kHartreeEv = 27.211386245988;
+constexpr double kFieldAu = 5.14220674763e11;   // V/m
+constexpr double kTimeAu = 2.4188843265857e-17;  // s
+constexpr double kMeC2Ev = 510998.95;
+constexpr double kElemCharge = 1.602176634e-19;  // C
+constexpr double kElectronMass = 9.1093837015e-31;  // kg
+constexpr double kLotzA = 4.5e-14;               // cm^2 eV^2
+
+// ---------------------------------------------------------------- rates ---
+
+// E1(x) = int_x^inf e^-t/t dt: power series up to 1, even continued fraction
+// (modified Lentz) beyond.
+__device__ inline double expint_e1(double x) {
+  if (!(x > 0.0)) return __longlong_as_double(0x7ff0000000000000LL);  // +inf
+  if (x <= 1.0) {
+    double sum = 0.0, term = 1.0;
+    for (int k = 1; k < 60; ++k) {
+      term *= -x / k;
+      const double add = -term / k;
+      sum += add;
+      if (fabs(add) < 1e-18 * fabs(sum)) break;
+    }
+    return -kEulerGamma - log(x) + sum;
+  }
+  const double tiny = 1e-300;
+  double b = x + 1.0, c = 1.0 / tiny, d = 1.0 / b, h = d;
+  for (int i = 1; i < 300; ++i) {
+    const double an = -static_cast<double>(i) * i;
+    b += 2.0;
+    d = 1.0 / (an * d + b);
+    c = b + an / c;
+    const double del = c * d;
+    h *= del;
+    if (fabs(del - 1.0) < 1e-16) break;
+  }
+  return h * exp(-x);
+}
+
+// Static ADK rate (a.u.) at field F (a.u.), potential ip (a.u.), residual
+// charge Z: n* = Z/sqrt(2 ip), l* = n* - 1, l = m = 0.
+__device__ inline double adk_rate_au(double F, double ip, double Z) {
+  if (!(F > 0.0)) return 0.0;
+  const double ns = Z / sqrt(2.0 * ip);
+  const double ls = ns - 1.0;
+  const double c2 = pow(2.0, 2.0 * ns) / (ns * tgamma(ns + ls + 1.0) * tgamma(ns - ls));
+  const double f0 = pow(2.0 * ip, 1.5);
+  return c2 * ip * pow(2.0 * f0 / F, 2.0 * ns - 1.0) * exp(-2.0 * f0 / (3.0 * F));
+}
+
+// Lotz rate coefficient (cm^3/s): sqrt(8/(pi m_e)) a q E1(P/T) / (P sqrt(T)).
+__device__ inline double lotz_rate_cgs(double P, double T, double q) {
+  if (!(T > 0.0) || !(q > 0.0)) return 0.0;
+  const double v_th = sqrt(8.0 * kElemCharge / (kPi * kElectronMass)) * 100.0;
+  return v_th * kLotzA * q * expint_e1(P / T) / (P * sqrt(T));
+}
+
+// Total rate per unit time 1/omega of charge state z at |a| (paper units),
+// ne (cm^-3), te (eV).
+__device__ inline double rate_plain(const IonDev& io, double a_mag, int z, double ne, double te) {
+  const double F = a_mag * kMeC2Ev * io.k_si / kFieldAu;
+  const double w_ofi = adk_rate_au(F, io.ip_ev[z] / kHartreeEv, static_cast<double>(z + 1)) /
+                       kTimeAu;
+  const double w_ci = ne > 0.0 ? ne * lotz_rate_cgs(io.ip_ev[z], te, io.q_outer[z]) : 0.0;
+  return (w_ofi + w_ci) / io.omega;
+}
+
+}  // namespace rate
+
 // --------------------------------------------------------------- laser --
 
 // Field-amplitude envelope (Eq. 3 and its readings): 0 Gaussian with

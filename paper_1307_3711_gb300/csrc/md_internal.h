@@ -39,6 +39,9 @@ cudaError_t launch_upload(const UploadArgs& a, cudaStream_t s);
 // Ionization pass of one cluster: field + local moments, then the decision.
 cudaError_t launch_ion_pass(const IonArgs& a, cudaStream_t s);
 
+// Surrogate rates of the ions inside its domain (rate_model 2).
+cudaError_t launch_ion_mlp(const IonArgs& a, cudaStream_t s);
+
 // Records the thread-local message returned by md_last_error() and returns
 // the status (implemented in md_runtime.cu).
 md_status report_error(md_status status, const char* msg);

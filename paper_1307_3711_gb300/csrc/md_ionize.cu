@@ -21,73 +21,8 @@ namespace md {
 
 namespace {
 
-constexpr double kPi = 3.14159265358979323846;
-constexpr double kEulerGamma = 0.57721566490153286061;
-constexpr double kHartreeEv = 27.211386245988;
-constexpr double kFieldAu = 5.14220674763e11;   // V/m
-constexpr double kTimeAu = 2.4188843265857e-17;  // s
-constexpr double kMeC2Ev = 510998.95;
-constexpr double kElemCharge = 1.602176634e-19;  // C
-constexpr double kElectronMass = 9.1093837015e-31;  // kg
-constexpr double kLotzA = 4.5e-14;               // cm^2 eV^2
-
-// ---------------------------------------------------------------- rates ---
-
-// E1(x) = int_x^inf e^-t/t dt: power series up to 1, even continued fraction
-// (modified Lentz) beyond.
-__device__ double expint_e1(double x) {
-  if (!(x > 0.0)) return __longlong_as_double(0x7ff0000000000000LL);  // +inf
-  if (x <= 1.0) {
-    double sum = 0.0, term = 1.0;
-    for (int k = 1; k < 60; ++k) {
-      term *= -x / k;
-      const double add = -term / k;
-      sum += add;
-      if (fabs(add) < 1e-18 * fabs(sum)) break;
-    }
-    return -kEulerGamma - log(x) + sum;
-  }
-  const double tiny = 1e-300;
-  double b = x + 1.0, c = 1.0 / tiny, d = 1.0 / b, h = d;
-  for (int i = 1; i < 300; ++i) {
-    const double an = -static_cast<double>(i) * i;
-    b += 2.0;
-    d = 1.0 / (an * d + b);
-    c = b + an / c;
-    const double del = c * d;
-    h *= del;
-    if (fabs(del - 1.0) < 1e-16) break;
-  }
-  return h * exp(-x);
-}
-
-// Static ADK rate (a.u.) at field F (a.u.), potential ip (a.u.), residual
-// charge Z: n* = Z/sqrt(2 ip), l* = n* - 1, l = m = 0.
-__device__ double adk_rate_au(double F, double ip, double Z) {
-  if (!(F > 0.0)) return 0.0;
-  const double ns = Z / sqrt(2.0 * ip);
-  const double ls = ns - 1.0;
-  const double c2 = pow(2.0, 2.0 * ns) / (ns * tgamma(ns + ls + 1.0) * tgamma(ns - ls));
-  const double f0 = pow(2.0 * ip, 1.5);
-  return c2 * ip * pow(2.0 * f0 / F, 2.0 * ns - 1.0) * exp(-2.0 * f0 / (3.0 * F));
-}
-
-// Lotz rate coefficient (cm^3/s): sqrt(8/(pi m_e)) a q E1(P/T) / (P sqrt(T)).
-__device__ double lotz_rate_cgs(double P, double T, double q) {
-  if (!(T > 0.0) || !(q > 0.0)) return 0.0;
-  const double v_th = sqrt(8.0 * kElemCharge / (kPi * kElectronMass)) * 100.0;
-  return v_th * kLotzA * q * expint_e1(P / T) / (P * sqrt(T));
-}
-
-// Total rate per unit time 1/omega of charge state z at |a| (paper units),
-// ne (cm^-3), te (eV).
-__device__ double rate_plain(const IonDev& io, double a_mag, int z, double ne, double te) {
-  const double F = a_mag * kMeC2Ev * io.k_si / kFieldAu;
-  const double w_ofi = adk_rate_au(F, io.ip_ev[z] / kHartreeEv, static_cast<double>(z + 1)) /
-                       kTimeAu;
-  const double w_ci = ne > 0.0 ? ne * lotz_rate_cgs(io.ip_ev[z], te, io.q_outer[z]) : 0.0;
-  return (w_ofi + w_ci) / io.omega;
-}
+using rate::kMeC2Ev;
+using rate::kPi;
 
 __device__ __forceinline__ bool pass_active(const IonArgs& a, long long step) {
   if (a.ion.rate_model == 0) return false;
@@ -200,18 +135,17 @@ __device__ __forceinline__ double laser_ax(const ClusterDev& c, double t, double
   return amp * sn;
 }
 
-__global__ void __launch_bounds__(256) k_ion_decide(const IonArgs a) {
+// Per ion: total field with the laser at t_n, local density and temperature.
+__global__ void __launch_bounds__(256) k_ion_inputs(const IonArgs a) {
   const long long step = __ldcg(a.step);
   if (!pass_active(a, step)) return;
   const long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= a.ion.n_ions) return;
-  const long long i = a.c.off + t;
   const double* sc = a.scratch + 8 * t;
   const double tn = a.c.t0 + static_cast<double>(step) * a.c.dt;
   double lay;
   const double lax = laser_ax(a.c, tn, &lay);
   const double ex = sc[0] + lax, ey = sc[1] + lay, ez = sc[2];
-  const double emag = sqrt(ex * ex + ey * ey + ez * ez);
   double ne = 0.0, te = 0.0;
   if (sc[3] > 0.0) {
     const double lk = a.ion.r_loc / a.ion.k_si;  // r_loc in metres
@@ -222,14 +156,28 @@ __global__ void __launch_bounds__(256) k_ion_decide(const IonArgs a) {
     te = var > 0.0 ? kMeC2Ev * var / 3.0 : 0.0;
   }
   double* o = a.out + 4 * t;
-  o[0] = emag;
+  o[0] = sqrt(ex * ex + ey * ey + ez * ez);
   o[1] = ne;
   o[2] = te;
   o[3] = 0.0;
+  a.nu[t] = -1.0;
+}
+
+// Per ion: rate (surrogate if it set one, else static ADK + Lotz), P, Philox
+// draw, charge update and electron slot activation.
+__global__ void __launch_bounds__(256) k_ion_decide(const IonArgs a) {
+  const long long step = __ldcg(a.step);
+  if (!pass_active(a, step)) return;
+  const long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= a.ion.n_ions) return;
+  const long long i = a.c.off + t;
+  double* o = a.out + 4 * t;
+  const double emag = o[0], ne = o[1], te = o[2];
   a.fired[t] = 0;
   const int z = a.zq[i];
   if (a.kind[i] != 0 || z < 0 || z >= a.ion.zmax) return;
-  double nu = rate_plain(a.ion, emag, z, ne, te);
+  const double nu_s = a.nu[t];
+  const double nu = nu_s >= 0.0 ? nu_s : rate::rate_plain(a.ion, emag, z, ne, te);
   const double dt_ion = (a.ion.ionize_every > 0 ? a.ion.ionize_every : 1) * a.c.dt;
   const double P = -expm1(-nu * dt_ion);
   o[3] = P;
@@ -283,6 +231,11 @@ cudaError_t launch_ion_pass(const IonArgs& a, cudaStream_t s) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const unsigned g2 = static_cast<unsigned>((a.ion.n_ions + 255) / 256);
+  k_ion_inputs<<<g2, 256, 0, s>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (a.ion.rate_model == 2 && a.mlp) {
+    if ((e = launch_ion_mlp(a, s)) != cudaSuccess) return e;
+  }
   k_ion_decide<<<g2, 256, 0, s>>>(a);
   return cudaGetLastError();
 }

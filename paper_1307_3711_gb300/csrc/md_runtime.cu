@@ -109,7 +109,8 @@ struct md_ctx {
   double* d_ion_scratch = nullptr;     // [max n_ions][8]
   double* d_ion_out = nullptr;         // [sum n_ions][4]
   unsigned char* d_ion_fired = nullptr;
-  const float* d_mlp = nullptr;        // surrogate weights (device), if set
+  double* d_ion_nu = nullptr;          // [sum n_ions] surrogate rates (-1: plain)
+  float* d_mlp = nullptr;              // surrogate parameters (device), if set
 };
 
 namespace {
@@ -416,6 +417,7 @@ md::IonArgs ion_args(md_ctx* c, int ci, int force) {
   a.scratch = c->d_ion_scratch;
   a.out = c->d_ion_out + 4 * c->ion_out_off[ci];
   a.fired = c->d_ion_fired + c->ion_out_off[ci];
+  a.nu = c->d_ion_nu + c->ion_out_off[ci];
   a.mlp = c->d_mlp;
   return a;
 }
@@ -501,6 +503,8 @@ void free_ctx(md_ctx* c) {
   cudaFree(c->d_ion_scratch);
   cudaFree(c->d_ion_out);
   cudaFree(c->d_ion_fired);
+  cudaFree(c->d_ion_nu);
+  cudaFree(c->d_mlp);
   if (c->h_raw) cudaFreeHost(c->h_raw);
   if (c->h_diag) cudaFreeHost(c->h_diag);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -709,7 +713,8 @@ md_status md_init(md_ctx** out, const md_config* cfgs, int32_t n_clusters,
     }
     if (dev_alloc(&c->d_ion_scratch, 8 * static_cast<size_t>(max_ion)) != cudaSuccess ||
         dev_alloc(&c->d_ion_out, 4 * static_cast<size_t>(sum_ion)) != cudaSuccess ||
-        dev_alloc(&c->d_ion_fired, static_cast<size_t>(sum_ion)) != cudaSuccess)
+        dev_alloc(&c->d_ion_fired, static_cast<size_t>(sum_ion)) != cudaSuccess ||
+        dev_alloc(&c->d_ion_nu, static_cast<size_t>(sum_ion)) != cudaSuccess)
       return bail(fail(MD_ERR_OOM, "ionization buffers"));
     cudaMemsetAsync(c->d_ion_out, 0, sizeof(double) * 4 * sum_ion, c->stream);
     cudaMemsetAsync(c->d_ion_fired, 0, sum_ion, c->stream);
@@ -775,6 +780,29 @@ md_status md_ionize(md_ctx* c) {
   if (!c->any_ion) return MD_OK;
   cudaError_t e = launch_ion_all(c, 1, c->stream);
   if (e != cudaSuccess) return cuda_fail(e, "ionization launch");
+  return MD_OK;
+}
+
+md_status md_set_rate_mlp(md_ctx* c, const float* params, const md_mlp_train_config* domain) {
+  if (!c || !params || !domain) return fail(MD_ERR_ARG, "NULL argument");
+  if (!(domain->e_min > 0.0 && domain->e_max > domain->e_min && domain->ne_min > 0.0 &&
+        domain->ne_max > domain->ne_min && domain->te_min > 0.0 &&
+        domain->te_max > domain->te_min))
+    return fail(MD_ERR_ARG, "bad surrogate domain");
+  for (int ci = 0; ci < c->n_clusters; ++ci)
+    if (c->ion[ci].rate_model == 2 && c->ion[ci].zmax > 8)
+      return fail(MD_ERR_ARG, "cluster %d: the surrogate has 8 outputs (zmax <= 8)", ci);
+  MD_CUDA(cudaStreamSynchronize(c->stream));
+  if (!c->d_mlp) MD_CUDA(dev_alloc(&c->d_mlp, 5000));
+  MD_CUDA(cudaMemcpyAsync(c->d_mlp, params, sizeof(float) * 5000, cudaMemcpyHostToDevice,
+                          c->stream));
+  MD_CUDA(cudaStreamSynchronize(c->stream));
+  for (auto& io : c->ion) {
+    io.dom[0] = domain->e_min; io.dom[1] = domain->e_max;
+    io.dom[2] = domain->ne_min; io.dom[3] = domain->ne_max;
+    io.dom[4] = domain->te_min; io.dom[5] = domain->te_max;
+  }
+  destroy_graph(c);  // kernel arguments changed
   return MD_OK;
 }
 

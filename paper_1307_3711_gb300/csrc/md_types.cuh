@@ -38,6 +38,7 @@ struct IonDev {
   double omega;       // laser angular frequency, rad/s
   double ip_ev[kMaxZ];
   double q_outer[kMaxZ];
+  double dom[6];      // surrogate domain: |E| min/max, n_e min/max, T_e min/max
 };
 
 struct Unit {
@@ -92,6 +93,7 @@ struct IonArgs {
   int force;          // 1: run regardless of ionize_every
   double* scratch;    // [n_ions][8]: ex, ey, ez, sw, swux, swuy, swuz, swu2
   double* out;        // [n_ions][4]: |E|, ne (cm^-3), Te (eV), P
+  double* nu;         // [n_ions]: rate from the surrogate, or -1 (use the plain rate)
   unsigned char* fired;  // [n_ions]
   const float* mlp;   // surrogate weights (rate_model 2) or nullptr
 };

@@ -67,6 +67,22 @@ class Tuning(C.Structure):
                 self.min_blocks)
 
 
+class MlpTrainConfig(C.Structure):
+    _fields_ = [("ip_ev", C.c_double * 16), ("q_outer", C.c_double * 16), ("zmax", C.c_int32),
+                ("epochs", C.c_int32), ("lambda_um", C.c_double), ("n_samples", C.c_int64),
+                ("batch", C.c_int32), ("reserved", C.c_int32), ("lr", C.c_double),
+                ("seed", C.c_uint64), ("e_min", C.c_double), ("e_max", C.c_double),
+                ("ne_min", C.c_double), ("ne_max", C.c_double), ("te_min", C.c_double),
+                ("te_max", C.c_double)]
+
+
+class MlpReport(C.Structure):
+    _fields_ = [("loss_first", C.c_double), ("loss_last", C.c_double),
+                ("holdout_median_dlog10", C.c_double), ("holdout_p99_dlog10", C.c_double),
+                ("holdout_max_dlog10", C.c_double), ("train_ms", C.c_double),
+                ("n_holdout", C.c_int64), ("steps", C.c_int64)]
+
+
 _ctx_p = C.c_void_p
 _st = C.c_int
 _p = C.c_void_p
@@ -91,6 +107,14 @@ _SIGS = {
                                       _p, _p]),
     "md_coulomb_field_device_noalloc": (_st, [_p, C.c_int64, _p, C.c_int64, C.c_float, C.c_int64,
                                               _p, _p, _p]),
+    "md_mlp_train": (_st, [C.POINTER(MlpTrainConfig), _p, C.POINTER(MlpReport), _p]),
+    "md_set_rate_mlp": (_st, [_ctx_p, _p, C.POINTER(MlpTrainConfig)]),
+    "md_mlp_forward_device": (_st, [_p, _p, C.c_int64, _p, _p]),
+    "md_mlp_loss_grad_device": (_st, [_p, _p, _p, _p, C.c_int64, _p, _p, _p]),
+    "md_mlp_samples_device": (_st, [C.POINTER(MlpTrainConfig), C.c_int64, C.c_uint64, _p, _p, _p,
+                                    _p, _p]),
+    "md_ion_rates_device": (_st, [C.POINTER(MlpTrainConfig), C.c_int32, _p, _p, _p, _p, _p,
+                                  C.c_int64, _p, _p]),
     "md_coulomb_constant": (C.c_double, [C.c_double]),
     "md_a0_from_intensity": (C.c_double, [C.c_double, C.c_double]),
     "md_n_atoms": (C.c_double, [C.c_double, C.c_double]),
@@ -290,6 +314,11 @@ class Context:
                                       _ptr(prob), _ptr(fired)))
         return {"emag": emag, "ne": ne, "te": te, "prob": prob, "fired": fired}
 
+    def set_rate_mlp(self, params, domain: "MlpTrainConfig"):
+        w = np.ascontiguousarray(params, dtype=np.float32)
+        assert w.size == 5000
+        _check(_lib.md_set_rate_mlp(self._h, _ptr(w), C.byref(domain)))
+
     def tuning(self):
         t = Tuning()
         _check(_lib.md_get_tuning(self._h, C.byref(t)))
@@ -326,3 +355,59 @@ def coulomb_field_device_noalloc(src_ptr: int, ns: int, tgt_ptr: int, nt: int, e
         C.c_void_p(src_ptr), int(ns), C.c_void_p(tgt_ptr), int(nt), float(eps2),
         int(self_offset), C.c_void_p(e_ptr), C.c_void_p(phi_ptr) if phi_ptr else None,
         C.c_void_p(stream) if stream else None))
+
+
+# ---------------------------------------------------------- rate surrogate --
+
+def mlp_train_config(species, zmax=8, n_samples=1 << 20, epochs=8, batch=8192, lr=3e-3,
+                     seed=1, lambda_um=0.8, e_range=(1e-3, 1.0), ne_range=(1e15, 1e24),
+                     te_range=(0.1, 1e4)) -> MlpTrainConfig:
+    c = MlpTrainConfig()
+    for k, v in enumerate(species["ip_ev"]):
+        c.ip_ev[k] = v
+    for k, v in enumerate(species["q_outer"]):
+        c.q_outer[k] = v
+    c.zmax, c.epochs, c.lambda_um, c.n_samples = zmax, epochs, lambda_um, n_samples
+    c.batch, c.reserved, c.lr, c.seed = batch, 0, lr, seed
+    c.e_min, c.e_max = e_range
+    c.ne_min, c.ne_max = ne_range
+    c.te_min, c.te_max = te_range
+    return c
+
+
+def mlp_train(cfg: MlpTrainConfig, stream=None):
+    """Train the surrogate on the GPU; returns (params float32[5000], report dict)."""
+    out = np.zeros(5000, np.float32)
+    rep = MlpReport()
+    _check(_lib.md_mlp_train(C.byref(cfg), _ptr(out), C.byref(rep),
+                             C.c_void_p(stream) if stream else None))
+    return out, {k: getattr(rep, k) for k, _ in MlpReport._fields_}
+
+
+def _vp(x):
+    return C.c_void_p(x) if x else None
+
+
+def mlp_forward_device(params_ptr, feats_ptr, n, y_ptr, stream=None):
+    _check(_lib.md_mlp_forward_device(_vp(params_ptr), _vp(feats_ptr), int(n), _vp(y_ptr),
+                                      _vp(stream)))
+
+
+def mlp_loss_grad_device(params_ptr, feats_ptr, z_ptr, target_ptr, n, grad_ptr, loss_ptr,
+                         stream=None):
+    _check(_lib.md_mlp_loss_grad_device(_vp(params_ptr), _vp(feats_ptr), _vp(z_ptr),
+                                        _vp(target_ptr), int(n), _vp(grad_ptr), _vp(loss_ptr),
+                                        _vp(stream)))
+
+
+def mlp_samples_device(cfg, n, seed, feats_ptr, z_ptr, target_ptr, raw_ptr=None, stream=None):
+    _check(_lib.md_mlp_samples_device(C.byref(cfg), int(n), int(seed) & (2 ** 64 - 1),
+                                      _vp(feats_ptr), _vp(z_ptr), _vp(target_ptr), _vp(raw_ptr),
+                                      _vp(stream)))
+
+
+def ion_rates_device(cfg, model, params_ptr, emag_ptr, z_ptr, ne_ptr, te_ptr, n, nu_ptr,
+                     stream=None):
+    _check(_lib.md_ion_rates_device(C.byref(cfg), int(model), _vp(params_ptr), _vp(emag_ptr),
+                                    _vp(z_ptr), _vp(ne_ptr), _vp(te_ptr), int(n), _vp(nu_ptr),
+                                    _vp(stream)))
