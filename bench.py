@@ -37,6 +37,14 @@ UNIT = "pair/s"
 RECORD_BYTES = 3 * 8 + 3 * 8 + 4 + 8 + 8 + 1   # x, u, z, mass, w, kind per record
 FP32_INSTR_PER_PAIR = 12
 L2_FLUSH_BYTES = 512 << 20
+WORKLOAD_TEXT = {
+    "xe3_200k": "{name}: N={n} (Xe3+ ions + electrons, 10 eV), one cluster per GPU",
+    "scan256": "parameter scan of {clusters} clusters (N log-uniform 1k-50k, Z 1-8, R0 1-8 nm, "
+               "a0 0.01-0.3, 20-200 fs), {n} records in one persistent launch per step",
+    "precision_1m": "{name}: N={n}, laser off",
+    "ar_ionize": "{name}: N={n} records (neutral Ar atoms + 8 electron slots each), plain "
+                 "ADK + Lotz ionization before every step",
+}
 
 
 def parse_args():
@@ -53,6 +61,11 @@ def parse_args():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tuning", default=None,
                     help="force a kernel configuration: threads,r,tile,packed[,jsplit[,min_blocks]]")
+    ap.add_argument("--workload", default="xe3_200k",
+                    choices=["xe3_200k", "scan256", "precision_1m", "ar_ionize"],
+                    help="xe3_200k: the headline N=200k cluster; scan256: 256 clusters of a "
+                         "parameter scan in one persistent launch; precision_1m: 500k Ar+ + 500k "
+                         "e, laser off; ar_ionize: neutral Ar atoms ionizing (plain rates)")
     return ap.parse_args()
 
 
@@ -164,13 +177,15 @@ def workload(n: int, seed: int):
     return w
 
 
-def cpu_oracle_rate(w, seconds: float, seed: int = 0):
+def cpu_oracle_rate(w, seconds: float, seed: int = 0, e_gpu=None):
     """The FP64 oracle's direct sum (OpenMP over targets, all host cores) on
-    sampled targets of the workload, sized to about `seconds` of CPU time."""
+    sampled targets of the workload, sized to about `seconds` of CPU time.
+    With e_gpu (the GPU field of the same state) it also returns the floored
+    relative field error |E - E64| / max(|E64|, rms |E64|) at those targets."""
     import oracle
     c = w.cluster
     kc = oracle.coulomb_constant(w.lambda_um)
-    q = c.w * c.z
+    q = c.w * c.z * c.active
     threads = os.cpu_count() or 1
     rng = np.random.default_rng(seed)
     nt = 256
@@ -183,12 +198,61 @@ def cpu_oracle_rate(w, seconds: float, seed: int = 0):
             break
         nt = min(c.n, nt * 4)
     nt = int(min(c.n, max(64, nt * seconds / max(dt, 1e-6))))
-    idx = rng.choice(c.n, nt, replace=False)
+    idx = np.sort(rng.choice(c.n, nt, replace=False))
     t0 = time.perf_counter()
-    oracle.coulomb_field(c.x[idx], c.x, q, w.eps, kc, self_idx=idx, nthreads=threads)
+    e64 = oracle.coulomb_field(c.x[idx], c.x, q, w.eps, kc, self_idx=idx, nthreads=threads)
     dt = time.perf_counter() - t0
     pairs = nt * c.n
-    return pairs / dt, threads, nt, dt
+    err = None
+    if e_gpu is not None:
+        live = c.active[idx] > 0
+        nrm = np.linalg.norm(e64[live], axis=1)
+        rel = np.linalg.norm(e_gpu[idx][live] - e64[live], axis=1) / np.maximum(
+            nrm, np.sqrt(np.mean(nrm ** 2)))
+        err = {"median": float(np.median(rel)), "p99": float(np.percentile(rel, 99)),
+               "max": float(rel.max()), "n_targets": int(live.sum()),
+               "metric": "|E - E_fp64| / max(|E_fp64|, rms|E_fp64|) at sampled targets, "
+                         "GPU FP32/Kahan sum vs FP64 oracle, initial state"}
+    return pairs / dt, threads, nt, dt, err
+
+
+def build_contexts(md, args, rank, stream):
+    """The workload's clusters -> (context, list of workloads, pairs per step)."""
+    if args.workload == "scan256":
+        scan = synth.batched_scan(256, seed=rank)
+        cfgs, parts, ws = [], [], []
+        for e in scan:
+            cl = synth.scan_cluster(e)
+            w = synth.Workload(f"scan_{e.seed}", cl, a0=e.a0, pol=0, env=synth.ENV_SIN2, tau=e.tau,
+                               eps=synth.nm_to_len(0.1), dt=0.02, nsteps=0)
+            ws.append(w)
+            cfgs.append(md.config_from_workload(w))
+            parts.append(md.HostParticles.from_cluster(cl))
+        pairs = float(sum(float(w.cluster.n) ** 2 for w in ws))
+        return md.Context(cfgs, parts, stream=stream), ws, pairs
+    if args.workload == "precision_1m":
+        w = synth.precision_1m(seed=rank, a0=0.0)
+    elif args.workload == "ar_ionize":
+        n = args.n if args.n != 200000 else 20000
+        c = synth.make_cluster(rank, n, 0, synth.nm_to_len(8.0 * (n / 200000) ** (1 / 3)), 0,
+                               synth.ARGON["mass"], n_electron_slots=8 * n)
+        rw = synth.nm_to_len(synth.ARGON["r_w_nm"])
+        w = synth.Workload(f"ar{n // 1000}k_ionize", c, a0=0.0617, pol=0, env=synth.ENV_SIN2,
+                           tau=synth.sin2_length_from_fwhm(synth.fs_to_time(100.0, 0.806), ),
+                           eps=synth.nm_to_len(0.1), dt=0.02, nsteps=0, lambda_um=0.806)
+        cfg = md.config_from_workload(w)
+        ion = md.make_config(rate_model=md.RATES_PLAIN, ionize_every=1, zmax=8, n_ions=n,
+                             slot_base=n, seed=rank + 1, r_loc=3 * rw, r_create=rw,
+                             species=synth.ARGON)
+        for f in ("rate_model", "ionize_every", "zmax", "n_ions", "slot_base", "seed", "r_loc",
+                  "r_create", "ip_ev", "q_outer"):
+            setattr(cfg, f, getattr(ion, f))
+        return (md.Context([cfg], [md.HostParticles.from_cluster(c)], stream=stream), [w],
+                float(c.n) ** 2)
+    else:
+        w = workload(args.n, seed=rank)
+    return (md.Context([md.config_from_workload(w)], [md.HostParticles.from_cluster(w.cluster)],
+                       stream=stream), [w], float(w.cluster.n) ** 2)
 
 
 # --------------------------------------------------------------- native --
@@ -206,11 +270,12 @@ def run_native(args):
     # one non-default stream shared by torch (events, L2 flush) and the library
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    w = workload(args.n, seed=rank)
-    n = w.cluster.n
-    pairs_per_step = float(n) * float(n)
-    host = md.HostParticles.from_cluster(w.cluster)
-    ctx = md.Context([md.config_from_workload(w)], [host], stream=stream.cuda_stream)
+    ctx, ws, pairs_per_step = build_contexts(md, args, rank, stream.cuda_stream)
+    w = ws[0]
+    n = sum(x.cluster.n for x in ws)
+    # FP32/Kahan field of the initial state, compared with the FP64 oracle in
+    # the CPU-baseline leg below
+    e_gpu0 = ctx.fields(0) if len(ws) == 1 else None
     sms, gpu_name = md.device_info()
 
     tune_ms = None
@@ -260,35 +325,48 @@ def run_native(args):
     peak_max = 128.0 * sms * 2070e6 / FP32_INSTR_PER_PAIR
 
     # end to end through the C ABI with host buffers: upload, step, download
-    pinned = {}
-    for k in ("x", "u", "z", "mass", "w", "kind"):
-        a = getattr(host, k)
-        t = torch.empty(a.shape, dtype=getattr(torch, str(a.dtype)), pin_memory=True)
-        t.numpy()[...] = a
-        pinned[k] = t
-    hp = md.HostParticles(*(pinned[k].numpy() for k in ("x", "u", "z", "mass", "w", "kind")))
+    hps = []
+    for x in ws:
+        hx = md.HostParticles.from_cluster(x.cluster)
+        pinned = {}
+        for k in ("x", "u", "z", "mass", "w", "kind"):
+            a = getattr(hx, k)
+            t = torch.empty(a.shape, dtype=getattr(torch, str(a.dtype)), pin_memory=True)
+            t.numpy()[...] = a
+            pinned[k] = t
+        hps.append(md.HostParticles(*(pinned[k].numpy()
+                                      for k in ("x", "u", "z", "mass", "w", "kind"))))
     e2e_t = []
-    for s in range(args.e2e_steps + 1):
+    for s_ in range(args.e2e_steps + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ctx.set_particles(0, hp)
+        for k, hp in enumerate(hps):
+            ctx.set_particles(k, hp)
         ctx.step(1)
-        ctx.get_particles(0, out=hp)
+        for k, hp in enumerate(hps):
+            ctx.get_particles(k, out=hp)
         t1 = time.perf_counter()
-        if s > 0:
+        if s_ > 0:
             e2e_t.append(t1 - t0)
     e2e_local = float(np.mean(e2e_t))
     e2e_max = dist.max(e2e_local)
     e2e_value = world * pairs_per_step / e2e_max
 
     cpu = None
+    force_err = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, threads, nt, secs = cpu_oracle_rate(w, args.cpu_seconds)
+        rate, threads, nt, secs, force_err = cpu_oracle_rate(w, args.cpu_seconds, e_gpu=e_gpu0)
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"FP64 field at {nt} sampled targets from all {n} sources "
-                         f"({nt * n:.3g} pairs, {secs:.1f} s, OpenMP over targets)",
-               "steps_per_s": rate / pairs_per_step}
+               "sample": f"FP64 field at {nt} sampled targets from all {w.cluster.n} sources "
+                         f"({nt * w.cluster.n:.3g} pairs, {secs:.1f} s, OpenMP over targets)",
+               "steps_per_s": rate / (float(w.cluster.n) ** 2)}
 
+    launches_per_step = 1 + (4 if args.workload == "ar_ionize" else 0)
+    ion_state = None
+    if args.workload == "ar_ionize":
+        d = ctx.diagnostics(0)
+        ion_state = {"charge_fractions": (d["charge_count"][:9] / w.cluster.n_ions).tolist(),
+                     "active_records": int(d["n_active"])}
     ctx.close()
     dist.close()
     if rank != 0:
@@ -308,8 +386,9 @@ def run_native(args):
         "dtype": "f32",
         "data": "synthetic",
         "config": {
-            "workload": f"{w.name}: N={n} (Xe3+ ions + electrons, 10 eV), one cluster per GPU",
-            "n_particles": n, "pairs_per_step": pairs_per_step,
+            "workload": WORKLOAD_TEXT[args.workload].format(name=w.name, n=n,
+                                                            clusters=len(ws)),
+            "n_particles": n, "pairs_per_step": pairs_per_step, "ionization": ion_state,
             "softening_nm": 0.1, "dt": w.dt, "a0": w.a0, "envelope": "sin2, 100 fs FWHM",
             "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write outside the "
                   "timed events)",
@@ -337,11 +416,12 @@ def run_native(args):
         },
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": RECORD_BYTES * n,
-                "d2h_bytes_per_step": RECORD_BYTES * n,
+                "d2h_bytes_per_step": RECORD_BYTES * n, "wall_s_per_step": e2e_max,
                 "what": "md_set_particles + md_step(1) + md_get_particles from pinned host "
                         "arrays, wall clock"},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * launches_per_step,
         "cpu_baseline": cpu,
+        "force_err_vs_fp64": force_err,
     }
     print(json.dumps(line), flush=True)
 

@@ -218,6 +218,18 @@ md_status md_ionize(md_ctx *ctx);
 md_status md_get_ionization(md_ctx *ctx, int32_t cluster, double *emag, double *ne, double *te,
                             double *prob, uint8_t *fired);
 
+/* md_set_step: sets the step counter (with md_set_particles, a checkpoint is
+ * restored exactly: the laser time and the Philox counters derive from the
+ * step).  Synchronous. */
+md_status md_set_step(md_ctx *ctx, int64_t step);
+
+/* md_wait_selftest: exercises the bounded device waits.  One CTA waits on an
+ * mbarrier phase that nothing completes; after budget_ms (0 < budget_ms <=
+ * 5000, converted with the nominal SM clock) the wait gives up, the kernel
+ * sets the context's error word and returns.  Returns MD_ERR_TIMEOUT (the
+ * expected outcome) and leaves the context usable. */
+md_status md_wait_selftest(md_ctx *ctx, double budget_ms);
+
 /* Step counter of the context (steps taken since md_init). Synchronous. */
 md_status md_get_step(md_ctx *ctx, int64_t *step);
 

@@ -80,12 +80,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait for phase `parity` of `bar`: false after kWaitBudget cycles.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait for phase `parity` of `bar`: false after `budget` cycles.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          long long budget = kWaitBudget) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > kWaitBudget) return false;
+    if (clock64() - t0 > budget) return false;
   }
   return true;
 }
@@ -353,6 +354,14 @@ __device__ __forceinline__ void issue_tile(Stage<TILE, STAGES>& sm, unsigned g, 
   bulk_g2s(&sm.tile[s][0], src + j0, cnt * 16u, &sm.full[s]);
 }
 
+// Whether any record in [r0, r1] lies in a live group (no flags: all live).
+__device__ __forceinline__ bool any_live(const unsigned char* live, long long r0, long long r1) {
+  if (!live) return true;
+  for (long long g = r0 / kLiveGroup; g <= r1 / kLiveGroup; ++g)
+    if (live[g]) return true;
+  return false;
+}
+
 // Sum over all ns sources for the R targets held by this thread, streaming the
 // sources through the STAGES-deep TMA ring.  `it` counts tiles this CTA has
 // consumed so far (sets the barrier phases).  Returns false (uniformly across
@@ -363,7 +372,9 @@ __device__ __forceinline__ bool sum_sources(Stage<TILE, STAGES>& sm, unsigned& i
                                             const float4* __restrict__ src, long long ns,
                                             const float (&xi)[R], const float (&yi)[R],
                                             const float (&zi)[R], float eps2, Acc<R, POT>& acc,
-                                            int* err, int* s_abort) {
+                                            int* err, int* s_abort,
+                                            const unsigned char* live = nullptr,
+                                            long long gbase = 0) {
   const int ntiles = static_cast<int>((ns + TILE - 1) / TILE);
   if (threadIdx.x == 0) {
     for (int k = 0; k < STAGES && k < ntiles; ++k) issue_tile<TILE, STAGES>(sm, it + k, src, ns, k);
@@ -376,7 +387,11 @@ __device__ __forceinline__ bool sum_sources(Stage<TILE, STAGES>& sm, unsigned& i
       atomicOr(err, kErrTimeout);
       *s_abort = 1;
     }
-    if (!*reinterpret_cast<volatile int*>(s_abort)) {
+    const long long rem0 = ns - static_cast<long long>(t) * TILE;
+    const bool tile_live = any_live(live, gbase + static_cast<long long>(t) * TILE,
+                                    gbase + static_cast<long long>(t) * TILE +
+                                        (rem0 < TILE ? rem0 : TILE) - 1);
+    if (tile_live && !*reinterpret_cast<volatile int*>(s_abort)) {
       const uint32_t tile = smem_u32(&sm.tile[s][0]);
       const long long rem = ns - static_cast<long long>(t) * TILE;
       const int cnt = static_cast<int>(rem < TILE ? rem : TILE);
@@ -526,7 +541,9 @@ __device__ __forceinline__ bool sum_sources_packed(Stage<TILE, STAGES>& sm, DupT
                                                    const float4* __restrict__ src, long long ns,
                                                    const float (&xi)[R], const float (&yi)[R],
                                                    const float (&zi)[R], float eps2, int* err,
-                                                   int* s_abort) {
+                                                   int* s_abort,
+                                                   const unsigned char* live = nullptr,
+                                                   long long gbase = 0) {
   static_assert(R % 2 == 0, "packed path needs an even number of i-particles per thread");
   constexpr int P = R / 2;
   const int tid = threadIdx.x;
@@ -556,7 +573,9 @@ __device__ __forceinline__ bool sum_sources_packed(Stage<TILE, STAGES>& sm, DupT
     }
     const long long rem = ns - static_cast<long long>(t) * TILE;
     const int cnt = static_cast<int>(rem < TILE ? rem : TILE);
-    if (!*reinterpret_cast<volatile int*>(s_abort)) {
+    const bool tile_live = any_live(live, gbase + static_cast<long long>(t) * TILE,
+                                    gbase + static_cast<long long>(t) * TILE + cnt - 1);
+    if (tile_live && !*reinterpret_cast<volatile int*>(s_abort)) {
       for (int k = tid; k < cnt; k += THREADS) {
         const float4 p = sm.tile[s][k];
         dup.v[k][0] = make_ulonglong2(f2_pack(p.x, p.x), f2_pack(p.y, p.y));
@@ -578,6 +597,10 @@ __device__ __forceinline__ bool sum_sources_packed(Stage<TILE, STAGES>& sm, DupT
     // the stage is expanded into dup: refill it while this tile is summed
     if (tid == 0 && t + STAGES < ntiles)
       issue_tile<TILE, STAGES>(sm, it + t + STAGES, src, ns, t + STAGES);
+    if (!tile_live) {
+      __syncthreads();
+      continue;
+    }
     const uint32_t dbase = smem_u32(&dup.v[0][0]);
     int j = 0;
     for (; j + 8 <= cnt; j += 8) {
@@ -700,7 +723,11 @@ __global__ void __launch_bounds__(THREADS, MINB) k_step(const StepArgs a) {
     }
     __syncthreads();
     if (s_unit >= a.n_units) break;
-    {
+    if (any_live(a.tgt_live, s_c.off + static_cast<long long>(s_un.block) * (THREADS * R),
+                 (s_c.off + static_cast<long long>(s_un.block + 1) * (THREADS * R) <
+                          s_c.off + s_c.n_pad
+                      ? s_c.off + static_cast<long long>(s_un.block + 1) * (THREADS * R)
+                      : s_c.off + s_c.n_pad) - 1)) {
       const float4* __restrict__ cur = (step & 1) ? a.posq1 : a.posq0;
       const long long i0 = s_c.off + static_cast<long long>(s_un.block) * (THREADS * R);
       const long long iend = s_c.off + s_c.n_pad;
@@ -720,11 +747,13 @@ __global__ void __launch_bounds__(THREADS, MINB) k_step(const StepArgs a) {
       Acc<R, false> acc;
       if constexpr (PACK) {
         ok = sum_sources_packed<THREADS, R, TILE, STAGES, false>(
-            sm, dup, ks, it, cur + s_c.off + j0, jn, xi, yi, zi, s_c.eps2, a.err, &s_abort);
+            sm, dup, ks, it, cur + s_c.off + j0, jn, xi, yi, zi, s_c.eps2, a.err, &s_abort,
+            a.src_live, s_c.off + j0);
       } else {
         acc.zero();
         ok = sum_sources<THREADS, R, TILE, STAGES, false>(sm, it, cur + s_c.off + j0, jn, xi, yi,
-                                                          zi, s_c.eps2, acc, a.err, &s_abort);
+                                                          zi, s_c.eps2, acc, a.err, &s_abort,
+                                                          a.src_live, s_c.off + j0);
       }
       if (!ok) return;
 

@@ -36,8 +36,16 @@ cudaError_t launch_ffma_probe(int blocks, int iters, bool packed, float* sink, c
 
 cudaError_t launch_upload(const UploadArgs& a, cudaStream_t s);
 
+// Launches one CTA whose mbarrier wait can never complete (bounded by budget).
+cudaError_t launch_wait_selftest(long long budget, int* err, cudaStream_t s);
+
 // Ionization pass of one cluster: field + local moments, then the decision.
 cudaError_t launch_ion_pass(const IonArgs& a, cudaStream_t s);
+
+// Liveness flags of all records (contexts with ionization).
+cudaError_t launch_live_init(const float4* posq0, const float4* posq1, const unsigned char* kind,
+                             const long long* step, long long n_total, unsigned char* src_live,
+                             unsigned char* tgt_live, cudaStream_t s);
 
 // Surrogate rates of the ions inside its domain (rate_model 2).
 cudaError_t launch_ion_mlp(const IonArgs& a, cudaStream_t s);

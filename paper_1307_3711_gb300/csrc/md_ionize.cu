@@ -73,10 +73,12 @@ __global__ void __launch_bounds__(THREADS) k_ion_field(const IonArgs a) {
       atomicOr(a.err, kErrTimeout);
       s_abort = 1;
     }
-    if (!*reinterpret_cast<volatile int*>(&s_abort)) {
-      const long long jb = static_cast<long long>(t) * TILE;
-      const long long rem = ns - jb;
-      const int cnt = static_cast<int>(rem < TILE ? rem : TILE);
+    const long long jb = static_cast<long long>(t) * TILE;
+    const long long rem = ns - jb;
+    const int cnt = static_cast<int>(rem < TILE ? rem : TILE);
+    if (any_live(a.src_live, a.c.off + jb, a.c.off + jb + cnt - 1) &&
+        !*reinterpret_cast<volatile int*>(&s_abort)) {
+#pragma unroll 4
       for (int j = 0; j < cnt; ++j) {
         const float4 p = sm.tile[s][j];
 #pragma unroll
@@ -194,6 +196,7 @@ __global__ void __launch_bounds__(256) k_ion_decide(const IonArgs a) {
   a.zq[i] = z1;
   a.qm[i] = static_cast<float>(z1 / a.mass[i]);
   cur[i].w = static_cast<float>(kc_w * z1);
+  if (a.src_live) a.src_live[i / kLiveGroup] = 1;
   // the freed electron: uniform in the ball of radius r_create around the ion
   const double u1 = (static_cast<double>(wv.y) + 0.5) * (1.0 / 4294967296.0);
   const double u2 = (static_cast<double>(wv.z) + 0.5) * (1.0 / 4294967296.0);
@@ -215,13 +218,46 @@ __global__ void __launch_bounds__(256) k_ion_decide(const IonArgs a) {
   a.kind[e] = 1;
   cur[e] = make_float4(static_cast<float>(X), static_cast<float>(Y), static_cast<float>(Z),
                        static_cast<float>(-kc_w));
+  if (a.src_live) {
+    a.src_live[e / kLiveGroup] = 1;
+    a.tgt_live[e / kLiveGroup] = 1;
+  }
 }
 
-constexpr int kIonThreads = 128;
-constexpr int kIonR = 2;
+// Liveness flags from the current records: a group of kLiveGroup records is
+// a live source if one of them carries charge, a live target if one of them
+// is not INACTIVE.
+__global__ void k_live_init(const float4* posq0, const float4* posq1, const unsigned char* kind,
+                            const long long* step, long long n_total, unsigned char* src_live,
+                            unsigned char* tgt_live) {
+  const long long g = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const long long r0 = g * kLiveGroup;
+  if (r0 >= n_total) return;
+  const float4* cur = (__ldcg(step) & 1) ? posq1 : posq0;
+  const long long r1 = r0 + kLiveGroup < n_total ? r0 + kLiveGroup : n_total;
+  unsigned char s = 0, t = 0;
+  for (long long r = r0; r < r1; ++r) {
+    if (cur[r].w != 0.0f) s = 1;
+    if (kind[r] != 2) t = 1;
+  }
+  src_live[g] = s;
+  tgt_live[g] = t;
+}
+
+constexpr int kIonThreads = 64;
+constexpr int kIonR = 1;
 constexpr int kIonTile = 512;
 
 }  // namespace
+
+cudaError_t launch_live_init(const float4* posq0, const float4* posq1, const unsigned char* kind,
+                             const long long* step, long long n_total, unsigned char* src_live,
+                             unsigned char* tgt_live, cudaStream_t s) {
+  const long long groups = (n_total + kLiveGroup - 1) / kLiveGroup;
+  k_live_init<<<static_cast<unsigned>((groups + 255) / 256), 256, 0, s>>>(
+      posq0, posq1, kind, step, n_total, src_live, tgt_live);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_ion_pass(const IonArgs& a, cudaStream_t s) {
   if (a.ion.n_ions <= 0) return cudaSuccess;

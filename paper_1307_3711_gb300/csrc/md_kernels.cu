@@ -188,6 +188,26 @@ cudaError_t launch_ffma_probe(int blocks, int iters, bool packed, float* sink, c
   return cudaGetLastError();
 }
 
+// Self-test of the bounded waits: one CTA waits on an mbarrier phase that no
+// arrival or copy ever completes; the wait gives up after `budget` cycles,
+// sets the timeout bit in *err and the kernel returns normally.
+__global__ void k_wait_selftest(long long budget, int* err) {
+  __shared__ alignas(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (!mbar_wait(&bar, 0u, budget)) {
+    if (threadIdx.x == 0) atomicOr(err, kErrTimeout);
+  }
+}
+
+cudaError_t launch_wait_selftest(long long budget, int* err, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(budget, err);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_upload(const UploadArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
   const unsigned grid = static_cast<unsigned>((a.n + 255) / 256);

@@ -110,6 +110,8 @@ struct md_ctx {
   double* d_ion_out = nullptr;         // [sum n_ions][4]
   unsigned char* d_ion_fired = nullptr;
   double* d_ion_nu = nullptr;          // [sum n_ions] surrogate rates (-1: plain)
+  unsigned char* d_src_live = nullptr; // liveness flags per kLiveGroup records
+  unsigned char* d_tgt_live = nullptr;
   float* d_mlp = nullptr;              // surrogate parameters (device), if set
 };
 
@@ -238,6 +240,8 @@ md::StepArgs step_args(md_ctx* c) {
   a.part = c->d_fpart;
   a.iblk_cnt = c->d_iblk_cnt;
   a.n_total = c->n_total;
+  a.src_live = c->d_src_live;
+  a.tgt_live = c->d_tgt_live;
   return a;
 }
 
@@ -419,6 +423,8 @@ md::IonArgs ion_args(md_ctx* c, int ci, int force) {
   a.fired = c->d_ion_fired + c->ion_out_off[ci];
   a.nu = c->d_ion_nu + c->ion_out_off[ci];
   a.mlp = c->d_mlp;
+  a.src_live = c->d_src_live;
+  a.tgt_live = c->d_tgt_live;
   return a;
 }
 
@@ -504,6 +510,8 @@ void free_ctx(md_ctx* c) {
   cudaFree(c->d_ion_out);
   cudaFree(c->d_ion_fired);
   cudaFree(c->d_ion_nu);
+  cudaFree(c->d_src_live);
+  cudaFree(c->d_tgt_live);
   cudaFree(c->d_mlp);
   if (c->h_raw) cudaFreeHost(c->h_raw);
   if (c->h_diag) cudaFreeHost(c->h_diag);
@@ -549,6 +557,9 @@ md_status upload_cluster(md_ctx* c, int ci, const md_particles& p) {
   a.kind = c->d_kind;
   a.step = c->d_step;
   MD_CUDA(md::launch_upload(a, c->stream));
+  if (c->d_src_live)
+    MD_CUDA(md::launch_live_init(c->d_posq[0], c->d_posq[1], c->d_kind, c->d_step, c->n_total,
+                                 c->d_src_live, c->d_tgt_live, c->stream));
   // the pinned staging buffer is reused by the next call: wait for the copy
   MD_CUDA(cudaStreamSynchronize(c->stream));
   return MD_OK;
@@ -716,6 +727,10 @@ md_status md_init(md_ctx** out, const md_config* cfgs, int32_t n_clusters,
         dev_alloc(&c->d_ion_fired, static_cast<size_t>(sum_ion)) != cudaSuccess ||
         dev_alloc(&c->d_ion_nu, static_cast<size_t>(sum_ion)) != cudaSuccess)
       return bail(fail(MD_ERR_OOM, "ionization buffers"));
+    const size_t groups = static_cast<size_t>((c->n_total + md::kLiveGroup - 1) / md::kLiveGroup);
+    if (dev_alloc(&c->d_src_live, groups) != cudaSuccess ||
+        dev_alloc(&c->d_tgt_live, groups) != cudaSuccess)
+      return bail(fail(MD_ERR_OOM, "liveness flags"));
     cudaMemsetAsync(c->d_ion_out, 0, sizeof(double) * 4 * sum_ion, c->stream);
     cudaMemsetAsync(c->d_ion_fired, 0, sum_ion, c->stream);
   }
@@ -825,6 +840,36 @@ md_status md_get_ionization(md_ctx* c, int32_t cluster, double* emag, double* ne
     if (te) te[i] = out[4 * i + 2];
     if (prob) prob[i] = out[4 * i + 3];
   }
+  return check_device_error(c);
+}
+
+md_status md_set_step(md_ctx* c, int64_t step) {
+  if (!c) return fail(MD_ERR_ARG, "ctx is NULL");
+  if (step < 0) return fail(MD_ERR_ARG, "step < 0");
+  // the j-stream buffer in use is selected by the parity of the step: move
+  // the current positions to the buffer of the new parity
+  long long cur = 0;
+  MD_CUDA(cudaMemcpyAsync(&cur, c->d_step, sizeof(cur), cudaMemcpyDeviceToHost, c->stream));
+  MD_CUDA(cudaStreamSynchronize(c->stream));
+  if ((cur & 1) != (step & 1))
+    MD_CUDA(cudaMemcpyAsync(c->d_posq[step & 1], c->d_posq[cur & 1],
+                            sizeof(float4) * static_cast<size_t>(c->n_total),
+                            cudaMemcpyDeviceToDevice, c->stream));
+  long long v = step;
+  MD_CUDA(cudaMemcpyAsync(c->d_step, &v, sizeof(v), cudaMemcpyHostToDevice, c->stream));
+  MD_CUDA(cudaStreamSynchronize(c->stream));
+  return MD_OK;
+}
+
+md_status md_wait_selftest(md_ctx* c, double budget_ms) {
+  if (!c) return fail(MD_ERR_ARG, "ctx is NULL");
+  if (!(budget_ms > 0.0) || budget_ms > 5000.0)
+    return fail(MD_ERR_ARG, "budget_ms must be in (0, 5000]");
+  int clk_khz = 0;
+  MD_CUDA(cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, c->device));
+  const long long budget = static_cast<long long>(budget_ms * clk_khz);
+  MD_CUDA(md::launch_wait_selftest(budget, c->d_err, c->stream));
+  MD_CUDA(cudaStreamSynchronize(c->stream));
   return check_device_error(c);
 }
 
@@ -1022,29 +1067,41 @@ md_status md_autotune(md_ctx* c, int32_t steps, double* times_ms, int32_t cap) {
   if (!c) return fail(MD_ERR_ARG, "ctx is NULL");
   if (steps < 1) return fail(MD_ERR_ARG, "steps < 1");
   const size_t N = static_cast<size_t>(c->n_total);
-  // back up the mutable state, time each configuration, restore
-  float4* bq[2] = {nullptr, nullptr};
-  double* bx[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  long long step0 = 0;
-  md_status st = MD_OK;
-  auto release = [&]() {
-    for (auto p : bq) cudaFree(p);
-    for (auto p : bx) cudaFree(p);
+  const size_t G = static_cast<size_t>((c->n_total + md::kLiveGroup - 1) / md::kLiveGroup);
+  // every mutable device array of the state (ionization changes charges,
+  // kinds, weights and flags as well): backed up, restored after each trial
+  struct Buf {
+    void* dev;
+    size_t bytes;
+    void* copy;
   };
-  bool ok = true;
-  for (int k = 0; k < 2; ++k) ok &= dev_alloc(&bq[k], N) == cudaSuccess;
-  for (int k = 0; k < 6; ++k) ok &= dev_alloc(&bx[k], N) == cudaSuccess;
-  if (!ok) {
-    release();
-    return fail(MD_ERR_OOM, "autotune backup allocation failed");
+  std::vector<Buf> bufs = {{c->d_posq[0], N * sizeof(float4), nullptr},
+                           {c->d_posq[1], N * sizeof(float4), nullptr},
+                           {c->d_qm, N * sizeof(float), nullptr},
+                           {c->d_w, N * sizeof(double), nullptr},
+                           {c->d_mass, N * sizeof(double), nullptr},
+                           {c->d_z, N * sizeof(int), nullptr},
+                           {c->d_kind, N, nullptr}};
+  for (int k = 0; k < 3; ++k) {
+    bufs.push_back({c->d_x[k], N * sizeof(double), nullptr});
+    bufs.push_back({c->d_u[k], N * sizeof(double), nullptr});
+  }
+  if (c->d_src_live) {
+    bufs.push_back({c->d_src_live, G, nullptr});
+    bufs.push_back({c->d_tgt_live, G, nullptr});
+  }
+  auto release = [&]() {
+    for (auto& b : bufs) cudaFree(b.copy);
+  };
+  for (auto& b : bufs) {
+    if (cudaMalloc(&b.copy, b.bytes) != cudaSuccess) {
+      release();
+      return fail(MD_ERR_OOM, "autotune backup allocation failed");
+    }
   }
   cudaStream_t s = c->stream;
-  for (int k = 0; k < 2; ++k)
-    cudaMemcpyAsync(bq[k], c->d_posq[k], N * sizeof(float4), cudaMemcpyDeviceToDevice, s);
-  for (int k = 0; k < 3; ++k) {
-    cudaMemcpyAsync(bx[k], c->d_x[k], N * sizeof(double), cudaMemcpyDeviceToDevice, s);
-    cudaMemcpyAsync(bx[3 + k], c->d_u[k], N * sizeof(double), cudaMemcpyDeviceToDevice, s);
-  }
+  long long step0 = 0;
+  for (auto& b : bufs) cudaMemcpyAsync(b.copy, b.dev, b.bytes, cudaMemcpyDeviceToDevice, s);
   cudaMemcpyAsync(&step0, c->d_step, sizeof(step0), cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);
   const int cfg0 = c->cfg, cps0 = c->ctas_per_sm, js0 = c->jsplit;
@@ -1055,6 +1112,7 @@ md_status md_autotune(md_ctx* c, int32_t steps, double* times_ms, int32_t cap) {
   cudaEventCreate(&e1);
   double best = 1e300;
   int best_cfg = cfg0;
+  md_status st = MD_OK;
   for (int i = 0; i < n && st == MD_OK; ++i) {
     if (times_ms && i < cap) times_ms[i] = -1.0;
     int bps = 0;
@@ -1076,13 +1134,7 @@ md_status md_autotune(md_ctx* c, int32_t steps, double* times_ms, int32_t cap) {
       best_cfg = i;
     }
     if (st == MD_OK) st = check_device_error(c);
-    // restore the state before the next configuration
-    for (int k = 0; k < 2; ++k)
-      cudaMemcpyAsync(c->d_posq[k], bq[k], N * sizeof(float4), cudaMemcpyDeviceToDevice, s);
-    for (int k = 0; k < 3; ++k) {
-      cudaMemcpyAsync(c->d_x[k], bx[k], N * sizeof(double), cudaMemcpyDeviceToDevice, s);
-      cudaMemcpyAsync(c->d_u[k], bx[3 + k], N * sizeof(double), cudaMemcpyDeviceToDevice, s);
-    }
+    for (auto& b : bufs) cudaMemcpyAsync(b.dev, b.copy, b.bytes, cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(c->d_step, &step0, sizeof(step0), cudaMemcpyHostToDevice, s);
     cudaStreamSynchronize(s);
   }

@@ -10,6 +10,7 @@ constexpr int kPad = 16;                          // records per cluster padded 
 constexpr long long kWaitBudget = 4000000000LL;   // clock64 cycles (about 2 s)
 constexpr int kErrTimeout = 1;
 constexpr int kHistBins = 16;
+constexpr int kLiveGroup = 64;  // records per liveness flag
 
 struct ClusterDev {
   long long off;   // first record of the cluster
@@ -69,6 +70,10 @@ struct StepArgs {
   double* part;
   unsigned* iblk_cnt;
   long long n_total;
+  // liveness per group of kLiveGroup records (nullptr: everything live):
+  // src_live = some record carries charge, tgt_live = some record is active
+  const unsigned char* src_live;
+  const unsigned char* tgt_live;
 };
 
 // Arguments of the ionization kernels of one cluster.
@@ -96,6 +101,8 @@ struct IonArgs {
   double* nu;         // [n_ions]: rate from the surrogate, or -1 (use the plain rate)
   unsigned char* fired;  // [n_ions]
   const float* mlp;   // surrogate weights (rate_model 2) or nullptr
+  unsigned char* src_live;  // liveness flags (set when a record becomes charged / active)
+  unsigned char* tgt_live;
 };
 
 struct FieldArgs {

@@ -97,6 +97,8 @@ _SIGS = {
     "md_set_particles": (_st, [_ctx_p, C.c_int32, C.POINTER(Particles)]),
     "md_get_fields": (_st, [_ctx_p, C.c_int32, _p, _p]),
     "md_get_step": (_st, [_ctx_p, C.POINTER(C.c_int64)]),
+    "md_set_step": (_st, [_ctx_p, C.c_int64]),
+    "md_wait_selftest": (_st, [_ctx_p, C.c_double]),
     "md_ionize": (_st, [_ctx_p]),
     "md_get_ionization": (_st, [_ctx_p, C.c_int32, _p, _p, _p, _p, _p]),
     "md_tuning_list": (C.c_int32, [C.POINTER(Tuning), C.c_int32]),
@@ -302,6 +304,13 @@ class Context:
         phi = np.zeros(n) if potential else None
         _check(_lib.md_get_fields(self._h, cluster, _ptr(e), _ptr(phi)))
         return (e, phi) if potential else e
+
+    def set_step(self, step: int):
+        _check(_lib.md_set_step(self._h, int(step)))
+
+    def wait_selftest(self, budget_ms: float) -> int:
+        """Status of the bounded-wait self-test (MD_ERR_TIMEOUT expected)."""
+        return int(_lib.md_wait_selftest(self._h, float(budget_ms)))
 
     def ionize(self):
         _check(_lib.md_ionize(self._h))

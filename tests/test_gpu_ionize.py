@@ -139,3 +139,30 @@ def test_ionization_in_steps_conserves_charge(md):
         assert g.z[:n].sum() > 0
         d = ctx.diagnostics(0)
         assert d["charge_count"].sum() == n and d["n_nonfinite"] == 0
+
+
+def test_dead_tiles_skipped_and_autotune_restores_ionizing_state(md):
+    """Records of an ionizing cluster that carry no charge are skipped as
+    sources and inactive slots as targets: a step of the neutral cluster does
+    no pair work, and the ionized result does not depend on the kernel
+    configuration picked by the autotuner (which restores all state)."""
+    c, kw = ar_case(n_atoms=2000)
+    kw["ionize_every"] = 1
+    res = []
+    for tune in (False, True):
+        with md.Context([md.make_config(**kw)], [md.HostParticles.from_cluster(c)]) as ctx:
+            if tune:
+                before = ctx.get_particles(0)
+                ctx.step(2)
+                mid = ctx.get_particles(0)
+                ctx.autotune(2)
+                again = ctx.get_particles(0)
+                assert np.array_equal(mid.z, again.z) and np.array_equal(mid.kind, again.kind)
+                assert np.array_equal(mid.x, again.x)
+                ctx.set_particles(0, before)
+                ctx.set_step(0)
+            ctx.set_tuning(128, 4, 512, 0, 1, 0)
+            ctx.step(12)
+            res.append(ctx.get_particles(0))
+    assert np.array_equal(res[0].z, res[1].z) and np.array_equal(res[0].x, res[1].x)
+    assert res[0].z[:2000].sum() > 0

@@ -325,3 +325,58 @@ def test_periodic_boundary_wraps_into_box(md):
     d = np.abs(g.x - st.x)
     d = np.minimum(d, L - d)
     assert np.percentile(d.max(1), 90) < 1e-5 * L
+
+
+def test_checkpoint_resume_is_exact(md):
+    """A checkpoint (particles + step) restored into a new context continues
+    bit-identically, ionization included (Philox is keyed on the step)."""
+    n = 600
+    c = synth.make_cluster(3, n, 0, synth.nm_to_len(2.0), 0, synth.ARGON["mass"],
+                           n_electron_slots=n * 8)
+    rw = synth.nm_to_len(synth.ARGON["r_w_nm"])
+    cfg = md.make_config(a0=0.1, tau=1.0, dt=0.05, softening=synth.nm_to_len(0.1), envelope=3,
+                         rate_model=1, ionize_every=2, zmax=8, n_ions=n, slot_base=n, seed=5,
+                         r_loc=3 * rw, r_create=rw, species=synth.ARGON)
+    with md.Context([cfg], [md.HostParticles.from_cluster(c)]) as a:
+        a.step(13)
+        ck = a.get_particles(0)
+        a.step(17)
+        ref = a.get_particles(0)
+    with md.Context([cfg], [md.HostParticles.from_cluster(c)]) as b:
+        b.set_particles(0, ck)
+        b.set_step(13)
+        b.step(17)
+        got = b.get_particles(0)
+        assert b.step_index() == 30
+    assert np.array_equal(got.x, ref.x) and np.array_equal(got.u, ref.u)
+    assert np.array_equal(got.z, ref.z) and np.array_equal(got.kind, ref.kind)
+
+
+def test_bounded_wait_times_out_and_context_survives(md):
+    """A device wait that nothing completes returns MD_ERR_TIMEOUT after its
+    budget; the context keeps working afterwards."""
+    w = synth.xe3_cluster(2000, seed=1)
+    with ctx_for(md, w) as ctx:
+        assert ctx.wait_selftest(20.0) == md.MD_ERR_TIMEOUT
+        ctx.step(3)
+        ctx.sync()
+        d = ctx.diagnostics(0)
+        assert d["step"] == 3 and d["n_nonfinite"] == 0
+
+
+def test_mixed_boundary_periodic_then_open(md):
+    """Mixed boundary (Sec. II): wrapped while t < t_switch, free flight after."""
+    c = synth.make_cluster(8, 100, 300, 0.01, 3, synth.MASS_XE, kT_e_ev=5000.0)
+    L = 0.02
+    w = synth.Workload("mixed", c, a0=0.0, pol=0, env=3, tau=1.0, eps=1e-3, dt=0.05, nsteps=0,
+                       boundary=2, box=L, t_switch=1.0)
+    with ctx_for(md, w) as ctx:
+        ctx.step(19)                 # drifts up to t = 19 dt = 0.95 < t_switch: wrapped
+        g1 = ctx.get_particles(0)
+        ctx.step(41)                 # open from t = 1.0 on: fast electrons leave the box
+        g2 = ctx.get_particles(0)
+    assert g1.x.min() >= -L / 2 and g1.x.max() <= L / 2
+    assert np.abs(g2.x).max() > L / 2
+    st = oracle_state(c)
+    oracle.md_steps(st, oracle_params(w), 60)
+    assert np.percentile(np.abs(g2.x - st.x).max(1), 90) < 1e-4 * L
