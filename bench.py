@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -42,8 +43,9 @@ WORKLOAD_TEXT = {
     "scan256": "parameter scan of {clusters} clusters (N log-uniform 1k-50k, Z 1-8, R0 1-8 nm, "
                "a0 0.01-0.3, 20-200 fs), {n} records in one persistent launch per step",
     "precision_1m": "{name}: N={n}, laser off",
-    "ar_ionize": "{name}: N={n} records (neutral Ar atoms + 8 electron slots each), plain "
-                 "ADK + Lotz ionization before every step",
+    "ar_ionize": "{name}: {atoms} Ar atoms (neutral at the start) in an 8 nm sphere + 8 "
+                 "electron slots each ({n} records), ADK + Lotz ionization before every step "
+                 "({rates} rates), from the pulse peak",
 }
 
 
@@ -53,7 +55,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--n", type=int, default=200000, help="particles per cluster")
+    ap.add_argument("--n", type=int, default=None,
+                    help="particles per cluster (ar_ionize: atoms; default 200000)")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle sample")
@@ -65,8 +68,14 @@ def parse_args():
                     choices=["xe3_200k", "scan256", "precision_1m", "ar_ionize"],
                     help="xe3_200k: the headline N=200k cluster; scan256: 256 clusters of a "
                          "parameter scan in one persistent launch; precision_1m: 500k Ar+ + 500k "
-                         "e, laser off; ar_ionize: neutral Ar atoms ionizing (plain rates)")
-    return ap.parse_args()
+                         "e, laser off; ar_ionize: neutral Ar atoms ionizing")
+    ap.add_argument("--rates", default="plain", choices=["plain", "mlp"],
+                    help="ar_ionize: plain ADK + Lotz rates, or the BF16 surrogate trained on "
+                         "the GPU before the run (plain rates outside its domain)")
+    args = ap.parse_args()
+    if args.n is None:
+        args.n = 200000
+    return args
 
 
 # ----------------------------------------------------------- distributed --
@@ -216,6 +225,42 @@ def cpu_oracle_rate(w, seconds: float, seed: int = 0, e_gpu=None):
     return pairs / dt, threads, nt, dt, err
 
 
+def ar_ionize_context(md, args, rank, stream):
+    """Neutral argon cluster at the density of 200k atoms in an 8 nm sphere, 8
+    inactive electron slots per atom, 806 nm pulse of 8e15 W/cm^2 (a0 = 0.0617)
+    with a 100 fs sin^2 envelope, started just before a field crest at the
+    envelope peak so that the timed steps ionize."""
+    n = args.n
+    c = synth.make_cluster(rank, n, 0, synth.nm_to_len(8.0 * (n / 200000) ** (1 / 3), 0.806), 0,
+                           synth.ARGON["mass"], n_electron_slots=8 * n)
+    rw = synth.nm_to_len(synth.ARGON["r_w_nm"], 0.806)
+    tau = synth.sin2_length_from_fwhm(synth.fs_to_time(100.0, 0.806))
+    # a_x = a0 env(t) sin(t): the crest nearest the envelope peak, less 0.3 rad
+    t0 = math.floor(tau / 2 / math.pi) * math.pi + 0.5 * math.pi - 0.3
+    w = synth.Workload(f"ar{n // 1000}k_ionize", c, a0=0.0617, pol=0, env=synth.ENV_SIN2,
+                       tau=tau, eps=synth.nm_to_len(0.1, 0.806), dt=0.02, nsteps=0, t0=t0,
+                       lambda_um=0.806)
+    cfg = md.config_from_workload(w)
+    model = md.RATES_MLP if args.rates == "mlp" else md.RATES_PLAIN
+    ion = md.make_config(rate_model=model, ionize_every=1, zmax=8, n_ions=n, slot_base=n,
+                         seed=rank + 1, r_loc=3 * rw, r_create=rw, species=synth.ARGON)
+    for f in ("rate_model", "ionize_every", "zmax", "n_ions", "slot_base", "seed", "r_loc",
+              "r_create", "ip_ev", "q_outer"):
+        setattr(cfg, f, getattr(ion, f))
+    ctx = md.Context([cfg], [md.HostParticles.from_cluster(c)], stream=stream)
+    info = {"rates": args.rates, "t0": t0, "kernels_per_step": 1 + (4 if model == md.RATES_MLP
+                                                                     else 3)}
+    if model == md.RATES_MLP:
+        tc = md.mlp_train_config(synth.ARGON, n_samples=10 << 20, epochs=80, batch=8192,
+                                 lr=3e-3, seed=11, lambda_um=0.806)
+        t_train = time.perf_counter()
+        params, rep = md.mlp_train(tc, stream)
+        info["surrogate_training"] = dict(rep, wall_s=time.perf_counter() - t_train,
+                                          samples=tc.n_samples, epochs=tc.epochs)
+        ctx.set_rate_mlp(params, tc)
+    return ctx, [w], None, info
+
+
 def build_contexts(md, args, rank, stream):
     """The workload's clusters -> (context, list of workloads, pairs per step)."""
     if args.workload == "scan256":
@@ -229,30 +274,15 @@ def build_contexts(md, args, rank, stream):
             cfgs.append(md.config_from_workload(w))
             parts.append(md.HostParticles.from_cluster(cl))
         pairs = float(sum(float(w.cluster.n) ** 2 for w in ws))
-        return md.Context(cfgs, parts, stream=stream), ws, pairs
+        return md.Context(cfgs, parts, stream=stream), ws, pairs, {}
     if args.workload == "precision_1m":
         w = synth.precision_1m(seed=rank, a0=0.0)
     elif args.workload == "ar_ionize":
-        n = args.n if args.n != 200000 else 20000
-        c = synth.make_cluster(rank, n, 0, synth.nm_to_len(8.0 * (n / 200000) ** (1 / 3)), 0,
-                               synth.ARGON["mass"], n_electron_slots=8 * n)
-        rw = synth.nm_to_len(synth.ARGON["r_w_nm"])
-        w = synth.Workload(f"ar{n // 1000}k_ionize", c, a0=0.0617, pol=0, env=synth.ENV_SIN2,
-                           tau=synth.sin2_length_from_fwhm(synth.fs_to_time(100.0, 0.806), ),
-                           eps=synth.nm_to_len(0.1), dt=0.02, nsteps=0, lambda_um=0.806)
-        cfg = md.config_from_workload(w)
-        ion = md.make_config(rate_model=md.RATES_PLAIN, ionize_every=1, zmax=8, n_ions=n,
-                             slot_base=n, seed=rank + 1, r_loc=3 * rw, r_create=rw,
-                             species=synth.ARGON)
-        for f in ("rate_model", "ionize_every", "zmax", "n_ions", "slot_base", "seed", "r_loc",
-                  "r_create", "ip_ev", "q_outer"):
-            setattr(cfg, f, getattr(ion, f))
-        return (md.Context([cfg], [md.HostParticles.from_cluster(c)], stream=stream), [w],
-                float(c.n) ** 2)
+        return ar_ionize_context(md, args, rank, stream)
     else:
         w = workload(args.n, seed=rank)
     return (md.Context([md.config_from_workload(w)], [md.HostParticles.from_cluster(w.cluster)],
-                       stream=stream), [w], float(w.cluster.n) ** 2)
+                       stream=stream), [w], float(w.cluster.n) ** 2, {})
 
 
 # --------------------------------------------------------------- native --
@@ -270,12 +300,13 @@ def run_native(args):
     # one non-default stream shared by torch (events, L2 flush) and the library
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    ctx, ws, pairs_per_step = build_contexts(md, args, rank, stream.cuda_stream)
+    ctx, ws, pairs_per_step, info = build_contexts(md, args, rank, stream.cuda_stream)
+    ionizing = args.workload == "ar_ionize"
     w = ws[0]
     n = sum(x.cluster.n for x in ws)
     # FP32/Kahan field of the initial state, compared with the FP64 oracle in
     # the CPU-baseline leg below
-    e_gpu0 = ctx.fields(0) if len(ws) == 1 else None
+    e_gpu0 = ctx.fields(0) if len(ws) == 1 and not ionizing else None
     sms, gpu_name = md.device_info()
 
     tune_ms = None
@@ -300,17 +331,24 @@ def run_native(args):
     dist.barrier()
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
+    step_pairs = []
     for e0, e1 in evs:
         flush.zero_()                # L2 flushed between timed steps, outside the events
         e0.record(stream)
         ctx.step(1)
         e1.record(stream)
+        if ionizing:
+            # records active after the step's ionization pass (the pairs its
+            # Coulomb sum covered); read outside the events
+            step_pairs.append(float(ctx.diagnostics(0)["n_active"]) ** 2)
     torch.cuda.synchronize()
     dist.barrier()
     wall = time.perf_counter() - wall0
     clocks = sampler.stop()
     ctx.sync()
     step_ms = [a.elapsed_time(b) for a, b in evs]
+    if ionizing:
+        pairs_per_step = float(np.mean(step_pairs))
     t_local = sum(step_ms) / 1e3
     t_max = dist.max(t_local)
     ms_per_step = t_max * 1e3 / args.steps
@@ -336,7 +374,7 @@ def run_native(args):
             pinned[k] = t
         hps.append(md.HostParticles(*(pinned[k].numpy()
                                       for k in ("x", "u", "z", "mass", "w", "kind"))))
-    e2e_t = []
+    e2e_t, e2e_pairs = [], []
     for s_ in range(args.e2e_steps + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -348,9 +386,15 @@ def run_native(args):
         t1 = time.perf_counter()
         if s_ > 0:
             e2e_t.append(t1 - t0)
+            e2e_pairs.append(float(np.count_nonzero(hps[0].kind != md.KIND_INACTIVE)) ** 2
+                             if ionizing else pairs_per_step)
+        if ionizing:   # back to the neutral cluster for the next end-to-end step
+            init = md.HostParticles.from_cluster(ws[0].cluster)
+            for k in ("x", "u", "z", "mass", "w", "kind"):
+                getattr(hps[0], k)[...] = getattr(init, k)
     e2e_local = float(np.mean(e2e_t))
     e2e_max = dist.max(e2e_local)
-    e2e_value = world * pairs_per_step / e2e_max
+    e2e_value = world * float(np.mean(e2e_pairs)) / e2e_max
 
     cpu = None
     force_err = None
@@ -361,12 +405,17 @@ def run_native(args):
                          f"({nt * w.cluster.n:.3g} pairs, {secs:.1f} s, OpenMP over targets)",
                "steps_per_s": rate / (float(w.cluster.n) ** 2)}
 
-    launches_per_step = 1 + (4 if args.workload == "ar_ionize" else 0)
+    launches_per_step = info.get("kernels_per_step", 1)
     ion_state = None
-    if args.workload == "ar_ionize":
+    if ionizing:
         d = ctx.diagnostics(0)
-        ion_state = {"charge_fractions": (d["charge_count"][:9] / w.cluster.n_ions).tolist(),
-                     "active_records": int(d["n_active"])}
+        ion_state = dict(info, charge_fractions=(d["charge_count"][:9] / w.cluster.n_ions).tolist(),
+                         active_records_after_timed_steps=int(d["n_active"]),
+                         pairs_counted="(active records after each step's ionization pass)^2, "
+                                       "averaged over the timed steps",
+                         step_includes="ionization field + moments, rate inputs, "
+                                       + ("surrogate rates, " if args.rates == "mlp" else "")
+                                       + "decision, fused Coulomb/laser/push step")
     ctx.close()
     dist.close()
     if rank != 0:
@@ -387,7 +436,8 @@ def run_native(args):
         "data": "synthetic",
         "config": {
             "workload": WORKLOAD_TEXT[args.workload].format(name=w.name, n=n,
-                                                            clusters=len(ws)),
+                                                            clusters=len(ws), atoms=args.n,
+                                                            rates=args.rates),
             "n_particles": n, "pairs_per_step": pairs_per_step, "ionization": ion_state,
             "softening_nm": 0.1, "dt": w.dt, "a0": w.a0, "envelope": "sin2, 100 fs FWHM",
             "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write outside the "
@@ -436,10 +486,10 @@ def run_reference(args):
         return
     w = workload(args.n, seed=0)
     n = w.cluster.n
-    per_step = max(1.0, 150.0 / max(1, args.steps + args.warmup))
+    per_step = min(args.cpu_seconds, max(0.2, 150.0 / max(1, args.steps + args.warmup)))
     rates = []
     for s in range(args.warmup + args.steps):
-        rate, threads, nt, secs = cpu_oracle_rate(w, per_step, seed=s)
+        rate, threads, nt, secs, _ = cpu_oracle_rate(w, per_step, seed=s)
         if s >= args.warmup:
             rates.append((rate, nt, secs))
     value = float(np.mean([r[0] for r in rates]))
