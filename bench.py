@@ -354,6 +354,22 @@ def run_native(args):
     ms_per_step = t_max * 1e3 / args.steps
     value = world * pairs_per_step * args.steps / t_max
 
+    ion_state = None
+    if ionizing:
+        # the state the timed steps reached (the end-to-end leg below restarts
+        # from the neutral cluster)
+        d = ctx.diagnostics(0)
+        ion_state = dict(info, charge_fractions=(d["charge_count"][:9] / w.cluster.n_ions).tolist(),
+                         active_records_after_timed_steps=int(d["n_active"]),
+                         active_records_per_timed_step=[int(round(math.sqrt(p)))
+                                                        for p in step_pairs],
+                         ms_per_timed_step=step_ms,
+                         pairs_counted="(active records after each step's ionization pass)^2, "
+                                       "averaged over the timed steps",
+                         step_includes="ionization field + moments, rate inputs, "
+                                       + ("surrogate rates, " if args.rates == "mlp" else "")
+                                       + "decision, fused Coulomb/laser/push step")
+
     # FP32 roofline of the step kernel (the only kernel of a step)
     ffma_per_s, ffma2_per_s = md.measure_fp32_peak(stream.cuda_stream)
     achieved = pairs_per_step / (statistics.mean(step_ms) / 1e3)
@@ -406,16 +422,6 @@ def run_native(args):
                "steps_per_s": rate / (float(w.cluster.n) ** 2)}
 
     launches_per_step = info.get("kernels_per_step", 1)
-    ion_state = None
-    if ionizing:
-        d = ctx.diagnostics(0)
-        ion_state = dict(info, charge_fractions=(d["charge_count"][:9] / w.cluster.n_ions).tolist(),
-                         active_records_after_timed_steps=int(d["n_active"]),
-                         pairs_counted="(active records after each step's ionization pass)^2, "
-                                       "averaged over the timed steps",
-                         step_includes="ionization field + moments, rate inputs, "
-                                       + ("surrogate rates, " if args.rates == "mlp" else "")
-                                       + "decision, fused Coulomb/laser/push step")
     ctx.close()
     dist.close()
     if rank != 0:

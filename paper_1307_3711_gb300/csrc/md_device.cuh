@@ -362,6 +362,21 @@ __device__ __forceinline__ bool any_live(const unsigned char* live, long long r0
   return false;
 }
 
+// First tile index >= t of a source range (ns records from global record
+// gbase, tiles of `tile` records) that overlaps a live group, or ntiles if
+// none does (no flags: t itself).  Dead tiles are neither copied nor summed.
+__device__ __forceinline__ int next_live_tile(const unsigned char* live, long long gbase,
+                                              long long ns, int t, int ntiles, int tile) {
+  if (!live || t >= ntiles) return t;
+  const long long r = gbase + static_cast<long long>(t) * tile;
+  const long long gend = (gbase + ns - 1) / kLiveGroup;
+  long long g = r / kLiveGroup;
+  while (g <= gend && !live[g]) ++g;
+  if (g > gend) return ntiles;
+  const long long rr = g * kLiveGroup > r ? g * kLiveGroup : r;
+  return static_cast<int>((rr - gbase) / tile);
+}
+
 // Sum over all ns sources for the R targets held by this thread, streaming the
 // sources through the STAGES-deep TMA ring.  `it` counts tiles this CTA has
 // consumed so far (sets the barrier phases).  Returns false (uniformly across
@@ -376,29 +391,34 @@ __device__ __forceinline__ bool sum_sources(Stage<TILE, STAGES>& sm, unsigned& i
                                             const unsigned char* live = nullptr,
                                             long long gbase = 0) {
   const int ntiles = static_cast<int>((ns + TILE - 1) / TILE);
+  // consumers and the issuing thread walk the same sequence of live tiles;
+  // the k-th live tile goes through ring stage (it + k) % STAGES
+  int t = next_live_tile(live, gbase, ns, 0, ntiles, TILE);
+  int ti = t;          // issue cursor (thread 0)
+  unsigned issued = 0;
   if (threadIdx.x == 0) {
-    for (int k = 0; k < STAGES && k < ntiles; ++k) issue_tile<TILE, STAGES>(sm, it + k, src, ns, k);
+    for (; issued < static_cast<unsigned>(STAGES) && ti < ntiles; ++issued) {
+      issue_tile<TILE, STAGES>(sm, it + issued, src, ns, ti);
+      ti = next_live_tile(live, gbase, ns, ti + 1, ntiles, TILE);
+    }
   }
-  for (int t = 0; t < ntiles; ++t) {
-    const unsigned g = it + t;
+  unsigned k = 0;
+  for (; t < ntiles; ++k) {
+    const unsigned g = it + k;
     const int s = static_cast<int>(g % STAGES);
     const uint32_t parity = (g / STAGES) & 1u;
     if (!mbar_wait(&sm.full[s], parity)) {
       atomicOr(err, kErrTimeout);
       *s_abort = 1;
     }
-    const long long rem0 = ns - static_cast<long long>(t) * TILE;
-    const bool tile_live = any_live(live, gbase + static_cast<long long>(t) * TILE,
-                                    gbase + static_cast<long long>(t) * TILE +
-                                        (rem0 < TILE ? rem0 : TILE) - 1);
-    if (tile_live && !*reinterpret_cast<volatile int*>(s_abort)) {
+    if (!*reinterpret_cast<volatile int*>(s_abort)) {
       const uint32_t tile = smem_u32(&sm.tile[s][0]);
       const long long rem = ns - static_cast<long long>(t) * TILE;
       const int cnt = static_cast<int>(rem < TILE ? rem : TILE);
       int j = 0;
       for (; j + 8 <= cnt; j += 8) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) pair<R, POT>(lds_f4(tile + 16u * (j + k)), xi, yi, zi, eps2, acc);
+        for (int q = 0; q < 8; ++q) pair<R, POT>(lds_f4(tile + 16u * (j + q)), xi, yi, zi, eps2, acc);
         if (POT) {
           // potential terms of one species share a sign: fold them often so
           // the FP32 partial stays small against a cancelling total
@@ -415,19 +435,23 @@ __device__ __forceinline__ bool sum_sources(Stage<TILE, STAGES>& sm, unsigned& i
     __syncthreads();
     if (*reinterpret_cast<volatile int*>(s_abort)) {
       if (threadIdx.x == 0) {
-        const int last = (t + STAGES < ntiles) ? t + STAGES : ntiles;
-        for (int k = t + 1; k < last; ++k) {
-          const unsigned gk = it + k;
-          mbar_wait(&sm.full[gk % STAGES], (gk / STAGES) & 1u);
+        // wait (bounded) for the copies still in flight before leaving
+        for (unsigned q = k + 1; q < issued; ++q) {
+          const unsigned gq = it + q;
+          mbar_wait(&sm.full[gq % STAGES], (gq / STAGES) & 1u);
         }
       }
       __syncthreads();
       return false;
     }
-    if (threadIdx.x == 0 && t + STAGES < ntiles)
-      issue_tile<TILE, STAGES>(sm, it + t + STAGES, src, ns, t + STAGES);
+    if (threadIdx.x == 0 && ti < ntiles) {
+      issue_tile<TILE, STAGES>(sm, it + issued, src, ns, ti);
+      ++issued;
+      ti = next_live_tile(live, gbase, ns, ti + 1, ntiles, TILE);
+    }
+    t = next_live_tile(live, gbase, ns, t + 1, ntiles, TILE);
   }
-  it += static_cast<unsigned>(ntiles);
+  it += k;
   return true;
 }
 
@@ -560,11 +584,19 @@ __device__ __forceinline__ bool sum_sources_packed(Stage<TILE, STAGES>& sm, DupT
   }
   const u64 e2 = f2_pack(eps2, eps2);
   const int ntiles = static_cast<int>((ns + TILE - 1) / TILE);
+  // live tiles only, in the same order for the issuing thread and the consumers
+  int t = next_live_tile(live, gbase, ns, 0, ntiles, TILE);
+  int ti = t;
+  unsigned issued = 0;
   if (tid == 0) {
-    for (int k = 0; k < STAGES && k < ntiles; ++k) issue_tile<TILE, STAGES>(sm, it + k, src, ns, k);
+    for (; issued < static_cast<unsigned>(STAGES) && ti < ntiles; ++issued) {
+      issue_tile<TILE, STAGES>(sm, it + issued, src, ns, ti);
+      ti = next_live_tile(live, gbase, ns, ti + 1, ntiles, TILE);
+    }
   }
-  for (int t = 0; t < ntiles; ++t) {
-    const unsigned g = it + t;
+  unsigned kt = 0;
+  for (; t < ntiles; ++kt) {
+    const unsigned g = it + kt;
     const int s = static_cast<int>(g % STAGES);
     const uint32_t parity = (g / STAGES) & 1u;
     if (!mbar_wait(&sm.full[s], parity)) {
@@ -573,9 +605,7 @@ __device__ __forceinline__ bool sum_sources_packed(Stage<TILE, STAGES>& sm, DupT
     }
     const long long rem = ns - static_cast<long long>(t) * TILE;
     const int cnt = static_cast<int>(rem < TILE ? rem : TILE);
-    const bool tile_live = any_live(live, gbase + static_cast<long long>(t) * TILE,
-                                    gbase + static_cast<long long>(t) * TILE + cnt - 1);
-    if (tile_live && !*reinterpret_cast<volatile int*>(s_abort)) {
+    if (!*reinterpret_cast<volatile int*>(s_abort)) {
       for (int k = tid; k < cnt; k += THREADS) {
         const float4 p = sm.tile[s][k];
         dup.v[k][0] = make_ulonglong2(f2_pack(p.x, p.x), f2_pack(p.y, p.y));
@@ -585,21 +615,19 @@ __device__ __forceinline__ bool sum_sources_packed(Stage<TILE, STAGES>& sm, DupT
     __syncthreads();
     if (*reinterpret_cast<volatile int*>(s_abort)) {
       if (tid == 0) {
-        const int last = (t + STAGES < ntiles) ? t + STAGES : ntiles;
-        for (int k = t + 1; k < last; ++k) {
-          const unsigned gk = it + k;
-          mbar_wait(&sm.full[gk % STAGES], (gk / STAGES) & 1u);
+        for (unsigned q = kt + 1; q < issued; ++q) {
+          const unsigned gq = it + q;
+          mbar_wait(&sm.full[gq % STAGES], (gq / STAGES) & 1u);
         }
       }
       __syncthreads();
       return false;
     }
     // the stage is expanded into dup: refill it while this tile is summed
-    if (tid == 0 && t + STAGES < ntiles)
-      issue_tile<TILE, STAGES>(sm, it + t + STAGES, src, ns, t + STAGES);
-    if (!tile_live) {
-      __syncthreads();
-      continue;
+    if (tid == 0 && ti < ntiles) {
+      issue_tile<TILE, STAGES>(sm, it + issued, src, ns, ti);
+      ++issued;
+      ti = next_live_tile(live, gbase, ns, ti + 1, ntiles, TILE);
     }
     const uint32_t dbase = smem_u32(&dup.v[0][0]);
     int j = 0;
@@ -643,8 +671,9 @@ __device__ __forceinline__ bool sum_sources_packed(Stage<TILE, STAGES>& sm, DupT
       }
     }
     __syncthreads();  // dup is rewritten by the next tile
+    t = next_live_tile(live, gbase, ns, t + 1, ntiles, TILE);
   }
-  it += static_cast<unsigned>(ntiles);
+  it += kt;
   return true;
 }
 
@@ -683,6 +712,13 @@ __device__ __forceinline__ void push_record(const StepArgs& a, const ClusterDev&
   a.uz[i] = Uz;
   nxt[i] = make_float4(static_cast<float>(X), static_cast<float>(Y), static_cast<float>(Z),
                        cur[i].w);
+  if (a.vel) {
+    float4 v = a.vel[i];
+    v.x = static_cast<float>(Ux);
+    v.y = static_cast<float>(Uy);
+    v.z = static_cast<float>(Uz);
+    a.vel[i] = v;
+  }
 }
 
 // One full MD step for every work unit (cluster, i-block): field at x^n from

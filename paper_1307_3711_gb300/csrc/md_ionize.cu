@@ -32,10 +32,37 @@ __device__ __forceinline__ bool pass_active(const IonArgs& a, long long step) {
 
 // --------------------------------------------------------- field + moments
 
+// Source tiles of the ionization pass: positions/charges and, for the same
+// records, the FP32 velocity stream, landed by two bulk copies on one barrier.
+template <int TILE, int STAGES>
+struct IonStage {
+  alignas(128) float4 pos[STAGES][TILE];
+  alignas(128) float4 vel[STAGES][TILE];
+  alignas(8) uint64_t full[STAGES];
+};
+
+template <int TILE, int STAGES>
+__device__ __forceinline__ void issue_ion_tile(IonStage<TILE, STAGES>& sm, unsigned g,
+                                               const float4* pos, const float4* vel, long long ns,
+                                               int t) {
+  const int s = static_cast<int>(g % STAGES);
+  const long long j0 = static_cast<long long>(t) * TILE;
+  const long long rem = ns - j0;
+  const uint32_t bytes = static_cast<uint32_t>(rem < TILE ? rem : TILE) * 16u;
+  fence_proxy_async_smem();
+  mbar_arrive_expect_tx(&sm.full[s], 2u * bytes);
+  bulk_g2s(&sm.pos[s][0], pos + j0, bytes, &sm.full[s]);
+  bulk_g2s(&sm.vel[s][0], vel + j0, bytes, &sm.full[s]);
+}
+
 // Field (FP32/Kahan) and local electron moments at R ion targets per thread.
+// The moments are FP32 sums of w, w du and w du^2 with du = u - u_ref, u_ref
+// the velocity of the first electron found within r_loc (in source order):
+// the variance is unchanged by the shift, and centring the sums keeps the
+// thermal spread from cancelling against a common drift.
 template <int THREADS, int R, int TILE, int STAGES>
 __global__ void __launch_bounds__(THREADS) k_ion_field(const IonArgs a) {
-  __shared__ Stage<TILE, STAGES> sm;
+  __shared__ IonStage<TILE, STAGES> sm;
   __shared__ int s_abort;
   const long long step = __ldcg(a.step);
   if (!pass_active(a, step)) return;
@@ -47,13 +74,17 @@ __global__ void __launch_bounds__(THREADS) k_ion_field(const IonArgs a) {
   __syncthreads();
   const float4* __restrict__ cur = (step & 1) ? a.posq1 : a.posq0;
   const float4* src = cur + a.c.off;
+  const float4* vsrc = a.vel + a.c.off;
   const long long ns = a.c.n_pad;
   const long long t0 = static_cast<long long>(blockIdx.x) * (THREADS * R);
   const float rloc2 = static_cast<float>(a.ion.r_loc * a.ion.r_loc);
+  const float eps2 = a.c.eps2;
   float xi[R], yi[R], zi[R];
   Acc<R, false> acc;
   acc.zero();
-  double mom[R][5];
+  // per target: sum w, sum w du (3), sum w du^2, u_ref (3); ref set once
+  float mw[R], mx[R], my[R], mz[R], mq[R], rx[R], ry[R], rz[R];
+  bool have[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const long long t = t0 + threadIdx.x + r * THREADS;
@@ -61,43 +92,59 @@ __global__ void __launch_bounds__(THREADS) k_ion_field(const IonArgs a) {
     xi[r] = p.x;
     yi[r] = p.y;
     zi[r] = p.z;
-#pragma unroll
-    for (int k = 0; k < 5; ++k) mom[r][k] = 0.0;
+    mw[r] = mx[r] = my[r] = mz[r] = mq[r] = rx[r] = ry[r] = rz[r] = 0.0f;
+    have[r] = false;
   }
   const int ntiles = static_cast<int>((ns + TILE - 1) / TILE);
-  if (threadIdx.x == 0)
-    for (int k = 0; k < STAGES && k < ntiles; ++k) issue_tile<TILE, STAGES>(sm, k, src, ns, k);
-  for (int t = 0; t < ntiles; ++t) {
-    const int s = t % STAGES;
-    if (!mbar_wait(&sm.full[s], (t / STAGES) & 1u)) {
+  // only tiles holding a live group are copied and summed, in the same order
+  // for the issuing thread and the consumers
+  const long long gb = a.c.off;
+  int t = next_live_tile(a.src_live, gb, ns, 0, ntiles, TILE);
+  int ti = t;
+  unsigned issued = 0;
+  if (threadIdx.x == 0) {
+    for (; issued < static_cast<unsigned>(STAGES) && ti < ntiles; ++issued) {
+      issue_ion_tile<TILE, STAGES>(sm, issued, src, vsrc, ns, ti);
+      ti = next_live_tile(a.src_live, gb, ns, ti + 1, ntiles, TILE);
+    }
+  }
+  for (unsigned k = 0; t < ntiles; ++k) {
+    const int s = static_cast<int>(k % STAGES);
+    if (!mbar_wait(&sm.full[s], (k / STAGES) & 1u)) {
       atomicOr(a.err, kErrTimeout);
       s_abort = 1;
     }
     const long long jb = static_cast<long long>(t) * TILE;
     const long long rem = ns - jb;
     const int cnt = static_cast<int>(rem < TILE ? rem : TILE);
-    if (any_live(a.src_live, a.c.off + jb, a.c.off + jb + cnt - 1) &&
-        !*reinterpret_cast<volatile int*>(&s_abort)) {
+    if (!*reinterpret_cast<volatile int*>(&s_abort)) {
+      const uint32_t ptile = smem_u32(&sm.pos[s][0]);
 #pragma unroll 4
       for (int j = 0; j < cnt; ++j) {
-        const float4 p = sm.tile[s][j];
+        const float4 p = lds_f4(ptile + 16u * j);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           const float dx = p.x - xi[r], dy = p.y - yi[r], dz = p.z - zi[r];
           const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          const float ri = rsqrt_mufu(d2 + a.c.eps2);
+          const float ri = rsqrt_mufu(d2 + eps2);
           const float s3 = p.w * ri * ri * ri;
           acc.ax[r] = fmaf(dx, s3, acc.ax[r]);
           acc.ay[r] = fmaf(dy, s3, acc.ay[r]);
           acc.az[r] = fmaf(dz, s3, acc.az[r]);
           if (p.w < 0.0f && d2 < rloc2) {  // an electron within r_loc
-            const long long jg = a.c.off + jb + j;
-            const double w = a.w[jg], ux = a.ux[jg], uy = a.uy[jg], uz = a.uz[jg];
-            mom[r][0] += w;
-            mom[r][1] += w * ux;
-            mom[r][2] += w * uy;
-            mom[r][3] += w * uz;
-            mom[r][4] += w * (ux * ux + uy * uy + uz * uz);
+            const float4 v = sm.vel[s][j];
+            if (!have[r]) {
+              rx[r] = v.x;
+              ry[r] = v.y;
+              rz[r] = v.z;
+              have[r] = true;
+            }
+            const float ux = v.x - rx[r], uy = v.y - ry[r], uz = v.z - rz[r];
+            mw[r] += v.w;
+            mx[r] = fmaf(v.w, ux, mx[r]);
+            my[r] = fmaf(v.w, uy, my[r]);
+            mz[r] = fmaf(v.w, uz, mz[r]);
+            mq[r] = fmaf(v.w, fmaf(ux, ux, fmaf(uy, uy, uz * uz)), mq[r]);
           }
         }
       }
@@ -106,24 +153,31 @@ __global__ void __launch_bounds__(THREADS) k_ion_field(const IonArgs a) {
     __syncthreads();
     if (*reinterpret_cast<volatile int*>(&s_abort)) {
       if (threadIdx.x == 0) {
-        const int last = (t + STAGES < ntiles) ? t + STAGES : ntiles;
-        for (int k = t + 1; k < last; ++k) mbar_wait(&sm.full[k % STAGES], (k / STAGES) & 1u);
+        for (unsigned q = k + 1; q < issued; ++q)
+          mbar_wait(&sm.full[q % STAGES], (q / STAGES) & 1u);
       }
       return;
     }
-    if (threadIdx.x == 0 && t + STAGES < ntiles)
-      issue_tile<TILE, STAGES>(sm, t + STAGES, src, ns, t + STAGES);
+    if (threadIdx.x == 0 && ti < ntiles) {
+      issue_ion_tile<TILE, STAGES>(sm, issued, src, vsrc, ns, ti);
+      ++issued;
+      ti = next_live_tile(a.src_live, gb, ns, ti + 1, ntiles, TILE);
+    }
+    t = next_live_tile(a.src_live, gb, ns, t + 1, ntiles, TILE);
   }
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    const long long t = t0 + threadIdx.x + r * THREADS;
-    if (t >= a.ion.n_ions) continue;
-    double* o = a.scratch + 8 * t;
+    const long long tt = t0 + threadIdx.x + r * THREADS;
+    if (tt >= a.ion.n_ions) continue;
+    double* o = a.scratch + 8 * tt;
     o[0] = -(static_cast<double>(acc.sx[r]) - acc.cx[r]);
     o[1] = -(static_cast<double>(acc.sy[r]) - acc.cy[r]);
     o[2] = -(static_cast<double>(acc.sz[r]) - acc.cz[r]);
-#pragma unroll
-    for (int k = 0; k < 5; ++k) o[3 + k] = mom[r][k];
+    o[3] = mw[r];
+    o[4] = mx[r];
+    o[5] = my[r];
+    o[6] = mz[r];
+    o[7] = mq[r];
   }
 }
 
@@ -218,6 +272,9 @@ __global__ void __launch_bounds__(256) k_ion_decide(const IonArgs a) {
   a.kind[e] = 1;
   cur[e] = make_float4(static_cast<float>(X), static_cast<float>(Y), static_cast<float>(Z),
                        static_cast<float>(-kc_w));
+  if (a.vel)
+    a.vel[e] = make_float4(static_cast<float>(a.ux[i]), static_cast<float>(a.uy[i]),
+                           static_cast<float>(a.uz[i]), static_cast<float>(a.w[i]));
   if (a.src_live) {
     a.src_live[e / kLiveGroup] = 1;
     a.tgt_live[e / kLiveGroup] = 1;
@@ -245,7 +302,7 @@ __global__ void k_live_init(const float4* posq0, const float4* posq1, const unsi
 }
 
 constexpr int kIonThreads = 64;
-constexpr int kIonR = 1;
+constexpr int kIonR = 2;
 constexpr int kIonTile = 512;
 
 }  // namespace

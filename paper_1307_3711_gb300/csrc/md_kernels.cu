@@ -59,6 +59,9 @@ __global__ void k_upload(const UploadArgs a) {
   const float4 p = make_float4(static_cast<float>(X), static_cast<float>(Y), static_cast<float>(Z), q);
   const long long step = __ldcg(a.step);
   if (step & 1) a.posq1[i] = p; else a.posq0[i] = p;
+  if (a.vel)
+    a.vel[i] = make_float4(static_cast<float>(a.hu[3 * k]), static_cast<float>(a.hu[3 * k + 1]),
+                           static_cast<float>(a.hu[3 * k + 2]), static_cast<float>(a.hw[k]));
 }
 
 __global__ void k_download(const DownloadArgs a) {  const long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;

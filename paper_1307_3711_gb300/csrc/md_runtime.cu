@@ -112,6 +112,7 @@ struct md_ctx {
   double* d_ion_nu = nullptr;          // [sum n_ions] surrogate rates (-1: plain)
   unsigned char* d_src_live = nullptr; // liveness flags per kLiveGroup records
   unsigned char* d_tgt_live = nullptr;
+  float4* d_vel = nullptr;             // FP32 (ux, uy, uz, w) per record
   float* d_mlp = nullptr;              // surrogate parameters (device), if set
 };
 
@@ -242,6 +243,7 @@ md::StepArgs step_args(md_ctx* c) {
   a.n_total = c->n_total;
   a.src_live = c->d_src_live;
   a.tgt_live = c->d_tgt_live;
+  a.vel = c->d_vel;
   return a;
 }
 
@@ -425,6 +427,7 @@ md::IonArgs ion_args(md_ctx* c, int ci, int force) {
   a.mlp = c->d_mlp;
   a.src_live = c->d_src_live;
   a.tgt_live = c->d_tgt_live;
+  a.vel = c->d_vel;
   return a;
 }
 
@@ -512,6 +515,7 @@ void free_ctx(md_ctx* c) {
   cudaFree(c->d_ion_nu);
   cudaFree(c->d_src_live);
   cudaFree(c->d_tgt_live);
+  cudaFree(c->d_vel);
   cudaFree(c->d_mlp);
   if (c->h_raw) cudaFreeHost(c->h_raw);
   if (c->h_diag) cudaFreeHost(c->h_diag);
@@ -556,6 +560,7 @@ md_status upload_cluster(md_ctx* c, int ci, const md_particles& p) {
   a.zq = c->d_z;
   a.kind = c->d_kind;
   a.step = c->d_step;
+  a.vel = c->d_vel;
   MD_CUDA(md::launch_upload(a, c->stream));
   if (c->d_src_live)
     MD_CUDA(md::launch_live_init(c->d_posq[0], c->d_posq[1], c->d_kind, c->d_step, c->n_total,
@@ -731,6 +736,9 @@ md_status md_init(md_ctx** out, const md_config* cfgs, int32_t n_clusters,
     if (dev_alloc(&c->d_src_live, groups) != cudaSuccess ||
         dev_alloc(&c->d_tgt_live, groups) != cudaSuccess)
       return bail(fail(MD_ERR_OOM, "liveness flags"));
+    if (dev_alloc(&c->d_vel, N) != cudaSuccess)
+      return bail(fail(MD_ERR_OOM, "velocity stream"));
+    cudaMemsetAsync(c->d_vel, 0, N * sizeof(float4), c->stream);
     cudaMemsetAsync(c->d_ion_out, 0, sizeof(double) * 4 * sum_ion, c->stream);
     cudaMemsetAsync(c->d_ion_fired, 0, sum_ion, c->stream);
   }
@@ -1090,6 +1098,7 @@ md_status md_autotune(md_ctx* c, int32_t steps, double* times_ms, int32_t cap) {
     bufs.push_back({c->d_src_live, G, nullptr});
     bufs.push_back({c->d_tgt_live, G, nullptr});
   }
+  if (c->d_vel) bufs.push_back({c->d_vel, N * sizeof(float4), nullptr});
   auto release = [&]() {
     for (auto& b : bufs) cudaFree(b.copy);
   };

@@ -74,6 +74,9 @@ struct StepArgs {
   // src_live = some record carries charge, tgt_live = some record is active
   const unsigned char* src_live;
   const unsigned char* tgt_live;
+  // FP32 copy (ux, uy, uz, w) of every record's u and weight, read by the
+  // ionization pass for the local electron moments (nullptr: not kept)
+  float4* vel;
 };
 
 // Arguments of the ionization kernels of one cluster.
@@ -96,13 +99,15 @@ struct IonArgs {
   const long long* step;
   int* err;
   int force;          // 1: run regardless of ionize_every
-  double* scratch;    // [n_ions][8]: ex, ey, ez, sw, swux, swuy, swuz, swu2
+  double* scratch;    // [n_ions][8]: ex, ey, ez, sw, sw du_x, sw du_y, sw du_z, sw du^2
+                      // (du = u - the first local electron's u: same variance)
   double* out;        // [n_ions][4]: |E|, ne (cm^-3), Te (eV), P
   double* nu;         // [n_ions]: rate from the surrogate, or -1 (use the plain rate)
   unsigned char* fired;  // [n_ions]
   const float* mlp;   // surrogate weights (rate_model 2) or nullptr
   unsigned char* src_live;  // liveness flags (set when a record becomes charged / active)
   unsigned char* tgt_live;
+  float4* vel;        // FP32 (ux, uy, uz, w) per record
 };
 
 struct FieldArgs {
@@ -168,6 +173,7 @@ struct UploadArgs {
   int* zq;
   unsigned char* kind;
   const long long* step;
+  float4* vel;        // FP32 (ux, uy, uz, w) or nullptr
 };
 
 struct DownloadArgs {

@@ -90,7 +90,8 @@ def test_ionization_decisions_bit_exact_with_oracle(md):
 
 def test_ionization_inputs_match_oracle(md):
     """The GPU's field magnitude at the ions agrees with the FP64 oracle to the
-    FP32 field tolerance; with no electrons yet the local moments vanish."""
+    FP32 field tolerance, the local electron density exactly and the local
+    temperature to FP32 rounding."""
     c, kw = ar_case(n_atoms=800)
     n = c.n_ions
     # pre-ionize half the atoms so that the field and moments are non-trivial
@@ -120,7 +121,9 @@ def test_ionization_inputs_match_oracle(md):
     assert both.sum() > 0.5 * (ne64 > 0).sum()
     same = np.isclose(info["ne"][both], ne64[both], rtol=1e-12)
     assert same.mean() > 0.95
-    np.testing.assert_allclose(info["te"][both][same], te64[both][same], rtol=1e-9, atol=1e-9)
+    # the GPU sums the moments in FP32 about the first local electron's u:
+    # single-precision rounding of a few hundred terms, no cancellation
+    np.testing.assert_allclose(info["te"][both][same], te64[both][same], rtol=2e-5, atol=1e-6)
 
 
 def test_ionization_in_steps_conserves_charge(md):
@@ -166,3 +169,42 @@ def test_dead_tiles_skipped_and_autotune_restores_ionizing_state(md):
             res.append(ctx.get_particles(0))
     assert np.array_equal(res[0].z, res[1].z) and np.array_equal(res[0].x, res[1].x)
     assert res[0].z[:2000].sum() > 0
+
+
+def test_ionizing_steps_follow_oracle(md):
+    """md_step with a pass before every step, at the density and pulse of the
+    ionizing benchmark: at each step the pass sees the same |E| as the FP64
+    oracle on the GPU's own state and takes the oracle's decisions, and the
+    charge states keep climbing past the first pass."""
+    n = 2000
+    lam = 0.806
+    c = synth.make_cluster(3, n, 0, synth.nm_to_len(8.0 * (n / 200000) ** (1 / 3), lam), 0,
+                           AR["mass"], n_electron_slots=8 * n)
+    rw = synth.nm_to_len(AR["r_w_nm"], lam)
+    tau = synth.sin2_length_from_fwhm(synth.fs_to_time(100.0, lam))
+    t0 = np.floor(tau / 2 / np.pi) * np.pi + 0.5 * np.pi - 0.3
+    eps = synth.nm_to_len(0.1, lam)
+    kw = dict(a0=0.0617, tau=tau, t0=t0, dt=0.02, softening=eps, envelope=synth.ENV_SIN2,
+              lambda_um=lam, rate_model=1, ionize_every=1, zmax=8, n_ions=n, slot_base=n,
+              seed=5, r_loc=3 * rw, r_create=rw, species=AR)
+    p = oracle.make_params(a0=kw["a0"], tau=tau, t0=t0, dt=kw["dt"], eps=eps,
+                           env=synth.ENV_SIN2, lambda_um=lam)
+    with md.Context([md.make_config(**kw)], [md.HostParticles.from_cluster(c)]) as ctx:
+        for k in range(6):
+            g = ctx.get_particles(0)
+            st = oracle.State(g.x, g.u, g.z, g.mass, g.w, (g.kind != md.KIND_INACTIVE)
+                              .astype(np.uint8), step=ctx.step_index())
+            z0 = st.z[:n].copy()
+            fired_ref, amag_ref, ne_ref, te_ref = oracle.ionize_pass(
+                st, p, AR, n, n, 8, kw["seed"], kw["dt"], kw["r_loc"], kw["r_create"], lam,
+                nthreads=os.cpu_count() or 1)
+            ctx.step(1)
+            info = ctx.ionization(0)
+            rel = np.abs(info["emag"] - amag_ref) / np.sqrt(np.mean(amag_ref ** 2))
+            print(k, "fired gpu", int(info["fired"].sum()), "oracle", int(fired_ref.sum()),
+                  "emag rel p99 %.3g" % np.percentile(rel, 99),
+                  "z hist", np.bincount(z0, minlength=9)[:9])
+            assert np.percentile(rel, 99) < 2e-5, k
+            agree = info["fired"].astype(bool) == fired_ref.astype(bool)
+            assert agree.mean() > 0.995, k
+    assert np.bincount(st.z[:n], minlength=9)[2:].sum() > 0.3 * n
