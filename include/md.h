@@ -94,8 +94,9 @@ typedef struct {
     int32_t zmax;         /* highest charge state, 1..16 */
     int32_t n_ions;       /* records [0, n_ions) are the atoms/ions that can ionize */
     int32_t reserved;     /* must be 0 */
-    int64_t slot_base;    /* the electron freed from ion i at charge z becomes record
-                             slot_base + z * n_ions + i (INACTIVE until then) */
+    int64_t slot_base;    /* records [slot_base, slot_base + zmax n_ions) are electron
+                             slots (INACTIVE until used); freed electrons fill them
+                             densely, after the last active one (see md_ionize) */
     uint64_t seed;        /* Philox key */
     double r_loc;         /* local electron moments from electrons within r_loc of the ion */
     double r_create;      /* new electron uniform in the ball of this radius around the ion */
@@ -206,9 +207,14 @@ md_status md_get_fields(md_ctx *ctx, int32_t cluster, double *e, double *phi);
  * r_loc (density in cm^-3, temperature in eV), the total rate (static ADK +
  * Lotz, or the surrogate), P = 1 - exp(-nu dt_ion), alpha from
  * Philox4x32-10(counter = (i, step lo, step hi, 0), key = seed); if
- * alpha < P the ion's charge rises by one and slot_base + z n_ions + i
- * becomes an electron at x_i + r (r uniform in the ball of radius r_create,
- * from Philox words 1-3) with the ion's u and weight.  Asynchronous. */
+ * alpha < P the ion's charge rises by one and it frees an electron at x_i + r
+ * (r uniform in the ball of radius r_create, from Philox words 1-3) with the
+ * ion's u and weight.  The electrons freed in one pass take the next free
+ * slots in the order of their ions' indices: the first goes to the record
+ * after the last active slot, so the active slots stay one dense block.
+ * md_init and md_set_particles reject (MD_ERR_ARG) a state in which the
+ * ionizations still possible (sum over ions of zmax - z) do not fit after its
+ * last active slot.  Asynchronous. */
 md_status md_ionize(md_ctx *ctx);
 
 /* md_get_ionization: per-ion results of the last pass of cluster `cluster`
@@ -286,9 +292,12 @@ md_status md_coulomb_field_device_noalloc(const void *src, int64_t ns, const voi
 
 /* ---- learned rate surrogate ------------------------------------------------
  * Not from the paper: a 4 -> 64 -> 64 -> 8 MLP (SiLU) standing in for the
- * per-ion rate evaluation of the ionization pass, with BF16 weights and FP32
- * accumulation on the tensor cores.  Features: ((log10 max(|E|,1e-6)+1.5)/1.5,
- * z/8, (log10 max(n_e,1e15)-19.5)/4.5, (log10 max(T_e,0.1)-1.5)/2.5); output
+ * per-ion rate evaluation of the ionization pass.  The hidden layers run on
+ * the tensor cores with BF16 weights and activations and FP32 accumulation;
+ * the output layer is an FP32 dot product.  Features of an ion of charge z:
+ * ((log10(F/F0)+1.4)/1.5, z/8, (log10 max(n_e,1e15)-19.5)/4.5,
+ * (log10(max(T_e,0.1)/Ip)+0.2)/3) with F = max(|E|,1e-6) in atomic units,
+ * Ip = ip_ev[z], F0 = (2 Ip/E_h)^(3/2); output
  * y_k ~ (log10(nu_k + 1e-12)+6)/6 for the step k -> k+1, inverted as
  * nu = max(10^(6y-6) - 1e-12, 0) (rates below 1e-12 per unit time never
  * ionize: P < 1e-13 per pass).  Parameters:
@@ -321,7 +330,7 @@ typedef struct {
 
 /* md_mlp_train: draws n_samples of (|E|, z, n_e, T_e) log-uniform over the
  * domain with Philox, labels them with the library's FP64 plain rate (static
- * ADK + Lotz), trains the surrogate on the GPU (BF16 forward/backward kernels,
+ * ADK + Lotz), trains the surrogate on the GPU (its own forward/backward kernels,
  * deterministic gradient reduction, Adam) and writes the FP32 parameters to
  * params_out (host, 5000 floats).  Allocates and frees its own device
  * buffers.  Synchronous on `stream`. */
@@ -330,7 +339,9 @@ md_status md_mlp_train(const md_mlp_train_config *cfg, float *params_out, md_mlp
 
 /* md_set_rate_mlp: installs surrogate parameters (host, 5000 floats) in the
  * context; clusters with rate_model MD_RATES_MLP then use it for ions inside
- * the domain of `domain` and the plain rates outside. */
+ * the domain of `domain` and the plain rates outside.  `domain` is the
+ * training configuration: MD_ERR_ARG if its species table (ip_ev, q_outer
+ * below zmax) or wavelength differs from such a cluster's. */
 md_status md_set_rate_mlp(md_ctx *ctx, const float *params, const md_mlp_train_config *domain);
 
 /* Device-buffer entry points of the surrogate (all pointers device memory):

@@ -105,7 +105,7 @@ def lib():
             L.mo_nparam.restype = i
             L.mo_nparam.argtypes = []
             L.mo_features.restype = None
-            L.mo_features.argtypes = [d, i, d, d, p]
+            L.mo_features.argtypes = [d, i, d, d, d, d, p]
             L.mo_target.restype = d
             L.mo_target.argtypes = [d]
             L.mo_rate_from_output.restype = d
@@ -352,14 +352,23 @@ def decide(ids, z, a_mag, ne, te, species, zmax, seed, step, dt_ion, r_create,
     return z, fired, off, prob
 
 
+def next_free_slot(state: "State", slot_base, n_ion, zmax):
+    """The record after the last active one in the electron-slot region
+    [slot_base, slot_base + zmax n_ion), or slot_base if none is active."""
+    region = state.active[slot_base:slot_base + zmax * n_ion]
+    act = np.nonzero(region)[0]
+    return slot_base + (int(act[-1]) + 1 if act.size else 0)
+
+
 def ionize_pass(state: "State", params: Params, species, n_ion, slot_base, zmax, seed, dt_ion,
                 r_loc, r_create, lambda_um=0.8, nthreads=1):
     """One ionization pass at step state.step (Sec. II): for each ion record
     i < n_ion (id = i) of charge z < zmax, the field |E_coulomb + a(t_n)| at
     x_i, the local electron moments, the Philox decision; an ionizing ion gets
-    z + 1 and activates electron slot slot_base + z_old * n_ion + i at
-    x_i + offset with the ion's u and weight.  Returns (fired, field_mag, ne,
-    te) of the ions; modifies state."""
+    z + 1 and frees an electron at x_i + offset with the ion's u and weight.
+    The electrons freed in one pass take the next free slots (next_free_slot)
+    in the order of their ions' indices.  Returns (fired, field_mag, ne, te)
+    of the ions; modifies state."""
     ions = np.arange(n_ion, dtype=np.int64)
     q = state.q()
     e = coulomb_field(state.x[:n_ion], state.x, q, params.eps, params.kc, self_idx=ions,
@@ -371,15 +380,16 @@ def ionize_pass(state: "State", params: Params, species, n_ion, slot_base, zmax,
     z_old = state.z[:n_ion].copy()
     z_new, fired, off, _ = decide(ions, z_old, amag, ne, te, species, zmax, seed, state.step,
                                   dt_ion, r_create, lambda_um)
+    slot = next_free_slot(state, slot_base, n_ion, zmax)
     for i in np.nonzero(fired)[0]:
-        slot = slot_base + z_old[i] * n_ion + i
-        assert state.active[slot] == 0
+        assert slot < slot_base + zmax * n_ion and state.active[slot] == 0
         state.x[slot] = state.x[i] + off[i]
         state.u[slot] = state.u[i]
         state.z[slot] = -1
         state.mass[slot] = 1.0
         state.w[slot] = state.w[i]
         state.active[slot] = 1
+        slot += 1
     state.z[:n_ion] = z_new
     return fired, amag, ne, te
 
@@ -391,9 +401,11 @@ def mlp_nparam():
     return lib().mo_nparam()
 
 
-def mlp_features(e_mag, z, ne, te):
+def mlp_features(e_mag, z, ne, te, ip_ev, lambda_um=0.8):
+    """Surrogate inputs of one ion; ip_ev = ionization energy of charge z."""
     f = np.zeros(4)
-    lib().mo_features(float(e_mag), int(z), float(ne), float(te), _ptr(f))
+    lib().mo_features(float(e_mag), int(z), float(ne), float(te), float(ip_ev),
+                      float(lambda_um), _ptr(f))
     return f
 
 

@@ -4,9 +4,14 @@
  *
  * The surrogate is not from the paper: it stands in for the per-ion rate
  * evaluation of Sec. II (nu_total = nu_ofi + nu_ci).  Definition:
- *   features  f = ((log10 max(|E|, 1e-6) + 1.5) / 1.5,  z / 8,
+ *   features  f = ((log10(F / F0) + 1.4) / 1.5,  z / 8,
  *                  (log10 max(n_e, 1e15) - 19.5) / 4.5,
- *                  (log10 max(T_e, 0.1) - 1.5) / 2.5)
+ *                  (log10(max(T_e, 0.1) / Ip) + 0.2) / 3)
+ *             with F = max(|E|, 1e-6) in atomic units of field, Ip the
+ *             ionization energy of charge state z and F0 = (2 Ip / E_h)^(3/2)
+ *             (the field scale of the tunnel exponent), so that the field and
+ *             temperature enter relative to the scales of the rate of the
+ *             charge state at hand;
  *   network   h1 = silu(W1 f + b1)    (64)
  *             h2 = silu(W2 h1 + b2)   (64)
  *             y  = W3 h2 + b3          (8)
@@ -37,12 +42,23 @@
 
 int mo_nparam(void) { return NPARAM; }
 
-void mo_features(double e_mag, int z, double ne, double te, double f[4])
+/* |E| in the paper's unit a = eE/(m_e omega c) -> atomic units of field:
+ * E = a m_e c omega / e = a (m_e c^2 / e) k, divided by the atomic field. */
+#define MO_ME_C2_EV 510998.95          /* electron rest energy, eV */
+#define MO_HARTREE_EV 27.211386245988  /* Hartree energy, eV */
+#define MO_FIELD_AU 5.14220674763e11   /* atomic unit of field, V/m */
+#define MO_PI 3.14159265358979323846
+
+void mo_features(double e_mag, int z, double ne, double te, double ip_ev, double lambda_um,
+                 double f[4])
 {
-    f[0] = (log10(fmax(e_mag, 1e-6)) + 1.5) / 1.5;
+    double k = 2.0 * MO_PI / (lambda_um * 1e-6);
+    double F = fmax(e_mag, 1e-6) * MO_ME_C2_EV * k / MO_FIELD_AU;
+    double F0 = pow(2.0 * ip_ev / MO_HARTREE_EV, 1.5);
+    f[0] = (log10(F / F0) + 1.4) / 1.5;
     f[1] = z / 8.0;
     f[2] = (log10(fmax(ne, 1e15)) - 19.5) / 4.5;
-    f[3] = (log10(fmax(te, 0.1)) - 1.5) / 2.5;
+    f[3] = (log10(fmax(te, 0.1) / ip_ev) + 0.2) / 3.0;
 }
 
 double mo_target(double nu) { return (log10(fmax(nu, 0.0) + 1e-12) + 6.0) / 6.0; }

@@ -8,8 +8,11 @@
 //                 the electrons within r_loc (gathered from the FP64 state);
 //   k_ion_decide  per ion: laser field at t_n, |E|, local density and
 //                 temperature, total rate (static ADK + Lotz, or the learned
-//                 surrogate), P = 1 - exp(-nu dt_ion), a Philox4x32-10 draw and
-//                 the charge update with activation of its electron slot.
+//                 surrogate), P = 1 - exp(-nu dt_ion) and a Philox4x32-10 draw;
+//   k_ion_apply   one CTA per cluster: the ions that fired, in index order,
+//                 get charge z + 1 and free their electrons into the next free
+//                 slots (an exclusive scan of the fired flags gives each its
+//                 slot), so the active slots stay one dense block.
 // The decision runs after the whole field pass, so no charge changes while
 // any other ion's field is being summed.  Rates are FP64, as on the host.
 #include <cmath>
@@ -219,8 +222,8 @@ __global__ void __launch_bounds__(256) k_ion_inputs(const IonArgs a) {
   a.nu[t] = -1.0;
 }
 
-// Per ion: rate (surrogate if it set one, else static ADK + Lotz), P, Philox
-// draw, charge update and electron slot activation.
+// Per ion: rate (surrogate if it set one, else static ADK + Lotz), P and the
+// Philox draw; sets fired[t].  No state changes here.
 __global__ void __launch_bounds__(256) k_ion_decide(const IonArgs a) {
   const long long step = __ldcg(a.step);
   if (!pass_active(a, step)) return;
@@ -242,8 +245,16 @@ __global__ void __launch_bounds__(256) k_ion_decide(const IonArgs a) {
                  static_cast<uint32_t>(static_cast<unsigned long long>(step) >> 32), 0u),
       make_uint2(static_cast<uint32_t>(a.ion.seed), static_cast<uint32_t>(a.ion.seed >> 32)));
   const double alpha = (static_cast<double>(wv.x) + 1.0) * (1.0 / 4294967296.0);
-  if (!(alpha < P)) return;
-  a.fired[t] = 1;
+  if (alpha < P) a.fired[t] = 1;
+}
+
+// Ionization of ion t (cluster-relative) freeing its electron into record e
+// (cluster-relative): charge update, the electron uniform in the ball of
+// radius r_create around the ion (Philox words 1-3 of the decision's draw)
+// with the ion's u and weight, liveness flags.
+__device__ void apply_one(const IonArgs& a, long long step, long long t, long long e_rel) {
+  const long long i = a.c.off + t;
+  const int z = a.zq[i];
   const int z1 = z + 1;
   const double kc_w = a.ion.kc * a.w[i];
   float4* cur = (step & 1) ? a.posq1 : a.posq0;
@@ -251,13 +262,16 @@ __global__ void __launch_bounds__(256) k_ion_decide(const IonArgs a) {
   a.qm[i] = static_cast<float>(z1 / a.mass[i]);
   cur[i].w = static_cast<float>(kc_w * z1);
   if (a.src_live) a.src_live[i / kLiveGroup] = 1;
-  // the freed electron: uniform in the ball of radius r_create around the ion
+  const uint4 wv = philox4x32_10(
+      make_uint4(static_cast<uint32_t>(t), static_cast<uint32_t>(step),
+                 static_cast<uint32_t>(static_cast<unsigned long long>(step) >> 32), 0u),
+      make_uint2(static_cast<uint32_t>(a.ion.seed), static_cast<uint32_t>(a.ion.seed >> 32)));
   const double u1 = (static_cast<double>(wv.y) + 0.5) * (1.0 / 4294967296.0);
   const double u2 = (static_cast<double>(wv.z) + 0.5) * (1.0 / 4294967296.0);
   const double u3 = (static_cast<double>(wv.w) + 0.5) * (1.0 / 4294967296.0);
   const double ct = 2.0 * u1 - 1.0, st = sqrt(fmax(0.0, 1.0 - ct * ct));
   const double ph = 2.0 * kPi * u2, rr = a.ion.r_create * cbrt(u3);
-  const long long e = a.c.off + a.ion.slot_base + static_cast<long long>(z) * a.ion.n_ions + t;
+  const long long e = a.c.off + e_rel;
   const double X = a.x[i] + rr * st * cos(ph), Y = a.y[i] + rr * st * sin(ph), Z = a.z[i] + rr * ct;
   a.x[e] = X;
   a.y[e] = Y;
@@ -279,6 +293,49 @@ __global__ void __launch_bounds__(256) k_ion_decide(const IonArgs a) {
     a.src_live[e / kLiveGroup] = 1;
     a.tgt_live[e / kLiveGroup] = 1;
   }
+}
+
+constexpr int kApplyThreads = 1024;
+
+// One CTA: thread k takes a contiguous chunk of ions; an exclusive scan of the
+// per-chunk fired counts gives each fired ion, in index order, the slot
+// *next_slot + (fired ions before it); *next_slot then advances past them.
+__global__ void __launch_bounds__(kApplyThreads) k_ion_apply(const IonArgs a) {
+  __shared__ long long s_warp[kApplyThreads / 32];
+  __shared__ long long s_base;
+  const long long step = __ldcg(a.step);
+  if (!pass_active(a, step)) return;
+  const long long n = a.ion.n_ions;
+  const long long chunk = (n + kApplyThreads - 1) / kApplyThreads;
+  const long long b = chunk * threadIdx.x;
+  const long long e = b + chunk < n ? b + chunk : n;
+  long long cnt = 0;
+  for (long long t = b; t < e; ++t) cnt += a.fired[t];
+  // block-wide exclusive scan of cnt
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  long long incl = cnt;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const long long v = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += v;
+  }
+  if (lane == 31) s_warp[warp] = incl;
+  if (threadIdx.x == 0) s_base = *a.next_slot;
+  __syncthreads();
+  if (warp == 0) {
+    long long w = lane < kApplyThreads / 32 ? s_warp[lane] : 0;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const long long v = __shfl_up_sync(0xffffffffu, w, d);
+      if (lane >= d) w += v;
+    }
+    if (lane < kApplyThreads / 32) s_warp[lane] = w;  // inclusive over warps
+  }
+  __syncthreads();
+  long long slot = s_base + (warp > 0 ? s_warp[warp - 1] : 0) + (incl - cnt);
+  for (long long t = b; t < e; ++t)
+    if (a.fired[t]) apply_one(a, step, t, slot++);
+  if (threadIdx.x == kApplyThreads - 1) *a.next_slot = s_base + s_warp[kApplyThreads / 32 - 1];
 }
 
 // Liveness flags from the current records: a group of kLiveGroup records is
@@ -330,6 +387,8 @@ cudaError_t launch_ion_pass(const IonArgs& a, cudaStream_t s) {
     if ((e = launch_ion_mlp(a, s)) != cudaSuccess) return e;
   }
   k_ion_decide<<<g2, 256, 0, s>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_ion_apply<<<1, kApplyThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -1,17 +1,22 @@
 // md_mlp.cu -- learned surrogate of the ionization rate (not from the paper:
 // it stands in for the per-ion rate evaluation nu_ofi + nu_ci of Sec. II).
 //
-// Network 4 -> 64 -> 64 -> 8 (SiLU hidden layers), BF16 weights and
-// activations, FP32 accumulation on the tensor cores with
-// mma.sync.m16n8k16.row.col.f32.bf16.bf16.f32: one warp carries 16 samples
-// through all three layers without leaving registers, because the C fragment
-// of an m16n8 tile (rows g, g+8; columns 2t, 2t+1) is exactly the A fragment
-// slice of the next layer's k-step.  At width 64 the layer is a handful of
+// Network 4 -> 64 -> 64 -> 8 (SiLU hidden layers).  The two hidden layers run
+// on the tensor cores with BF16 weights and activations and FP32 accumulation
+// (mma.sync.m16n8k16.row.col.f32.bf16.bf16.f32): one warp carries 16 samples
+// through both without leaving registers, because the C fragment of an m16n8
+// tile (rows g, g+8; columns 2t, 2t+1) is exactly the A fragment slice of the
+// next layer's k-step.  The output layer (8 x 64) is a per-sample FP32 dot
+// product on the CUDA cores from the FP32 hidden activations, finished by a
+// shuffle reduction over the 4 lanes of a quad: BF16 rounding of the last
+// layer alone doubles the error of the fitted log-rate, and an ion needs only
+// the output row of its own charge state.  At width 64 a layer is a handful of
 // mma instructions, so the tcgen05/TMEM machinery would cost more than the
 // work it carries.
 //
-// Features f = ((log10 max(|E|,1e-6) + 1.5)/1.5, z/8,
-//               (log10 max(n_e,1e15) - 19.5)/4.5, (log10 max(T_e,0.1) - 1.5)/2.5);
+// Features f = ((log10(F/F0) + 1.4)/1.5, z/8, (log10 max(n_e,1e15) - 19.5)/4.5,
+//               (log10(max(T_e,0.1)/Ip) + 0.2)/3), F = max(|E|,1e-6) in atomic
+// units, Ip the ionization energy of charge state z, F0 = (2 Ip/E_h)^(3/2);
 // output y_k ~ (log10(nu_k + 1e-12) + 6)/6 for z = k -> k+1, inverted as
 // nu = max(10^(6y - 6) - 1e-12, 0): rates below 1e-12 per unit time (P < 1e-13
 // per pass) never ionize, and the additive floor keeps the target smooth.
@@ -19,8 +24,9 @@
 //
 // Training: samples (|E|, z, n_e, T_e) drawn log-uniformly by Philox and
 // labelled by the library's own FP64 plain rate; minibatch forward/backward
-// (activation gradients on the tensor cores, weight gradients accumulated per
-// CTA in FP32 in a fixed order), then a deterministic reduction and Adam.
+// (hidden-layer activation gradients on the tensor cores, weight gradients
+// accumulated per CTA in FP32 in a fixed order), then a deterministic
+// reduction and Adam.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -61,17 +67,26 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1
 
 __device__ __forceinline__ float silu(float a) { return a / (1.0f + __expf(-a)); }
 
+// Element o of an 8-vector held in registers, without dynamic indexing
+// (which would move the whole fragment state to local memory).
+__device__ __forceinline__ float pick8(const float (&v)[8], int o) {
+  float r = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) r = (k == o) ? v[k] : r;
+  return r;
+}
+
 __device__ __forceinline__ float dsilu(float a) {
   const float s = 1.0f / (1.0f + __expf(-a));
   return s * (1.0f + a * (1.0f - s));
 }
 
-// Weights of one CTA in shared memory: BF16 matrices (W1 padded to K = 16),
-// FP32 biases.
+// Weights of one CTA in shared memory: BF16 hidden-layer matrices (W1 padded
+// to K = 16), FP32 output layer and biases.
 struct MlpWeights {
   alignas(16) __nv_bfloat16 w1[kNH][16];
   alignas(16) __nv_bfloat16 w2[kNH][kNH];
-  alignas(16) __nv_bfloat16 w3[kNO][kNH];
+  alignas(16) float w3[kNO][kNH];
   float b1[kNH], b2[kNH], b3[kNO];
 };
 
@@ -83,7 +98,7 @@ __device__ void load_weights(const float* __restrict__ p, MlpWeights& w) {
   for (int e = threadIdx.x; e < kNH * kNH; e += blockDim.x)
     w.w2[e >> 6][e & 63] = __float2bfloat16_rn(p[kOffW2 + e]);
   for (int e = threadIdx.x; e < kNO * kNH; e += blockDim.x)
-    w.w3[e >> 6][e & 63] = __float2bfloat16_rn(p[kOffW3 + e]);
+    w.w3[e >> 6][e & 63] = p[kOffW3 + e];
   for (int e = threadIdx.x; e < kNH; e += blockDim.x) {
     w.b1[e] = p[kOffB1 + e];
     w.b2[e] = p[kOffB2 + e];
@@ -105,7 +120,7 @@ struct Fwd {
   float a1[8][4];     // layer-1 pre-activations, C layout per n-tile
   float a2[8][4];     // layer-2 pre-activations
   uint32_t h1[4][4];  // silu(a1) as BF16 A fragments of layer 2 (per k-step)
-  uint32_t h2[4][4];  // silu(a2) as BF16 A fragments of layer 3
+  float yall[2][kNO]; // all outputs of rows g and g+8 (every lane of the quad)
   float y[4];         // outputs: (g, 2t), (g, 2t+1), (g+8, 2t), (g+8, 2t+1)
 };
 
@@ -121,8 +136,9 @@ __device__ __forceinline__ void c_to_a(const float (&c)[8][4], uint32_t (&a)[4][
 }
 
 // x: features of rows g and g+8 of this warp's tile (x_lo, x_hi: 4 values).
-__device__ __forceinline__ void forward(const MlpWeights& w, const float (&xg)[4],
-                                        const float (&xg8)[4], Fwd& f) {
+// Hidden layers only: a1, h1, a2.
+__device__ __forceinline__ void forward_hidden(const MlpWeights& w, const float (&xg)[4],
+                                               const float (&xg8)[4], Fwd& f) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   // layer 1: A = features padded to K = 16 (columns 0..3 real)
   const uint32_t x0 = t < 2 ? pack_bf16(xg[2 * t], xg[2 * t + 1]) : 0u;
@@ -145,20 +161,80 @@ __device__ __forceinline__ void forward(const MlpWeights& w, const float (&xg)[4
                ld_pair(&w.w2[8 * j + g][16 * kk + 2 * t]),
                ld_pair(&w.w2[8 * j + g][16 * kk + 8 + 2 * t]));
   }
-  c_to_a(f.a2, f.h2);
-  // layer 3 (one n-tile of 8 outputs)
-  f.y[0] = w.b3[2 * t]; f.y[1] = w.b3[2 * t + 1]; f.y[2] = f.y[0]; f.y[3] = f.y[1];
-#pragma unroll
-  for (int kk = 0; kk < 4; ++kk)
-    mma_bf16(f.y, f.h2[kk][0], f.h2[kk][1], f.h2[kk][2], f.h2[kk][3],
-             ld_pair(&w.w3[g][16 * kk + 2 * t]), ld_pair(&w.w3[g][16 * kk + 8 + 2 * t]));
 }
 
-__device__ __forceinline__ void features_of(double emag, int z, double ne, double te, float* f) {
-  f[0] = static_cast<float>((log10(fmax(emag, 1e-6)) + 1.5) / 1.5);
-  f[1] = static_cast<float>(z / 8.0);
-  f[2] = static_cast<float>((log10(fmax(ne, 1e15)) - 19.5) / 4.5);
-  f[3] = static_cast<float>((log10(fmax(te, 0.1)) - 1.5) / 2.5);
+// All 8 outputs of rows g and g+8 (every lane of the quad gets them).
+__device__ __forceinline__ void forward(const MlpWeights& w, const float (&xg)[4],
+                                        const float (&xg8)[4], Fwd& f) {
+  forward_hidden(w, xg, xg8, f);
+  const int t = threadIdx.x & 3;
+  // layer 3 in FP32: partial dot products over this lane's 16 columns of
+  // rows g and g+8, summed over the quad (lanes t = 0..3)
+#pragma unroll
+  for (int o = 0; o < kNO; ++o) {
+    float p0 = 0.0f, p1 = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float w0 = w.w3[o][8 * j + 2 * t], w1 = w.w3[o][8 * j + 2 * t + 1];
+      p0 = fmaf(w0, silu(f.a2[j][0]), fmaf(w1, silu(f.a2[j][1]), p0));
+      p1 = fmaf(w0, silu(f.a2[j][2]), fmaf(w1, silu(f.a2[j][3]), p1));
+    }
+    p0 += __shfl_xor_sync(0xffffffffu, p0, 1);
+    p1 += __shfl_xor_sync(0xffffffffu, p1, 1);
+    p0 += __shfl_xor_sync(0xffffffffu, p0, 2);
+    p1 += __shfl_xor_sync(0xffffffffu, p1, 2);
+    f.yall[0][o] = p0 + w.b3[o];
+    f.yall[1][o] = p1 + w.b3[o];
+  }
+#pragma unroll
+  for (int o = 0; o < kNO; ++o) {
+    if (o == 2 * t) { f.y[0] = f.yall[0][o]; f.y[2] = f.yall[1][o]; }
+    if (o == 2 * t + 1) { f.y[1] = f.yall[0][o]; f.y[3] = f.yall[1][o]; }
+  }
+}
+
+// Surrogate inputs of an ion of charge z: field relative to the tunnelling
+// scale F0 = (2 Ip/E_h)^(3/2) of that charge state (atomic units), density,
+// temperature relative to Ip.  FP32 (the first layer rounds them to BF16).
+__device__ __forceinline__ void features_of(const IonDev& io, double emag, int z, double ne,
+                                            double te, float* f) {
+  const float ip = static_cast<float>(io.ip_ev[z]);
+  const float fau = static_cast<float>(rate::kMeC2Ev * io.k_si / rate::kFieldAu);
+  const float lf = log10f(fmaxf(static_cast<float>(emag), 1e-6f)) + log10f(fau);
+  const float lf0 = 1.5f * log10f(2.0f * ip / static_cast<float>(rate::kHartreeEv));
+  f[0] = (lf - lf0 + 1.4f) / 1.5f;
+  f[1] = static_cast<float>(z) / 8.0f;
+  f[2] = (log10f(fmaxf(static_cast<float>(ne), 1e15f)) - 19.5f) / 4.5f;
+  f[3] = (log10f(fmaxf(static_cast<float>(te), 0.1f) / ip) + 0.2f) / 3.0f;
+}
+
+// Rate from the network output: nu = max(10^(6y - 6) - 1e-12, 0), the power
+// in FP32 (the surrogate is good to a few per cent), the floor in FP64.
+__device__ __forceinline__ double rate_of_output(float y) {
+  return fmax(static_cast<double>(exp10f(6.0f * y - 6.0f)) - 1e-12, 0.0);
+}
+
+// Output of the charge state of each row only (rows g and g+8 of the warp's
+// tile): the FP32 dot product of that row of W3, summed over the quad.
+__device__ __forceinline__ void forward_sel(const MlpWeights& w, const float (&xg)[4],
+                                            const float (&xg8)[4], int z0, int z1,
+                                            float (&ysel)[2]) {
+  Fwd f;
+  forward_hidden(w, xg, xg8, f);
+  const int t = threadIdx.x & 3;
+  float p0 = 0.0f, p1 = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int c0 = 8 * j + 2 * t;
+    p0 = fmaf(w.w3[z0][c0], silu(f.a2[j][0]), fmaf(w.w3[z0][c0 + 1], silu(f.a2[j][1]), p0));
+    p1 = fmaf(w.w3[z1][c0], silu(f.a2[j][2]), fmaf(w.w3[z1][c0 + 1], silu(f.a2[j][3]), p1));
+  }
+  p0 += __shfl_xor_sync(0xffffffffu, p0, 1);
+  p1 += __shfl_xor_sync(0xffffffffu, p1, 1);
+  p0 += __shfl_xor_sync(0xffffffffu, p0, 2);
+  p1 += __shfl_xor_sync(0xffffffffu, p1, 2);
+  ysel[0] = p0 + w.b3[z0];
+  ysel[1] = p1 + w.b3[z1];
 }
 
 // ------------------------------------------------------------ inference --
@@ -211,31 +287,30 @@ __global__ void __launch_bounds__(32 * kWarps) k_ion_mlp_rates(const IonArgs a) 
       if (s[h] < n) {
         const double* o = a.out + 4 * s[h];
         zs[h] = a.zq[a.c.off + s[h]];
-        features_of(o[0], zs[h] < 0 ? 0 : zs[h], o[1], o[2], x[h]);
+        features_of(a.ion, o[0], zs[h] < 0 ? 0 : (zs[h] < kNO ? zs[h] : kNO - 1), o[1], o[2],
+                    x[h]);
       }
     }
-    Fwd f;
-    forward(w, x[0], x[1], f);
+    float ysel[2];
+    forward_sel(w, x[0], x[1], zs[0] < 0 ? 0 : (zs[0] < kNO ? zs[0] : kNO - 1),
+                zs[1] < 0 ? 0 : (zs[1] < kNO ? zs[1] : kNO - 1), ysel);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      if (s[h] >= n || zs[h] < 0 || zs[h] >= a.ion.zmax) continue;
-      const int col = zs[h];
-      if ((col >> 1) != t) continue;  // the lane holding column z writes
+      if (t != 0 || s[h] >= n || zs[h] < 0 || zs[h] >= a.ion.zmax) continue;
       const double* o = a.out + 4 * s[h];
       const bool inside = o[0] >= a.ion.dom[0] && o[0] <= a.ion.dom[1] &&
                           (o[1] == 0.0 || (o[1] >= a.ion.dom[2] && o[1] <= a.ion.dom[3])) &&
                           (o[1] == 0.0 || (o[2] >= a.ion.dom[4] && o[2] <= a.ion.dom[5]));
       if (!inside) continue;
-      const float yz = f.y[2 * h + (col & 1)];
-      a.nu[s[h]] = fmax(pow(10.0, 6.0 * static_cast<double>(yz) - 6.0) - 1e-12, 0.0);
+      a.nu[s[h]] = rate_of_output(ysel[h]);
     }
   }
 }
 
 // -------------------------------------------------------------- training --
 
-// Per-warp staging for the weight gradients: x, bf16-rounded h1/h2, dy, da1,
-// da2 of 16 samples.
+// Per-warp staging for the weight gradients: x and h1 (BF16-rounded, as the
+// tensor-core layers use them), h2 (FP32), dy, da1, da2 of 16 samples.
 struct WarpStage {
   float x[16][kNI];
   float h1[16][kNH];
@@ -301,16 +376,22 @@ __global__ void __launch_bounds__(32 * kWarps) k_mlp_train(const float* __restri
     if (zg == 2 * t + 1) lsum += (f.y[1] - tg) * (f.y[1] - tg);
     if (zg8 == 2 * t) lsum += (f.y[2] - tg8) * (f.y[2] - tg8);
     if (zg8 == 2 * t + 1) lsum += (f.y[3] - tg8) * (f.y[3] - tg8);
-    // dh2 = dy W3 (K = 8 outputs, padded to 16)
-    const uint32_t dya0 = pack_bf16(dy[0], dy[1]), dya1 = pack_bf16(dy[2], dy[3]);
+    // dh2 = dy W3 in FP32: every lane of the quad has both rows' outputs, so
+    // each forms the gradient of its own 16 columns from the selected row of W3
+    const float dsel0 = (zg >= 0 && zg < kNO) ? coef * (pick8(f.yall[0], zg) - tg) : 0.0f;
+    const float dsel1 = (zg8 >= 0 && zg8 < kNO) ? coef * (pick8(f.yall[1], zg8) - tg8) : 0.0f;
+    const int zr0 = (zg >= 0 && zg < kNO) ? zg : 0, zr1 = (zg8 >= 0 && zg8 < kNO) ? zg8 : 0;
     float dh[8][4];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      dh[j][0] = dh[j][1] = dh[j][2] = dh[j][3] = 0.0f;
-      const uint32_t bb = pair_of(S.w.w3[2 * t][8 * j + g], S.w.w3[2 * t + 1][8 * j + g]);
-      mma_bf16(dh[j], dya0, dya1, 0u, 0u, bb, 0u);
+      const int c0 = 8 * j + 2 * t;
+      dh[j][0] = dsel0 * S.w.w3[zr0][c0];
+      dh[j][1] = dsel0 * S.w.w3[zr0][c0 + 1];
+      dh[j][2] = dsel1 * S.w.w3[zr1][c0];
+      dh[j][3] = dsel1 * S.w.w3[zr1][c0 + 1];
     }
-    // da2 = dh2 * silu'(a2); stage h2 (as used), dy, da2
+    // da2 = dh2 * silu'(a2); stage h2 (FP32, as the output layer uses it), h1
+    // (BF16, as layer 2 uses it), dy, da2
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
 #pragma unroll
@@ -318,10 +399,10 @@ __global__ void __launch_bounds__(32 * kWarps) k_mlp_train(const float* __restri
       const int c0 = 8 * j + 2 * t;
       st.da2[g][c0] = dh[j][0]; st.da2[g][c0 + 1] = dh[j][1];
       st.da2[g + 8][c0] = dh[j][2]; st.da2[g + 8][c0 + 1] = dh[j][3];
-      st.h2[g][c0] = bf16_round(silu(f.a2[j][0]));
-      st.h2[g][c0 + 1] = bf16_round(silu(f.a2[j][1]));
-      st.h2[g + 8][c0] = bf16_round(silu(f.a2[j][2]));
-      st.h2[g + 8][c0 + 1] = bf16_round(silu(f.a2[j][3]));
+      st.h2[g][c0] = silu(f.a2[j][0]);
+      st.h2[g][c0 + 1] = silu(f.a2[j][1]);
+      st.h2[g + 8][c0] = silu(f.a2[j][2]);
+      st.h2[g + 8][c0 + 1] = silu(f.a2[j][3]);
       st.h1[g][c0] = bf16_round(silu(f.a1[j][0]));
       st.h1[g][c0 + 1] = bf16_round(silu(f.a1[j][1]));
       st.h1[g + 8][c0] = bf16_round(silu(f.a1[j][2]));
@@ -423,7 +504,7 @@ __global__ void k_mlp_samples(IonDev io, long long n, unsigned long long seed, f
   const double emag = pow(10.0, le), ne = pow(10.0, ln), te = pow(10.0, lt);
   const int z = static_cast<int>(w.y % static_cast<uint32_t>(io.zmax));
   const double nu = rate::rate_plain(io, emag, z, ne, te);
-  features_of(emag, z, ne, te, feats + 4 * s);
+  features_of(io, emag, z, ne, te, feats + 4 * s);
   zs[s] = z;
   target[s] = static_cast<float>((log10(fmax(nu, 0.0) + 1e-12) + 6.0) / 6.0);
   if (raw) {
@@ -492,22 +573,22 @@ __global__ void __launch_bounds__(32 * kWarps) k_rates_mlp(IonDev io, const floa
     for (int h = 0; h < 2; ++h) {
       z[h] = s[h] < n ? zs[s[h]] : 0;
       x[h][0] = x[h][1] = x[h][2] = x[h][3] = 0.0f;
-      if (s[h] < n) features_of(emag[s[h]], z[h], ne[s[h]], te[s[h]], x[h]);
+      if (s[h] < n)  // out-of-range charges get a valid row here and no surrogate rate below
+        features_of(io, emag[s[h]], z[h] < 0 ? 0 : (z[h] < kNO ? z[h] : kNO - 1), ne[s[h]],
+                    te[s[h]], x[h]);
     }
-    Fwd f;
-    forward(w, x[0], x[1], f);
+    float ysel[2];
+    forward_sel(w, x[0], x[1], z[0] < 0 ? 0 : (z[0] < kNO ? z[0] : kNO - 1),
+                z[1] < 0 ? 0 : (z[1] < kNO ? z[1] : kNO - 1), ysel);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int zc = (z[h] >= 0 && z[h] < kNO) ? z[h] : 0;  // the lane that writes sample h
-      if (s[h] >= n || (zc >> 1) != t) continue;
+      if (t != 0 || s[h] >= n) continue;  // lane t = 0 of the quad writes
       const long long k = s[h];
       const bool inside = z[h] >= 0 && z[h] < io.zmax && emag[k] >= io.dom[0] &&
                           emag[k] <= io.dom[1] &&
                           (ne[k] == 0.0 || (ne[k] >= io.dom[2] && ne[k] <= io.dom[3] &&
                                             te[k] >= io.dom[4] && te[k] <= io.dom[5]));
-      nu[k] = inside ? fmax(pow(10.0, 6.0 * static_cast<double>(f.y[2 * h + (zc & 1)]) - 6.0) -
-                                1e-12, 0.0)
-                     : -1.0;
+      nu[k] = inside ? rate_of_output(ysel[h]) : -1.0;
     }
   }
 }

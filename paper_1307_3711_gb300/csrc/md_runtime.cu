@@ -113,6 +113,7 @@ struct md_ctx {
   unsigned char* d_src_live = nullptr; // liveness flags per kLiveGroup records
   unsigned char* d_tgt_live = nullptr;
   float4* d_vel = nullptr;             // FP32 (ux, uy, uz, w) per record
+  long long* d_ion_next = nullptr;     // [n_clusters] next free electron slot
   float* d_mlp = nullptr;              // surrogate parameters (device), if set
 };
 
@@ -428,6 +429,7 @@ md::IonArgs ion_args(md_ctx* c, int ci, int force) {
   a.src_live = c->d_src_live;
   a.tgt_live = c->d_tgt_live;
   a.vel = c->d_vel;
+  a.next_slot = c->d_ion_next + ci;
   return a;
 }
 
@@ -516,6 +518,7 @@ void free_ctx(md_ctx* c) {
   cudaFree(c->d_src_live);
   cudaFree(c->d_tgt_live);
   cudaFree(c->d_vel);
+  cudaFree(c->d_ion_next);
   cudaFree(c->d_mlp);
   if (c->h_raw) cudaFreeHost(c->h_raw);
   if (c->h_diag) cudaFreeHost(c->h_diag);
@@ -525,6 +528,24 @@ void free_ctx(md_ctx* c) {
 
 md_status upload_cluster(md_ctx* c, int ci, const md_particles& p) {
   const long long n = p.n;
+  long long next_slot = 0;
+  if (c->d_ion_next && c->ion[ci].rate_model) {
+    // electrons are freed into the slots after the last active one; all the
+    // ionizations still possible must fit before the end of the slot region
+    const md::IonDev& io = c->ion[ci];
+    const long long end = io.slot_base + static_cast<long long>(io.zmax) * io.n_ions;
+    long long last = -1, remaining = 0;
+    for (long long r = io.slot_base; r < end; ++r) {
+      const int kd = p.kind ? p.kind[r] : (p.z[r] < 0 ? MD_KIND_ELECTRON : MD_KIND_ION);
+      if (kd != MD_KIND_INACTIVE) last = r;
+    }
+    for (long long i = 0; i < io.n_ions; ++i) remaining += std::max(0, io.zmax - p.z[i]);
+    next_slot = last >= 0 ? last + 1 : io.slot_base;
+    if (next_slot + remaining > end)
+      return fail(MD_ERR_ARG,
+                  "cluster %d: %lld more ionizations possible but only %lld free electron slots "
+                  "after the last active one", ci, remaining, end - next_slot);
+  }
   RawView h = raw_view(c->h_raw, n);
   std::memcpy(h.x, p.x, sizeof(double) * 3 * n);
   std::memcpy(h.u, p.u, sizeof(double) * 3 * n);
@@ -562,6 +583,9 @@ md_status upload_cluster(md_ctx* c, int ci, const md_particles& p) {
   a.step = c->d_step;
   a.vel = c->d_vel;
   MD_CUDA(md::launch_upload(a, c->stream));
+  if (c->d_ion_next && c->ion[ci].rate_model)
+    MD_CUDA(cudaMemcpyAsync(c->d_ion_next + ci, &next_slot, sizeof(long long),
+                            cudaMemcpyHostToDevice, c->stream));
   if (c->d_src_live)
     MD_CUDA(md::launch_live_init(c->d_posq[0], c->d_posq[1], c->d_kind, c->d_step, c->n_total,
                                  c->d_src_live, c->d_tgt_live, c->stream));
@@ -736,8 +760,10 @@ md_status md_init(md_ctx** out, const md_config* cfgs, int32_t n_clusters,
     if (dev_alloc(&c->d_src_live, groups) != cudaSuccess ||
         dev_alloc(&c->d_tgt_live, groups) != cudaSuccess)
       return bail(fail(MD_ERR_OOM, "liveness flags"));
-    if (dev_alloc(&c->d_vel, N) != cudaSuccess)
+    if (dev_alloc(&c->d_vel, N) != cudaSuccess ||
+        dev_alloc(&c->d_ion_next, static_cast<size_t>(n_clusters)) != cudaSuccess)
       return bail(fail(MD_ERR_OOM, "velocity stream"));
+    cudaMemsetAsync(c->d_ion_next, 0, sizeof(long long) * n_clusters, c->stream);
     cudaMemsetAsync(c->d_vel, 0, N * sizeof(float4), c->stream);
     cudaMemsetAsync(c->d_ion_out, 0, sizeof(double) * 4 * sum_ion, c->stream);
     cudaMemsetAsync(c->d_ion_fired, 0, sum_ion, c->stream);
@@ -812,9 +838,23 @@ md_status md_set_rate_mlp(md_ctx* c, const float* params, const md_mlp_train_con
         domain->ne_max > domain->ne_min && domain->te_min > 0.0 &&
         domain->te_max > domain->te_min))
     return fail(MD_ERR_ARG, "bad surrogate domain");
-  for (int ci = 0; ci < c->n_clusters; ++ci)
-    if (c->ion[ci].rate_model == 2 && c->ion[ci].zmax > 8)
+  for (int ci = 0; ci < c->n_clusters; ++ci) {
+    const md::IonDev& io = c->ion[ci];
+    if (io.rate_model != 2) continue;
+    if (io.zmax > 8)
       return fail(MD_ERR_ARG, "cluster %d: the surrogate has 8 outputs (zmax <= 8)", ci);
+    // the surrogate's inputs are scaled by the species' ionization energies
+    // and the laser wavelength it was trained for
+    const double k_train = 2.0 * 3.14159265358979323846 / (domain->lambda_um * 1e-6);
+    bool same = std::fabs(k_train - io.k_si) <= 1e-12 * io.k_si;
+    for (int z = 0; z < io.zmax; ++z)
+      same = same && std::fabs(domain->ip_ev[z] - io.ip_ev[z]) <= 1e-12 * io.ip_ev[z] &&
+             domain->q_outer[z] == io.q_outer[z];
+    if (!same)
+      return fail(MD_ERR_ARG,
+                  "cluster %d: the surrogate was trained for another species table or "
+                  "wavelength", ci);
+  }
   MD_CUDA(cudaStreamSynchronize(c->stream));
   if (!c->d_mlp) MD_CUDA(dev_alloc(&c->d_mlp, 5000));
   MD_CUDA(cudaMemcpyAsync(c->d_mlp, params, sizeof(float) * 5000, cudaMemcpyHostToDevice,
@@ -1099,6 +1139,8 @@ md_status md_autotune(md_ctx* c, int32_t steps, double* times_ms, int32_t cap) {
     bufs.push_back({c->d_tgt_live, G, nullptr});
   }
   if (c->d_vel) bufs.push_back({c->d_vel, N * sizeof(float4), nullptr});
+  if (c->d_ion_next)
+    bufs.push_back({c->d_ion_next, sizeof(long long) * c->n_clusters, nullptr});
   auto release = [&]() {
     for (auto& b : bufs) cudaFree(b.copy);
   };

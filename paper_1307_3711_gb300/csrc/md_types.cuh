@@ -31,7 +31,7 @@ struct IonDev {
   int ionize_every;   // pass before every k-th step (0: explicit calls only)
   int zmax;
   int n_ions;         // records [off, off + n_ions) can ionize
-  long long slot_base;  // cluster-relative first electron slot (z-major)
+  long long slot_base;  // cluster-relative first electron slot (filled densely)
   unsigned long long seed;
   double r_loc, r_create;
   double kc;          // K_C of the cluster: Q = kc w z
@@ -108,6 +108,7 @@ struct IonArgs {
   unsigned char* src_live;  // liveness flags (set when a record becomes charged / active)
   unsigned char* tgt_live;
   float4* vel;        // FP32 (ux, uy, uz, w) per record
+  long long* next_slot;  // cluster-relative record of the next free electron slot
 };
 
 struct FieldArgs {

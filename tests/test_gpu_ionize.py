@@ -1,6 +1,6 @@
 """GPU ionization pass (Sec. II, ionization paragraph) against the oracle:
 Philox agreement with cuRAND and the oracle, bit-exact decisions from the same
-inputs, exact charge conservation, the electron-slot layout."""
+inputs, exact charge conservation, the dense electron-slot layout."""
 import ctypes as C
 import os
 import subprocess
@@ -77,12 +77,17 @@ def test_ionization_decisions_bit_exact_with_oracle(md):
             assert np.array_equal(info["fired"], fired_ref), k
             assert np.array_equal(g1.z[:n], z_ref), k
             np.testing.assert_allclose(info["prob"], p_ref, rtol=1e-12, atol=1e-300)
-            # the freed electrons sit at their slots, offset as the oracle places them
-            for i in np.nonzero(fired_ref)[0]:
-                slot = n + g0.z[i] * n + i
+            # the freed electrons fill the next free slots in ion order, offset
+            # as the oracle places them
+            n_el = int(np.sum(g0.kind[n:] == md.KIND_ELECTRON))
+            for rank, i in enumerate(np.nonzero(fired_ref)[0]):
+                slot = n + n_el + rank
+                assert g0.kind[slot] == md.KIND_INACTIVE
                 assert g1.kind[slot] == md.KIND_ELECTRON and g1.z[slot] == -1
                 np.testing.assert_allclose(g1.x[slot] - g0.x[i], off_ref[i], atol=1e-12)
                 np.testing.assert_array_equal(g1.u[slot], g0.u[i])
+            live = g1.kind[n:] != md.KIND_INACTIVE
+            assert live[:int(live.sum())].all()
             total_fired += int(fired_ref.sum())
             ctx.step(3)
         assert total_fired > 0.2 * n
@@ -142,6 +147,30 @@ def test_ionization_in_steps_conserves_charge(md):
         assert g.z[:n].sum() > 0
         d = ctx.diagnostics(0)
         assert d["charge_count"].sum() == n and d["n_nonfinite"] == 0
+
+
+def test_slot_capacity_checked_on_upload(md):
+    """A state whose free slots after the last active one cannot take all the
+    ionizations still possible is rejected; the same state with the electron
+    moved to the first slot is accepted."""
+    n, zmax = 4, 2
+    x = np.zeros((12, 3)); x[:, 0] = np.arange(12) * 1e-3
+    z = np.zeros(12, np.int32); z[0] = 1
+    kind = np.full(12, md.KIND_INACTIVE, np.uint8); kind[:n] = md.KIND_ION
+    kw = dict(a0=0.01, rate_model=1, ionize_every=1, zmax=zmax, n_ions=n, slot_base=n,
+              seed=1, r_loc=1e-3, r_create=1e-4, softening=1e-4, species=AR)
+    bad_z, bad_kind = z.copy(), kind.copy()
+    bad_z[10], bad_kind[10] = -1, md.KIND_ELECTRON   # 7 more ionizations, 1 slot left
+    with pytest.raises(md.MDError):
+        md.Context([md.make_config(**kw)],
+                   [md.HostParticles(x, np.zeros((12, 3)), bad_z, np.ones(12), np.ones(12),
+                                     bad_kind)])
+    ok_z, ok_kind = z.copy(), kind.copy()
+    ok_z[4], ok_kind[4] = -1, md.KIND_ELECTRON
+    with md.Context([md.make_config(**kw)],
+                    [md.HostParticles(x, np.zeros((12, 3)), ok_z, np.ones(12), np.ones(12),
+                                      ok_kind)]) as ctx:
+        ctx.step(2)
 
 
 def test_dead_tiles_skipped_and_autotune_restores_ionizing_state(md):
@@ -207,4 +236,8 @@ def test_ionizing_steps_follow_oracle(md):
             assert np.percentile(rel, 99) < 2e-5, k
             agree = info["fired"].astype(bool) == fired_ref.astype(bool)
             assert agree.mean() > 0.995, k
+            if agree.all():   # same decisions: same charges, same dense slots
+                g1 = ctx.get_particles(0)
+                assert np.array_equal(g1.z, st.z)
+                assert np.array_equal(g1.kind != md.KIND_INACTIVE, st.active > 0)
     assert np.bincount(st.z[:n], minlength=9)[2:].sum() > 0.3 * n

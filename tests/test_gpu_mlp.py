@@ -102,7 +102,8 @@ def test_samples_are_labelled_by_the_plain_rate(md):
         nu = oracle.rate_total(raw[k, 0], int(z[k]), raw[k, 1], raw[k, 2], AR)
         assert t[k] == pytest.approx(oracle.mlp_target(nu), abs=2e-7)
         np.testing.assert_allclose(f[k], oracle.mlp_features(raw[k, 0], int(z[k]), raw[k, 1],
-                                                             raw[k, 2]), atol=2e-6)
+                                                             raw[k, 2], AR["ip_ev"][int(z[k])]),
+                                   atol=2e-6)
 
 
 def test_plain_rate_entry_point_matches_oracle(md):
@@ -140,11 +141,14 @@ def test_training_accuracy(md, trained):
 
 def test_surrogate_charge_states_match_plain_rates(md, trained):
     """The same Ar cluster and seed, ionized with the plain rates and with the
-    surrogate: the charge-state fractions agree within 0.01 per state."""
+    surrogate: the charge-state fractions agree within 0.01 per state.  The
+    runs decorrelate (chaotic dynamics), so each fraction carries binomial
+    noise of about sqrt(p(1-p)/n): 50k atoms keep it near 0.0015, and a plain
+    run with another seed shows the noise level."""
     cfg, params, _ = trained
-    n = 20000
-    c = synth.make_cluster(6, n, 0, synth.nm_to_len(5.7), 0, AR["mass"],
-                           n_electron_slots=n * 8)
+    n = 50000
+    c = synth.make_cluster(6, n, 0, synth.nm_to_len(5.7 * (n / 20000) ** (1 / 3)), 0,
+                           AR["mass"], n_electron_slots=n * 8)
     rw = synth.nm_to_len(AR["r_w_nm"])
     fracs = []
     for model, seed in ((1, 99), (2, 99), (1, 98)):
@@ -160,6 +164,7 @@ def test_surrogate_charge_states_match_plain_rates(md, trained):
     print("charge fractions plain", np.round(fracs[0], 4), "surrogate", np.round(fracs[1], 4),
           "plain, other seed", np.round(fracs[2], 4))
     assert fracs[0][1:].sum() > 0.3   # the run ionized
+    assert np.abs(fracs[0] - fracs[2]).max() <= 0.01   # seed-to-seed noise below the bound
     assert np.abs(fracs[0] - fracs[1]).max() <= 0.01
 
 

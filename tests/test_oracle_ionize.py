@@ -177,7 +177,8 @@ def test_electron_placement_uniform_in_ball():
 
 def test_ionize_pass_conserves_charge_and_uses_slots():
     """Neutral Ar atoms in a strong field: every pass conserves the total
-    charge exactly; slot slot_base + z_old n_ion + i is the new electron."""
+    charge exactly; the electrons freed in a pass fill the next free slots in
+    the order of their ions, so the active slots stay one dense block."""
     n_ion, zmax = 300, 8
     c = synth.make_cluster(4, n_ion, 0, synth.nm_to_len(2.0), 0, AR["mass"],
                            n_electron_slots=n_ion * zmax)
@@ -188,14 +189,31 @@ def test_ionize_pass_conserves_charge_and_uses_slots():
     total = []
     for k in range(4):
         st.step = 10 + k
-        z_before = st.z[:n_ion].copy()
+        before = st.copy()
+        n_before = int(st.active[n_ion:].sum())
         fired, amag, ne, te = oracle.ionize_pass(st, p, AR, n_ion, n_ion, zmax, seed=3,
                                                  dt_ion=5.0, r_loc=r_loc,
                                                  r_create=synth.nm_to_len(AR["r_w_nm"]))
         total.append(int(np.sum(st.w * st.z * st.active)))
-        for i in np.nonzero(fired)[0]:
-            slot = n_ion + z_before[i] * n_ion + i
+        for rank, i in enumerate(np.nonzero(fired)[0]):
+            slot = n_ion + n_before + rank
+            assert before.active[slot] == 0
             assert st.active[slot] == 1 and st.z[slot] == -1
+            assert np.array_equal(st.u[slot], before.u[i])
+            assert np.linalg.norm(st.x[slot] - before.x[i]) <= synth.nm_to_len(AR["r_w_nm"])
+        n_el = int(st.active[n_ion:].sum())
+        assert st.active[n_ion:n_ion + n_el].all() and not st.active[n_ion + n_el:].any()
     assert total == [0, 0, 0, 0]
     assert st.z[:n_ion].max() >= 2
     assert st.active[n_ion:].sum() == st.z[:n_ion].sum()
+
+
+def test_next_free_slot_follows_the_last_active_slot():
+    """A state whose slot region has holes: new electrons go after the last
+    active slot, never into a hole."""
+    n_ion, zmax = 4, 2
+    st = oracle.State(np.zeros((12, 3)), np.zeros((12, 3)), np.zeros(12, np.int32),
+                      np.ones(12), np.ones(12), np.zeros(12, np.uint8))
+    assert oracle.next_free_slot(st, 4, n_ion, zmax) == 4
+    st.active[[4, 7]] = 1
+    assert oracle.next_free_slot(st, 4, n_ion, zmax) == 8

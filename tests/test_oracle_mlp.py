@@ -53,8 +53,24 @@ def test_output_map_inverts_target(nu):
 
 
 def test_features_definition_points():
-    f = oracle.mlp_features(10 ** -1.5, 8, 10 ** 19.5, 10 ** 1.5)
-    np.testing.assert_allclose(f, [0.0, 1.0, 0.0, 0.0], atol=1e-15)
-    f = oracle.mlp_features(0.0, 0, 0.0, 0.0)  # floors: 1e-6, 1e15 cm^-3, 0.1 eV
-    np.testing.assert_allclose(f, [(-6 + 1.5) / 1.5, 0.0, (15 - 19.5) / 4.5, (-1 - 1.5) / 2.5],
-                               atol=1e-15)
+    """The field enters relative to F0 = (2 Ip)^(3/2) (atomic units) and the
+    temperature relative to Ip: scaling Ip by 4 and the field by 8, or Ip and
+    T_e by 2, leaves the features unchanged; at F = F0 the field feature is
+    (0 + 1.4)/1.5.  The atomic field in the paper's unit a = eE/(m_e omega c)
+    follows from SI constants."""
+    e_au_paper = 5.14220674763e11 * 1.602176634e-19 / (
+        9.1093837015e-31 * 299792458.0 * 2 * np.pi * 299792458.0 / 0.8e-6)
+    hartree = 27.211386245988
+    # hydrogen-like Ip = E_h / 2: F0 = 1 atomic unit
+    f = oracle.mlp_features(e_au_paper, 8, 10 ** 19.5, 0.5 * hartree * 10 ** -0.2,
+                            0.5 * hartree)
+    np.testing.assert_allclose(f, [1.4 / 1.5, 1.0, 0.0, 0.0], atol=1e-9)
+    a = oracle.mlp_features(0.05, 3, 1e21, 40.0, 60.0)
+    b = oracle.mlp_features(0.4, 3, 1e21, 80.0, 240.0)
+    c = oracle.mlp_features(0.4, 3, 1e21, 160.0, 240.0)
+    assert a[0] == pytest.approx(b[0], abs=1e-12)
+    assert a[3] == pytest.approx(c[3], abs=1e-12)
+    f = oracle.mlp_features(0.0, 0, 0.0, 0.0, 15.0)  # floors: 1e-6, 1e15 cm^-3, 0.1 eV
+    g = oracle.mlp_features(1e-6, 0, 1e15, 0.1, 15.0)
+    np.testing.assert_allclose(f, g, atol=1e-15)
+    assert f[2] == pytest.approx((15 - 19.5) / 4.5) and f[1] == 0.0
