@@ -101,6 +101,12 @@ __device__ __forceinline__ float4 lds_f4(uint32_t addr) {
   return v;
 }
 
+__device__ __forceinline__ float lds_f32(uint32_t addr) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr));
+  return v;
+}
+
 __device__ __forceinline__ ulonglong2 lds_u64x2(uint32_t addr) {
   ulonglong2 v;
   asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "r"(addr));
@@ -320,6 +326,40 @@ __device__ __forceinline__ void pair(const float4 p, const float (&xi)[R], const
   }
 }
 
+// The same for a tile whose sources all carry one charge Q: the sum of
+// (x_j - x_i)/(r^2+eps^2)^{3/2} (and 1/sqrt(r^2+eps^2)) without Q, which then
+// multiplies the tile partial once (fold_q).  One FP32 multiply less per pair.
+template <int R, bool POT>
+__device__ __forceinline__ void pair_u(const float4 p, const float (&xi)[R], const float (&yi)[R],
+                                       const float (&zi)[R], float eps2, Acc<R, POT>& a) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const float dx = p.x - xi[r];
+    const float dy = p.y - yi[r];
+    const float dz = p.z - zi[r];
+    float r2 = fmaf(dx, dx, eps2);
+    r2 = fmaf(dy, dy, r2);
+    r2 = fmaf(dz, dz, r2);
+    const float ri = rsqrt_mufu(r2);
+    const float ri2 = ri * ri;
+    const float s = ri2 * ri;
+    a.ax[r] = fmaf(dx, s, a.ax[r]);
+    a.ay[r] = fmaf(dy, s, a.ay[r]);
+    a.az[r] = fmaf(dz, s, a.az[r]);
+    if (POT) a.ap[r] += ri;
+  }
+}
+
+// Whether all cnt sources of a landed tile carry the charge of the first one
+// (q receives it).  Each warp decides for itself from the same shared data.
+__device__ __forceinline__ bool tile_uniform_q(uint32_t tile, int cnt, float& q) {
+  q = lds_f32(tile + 12u);
+  bool ok = true;
+  for (int k = static_cast<int>(threadIdx.x & 31u); k < cnt; k += 32)
+    ok = ok && (lds_f32(tile + 16u * k + 12u) == q);
+  return __all_sync(0xffffffffu, ok);
+}
+
 template <int R, bool POT>
 __device__ __forceinline__ void fold(Acc<R, POT>& a) {
 #pragma unroll
@@ -336,6 +376,18 @@ __device__ __forceinline__ void fold(Acc<R, POT>& a) {
 }
 
 // Shared-memory staging of the j-stream.
+template <int R, bool POT>
+__device__ __forceinline__ void fold_q(Acc<R, POT>& a, float q) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    a.ax[r] *= q;
+    a.ay[r] *= q;
+    a.az[r] *= q;
+    if (POT) a.ap[r] *= q;
+  }
+  fold<R, POT>(a);
+}
+
 template <int TILE, int STAGES>
 struct Stage {
   alignas(128) float4 tile[STAGES][TILE];
@@ -415,22 +467,46 @@ __device__ __forceinline__ bool sum_sources(Stage<TILE, STAGES>& sm, unsigned& i
       const uint32_t tile = smem_u32(&sm.tile[s][0]);
       const long long rem = ns - static_cast<long long>(t) * TILE;
       const int cnt = static_cast<int>(rem < TILE ? rem : TILE);
-      int j = 0;
-      for (; j + 8 <= cnt; j += 8) {
+      float qt;
+      if (tile_uniform_q(tile, cnt, qt)) {
+        // one charge for the whole tile (records are grouped by species);
+        // an uncharged tile adds nothing
+        if (qt != 0.0f) {
+          int j = 0;
+          for (; j + 8 <= cnt; j += 8) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) pair<R, POT>(lds_f4(tile + 16u * (j + q)), xi, yi, zi, eps2, acc);
-        if (POT) {
-          // potential terms of one species share a sign: fold them often so
-          // the FP32 partial stays small against a cancelling total
+            for (int q = 0; q < 8; ++q)
+              pair_u<R, POT>(lds_f4(tile + 16u * (j + q)), xi, yi, zi, eps2, acc);
+            if (POT) {
 #pragma unroll
-          for (int r = 0; r < R; ++r) {
-            kahan_add(acc.sp[r], acc.cp[r], acc.ap[r]);
-            acc.ap[r] = 0.0f;
+              for (int r = 0; r < R; ++r) {
+                kahan_add(acc.sp[r], acc.cp[r], acc.ap[r] * qt);
+                acc.ap[r] = 0.0f;
+              }
+            }
+          }
+          for (; j < cnt; ++j) pair_u<R, POT>(lds_f4(tile + 16u * j), xi, yi, zi, eps2, acc);
+          fold_q<R, POT>(acc, qt);
+        }
+      } else {
+        int j = 0;
+        for (; j + 8 <= cnt; j += 8) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            pair<R, POT>(lds_f4(tile + 16u * (j + q)), xi, yi, zi, eps2, acc);
+          if (POT) {
+            // potential terms of one species share a sign: fold them often so
+            // the FP32 partial stays small against a cancelling total
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              kahan_add(acc.sp[r], acc.cp[r], acc.ap[r]);
+              acc.ap[r] = 0.0f;
+            }
           }
         }
+        for (; j < cnt; ++j) pair<R, POT>(lds_f4(tile + 16u * j), xi, yi, zi, eps2, acc);
+        fold<R, POT>(acc);
       }
-      for (; j < cnt; ++j) pair<R, POT>(lds_f4(tile + 16u * j), xi, yi, zi, eps2, acc);
-      fold<R, POT>(acc);
     }
     __syncthreads();
     if (*reinterpret_cast<volatile int*>(s_abort)) {
@@ -554,6 +630,31 @@ __device__ __forceinline__ void pair2(const ulonglong2 xy, const ulonglong2 zq, 
   }
 }
 
+// pair2 for a tile of one charge (see pair_u): no charge multiply per pair.
+template <int P, bool POT>
+__device__ __forceinline__ void pair2_u(const ulonglong2 xy, const ulonglong2 zq,
+                                        const u64 (&xi)[P], const u64 (&yi)[P],
+                                        const u64 (&zi)[P], u64 e2, AccP<P, POT>& a) {
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const u64 dx = f2_sub(xy.x, xi[p]);
+    const u64 dy = f2_sub(xy.y, yi[p]);
+    const u64 dz = f2_sub(zq.x, zi[p]);
+    u64 r2 = f2_fma(dx, dx, e2);
+    r2 = f2_fma(dy, dy, r2);
+    r2 = f2_fma(dz, dz, r2);
+    float lo, hi;
+    f2_unpack(r2, lo, hi);
+    const u64 ri = f2_pack(rsqrt_mufu(lo), rsqrt_mufu(hi));
+    const u64 ri2 = f2_mul(ri, ri);
+    const u64 s = f2_mul(ri2, ri);
+    a.ax[p] = f2_fma(dx, s, a.ax[p]);
+    a.ay[p] = f2_fma(dy, s, a.ay[p]);
+    a.az[p] = f2_fma(dz, s, a.az[p]);
+    if (POT) a.ap[p] = f2_add(a.ap[p], ri);
+  }
+}
+
 // As sum_sources, with the pair arithmetic in packed f32x2.  Each landed
 // tile is first expanded into `dup` (which frees its TMA stage at once, so a
 // single stage suffices), then the R targets of this thread are summed two at
@@ -605,7 +706,10 @@ __device__ __forceinline__ bool sum_sources_packed(Stage<TILE, STAGES>& sm, DupT
     }
     const long long rem = ns - static_cast<long long>(t) * TILE;
     const int cnt = static_cast<int>(rem < TILE ? rem : TILE);
+    float qt = 0.0f;
+    bool uni = false;
     if (!*reinterpret_cast<volatile int*>(s_abort)) {
+      uni = tile_uniform_q(smem_u32(&sm.tile[s][0]), cnt, qt);
       for (int k = tid; k < cnt; k += THREADS) {
         const float4 p = sm.tile[s][k];
         dup.v[k][0] = make_ulonglong2(f2_pack(p.x, p.x), f2_pack(p.y, p.y));
@@ -630,26 +734,61 @@ __device__ __forceinline__ bool sum_sources_packed(Stage<TILE, STAGES>& sm, DupT
       ti = next_live_tile(live, gbase, ns, ti + 1, ntiles, TILE);
     }
     const uint32_t dbase = smem_u32(&dup.v[0][0]);
+    if (uni && qt == 0.0f) {  // an uncharged tile adds nothing
+      __syncthreads();
+      t = next_live_tile(live, gbase, ns, t + 1, ntiles, TILE);
+      continue;
+    }
+    const u64 qq = f2_pack(qt, qt);
     int j = 0;
-    for (; j + 8 <= cnt; j += 8) {
+    if (uni) {
+      for (; j + 8 <= cnt; j += 8) {
 #pragma unroll
-      for (int k = 0; k < 8; ++k)
-        pair2<P, POT>(lds_u64x2(dbase + 32u * (j + k)), lds_u64x2(dbase + 32u * (j + k) + 16u),
-                      xi2, yi2, zi2, e2, a);
-      if (POT) {
+        for (int k = 0; k < 8; ++k)
+          pair2_u<P, POT>(lds_u64x2(dbase + 32u * (j + k)),
+                          lds_u64x2(dbase + 32u * (j + k) + 16u), xi2, yi2, zi2, e2, a);
+        if (POT) {
 #pragma unroll
-        for (int p = 0; p < P; ++p) {
-          u64 sp = ks.v[6][p][tid], cp = ks.v[7][p][tid];
-          kahan_add2(sp, cp, a.ap[p]);
-          ks.v[6][p][tid] = sp;
-          ks.v[7][p][tid] = cp;
-          a.ap[p] = 0ull;
+          for (int p = 0; p < P; ++p) {
+            u64 sp = ks.v[6][p][tid], cp = ks.v[7][p][tid];
+            kahan_add2(sp, cp, f2_mul(a.ap[p], qq));
+            ks.v[6][p][tid] = sp;
+            ks.v[7][p][tid] = cp;
+            a.ap[p] = 0ull;
+          }
         }
       }
+      for (; j < cnt; ++j)
+        pair2_u<P, POT>(lds_u64x2(dbase + 32u * j), lds_u64x2(dbase + 32u * j + 16u), xi2, yi2,
+                        zi2, e2, a);
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        a.ax[p] = f2_mul(a.ax[p], qq);
+        a.ay[p] = f2_mul(a.ay[p], qq);
+        a.az[p] = f2_mul(a.az[p], qq);
+        if (POT) a.ap[p] = f2_mul(a.ap[p], qq);
+      }
+    } else {
+      for (; j + 8 <= cnt; j += 8) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          pair2<P, POT>(lds_u64x2(dbase + 32u * (j + k)), lds_u64x2(dbase + 32u * (j + k) + 16u),
+                        xi2, yi2, zi2, e2, a);
+        if (POT) {
+#pragma unroll
+          for (int p = 0; p < P; ++p) {
+            u64 sp = ks.v[6][p][tid], cp = ks.v[7][p][tid];
+            kahan_add2(sp, cp, a.ap[p]);
+            ks.v[6][p][tid] = sp;
+            ks.v[7][p][tid] = cp;
+            a.ap[p] = 0ull;
+          }
+        }
+      }
+      for (; j < cnt; ++j)
+        pair2<P, POT>(lds_u64x2(dbase + 32u * j), lds_u64x2(dbase + 32u * j + 16u), xi2, yi2,
+                      zi2, e2, a);
     }
-    for (; j < cnt; ++j)
-      pair2<P, POT>(lds_u64x2(dbase + 32u * j), lds_u64x2(dbase + 32u * j + 16u), xi2, yi2, zi2,
-                    e2, a);
 #pragma unroll
     for (int p = 0; p < P; ++p) {
       u64 sv, cv;
