@@ -102,7 +102,8 @@ cudaError_t blocks_per_sm_t(int* out) {
 const KernelConfig kConfigs[] = {
     // scalar FP32 pair arithmetic
     MD_STEP_CONFIG(128, 1, 512, 2, false, 0), MD_STEP_CONFIG(128, 4, 512, 2, false, 0),
-    MD_STEP_CONFIG(256, 2, 512, 2, false, 0),
+    MD_STEP_CONFIG(256, 2, 512, 2, false, 0), MD_STEP_CONFIG(128, 8, 512, 2, false, 0),
+    MD_STEP_CONFIG(256, 4, 512, 2, false, 0),
     // packed f32x2 pair arithmetic (tile expanded in shared memory, one TMA stage)
     MD_STEP_CONFIG(128, 4, 256, 1, true, 0), MD_STEP_CONFIG(256, 4, 256, 1, true, 0),
     MD_STEP_CONFIG(128, 8, 256, 1, true, 0),

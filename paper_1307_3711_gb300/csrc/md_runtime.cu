@@ -369,7 +369,7 @@ int default_config(md_ctx* c) {
   int ncfg = 0;
   const md::KernelConfig* cfgs = md::step_configs(&ncfg);
   for (int i = 0; i < ncfg; ++i)
-    if (cfgs[i].threads == 128 && cfgs[i].r == 8 && cfgs[i].packed) return i;
+    if (cfgs[i].threads == 128 && cfgs[i].r == 4 && !cfgs[i].packed) return i;
   return 0;
 }
 
