@@ -217,6 +217,42 @@ md_status md_get_fields(md_ctx *ctx, int32_t cluster, double *e, double *phi);
  * last active slot.  Asynchronous. */
 md_status md_ionize(md_ctx *ctx);
 
+/* ---- ion energy detectors (Sec. III, Fig. 3) --------------------------------
+ * The paper compares ion energy distributions seen along and across the laser
+ * polarization.  Here they are read at a fixed radius: an ion (kind ION,
+ * z >= 1) that crosses the sphere |x - center| = radius outward during a step,
+ * |x^n - c| < radius <= |x^{n+1} - c| (x^{n+1} after the boundary), is
+ * recorded once, with its kinetic energy (gamma - 1) m c^2 at u^{n+1/2} (eV),
+ * in up to five histograms: 0 = +x, 1 = -x, 2 = +y, 3 = -y (direction
+ * (x^{n+1} - c)/|x^{n+1} - c| within cone_half_angle_deg of the axis) and
+ * 4 = all directions.  Bins: n_bins of width e_max_ev / n_bins over
+ * [0, e_max_ev) plus an overflow bin n_bins.  Counts are macro-ions.  The
+ * crossing, cone and bin are decided in FP64 with each operation rounded to
+ * nearest in a fixed order (no fused multiply-add). */
+typedef struct {
+    double radius;              /* paper units (e.g. 9 R0) */
+    double cone_half_angle_deg; /* 0..90 */
+    double e_max_ev;            /* > 0 */
+    int32_t n_bins;             /* 1..4096 */
+    int32_t reserved;           /* must be 0 */
+    double center[3];           /* sphere centre, paper units */
+} md_detector_config;
+
+/* md_set_detectors: configures (d != NULL) or switches off (d == NULL) the
+ * detectors of cluster `cluster`; a new configuration starts with empty
+ * histograms and no ion recorded.  The first call allocates the histograms
+ * of all clusters (5 x 4097 x 8 B each) and one byte per record.
+ * Synchronous. */
+md_status md_set_detectors(md_ctx *ctx, int32_t cluster, const md_detector_config *d);
+
+/* md_get_iedf: the detector histograms of cluster `cluster` (host
+ * detected[5][n_bins + 1], or NULL) and, if inside != NULL (host
+ * [n_bins + 1]), the histogram of the ions not yet recorded at their current
+ * u (u^{n-1/2}); together they are the total ion energy distribution.
+ * MD_ERR_STATE without detectors.  Allocates n_bins + 1 counters on the device
+ * for `inside` during the call.  Synchronous. */
+md_status md_get_iedf(md_ctx *ctx, int32_t cluster, uint64_t *detected, uint64_t *inside);
+
 /* md_get_ionization: per-ion results of the last pass of cluster `cluster`
  * (host arrays of n_ions entries, any may be NULL): field magnitude |E| (paper
  * units), local electron density (cm^-3) and temperature (eV), probability P

@@ -88,6 +88,10 @@ def lib():
             L.or_diagnostics.restype = None
             L.or_diagnostics.argtypes = [i, p, p, p, p, p, p, p, C.POINTER(Params), i64,
                                          p, p, p, p, i]
+            L.or_detect.restype = None
+            L.or_detect.argtypes = [i, p, p, p, p, p, p, p, d, d, d, i, p, p]
+            L.or_iedf_inside.restype = None
+            L.or_iedf_inside.argtypes = [i, p, p, p, p, p, d, i, p]
             L.io_philox4x32_10.restype = None
             L.io_philox4x32_10.argtypes = [p, p, p]
             L.io_uniform_open0.restype = d
@@ -280,6 +284,51 @@ def diagnostics(state: State, params: Params, nthreads: int = 1) -> dict:
     return {"ke": out[0], "ke_ions": out[1], "ke_electrons": out[2], "pe": out[3],
             "p": out[4:7].copy(), "n_active": int(out[7]),
             "total": out[0] + out[3]}
+
+
+# ------------------------------------------------------------- detectors ---
+# Ion energy detectors at a fixed radius (Sec. III, Fig. 3); md_oracle.c.
+
+DETECTORS = ("+x", "-x", "+y", "-y", "all")
+
+
+class Detectors:
+    """Detector sphere (radius, centre), cone half-angle (degrees), energy
+    bins [0, e_max_ev) in nbins + overflow; hist[5][nbins + 1] of ion counts
+    and the crossed flag of every record."""
+
+    def __init__(self, n, radius, cone_deg=30.0, e_max_ev=1e4, nbins=100, center=(0, 0, 0)):
+        self.radius, self.cone_deg, self.e_max_ev, self.nbins = radius, cone_deg, e_max_ev, nbins
+        self.center = np.ascontiguousarray(center, dtype=np.float64)
+        self.crossed = np.zeros(n, np.uint8)
+        self.hist = np.zeros((5, nbins + 1), np.uint64)
+
+    def record(self, x_prev, x_next, state: "State"):
+        """Ions of `state` (u = u^{n+1/2}) that crossed between x_prev and x_next."""
+        xp = _f64(x_prev, (-1, 3))
+        xn = _f64(x_next, (-1, 3))
+        lib().or_detect(state.n, _ptr(xp), _ptr(xn), _ptr(state.u), _ptr(state.mass),
+                        _ptr(state.z), _ptr(state.active), _ptr(self.center),
+                        float(self.radius), float(np.cos(np.radians(self.cone_deg))),
+                        float(self.e_max_ev), int(self.nbins), _ptr(self.crossed),
+                        _ptr(self.hist))
+
+    def inside(self, state: "State"):
+        h = np.zeros(self.nbins + 1, np.uint64)
+        lib().or_iedf_inside(state.n, _ptr(state.u), _ptr(state.mass), _ptr(state.z),
+                             _ptr(state.active), _ptr(self.crossed), float(self.e_max_ev),
+                             int(self.nbins), _ptr(h))
+        return h
+
+
+def md_steps_detected(state: State, params: Params, nsteps: int, det: Detectors,
+                      nthreads: int = 1) -> State:
+    """md_steps one step at a time, recording detector crossings."""
+    for _ in range(nsteps):
+        x_prev = state.x.copy()
+        md_steps(state, params, 1, nthreads)
+        det.record(x_prev, state.x, state)
+    return state
 
 
 # ------------------------------------------------------------- ionization ---

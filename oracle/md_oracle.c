@@ -37,6 +37,7 @@
 #endif
 
 #define OR_PI 3.14159265358979323846
+#define OR_ME_C2_EV 510998.95  /* electron rest energy, eV */
 /* classical electron radius in metres (CODATA 2018) */
 #define OR_R_E 2.8179403262e-15
 
@@ -272,3 +273,67 @@ void or_diagnostics(int n, const double *x, const double *u, const double *qm,
     out[0] = ke; out[1] = kei; out[2] = kee; out[3] = pe;
     out[4] = px; out[5] = py; out[6] = pz; out[7] = na;
 }
+
+/* ------------------------------------------------- directional detectors */
+
+/* Ion energy detectors on a sphere of radius R around `center` (the IEDF of
+ * Sec. III, Fig. 3, read at a fixed radius): an ion (active, z >= 1) that
+ * first crosses the sphere outward during a step, |x^n - c| < R <= |x^{n+1} - c|,
+ * is recorded once with its kinetic energy (gamma - 1) m c^2 at u^{n+1/2}.
+ * Detectors: 0 = +x, 1 = -x, 2 = +y, 3 = -y (the ion's direction
+ * (x^{n+1} - c)/|x^{n+1} - c| within the cone of half-angle theta around the
+ * axis: component >= cos(theta) |x^{n+1} - c|), 4 = all directions.
+ * Histogram hist[5][nbins + 1]: bin floor(E nbins / e_max) for E < e_max,
+ * bin nbins for E >= e_max (eV).  crossed[i] marks recorded ions.
+ * Floating point is evaluated in the order written (no contraction). */
+static double or_ke_ev(const double u[3], double mass)
+{
+    double uu = (u[0] * u[0] + u[1] * u[1]) + u[2] * u[2];
+    return (uu / (sqrt(1.0 + uu) + 1.0)) * mass * OR_ME_C2_EV;
+}
+
+static int or_energy_bin(double ke, double e_max, int nbins)
+{
+    if (!(ke < e_max)) return nbins;
+    int b = (int)floor(ke * (double)nbins / e_max);
+    return b < 0 ? 0 : (b >= nbins ? nbins - 1 : b);
+}
+
+void or_detect(int n, const double *x_prev, const double *x_next, const double *u,
+               const double *mass, const int32_t *z, const uint8_t *active,
+               const double center[3], double radius, double cos_cone, double e_max_ev,
+               int nbins, uint8_t *crossed, uint64_t *hist)
+{
+    double R2 = radius * radius;
+    for (int i = 0; i < n; ++i) {
+        if (!active[i] || z[i] < 1 || crossed[i]) continue;
+        double a0 = x_prev[3 * i] - center[0], a1 = x_prev[3 * i + 1] - center[1],
+               a2 = x_prev[3 * i + 2] - center[2];
+        double b0 = x_next[3 * i] - center[0], b1 = x_next[3 * i + 1] - center[1],
+               b2 = x_next[3 * i + 2] - center[2];
+        double rp2 = (a0 * a0 + a1 * a1) + a2 * a2;
+        double rn2 = (b0 * b0 + b1 * b1) + b2 * b2;
+        if (!(rp2 < R2 && rn2 >= R2)) continue;
+        crossed[i] = 1;
+        int bin = or_energy_bin(or_ke_ev(&u[3 * i], mass[i]), e_max_ev, nbins);
+        double c = cos_cone * sqrt(rn2);
+        hist[4 * (nbins + 1) + bin] += 1;
+        if (b0 >= c) hist[0 * (nbins + 1) + bin] += 1;
+        if (-b0 >= c) hist[1 * (nbins + 1) + bin] += 1;
+        if (b1 >= c) hist[2 * (nbins + 1) + bin] += 1;
+        if (-b1 >= c) hist[3 * (nbins + 1) + bin] += 1;
+    }
+}
+
+/* Energy histogram hist[nbins + 1] of the ions (active, z >= 1) not yet
+ * recorded by the detectors, at momentum u (the rest of the total IEDF). */
+void or_iedf_inside(int n, const double *u, const double *mass, const int32_t *z,
+                    const uint8_t *active, const uint8_t *crossed, double e_max_ev, int nbins,
+                    uint64_t *hist)
+{
+    for (int i = 0; i < n; ++i) {
+        if (!active[i] || z[i] < 1 || crossed[i]) continue;
+        hist[or_energy_bin(or_ke_ev(&u[3 * i], mass[i]), e_max_ev, nbins)] += 1;
+    }
+}
+

@@ -818,6 +818,53 @@ __device__ __forceinline__ bool sum_sources_packed(Stage<TILE, STAGES>& sm, DupT
 
 // ------------------------------------------------------------ step kernel --
 
+// Ion energy detectors.  The decisions (crossing, cone, energy bin) are FP64
+// with every operation rounded to nearest in the order written, no
+// contraction, so they are taken exactly as a plain sequential program takes
+// them from the same numbers.
+constexpr double kDetMeC2Ev = 510998.95;
+
+__device__ __forceinline__ double det_norm2(double a, double b, double c) {
+  return __dadd_rn(__dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b)), __dmul_rn(c, c));
+}
+
+// (gamma - 1) m c^2 in eV, as u^2/(sqrt(1 + u^2) + 1) m c^2.
+__device__ __forceinline__ double det_ke_ev(double ux, double uy, double uz, double mass) {
+  const double uu = det_norm2(ux, uy, uz);
+  const double g1 = __ddiv_rn(uu, __dadd_rn(__dsqrt_rn(__dadd_rn(1.0, uu)), 1.0));
+  return __dmul_rn(__dmul_rn(g1, mass), kDetMeC2Ev);
+}
+
+__device__ __forceinline__ int det_bin(double ke, double emax, int nbins) {
+  if (!(ke < emax)) return nbins;
+  const int b = static_cast<int>(floor(__ddiv_rn(__dmul_rn(ke, static_cast<double>(nbins)), emax)));
+  return b < 0 ? 0 : (b >= nbins ? nbins - 1 : b);
+}
+
+// Records ion i if it crossed the detector sphere outward in this step:
+// histograms +x, -x, +y, -y (cone of half-angle acos(det_cos)) and all.
+__device__ __forceinline__ void detect(unsigned long long* hist, unsigned char* crossed,
+                                       const ClusterDev& c, long long i, double x0, double y0,
+                                       double z0, double x1, double y1, double z1, double ux,
+                                       double uy, double uz, double mass) {
+  if (crossed[i]) return;
+  const double rp2 = det_norm2(__dsub_rn(x0, c.det_c[0]), __dsub_rn(y0, c.det_c[1]),
+                               __dsub_rn(z0, c.det_c[2]));
+  const double b0 = __dsub_rn(x1, c.det_c[0]), b1 = __dsub_rn(y1, c.det_c[1]);
+  const double rn2 = det_norm2(b0, b1, __dsub_rn(z1, c.det_c[2]));
+  if (!(rp2 < c.det_r2 && rn2 >= c.det_r2)) return;
+  crossed[i] = 1;
+  const int nb1 = c.det_nbins + 1;
+  const int bin = det_bin(det_ke_ev(ux, uy, uz, mass), c.det_emax, c.det_nbins);
+  const double cc = __dmul_rn(c.det_cos, __dsqrt_rn(rn2));
+  unsigned long long* h = hist + c.det_off;
+  atomicAdd(h + 4 * nb1 + bin, 1ull);
+  if (b0 >= cc) atomicAdd(h + 0 * nb1 + bin, 1ull);
+  if (-b0 >= cc) atomicAdd(h + 1 * nb1 + bin, 1ull);
+  if (b1 >= cc) atomicAdd(h + 2 * nb1 + bin, 1ull);
+  if (-b1 >= cc) atomicAdd(h + 3 * nb1 + bin, 1ull);
+}
+
 // Laser + Boris kick (FP32 increment) + FP64 drift + boundary for record i
 // with Coulomb field (ex, ey, ez); writes x, u and the next j-stream entry.
 __device__ __forceinline__ void push_record(const StepArgs& a, const ClusterDev& c, long long i,
@@ -843,6 +890,9 @@ __device__ __forceinline__ void push_record(const StepArgs& a, const ClusterDev&
     Y = wrap_periodic(Y, c.box);
     Z = wrap_periodic(Z, c.box);
   }
+  if (c.det_nbins > 0 && a.det_hist && a.qm[i] > 0.0f)
+    detect(a.det_hist, a.det_crossed, c, i, a.x[i], a.y[i], a.z[i], X, Y, Z, Ux, Uy, Uz,
+           a.mass[i]);
   a.x[i] = X;
   a.y[i] = Y;
   a.z[i] = Z;

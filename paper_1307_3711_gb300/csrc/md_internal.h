@@ -56,4 +56,11 @@ md_status report_error(md_status status, const char* msg);
 md_status report_cuda_error(cudaError_t e, const char* what);
 cudaError_t launch_download(const DownloadArgs& a, cudaStream_t s);
 
+// Energy histogram [det_nbins + 1] of the cluster's ions not recorded by the
+// detectors (added to `hist`).
+cudaError_t launch_iedf_inside(const ClusterDev& c, const double* ux, const double* uy,
+                               const double* uz, const double* mass, const int* zq,
+                               const unsigned char* kind, const unsigned char* crossed,
+                               unsigned long long* hist, cudaStream_t s);
+
 }  // namespace md

@@ -64,6 +64,30 @@ __global__ void k_upload(const UploadArgs a) {
                            static_cast<float>(a.hu[3 * k + 2]), static_cast<float>(a.hw[k]));
 }
 
+// Energy histogram of the ions (kind ION, z >= 1) of a cluster that the
+// detectors have not recorded, at their current u.
+__global__ void k_iedf_inside(const ClusterDev c, const double* ux, const double* uy,
+                              const double* uz, const double* mass, const int* zq,
+                              const unsigned char* kind, const unsigned char* crossed,
+                              unsigned long long* hist) {
+  const long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= c.n) return;
+  const long long i = c.off + k;
+  if (kind[i] != 0 || zq[i] < 1 || crossed[i]) return;
+  atomicAdd(hist + det_bin(det_ke_ev(ux[i], uy[i], uz[i], mass[i]), c.det_emax, c.det_nbins),
+            1ull);
+}
+
+cudaError_t launch_iedf_inside(const ClusterDev& c, const double* ux, const double* uy,
+                               const double* uz, const double* mass, const int* zq,
+                               const unsigned char* kind, const unsigned char* crossed,
+                               unsigned long long* hist, cudaStream_t s) {
+  if (c.n <= 0) return cudaSuccess;
+  k_iedf_inside<<<static_cast<unsigned>((c.n + 255) / 256), 256, 0, s>>>(c, ux, uy, uz, mass, zq,
+                                                                         kind, crossed, hist);
+  return cudaGetLastError();
+}
+
 __global__ void k_download(const DownloadArgs a) {  const long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k >= a.n) return;
   const long long i = a.off + k;

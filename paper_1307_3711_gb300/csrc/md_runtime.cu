@@ -114,8 +114,14 @@ struct md_ctx {
   unsigned char* d_tgt_live = nullptr;
   float4* d_vel = nullptr;             // FP32 (ux, uy, uz, w) per record
   long long* d_ion_next = nullptr;     // [n_clusters] next free electron slot
+
+  // ion energy detectors (allocated by the first md_set_detectors)
+  unsigned long long* d_det_hist = nullptr;  // [clusters][5][kDetMaxBins + 1]
+  unsigned char* d_det_crossed = nullptr;    // [n_total]
   float* d_mlp = nullptr;              // surrogate parameters (device), if set
 };
+
+constexpr int kDetMaxBins = 4096;  // energy bins per detector histogram
 
 namespace {
 
@@ -245,6 +251,9 @@ md::StepArgs step_args(md_ctx* c) {
   a.src_live = c->d_src_live;
   a.tgt_live = c->d_tgt_live;
   a.vel = c->d_vel;
+  a.det_hist = c->d_det_hist;
+  a.det_crossed = c->d_det_crossed;
+  a.mass = c->d_mass;
   return a;
 }
 
@@ -519,6 +528,8 @@ void free_ctx(md_ctx* c) {
   cudaFree(c->d_tgt_live);
   cudaFree(c->d_vel);
   cudaFree(c->d_ion_next);
+  cudaFree(c->d_det_hist);
+  cudaFree(c->d_det_crossed);
   cudaFree(c->d_mlp);
   if (c->h_raw) cudaFreeHost(c->h_raw);
   if (c->h_diag) cudaFreeHost(c->h_diag);
@@ -676,6 +687,7 @@ md_status md_init(md_ctx** out, const md_config* cfgs, int32_t n_clusters,
   for (int i = 0; i < n_clusters; ++i) {
     const md_config& f = cfgs[i];
     md::ClusterDev d;
+    std::memset(&d, 0, sizeof(d));  // detectors off
     d.off = off;
     d.n = static_cast<int>(parts[i].n);
     d.n_pad = static_cast<int>((parts[i].n + md::kPad - 1) / md::kPad * md::kPad);
@@ -867,6 +879,82 @@ md_status md_set_rate_mlp(md_ctx* c, const float* params, const md_mlp_train_con
   }
   destroy_graph(c);  // kernel arguments changed
   return MD_OK;
+}
+
+md_status md_set_detectors(md_ctx* c, int32_t cluster, const md_detector_config* d) {
+  if (!c) return fail(MD_ERR_ARG, "ctx is NULL");
+  if (cluster < 0 || cluster >= c->n_clusters) return fail(MD_ERR_ARG, "bad cluster index");
+  if (d && !(d->radius > 0.0 && d->cone_half_angle_deg >= 0.0 &&
+             d->cone_half_angle_deg <= 90.0 && d->e_max_ev > 0.0 && d->n_bins >= 1 &&
+             d->n_bins <= kDetMaxBins && d->reserved == 0 && std::isfinite(d->center[0]) &&
+             std::isfinite(d->center[1]) && std::isfinite(d->center[2])))
+    return fail(MD_ERR_ARG, "detectors: radius > 0, cone in [0, 90] degrees, e_max_ev > 0, "
+                "1 <= n_bins <= %d, reserved = 0, finite centre", kDetMaxBins);
+  MD_CUDA(cudaStreamSynchronize(c->stream));
+  const size_t per = 5 * static_cast<size_t>(kDetMaxBins + 1);
+  if (d && !c->d_det_hist) {
+    MD_CUDA(dev_alloc(&c->d_det_hist, per * c->n_clusters));
+    MD_CUDA(dev_alloc(&c->d_det_crossed, static_cast<size_t>(c->n_total)));
+    MD_CUDA(cudaMemsetAsync(c->d_det_hist, 0, sizeof(unsigned long long) * per * c->n_clusters,
+                            c->stream));
+    MD_CUDA(cudaMemsetAsync(c->d_det_crossed, 0, static_cast<size_t>(c->n_total), c->stream));
+  }
+  md::ClusterDev& cl = c->cl[cluster];
+  if (d) {
+    cl.det_nbins = d->n_bins;
+    cl.det_r2 = d->radius * d->radius;
+    cl.det_cos = std::cos(d->cone_half_angle_deg * 3.14159265358979323846 / 180.0);
+    cl.det_emax = d->e_max_ev;
+    for (int k = 0; k < 3; ++k) cl.det_c[k] = d->center[k];
+    cl.det_off = static_cast<long long>(per) * cluster;
+    // a new configuration starts empty
+    MD_CUDA(cudaMemsetAsync(c->d_det_hist + per * cluster, 0, sizeof(unsigned long long) * per,
+                            c->stream));
+    MD_CUDA(cudaMemsetAsync(c->d_det_crossed + cl.off, 0, static_cast<size_t>(cl.n_pad),
+                            c->stream));
+  } else {
+    cl.det_nbins = 0;
+  }
+  MD_CUDA(cudaMemcpyAsync(c->d_cl + cluster, &cl, sizeof(md::ClusterDev),
+                          cudaMemcpyHostToDevice, c->stream));
+  MD_CUDA(cudaStreamSynchronize(c->stream));
+  destroy_graph(c);  // kernel arguments changed
+  return check_device_error(c);
+}
+
+md_status md_get_iedf(md_ctx* c, int32_t cluster, uint64_t* detected, uint64_t* inside) {
+  if (!c) return fail(MD_ERR_ARG, "ctx is NULL");
+  if (cluster < 0 || cluster >= c->n_clusters) return fail(MD_ERR_ARG, "bad cluster index");
+  const md::ClusterDev& cl = c->cl[cluster];
+  if (!c->d_det_hist || cl.det_nbins <= 0)
+    return fail(MD_ERR_STATE, "cluster %d has no detectors (md_set_detectors)", cluster);
+  const int nb1 = cl.det_nbins + 1;
+  std::vector<unsigned long long> h(5 * static_cast<size_t>(nb1));
+  MD_CUDA(cudaMemcpyAsync(h.data(), c->d_det_hist + cl.det_off,
+                          sizeof(unsigned long long) * h.size(), cudaMemcpyDeviceToHost,
+                          c->stream));
+  std::vector<unsigned long long> hin;
+  if (inside) {
+    unsigned long long* d_in = nullptr;
+    MD_CUDA(dev_alloc(&d_in, static_cast<size_t>(nb1)));
+    cudaError_t e = cudaMemsetAsync(d_in, 0, sizeof(unsigned long long) * nb1, c->stream);
+    if (e == cudaSuccess)
+      e = md::launch_iedf_inside(cl, c->d_u[0], c->d_u[1], c->d_u[2], c->d_mass, c->d_z,
+                                 c->d_kind, c->d_det_crossed, d_in, c->stream);
+    hin.resize(nb1);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(hin.data(), d_in, sizeof(unsigned long long) * nb1,
+                          cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(d_in);
+    if (e != cudaSuccess) return cuda_fail(e, "inside IEDF");
+  }
+  MD_CUDA(cudaStreamSynchronize(c->stream));
+  if (detected)
+    for (size_t k = 0; k < h.size(); ++k) detected[k] = h[k];
+  if (inside)
+    for (int k = 0; k < nb1; ++k) inside[k] = hin[k];
+  return check_device_error(c);
 }
 
 md_status md_get_ionization(md_ctx* c, int32_t cluster, double* emag, double* ne, double* te,
@@ -1141,6 +1229,11 @@ md_status md_autotune(md_ctx* c, int32_t steps, double* times_ms, int32_t cap) {
   if (c->d_vel) bufs.push_back({c->d_vel, N * sizeof(float4), nullptr});
   if (c->d_ion_next)
     bufs.push_back({c->d_ion_next, sizeof(long long) * c->n_clusters, nullptr});
+  if (c->d_det_hist) {
+    bufs.push_back({c->d_det_hist, sizeof(unsigned long long) * c->n_clusters * 5 *
+                                       (kDetMaxBins + 1), nullptr});
+    bufs.push_back({c->d_det_crossed, N, nullptr});
+  }
   auto release = [&]() {
     for (auto& b : bufs) cudaFree(b.copy);
   };

@@ -21,6 +21,10 @@ struct ClusterDev {
   double a0, tau, t0, dt, box, t_switch;
   float eps2;
   int pol, env, boundary;
+  // ion energy detectors on the sphere |x - det_c| = sqrt(det_r2) (off: det_nbins = 0)
+  int det_nbins;
+  double det_r2, det_cos, det_emax, det_c[3];
+  long long det_off;  // first histogram entry of the cluster (5 x (det_nbins + 1) entries)
 };
 
 constexpr int kMaxZ = 16;
@@ -77,6 +81,10 @@ struct StepArgs {
   // FP32 copy (ux, uy, uz, w) of every record's u and weight, read by the
   // ionization pass for the local electron moments (nullptr: not kept)
   float4* vel;
+  // ion energy detectors (nullptr: none configured)
+  unsigned long long* det_hist;
+  unsigned char* det_crossed;
+  const double* mass;
 };
 
 // Arguments of the ionization kernels of one cluster.

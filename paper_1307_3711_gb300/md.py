@@ -76,6 +76,15 @@ class MlpTrainConfig(C.Structure):
                 ("te_max", C.c_double)]
 
 
+class DetectorConfig(C.Structure):
+    _fields_ = [("radius", C.c_double), ("cone_half_angle_deg", C.c_double),
+                ("e_max_ev", C.c_double), ("n_bins", C.c_int32), ("reserved", C.c_int32),
+                ("center", C.c_double * 3)]
+
+
+DETECTORS = ("+x", "-x", "+y", "-y", "all")
+
+
 class MlpReport(C.Structure):
     _fields_ = [("loss_first", C.c_double), ("loss_last", C.c_double),
                 ("holdout_median_dlog10", C.c_double), ("holdout_p99_dlog10", C.c_double),
@@ -101,6 +110,8 @@ _SIGS = {
     "md_wait_selftest": (_st, [_ctx_p, C.c_double]),
     "md_ionize": (_st, [_ctx_p]),
     "md_get_ionization": (_st, [_ctx_p, C.c_int32, _p, _p, _p, _p, _p]),
+    "md_set_detectors": (_st, [_ctx_p, C.c_int32, C.POINTER(DetectorConfig)]),
+    "md_get_iedf": (_st, [_ctx_p, C.c_int32, _p, _p]),
     "md_tuning_list": (C.c_int32, [C.POINTER(Tuning), C.c_int32]),
     "md_set_tuning": (_st, [_ctx_p, C.POINTER(Tuning)]),
     "md_get_tuning": (_st, [_ctx_p, C.POINTER(Tuning)]),
@@ -322,6 +333,30 @@ class Context:
         _check(_lib.md_get_ionization(self._h, cluster, _ptr(emag), _ptr(ne), _ptr(te),
                                       _ptr(prob), _ptr(fired)))
         return {"emag": emag, "ne": ne, "te": te, "prob": prob, "fired": fired}
+
+    def set_detectors(self, cluster, radius, cone_deg=30.0, e_max_ev=1e4, n_bins=100,
+                      center=(0.0, 0.0, 0.0)):
+        """Ion energy detectors on the sphere of `radius` (paper units); None
+        as radius switches them off."""
+        self._det_bins = getattr(self, "_det_bins", {})
+        if radius is None:
+            _check(_lib.md_set_detectors(self._h, cluster, None))
+            self._det_bins.pop(cluster, None)
+            return
+        d = DetectorConfig(float(radius), float(cone_deg), float(e_max_ev), int(n_bins), 0,
+                           (C.c_double * 3)(*center))
+        _check(_lib.md_set_detectors(self._h, cluster, C.byref(d)))
+        self._det_bins[cluster] = int(n_bins)
+
+    def iedf(self, cluster=0):
+        """(detected [5][n_bins + 1], inside [n_bins + 1]) ion counts per energy bin."""
+        nb = getattr(self, "_det_bins", {}).get(cluster)
+        if nb is None:  # no detectors: the library reports the state error
+            _check(_lib.md_get_iedf(self._h, cluster, None, None))
+        det = np.zeros((5, nb + 1), np.uint64)
+        ins = np.zeros(nb + 1, np.uint64)
+        _check(_lib.md_get_iedf(self._h, cluster, _ptr(det), _ptr(ins)))
+        return det, ins
 
     def set_rate_mlp(self, params, domain: "MlpTrainConfig"):
         w = np.ascontiguousarray(params, dtype=np.float32)

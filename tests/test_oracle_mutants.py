@@ -81,6 +81,15 @@ MUTANTS_OTHER = [
      "grad[OFF_W2 + k * NH + j] += da2[j] * h1[k];", "test_oracle_mlp.py"),
     ("mlp_loss_scale", "mlp_oracle.c", "dy[zs] = 2.0 * r / n;", "dy[zs] = r / n;",
      "test_oracle_mlp.py"),
+    ("detector_no_cone", "md_oracle.c", "if (b0 >= c) hist[0 * (nbins + 1) + bin] += 1;",
+     "if (b0 >= 0.0) hist[0 * (nbins + 1) + bin] += 1;", "test_oracle_detectors.py"),
+    ("detector_inward", "md_oracle.c", "if (!(rp2 < R2 && rn2 >= R2)) continue;",
+     "if (!(rp2 >= R2 && rn2 < R2)) continue;", "test_oracle_detectors.py"),
+    ("detector_gamma_not_minus_one", "md_oracle.c",
+     "return (uu / (sqrt(1.0 + uu) + 1.0)) * mass * OR_ME_C2_EV;",
+     "return sqrt(1.0 + uu) * mass * OR_ME_C2_EV;", "test_oracle_detectors.py"),
+    ("detector_no_once", "md_oracle.c", "        crossed[i] = 1;\n", "\n",
+     "test_oracle_detectors.py"),
 ]
 
 
