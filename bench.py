@@ -37,6 +37,11 @@ METRIC = "Coulomb pair interactions/s & steps/s at N=200k on 1 GB300; force err 
 UNIT = "pair/s"
 RECORD_BYTES = 3 * 8 + 3 * 8 + 4 + 8 + 8 + 1   # x, u, z, mass, w, kind per record
 FP32_INSTR_PER_PAIR = 12
+# DRAM bytes (read + write) per launch of the step kernel, from one ncu capture
+# of the named workload in the named kernel configuration
+# (profiles/k_step_traffic_xe3_200k.md); reported only when the timed run uses
+# that configuration.
+STEP_TRAFFIC_BYTES = {("xe3_200k", 200000, 128, 4, 512, False): 33.54e6}
 L2_FLUSH_BYTES = 512 << 20
 WORKLOAD_TEXT = {
     "xe3_200k": "{name}: N={n} (Xe3+ ions + electrons, 10 eV), one cluster per GPU",
@@ -468,7 +473,9 @@ def run_native(args):
             "frac_of_measured_ffma": achieved / peak_probe,
             "measured_ffma_tflops": 2 * ffma_per_s / 1e12,
             "measured_packed_f32x2_fma_tflops": 2 * ffma2_per_s / 1e12,
-            "traffic": None,
+            "traffic": STEP_TRAFFIC_BYTES.get((args.workload, n, tuning[0], tuning[1],
+                                                tuning[2], bool(tuning[5]))),
+            "traffic_unit": "B per launch (dram read + write, ncu)",
         },
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": RECORD_BYTES * n,
