@@ -196,6 +196,8 @@ md_status md_set_particles(md_ctx *ctx, int32_t cluster, const md_particles *in)
 /* md_get_fields: the Coulomb field (without the laser) and, if phi != NULL,
  * the potential K_C sum_{j!=i} Q_j / sqrt(r^2+eps^2) at the current positions
  * of cluster `cluster`, computed by the same FP32/Kahan sum as md_step.
+ * In clusters with ionization, records in a block of 256 targets with no
+ * active record get zero, and uncharged groups of 64 sources are skipped.
  * e: host [n][3], phi: host [n] or NULL.  Synchronous. */
 md_status md_get_fields(md_ctx *ctx, int32_t cluster, double *e, double *phi);
 

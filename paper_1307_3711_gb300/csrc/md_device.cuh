@@ -843,6 +843,9 @@ __device__ __forceinline__ int det_bin(double ke, double emax, int nbins) {
 
 // Records ion i if it crossed the detector sphere outward in this step:
 // histograms +x, -x, +y, -y (cone of half-angle acos(det_cos)) and all.
+// Compiled only into the step kernels instantiated with detectors: present in
+// the epilogue, even behind a branch that is never taken, it changes the code
+// of the whole kernel (2.6 % slower).
 __device__ __forceinline__ void detect(unsigned long long* hist, unsigned char* crossed,
                                        const ClusterDev& c, long long i, double x0, double y0,
                                        double z0, double x1, double y1, double z1, double ux,
@@ -867,6 +870,7 @@ __device__ __forceinline__ void detect(unsigned long long* hist, unsigned char* 
 
 // Laser + Boris kick (FP32 increment) + FP64 drift + boundary for record i
 // with Coulomb field (ex, ey, ez); writes x, u and the next j-stream entry.
+template <bool DET>
 __device__ __forceinline__ void push_record(const StepArgs& a, const ClusterDev& c, long long i,
                                             double ex, double ey, double ez, const float* las,
                                             double t_next, const float4* cur, float4* nxt) {
@@ -890,9 +894,11 @@ __device__ __forceinline__ void push_record(const StepArgs& a, const ClusterDev&
     Y = wrap_periodic(Y, c.box);
     Z = wrap_periodic(Z, c.box);
   }
-  if (c.det_nbins > 0 && a.det_hist && a.qm[i] > 0.0f)
-    detect(a.det_hist, a.det_crossed, c, i, a.x[i], a.y[i], a.z[i], X, Y, Z, Ux, Uy, Uz,
-           a.mass[i]);
+  if constexpr (DET) {
+    if (c.det_nbins > 0 && a.det_hist && a.qm[i] > 0.0f)
+      detect(a.det_hist, a.det_crossed, c, i, a.x[i], a.y[i], a.z[i], X, Y, Z, Ux, Uy, Uz,
+             a.mass[i]);
+  }
   a.x[i] = X;
   a.y[i] = Y;
   a.z[i] = Z;
@@ -913,7 +919,7 @@ __device__ __forceinline__ void push_record(const StepArgs& a, const ClusterDev&
 // One full MD step for every work unit (cluster, i-block): field at x^n from
 // all sources of the cluster, laser at t_n, Boris kick, FP64 drift, boundary,
 // new j-stream entry.  Persistent: CTAs take units from an atomic ticket.
-template <int THREADS, int R, int TILE, int STAGES, bool PACK, int MINB>
+template <int THREADS, int R, int TILE, int STAGES, bool PACK, int MINB, bool DET>
 __global__ void __launch_bounds__(THREADS, MINB) k_step(const StepArgs a) {
   __shared__ Stage<TILE, STAGES> sm;
   __shared__ DupTile<PACK ? TILE : 1> dup;
@@ -1011,7 +1017,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_step(const StepArgs a) {
             if (i >= eend) continue;
             double ex, ey, ez;
             field_of(r, ex, ey, ez);
-            push_record(a, s_c, i, ex, ey, ez, s_las, t_next, cur2, nxt);
+            push_record<DET>(a, s_c, i, ex, ey, ez, s_las, t_next, cur2, nxt);
           }
         } else {
 #pragma unroll
@@ -1020,7 +1026,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_step(const StepArgs a) {
             if (i >= eend) continue;
             double ex, ey, ez;
             field_of(r, ex, ey, ez);
-            push_record(a, s_c, i, ex, ey, ez, s_las, t_next, cur2, nxt);
+            push_record<DET>(a, s_c, i, ex, ey, ez, s_las, t_next, cur2, nxt);
           }
         }
       } else {
@@ -1061,7 +1067,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_step(const StepArgs a) {
               ey += __ldcg(p + 1);
               ez += __ldcg(p + 2);
             }
-            push_record(a, s_c, i, ex, ey, ez, s_las, t_next, cur2, nxt);
+            push_record<DET>(a, s_c, i, ex, ey, ez, s_las, t_next, cur2, nxt);
           }
         }
       }
@@ -1096,6 +1102,18 @@ __global__ void __launch_bounds__(THREADS) k_field(const FieldArgs a) {
   }
   __syncthreads();
   const long long i0 = static_cast<long long>(blockIdx.x) * (THREADS * R);
+  const long long i1 = (i0 + THREADS * R < a.nt ? i0 + THREADS * R : a.nt) - 1;
+  if (a.tgt_live && !any_live(a.tgt_live, a.gbase + i0, a.gbase + i1)) {
+    // no active record among these targets: zero field and potential
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const long long i = i0 + threadIdx.x + r * THREADS;
+      if (i >= a.nt) continue;
+      a.e[3 * i + 0] = a.e[3 * i + 1] = a.e[3 * i + 2] = 0.0;
+      if (POT && a.phi) a.phi[i] = 0.0;
+    }
+    return;
+  }
   float xi[R], yi[R], zi[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
@@ -1109,7 +1127,7 @@ __global__ void __launch_bounds__(THREADS) k_field(const FieldArgs a) {
   acc.zero();
   unsigned it = 0;
   if (!sum_sources<THREADS, R, TILE, STAGES, POT>(sm, it, a.src, a.ns, xi, yi, zi, a.eps2, acc,
-                                                   a.err, &s_abort))
+                                                   a.err, &s_abort, a.src_live, a.gbase))
     return;
 #pragma unroll
   for (int r = 0; r < R; ++r) {

@@ -19,6 +19,10 @@ struct KernelConfig {
   int min_blocks;  // launch bound: CTAs per SM the register budget is sized for
   cudaError_t (*launch_step)(const StepArgs& a, int grid, cudaStream_t s);
   cudaError_t (*max_blocks_per_sm)(int* out);
+  // the same configuration compiled with the ion energy detectors in the
+  // epilogue (used while any cluster of the context has detectors)
+  cudaError_t (*launch_step_det)(const StepArgs& a, int grid, cudaStream_t s);
+  cudaError_t (*max_blocks_per_sm_det)(int* out);
 };
 
 const KernelConfig* step_configs(int* count);

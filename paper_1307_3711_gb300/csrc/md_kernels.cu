@@ -105,21 +105,23 @@ __global__ void k_download(const DownloadArgs a) {  const long long k = static_c
 
 namespace {
 
-template <int T, int R, int TILE, int ST, bool PK, int MB>
+template <int T, int R, int TILE, int ST, bool PK, int MB, bool DET>
 cudaError_t launch_step_t(const StepArgs& a, int grid, cudaStream_t s) {
-  k_step<T, R, TILE, ST, PK, MB><<<grid, T, 0, s>>>(a);
+  k_step<T, R, TILE, ST, PK, MB, DET><<<grid, T, 0, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int T, int R, int TILE, int ST, bool PK, int MB>
+template <int T, int R, int TILE, int ST, bool PK, int MB, bool DET>
 cudaError_t blocks_per_sm_t(int* out) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_step<T, R, TILE, ST, PK, MB>, T, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_step<T, R, TILE, ST, PK, MB, DET>,
+                                                       T, 0);
 }
 
 // threads, i-particles per thread, sources per tile, TMA stages, packed, min CTAs per SM
-#define MD_STEP_CONFIG(T, R, TILE, ST, PK, MB) \
-  {T, R, TILE, ST, PK, MB, &launch_step_t<T, R, TILE, ST, PK, MB>, \
-   &blocks_per_sm_t<T, R, TILE, ST, PK, MB>}
+#define MD_STEP_CONFIG(T, R, TILE, ST, PK, MB)                                          \
+  {T, R, TILE, ST, PK, MB, &launch_step_t<T, R, TILE, ST, PK, MB, false>,              \
+   &blocks_per_sm_t<T, R, TILE, ST, PK, MB, false>,                                      \
+   &launch_step_t<T, R, TILE, ST, PK, MB, true>, &blocks_per_sm_t<T, R, TILE, ST, PK, MB, true>}
 
 // min CTAs per SM = 0 leaves the register budget to ptxas; a positive value
 // caps it at 64K / (threads x value)
@@ -437,6 +439,9 @@ extern "C" md_status md_coulomb_field_device_noalloc(const void* src, int64_t ns
   a.e = e;
   a.phi = phi;
   a.err = sc.err;
+  a.src_live = nullptr;
+  a.tgt_live = nullptr;
+  a.gbase = 0;
   const unsigned grid = static_cast<unsigned>(nblk * nseg);
   if (phi)
     k_field_noalloc<kNoAllocThreads, kNoAllocR, kNoAllocTile, 2, true>

@@ -118,6 +118,7 @@ struct md_ctx {
   // ion energy detectors (allocated by the first md_set_detectors)
   unsigned long long* d_det_hist = nullptr;  // [clusters][5][kDetMaxBins + 1]
   unsigned char* d_det_crossed = nullptr;    // [n_total]
+  bool det_on = false;                       // some cluster has detectors
   float* d_mlp = nullptr;              // surrogate parameters (device), if set
 };
 
@@ -306,7 +307,7 @@ md_status configure(md_ctx* c, int cfg, int ctas_per_sm, int jsplit) {
   const md::KernelConfig& k = cfgs[cfg];
   const long long per = static_cast<long long>(k.threads) * k.r;
   int bps = 0;
-  MD_CUDA(k.max_blocks_per_sm(&bps));
+  MD_CUDA(c->det_on ? k.max_blocks_per_sm_det(&bps) : k.max_blocks_per_sm(&bps));
   if (bps < 1) return fail(MD_ERR_CUDA, "kernel configuration %d does not fit on an SM", cfg);
   const int cps = ctas_per_sm > 0 ? std::min(ctas_per_sm, bps) : bps;
   const long long slots = static_cast<long long>(cps) * c->sm_count;
@@ -463,7 +464,8 @@ md_status launch_steps_direct(md_ctx* c, int n) {
       cudaError_t e = launch_ion_all(c, 0, c->stream);
       if (e != cudaSuccess) return cuda_fail(e, "ionization launch");
     }
-    cudaError_t e = cfgs[c->cfg].launch_step(a, c->grid, c->stream);
+    cudaError_t e = c->det_on ? cfgs[c->cfg].launch_step_det(a, c->grid, c->stream)
+                              : cfgs[c->cfg].launch_step(a, c->grid, c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
   }
   return MD_OK;
@@ -480,7 +482,9 @@ md_status build_graph(md_ctx* c) {
     const md::StepArgs a = step_args(c);
     for (int s = 0; s < kGraphSteps && e == cudaSuccess; ++s) {
       if (c->any_ion) e = launch_ion_all(c, 0, cs);
-      if (e == cudaSuccess) e = cfgs[c->cfg].launch_step(a, c->grid, cs);
+      if (e == cudaSuccess)
+        e = c->det_on ? cfgs[c->cfg].launch_step_det(a, c->grid, cs)
+                      : cfgs[c->cfg].launch_step(a, c->grid, cs);
     }
     cudaError_t e2 = cudaStreamEndCapture(cs, &g);
     if (e == cudaSuccess) e = e2;
@@ -919,6 +923,15 @@ md_status md_set_detectors(md_ctx* c, int32_t cluster, const md_detector_config*
                           cudaMemcpyHostToDevice, c->stream));
   MD_CUDA(cudaStreamSynchronize(c->stream));
   destroy_graph(c);  // kernel arguments changed
+  bool on = false;
+  for (const auto& k : c->cl) on = on || k.det_nbins > 0;
+  if (on != c->det_on) {
+    // the step kernels with and without the detector epilogue are separate
+    // instantiations (possibly with other occupancy): size the grid anew
+    c->det_on = on;
+    md_status st = configure(c, c->cfg, c->ctas_per_sm, c->jsplit);
+    if (st != MD_OK) return st;
+  }
   return check_device_error(c);
 }
 
@@ -1036,6 +1049,9 @@ static md_status run_fields(md_ctx* c, int ci, bool potential) {
   a.e = c->d_e;
   a.phi = potential ? c->d_phi : nullptr;
   a.err = c->d_err;
+  a.src_live = c->d_src_live;
+  a.tgt_live = c->d_tgt_live;
+  a.gbase = cl.off;
   MD_CUDA(md::launch_field(a, potential, c->stream));
   return MD_OK;
 }
@@ -1260,7 +1276,10 @@ md_status md_autotune(md_ctx* c, int32_t steps, double* times_ms, int32_t cap) {
   for (int i = 0; i < n && st == MD_OK; ++i) {
     if (times_ms && i < cap) times_ms[i] = -1.0;
     int bps = 0;
-    if (cfgs[i].max_blocks_per_sm(&bps) != cudaSuccess || bps < 1) continue;  // does not fit
+    if ((c->det_on ? cfgs[i].max_blocks_per_sm_det(&bps) : cfgs[i].max_blocks_per_sm(&bps)) !=
+            cudaSuccess ||
+        bps < 1)
+      continue;  // does not fit
     st = configure(c, i, 0, 0);
     if (st != MD_OK) break;
     st = launch_steps_direct(c, 1);  // warm-up
@@ -1317,6 +1336,9 @@ md_status md_coulomb_field_device(const void* src, int64_t ns, const void* tgt, 
   a.e = e;
   a.phi = phi;
   a.err = d_err;
+  a.src_live = nullptr;
+  a.tgt_live = nullptr;
+  a.gbase = 0;
   MD_CUDA(md::launch_field(a, phi != nullptr, static_cast<cudaStream_t>(stream)));
   return MD_OK;
 }

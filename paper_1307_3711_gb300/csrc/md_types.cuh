@@ -129,6 +129,11 @@ struct FieldArgs {
   double* e;              // [nt][3]
   double* phi;            // [nt] or nullptr
   int* err;
+  // liveness flags of the context (nullptr: everything live); source record j
+  // and target record i are global records gbase + j and gbase + i
+  const unsigned char* src_live;
+  const unsigned char* tgt_live;
+  long long gbase;
 };
 
 struct DiagPartial {
