@@ -266,6 +266,43 @@ def ar_ionize_context(md, args, rank, stream):
     return ctx, [w], None, info
 
 
+def precision_study(md, ctx, w, n_targets=10000, n_oracle=2000, seed=0):
+    """FP32/Kahan field of the state against the FP64 GPU reference on a
+    seeded subset of targets, and the FP64 GPU reference against the FP64
+    oracle (bitwise) on part of that subset."""
+    import torch
+    import oracle
+    c = w.cluster
+    kc = md.coulomb_constant(w.lambda_um)
+    g = ctx.get_particles(0)
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(c.n, min(n_targets, c.n), replace=False)).astype(np.int64)
+    q = np.where(g.kind != md.KIND_INACTIVE, g.w * g.z, 0.0)
+    dev = lambda a: torch.tensor(np.ascontiguousarray(a), device="cuda")
+    dxs, dqs, dxt, dsi = dev(g.x), dev(q), dev(g.x[idx]), dev(idx)
+    e64 = torch.zeros((len(idx), 3), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    md.coulomb_field_fp64_device(dxs.data_ptr(), dqs.data_ptr(), c.n, dxt.data_ptr(),
+                                 dsi.data_ptr(), len(idx), w.eps, kc, e64.data_ptr(), 0)
+    torch.cuda.synchronize()
+    t64 = time.perf_counter() - t0
+    e64 = e64.cpu().numpy()
+    e32 = ctx.fields(0)[idx]
+    nrm = np.linalg.norm(e64, axis=1)
+    rel = np.linalg.norm(e32 - e64, axis=1) / np.maximum(nrm, np.sqrt(np.mean(nrm ** 2)))
+    m = min(n_oracle, len(idx))
+    e_or = oracle.coulomb_field(g.x[idx[:m]], g.x, q, w.eps, kc, self_idx=idx[:m],
+                                nthreads=os.cpu_count() or 1)
+    return {"targets": int(len(idx)), "fp64_gpu_reference_s": t64,
+            "fp32_kahan_vs_fp64_gpu": {"median": float(np.median(rel)),
+                                       "p99": float(np.percentile(rel, 99)),
+                                       "max": float(rel.max())},
+            "fp64_gpu_vs_oracle_bitwise_equal": f"{int(np.sum(np.all(e_or == e64[:m], axis=1)))}"
+                                                f"/{m} targets",
+            "metric": "|E - E_fp64| / max(|E_fp64|, rms|E_fp64|), state after the timed steps"}
+
+
 def build_contexts(md, args, rank, stream):
     """The workload's clusters -> (context, list of workloads, pairs per step)."""
     if args.workload == "scan256":
@@ -329,6 +366,7 @@ def run_native(args):
         ctx.step(1)
     torch.cuda.synchronize()
 
+    d_before = ctx.diagnostics(0) if args.workload == "precision_1m" else None
     sampler = ClockSampler(gpu_id_for(local))
     time.sleep(0.3)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -359,6 +397,17 @@ def run_native(args):
     ms_per_step = t_max * 1e3 / args.steps
     value = world * pairs_per_step * args.steps / t_max
 
+    precision = None
+    if args.workload == "precision_1m":
+        d_after = ctx.diagnostics(0)
+        precision = precision_study(md, ctx, w)
+        precision["energy_drift"] = {
+            "relative_to_pe0": (d_after["total"] - d_before["total"]) / abs(d_before["pe"]),
+            "total_before": d_before["total"], "total_after": d_after["total"],
+            "pe_before": d_before["pe"], "ke_after": d_after["ke"],
+            "steps": args.steps, "dt": w.dt, "laser": "off",
+            "what": "(E_total after - before) / |PE before| over the timed steps (the cluster "
+                    "starts cold: KE = 0), FP64 sums, m_e c^2 units"}
     ion_state = None
     if ionizing:
         # the state the timed steps reached (the end-to-end leg below restarts
@@ -485,6 +534,7 @@ def run_native(args):
         "gpu_launches": args.steps * launches_per_step,
         "cpu_baseline": cpu,
         "force_err_vs_fp64": force_err,
+        "precision_study": precision,
     }
     print(json.dumps(line), flush=True)
 

@@ -328,6 +328,25 @@ md_status md_coulomb_field_device_noalloc(const void *src, int64_t ns, const voi
                                           int64_t nt, float eps2, int64_t self_offset,
                                           double *e, double *phi, void *stream);
 
+/* md_coulomb_field_fp64_device: the FP64 reference of the direct sum (the
+ * precision study's reference, not on the hot path).  For each target i:
+ *   E_i   = kc sum_j Q_j (x_i - x_j) / (|x_i - x_j|^2 + eps^2)^{3/2}
+ *   phi_i = kc sum_j Q_j / sqrt(|x_i - x_j|^2 + eps^2)
+ * over sources j in index order, skipping j == self_idx[i] and Q_j == 0, every
+ * operation rounded to nearest in the order of this formula (no fused
+ * multiply-add), so that a plain sequential program evaluating the same
+ * formula in the same order gets the same bits.
+ *   xs: device double[ns][3] source positions; qs: device double[ns] macro
+ *   charges w z; xt: device double[nt][3] targets; self_idx: device
+ *   int64[nt] (the source that is target i, or -1) or NULL; eps >= 0, kc > 0
+ *   (paper units); e: device double[nt][3] out; phi: device double[nt] or NULL.
+ * Caller-owned device buffers.  One thread per target: O(nt ns) FP64
+ * operations, meant for subsets of targets.  Asynchronous on `stream`. */
+md_status md_coulomb_field_fp64_device(const double *xs, const double *qs, int64_t ns,
+                                       const double *xt, const int64_t *self_idx, int64_t nt,
+                                       double eps, double kc, double *e, double *phi,
+                                       void *stream);
+
 /* ---- learned rate surrogate ------------------------------------------------
  * Not from the paper: a 4 -> 64 -> 64 -> 8 MLP (SiLU) standing in for the
  * per-ion rate evaluation of the ionization pass.  The hidden layers run on

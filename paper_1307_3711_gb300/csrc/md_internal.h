@@ -60,6 +60,11 @@ md_status report_error(md_status status, const char* msg);
 md_status report_cuda_error(cudaError_t e, const char* what);
 cudaError_t launch_download(const DownloadArgs& a, cudaStream_t s);
 
+// FP64 reference direct sum (see md_coulomb_field_fp64_device).
+cudaError_t launch_field_fp64(const double* xs, const double* qs, long long ns, const double* xt,
+                              const long long* self_idx, long long nt, double eps, double kc,
+                              double* e, double* phi, cudaStream_t s);
+
 // Energy histogram [det_nbins + 1] of the cluster's ions not recorded by the
 // detectors (added to `hist`).
 cudaError_t launch_iedf_inside(const ClusterDev& c, const double* ux, const double* uy,

@@ -88,6 +88,69 @@ cudaError_t launch_iedf_inside(const ClusterDev& c, const double* ux, const doub
   return cudaGetLastError();
 }
 
+// FP64 reference of the direct sum: per target, the plain sum over sources in
+// index order of Q_j (x_i - x_j) / (r^2 + eps^2)^{3/2} and Q_j / r, skipping
+// the target's own record and uncharged sources, each operation rounded to
+// nearest in the order written (no fused multiply-add).  Sources are staged
+// through shared memory in tiles of kRefTile.
+constexpr int kRefThreads = 128;
+constexpr int kRefTile = 256;
+
+__global__ void __launch_bounds__(kRefThreads)
+    k_field_fp64(const double* __restrict__ xs, const double* __restrict__ qs, long long ns,
+                 const double* __restrict__ xt, const long long* __restrict__ self_idx,
+                 long long nt, double eps, double kc, double* e, double* phi) {
+  __shared__ double sx[kRefTile], sy[kRefTile], sz[kRefTile], sq[kRefTile];
+  const long long i = static_cast<long long>(blockIdx.x) * kRefThreads + threadIdx.x;
+  const bool live = i < nt;
+  const double xi = live ? xt[3 * i] : 0.0, yi = live ? xt[3 * i + 1] : 0.0,
+               zi = live ? xt[3 * i + 2] : 0.0;
+  const long long self = (live && self_idx) ? self_idx[i] : -1;
+  const double eps2 = __dmul_rn(eps, eps);
+  double ex = 0.0, ey = 0.0, ez = 0.0, ph = 0.0;
+  for (long long j0 = 0; j0 < ns; j0 += kRefTile) {
+    const int cnt = static_cast<int>(ns - j0 < kRefTile ? ns - j0 : kRefTile);
+    __syncthreads();
+    for (int k = threadIdx.x; k < cnt; k += kRefThreads) {
+      sx[k] = xs[3 * (j0 + k)];
+      sy[k] = xs[3 * (j0 + k) + 1];
+      sz[k] = xs[3 * (j0 + k) + 2];
+      sq[k] = qs[j0 + k];
+    }
+    __syncthreads();
+    if (!live) continue;
+    for (int k = 0; k < cnt; ++k) {
+      const double q = sq[k];
+      if (j0 + k == self || q == 0.0) continue;
+      const double dx = __dsub_rn(xi, sx[k]);
+      const double dy = __dsub_rn(yi, sy[k]);
+      const double dz = __dsub_rn(zi, sz[k]);
+      const double r2 = __dadd_rn(
+          __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)), eps2);
+      const double r = __dsqrt_rn(r2);
+      const double inv_r3 = __ddiv_rn(1.0, __dmul_rn(r2, r));
+      ex = __dadd_rn(ex, __dmul_rn(__dmul_rn(q, dx), inv_r3));
+      ey = __dadd_rn(ey, __dmul_rn(__dmul_rn(q, dy), inv_r3));
+      ez = __dadd_rn(ez, __dmul_rn(__dmul_rn(q, dz), inv_r3));
+      ph = __dadd_rn(ph, __ddiv_rn(q, r));
+    }
+  }
+  if (!live) return;
+  e[3 * i] = __dmul_rn(kc, ex);
+  e[3 * i + 1] = __dmul_rn(kc, ey);
+  e[3 * i + 2] = __dmul_rn(kc, ez);
+  if (phi) phi[i] = __dmul_rn(kc, ph);
+}
+
+cudaError_t launch_field_fp64(const double* xs, const double* qs, long long ns, const double* xt,
+                              const long long* self_idx, long long nt, double eps, double kc,
+                              double* e, double* phi, cudaStream_t s) {
+  if (nt <= 0) return cudaSuccess;
+  k_field_fp64<<<static_cast<unsigned>((nt + kRefThreads - 1) / kRefThreads), kRefThreads, 0, s>>>(
+      xs, qs, ns, xt, self_idx, nt, eps, kc, e, phi);
+  return cudaGetLastError();
+}
+
 __global__ void k_download(const DownloadArgs a) {  const long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k >= a.n) return;
   const long long i = a.off + k;

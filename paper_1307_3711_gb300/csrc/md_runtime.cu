@@ -1311,6 +1311,19 @@ md_status md_autotune(md_ctx* c, int32_t steps, double* times_ms, int32_t cap) {
   return configure(c, best_cfg, 0, 0);
 }
 
+md_status md_coulomb_field_fp64_device(const double* xs, const double* qs, int64_t ns,
+                                       const double* xt, const int64_t* self_idx, int64_t nt,
+                                       double eps, double kc, double* e, double* phi,
+                                       void* stream) {
+  if (ns < 0 || nt < 0) return fail(MD_ERR_ARG, "negative size");
+  if (nt == 0) return MD_OK;
+  if (!xs || !qs || !xt || !e) return fail(MD_ERR_ARG, "NULL pointer");
+  if (!(eps >= 0.0) || !(kc > 0.0)) return fail(MD_ERR_ARG, "eps must be >= 0 and kc > 0");
+  MD_CUDA(md::launch_field_fp64(xs, qs, ns, xt, reinterpret_cast<const long long*>(self_idx), nt,
+                                eps, kc, e, phi, static_cast<cudaStream_t>(stream)));
+  return MD_OK;
+}
+
 md_status md_coulomb_field_device(const void* src, int64_t ns, const void* tgt, int64_t nt,
                                   float eps2, int64_t self_offset, double* e, double* phi,
                                   void* stream) {

@@ -111,6 +111,8 @@ _SIGS = {
     "md_ionize": (_st, [_ctx_p]),
     "md_get_ionization": (_st, [_ctx_p, C.c_int32, _p, _p, _p, _p, _p]),
     "md_set_detectors": (_st, [_ctx_p, C.c_int32, C.POINTER(DetectorConfig)]),
+    "md_coulomb_field_fp64_device": (_st, [_p, _p, C.c_int64, _p, _p, C.c_int64, C.c_double,
+                                           C.c_double, _p, _p, _p]),
     "md_get_iedf": (_st, [_ctx_p, C.c_int32, _p, _p]),
     "md_tuning_list": (C.c_int32, [C.POINTER(Tuning), C.c_int32]),
     "md_set_tuning": (_st, [_ctx_p, C.POINTER(Tuning)]),
@@ -388,6 +390,15 @@ def coulomb_field_device(src_ptr: int, ns: int, tgt_ptr: int, nt: int, eps2: flo
                                         C.c_void_p(e_ptr),
                                         C.c_void_p(phi_ptr) if phi_ptr else None,
                                         C.c_void_p(stream) if stream else None))
+
+
+def coulomb_field_fp64_device(xs_ptr: int, qs_ptr: int, ns: int, xt_ptr: int, self_ptr: int,
+                              nt: int, eps: float, kc: float, e_ptr: int, phi_ptr: int = 0,
+                              stream=None):
+    """FP64 reference direct sum on caller device buffers (see md.h)."""
+    _check(_lib.md_coulomb_field_fp64_device(_vp(xs_ptr), _vp(qs_ptr), int(ns), _vp(xt_ptr),
+                                             _vp(self_ptr), int(nt), float(eps), float(kc),
+                                             _vp(e_ptr), _vp(phi_ptr), _vp(stream)))
 
 
 def coulomb_field_device_noalloc(src_ptr: int, ns: int, tgt_ptr: int, nt: int, eps2: float,
