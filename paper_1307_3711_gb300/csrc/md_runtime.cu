@@ -140,6 +140,17 @@ struct RawView {
   unsigned char* kind;
 };
 
+// Whether host memory is page-locked (registered or allocated by CUDA), so
+// that an asynchronous copy can use it directly.
+bool is_pinned(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the error of an unknown pointer
+    return false;
+  }
+  return at.type == cudaMemoryTypeHost;
+}
+
 RawView raw_view(unsigned char* base, long long n) {
   RawView v;
   size_t o = 0;
@@ -561,17 +572,29 @@ md_status upload_cluster(md_ctx* c, int ci, const md_particles& p) {
                   "cluster %d: %lld more ionizations possible but only %lld free electron slots "
                   "after the last active one", ci, remaining, end - next_slot);
   }
+  // each array goes to the device raw buffer directly when the caller's
+  // memory is page-locked, else through the context's pinned staging buffer
   RawView h = raw_view(c->h_raw, n);
-  std::memcpy(h.x, p.x, sizeof(double) * 3 * n);
-  std::memcpy(h.u, p.u, sizeof(double) * 3 * n);
-  std::memcpy(h.mass, p.mass, sizeof(double) * n);
-  std::memcpy(h.w, p.w, sizeof(double) * n);
-  std::memcpy(h.z, p.z, sizeof(int) * n);
-  for (long long i = 0; i < n; ++i)
-    h.kind[i] = p.kind ? p.kind[i] : static_cast<unsigned char>(p.z[i] < 0 ? 1 : 0);
-  MD_CUDA(cudaMemcpyAsync(c->d_raw, c->h_raw, raw_record_bytes() * n, cudaMemcpyHostToDevice,
-                          c->stream));
   RawView d = raw_view(c->d_raw, n);
+  auto put = [&](void* dst, void* stage, const void* src, size_t bytes) -> cudaError_t {
+    if (!is_pinned(src)) {
+      std::memcpy(stage, src, bytes);
+      src = stage;
+    }
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream);
+  };
+  MD_CUDA(put(d.x, h.x, p.x, sizeof(double) * 3 * n));
+  MD_CUDA(put(d.u, h.u, p.u, sizeof(double) * 3 * n));
+  MD_CUDA(put(d.mass, h.mass, p.mass, sizeof(double) * n));
+  MD_CUDA(put(d.w, h.w, p.w, sizeof(double) * n));
+  MD_CUDA(put(d.z, h.z, p.z, sizeof(int) * n));
+  if (p.kind) {
+    MD_CUDA(put(d.kind, h.kind, p.kind, n));
+  } else {
+    for (long long i = 0; i < n; ++i)
+      h.kind[i] = static_cast<unsigned char>(p.z[i] < 0 ? MD_KIND_ELECTRON : MD_KIND_ION);
+    MD_CUDA(cudaMemcpyAsync(d.kind, h.kind, n, cudaMemcpyHostToDevice, c->stream));
+  }
   md::UploadArgs a;
   a.hx = d.x;
   a.hu = d.u;
@@ -1148,16 +1171,31 @@ md_status md_get_particles(md_ctx* c, int32_t cluster, md_particles* out) {
   a.zq = c->d_z;
   a.kind = c->d_kind;
   MD_CUDA(md::launch_download(a, c->stream));
-  MD_CUDA(cudaMemcpyAsync(c->h_raw, c->d_raw, raw_record_bytes() * n, cudaMemcpyDeviceToHost,
-                          c->stream));
-  MD_CUDA(cudaStreamSynchronize(c->stream));
+  // page-locked caller arrays receive their copy directly; the others go
+  // through the pinned staging buffer
   RawView h = raw_view(c->h_raw, n);
-  if (out->x) std::memcpy(out->x, h.x, sizeof(double) * 3 * n);
-  if (out->u) std::memcpy(out->u, h.u, sizeof(double) * 3 * n);
-  if (out->z) std::memcpy(out->z, h.z, sizeof(int) * n);
-  if (out->mass) std::memcpy(out->mass, h.mass, sizeof(double) * n);
-  if (out->w) std::memcpy(out->w, h.w, sizeof(double) * n);
-  if (out->kind) std::memcpy(out->kind, h.kind, n);
+  struct Part {
+    void* user;
+    void* stage;
+    const void* dev;
+    size_t bytes;
+    bool direct;
+  };
+  Part parts[6] = {{out->x, h.x, d.x, sizeof(double) * 3 * n, false},
+                   {out->u, h.u, d.u, sizeof(double) * 3 * n, false},
+                   {out->z, h.z, d.z, sizeof(int) * n, false},
+                   {out->mass, h.mass, d.mass, sizeof(double) * n, false},
+                   {out->w, h.w, d.w, sizeof(double) * n, false},
+                   {out->kind, h.kind, d.kind, static_cast<size_t>(n), false}};
+  for (Part& q : parts) {
+    if (!q.user) continue;
+    q.direct = is_pinned(q.user);
+    MD_CUDA(cudaMemcpyAsync(q.direct ? q.user : q.stage, q.dev, q.bytes, cudaMemcpyDeviceToHost,
+                            c->stream));
+  }
+  MD_CUDA(cudaStreamSynchronize(c->stream));
+  for (const Part& q : parts)
+    if (q.user && !q.direct) std::memcpy(q.user, q.stage, q.bytes);
   return check_device_error(c);
 }
 

@@ -407,3 +407,31 @@ def test_fp64_reference_field_matches_oracle_bitwise(md):
                                           potential=True)
     assert np.array_equal(e.cpu().numpy(), e_ref)
     assert np.array_equal(phi.cpu().numpy(), phi_ref)
+
+
+def test_pinned_and_pageable_host_buffers_give_the_same_records(md):
+    """md_set_particles / md_get_particles copy page-locked caller arrays
+    directly and pageable ones through the staging buffer: same records."""
+    import torch
+    w = synth.plain_fp64_2k(seed=3)
+    hp = md.HostParticles.from_cluster(w.cluster)
+
+    def pinned(a):
+        t = torch.empty(a.shape, dtype=getattr(torch, str(a.dtype)), pin_memory=True)
+        t.numpy()[...] = a
+        return t
+
+    keep = [pinned(getattr(hp, k)) for k in ("x", "u", "z", "mass", "w", "kind")]
+    hpp = md.HostParticles(*(t.numpy() for t in keep))
+    with md.Context([md.config_from_workload(w)], [hp]) as a, \
+            md.Context([md.config_from_workload(w)], [hp]) as b:
+        a.set_particles(0, hp)
+        b.set_particles(0, hpp)
+        a.step(3)
+        b.step(3)
+        ga = a.get_particles(0)
+        outp = md.HostParticles(*(pinned(np.zeros_like(getattr(hp, k))).numpy()
+                                  for k in ("x", "u", "z", "mass", "w", "kind")))
+        gb = b.get_particles(0, out=outp)
+        for k in ("x", "u", "z", "mass", "w", "kind"):
+            assert np.array_equal(getattr(ga, k), getattr(gb, k)), k
