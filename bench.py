@@ -120,6 +120,13 @@ class Dist:
             self.pg.destroy_process_group()
 
 
+def whole_job_value(world: int, pairs_per_step: float, steps: int, t_max: float) -> float:
+    """Pairs per second of the whole job: every rank advances its own cluster
+    (replicas, weak scaling) through the same number of steps, and the job
+    takes as long as its slowest rank."""
+    return world * pairs_per_step * steps / t_max
+
+
 # --------------------------------------------------------------- clocks --
 
 class ClockSampler:
@@ -395,7 +402,7 @@ def run_native(args):
     t_local = sum(step_ms) / 1e3
     t_max = dist.max(t_local)
     ms_per_step = t_max * 1e3 / args.steps
-    value = world * pairs_per_step * args.steps / t_max
+    value = whole_job_value(world, pairs_per_step, args.steps, t_max)
 
     precision = None
     if args.workload == "precision_1m":
