@@ -76,9 +76,11 @@ __global__ void __launch_bounds__(THREADS) k_ion_field(const IonArgs a) {
   }
   __syncthreads();
   const float4* __restrict__ cur = (step & 1) ? a.posq1 : a.posq0;
-  const float4* src = cur + a.c.off;
-  const float4* vsrc = a.vel + a.c.off;
-  const long long ns = a.c.n_pad;
+  // this CTA sums source segment blockIdx.y: records [j0, j0 + ns) of the cluster
+  const long long j0 = static_cast<long long>(blockIdx.y) * a.seg_len;
+  const long long ns = (a.c.n_pad - j0 < a.seg_len) ? a.c.n_pad - j0 : a.seg_len;
+  const float4* src = cur + a.c.off + j0;
+  const float4* vsrc = a.vel + a.c.off + j0;
   const long long t0 = static_cast<long long>(blockIdx.x) * (THREADS * R);
   const float rloc2 = static_cast<float>(a.ion.r_loc * a.ion.r_loc);
   const float eps2 = a.c.eps2;
@@ -101,7 +103,7 @@ __global__ void __launch_bounds__(THREADS) k_ion_field(const IonArgs a) {
   const int ntiles = static_cast<int>((ns + TILE - 1) / TILE);
   // only tiles holding a live group are copied and summed, in the same order
   // for the issuing thread and the consumers
-  const long long gb = a.c.off;
+  const long long gb = a.c.off + j0;
   int t = next_live_tile(a.src_live, gb, ns, 0, ntiles, TILE);
   int ti = t;
   unsigned issued = 0;
@@ -172,7 +174,7 @@ __global__ void __launch_bounds__(THREADS) k_ion_field(const IonArgs a) {
   for (int r = 0; r < R; ++r) {
     const long long tt = t0 + threadIdx.x + r * THREADS;
     if (tt >= a.ion.n_ions) continue;
-    double* o = a.scratch + 8 * tt;
+    double* o = a.scratch + kIonScratch * (static_cast<long long>(blockIdx.y) * a.ion.n_ions + tt);
     o[0] = -(static_cast<double>(acc.sx[r]) - acc.cx[r]);
     o[1] = -(static_cast<double>(acc.sy[r]) - acc.cy[r]);
     o[2] = -(static_cast<double>(acc.sz[r]) - acc.cz[r]);
@@ -181,6 +183,9 @@ __global__ void __launch_bounds__(THREADS) k_ion_field(const IonArgs a) {
     o[5] = my[r];
     o[6] = mz[r];
     o[7] = mq[r];
+    o[8] = rx[r];
+    o[9] = ry[r];
+    o[10] = rz[r];
   }
 }
 
@@ -200,18 +205,40 @@ __global__ void __launch_bounds__(256) k_ion_inputs(const IonArgs a) {
   if (!pass_active(a, step)) return;
   const long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= a.ion.n_ions) return;
-  const double* sc = a.scratch + 8 * t;
+  if (t == 0) *a.pass_slot = *a.next_slot;  // the apply kernel's base for this pass
+  // combine the source segments in order: fields add; the moments of each
+  // segment are shifted to the reference of the first segment with electrons
+  // (sums about r_s -> sums about r: S += W d, Q += 2 d.S + W |d|^2, d = r_s - r)
+  double fx = 0.0, fy = 0.0, fz = 0.0, W = 0.0, S[3] = {0.0, 0.0, 0.0}, Q = 0.0, ref[3];
+  bool have = false;
+  for (int sg = 0; sg < a.nseg; ++sg) {
+    const double* sc = a.scratch + kIonScratch * (static_cast<long long>(sg) * a.ion.n_ions + t);
+    fx += sc[0];
+    fy += sc[1];
+    fz += sc[2];
+    if (!(sc[3] > 0.0)) continue;
+    if (!have) {
+      ref[0] = sc[8]; ref[1] = sc[9]; ref[2] = sc[10];
+      have = true;
+    }
+    const double d0 = sc[8] - ref[0], d1 = sc[9] - ref[1], d2 = sc[10] - ref[2];
+    Q += sc[7] + 2.0 * (d0 * sc[4] + d1 * sc[5] + d2 * sc[6]) + sc[3] * (d0 * d0 + d1 * d1 + d2 * d2);
+    S[0] += sc[4] + sc[3] * d0;
+    S[1] += sc[5] + sc[3] * d1;
+    S[2] += sc[6] + sc[3] * d2;
+    W += sc[3];
+  }
   const double tn = a.c.t0 + static_cast<double>(step) * a.c.dt;
   double lay;
   const double lax = laser_ax(a.c, tn, &lay);
-  const double ex = sc[0] + lax, ey = sc[1] + lay, ez = sc[2];
+  const double ex = fx + lax, ey = fy + lay, ez = fz;
   double ne = 0.0, te = 0.0;
-  if (sc[3] > 0.0) {
+  if (W > 0.0) {
     const double lk = a.ion.r_loc / a.ion.k_si;  // r_loc in metres
     const double vol_cm3 = (4.0 / 3.0) * kPi * lk * lk * lk * 1e6;
-    const double mx = sc[4] / sc[3], my = sc[5] / sc[3], mz = sc[6] / sc[3];
-    const double var = sc[7] / sc[3] - (mx * mx + my * my + mz * mz);
-    ne = sc[3] / vol_cm3;
+    const double mx = S[0] / W, my = S[1] / W, mz = S[2] / W;
+    const double var = Q / W - (mx * mx + my * my + mz * mz);
+    ne = W / vol_cm3;
     te = var > 0.0 ? kMeC2Ev * var / 3.0 : 0.0;
   }
   double* o = a.out + 4 * t;
@@ -223,29 +250,35 @@ __global__ void __launch_bounds__(256) k_ion_inputs(const IonArgs a) {
 }
 
 // Per ion: rate (surrogate if it set one, else static ADK + Lotz), P and the
-// Philox draw; sets fired[t].  No state changes here.
+// Philox draw; sets fired[t] and the number of fired ions of the block.  No
+// state changes here.
 __global__ void __launch_bounds__(256) k_ion_decide(const IonArgs a) {
   const long long step = __ldcg(a.step);
   if (!pass_active(a, step)) return;
   const long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (t >= a.ion.n_ions) return;
-  const long long i = a.c.off + t;
-  double* o = a.out + 4 * t;
-  const double emag = o[0], ne = o[1], te = o[2];
-  a.fired[t] = 0;
-  const int z = a.zq[i];
-  if (a.kind[i] != 0 || z < 0 || z >= a.ion.zmax) return;
-  const double nu_s = a.nu[t];
-  const double nu = nu_s >= 0.0 ? nu_s : rate::rate_plain(a.ion, emag, z, ne, te);
-  const double dt_ion = (a.ion.ionize_every > 0 ? a.ion.ionize_every : 1) * a.c.dt;
-  const double P = -expm1(-nu * dt_ion);
-  o[3] = P;
-  const uint4 wv = philox4x32_10(
-      make_uint4(static_cast<uint32_t>(t), static_cast<uint32_t>(step),
-                 static_cast<uint32_t>(static_cast<unsigned long long>(step) >> 32), 0u),
-      make_uint2(static_cast<uint32_t>(a.ion.seed), static_cast<uint32_t>(a.ion.seed >> 32)));
-  const double alpha = (static_cast<double>(wv.x) + 1.0) * (1.0 / 4294967296.0);
-  if (alpha < P) a.fired[t] = 1;
+  int fired = 0;
+  if (t < a.ion.n_ions) {
+    const long long i = a.c.off + t;
+    double* o = a.out + 4 * t;
+    const int z = a.zq[i];
+    if (a.kind[i] == 0 && z >= 0 && z < a.ion.zmax) {
+      const double emag = o[0], ne = o[1], te = o[2];
+      const double nu_s = a.nu[t];
+      const double nu = nu_s >= 0.0 ? nu_s : rate::rate_plain(a.ion, emag, z, ne, te);
+      const double dt_ion = (a.ion.ionize_every > 0 ? a.ion.ionize_every : 1) * a.c.dt;
+      const double P = -expm1(-nu * dt_ion);
+      o[3] = P;
+      const uint4 wv = philox4x32_10(
+          make_uint4(static_cast<uint32_t>(t), static_cast<uint32_t>(step),
+                     static_cast<uint32_t>(static_cast<unsigned long long>(step) >> 32), 0u),
+          make_uint2(static_cast<uint32_t>(a.ion.seed), static_cast<uint32_t>(a.ion.seed >> 32)));
+      const double alpha = (static_cast<double>(wv.x) + 1.0) * (1.0 / 4294967296.0);
+      fired = alpha < P ? 1 : 0;
+    }
+    a.fired[t] = static_cast<unsigned char>(fired);
+  }
+  const int cnt = __syncthreads_count(fired);
+  if (threadIdx.x == 0) a.blk_fired[blockIdx.x] = cnt;
 }
 
 // Ionization of ion t (cluster-relative) freeing its electron into record e
@@ -295,47 +328,39 @@ __device__ void apply_one(const IonArgs& a, long long step, long long t, long lo
   }
 }
 
-constexpr int kApplyThreads = 1024;
-
-// One CTA: thread k takes a contiguous chunk of ions; an exclusive scan of the
-// per-chunk fired counts gives each fired ion, in index order, the slot
-// *next_slot + (fired ions before it); *next_slot then advances past them.
-__global__ void __launch_bounds__(kApplyThreads) k_ion_apply(const IonArgs a) {
-  __shared__ long long s_warp[kApplyThreads / 32];
+// The fired ions, in index order, take the slots *pass_slot + (fired ions
+// before them): each block adds the counts of the blocks before it (from
+// k_ion_decide) to an in-block scan; the last block advances *next_slot.
+__global__ void __launch_bounds__(256) k_ion_apply(const IonArgs a) {
+  __shared__ int s_part[8], s_warp[8];
   __shared__ long long s_base;
   const long long step = __ldcg(a.step);
   if (!pass_active(a, step)) return;
-  const long long n = a.ion.n_ions;
-  const long long chunk = (n + kApplyThreads - 1) / kApplyThreads;
-  const long long b = chunk * threadIdx.x;
-  const long long e = b + chunk < n ? b + chunk : n;
-  long long cnt = 0;
-  for (long long t = b; t < e; ++t) cnt += a.fired[t];
-  // block-wide exclusive scan of cnt
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  long long incl = cnt;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // fired ions of the blocks before this one
+  int before = 0;
+  for (int b = tid; b < static_cast<int>(blockIdx.x); b += 256) before += a.blk_fired[b];
 #pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const long long v = __shfl_up_sync(0xffffffffu, incl, d);
-    if (lane >= d) incl += v;
-  }
-  if (lane == 31) s_warp[warp] = incl;
-  if (threadIdx.x == 0) s_base = *a.next_slot;
+  for (int d = 16; d > 0; d >>= 1) before += __shfl_xor_sync(0xffffffffu, before, d);
+  if (lane == 0) s_part[warp] = before;
+  const long long t = static_cast<long long>(blockIdx.x) * 256 + tid;
+  const int f = (t < a.ion.n_ions) ? a.fired[t] : 0;
+  const unsigned ball = __ballot_sync(0xffffffffu, f);
+  if (lane == 0) s_warp[warp] = __popc(ball);
   __syncthreads();
-  if (warp == 0) {
-    long long w = lane < kApplyThreads / 32 ? s_warp[lane] : 0;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const long long v = __shfl_up_sync(0xffffffffu, w, d);
-      if (lane >= d) w += v;
-    }
-    if (lane < kApplyThreads / 32) s_warp[lane] = w;  // inclusive over warps
+  if (tid == 0) {
+    long long b = 0;
+    for (int w = 0; w < 8; ++w) b += s_part[w];
+    s_base = *a.pass_slot + b;
   }
   __syncthreads();
-  long long slot = s_base + (warp > 0 ? s_warp[warp - 1] : 0) + (incl - cnt);
-  for (long long t = b; t < e; ++t)
-    if (a.fired[t]) apply_one(a, step, t, slot++);
-  if (threadIdx.x == kApplyThreads - 1) *a.next_slot = s_base + s_warp[kApplyThreads / 32 - 1];
+  int wpre = 0, total = 0;
+  for (int w = 0; w < 8; ++w) {
+    wpre += (w < warp) ? s_warp[w] : 0;
+    total += s_warp[w];
+  }
+  if (f) apply_one(a, step, t, s_base + wpre + __popc(ball & ((1u << lane) - 1u)));
+  if (blockIdx.x == gridDim.x - 1 && tid == 0) *a.next_slot = s_base + total;
 }
 
 // Liveness flags from the current records: a group of kLiveGroup records is
@@ -376,7 +401,8 @@ cudaError_t launch_live_init(const float4* posq0, const float4* posq1, const uns
 cudaError_t launch_ion_pass(const IonArgs& a, cudaStream_t s) {
   if (a.ion.n_ions <= 0) return cudaSuccess;
   const long long per = kIonThreads * kIonR;
-  const unsigned g1 = static_cast<unsigned>((a.ion.n_ions + per - 1) / per);
+  const dim3 g1(static_cast<unsigned>((a.ion.n_ions + per - 1) / per),
+                static_cast<unsigned>(a.nseg));
   k_ion_field<kIonThreads, kIonR, kIonTile, 2><<<g1, kIonThreads, 0, s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -388,7 +414,7 @@ cudaError_t launch_ion_pass(const IonArgs& a, cudaStream_t s) {
   }
   k_ion_decide<<<g2, 256, 0, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_ion_apply<<<1, kApplyThreads, 0, s>>>(a);
+  k_ion_apply<<<g2, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -106,7 +106,9 @@ struct md_ctx {
   std::vector<md::IonDev> ion;
   std::vector<long long> ion_out_off;  // per cluster, into d_ion_out / d_ion_fired
   bool any_ion = false;
-  double* d_ion_scratch = nullptr;     // [max n_ions][8]
+  double* d_ion_scratch = nullptr;     // [kIonMaxSeg][max n_ions][kIonScratch]
+  int* d_ion_blk = nullptr;            // [ceil(max n_ions / 256)] fired ions per block
+  long long* d_ion_pass = nullptr;     // [n_clusters] first free slot at the pass start
   double* d_ion_out = nullptr;         // [sum n_ions][4]
   unsigned char* d_ion_fired = nullptr;
   double* d_ion_nu = nullptr;          // [sum n_ions] surrogate rates (-1: plain)
@@ -443,6 +445,18 @@ md::IonArgs ion_args(md_ctx* c, int ci, int force) {
   a.err = c->d_err;
   a.force = force;
   a.scratch = c->d_ion_scratch;
+  a.blk_fired = c->d_ion_blk;
+  a.pass_slot = c->d_ion_pass + ci;
+  // split the sources of the field pass until about 8 CTAs per SM are busy,
+  // keeping at least 4 tiles of sources per segment
+  {
+    const long long ion_blocks = (a.ion.n_ions + 127) / 128;
+    const long long want = (8LL * c->sm_count + ion_blocks - 1) / std::max(1LL, ion_blocks);
+    const long long by_len = std::max(1LL, static_cast<long long>(a.c.n_pad) / 2048);
+    a.nseg = static_cast<int>(std::max(1LL, std::min({want, by_len,
+                                                      static_cast<long long>(md::kIonMaxSeg)})));
+    a.seg_len = (a.c.n_pad + a.nseg - 1) / a.nseg;
+  }
   a.out = c->d_ion_out + 4 * c->ion_out_off[ci];
   a.fired = c->d_ion_fired + c->ion_out_off[ci];
   a.nu = c->d_ion_nu + c->ion_out_off[ci];
@@ -536,6 +550,8 @@ void free_ctx(md_ctx* c) {
   cudaFree(c->d_iblk_cnt);
   cudaFree(c->d_raw);
   cudaFree(c->d_ion_scratch);
+  cudaFree(c->d_ion_blk);
+  cudaFree(c->d_ion_pass);
   cudaFree(c->d_ion_out);
   cudaFree(c->d_ion_fired);
   cudaFree(c->d_ion_nu);
@@ -790,7 +806,10 @@ md_status md_init(md_ctx** out, const md_config* cfgs, int32_t n_clusters,
       max_ion = std::max<long long>(max_ion, io.n_ions);
       sum_ion += io.n_ions;
     }
-    if (dev_alloc(&c->d_ion_scratch, 8 * static_cast<size_t>(max_ion)) != cudaSuccess ||
+    if (dev_alloc(&c->d_ion_scratch, static_cast<size_t>(md::kIonMaxSeg) * md::kIonScratch *
+                                         static_cast<size_t>(max_ion)) != cudaSuccess ||
+        dev_alloc(&c->d_ion_blk, static_cast<size_t>((max_ion + 255) / 256)) != cudaSuccess ||
+        dev_alloc(&c->d_ion_pass, static_cast<size_t>(n_clusters)) != cudaSuccess ||
         dev_alloc(&c->d_ion_out, 4 * static_cast<size_t>(sum_ion)) != cudaSuccess ||
         dev_alloc(&c->d_ion_fired, static_cast<size_t>(sum_ion)) != cudaSuccess ||
         dev_alloc(&c->d_ion_nu, static_cast<size_t>(sum_ion)) != cudaSuccess)

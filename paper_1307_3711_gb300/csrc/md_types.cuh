@@ -28,6 +28,8 @@ struct ClusterDev {
 };
 
 constexpr int kMaxZ = 16;
+constexpr int kIonScratch = 11;   // doubles per ion and source segment
+constexpr int kIonMaxSeg = 8;     // source segments of the ionization field pass
 
 // Ionization parameters of one cluster (Sec. II, ionization paragraph).
 struct IonDev {
@@ -107,8 +109,13 @@ struct IonArgs {
   const long long* step;
   int* err;
   int force;          // 1: run regardless of ionize_every
-  double* scratch;    // [n_ions][8]: ex, ey, ez, sw, sw du_x, sw du_y, sw du_z, sw du^2
-                      // (du = u - the first local electron's u: same variance)
+  double* scratch;    // [nseg][n_ions][kIonScratch]: ex, ey, ez, sw, sw du_x, sw du_y,
+                      // sw du_z, sw du^2, u_ref (3) of each source segment (du = u -
+                      // u_ref, u_ref = the segment's first local electron's u)
+  int nseg;           // source segments of the field pass
+  long long seg_len;  // sources per segment
+  int* blk_fired;     // [ceil(n_ions / 256)] fired ions per block of the decision
+  long long* pass_slot;  // first free slot at the start of the pass
   double* out;        // [n_ions][4]: |E|, ne (cm^-3), Te (eV), P
   double* nu;         // [n_ions]: rate from the surrogate, or -1 (use the plain rate)
   unsigned char* fired;  // [n_ions]
