@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1390,11 +1391,22 @@ md_status md_coulomb_field_device(const void* src, int64_t ns, const void* tgt, 
   if ((reinterpret_cast<uintptr_t>(src) & 15) || (reinterpret_cast<uintptr_t>(tgt) & 15))
     return fail(MD_ERR_ARG, "src and tgt must be 16-byte aligned");
   if (!(eps2 > 0.0f)) return fail(MD_ERR_ARG, "eps2 must be > 0");
-  static int* d_err = nullptr;  // per-process error word of the stateless call
-  if (!d_err) {
-    cudaError_t ce = cudaMalloc(reinterpret_cast<void**>(&d_err), sizeof(int));
-    if (ce != cudaSuccess) return cuda_fail(ce, "cudaMalloc");
-    cudaMemset(d_err, 0, sizeof(int));
+  // one error word per device of the process, allocated on first use there
+  static std::mutex mu;
+  static std::vector<int*> words;
+  int dev = 0;
+  MD_CUDA(cudaGetDevice(&dev));
+  int* d_err = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (static_cast<int>(words.size()) <= dev) words.resize(dev + 1, nullptr);
+    if (!words[dev]) {
+      cudaError_t ce = cudaMalloc(reinterpret_cast<void**>(&words[dev]), sizeof(int));
+      if (ce != cudaSuccess) return cuda_fail(ce, "cudaMalloc");
+      ce = cudaMemset(words[dev], 0, sizeof(int));
+      if (ce != cudaSuccess) return cuda_fail(ce, "cudaMemset");
+    }
+    d_err = words[dev];
   }
   md::FieldArgs a;
   a.src = static_cast<const float4*>(src);
