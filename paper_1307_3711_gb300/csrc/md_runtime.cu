@@ -174,8 +174,14 @@ RawView raw_view(unsigned char* base, long long n) {
 md_status validate_config(const md_config& c, int idx) {
   if (!(c.dt > 0.0) || !std::isfinite(c.dt))
     return fail(MD_ERR_ARG, "cluster %d: dt must be > 0", idx);
-  if (!(c.softening > 0.0) || !std::isfinite(c.softening))
-    return fail(MD_ERR_ARG, "cluster %d: softening must be > 0 (the GPU sum keeps the self pair)", idx);
+  if (!(c.softening > 0.0) || !std::isfinite(c.softening) ||
+      !(static_cast<float>(c.softening * c.softening) >= 1.1754944e-38f))
+    return fail(MD_ERR_ARG,
+                "cluster %d: softening must be > 0 with softening^2 a normal FP32 number (the "
+                "GPU sum keeps the self pair)", idx);
+  if (!std::isfinite(c.a0) || !std::isfinite(c.t0) || !std::isfinite(c.tau) ||
+      !std::isfinite(c.box) || !std::isfinite(c.t_switch))
+    return fail(MD_ERR_ARG, "cluster %d: a0, t0, tau, box and t_switch must be finite", idx);
   if (!(c.lambda_um > 0.0)) return fail(MD_ERR_ARG, "cluster %d: lambda_um must be > 0", idx);
   if (c.polarization != 0 && c.polarization != 1)
     return fail(MD_ERR_ARG, "cluster %d: polarization must be 0 or 1", idx);
@@ -231,6 +237,12 @@ md_status validate_particles(const md_particles& p, int idx, long long expect_n)
       return fail(MD_ERR_ARG, "cluster %d: record %lld: electron with z >= 0", idx, i);
     if (kd == MD_KIND_ION && p.z[i] < 0)
       return fail(MD_ERR_ARG, "cluster %d: record %lld: ion with z < 0", idx, i);
+    if (!(std::isfinite(p.x[3 * i]) && std::isfinite(p.x[3 * i + 1]) &&
+          std::isfinite(p.x[3 * i + 2]) && std::isfinite(p.u[3 * i]) &&
+          std::isfinite(p.u[3 * i + 1]) && std::isfinite(p.u[3 * i + 2]) &&
+          std::isfinite(p.w[i])))
+      return fail(MD_ERR_ARG, "cluster %d: record %lld: non-finite position, momentum or weight",
+                  idx, i);
   }
   return MD_OK;
 }

@@ -64,6 +64,8 @@ def _one(md, **kw):
     ({"dt": 0.0}, "dt"), ({"softening": 0.0}, "softening"), ({"lambda_um": -1.0}, "lambda"),
     ({"polarization": 2}, "polarization"), ({"envelope": 9}, "envelope"),
     ({"boundary": 1, "box": 0.0}, "box"), ({"tau": 0.0, "envelope": 1}, "tau"),
+    ({"softening": 1e-30}, "softening"), ({"a0": float("nan")}, "finite"),
+    ({"t0": float("inf")}, "finite"),
 ])
 def test_init_rejects_bad_config_on_host(md, kw, what):
     cfg, p = _one(md, **kw)
@@ -83,6 +85,12 @@ def test_init_rejects_inconsistent_particles(md):
     p = md.HostParticles(np.zeros((2, 3)), np.zeros((2, 3)), [1, -1], [0.0, 1.0], [1.0, 1.0])
     with pytest.raises(md.MDError):
         md.Context([cfg], [p])
+    x = np.zeros((2, 3))
+    x[1, 2] = np.nan
+    p = md.HostParticles(x, np.zeros((2, 3)), [1, -1], [1000.0, 1.0], [1.0, 1.0])
+    with pytest.raises(md.MDError) as ei:
+        md.Context([cfg], [p])
+    assert "non-finite" in str(ei.value)
 
 
 def test_init_without_gpu_fails_cleanly(md):
