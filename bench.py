@@ -70,7 +70,8 @@ def parse_args():
     ap.add_argument("--tuning", default=None,
                     help="force a kernel configuration: threads,r,tile,packed[,jsplit[,min_blocks]]")
     ap.add_argument("--workload", default="xe3_200k",
-                    choices=["xe3_200k", "scan256", "precision_1m", "ar_ionize", "iedf"],
+                    choices=["xe3_200k", "scan256", "precision_1m", "ar_ionize", "iedf",
+                             "nscale"],
                     help="xe3_200k: the headline N=200k cluster; scan256: 256 clusters of a "
                          "parameter scan in one persistent launch; precision_1m: 500k Ar+ + 500k "
                          "e, laser off; ar_ionize: neutral Ar atoms ionizing; iedf: a small "
@@ -310,6 +311,73 @@ def precision_study(md, ctx, w, n_targets=10000, n_oracle=2000, seed=0):
             "fp64_gpu_vs_oracle_bitwise_equal": f"{int(np.sum(np.all(e_or == e64[:m], axis=1)))}"
                                                 f"/{m} targets",
             "metric": "|E - E_fp64| / max(|E_fp64|, rms|E_fp64|), state after the timed steps"}
+
+
+def single_thread_rate(w, seconds: float):
+    """The same FP64 oracle sum on one host core (the paper's code without
+    its OpenMP loop), on a sample sized to about `seconds`."""
+    import oracle
+    c = w.cluster
+    kc = oracle.coulomb_constant(w.lambda_um)
+    q = c.w * c.z * c.active
+    rng = np.random.default_rng(1)
+    nt = 16
+    while True:
+        idx = rng.choice(c.n, nt, replace=False)
+        t0 = time.perf_counter()
+        oracle.coulomb_field(c.x[idx], c.x, q, w.eps, kc, self_idx=idx, nthreads=1)
+        dt = time.perf_counter() - t0
+        if dt > 0.2 or nt >= c.n:
+            break
+        nt = min(c.n, nt * 4)
+    nt = int(min(c.n, max(16, nt * seconds / max(dt, 1e-6))))
+    idx = rng.choice(c.n, nt, replace=False)
+    t0 = time.perf_counter()
+    oracle.coulomb_field(c.x[idx], c.x, q, w.eps, kc, self_idx=idx, nthreads=1)
+    dt = time.perf_counter() - t0
+    return {"value": nt * c.n / dt, "unit": UNIT, "cores": 1,
+            "sample": f"FP64 field at {nt} sampled targets from all {c.n} sources ({dt:.1f} s)"}
+
+
+def run_nscale(args):
+    """Step time against N for the headline cluster family (Xe3+ + 3 e per
+    ion at the density of the 400k case), one autotuned context per N: the
+    GPU counterpart of the paper's Fig. 7b (time ~ N^2)."""
+    import torch
+    from paper_1307_3711_gb300 import build
+    build.build()
+    from paper_1307_3711_gb300 import md
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    sms, gpu_name = md.device_info()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    rows = []
+    for n in (20000, 50000, 100000, 200000, 400000):
+        w = workload(n, seed=0)
+        with md.Context([md.config_from_workload(w)], [md.HostParticles.from_cluster(w.cluster)],
+                        stream=stream.cuda_stream) as ctx:
+            ctx.autotune(3)
+            for _ in range(3):
+                ctx.step(1)
+            ms = []
+            for _ in range(max(args.steps // 6, 5)):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx.step(1)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            t = statistics.mean(ms)
+            pairs = float(n) ** 2
+            peak = 128.0 * sms * 2070e6 / FP32_INSTR_PER_PAIR
+            rows.append({"n": n, "ms_per_step": t, "pairs_per_s": pairs / (t / 1e3),
+                         "frac_at_max_clock": pairs / (t / 1e3) / peak,
+                         "tuning": list(ctx.tuning())})
+    print(json.dumps({"workload": "nscale: xe3 clusters at the density of the 400k case",
+                      "device": gpu_name, "l2": "flushed between timed steps",
+                      "rows": rows}), flush=True)
 
 
 def build_contexts(md, args, rank, stream):
@@ -552,7 +620,8 @@ def run_native(args):
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"FP64 field at {nt} sampled targets from all {w.cluster.n} sources "
                          f"({nt * w.cluster.n:.3g} pairs, {secs:.1f} s, OpenMP over targets)",
-               "steps_per_s": rate / (float(w.cluster.n) ** 2)}
+               "steps_per_s": rate / (float(w.cluster.n) ** 2),
+               "single_thread": single_thread_rate(w, 3.0)}
 
     launches_per_step = info.get("kernels_per_step", 1)
     ctx.close()
@@ -659,6 +728,8 @@ def main():
         run_reference(args)
     elif args.workload == "iedf":
         run_iedf(args)
+    elif args.workload == "nscale":
+        run_nscale(args)
     else:
         run_native(args)
 
