@@ -435,3 +435,73 @@ def test_pinned_and_pageable_host_buffers_give_the_same_records(md):
         gb = b.get_particles(0, out=outp)
         for k in ("x", "u", "z", "mass", "w", "kind"):
             assert np.array_equal(getattr(ga, k), getattr(gb, k)), k
+
+
+# ----------------------------------------------- full sizes, bench launch --
+
+def _one_step_sampled(md, clusters, n_sample, seed, autotune=True):
+    """One md_step of the given workloads in one context (the configuration the
+    autotuner picks, as the bench times it), against the FP64 oracle's field +
+    Boris kick + drift at sampled particles of each cluster: the momentum
+    increment and the displacement, floored relative error per particle."""
+    rng = np.random.default_rng(seed)
+    cfgs = [md.config_from_workload(w) for w in clusters]
+    parts = [md.HostParticles.from_cluster(w.cluster) for w in clusters]
+    errs_u, errs_x = [], []
+    with md.Context(cfgs, parts) as ctx:
+        if autotune:
+            ctx.autotune(2)
+        g0 = [ctx.get_particles(k) for k in range(len(clusters))]
+        ctx.step(1)
+        g1 = [ctx.get_particles(k) for k in range(len(clusters))]
+        tuning = ctx.tuning()
+    for k, w in enumerate(clusters):
+        c = w.cluster
+        kc = oracle.coulomb_constant(w.lambda_um)
+        q = np.where(g0[k].kind != md.KIND_INACTIVE, g0[k].w * g0[k].z, 0.0)
+        idx = np.sort(rng.choice(c.n, min(n_sample, c.n), replace=False))
+        e64 = oracle.coulomb_field(g0[k].x[idx], g0[k].x, q, w.eps, kc, self_idx=idx,
+                                   nthreads=8)
+        a, b = oracle.laser_fields(w.t0, w.a0, w.pol, w.env, w.tau)
+        du_ref, dx_ref = [], []
+        for m, i in enumerate(idx):
+            qm = g0[k].z[i] / g0[k].mass[i]
+            u1 = oracle.boris_kick(g0[k].u[i], e64[m] + a, b, qm, w.dt)
+            du_ref.append(u1 - g0[k].u[i])
+            dx_ref.append(oracle.drift(g0[k].x[i], u1, w.dt) - g0[k].x[i])
+        du_ref, dx_ref = np.array(du_ref), np.array(dx_ref)
+        errs_u.append(force_error(g1[k].u[idx] - g0[k].u[idx], du_ref))
+        errs_x.append(force_error(g1[k].x[idx] - g0[k].x[idx], dx_ref))
+    return np.concatenate(errs_u), np.concatenate(errs_x), tuning
+
+
+def test_step_parity_headline_in_bench_configuration(md):
+    """N = 200k (the bench's workload and autotuned launch): the kick of one
+    step at 500 sampled particles is the FP64 oracle's within the force gate."""
+    eu, ex, tuning = _one_step_sampled(md, [synth.headline_200k(0)], 500, 11)
+    print("tuning", tuning, "kick", summary(eu), "drift", summary(ex))
+    assert summary(eu)["p99"] <= FORCE_P99
+    assert summary(ex)["p99"] <= FORCE_P99
+
+
+def test_step_parity_precision_1m_sampled(md):
+    """N = 1M (500k Ar+ + 500k e): one autotuned step, 200 sampled particles."""
+    eu, ex, tuning = _one_step_sampled(md, [synth.precision_1m(0)], 200, 12)
+    print("tuning", tuning, "kick", summary(eu), "drift", summary(ex))
+    assert summary(eu)["p99"] <= FORCE_P99
+    assert summary(ex)["p99"] <= FORCE_P99
+
+
+def test_step_parity_batched_scan_sampled(md):
+    """The 256-cluster scan in one persistent launch: one autotuned step, 8
+    sampled particles in each of the 256 clusters."""
+    scan = synth.batched_scan(256, seed=0)
+    ws = []
+    for e in scan:
+        ws.append(synth.Workload(f"scan_{e.seed}", synth.scan_cluster(e), a0=e.a0, pol=0,
+                                 env=synth.ENV_SIN2, tau=e.tau, eps=synth.nm_to_len(0.1),
+                                 dt=0.02, nsteps=0))
+    eu, ex, tuning = _one_step_sampled(md, ws, 8, 13)
+    print("tuning", tuning, "kick", summary(eu), "drift", summary(ex))
+    assert summary(eu)["p99"] <= FORCE_P99
+    assert summary(ex)["p99"] <= FORCE_P99
