@@ -241,3 +241,50 @@ def test_ionizing_steps_follow_oracle(md):
                 assert np.array_equal(g1.z, st.z)
                 assert np.array_equal(g1.kind != md.KIND_INACTIVE, st.active > 0)
     assert np.bincount(st.z[:n], minlength=9)[2:].sum() > 0.3 * n
+
+
+def test_ionization_pass_full_size_sampled(md):
+    """200k Ar atoms + 1.6M slots (the learned-ionization configuration), after
+    two ionizing steps from the pulse peak: a forced pass gives, at 300 sampled
+    ions, the oracle's |E| (FP32 tolerance), n_e exactly, T_e to FP32 rounding
+    and, from the GPU's inputs, the oracle's decisions."""
+    n = 200000
+    lam = 0.806
+    c = synth.make_cluster(0, n, 0, synth.nm_to_len(8.0, lam), 0, AR["mass"],
+                           n_electron_slots=8 * n)
+    rw = synth.nm_to_len(AR["r_w_nm"], lam)
+    tau = synth.sin2_length_from_fwhm(synth.fs_to_time(100.0, lam))
+    t0 = np.floor(tau / 2 / np.pi) * np.pi + 0.5 * np.pi - 0.3
+    eps = synth.nm_to_len(0.1, lam)
+    kw = dict(a0=0.0617, tau=tau, t0=t0, dt=0.02, softening=eps, envelope=synth.ENV_SIN2,
+              lambda_um=lam, rate_model=1, ionize_every=1, zmax=8, n_ions=n, slot_base=n,
+              seed=9, r_loc=3 * rw, r_create=rw, species=AR)
+    with md.Context([md.make_config(**kw)], [md.HostParticles.from_cluster(c)]) as ctx:
+        ctx.autotune(2)
+        ctx.step(2)
+        g = ctx.get_particles(0)
+        step = ctx.step_index()
+        ctx.ionize()
+        info = ctx.ionization(0)
+    st = oracle.State(g.x, g.u, g.z, g.mass, g.w, (g.kind != md.KIND_INACTIVE).astype(np.uint8),
+                      step=step)
+    rng = np.random.default_rng(4)
+    idx = np.sort(rng.choice(n, 300, replace=False))
+    kc = oracle.coulomb_constant(lam)
+    e64 = oracle.coulomb_field(st.x[idx], st.x, st.q(), eps, kc, self_idx=idx, nthreads=8)
+    a, _ = oracle.laser_fields(t0 + step * 0.02, 0.0617, 0, synth.ENV_SIN2, tau)
+    emag = np.linalg.norm(e64 + a[None, :], axis=1)
+    rel = np.abs(info["emag"][idx] - emag) / np.sqrt(np.mean(emag ** 2))
+    assert np.percentile(rel, 99) < 2e-5
+    ne64, te64 = oracle.local_moments(st.x[idx], st, kw["r_loc"], lam)
+    both = (ne64 > 0) & (info["ne"][idx] > 0)
+    assert both.sum() > 0.8 * len(idx)
+    same = np.isclose(info["ne"][idx][both], ne64[both], rtol=1e-12)
+    assert same.mean() > 0.95
+    np.testing.assert_allclose(info["te"][idx][both][same], te64[both][same], rtol=2e-5,
+                               atol=1e-6)
+    z_ref, fired_ref, _, p_ref = oracle.decide(idx, g.z[idx], info["emag"][idx], info["ne"][idx],
+                                               info["te"][idx], AR, 8, kw["seed"], step, 0.02,
+                                               kw["r_create"], lam)
+    assert np.array_equal(info["fired"][idx], fired_ref)
+    np.testing.assert_allclose(info["prob"][idx], p_ref, rtol=1e-12, atol=1e-300)
