@@ -41,7 +41,7 @@ FP32_INSTR_PER_PAIR = 12
 # of the named workload in the named kernel configuration
 # (profiles/k_step_traffic_xe3_200k.md); reported only when the timed run uses
 # that configuration.
-STEP_TRAFFIC_BYTES = {("xe3_200k", 200000, 128, 4, 512, False): 33.54e6}
+STEP_TRAFFIC_BYTES = {("xe3_200k", 200000, 128, 4, 512, False): 34.02e6}
 L2_FLUSH_BYTES = 512 << 20
 WORKLOAD_TEXT = {
     "xe3_200k": "{name}: N={n} (Xe3+ ions + electrons, 10 eV), one cluster per GPU",
