@@ -505,3 +505,46 @@ def test_step_parity_batched_scan_sampled(md):
     print("tuning", tuning, "kick", summary(eu), "drift", summary(ex))
     assert summary(eu)["p99"] <= FORCE_P99
     assert summary(ex)["p99"] <= FORCE_P99
+
+
+def test_heterogeneous_context_equals_single_runs_bitwise(md):
+    """One context with an ionizing argon cluster and a plain cluster with
+    detectors (so the step kernel with the detector epilogue runs for both):
+    every record, charge state and detector count equals the single-cluster
+    runs of the same clusters."""
+    AR = synth.ARGON
+    n = 1200
+    ca = synth.make_cluster(2, n, 0, synth.nm_to_len(2.5), 0, AR["mass"],
+                            n_electron_slots=8 * n)
+    rw = synth.nm_to_len(AR["r_w_nm"])
+    ka = md.make_config(a0=0.1, tau=1.0, dt=0.05, softening=synth.nm_to_len(0.1), envelope=3,
+                        rate_model=1, ionize_every=2, zmax=8, n_ions=n, slot_base=n,
+                        seed=7, r_loc=3 * rw, r_create=rw, species=AR)
+    # an exploding ion sphere: its ions reach the detectors within the run
+    r0 = synth.nm_to_len(2.0)
+    cb = synth.make_cluster(4, 600, 0, r0, 1, synth.MASS_40AMU)
+    kcb = oracle.coulomb_constant(0.8)
+    tau = math.sqrt(synth.MASS_40AMU * r0 ** 3 / (kcb * 600.0))
+    kb = md.make_config(a0=0.0, dt=tau / 40, softening=synth.nm_to_len(0.005),
+                        envelope=synth.ENV_FLAT)
+    pa = md.HostParticles.from_cluster(ca)
+    pb = md.HostParticles.from_cluster(cb)
+
+    def run(cfgs, parts, det_on):
+        with md.Context(cfgs, parts) as ctx:
+            ctx.set_tuning(128, 4, 512)
+            if det_on is not None:
+                ctx.set_detectors(det_on, 1.1 * r0, e_max_ev=500.0, n_bins=32)
+            ctx.step(40)
+            out = [ctx.get_particles(k) for k in range(len(cfgs))]
+            det = ctx.iedf(det_on)[0] if det_on is not None else None
+        return out, det
+
+    (ga, gb), det_both = run([ka, kb], [pa, pb], 1)
+    (sa,), _ = run([ka], [pa], None)
+    (sb,), det_b = run([kb], [pb], 0)
+    for g, ref in ((ga, sa), (gb, sb)):
+        for k in ("x", "u", "z", "kind"):
+            assert np.array_equal(getattr(g, k), getattr(ref, k)), k
+    assert np.array_equal(det_both, det_b)
+    assert ga.z[:n].sum() > 0 and det_b[4].sum() > 0
