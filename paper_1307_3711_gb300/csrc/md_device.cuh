@@ -91,6 +91,21 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
   return true;
 }
 
+// Bounds checks of the checked build (-DMD_CHECKED): an index outside
+// [lo, hi) sets kErrBounds in the error word and the access is skipped; the
+// normal build compiles them away.
+__device__ __forceinline__ bool in_range_checked(int* err, long long v, long long lo,
+                                                 long long hi) {
+  if (v >= lo && v < hi) return true;
+  atomicOr(err, kErrBounds);
+  return false;
+}
+#ifdef MD_CHECKED
+#define MD_IN_RANGE(err, v, lo, hi) ::md::in_range_checked((err), (v), (lo), (hi))
+#else
+#define MD_IN_RANGE(err, v, lo, hi) true
+#endif
+
 // Explicit shared-memory loads (the tiles are reached through references, so
 // the address space is stated rather than inferred).
 __device__ __forceinline__ float4 lds_f4(uint32_t addr) {
@@ -849,7 +864,7 @@ __device__ __forceinline__ int det_bin(double ke, double emax, int nbins) {
 __device__ __forceinline__ void detect(unsigned long long* hist, unsigned char* crossed,
                                        const ClusterDev& c, long long i, double x0, double y0,
                                        double z0, double x1, double y1, double z1, double ux,
-                                       double uy, double uz, double mass) {
+                                       double uy, double uz, double mass, int* err) {
   if (crossed[i]) return;
   const double rp2 = det_norm2(__dsub_rn(x0, c.det_c[0]), __dsub_rn(y0, c.det_c[1]),
                                __dsub_rn(z0, c.det_c[2]));
@@ -859,6 +874,7 @@ __device__ __forceinline__ void detect(unsigned long long* hist, unsigned char* 
   crossed[i] = 1;
   const int nb1 = c.det_nbins + 1;
   const int bin = det_bin(det_ke_ev(ux, uy, uz, mass), c.det_emax, c.det_nbins);
+  if (!MD_IN_RANGE(err, bin, 0, c.det_nbins + 1)) return;
   const double cc = __dmul_rn(c.det_cos, __dsqrt_rn(rn2));
   unsigned long long* h = hist + c.det_off;
   atomicAdd(h + 4 * nb1 + bin, 1ull);
@@ -874,6 +890,7 @@ template <bool DET>
 __device__ __forceinline__ void push_record(const StepArgs& a, const ClusterDev& c, long long i,
                                             double ex, double ey, double ez, const float* las,
                                             double t_next, const float4* cur, float4* nxt) {
+  if (!MD_IN_RANGE(a.err, i, c.off, c.off + c.n_pad)) return;
   double X = a.x[i], Y = a.y[i], Z = a.z[i];
   double Ux = a.ux[i], Uy = a.uy[i], Uz = a.uz[i];
   const float h = 0.5f * static_cast<float>(c.dt) * a.qm[i];
@@ -897,7 +914,7 @@ __device__ __forceinline__ void push_record(const StepArgs& a, const ClusterDev&
   if constexpr (DET) {
     if (c.det_nbins > 0 && a.det_hist && a.qm[i] > 0.0f)
       detect(a.det_hist, a.det_crossed, c, i, a.x[i], a.y[i], a.z[i], X, Y, Z, Ux, Uy, Uz,
-             a.mass[i]);
+             a.mass[i], a.err);
   }
   a.x[i] = X;
   a.y[i] = Y;
@@ -1040,6 +1057,8 @@ __global__ void __launch_bounds__(THREADS, MINB) k_step(const StepArgs a) {
           if (i >= eend) continue;
           double ex, ey, ez;
           field_of(r, ex, ey, ez);
+          if (!MD_IN_RANGE(a.err, seg, 0, s_c.nseg) || !MD_IN_RANGE(a.err, i, 0, a.n_total))
+            continue;
           double* p = a.part + 3 * (static_cast<long long>(seg) * a.n_total + i);
           __stcg(p + 0, ex);
           __stcg(p + 1, ey);

@@ -174,6 +174,7 @@ __global__ void __launch_bounds__(THREADS) k_ion_field(const IonArgs a) {
   for (int r = 0; r < R; ++r) {
     const long long tt = t0 + threadIdx.x + r * THREADS;
     if (tt >= a.ion.n_ions) continue;
+    if (!MD_IN_RANGE(a.err, blockIdx.y, 0, kIonMaxSeg)) continue;
     double* o = a.scratch + kIonScratch * (static_cast<long long>(blockIdx.y) * a.ion.n_ions + tt);
     o[0] = -(static_cast<double>(acc.sx[r]) - acc.cx[r]);
     o[1] = -(static_cast<double>(acc.sy[r]) - acc.cy[r]);
@@ -359,7 +360,14 @@ __global__ void __launch_bounds__(256) k_ion_apply(const IonArgs a) {
     wpre += (w < warp) ? s_warp[w] : 0;
     total += s_warp[w];
   }
-  if (f) apply_one(a, step, t, s_base + wpre + __popc(ball & ((1u << lane) - 1u)));
+  if (f) {
+    const long long slot = s_base + wpre + __popc(ball & ((1u << lane) - 1u));
+    // the upload check guarantees a free slot for every possible ionization
+    if (MD_IN_RANGE(a.err, slot, a.ion.slot_base,
+                    a.ion.slot_base + static_cast<long long>(a.ion.zmax) * a.ion.n_ions) &&
+        MD_IN_RANGE(a.err, slot, 0, a.c.n))
+      apply_one(a, step, t, slot);
+  }
   if (blockIdx.x == gridDim.x - 1 && tid == 0) *a.next_slot = s_base + total;
 }
 

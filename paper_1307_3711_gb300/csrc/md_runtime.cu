@@ -434,6 +434,10 @@ md_status check_device_error(md_ctx* c) {
       MD_CUDA(cudaMemsetAsync(c->d_iblk_cnt, 0, sizeof(unsigned) * c->iblk_cap, c->stream));
     return fail(MD_ERR_TIMEOUT, "a device-side wait exceeded its time budget");
   }
+  if (err & md::kErrBounds) {
+    MD_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+    return fail(MD_ERR_STATE, "a device-side bounds check failed (checked build)");
+  }
   return MD_OK;
 }
 

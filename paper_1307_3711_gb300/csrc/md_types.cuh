@@ -9,6 +9,7 @@ namespace md {
 constexpr int kPad = 16;                          // records per cluster padded to a multiple of this
 constexpr long long kWaitBudget = 4000000000LL;   // clock64 cycles (about 2 s)
 constexpr int kErrTimeout = 1;
+constexpr int kErrBounds = 2;   // a bounds check of the checked build failed
 constexpr int kHistBins = 16;
 constexpr int kLiveGroup = 64;  // records per liveness flag
 

@@ -14,7 +14,8 @@ import numpy as np
 
 from . import build as _build
 
-_LIB_PATH = _build.LIB
+# MD_CHECKED=1 selects the build with device-side bounds checks
+_LIB_PATH = _build.LIB_CHECKED if os.environ.get("MD_CHECKED") == "1" else _build.LIB
 if not os.path.exists(_LIB_PATH):
     raise ImportError(f"libmd.so not built ({_LIB_PATH}); run paper_1307_3711_gb300.build.build()")
 _lib = C.CDLL(_LIB_PATH)
