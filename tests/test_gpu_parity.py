@@ -548,3 +548,76 @@ def test_heterogeneous_context_equals_single_runs_bitwise(md):
             assert np.array_equal(getattr(g, k), getattr(ref, k)), k
     assert np.array_equal(det_both, det_b)
     assert ga.z[:n].sum() > 0 and det_b[4].sum() > 0
+
+
+def _weighted(w, seed):
+    """The same workload with macro weights w = N_atoms/N_macro (Eq. 1) drawn in
+    [0.5, 3]: charges K_C w z, kinetic energy w m (gamma - 1)."""
+    rng = np.random.default_rng(seed)
+    w.cluster.w = rng.uniform(0.5, 3.0, w.cluster.n)
+    return w
+
+
+def test_weighted_macroparticles_field_steps_and_diagnostics(md):
+    """Non-unit macro weights: the field, 10 steps and the FP64 diagnostics
+    agree with the oracle as for unit weights."""
+    w = _weighted(synth.plain_fp64_2k(1), 3)
+    c = w.cluster
+    kc = oracle.coulomb_constant(0.8)
+    with ctx_for(md, w) as ctx:
+        e = ctx.fields(0)
+        d0 = ctx.diagnostics(0)
+        ctx.step(10)
+        g = ctx.get_particles(0)
+        d1 = ctx.diagnostics(0)
+    e64 = oracle.self_field(c.x, c.w * c.z, w.eps, kc)
+    assert summary(force_error(e, e64))["p99"] <= FORCE_P99
+    st = oracle_state(c)
+    p = oracle_params(w)
+    o0 = oracle.diagnostics(st, p)
+    assert d0["pe"] == pytest.approx(o0["pe"], rel=1e-5)
+    oracle.md_steps(st, p, 10, nthreads=4)
+    o1 = oracle.diagnostics(st, p)
+    r0 = synth.nm_to_len(2.0)
+    assert np.abs(g.x - st.x).max() < 1e-6 * r0
+    assert np.percentile(np.abs(g.u - st.u).max(1), 99) < 2e-4 * np.abs(st.u).max()
+    assert np.array_equal(g.w, c.w)
+    assert d1["ke"] == pytest.approx(o1["ke"], rel=1e-4)
+    assert d1["pe"] == pytest.approx(o1["pe"], rel=1e-4)
+
+
+def test_weighted_ionization_inputs_and_freed_electron_weight(md):
+    """Weighted argon atoms: the local density counts electron weights
+    (n_e = sum w / V), and an ionizing atom frees an electron of its weight."""
+    AR = synth.ARGON
+    n = 800
+    c = synth.make_cluster(2, n, 0, synth.nm_to_len(2.5), 0, AR["mass"],
+                           n_electron_slots=n * 8)
+    rng = np.random.default_rng(6)
+    c.w[:n] = rng.uniform(0.5, 3.0, n)
+    rw = synth.nm_to_len(AR["r_w_nm"])
+    kw = dict(a0=0.1, tau=1.0, dt=0.05, softening=synth.nm_to_len(0.1), envelope=3,
+              rate_model=1, ionize_every=0, zmax=8, n_ions=n, slot_base=n, seed=1234567,
+              r_loc=3 * rw, r_create=rw, species=AR)
+    with md.Context([md.make_config(**kw)], [md.HostParticles.from_cluster(c)]) as ctx:
+        ctx.step(10)                     # a0 sin(t): the field is up by t = 0.5
+        g0 = ctx.get_particles(0)
+        ctx.ionize()
+        fired = np.nonzero(ctx.ionization(0)["fired"])[0]
+        g1 = ctx.get_particles(0)
+        ctx.step(3)
+        g2 = ctx.get_particles(0)
+        ctx.ionize()
+        info = ctx.ionization(0)
+    assert len(fired) > 0.1 * n
+    # the freed electrons fill the next slots in ion order, each with its atom's weight
+    slots = n + np.arange(len(fired))
+    assert np.array_equal(g1.kind[slots], np.full(len(fired), md.KIND_ELECTRON, np.uint8))
+    assert np.array_equal(g1.w[slots], g0.w[fired])
+    st = oracle.State(g2.x, g2.u, g2.z, g2.mass, g2.w,
+                      (g2.kind != md.KIND_INACTIVE).astype(np.uint8))
+    ne64, te64 = oracle.local_moments(g2.x[:n], st, kw["r_loc"])
+    both = (ne64 > 0) & (info["ne"] > 0)
+    assert both.sum() > 0.5 * (ne64 > 0).sum()
+    same = np.isclose(info["ne"][both], ne64[both], rtol=1e-6)
+    assert same.mean() > 0.95
