@@ -621,3 +621,25 @@ def test_weighted_ionization_inputs_and_freed_electron_weight(md):
     assert both.sum() > 0.5 * (ne64 > 0).sum()
     same = np.isclose(info["ne"][both], ne64[both], rtol=1e-6)
     assert same.mean() > 0.95
+
+
+@pytest.mark.parametrize("env,pol", [(synth.ENV_GAUSS, 0), (synth.ENV_GAUSS, 1),
+                                     (synth.ENV_LITERAL_EQ3, 0), (synth.ENV_FLAT, 1)])
+def test_envelopes_and_polarizations_follow_the_oracle(md, env, pol):
+    """One electron through each envelope reading of Eq. 3 (intensity-FWHM
+    Gaussian, the printed constant, flat) and both polarizations: the GPU's
+    laser and push follow the oracle's trajectory (FP32 kick increments)."""
+    a0, tau = 0.2, 30.0
+    c = synth.Cluster(np.zeros((1, 3)), np.zeros((1, 3)), np.array([-1], np.int32),
+                      np.ones(1), np.ones(1), np.ones(1, np.uint8))
+    w = synth.Workload("e", c, a0=a0, pol=pol, env=env, tau=tau, eps=1e-3, dt=0.02, nsteps=0,
+                       t0=5.0)
+    nsteps = 4000   # t from 5 to 85: the Gaussian peaks at 2 tau = 60
+    with ctx_for(md, w) as ctx:
+        ctx.step(nsteps)
+        g = ctx.get_particles(0)
+    st = oracle_state(c)
+    oracle.md_steps(st, oracle_params(w), nsteps)
+    assert np.abs(st.u[0]).max() > 0.05 * a0          # the pulse did push it
+    np.testing.assert_allclose(g.u[0], st.u[0], atol=2e-5 * a0)
+    np.testing.assert_allclose(g.x[0], st.x[0], atol=1e-4 * max(1.0, np.abs(st.x[0]).max()))
