@@ -288,3 +288,23 @@ def test_ionization_pass_full_size_sampled(md):
                                                kw["r_create"], lam)
     assert np.array_equal(info["fired"][idx], fired_ref)
     np.testing.assert_allclose(info["prob"][idx], p_ref, rtol=1e-12, atol=1e-300)
+
+
+def test_graph_replay_equals_direct_launches_when_ionizing(md):
+    """md_step(32) replays a captured graph of 16 steps (ionization pass and
+    step kernel, every 2nd step ionizing); 32 calls of md_step(1) launch
+    directly: the same bits, charges and slots."""
+    c, kw = ar_case(n_atoms=1500, a0=0.1)
+    kw["ionize_every"] = 2
+    out = []
+    for graph in (True, False):
+        with md.Context([md.make_config(**kw)], [md.HostParticles.from_cluster(c)]) as ctx:
+            if graph:
+                ctx.step(32)
+            else:
+                for _ in range(32):
+                    ctx.step(1)
+            out.append(ctx.get_particles(0))
+    for k in ("x", "u", "z", "kind", "w"):
+        assert np.array_equal(getattr(out[0], k), getattr(out[1], k)), k
+    assert out[0].z[:1500].sum() > 0
