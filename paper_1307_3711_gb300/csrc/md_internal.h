@@ -46,6 +46,11 @@ cudaError_t launch_wait_selftest(long long budget, int* err, cudaStream_t s);
 // Ionization pass of one cluster: field + local moments, then the decision.
 cudaError_t launch_ion_pass(const IonArgs& a, cudaStream_t s);
 
+// Shape of the field + moments kernel: ion targets per CTA and resident CTAs
+// per SM (for the choice of the source split).
+int ion_field_targets_per_cta();
+cudaError_t ion_field_blocks_per_sm(int* out);
+
 // Liveness flags of all records (contexts with ionization).
 cudaError_t launch_live_init(const float4* posq0, const float4* posq1, const unsigned char* kind,
                              const long long* step, long long n_total, unsigned char* src_live,

@@ -5,7 +5,8 @@
 //   k_ion_field   for every ion/atom record: the Coulomb field of all other
 //                 particles (the TMA-staged FP32/Kahan direct sum of the step
 //                 kernel) and the weight, momentum and momentum-square sums of
-//                 the electrons within r_loc (gathered from the FP64 state);
+//                 the electrons within r_loc (from the FP32 velocity stream,
+//                 landed beside the position tiles);
 //   k_ion_decide  per ion: laser field at t_n, |E|, local density and
 //                 temperature, total rate (static ADK + Lotz, or the learned
 //                 surrogate), P = 1 - exp(-nu dt_ion) and a Philox4x32-10 draw;
@@ -58,11 +59,90 @@ __device__ __forceinline__ void issue_ion_tile(IonStage<TILE, STAGES>& sm, unsig
   bulk_g2s(&sm.vel[s][0], vel + j0, bytes, &sm.full[s]);
 }
 
-// Field (FP32/Kahan) and local electron moments at R ion targets per thread.
-// The moments are FP32 sums of w, w du and w du^2 with du = u - u_ref, u_ref
-// the velocity of the first electron found within r_loc (in source order):
-// the variance is unchanged by the shift, and centring the sums keeps the
-// thermal spread from cancelling against a common drift.
+// Local electron moments of R ion targets: FP32 sums of w, w du and w du^2
+// with du = u - u_ref, u_ref the velocity of the first electron found within
+// r_loc (in source order).  The variance is unchanged by the shift, and
+// centring the sums keeps the thermal spread from cancelling against a common
+// drift.
+template <int R>
+struct LocalMoments {
+  float w[R], sx[R], sy[R], sz[R], sq[R], rx[R], ry[R], rz[R];
+  bool have[R];
+
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      w[r] = sx[r] = sy[r] = sz[r] = sq[r] = rx[r] = ry[r] = rz[r] = 0.0f;
+      have[r] = false;
+    }
+  }
+  // electron velocity record v = (ux, uy, uz, w) within r_loc of target r
+  __device__ __forceinline__ void add(int r, const float4 v) {
+    if (!have[r]) {
+      rx[r] = v.x;
+      ry[r] = v.y;
+      rz[r] = v.z;
+      have[r] = true;
+    }
+    const float ux = v.x - rx[r], uy = v.y - ry[r], uz = v.z - rz[r];
+    w[r] += v.w;
+    sx[r] = fmaf(v.w, ux, sx[r]);
+    sy[r] = fmaf(v.w, uy, sy[r]);
+    sz[r] = fmaf(v.w, uz, sz[r]);
+    sq[r] = fmaf(v.w, fmaf(ux, ux, fmaf(uy, uy, uz * uz)), sq[r]);
+  }
+};
+
+// Charge class of a landed tile (same answer in every warp): one charge for
+// all its sources or not, and whether any source is an electron (q < 0).
+__device__ __forceinline__ void tile_class(uint32_t tile, int cnt, float& q, bool& uniform,
+                                           bool& has_electron) {
+  q = lds_f32(tile + 12u);
+  bool ok = true, neg = false;
+  for (int k = static_cast<int>(threadIdx.x & 31u); k < cnt; k += 32) {
+    const float w = lds_f32(tile + 16u * k + 12u);
+    ok = ok && (w == q);
+    neg = neg || (w < 0.0f);
+  }
+  uniform = __all_sync(0xffffffffu, ok);
+  has_electron = __any_sync(0xffffffffu, neg);
+}
+
+// Pairs of one tile with the local moments.  UNIFORM: every source is an
+// electron of one charge, the charge is applied once per tile (fold_q);
+// otherwise each pair takes its own charge and only electrons count.
+// rloc2e = r_loc^2 + eps^2 is compared with r^2 + eps^2.
+template <int R, bool UNIFORM>
+__device__ __forceinline__ void ion_pairs_moments(uint32_t ptile, const float4* vtile, int cnt,
+                                                  const float (&xi)[R], const float (&yi)[R],
+                                                  const float (&zi)[R], float eps2, float rloc2e,
+                                                  Acc<R, false>& acc, LocalMoments<R>& m) {
+#pragma unroll 4
+  for (int j = 0; j < cnt; ++j) {
+    const float4 p = lds_f4(ptile + 16u * j);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float dx = p.x - xi[r], dy = p.y - yi[r], dz = p.z - zi[r];
+      float r2 = fmaf(dx, dx, eps2);
+      r2 = fmaf(dy, dy, r2);
+      r2 = fmaf(dz, dz, r2);
+      const float ri = rsqrt_mufu(r2);
+      const float ri2 = ri * ri;
+      const float s3 = UNIFORM ? ri2 * ri : p.w * ri2 * ri;
+      acc.ax[r] = fmaf(dx, s3, acc.ax[r]);
+      acc.ay[r] = fmaf(dy, s3, acc.ay[r]);
+      acc.az[r] = fmaf(dz, s3, acc.az[r]);
+      if ((UNIFORM || p.w < 0.0f) && r2 < rloc2e) m.add(r, vtile[j]);
+    }
+  }
+}
+
+// Field (FP32/Kahan) and local electron moments at R ion targets per thread,
+// from source segment blockIdx.y of the cluster's live records.  The live
+// records are the ions and electrons below the next free electron slot (the
+// slots are filled densely), split into gridDim.y equal segments.  Tiles of
+// one charge take the charge out of the pair loop; ion-only tiles skip the
+// moment test; uncharged tiles and dead record groups are skipped.
 template <int THREADS, int R, int TILE, int STAGES>
 __global__ void __launch_bounds__(THREADS) k_ion_field(const IonArgs a) {
   __shared__ IonStage<TILE, STAGES> sm;
@@ -76,20 +156,24 @@ __global__ void __launch_bounds__(THREADS) k_ion_field(const IonArgs a) {
   }
   __syncthreads();
   const float4* __restrict__ cur = (step & 1) ? a.posq1 : a.posq0;
-  // this CTA sums source segment blockIdx.y: records [j0, j0 + ns) of the cluster
-  const long long j0 = static_cast<long long>(blockIdx.y) * a.seg_len;
-  const long long ns = (a.c.n_pad - j0 < a.seg_len) ? a.c.n_pad - j0 : a.seg_len;
+  // live records [0, n_live): no active electron sits at or above the next free slot
+  long long n_live = __ldcg(a.next_slot);
+  n_live = n_live > a.ion.slot_base ? n_live : a.ion.slot_base;
+  n_live = n_live < a.c.n_pad ? (n_live > 0 ? n_live : 0) : a.c.n_pad;
+  const long long per_seg = (n_live + gridDim.y - 1) / gridDim.y;
+  const long long seg_len = (per_seg + TILE - 1) / TILE * TILE;
+  const long long j0 = static_cast<long long>(blockIdx.y) * seg_len;
+  const long long ns = (j0 >= n_live) ? 0 : ((n_live - j0 < seg_len) ? n_live - j0 : seg_len);
   const float4* src = cur + a.c.off + j0;
   const float4* vsrc = a.vel + a.c.off + j0;
   const long long t0 = static_cast<long long>(blockIdx.x) * (THREADS * R);
-  const float rloc2 = static_cast<float>(a.ion.r_loc * a.ion.r_loc);
   const float eps2 = a.c.eps2;
+  const float rloc2e = static_cast<float>(a.ion.r_loc * a.ion.r_loc) + eps2;
   float xi[R], yi[R], zi[R];
   Acc<R, false> acc;
   acc.zero();
-  // per target: sum w, sum w du (3), sum w du^2, u_ref (3); ref set once
-  float mw[R], mx[R], my[R], mz[R], mq[R], rx[R], ry[R], rz[R];
-  bool have[R];
+  LocalMoments<R> mom;
+  mom.zero();
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const long long t = t0 + threadIdx.x + r * THREADS;
@@ -97,8 +181,6 @@ __global__ void __launch_bounds__(THREADS) k_ion_field(const IonArgs a) {
     xi[r] = p.x;
     yi[r] = p.y;
     zi[r] = p.z;
-    mw[r] = mx[r] = my[r] = mz[r] = mq[r] = rx[r] = ry[r] = rz[r] = 0.0f;
-    have[r] = false;
   }
   const int ntiles = static_cast<int>((ns + TILE - 1) / TILE);
   // only tiles holding a live group are copied and summed, in the same order
@@ -124,36 +206,28 @@ __global__ void __launch_bounds__(THREADS) k_ion_field(const IonArgs a) {
     const int cnt = static_cast<int>(rem < TILE ? rem : TILE);
     if (!*reinterpret_cast<volatile int*>(&s_abort)) {
       const uint32_t ptile = smem_u32(&sm.pos[s][0]);
+      float qt;
+      bool uniform, has_e;
+      tile_class(ptile, cnt, qt, uniform, has_e);
+      if (uniform) {
+        if (qt < 0.0f) {
+          ion_pairs_moments<R, true>(ptile, &sm.vel[s][0], cnt, xi, yi, zi, eps2, rloc2e, acc,
+                                     mom);
+          fold_q<R, false>(acc, qt);
+        } else if (qt > 0.0f) {
 #pragma unroll 4
-      for (int j = 0; j < cnt; ++j) {
-        const float4 p = lds_f4(ptile + 16u * j);
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const float dx = p.x - xi[r], dy = p.y - yi[r], dz = p.z - zi[r];
-          const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          const float ri = rsqrt_mufu(d2 + eps2);
-          const float s3 = p.w * ri * ri * ri;
-          acc.ax[r] = fmaf(dx, s3, acc.ax[r]);
-          acc.ay[r] = fmaf(dy, s3, acc.ay[r]);
-          acc.az[r] = fmaf(dz, s3, acc.az[r]);
-          if (p.w < 0.0f && d2 < rloc2) {  // an electron within r_loc
-            const float4 v = sm.vel[s][j];
-            if (!have[r]) {
-              rx[r] = v.x;
-              ry[r] = v.y;
-              rz[r] = v.z;
-              have[r] = true;
-            }
-            const float ux = v.x - rx[r], uy = v.y - ry[r], uz = v.z - rz[r];
-            mw[r] += v.w;
-            mx[r] = fmaf(v.w, ux, mx[r]);
-            my[r] = fmaf(v.w, uy, my[r]);
-            mz[r] = fmaf(v.w, uz, mz[r]);
-            mq[r] = fmaf(v.w, fmaf(ux, ux, fmaf(uy, uy, uz * uz)), mq[r]);
-          }
+          for (int j = 0; j < cnt; ++j) pair_u<R, false>(lds_f4(ptile + 16u * j), xi, yi, zi, eps2, acc);
+          fold_q<R, false>(acc, qt);
         }
+      } else if (has_e) {
+        ion_pairs_moments<R, false>(ptile, &sm.vel[s][0], cnt, xi, yi, zi, eps2, rloc2e, acc,
+                                    mom);
+        fold<R, false>(acc);
+      } else {
+#pragma unroll 4
+        for (int j = 0; j < cnt; ++j) pair<R, false>(lds_f4(ptile + 16u * j), xi, yi, zi, eps2, acc);
+        fold<R, false>(acc);
       }
-      fold<R, false>(acc);
     }
     __syncthreads();
     if (*reinterpret_cast<volatile int*>(&s_abort)) {
@@ -179,14 +253,14 @@ __global__ void __launch_bounds__(THREADS) k_ion_field(const IonArgs a) {
     o[0] = -(static_cast<double>(acc.sx[r]) - acc.cx[r]);
     o[1] = -(static_cast<double>(acc.sy[r]) - acc.cy[r]);
     o[2] = -(static_cast<double>(acc.sz[r]) - acc.cz[r]);
-    o[3] = mw[r];
-    o[4] = mx[r];
-    o[5] = my[r];
-    o[6] = mz[r];
-    o[7] = mq[r];
-    o[8] = rx[r];
-    o[9] = ry[r];
-    o[10] = rz[r];
+    o[3] = mom.w[r];
+    o[4] = mom.sx[r];
+    o[5] = mom.sy[r];
+    o[6] = mom.sz[r];
+    o[7] = mom.sq[r];
+    o[8] = mom.rx[r];
+    o[9] = mom.ry[r];
+    o[10] = mom.rz[r];
   }
 }
 
@@ -368,7 +442,15 @@ __global__ void __launch_bounds__(256) k_ion_apply(const IonArgs a) {
         MD_IN_RANGE(a.err, slot, 0, a.c.n))
       apply_one(a, step, t, slot);
   }
-  if (blockIdx.x == gridDim.x - 1 && tid == 0) *a.next_slot = s_base + total;
+  if (blockIdx.x == gridDim.x - 1 && tid == 0) {
+    const long long next = s_base + total;
+    *a.next_slot = next;
+    // the step splits the live records, below the new next free slot (with
+    // the segment count the descriptor holds now)
+    if (a.cl_dev)
+      a.cl_dev->seg_len = live_seg_len(a.cl_dev->n_pad, a.cl_dev->nseg,
+                                       next > a.ion.slot_base ? next : a.ion.slot_base);
+  }
 }
 
 // Liveness flags from the current records: a group of kLiveGroup records is
@@ -391,8 +473,8 @@ __global__ void k_live_init(const float4* posq0, const float4* posq1, const unsi
   tgt_live[g] = t;
 }
 
-constexpr int kIonThreads = 64;
-constexpr int kIonR = 2;
+constexpr int kIonThreads = 128;
+constexpr int kIonR = 1;
 constexpr int kIonTile = 512;
 
 }  // namespace
@@ -406,8 +488,16 @@ cudaError_t launch_live_init(const float4* posq0, const float4* posq1, const uns
   return cudaGetLastError();
 }
 
+int ion_field_targets_per_cta() { return kIonThreads * kIonR; }
+
+cudaError_t ion_field_blocks_per_sm(int* out) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      out, k_ion_field<kIonThreads, kIonR, kIonTile, 2>, kIonThreads, 0);
+}
+
 cudaError_t launch_ion_pass(const IonArgs& a, cudaStream_t s) {
   if (a.ion.n_ions <= 0) return cudaSuccess;
+  if (a.nseg < 1 || a.nseg > kIonMaxSeg) return cudaErrorInvalidValue;
   const long long per = kIonThreads * kIonR;
   const dim3 g1(static_cast<unsigned>((a.ion.n_ions + per - 1) / per),
                 static_cast<unsigned>(a.nseg));

@@ -52,6 +52,10 @@ cudaError_t dev_alloc(T** p, size_t count) {
 struct md_ctx {
   int device = 0;
   int sm_count = 0;
+  int ion_field_bps = 1;   // resident CTAs per SM of the ionization field kernel
+  // per cluster: records live at the last upload (an ionizing cluster: below
+  // its next free electron slot), for the choice of the source split
+  std::vector<long long> live_host;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
 
@@ -296,10 +300,13 @@ void segments_for(const md::ClusterDev& cl, int S, int tile, int* nseg, int* seg
 
 long long units_for(const md_ctx* c, long long per, int S, int tile) {
   long long u = 0;
-  for (auto& cl : c->cl) {
+  for (int ci = 0; ci < c->n_clusters; ++ci) {
+    const md::ClusterDev& cl = c->cl[ci];
     int ns, len;
     segments_for(cl, S, tile, &ns, &len);
-    u += (cl.n_pad + per - 1) / per * ns;
+    // i-blocks past the live records finish at once: count the live ones
+    const long long live = ci < static_cast<int>(c->live_host.size()) ? c->live_host[ci] : cl.n_pad;
+    u += (std::max(1LL, live) + per - 1) / per * ns;
   }
   return u;
 }
@@ -464,15 +471,27 @@ md::IonArgs ion_args(md_ctx* c, int ci, int force) {
   a.scratch = c->d_ion_scratch;
   a.blk_fired = c->d_ion_blk;
   a.pass_slot = c->d_ion_pass + ci;
-  // split the sources of the field pass until about 8 CTAs per SM are busy,
-  // keeping at least 4 tiles of sources per segment
+  // split the live sources of the field pass into nseg equal segments: the
+  // (ion block, segment) CTAs fill whole waves of the resident CTA slots as
+  // well as possible, with a small cost per extra segment; each segment keeps
+  // at least 4 tiles of the cluster's records
   {
-    const long long ion_blocks = (a.ion.n_ions + 127) / 128;
-    const long long want = (8LL * c->sm_count + ion_blocks - 1) / std::max(1LL, ion_blocks);
+    const long long per = md::ion_field_targets_per_cta();
+    const long long ion_blocks = (a.ion.n_ions + per - 1) / per;
+    const long long cap = std::max(1LL, static_cast<long long>(c->ion_field_bps) * c->sm_count);
     const long long by_len = std::max(1LL, static_cast<long long>(a.c.n_pad) / 2048);
-    a.nseg = static_cast<int>(std::max(1LL, std::min({want, by_len,
-                                                      static_cast<long long>(md::kIonMaxSeg)})));
-    a.seg_len = (a.c.n_pad + a.nseg - 1) / a.nseg;
+    const int smax = static_cast<int>(std::min<long long>(md::kIonMaxSeg, by_len));
+    double best = -1.0;
+    a.nseg = 1;
+    for (int sg = 1; sg <= smax; ++sg) {
+      const long long units = ion_blocks * sg;
+      const long long waves = (units + cap - 1) / cap;
+      const double score = static_cast<double>(units) / static_cast<double>(waves * cap) - 0.002 * sg;
+      if (score > best + 1e-12) {
+        best = score;
+        a.nseg = sg;
+      }
+    }
   }
   a.out = c->d_ion_out + 4 * c->ion_out_off[ci];
   a.fired = c->d_ion_fired + c->ion_out_off[ci];
@@ -482,6 +501,7 @@ md::IonArgs ion_args(md_ctx* c, int ci, int force) {
   a.tgt_live = c->d_tgt_live;
   a.vel = c->d_vel;
   a.next_slot = c->d_ion_next + ci;
+  a.cl_dev = c->d_cl + ci;
   return a;
 }
 
@@ -657,6 +677,17 @@ md_status upload_cluster(md_ctx* c, int ci, const md_particles& p) {
   if (c->d_ion_next && c->ion[ci].rate_model)
     MD_CUDA(cudaMemcpyAsync(c->d_ion_next + ci, &next_slot, sizeof(long long),
                             cudaMemcpyHostToDevice, c->stream));
+  if (static_cast<int>(c->live_host.size()) < c->n_clusters)
+    c->live_host.resize(static_cast<size_t>(c->n_clusters), 0);
+  c->live_host[ci] = (c->d_ion_next && c->ion[ci].rate_model) ? next_slot : c->cl[ci].n_pad;
+  // the step's source segments must cover the new live records: reset the
+  // device descriptor's segment length (once the split is configured)
+  int live_len = 0;
+  if (c->d_ion_next && c->ion[ci].rate_model && c->cl[ci].nseg >= 1) {
+    live_len = md::live_seg_len(c->cl[ci].n_pad, c->cl[ci].nseg, next_slot);
+    MD_CUDA(cudaMemcpyAsync(&c->d_cl[ci].seg_len, &live_len, sizeof(int), cudaMemcpyHostToDevice,
+                            c->stream));
+  }
   if (c->d_src_live)
     MD_CUDA(md::launch_live_init(c->d_posq[0], c->d_posq[1], c->d_kind, c->d_step, c->n_total,
                                  c->d_src_live, c->d_tgt_live, c->stream));
@@ -734,6 +765,8 @@ md_status md_init(md_ctx** out, const md_config* cfgs, int32_t n_clusters,
     return bail(fail(MD_ERR_UNSUPPORTED, "device %s is sm_%d%d; this library is built for sm_103a",
                      prop.name, prop.major, prop.minor));
   c->sm_count = prop.multiProcessorCount;
+  e = md::ion_field_blocks_per_sm(&c->ion_field_bps);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor"));
   if (stream) {
     c->stream = static_cast<cudaStream_t>(stream);
   } else {

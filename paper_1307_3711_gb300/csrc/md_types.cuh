@@ -28,9 +28,21 @@ struct ClusterDev {
   long long det_off;  // first histogram entry of the cluster (5 x (det_nbins + 1) entries)
 };
 
+// Segment length that splits the live records [0, live) of a cluster of
+// n_pad records into nseg source segments of the step (a multiple of kPad).
+// It is at most the split of all n_pad records, so every segment starts
+// inside the cluster; the step's segments cover [0, live) whole.
+__host__ __device__ inline int live_seg_len(int n_pad, int nseg, long long live) {
+  nseg = nseg < 1 ? 1 : nseg;
+  live = live < 0 ? 0 : (live > n_pad ? n_pad : live);
+  long long len = (live + nseg - 1) / nseg;
+  len = (len + kPad - 1) / kPad * kPad;
+  return static_cast<int>(len < kPad ? kPad : len);
+}
+
 constexpr int kMaxZ = 16;
 constexpr int kIonScratch = 11;   // doubles per ion and source segment
-constexpr int kIonMaxSeg = 8;     // source segments of the ionization field pass
+constexpr int kIonMaxSeg = 32;    // source segments of the ionization field pass
 
 // Ionization parameters of one cluster (Sec. II, ionization paragraph).
 struct IonDev {
@@ -113,8 +125,7 @@ struct IonArgs {
   double* scratch;    // [nseg][n_ions][kIonScratch]: ex, ey, ez, sw, sw du_x, sw du_y,
                       // sw du_z, sw du^2, u_ref (3) of each source segment (du = u -
                       // u_ref, u_ref = the segment's first local electron's u)
-  int nseg;           // source segments of the field pass
-  long long seg_len;  // sources per segment
+  int nseg;           // source segments of the field pass (equal shares of the live records)
   int* blk_fired;     // [ceil(n_ions / 256)] fired ions per block of the decision
   long long* pass_slot;  // first free slot at the start of the pass
   double* out;        // [n_ions][4]: |E|, ne (cm^-3), Te (eV), P
@@ -125,6 +136,9 @@ struct IonArgs {
   unsigned char* tgt_live;
   float4* vel;        // FP32 (ux, uy, uz, w) per record
   long long* next_slot;  // cluster-relative record of the next free electron slot
+  // this cluster's descriptor on the device: the pass that moves next_slot
+  // also resets its seg_len to the split of the live records (live_seg_len)
+  ClusterDev* cl_dev;
 };
 
 struct FieldArgs {

@@ -308,3 +308,53 @@ def test_graph_replay_equals_direct_launches_when_ionizing(md):
     for k in ("x", "u", "z", "kind", "w"):
         assert np.array_equal(getattr(out[0], k), getattr(out[1], k)), k
     assert out[0].z[:1500].sum() > 0
+
+
+def test_step_after_ionization_splits_live_sources(md):
+    """Once passes have freed electrons into the dense slots, the step splits
+    only the live records (below the next free slot) into its source
+    segments, and the ionization field pass splits them likewise.  With 4
+    step segments (about 1.3k records each here, against 4.5k for a split of
+    all 18k records), the kick and drift of every active record in the step
+    after a pass are the FP64 oracle's (field of all charged live records,
+    laser, Boris) on the state the pass left."""
+    n = 2000
+    lam = 0.806
+    c = synth.make_cluster(4, n, 0, synth.nm_to_len(8.0 * (n / 200000) ** (1 / 3), lam), 0,
+                           AR["mass"], n_electron_slots=8 * n)
+    rw = synth.nm_to_len(AR["r_w_nm"], lam)
+    tau = synth.sin2_length_from_fwhm(synth.fs_to_time(100.0, lam))
+    t0 = np.floor(tau / 2 / np.pi) * np.pi + 0.5 * np.pi - 0.3
+    eps = synth.nm_to_len(0.1, lam)
+    kw = dict(a0=0.0617, tau=tau, t0=t0, dt=0.02, softening=eps, envelope=synth.ENV_SIN2,
+              lambda_um=lam, rate_model=1, ionize_every=0, zmax=8, n_ions=n, slot_base=n,
+              seed=9, r_loc=3 * rw, r_create=rw, species=AR)
+    kc = oracle.coulomb_constant(lam)
+    with md.Context([md.make_config(**kw)], [md.HostParticles.from_cluster(c)]) as ctx:
+        ctx.set_tuning(128, 4, 512, 0, 4, 0)
+        assert ctx.tuning()[4] == 4
+        worst = []
+        for k in range(3):
+            ctx.ionize()                  # frees electrons, moves the next free slot
+            g0 = ctx.get_particles(0)
+            step = ctx.step_index()
+            ctx.step(1)
+            g1 = ctx.get_particles(0)
+            act = np.flatnonzero(g0.kind != md.KIND_INACTIVE)
+            assert act.max() < n + 8 * n and act[-1] - act[0] + 1 == act.size  # dense
+            q = np.where(g0.kind != md.KIND_INACTIVE, g0.w * g0.z, 0.0)
+            e64 = oracle.coulomb_field(g0.x[act], g0.x, q, eps, kc, self_idx=act,
+                                       nthreads=os.cpu_count() or 1)
+            a, b = oracle.laser_fields(t0 + step * kw["dt"], kw["a0"], 0, synth.ENV_SIN2, tau)
+            du_ref, dx_ref = [], []
+            for m, i in enumerate(act):
+                u1 = oracle.boris_kick(g0.u[i], e64[m] + a, b, g0.z[i] / g0.mass[i], kw["dt"])
+                du_ref.append(u1 - g0.u[i])
+                dx_ref.append(oracle.drift(g0.x[i], u1, kw["dt"]) - g0.x[i])
+            eu = summary(force_error(g1.u[act] - g0.u[act], np.array(du_ref)))
+            ex = summary(force_error(g1.x[act] - g0.x[act], np.array(dx_ref)))
+            print(k, "active", act.size, "kick", eu, "drift", ex)
+            assert eu["p99"] <= 2e-5 and ex["p99"] <= 2e-5, k
+            worst.append(max(eu["max"], ex["max"]))
+        assert act.size > n + 500        # the passes freed electrons
+        assert max(worst) < 1e-3
