@@ -111,14 +111,46 @@ __device__ __forceinline__ void tile_class(uint32_t tile, int cnt, float& q, boo
 // Pairs of one tile with the local moments.  UNIFORM: every source is an
 // electron of one charge, the charge is applied once per tile (fold_q);
 // otherwise each pair takes its own charge and only electrons count.
-// rloc2e = r_loc^2 + eps^2 is compared with r^2 + eps^2.
+// rloc2e = r_loc^2 + eps^2 is compared with r^2 + eps^2.  Sources go in
+// groups of 4 with one (rarely taken) branch per group on the nearest of the
+// 4; inside it the electrons within r_loc are added in source order.
 template <int R, bool UNIFORM>
 __device__ __forceinline__ void ion_pairs_moments(uint32_t ptile, const float4* vtile, int cnt,
                                                   const float (&xi)[R], const float (&yi)[R],
                                                   const float (&zi)[R], float eps2, float rloc2e,
                                                   Acc<R, false>& acc, LocalMoments<R>& m) {
-#pragma unroll 4
-  for (int j = 0; j < cnt; ++j) {
+  constexpr int G = 4;
+  int j = 0;
+  for (; j + G <= cnt; j += G) {
+    float4 p[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) p[g] = lds_f4(ptile + 16u * (j + g));
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      float near2[G];
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const float dx = p[g].x - xi[r], dy = p[g].y - yi[r], dz = p[g].z - zi[r];
+        float r2 = fmaf(dx, dx, eps2);
+        r2 = fmaf(dy, dy, r2);
+        r2 = fmaf(dz, dz, r2);
+        const float ri = rsqrt_mufu(r2);
+        const float ri2 = ri * ri;
+        const float s3 = UNIFORM ? ri2 * ri : p[g].w * ri2 * ri;
+        acc.ax[r] = fmaf(dx, s3, acc.ax[r]);
+        acc.ay[r] = fmaf(dy, s3, acc.ay[r]);
+        acc.az[r] = fmaf(dz, s3, acc.az[r]);
+        near2[g] = (UNIFORM || p[g].w < 0.0f) ? r2 : rloc2e;
+      }
+      const float mn = fminf(fminf(near2[0], near2[1]), fminf(near2[2], near2[3]));
+      if (mn < rloc2e) {
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+          if (near2[g] < rloc2e) m.add(r, vtile[j + g]);
+      }
+    }
+  }
+  for (; j < cnt; ++j) {
     const float4 p = lds_f4(ptile + 16u * j);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -474,7 +506,7 @@ __global__ void k_live_init(const float4* posq0, const float4* posq1, const unsi
 }
 
 constexpr int kIonThreads = 128;
-constexpr int kIonR = 1;
+constexpr int kIonR = 2;
 constexpr int kIonTile = 512;
 
 }  // namespace
