@@ -71,12 +71,13 @@ def parse_args():
                     help="force a kernel configuration: threads,r,tile,packed[,jsplit[,min_blocks]]")
     ap.add_argument("--workload", default="xe3_200k",
                     choices=["xe3_200k", "scan256", "precision_1m", "ar_ionize", "iedf",
-                             "nscale"],
+                             "iedf_xe", "nscale"],
                     help="xe3_200k: the headline N=200k cluster; scan256: 256 clusters of a "
                          "parameter scan in one persistent launch; precision_1m: 500k Ar+ + 500k "
                          "e, laser off; ar_ionize: neutral Ar atoms ionizing; iedf: a small "
                          "ionizing Ar cluster through the whole pulse with ion energy detectors "
-                         "at 9 R0 (the IEDF along and across the polarization)")
+                         "at 9 R0 (the IEDF along and across the polarization); iedf_xe: the "
+                         "same for the Xe_2600 cluster of Sec. III (16 charge states)")
     ap.add_argument("--rates", default="plain", choices=["plain", "mlp"],
                     help="ar_ionize: plain ADK + Lotz rates, or the BF16 surrogate trained on "
                          "the GPU before the run (plain rates outside its domain)")
@@ -406,69 +407,102 @@ def build_contexts(md, args, rank, stream):
 
 # ------------------------------------------------------------------ iedf --
 
+def iedf_case(args):
+    """The two IEDF runs.  iedf: neutral Ar cluster (args.n atoms, default
+    4000, at the density of 200k atoms in 8 nm), 806 nm, 8e15 W/cm^2 (a0 =
+    0.0617), 100 fs sin^2 pulse, run to 1.5 pulse lengths, 8 charge states.
+    iedf_xe: the Xe_2600 case of Sec. III (2600 atoms, R0 from Eq. 1 with the
+    Wigner-Seitz radius of Sec. II), 790 nm, 4e15 W/cm^2 (a0 from Eq. 2),
+    28 fs sin^2 pulse (intensity FWHM), run to the pulse length + 1 ps so
+    most of the heavy ions reach the detectors, 16 charge states, Lotz
+    collisional rates with the xenon table."""
+    from paper_1307_3711_gb300 import md
+    if args.workload == "iedf_xe":
+        n = args.n if args.n != 200000 else 2600
+        lam, sp, zmax = 0.79, synth.XENON, 16
+        r0 = synth.nm_to_len(sp["r_w_nm"] * n ** (1 / 3), lam)
+        a0 = md.a0_from_intensity(4e15, lam)
+        tau = synth.sin2_length_from_fwhm(synth.fs_to_time(28.0, lam))
+        t_end = tau + synth.fs_to_time(1000.0, lam)
+        nb, e_max = 250, 5e5
+        text = (f"iedf_xe{n}: {n} Xe atoms (neutral at t = 0) in {sp['r_w_nm'] * n ** (1 / 3):.2f}"
+                f" nm + 16 slots each, 790 nm, 4e15 W/cm^2 (a0 {a0:.4f}), 28 fs sin^2, pulse "
+                "+ 1 ps, detectors at 9 R0")
+    else:
+        n = args.n if args.n != 200000 else 4000
+        lam, sp, zmax = 0.806, synth.ARGON, 8
+        r0 = synth.nm_to_len(8.0 * (n / 200000) ** (1 / 3), lam)
+        a0 = 0.0617
+        tau = synth.sin2_length_from_fwhm(synth.fs_to_time(100.0, lam))
+        t_end = 1.5 * tau
+        nb, e_max = 200, 2e5
+        text = (f"iedf_ar{n // 1000}k: {n} Ar atoms (neutral at t = 0) in "
+                f"{r0 / synth.nm_to_len(1.0, lam):.2f} nm + 8 slots each, 806 nm, a0 0.0617, "
+                "100 fs sin^2, 1.5 pulse lengths, detectors at 9 R0")
+    return dict(n=n, lam=lam, species=sp, zmax=zmax, r0=r0, a0=a0, tau=tau, t_end=t_end,
+                nb=nb, e_max=e_max, text=text)
+
+
 def run_iedf(args):
-    """Neutral Ar cluster (args.n atoms, default 4000, at the density of 200k
-    atoms in 8 nm), 806 nm, 8e15 W/cm^2, 100 fs sin^2 pulse, run from t = 0
-    to 1.5 pulse lengths with ionization before every step and detectors at
-    9 R0 (30-degree cones): ion counts and mean energies along (+-x) and
-    across (+-y) the polarization."""
+    """A small ionizing cluster through the whole pulse with ionization before
+    every step and detectors at 9 R0 (30-degree cones): ion counts and mean
+    energies along (+-x) and across (+-y) the polarization (iedf_case)."""
     import torch
     from paper_1307_3711_gb300 import build
     build.build()
     from paper_1307_3711_gb300 import md
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
-    n = args.n if args.n != 200000 else 4000
-    lam = 0.806
-    r0 = synth.nm_to_len(8.0 * (n / 200000) ** (1 / 3), lam)
-    c = synth.make_cluster(rank + 1, n, 0, r0, 0, synth.ARGON["mass"], n_electron_slots=8 * n)
-    rw = synth.nm_to_len(synth.ARGON["r_w_nm"], lam)
-    tau = synth.sin2_length_from_fwhm(synth.fs_to_time(100.0, lam))
-    cfg = md.make_config(a0=0.0617, tau=tau, dt=0.02, softening=synth.nm_to_len(0.1, lam),
+    k = iedf_case(args)
+    n, lam, sp, zmax, r0 = k["n"], k["lam"], k["species"], k["zmax"], k["r0"]
+    c = synth.make_cluster(rank + 1, n, 0, r0, 0, sp["mass"], n_electron_slots=zmax * n)
+    rw = synth.nm_to_len(sp["r_w_nm"], lam)
+    cfg = md.make_config(a0=k["a0"], tau=k["tau"], dt=0.02, softening=synth.nm_to_len(0.1, lam),
                          envelope=synth.ENV_SIN2, lambda_um=lam, rate_model=md.RATES_PLAIN,
-                         ionize_every=1, zmax=8, n_ions=n, slot_base=n, seed=rank + 3,
-                         r_loc=3 * rw, r_create=rw, species=synth.ARGON)
+                         ionize_every=1, zmax=zmax, n_ions=n, slot_base=n, seed=rank + 3,
+                         r_loc=3 * rw, r_create=rw, species=sp)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    nb, e_max = 200, 2e5
-    nsteps = int(1.5 * tau / 0.02)
+    nb, e_max = k["nb"], k["e_max"]
+    nsteps = int(k["t_end"] / 0.02)
     chunk = 2000
     with md.Context([cfg], [md.HostParticles.from_cluster(c)], stream=stream.cuda_stream) as ctx:
         ctx.set_detectors(0, 9 * r0, cone_deg=30.0, e_max_ev=e_max, n_bins=nb)
         ms, pairs, done = 0.0, 0.0, 0
         while done < nsteps:
-            k = min(chunk, nsteps - done)
+            kk = min(chunk, nsteps - done)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            ctx.step(k)
+            ctx.step(kk)
             e1.record(stream)
             torch.cuda.synchronize()
             ms += e0.elapsed_time(e1)
-            pairs += k * float(ctx.diagnostics(0)["n_active"]) ** 2   # sampled per chunk
-            done += k
-        d = ctx.diagnostics(0)
+            pairs += kk * float(ctx.diagnostics(0)["n_active"]) ** 2   # sampled per chunk
+            done += kk
+        zs = ctx.get_particles(0).z[:n]
         det, inside = ctx.iedf(0)
     if rank != 0:
         return
     centers = (np.arange(nb) + 0.5) * e_max / nb
     iedf = {}
-    for k, name in enumerate(md.DETECTORS):
-        h = det[k][:nb].astype(float)
-        iedf[name] = {"ions": int(det[k].sum()),
+    for j, name in enumerate(md.DETECTORS):
+        h = det[j][:nb].astype(float)
+        iedf[name] = {"ions": int(det[j].sum()),
                       "mean_kev": float((h * centers).sum() / max(h.sum(), 1.0) / 1e3),
-                      "overflow": int(det[k][nb])}
+                      "overflow": int(det[j][nb])}
+    hin = inside[:nb].astype(float)
     line = {
         "metric": METRIC, "value": pairs / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
         "steps": nsteps, "warmup": 0, "ms_per_step": ms / nsteps,
         "steps_per_s": nsteps / (ms / 1e3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"iedf_ar{n // 1000}k: {n} Ar atoms (neutral at t = 0) in "
-                               f"{r0 / synth.nm_to_len(1.0, lam):.2f} nm + 8 slots each, 806 nm, "
-                               "a0 0.0617, 100 fs sin^2, 1.5 pulse lengths, detectors at 9 R0",
+        "config": {"workload": k["text"],
                    "pairs_counted": "(active records)^2 sampled every 2000 steps",
                    "l2": "not flushed (a small cluster stays in L2)"},
-        "ionization": {"charge_fractions": (d["charge_count"][:9] / n).tolist()},
+        "ionization": {"charge_fractions": (np.bincount(zs, minlength=zmax + 1) / n).tolist(),
+                       "mean_charge": float(zs.mean())},
         "iedf": iedf, "ions_inside": int(inside.sum()),
+        "inside_mean_kev": float((hin * centers).sum() / max(hin.sum(), 1.0) / 1e3),
         "gpu_launches": 5 * nsteps,   # ion field, inputs, decision, apply, step
     }
     print(json.dumps(line), flush=True)
@@ -726,7 +760,7 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == "iedf":
+    elif args.workload in ("iedf", "iedf_xe"):
         run_iedf(args)
     elif args.workload == "nscale":
         run_nscale(args)

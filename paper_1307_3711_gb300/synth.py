@@ -40,6 +40,21 @@ ARGON = {
     "r_w_nm": 0.240,
 }
 
+# Xenon ionization data for the Xe runs (Sec. III, the Xe_2600 case, whose
+# collisional rates the paper takes from the Lotz formula): ionization energies
+# of Xe^z -> Xe^(z+1), z = 0..15 (eV, NIST Atomic Spectra Database, rounded),
+# and the electrons in the outermost occupied subshell of Xe^z (5p^6 ... 5p^1,
+# then 5s^2, 5s^1, then 4d^10 ... 4d^3).
+XENON = {
+    "name": "Xe",
+    "ip_ev": [12.1298, 20.975, 31.05, 42.20, 54.1, 66.703, 91.6, 105.978,
+              179.84, 202.0, 229.02, 255.0, 281.0, 314.0, 343.0, 374.0],
+    "q_outer": [6.0, 5.0, 4.0, 3.0, 2.0, 1.0, 2.0, 1.0,
+                10.0, 9.0, 8.0, 7.0, 6.0, 5.0, 4.0, 3.0],
+    "mass": MASS_XE,
+    "r_w_nm": R_W_ANGSTROM["Xe"] / 10.0,
+}
+
 
 def nm_to_len(nm: float, lambda_um: float = 0.8) -> float:
     """Length in nm -> units of 1/k (k = 2 pi / lambda)."""

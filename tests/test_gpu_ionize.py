@@ -358,3 +358,55 @@ def test_step_after_ionization_splits_live_sources(md):
             worst.append(max(eu["max"], ex["max"]))
         assert act.size > n + 500        # the passes freed electrons
         assert max(worst) < 1e-3
+
+
+def test_xenon_charge_states_up_to_15_follow_oracle(md):
+    """Xe (Sec. III, the Xe_2600 case, Lotz collisional rates) with 16 charge
+    states: ions at every charge 0..15, their electrons hot (200 eV) in the
+    16 slots per atom.  From the GPU's own |E|, n_e, T_e the oracle's decision
+    with the xenon table reproduces every fired flag, charge state and freed
+    electron, including ions past the 5s shell (z >= 8, the 4d electrons)."""
+    XE = synth.XENON
+    n, zmax, lam = 1600, 16, 0.79
+    rw = synth.nm_to_len(XE["r_w_nm"], lam)
+    r0 = rw * n ** (1.0 / 3.0)                       # Eq. 1 at solid density
+    c = synth.make_cluster(21, n, 0, r0, 0, XE["mass"], n_electron_slots=zmax * n)
+    z = c.z.copy()
+    z[:n] = np.arange(n) % zmax
+    n_el = int(z[:n].sum())
+    rng = np.random.default_rng(22)
+    x, u, active = c.x.copy(), c.u.copy(), c.active.copy()
+    x[n:n + n_el] = synth.uniform_sphere(rng, n_el, r0)
+    u[n:n + n_el] = rng.normal(size=(n_el, 3)) * synth.thermal_sigma_u(200.0, 1.0)
+    z[n:n + n_el] = -1
+    active[n:n + n_el] = 1
+    kind = np.where(active == 0, md.KIND_INACTIVE, np.where(z < 0, md.KIND_ELECTRON,
+                                                            md.KIND_ION)).astype(np.uint8)
+    hp = md.HostParticles(x, u, z, c.mass, c.w, kind)
+    kw = dict(a0=0.05, tau=1.0, t0=0.5 * np.pi, dt=0.5, softening=synth.nm_to_len(0.1, lam),
+              envelope=synth.ENV_FLAT, lambda_um=lam, rate_model=1, ionize_every=0, zmax=zmax,
+              n_ions=n, slot_base=n, seed=777, r_loc=3 * rw, r_create=rw, species=XE)
+    fired_high = 0
+    with md.Context([md.make_config(**kw)], [hp]) as ctx:
+        for k in range(4):
+            step = 100 + 7 * k
+            ctx.set_step(step)
+            g0 = ctx.get_particles(0)
+            ctx.ionize()
+            info = ctx.ionization(0)
+            g1 = ctx.get_particles(0)
+            z_ref, fired_ref, off_ref, p_ref = oracle.decide(
+                np.arange(n), g0.z[:n], info["emag"], info["ne"], info["te"], XE, zmax,
+                kw["seed"], step, kw["dt"], kw["r_create"], lambda_um=lam)
+            assert np.array_equal(info["fired"], fired_ref), k
+            assert np.array_equal(g1.z[:n], z_ref), k
+            np.testing.assert_allclose(info["prob"], p_ref, rtol=1e-12, atol=1e-300)
+            n_act = int(np.sum(g0.kind[n:] == md.KIND_ELECTRON))
+            for rank, i in enumerate(np.nonzero(fired_ref)[0]):
+                slot = n + n_act + rank
+                assert g1.kind[slot] == md.KIND_ELECTRON and g1.z[slot] == -1
+                np.testing.assert_allclose(g1.x[slot] - g0.x[i], off_ref[i], atol=1e-12)
+            assert not np.any(g1.z[:n] > zmax)
+            fired_high += int(np.sum(fired_ref.astype(bool) & (g0.z[:n] >= 8)))
+            assert np.all(info["prob"][g0.z[:n] >= zmax] == 0.0)
+    assert fired_high > 20

@@ -69,7 +69,7 @@ def test_adk_structure():
 
 
 @pytest.mark.parametrize("P,T,q", [(15.76, 5.0, 6), (15.76, 40.0, 6), (143.46, 30.0, 1),
-                                   (59.58, 200.0, 3)])
+                                   (59.58, 200.0, 3), (179.84, 150.0, 10), (374.0, 900.0, 3)])
 def test_lotz_rate_is_maxwell_average_of_cross_section(P, T, q):
     """<sigma v> of the Lotz cross section sigma = a q ln(E/P)/(E P) over a
     Maxwellian, integrated numerically in SI units, equals the closed form."""
@@ -85,6 +85,34 @@ def test_lotz_rate_is_maxwell_average_of_cross_section(P, T, q):
     val, _ = integrate.quad(integrand, Pj, Pj + 60 * Tj, limit=400, epsabs=0, epsrel=1e-11)
     assert oracle.lotz_rate_cgs(P, T, q) == pytest.approx(val * 1e6, rel=1e-8)  # m^3 -> cm^3
     assert oracle.lotz_rate_cgs(P, 0.0, q) == 0.0
+
+
+@pytest.mark.parametrize("species", [synth.ARGON, synth.XENON], ids=["Ar", "Xe"])
+def test_species_tables_follow_the_shell_structure(species):
+    """The ionization energies rise with the charge state; the outer-subshell
+    occupation counts down by one per ionization and restarts at a full
+    inner subshell (Ar: 3p^6, 3s^2; Xe: 5p^6, 5s^2, 4d^10)."""
+    ip, q = np.array(species["ip_ev"]), np.array(species["q_outer"])
+    assert ip.size == q.size and np.all(np.diff(ip) > 0)
+    shells = {"Ar": [6, 2], "Xe": [6, 2, 10]}[species["name"]]
+    expect = np.concatenate([np.arange(s, 0, -1) for s in shells])[:q.size]
+    assert np.array_equal(q, expect)
+
+
+@pytest.mark.parametrize("z", [0, 7, 8, 9, 15])
+def test_rate_total_indexes_the_xenon_table(z):
+    """Xe at 790 nm: the rate of Xe^z uses I_p(z), the residual charge z + 1
+    and the outer-subshell count q(z) of the table, for every charge state
+    up to 15 (ADK and Lotz pinned on their own above)."""
+    XE, lam = synth.XENON, 0.79
+    omega = 2 * math.pi * sc.c / (lam * 1e-6)
+    amag, ne, te = 0.3, 5e22, 400.0
+    F = amag * sc.m_e * sc.c * omega / sc.e / sc.physical_constants["atomic unit of electric field"][0]
+    ip = XE["ip_ev"][z] / sc.physical_constants["Hartree energy in eV"][0]
+    t_au = sc.physical_constants["atomic unit of time"][0]
+    nu = (oracle.adk_rate_au(F, ip, z + 1.0) / t_au
+          + ne * oracle.lotz_rate_cgs(XE["ip_ev"][z], te, XE["q_outer"][z])) / omega
+    assert oracle.rate_total(amag, z, ne, te, XE, lambda_um=lam) == pytest.approx(nu, rel=1e-8)
 
 
 def test_rate_total_units():
