@@ -46,6 +46,13 @@ cudaError_t launch_wait_selftest(long long budget, int* err, cudaStream_t s);
 // Ionization pass of one cluster: field + local moments, then the decision.
 cudaError_t launch_ion_pass(const IonArgs& a, cudaStream_t s);
 
+// Push of the first n_push ion records of cluster ci with the field the
+// ionization pass left in e_ion (clusters with a pass before every step; the
+// step kernel's units skip their i-blocks).  Launched after the pass and
+// before the step kernel.
+cudaError_t launch_ion_push(const StepArgs& a, int ci, const double* e_ion, long long n_push,
+                            bool det, cudaStream_t s);
+
 // Shape of the field + moments kernel: ion targets per CTA and resident CTAs
 // per SM (for the choice of the source split).
 int ion_field_targets_per_cta();

@@ -335,6 +335,11 @@ __global__ void __launch_bounds__(256) k_ion_inputs(const IonArgs a) {
     S[2] += sc[6] + sc[3] * d2;
     W += sc[3];
   }
+  if (a.e_ion) {
+    a.e_ion[3 * t + 0] = fx;
+    a.e_ion[3 * t + 1] = fy;
+    a.e_ion[3 * t + 2] = fz;
+  }
   const double tn = a.c.t0 + static_cast<double>(step) * a.c.dt;
   double lay;
   const double lax = laser_ax(a.c, tn, &lay);
@@ -471,8 +476,12 @@ __global__ void __launch_bounds__(256) k_ion_apply(const IonArgs a) {
     // the upload check guarantees a free slot for every possible ionization
     if (MD_IN_RANGE(a.err, slot, a.ion.slot_base,
                     a.ion.slot_base + static_cast<long long>(a.ion.zmax) * a.ion.n_ions) &&
-        MD_IN_RANGE(a.err, slot, 0, a.c.n))
+        MD_IN_RANGE(a.err, slot, 0, a.c.n)) {
       apply_one(a, step, t, slot);
+      // ions fired in this pass, in slot order (the charge changes of k_ion_fix)
+      if (a.fired_list && MD_IN_RANGE(a.err, slot - *a.pass_slot, 0, a.ion.n_ions))
+        a.fired_list[slot - *a.pass_slot] = static_cast<int>(t);
+    }
   }
   if (blockIdx.x == gridDim.x - 1 && tid == 0) {
     const long long next = s_base + total;
@@ -483,6 +492,83 @@ __global__ void __launch_bounds__(256) k_ion_apply(const IonArgs a) {
       a.cl_dev->seg_len = live_seg_len(a.cl_dev->n_pad, a.cl_dev->nseg,
                                        next > a.ion.slot_base ? next : a.ion.slot_base);
   }
+}
+
+// Field at the ions after the pass's charge changes, for the step (clusters
+// with a pass before every step).  The pass summed the field with the charges
+// before its decisions; each ion j it fired gained one charge (kc w_j) at x_j
+// and freed an electron (charge -kc w_j) at x_e.  By superposition the field
+// the step would sum at ion t is e_ion[t] + sum over the fired of
+// dQ (x_t - x_s) / (|x_t - x_s|^2 + eps^2)^{3/2}, summed here in FP32 with a
+// Kahan fold per chunk of kFixChunk fired ions.
+constexpr int kFixThreads = 256;
+constexpr int kFixChunk = 256;
+
+__global__ void __launch_bounds__(kFixThreads) k_ion_fix(const IonArgs a) {
+  __shared__ float4 s_src[2 * kFixChunk];
+  const long long step = __ldcg(a.step);
+  if (!pass_active(a, step)) return;
+  const long long base = __ldcg(a.pass_slot);
+  const long long nf = __ldcg(a.next_slot) - base;
+  if (nf <= 0) return;
+  const float4* __restrict__ cur = (step & 1) ? a.posq1 : a.posq0;
+  const long long t = static_cast<long long>(blockIdx.x) * kFixThreads + threadIdx.x;
+  const float4 pt = (t < a.ion.n_ions) ? cur[a.c.off + t] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float xi[1] = {pt.x}, yi[1] = {pt.y}, zi[1] = {pt.z};
+  Acc<1, false> acc;
+  acc.zero();
+  const float kc = static_cast<float>(a.ion.kc);
+  for (long long k0 = 0; k0 < nf; k0 += kFixChunk) {
+    const int cnt = static_cast<int>(nf - k0 < kFixChunk ? nf - k0 : kFixChunk);
+    __syncthreads();
+    if (threadIdx.x < cnt) {
+      const long long k = k0 + threadIdx.x;
+      const int j = a.fired_list[k];
+      float4 pj = make_float4(0.f, 0.f, 0.f, 0.f), pe = pj;
+      if (MD_IN_RANGE(a.err, j, 0, a.ion.n_ions) &&
+          MD_IN_RANGE(a.err, base + k, 0, a.c.n)) {
+        pj = cur[a.c.off + j];
+        pj.w = kc * static_cast<float>(a.w[a.c.off + j]);
+        pe = cur[a.c.off + base + k];
+      }
+      s_src[threadIdx.x] = pj;
+      s_src[kFixChunk + threadIdx.x] = pe;
+    }
+    __syncthreads();
+    for (int q = 0; q < cnt; ++q) {
+      pair<1, false>(s_src[q], xi, yi, zi, a.c.eps2, acc);
+      pair<1, false>(s_src[kFixChunk + q], xi, yi, zi, a.c.eps2, acc);
+    }
+    fold<1, false>(acc);
+  }
+  if (t >= a.ion.n_ions) return;
+  a.e_ion[3 * t + 0] -= static_cast<double>(acc.sx[0]) - acc.cx[0];
+  a.e_ion[3 * t + 1] -= static_cast<double>(acc.sy[0]) - acc.cy[0];
+  a.e_ion[3 * t + 2] -= static_cast<double>(acc.sz[0]) - acc.cz[0];
+}
+
+// Push of the first n_push ion records of cluster ci with the field of the
+// pass (e_ion) instead of a direct sum: the step kernel's units skip the
+// i-blocks that hold only these ions.  Runs after the pass and before the
+// step kernel, which advances the step counter.
+template <bool DET>
+__global__ void __launch_bounds__(256) k_push_ions(const StepArgs a, int ci, const double* e_ion,
+                                                  long long n_push) {
+  __shared__ ClusterDev s_c;
+  __shared__ float s_las[6];
+  const long long step = __ldcg(a.step);
+  if (threadIdx.x == 0) {
+    s_c = a.cl[ci];
+    laser_field(s_c, s_c.t0 + static_cast<double>(step) * s_c.dt, s_las);
+  }
+  __syncthreads();
+  const long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= n_push) return;
+  const float4* __restrict__ cur = (step & 1) ? a.posq1 : a.posq0;
+  float4* __restrict__ nxt = (step & 1) ? a.posq0 : a.posq1;
+  const double t_next = s_c.t0 + static_cast<double>(step + 1) * s_c.dt;
+  push_record<DET>(a, s_c, s_c.off + t, e_ion[3 * t + 0], e_ion[3 * t + 1], e_ion[3 * t + 2],
+                   s_las, t_next, cur, nxt);
 }
 
 // Liveness flags from the current records: a group of kLiveGroup records is
@@ -545,6 +631,23 @@ cudaError_t launch_ion_pass(const IonArgs& a, cudaStream_t s) {
   k_ion_decide<<<g2, 256, 0, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_ion_apply<<<g2, 256, 0, s>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (a.e_ion && a.fired_list) {
+    k_ion_fix<<<static_cast<unsigned>((a.ion.n_ions + kFixThreads - 1) / kFixThreads), kFixThreads,
+                0, s>>>(a);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+cudaError_t launch_ion_push(const StepArgs& a, int ci, const double* e_ion, long long n_push,
+                            bool det, cudaStream_t s) {
+  if (n_push <= 0) return cudaSuccess;
+  const unsigned g = static_cast<unsigned>((n_push + 255) / 256);
+  if (det)
+    k_push_ions<true><<<g, 256, 0, s>>>(a, ci, e_ion, n_push);
+  else
+    k_push_ions<false><<<g, 256, 0, s>>>(a, ci, e_ion, n_push);
   return cudaGetLastError();
 }
 

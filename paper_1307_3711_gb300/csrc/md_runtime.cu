@@ -117,6 +117,11 @@ struct md_ctx {
   double* d_ion_out = nullptr;         // [sum n_ions][4]
   unsigned char* d_ion_fired = nullptr;
   double* d_ion_nu = nullptr;          // [sum n_ions] surrogate rates (-1: plain)
+  // clusters with a pass before every step: the field at each ion after the
+  // pass (the step pushes those ions with it) and the ions fired per pass
+  double* d_ion_e = nullptr;           // [sum n_ions][3]
+  int* d_ion_list = nullptr;           // [sum n_ions]
+  std::vector<long long> ion_push;     // per cluster: ion records pushed with d_ion_e
   unsigned char* d_src_live = nullptr; // liveness flags per kLiveGroup records
   unsigned char* d_tgt_live = nullptr;
   float4* d_vel = nullptr;             // FP32 (ux, uy, uz, w) per record
@@ -288,6 +293,14 @@ md::StepArgs step_args(md_ctx* c) {
   return a;
 }
 
+// A cluster whose ionization pass runs before every step: the pass's field at
+// its ions (corrected for the pass's own charge changes) is the step's field
+// there, so the step pushes those ions with it instead of summing again.
+bool ions_fused(const md_ctx* c, int ci) {
+  const md::IonDev& io = c->ion[ci];
+  return c->d_ion_e && io.rate_model != 0 && io.ionize_every == 1 && io.n_ions > 0;
+}
+
 // Segments per i-block for a requested split S: each segment holds at least
 // one shared-memory tile of sources.
 void segments_for(const md::ClusterDev& cl, int S, int tile, int* nseg, int* seg_len) {
@@ -306,7 +319,8 @@ long long units_for(const md_ctx* c, long long per, int S, int tile) {
     segments_for(cl, S, tile, &ns, &len);
     // i-blocks past the live records finish at once: count the live ones
     const long long live = ci < static_cast<int>(c->live_host.size()) ? c->live_host[ci] : cl.n_pad;
-    u += (std::max(1LL, live) + per - 1) / per * ns;
+    const long long skip = ions_fused(c, ci) ? c->ion[ci].n_ions / per : 0;
+    u += std::max(1LL, (std::max(1LL, live) + per - 1) / per - skip) * ns;
   }
   return u;
 }
@@ -357,11 +371,17 @@ md_status configure(md_ctx* c, int cfg, int ctas_per_sm, int jsplit) {
     segments_for(cl, S, k.tile, &cl.nseg, &cl.seg_len);
     max_seg = std::max(max_seg, cl.nseg);
     const long long nb = (cl.n_pad + per - 1) / per;
-    for (long long b = 0; b < nb; ++b, ++ib)
+    // a cluster with a pass before every step: the i-blocks holding only ions
+    // are pushed with the pass's field (launch_ion_push), not summed again
+    const long long skip = ions_fused(c, ci) ? c->ion[ci].n_ions / per : 0;
+    c->ion_push[ci] = skip * per;
+    for (long long b = 0; b < nb; ++b, ++ib) {
+      if (b < skip) continue;
       for (int sg = 0; sg < cl.nseg; ++sg) {
         const long long len = std::min<long long>(cl.seg_len, cl.n_pad - static_cast<long long>(sg) * cl.seg_len);
         work.push_back({per * len, {ci, static_cast<int>(b), sg, ib}});
       }
+    }
   }
   std::stable_sort(work.begin(), work.end(),
                    [](const Work& a, const Work& b) { return a.cost > b.cost; });
@@ -502,6 +522,8 @@ md::IonArgs ion_args(md_ctx* c, int ci, int force) {
   a.vel = c->d_vel;
   a.next_slot = c->d_ion_next + ci;
   a.cl_dev = c->d_cl + ci;
+  a.e_ion = ions_fused(c, ci) ? c->d_ion_e + 3 * c->ion_out_off[ci] : nullptr;
+  a.fired_list = ions_fused(c, ci) ? c->d_ion_list + c->ion_out_off[ci] : nullptr;
   return a;
 }
 
@@ -517,6 +539,18 @@ cudaError_t launch_ion_all(md_ctx* c, int force, cudaStream_t s) {
   return cudaSuccess;
 }
 
+// Pushes of the ions whose field the pass left (ions_fused), before the step
+// kernel of the same step.
+cudaError_t launch_ion_pushes(md_ctx* c, const md::StepArgs& a, cudaStream_t s) {
+  for (int ci = 0; ci < c->n_clusters; ++ci) {
+    if (!ions_fused(c, ci) || c->ion_push[ci] <= 0) continue;
+    cudaError_t e = md::launch_ion_push(a, ci, c->d_ion_e + 3 * c->ion_out_off[ci],
+                                        c->ion_push[ci], c->det_on, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 md_status launch_steps_direct(md_ctx* c, int n) {
   int ncfg = 0;
   const md::KernelConfig* cfgs = md::step_configs(&ncfg);
@@ -524,6 +558,7 @@ md_status launch_steps_direct(md_ctx* c, int n) {
   for (int s = 0; s < n; ++s) {
     if (c->any_ion) {
       cudaError_t e = launch_ion_all(c, 0, c->stream);
+      if (e == cudaSuccess) e = launch_ion_pushes(c, a, c->stream);
       if (e != cudaSuccess) return cuda_fail(e, "ionization launch");
     }
     cudaError_t e = c->det_on ? cfgs[c->cfg].launch_step_det(a, c->grid, c->stream)
@@ -544,6 +579,7 @@ md_status build_graph(md_ctx* c) {
     const md::StepArgs a = step_args(c);
     for (int s = 0; s < kGraphSteps && e == cudaSuccess; ++s) {
       if (c->any_ion) e = launch_ion_all(c, 0, cs);
+      if (c->any_ion && e == cudaSuccess) e = launch_ion_pushes(c, a, cs);
       if (e == cudaSuccess)
         e = c->det_on ? cfgs[c->cfg].launch_step_det(a, c->grid, cs)
                       : cfgs[c->cfg].launch_step(a, c->grid, cs);
@@ -592,6 +628,8 @@ void free_ctx(md_ctx* c) {
   cudaFree(c->d_ion_out);
   cudaFree(c->d_ion_fired);
   cudaFree(c->d_ion_nu);
+  cudaFree(c->d_ion_e);
+  cudaFree(c->d_ion_list);
   cudaFree(c->d_src_live);
   cudaFree(c->d_tgt_live);
   cudaFree(c->d_vel);
@@ -815,6 +853,7 @@ md_status md_init(md_ctx** out, const md_config* cfgs, int32_t n_clusters,
     }
     c->ion_out_off.push_back(c->ion.empty() ? 0 : c->ion_out_off.back() + c->ion.back().n_ions);
     c->ion.push_back(io);
+    c->ion_push.push_back(0);
     if (f.rate_model) c->any_ion = true;
     off += d.n_pad;
     c->max_n = std::max<long long>(c->max_n, parts[i].n);
@@ -862,7 +901,9 @@ md_status md_init(md_ctx** out, const md_config* cfgs, int32_t n_clusters,
         dev_alloc(&c->d_ion_pass, static_cast<size_t>(n_clusters)) != cudaSuccess ||
         dev_alloc(&c->d_ion_out, 4 * static_cast<size_t>(sum_ion)) != cudaSuccess ||
         dev_alloc(&c->d_ion_fired, static_cast<size_t>(sum_ion)) != cudaSuccess ||
-        dev_alloc(&c->d_ion_nu, static_cast<size_t>(sum_ion)) != cudaSuccess)
+        dev_alloc(&c->d_ion_nu, static_cast<size_t>(sum_ion)) != cudaSuccess ||
+        dev_alloc(&c->d_ion_e, 3 * static_cast<size_t>(sum_ion)) != cudaSuccess ||
+        dev_alloc(&c->d_ion_list, static_cast<size_t>(sum_ion)) != cudaSuccess)
       return bail(fail(MD_ERR_OOM, "ionization buffers"));
     const size_t groups = static_cast<size_t>((c->n_total + md::kLiveGroup - 1) / md::kLiveGroup);
     if (dev_alloc(&c->d_src_live, groups) != cudaSuccess ||

@@ -139,6 +139,12 @@ struct IonArgs {
   // this cluster's descriptor on the device: the pass that moves next_slot
   // also resets its seg_len to the split of the live records (live_seg_len)
   ClusterDev* cl_dev;
+  // clusters with a pass before every step (nullptr otherwise): the Coulomb
+  // field at each ion after the pass's charge changes, [n_ions][3], which the
+  // step uses for the ions instead of summing their field again, and the ions
+  // fired in this pass in slot order, [n_ions]
+  double* e_ion;
+  int* fired_list;
 };
 
 struct FieldArgs {

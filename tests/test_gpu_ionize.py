@@ -410,3 +410,82 @@ def test_xenon_charge_states_up_to_15_follow_oracle(md):
             fired_high += int(np.sum(fired_ref.astype(bool) & (g0.z[:n] >= 8)))
             assert np.all(info["prob"][g0.z[:n] >= zmax] == 0.0)
     assert fired_high > 20
+
+
+def test_ions_pushed_with_the_pass_field_follow_oracle(md):
+    """With a pass before every step, the step pushes the ions with the field
+    the pass summed, corrected by superposition for the pass's own charge
+    changes (each fired ion's extra charge and its freed electron), instead
+    of summing their field again; only i-blocks that mix ions and electrons
+    are summed by the step kernel.  The kick and drift of every active record,
+    ions of both kinds included, are the FP64 oracle's on the state the pass
+    left."""
+    n = 2000
+    lam = 0.806
+    c = synth.make_cluster(5, n, 0, synth.nm_to_len(8.0 * (n / 200000) ** (1 / 3), lam), 0,
+                           AR["mass"], n_electron_slots=8 * n)
+    rw = synth.nm_to_len(AR["r_w_nm"], lam)
+    tau = synth.sin2_length_from_fwhm(synth.fs_to_time(100.0, lam))
+    t0 = np.floor(tau / 2 / np.pi) * np.pi + 0.5 * np.pi - 0.3
+    eps = synth.nm_to_len(0.1, lam)
+    kw = dict(a0=0.0617, tau=tau, t0=t0, dt=0.02, softening=eps, envelope=synth.ENV_SIN2,
+              lambda_um=lam, rate_model=1, ionize_every=1, zmax=8, n_ions=n, slot_base=n,
+              seed=13, r_loc=3 * rw, r_create=rw, species=AR)
+    p = oracle.make_params(a0=kw["a0"], tau=tau, t0=t0, dt=kw["dt"], eps=eps,
+                           env=synth.ENV_SIN2, lambda_um=lam)
+    kc = oracle.coulomb_constant(lam)
+    checked = 0
+    with md.Context([md.make_config(**kw)], [md.HostParticles.from_cluster(c)]) as ctx:
+        ctx.set_tuning(128, 4, 512, 0, 2, 0)   # 3 ion-only i-blocks of 512, one mixed
+        ctx.step(2)
+        for k in range(3):
+            g0 = ctx.get_particles(0)
+            step = ctx.step_index()
+            st = oracle.State(g0.x, g0.u, g0.z, g0.mass, g0.w, (g0.kind != md.KIND_INACTIVE)
+                              .astype(np.uint8), step=step)
+            fired_ref, _, _, _ = oracle.ionize_pass(
+                st, p, AR, n, n, 8, kw["seed"], kw["dt"], kw["r_loc"], kw["r_create"], lam,
+                nthreads=os.cpu_count() or 1)
+            ctx.step(1)
+            info = ctx.ionization(0)
+            g1 = ctx.get_particles(0)
+            if not np.array_equal(info["fired"], fired_ref):
+                continue               # a borderline draw: the states differ from here
+            act = np.flatnonzero(st.active)
+            e64 = oracle.coulomb_field(st.x[act], st.x, st.q(), eps, kc, self_idx=act,
+                                       nthreads=os.cpu_count() or 1)
+            a, b = oracle.laser_fields(t0 + step * kw["dt"], kw["a0"], 0, synth.ENV_SIN2, tau)
+            du_ref, dx_ref, du_las = [], [], []
+            for m, i in enumerate(act):
+                qm = st.z[i] / st.mass[i]
+                u1 = oracle.boris_kick(st.u[i], e64[m] + a, b, qm, kw["dt"])
+                du_ref.append(u1 - st.u[i])
+                dx_ref.append(oracle.drift(st.x[i], u1, kw["dt"]) - st.x[i])
+                du_las.append(oracle.boris_kick(st.u[i], a, b, qm, kw["dt"]) - st.u[i])
+            du_ref, dx_ref, du_las = np.array(du_ref), np.array(dx_ref), np.array(du_las)
+            err_u = force_error(g1.u[act] - st.u[act], du_ref)
+            err_x = force_error(g1.x[act] - st.x[act], dx_ref)
+            ions = act < n
+            # the ions' kick is mostly the laser's: measure their error against
+            # the Coulomb part of the kick, where the pass's field and its
+            # charge-change correction enter (a fired ion's own freed electron
+            # alone is ~10 % of it)
+            du_c = du_ref[ions] - du_las[ions]
+            err_c = force_error((g1.u[act] - st.u[act])[ions] - du_las[ions], du_c)
+            print(k, "fired", int(fired_ref.sum()), "ions vs Coulomb kick", summary(err_c),
+                  "all", summary(err_u), "drift", summary(err_x))
+            # a push with the pass's field left uncorrected would be this far off
+            q0 = np.where(g0.kind != md.KIND_INACTIVE, g0.w * g0.z, 0.0)
+            ion_idx = act[ions]
+            e_pre = oracle.coulomb_field(g0.x[ion_idx], g0.x, q0, eps, kc, self_idx=ion_idx,
+                                         nthreads=os.cpu_count() or 1)
+            du_pre = np.array([oracle.boris_kick(st.u[i], e_pre[m] + a, b, st.z[i] / st.mass[i],
+                                                 kw["dt"]) - st.u[i]
+                               for m, i in enumerate(ion_idx)])
+            err_pre = force_error(du_pre - du_las[ions], du_c)
+            assert int(fired_ref.sum()) > 0
+            assert summary(err_pre)["p99"] > 1e-3, summary(err_pre)
+            assert summary(err_c)["p99"] <= 1e-4 and summary(err_u)["p99"] <= 2e-5, k
+            assert summary(err_x)["p99"] <= 2e-5, k
+            checked += 1
+    assert checked >= 2
