@@ -188,8 +188,13 @@ md_status md_diagnostics(md_ctx *ctx, int32_t cluster, md_diag *out);
 
 /* md_get_particles / md_set_particles: copy cluster `cluster`'s records to /
  * from host arrays (n must equal the cluster's record count).  get is
- * synchronous; set is asynchronous with respect to the caller's later calls
- * but reads the host arrays before it returns (staged through pinned memory). */
+ * synchronous; set reads the host arrays before it returns (page-locked
+ * arrays are copied directly, others staged through pinned memory).
+ * set checks every record as md_init does (kind, positive mass if active,
+ * charge sign of the kind, finite x, u, w): MD_ERR_ARG names the first bad
+ * record and the state is left unchanged.  For a cluster without ionization
+ * the checks run on the GPU on the copied block; with ionization they run
+ * on the host, with the electron-slot capacity check. */
 md_status md_get_particles(md_ctx *ctx, int32_t cluster, md_particles *out);
 md_status md_set_particles(md_ctx *ctx, int32_t cluster, const md_particles *in);
 

@@ -38,6 +38,8 @@ cudaError_t launch_diag(const DiagArgs& a, int blocks, DiagPartial* out, cudaStr
 // fma.rn.f32, or packed fma.rn.f32x2 doing two lanes per instruction).
 cudaError_t launch_ffma_probe(int blocks, int iters, bool packed, float* sink, cudaStream_t s);
 
+// Staged records -> state.  With a.first_bad set, k_validate checks every
+// record first and a rejected block is not applied.
 cudaError_t launch_upload(const UploadArgs& a, cudaStream_t s);
 
 // Launches one CTA whose mbarrier wait can never complete (bounded by budget).

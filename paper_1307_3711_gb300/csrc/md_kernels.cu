@@ -36,9 +36,27 @@ __global__ void k_diag_final(const DiagPartial* __restrict__ part, int nblocks,
 // device state of one cluster starting at record `off`; writes the current
 // j-stream entry (x, y, z, K_C w z).
 
+// The checks md_set_particles makes of every record, on the staged copy in
+// device memory: kind in range, positive mass if active, charge sign matching
+// the kind, finite x, u and w.  Records the lowest index that fails.
+__global__ void k_validate(const UploadArgs a) {
+  const long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= a.n) return;
+  const unsigned char kd = a.hkind[k];
+  const int zq = a.hz[k];
+  bool bad = kd > 2;
+  bad = bad || (kd != 2 && !(a.hmass[k] > 0.0));
+  bad = bad || (kd == 1 && zq >= 0) || (kd == 0 && zq < 0);
+  bad = bad || !(isfinite(a.hx[3 * k]) && isfinite(a.hx[3 * k + 1]) && isfinite(a.hx[3 * k + 2]) &&
+                 isfinite(a.hu[3 * k]) && isfinite(a.hu[3 * k + 1]) && isfinite(a.hu[3 * k + 2]) &&
+                 isfinite(a.hw[k]));
+  if (bad) atomicMin(a.first_bad, static_cast<unsigned long long>(k));
+}
+
 __global__ void k_upload(const UploadArgs a) {
   const long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k >= a.n) return;
+  if (a.first_bad && *a.first_bad != kNoBadRecord) return;  // rejected: state unchanged
   const long long i = a.off + k;
   const unsigned char kd = a.hkind[k];
   const double X = a.hx[3 * k], Y = a.hx[3 * k + 1], Z = a.hx[3 * k + 2];
@@ -304,6 +322,12 @@ cudaError_t launch_wait_selftest(long long budget, int* err, cudaStream_t s) {
 cudaError_t launch_upload(const UploadArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
   const unsigned grid = static_cast<unsigned>((a.n + 255) / 256);
+  if (a.first_bad) {
+    cudaError_t e = cudaMemsetAsync(a.first_bad, 0xff, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    k_validate<<<grid, 256, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   k_upload<<<grid, 256, 0, s>>>(a);
   return cudaGetLastError();
 }

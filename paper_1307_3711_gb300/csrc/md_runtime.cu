@@ -91,6 +91,9 @@ struct md_ctx {
   unsigned char* h_raw = nullptr;
   size_t raw_bytes = 0;
   md::DiagPartial* h_diag = nullptr;
+  // first record the device rejected in md_set_particles (kNoBadRecord: none)
+  unsigned long long* d_first_bad = nullptr;
+  unsigned long long* h_first_bad = nullptr;
 
   // kernel configuration
   int cfg = -1;
@@ -229,7 +232,27 @@ md_status validate_ionization(const md_config& c, const md_particles& p, int idx
   return MD_OK;
 }
 
-md_status validate_particles(const md_particles& p, int idx, long long expect_n) {
+// The checks of one record (kind, mass, charge sign, finite x, u and w).
+md_status check_record(const md_particles& p, int idx, long long i) {
+  const int kd = p.kind ? p.kind[i] : (p.z[i] < 0 ? MD_KIND_ELECTRON : MD_KIND_ION);
+  if (kd < 0 || kd > 2) return fail(MD_ERR_ARG, "cluster %d: record %lld: bad kind", idx, i);
+  if (kd != MD_KIND_INACTIVE && !(p.mass[i] > 0.0))
+    return fail(MD_ERR_ARG, "cluster %d: record %lld: mass must be > 0", idx, i);
+  if (kd == MD_KIND_ELECTRON && p.z[i] >= 0)
+    return fail(MD_ERR_ARG, "cluster %d: record %lld: electron with z >= 0", idx, i);
+  if (kd == MD_KIND_ION && p.z[i] < 0)
+    return fail(MD_ERR_ARG, "cluster %d: record %lld: ion with z < 0", idx, i);
+  if (!(std::isfinite(p.x[3 * i]) && std::isfinite(p.x[3 * i + 1]) &&
+        std::isfinite(p.x[3 * i + 2]) && std::isfinite(p.u[3 * i]) &&
+        std::isfinite(p.u[3 * i + 1]) && std::isfinite(p.u[3 * i + 2]) &&
+        std::isfinite(p.w[i])))
+    return fail(MD_ERR_ARG, "cluster %d: record %lld: non-finite position, momentum or weight",
+                idx, i);
+  return MD_OK;
+}
+
+// Size and pointers of a particle block.
+md_status check_block(const md_particles& p, int idx, long long expect_n) {
   if (p.n < 1) return fail(MD_ERR_ARG, "cluster %d: n must be >= 1", idx);
   if (expect_n >= 0 && p.n != expect_n)
     return fail(MD_ERR_ARG, "cluster %d: n = %lld, context holds %lld", idx, (long long)p.n,
@@ -237,22 +260,14 @@ md_status validate_particles(const md_particles& p, int idx, long long expect_n)
   if (p.n > (1LL << 30)) return fail(MD_ERR_ARG, "cluster %d: n too large", idx);
   if (!p.x || !p.u || !p.z || !p.mass || !p.w)
     return fail(MD_ERR_ARG, "cluster %d: x, u, z, mass and w are required", idx);
-  for (long long i = 0; i < p.n; ++i) {
-    const int kd = p.kind ? p.kind[i] : (p.z[i] < 0 ? MD_KIND_ELECTRON : MD_KIND_ION);
-    if (kd < 0 || kd > 2) return fail(MD_ERR_ARG, "cluster %d: record %lld: bad kind", idx, i);
-    if (kd != MD_KIND_INACTIVE && !(p.mass[i] > 0.0))
-      return fail(MD_ERR_ARG, "cluster %d: record %lld: mass must be > 0", idx, i);
-    if (kd == MD_KIND_ELECTRON && p.z[i] >= 0)
-      return fail(MD_ERR_ARG, "cluster %d: record %lld: electron with z >= 0", idx, i);
-    if (kd == MD_KIND_ION && p.z[i] < 0)
-      return fail(MD_ERR_ARG, "cluster %d: record %lld: ion with z < 0", idx, i);
-    if (!(std::isfinite(p.x[3 * i]) && std::isfinite(p.x[3 * i + 1]) &&
-          std::isfinite(p.x[3 * i + 2]) && std::isfinite(p.u[3 * i]) &&
-          std::isfinite(p.u[3 * i + 1]) && std::isfinite(p.u[3 * i + 2]) &&
-          std::isfinite(p.w[i])))
-      return fail(MD_ERR_ARG, "cluster %d: record %lld: non-finite position, momentum or weight",
-                  idx, i);
-  }
+  return MD_OK;
+}
+
+md_status validate_particles(const md_particles& p, int idx, long long expect_n) {
+  md_status st = check_block(p, idx, expect_n);
+  if (st != MD_OK) return st;
+  for (long long i = 0; i < p.n; ++i)
+    if ((st = check_record(p, idx, i)) != MD_OK) return st;
   return MD_OK;
 }
 
@@ -426,7 +441,7 @@ md_status configure(md_ctx* c, int cfg, int ctas_per_sm, int jsplit) {
   return MD_OK;
 }
 
-// Default before autotuning: 128 threads x 8 i-particles per thread, packed.
+// Default before autotuning: 128 threads x 4 i-particles per thread, scalar.
 int default_config(md_ctx* c) {
   (void)c;
   int ncfg = 0;
@@ -639,11 +654,17 @@ void free_ctx(md_ctx* c) {
   cudaFree(c->d_mlp);
   if (c->h_raw) cudaFreeHost(c->h_raw);
   if (c->h_diag) cudaFreeHost(c->h_diag);
+  cudaFree(c->d_first_bad);
+  if (c->h_first_bad) cudaFreeHost(c->h_first_bad);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
 
-md_status upload_cluster(md_ctx* c, int ci, const md_particles& p) {
+// Records of cluster ci from the caller's host arrays.  device_check: the
+// records have not been checked on the host; k_validate checks the staged
+// copy and a rejected block is not applied (clusters without ionization,
+// whose upload has no other effect on the state).
+md_status upload_cluster(md_ctx* c, int ci, const md_particles& p, bool device_check = false) {
   const long long n = p.n;
   long long next_slot = 0;
   if (c->d_ion_next && c->ion[ci].rate_model) {
@@ -711,7 +732,11 @@ md_status upload_cluster(md_ctx* c, int ci, const md_particles& p) {
   a.kind = c->d_kind;
   a.step = c->d_step;
   a.vel = c->d_vel;
+  a.first_bad = device_check ? c->d_first_bad : nullptr;
   MD_CUDA(md::launch_upload(a, c->stream));
+  if (device_check)
+    MD_CUDA(cudaMemcpyAsync(c->h_first_bad, c->d_first_bad, sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, c->stream));
   if (c->d_ion_next && c->ion[ci].rate_model)
     MD_CUDA(cudaMemcpyAsync(c->d_ion_next + ci, &next_slot, sizeof(long long),
                             cudaMemcpyHostToDevice, c->stream));
@@ -731,6 +756,12 @@ md_status upload_cluster(md_ctx* c, int ci, const md_particles& p) {
                                  c->d_src_live, c->d_tgt_live, c->stream));
   // the pinned staging buffer is reused by the next call: wait for the copy
   MD_CUDA(cudaStreamSynchronize(c->stream));
+  if (device_check && *c->h_first_bad != md::kNoBadRecord) {
+    // the message of the host check, for the first record the device rejected
+    const md_status st = check_record(p, ci, static_cast<long long>(*c->h_first_bad));
+    return st != MD_OK ? st : fail(MD_ERR_ARG, "cluster %d: record %llu rejected", ci,
+                                   *c->h_first_bad);
+  }
   return MD_OK;
 }
 
@@ -889,6 +920,10 @@ md_status md_init(md_ctx** out, const md_config* cfgs, int32_t n_clusters,
   if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
   e = cudaMallocHost(reinterpret_cast<void**>(&c->h_raw), c->raw_bytes);
   if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMallocHost"));
+  if (dev_alloc(&c->d_first_bad, 1) != cudaSuccess ||
+      cudaMallocHost(reinterpret_cast<void**>(&c->h_first_bad), sizeof(unsigned long long)) !=
+          cudaSuccess)
+    return bail(fail(MD_ERR_OOM, "upload check buffers"));
   if (c->any_ion) {
     long long max_ion = 0, sum_ion = 0;
     for (auto& io : c->ion) {
@@ -1312,6 +1347,12 @@ md_status md_get_particles(md_ctx* c, int32_t cluster, md_particles* out) {
 md_status md_set_particles(md_ctx* c, int32_t cluster, const md_particles* in) {
   if (!c || !in) return fail(MD_ERR_ARG, "NULL argument");
   if (cluster < 0 || cluster >= c->n_clusters) return fail(MD_ERR_ARG, "bad cluster index");
+  if (!c->ion[cluster].rate_model) {
+    // the per-record checks run on the staged copy in device memory
+    md_status st = check_block(*in, cluster, c->cl[cluster].n);
+    if (st != MD_OK) return st;
+    return upload_cluster(c, cluster, *in, true);
+  }
   md_status st = validate_particles(*in, cluster, c->cl[cluster].n);
   if (st != MD_OK) return st;
   return upload_cluster(c, cluster, *in);

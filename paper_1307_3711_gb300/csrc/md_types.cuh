@@ -216,7 +216,13 @@ struct UploadArgs {
   unsigned char* kind;
   const long long* step;
   float4* vel;        // FP32 (ux, uy, uz, w) or nullptr
+  // index of the first record k_validate rejected (kNoBadRecord: none), or
+  // nullptr: the records were checked on the host.  A rejected block is not
+  // applied.
+  unsigned long long* first_bad;
 };
+
+constexpr unsigned long long kNoBadRecord = ~0ull;
 
 struct DownloadArgs {
   double* hx;

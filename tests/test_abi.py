@@ -93,6 +93,17 @@ def test_init_rejects_inconsistent_particles(md):
     assert "non-finite" in str(ei.value)
 
 
+def test_init_rejects_an_empty_cluster(md):
+    """A cluster of no records is an argument error, found on the host."""
+    cfg = md.make_config()
+    p = md.HostParticles(np.zeros((0, 3)), np.zeros((0, 3)), np.zeros(0, np.int32),
+                         np.zeros(0), np.zeros(0))
+    with pytest.raises(md.MDError) as ei:
+        md.Context([cfg], [p])
+    assert ei.value.status == md.MD_ERR_ARG
+    assert "n must be >= 1" in str(ei.value)
+
+
 def test_init_without_gpu_fails_cleanly(md):
     """Valid arguments but no usable GPU: a CUDA error status, not a crash."""
     from tests.helpers import has_gpu

@@ -116,6 +116,45 @@ def test_stateless_field_entry_point(md):
                                 e.data_ptr(), 0, stream)
 
 
+def test_stateless_fields_on_empty_and_single_inputs(md):
+    """Degenerate sizes of the stateless entry points (FP32/Kahan, allocation
+    free, FP64 reference): no sources gives a zero field and potential at
+    every target; no targets writes nothing; a lone source that is its own
+    target feels nothing; a negative size is an argument error."""
+    import torch
+    kc = oracle.coulomb_constant(0.8)
+    stream = torch.cuda.current_stream().cuda_stream
+    src = torch.tensor([[0.01, -0.02, 0.03, kc]], dtype=torch.float32, device="cuda")
+    tgt = torch.zeros((5, 4), dtype=torch.float32, device="cuda")
+    for fn in (md.coulomb_field_device, md.coulomb_field_device_noalloc):
+        e = torch.full((5, 3), float("nan"), dtype=torch.float64, device="cuda")
+        phi = torch.full((5,), float("nan"), dtype=torch.float64, device="cuda")
+        fn(src.data_ptr(), 0, tgt.data_ptr(), 5, 1e-6, -1, e.data_ptr(), phi.data_ptr(), stream)
+        torch.cuda.synchronize()
+        assert torch.all(e == 0) and torch.all(phi == 0)
+        e.fill_(7.0)
+        fn(src.data_ptr(), 1, tgt.data_ptr(), 0, 1e-6, -1, e.data_ptr(), phi.data_ptr(), stream)
+        torch.cuda.synchronize()
+        assert torch.all(e == 7.0)
+        e1 = torch.full((1, 3), float("nan"), dtype=torch.float64, device="cuda")
+        phi1 = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+        fn(src.data_ptr(), 1, src.data_ptr(), 1, 1e-6, 0, e1.data_ptr(), phi1.data_ptr(), stream)
+        torch.cuda.synchronize()
+        assert torch.all(e1 == 0) and torch.all(phi1 == 0)
+        with pytest.raises(md.MDError) as ei:
+            fn(src.data_ptr(), -1, tgt.data_ptr(), 5, 1e-6, -1, e.data_ptr(), 0, stream)
+        assert ei.value.status == md.MD_ERR_ARG
+    xs = torch.zeros((1, 3), dtype=torch.float64, device="cuda")
+    qs = torch.ones(1, dtype=torch.float64, device="cuda")
+    xt = torch.ones((5, 3), dtype=torch.float64, device="cuda")
+    e = torch.full((5, 3), float("nan"), dtype=torch.float64, device="cuda")
+    phi = torch.full((5,), float("nan"), dtype=torch.float64, device="cuda")
+    md.coulomb_field_fp64_device(xs.data_ptr(), qs.data_ptr(), 0, xt.data_ptr(), 0, 5, 1e-3, kc,
+                                 e.data_ptr(), phi.data_ptr(), stream)
+    torch.cuda.synchronize()
+    assert torch.all(e == 0) and torch.all(phi == 0)
+
+
 # ------------------------------------------------------------------ steps --
 
 def test_step_parity_short_2k(md):
@@ -307,6 +346,55 @@ def test_set_particles_round_trip(md):
         h = ctx.get_particles(0)
         assert np.array_equal(g.x, h.x) and np.array_equal(g.u, h.u)
         assert np.array_equal(g.kind, h.kind)
+
+
+def test_set_particles_rejects_bad_records_on_the_device(md):
+    """md_set_particles on a cluster without ionization checks the records on
+    the staged device copy: the first bad record is reported with the host
+    check's message, and a rejected block leaves the state unchanged."""
+    w = synth.xe3_cluster(3000, seed=7)
+    with ctx_for(md, w) as ctx:
+        ctx.step(2)
+        g0 = ctx.get_particles(0)
+
+        def rejected(edit, what):
+            g = ctx.get_particles(0)
+            edit(g)
+            with pytest.raises(md.MDError) as ei:
+                ctx.set_particles(0, g)
+            assert ei.value.status == md.MD_ERR_ARG and what in str(ei.value), str(ei.value)
+            h = ctx.get_particles(0)
+            for k in ("x", "u", "z", "mass", "w", "kind"):
+                assert np.array_equal(getattr(h, k), getattr(g0, k)), k
+
+        def nan_x(g):
+            g.x[2900, 1] = np.nan
+        rejected(nan_x, "record 2900: non-finite")
+
+        def inf_w_and_bad_kind(g):
+            g.w[1234] = np.inf
+            g.kind[2500] = 7
+        rejected(inf_w_and_bad_kind, "record 1234: non-finite")
+
+        def electron_sign(g):
+            e = int(np.flatnonzero(g.kind == md.KIND_ELECTRON)[5])
+            g.z[e] = 1
+            g.u[e + 3, 0] = np.nan
+        e5 = int(np.flatnonzero(g0.kind == md.KIND_ELECTRON)[5])
+        rejected(electron_sign, f"record {e5}: electron with z >= 0")
+
+        def no_mass(g):
+            g.mass[17] = 0.0
+        rejected(no_mass, "record 17: mass must be > 0")
+
+        def kind_range(g):
+            g.kind[0] = 3
+        rejected(kind_range, "record 0: bad kind")
+
+        g = ctx.get_particles(0)
+        g.x[:] += 0.002
+        ctx.set_particles(0, g)
+        assert np.array_equal(ctx.get_particles(0).x, g.x)
 
 
 def test_periodic_boundary_wraps_into_box(md):
