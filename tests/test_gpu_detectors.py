@@ -100,3 +100,38 @@ def test_detector_arguments_and_state(md):
         ctx.set_detectors(0, None)
         with pytest.raises(md.MDError):
             ctx.iedf(0)
+
+
+def test_detectors_on_an_ionizing_cluster_match_oracle(md):
+    """An Ar cluster ionizing before every step (its ion-only i-blocks pushed
+    with the pass's field, the rest by the step kernel) and detectors at
+    0.9 R0: every crossing recorded by either push matches the oracle's
+    detectors applied to the GPU's own states, step by step."""
+    n = 1500
+    r0 = synth.nm_to_len(2.5)
+    c = synth.make_cluster(8, n, 0, r0, 0, synth.ARGON["mass"], n_electron_slots=8 * n)
+    rw = synth.nm_to_len(synth.ARGON["r_w_nm"])
+    cfg = md.make_config(a0=0.3, tau=1.0, t0=0.5 * math.pi, dt=0.1,
+                         softening=synth.nm_to_len(0.1), envelope=synth.ENV_FLAT, rate_model=1,
+                         ionize_every=1, zmax=8, n_ions=n, slot_base=n, seed=31,
+                         r_loc=3 * rw, r_create=rw, species=synth.ARGON)
+    nb = 50
+    radius = 0.9 * r0
+    e_max_ev = 2e3
+    det = oracle.Detectors(c.n, radius=radius, cone_deg=30.0, e_max_ev=e_max_ev, nbins=nb)
+    with md.Context([cfg], [md.HostParticles.from_cluster(c)]) as ctx:
+        ctx.set_tuning(128, 4, 512, 0, 1, 0)      # ions 0..1023 pushed with the pass's field
+        ctx.set_detectors(0, radius, cone_deg=30.0, e_max_ev=e_max_ev, n_bins=nb)
+        g0 = ctx.get_particles(0)
+        for _ in range(300):
+            ctx.step(1)
+            g1 = ctx.get_particles(0)
+            det.record(g0.x, g1.x, state_of(g1))
+            g0 = g1
+        got, inside = ctx.iedf(0)
+    crossed = np.flatnonzero(det.crossed)
+    print("crossings", crossed.size, "pushed with the pass's field", int(np.sum(crossed < 1024)),
+          "charges", np.bincount(g0.z[:n], minlength=9))
+    assert np.sum(crossed < 1024) > 5 and np.sum(crossed >= 1024) > 2
+    np.testing.assert_array_equal(got, det.hist)
+    np.testing.assert_array_equal(inside, det.inside(state_of(g0)))
