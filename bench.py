@@ -477,7 +477,7 @@ def run_iedf(args):
             e1.record(stream)
             torch.cuda.synchronize()
             ms += e0.elapsed_time(e1)
-            pairs += kk * float(ctx.diagnostics(0)["n_active"]) ** 2   # sampled per chunk
+            pairs += kk * float(ctx.count_active(0)) ** 2   # sampled per chunk
             done += kk
         zs = ctx.get_particles(0).z[:n]
         det, inside = ctx.iedf(0)
@@ -564,7 +564,7 @@ def run_native(args):
         if ionizing:
             # records active after the step's ionization pass (the pairs its
             # Coulomb sum covered); read outside the events
-            step_pairs.append(float(ctx.diagnostics(0)["n_active"]) ** 2)
+            step_pairs.append(float(ctx.count_active(0)) ** 2)
     torch.cuda.synchronize()
     dist.barrier()
     wall = time.perf_counter() - wall0

@@ -186,6 +186,12 @@ md_status md_sync(md_ctx *ctx);
  * `cluster` at the current step (synchronous; out is caller-owned). */
 md_status md_diagnostics(md_ctx *ctx, int32_t cluster, md_diag *out);
 
+/* md_count_active: the number of records of cluster `cluster` that are not
+ * MD_KIND_INACTIVE (md_diag.n_active) without the rest of the diagnostics:
+ * an O(n) count, where md_diagnostics also sums the potential over all pairs.
+ * Synchronous; *out is caller-owned.  Errors: MD_ERR_ARG (NULL, bad index). */
+md_status md_count_active(md_ctx *ctx, int32_t cluster, int64_t *out);
+
 /* md_get_particles / md_set_particles: copy cluster `cluster`'s records to /
  * from host arrays (n must equal the cluster's record count).  get is
  * synchronous; set reads the host arrays before it returns (page-locked

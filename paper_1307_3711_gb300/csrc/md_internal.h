@@ -42,6 +42,10 @@ cudaError_t launch_ffma_probe(int blocks, int iters, bool packed, float* sink, c
 // record first and a rejected block is not applied.
 cudaError_t launch_upload(const UploadArgs& a, cudaStream_t s);
 
+// Count of the records [off, off + n) that are not INACTIVE, into *out.
+cudaError_t launch_count_active(const unsigned char* kind, long long off, long long n,
+                                unsigned long long* out, cudaStream_t s);
+
 // Launches one CTA whose mbarrier wait can never complete (bounded by budget).
 cudaError_t launch_wait_selftest(long long budget, int* err, cudaStream_t s);
 

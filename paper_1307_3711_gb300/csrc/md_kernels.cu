@@ -319,6 +319,23 @@ cudaError_t launch_wait_selftest(long long budget, int* err, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Records [off, off + n) whose kind is not INACTIVE, added to *out.
+__global__ void __launch_bounds__(256) k_count_active(const unsigned char* kind, long long off,
+                                                      long long n, unsigned long long* out) {
+  const long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int live = (k < n && kind[off + k] != 2) ? 1 : 0;
+  const int cnt = __syncthreads_count(live);
+  if (threadIdx.x == 0 && cnt) atomicAdd(out, static_cast<unsigned long long>(cnt));
+}
+
+cudaError_t launch_count_active(const unsigned char* kind, long long off, long long n,
+                                unsigned long long* out, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess || n <= 0) return e;
+  k_count_active<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(kind, off, n, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_upload(const UploadArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
   const unsigned grid = static_cast<unsigned>((a.n + 255) / 256);

@@ -91,9 +91,11 @@ struct md_ctx {
   unsigned char* h_raw = nullptr;
   size_t raw_bytes = 0;
   md::DiagPartial* h_diag = nullptr;
-  // first record the device rejected in md_set_particles (kNoBadRecord: none)
-  unsigned long long* d_first_bad = nullptr;
-  unsigned long long* h_first_bad = nullptr;
+  // one device word and its pinned host copy for synchronous queries: the
+  // first record the upload check rejected (kNoBadRecord: none), the count
+  // of active records
+  unsigned long long* d_word = nullptr;
+  unsigned long long* h_word = nullptr;
 
   // kernel configuration
   int cfg = -1;
@@ -654,8 +656,8 @@ void free_ctx(md_ctx* c) {
   cudaFree(c->d_mlp);
   if (c->h_raw) cudaFreeHost(c->h_raw);
   if (c->h_diag) cudaFreeHost(c->h_diag);
-  cudaFree(c->d_first_bad);
-  if (c->h_first_bad) cudaFreeHost(c->h_first_bad);
+  cudaFree(c->d_word);
+  if (c->h_word) cudaFreeHost(c->h_word);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -732,10 +734,10 @@ md_status upload_cluster(md_ctx* c, int ci, const md_particles& p, bool device_c
   a.kind = c->d_kind;
   a.step = c->d_step;
   a.vel = c->d_vel;
-  a.first_bad = device_check ? c->d_first_bad : nullptr;
+  a.first_bad = device_check ? c->d_word : nullptr;
   MD_CUDA(md::launch_upload(a, c->stream));
   if (device_check)
-    MD_CUDA(cudaMemcpyAsync(c->h_first_bad, c->d_first_bad, sizeof(unsigned long long),
+    MD_CUDA(cudaMemcpyAsync(c->h_word, c->d_word, sizeof(unsigned long long),
                             cudaMemcpyDeviceToHost, c->stream));
   if (c->d_ion_next && c->ion[ci].rate_model)
     MD_CUDA(cudaMemcpyAsync(c->d_ion_next + ci, &next_slot, sizeof(long long),
@@ -756,11 +758,11 @@ md_status upload_cluster(md_ctx* c, int ci, const md_particles& p, bool device_c
                                  c->d_src_live, c->d_tgt_live, c->stream));
   // the pinned staging buffer is reused by the next call: wait for the copy
   MD_CUDA(cudaStreamSynchronize(c->stream));
-  if (device_check && *c->h_first_bad != md::kNoBadRecord) {
+  if (device_check && *c->h_word != md::kNoBadRecord) {
     // the message of the host check, for the first record the device rejected
-    const md_status st = check_record(p, ci, static_cast<long long>(*c->h_first_bad));
+    const md_status st = check_record(p, ci, static_cast<long long>(*c->h_word));
     return st != MD_OK ? st : fail(MD_ERR_ARG, "cluster %d: record %llu rejected", ci,
-                                   *c->h_first_bad);
+                                   *c->h_word);
   }
   return MD_OK;
 }
@@ -920,8 +922,8 @@ md_status md_init(md_ctx** out, const md_config* cfgs, int32_t n_clusters,
   if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
   e = cudaMallocHost(reinterpret_cast<void**>(&c->h_raw), c->raw_bytes);
   if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMallocHost"));
-  if (dev_alloc(&c->d_first_bad, 1) != cudaSuccess ||
-      cudaMallocHost(reinterpret_cast<void**>(&c->h_first_bad), sizeof(unsigned long long)) !=
+  if (dev_alloc(&c->d_word, 1) != cudaSuccess ||
+      cudaMallocHost(reinterpret_cast<void**>(&c->h_word), sizeof(unsigned long long)) !=
           cudaSuccess)
     return bail(fail(MD_ERR_OOM, "upload check buffers"));
   if (c->any_ion) {
@@ -1235,6 +1237,20 @@ md_status md_get_fields(md_ctx* c, int32_t cluster, double* e, double* phi) {
     MD_CUDA(cudaMemcpyAsync(phi, c->d_phi, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
   MD_CUDA(cudaStreamSynchronize(c->stream));
   return check_device_error(c);
+}
+
+md_status md_count_active(md_ctx* c, int32_t cluster, int64_t* out) {
+  if (!c || !out) return fail(MD_ERR_ARG, "NULL argument");
+  if (cluster < 0 || cluster >= c->n_clusters) return fail(MD_ERR_ARG, "bad cluster index");
+  MD_CUDA(md::launch_count_active(c->d_kind, c->cl[cluster].off, c->cl[cluster].n,
+                                  c->d_word, c->stream));
+  MD_CUDA(cudaMemcpyAsync(c->h_word, c->d_word, sizeof(unsigned long long),
+                          cudaMemcpyDeviceToHost, c->stream));
+  MD_CUDA(cudaStreamSynchronize(c->stream));
+  md_status st = check_device_error(c);
+  if (st != MD_OK) return st;
+  *out = static_cast<int64_t>(*c->h_word);
+  return MD_OK;
 }
 
 md_status md_diagnostics(md_ctx* c, int32_t cluster, md_diag* out) {

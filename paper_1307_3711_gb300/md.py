@@ -103,6 +103,7 @@ _SIGS = {
     "md_step": (_st, [_ctx_p, C.c_int32]),
     "md_sync": (_st, [_ctx_p]),
     "md_diagnostics": (_st, [_ctx_p, C.c_int32, C.POINTER(Diag)]),
+    "md_count_active": (_st, [_ctx_p, C.c_int32, C.POINTER(C.c_int64)]),
     "md_get_particles": (_st, [_ctx_p, C.c_int32, C.POINTER(Particles)]),
     "md_set_particles": (_st, [_ctx_p, C.c_int32, C.POINTER(Particles)]),
     "md_get_fields": (_st, [_ctx_p, C.c_int32, _p, _p]),
@@ -307,6 +308,12 @@ class Context:
         s = out.struct()
         _check(_lib.md_get_particles(self._h, cluster, C.byref(s)))
         return out
+
+    def count_active(self, cluster: int = 0) -> int:
+        """Records of the cluster that are not INACTIVE (an O(n) count)."""
+        v = C.c_int64()
+        _check(_lib.md_count_active(self._h, cluster, C.byref(v)))
+        return v.value
 
     def set_particles(self, cluster: int, p: HostParticles):
         s = p.struct()

@@ -147,6 +147,7 @@ def test_ionization_in_steps_conserves_charge(md):
         assert g.z[:n].sum() > 0
         d = ctx.diagnostics(0)
         assert d["charge_count"].sum() == n and d["n_nonfinite"] == 0
+        assert ctx.count_active(0) == d["n_active"] == int(np.sum(g.kind != md.KIND_INACTIVE))
 
 
 def test_slot_capacity_checked_on_upload(md):
