@@ -1120,6 +1120,12 @@ __global__ void __launch_bounds__(THREADS) k_field(const FieldArgs a) {
     s_abort = 0;
   }
   __syncthreads();
+  // this CTA's sources: all, or segment blockIdx.y of a split
+  const bool split = a.nseg > 1;
+  const long long j0 = split ? static_cast<long long>(blockIdx.y) * a.seg_len : 0;
+  const long long jn = split ? (a.ns - j0 < a.seg_len ? (a.ns > j0 ? a.ns - j0 : 0) : a.seg_len)
+                             : a.ns;
+  double* part = split ? a.part + 4 * static_cast<long long>(blockIdx.y) * a.nt : nullptr;
   const long long i0 = static_cast<long long>(blockIdx.x) * (THREADS * R);
   const long long i1 = (i0 + THREADS * R < a.nt ? i0 + THREADS * R : a.nt) - 1;
   if (a.tgt_live && !any_live(a.tgt_live, a.gbase + i0, a.gbase + i1)) {
@@ -1128,6 +1134,10 @@ __global__ void __launch_bounds__(THREADS) k_field(const FieldArgs a) {
     for (int r = 0; r < R; ++r) {
       const long long i = i0 + threadIdx.x + r * THREADS;
       if (i >= a.nt) continue;
+      if (split) {
+        part[4 * i + 0] = part[4 * i + 1] = part[4 * i + 2] = part[4 * i + 3] = 0.0;
+        continue;
+      }
       a.e[3 * i + 0] = a.e[3 * i + 1] = a.e[3 * i + 2] = 0.0;
       if (POT && a.phi) a.phi[i] = 0.0;
     }
@@ -1145,18 +1155,29 @@ __global__ void __launch_bounds__(THREADS) k_field(const FieldArgs a) {
   Acc<R, POT> acc;
   acc.zero();
   unsigned it = 0;
-  if (!sum_sources<THREADS, R, TILE, STAGES, POT>(sm, it, a.src, a.ns, xi, yi, zi, a.eps2, acc,
-                                                   a.err, &s_abort, a.src_live, a.gbase))
+  if (!sum_sources<THREADS, R, TILE, STAGES, POT>(sm, it, a.src + j0, jn, xi, yi, zi, a.eps2,
+                                                   acc, a.err, &s_abort, a.src_live,
+                                                   a.gbase + j0))
     return;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const long long i = i0 + threadIdx.x + r * THREADS;
     if (i >= a.nt) continue;
-    a.e[3 * i + 0] = -(static_cast<double>(acc.sx[r]) - acc.cx[r]);
-    a.e[3 * i + 1] = -(static_cast<double>(acc.sy[r]) - acc.cy[r]);
-    a.e[3 * i + 2] = -(static_cast<double>(acc.sz[r]) - acc.cz[r]);
+    const double ex = -(static_cast<double>(acc.sx[r]) - acc.cx[r]);
+    const double ey = -(static_cast<double>(acc.sy[r]) - acc.cy[r]);
+    const double ez = -(static_cast<double>(acc.sz[r]) - acc.cz[r]);
+    double ph = POT ? static_cast<double>(acc.sp[r]) - acc.cp[r] : 0.0;
+    if (split) {
+      part[4 * i + 0] = ex;
+      part[4 * i + 1] = ey;
+      part[4 * i + 2] = ez;
+      part[4 * i + 3] = ph;
+      continue;
+    }
+    a.e[3 * i + 0] = ex;
+    a.e[3 * i + 1] = ey;
+    a.e[3 * i + 2] = ez;
     if (POT && a.phi) {
-      double ph = static_cast<double>(acc.sp[r]) - acc.cp[r];
       if (a.self_offset >= 0) {
         const long long js = i + a.self_offset;
         if (js < a.ns) ph -= static_cast<double>(a.src[js].w * rsqrt_mufu(a.eps2));

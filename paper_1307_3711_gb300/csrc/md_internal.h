@@ -27,8 +27,11 @@ struct KernelConfig {
 
 const KernelConfig* step_configs(int* count);
 
-// Field (and potential) at nt targets from ns sources (FP32/Kahan direct sum).
+// Field (and potential) at nt targets from ns sources (FP32/Kahan direct sum),
+// with the sources split as a.nseg / a.seg_len / a.part say.
 cudaError_t launch_field(const FieldArgs& a, bool potential, cudaStream_t s);
+int field_targets_per_cta();
+cudaError_t field_blocks_per_sm(int* out);
 
 // Diagnostics: per-block partials then a deterministic final sum.
 constexpr int kDiagThreads = 256;

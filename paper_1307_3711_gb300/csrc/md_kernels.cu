@@ -227,15 +227,53 @@ const KernelConfig* step_configs(int* count) {
   return kConfigs;
 }
 
+// Sum of the segment partials of a split k_field, in segment order, and the
+// potential's self term.
+__global__ void __launch_bounds__(256) k_field_combine(const FieldArgs a) {
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= a.nt) return;
+  double ex = 0.0, ey = 0.0, ez = 0.0, ph = 0.0;
+  for (int sg = 0; sg < a.nseg; ++sg) {
+    const double* p = a.part + 4 * (static_cast<long long>(sg) * a.nt + i);
+    ex += p[0];
+    ey += p[1];
+    ez += p[2];
+    ph += p[3];
+  }
+  a.e[3 * i + 0] = ex;
+  a.e[3 * i + 1] = ey;
+  a.e[3 * i + 2] = ez;
+  if (a.phi) {
+    // (a target block without active records has zero partials and stays zero)
+    if (a.self_offset >= 0 && ph != 0.0) {
+      const long long js = i + a.self_offset;
+      if (js < a.ns) ph -= static_cast<double>(a.src[js].w * rsqrt_mufu(a.eps2));
+    }
+    a.phi[i] = ph;
+  }
+}
+
 cudaError_t launch_field(const FieldArgs& a, bool potential, cudaStream_t s) {
   if (a.nt <= 0) return cudaSuccess;
+  if (a.nseg > 1 && (!a.part || a.seg_len <= 0)) return cudaErrorInvalidValue;
   const long long per = kFieldThreads * kFieldR;
-  const unsigned grid = static_cast<unsigned>((a.nt + per - 1) / per);
+  const dim3 grid(static_cast<unsigned>((a.nt + per - 1) / per),
+                  static_cast<unsigned>(a.nseg > 1 ? a.nseg : 1));
   if (potential)
     k_field<kFieldThreads, kFieldR, kFieldTile, 2, true><<<grid, kFieldThreads, 0, s>>>(a);
   else
     k_field<kFieldThreads, kFieldR, kFieldTile, 2, false><<<grid, kFieldThreads, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || a.nseg <= 1) return e;
+  k_field_combine<<<static_cast<unsigned>((a.nt + 255) / 256), 256, 0, s>>>(a);
   return cudaGetLastError();
+}
+
+int field_targets_per_cta() { return kFieldThreads * kFieldR; }
+
+cudaError_t field_blocks_per_sm(int* out) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      out, k_field<kFieldThreads, kFieldR, kFieldTile, 2, true>, kFieldThreads, 0);
 }
 
 cudaError_t launch_diag(const DiagArgs& a, int blocks, DiagPartial* out, cudaStream_t s) {

@@ -53,6 +53,8 @@ struct md_ctx {
   int device = 0;
   int sm_count = 0;
   int ion_field_bps = 1;   // resident CTAs per SM of the ionization field kernel
+  int field_bps = 1;       // resident CTAs per SM of the field kernel (md_get_fields)
+  double* d_field_part = nullptr;  // [kFieldMaxSeg][max n_pad][4] split partials
   // per cluster: records live at the last upload (an ionizing cluster: below
   // its next free electron slot), for the choice of the source split
   std::vector<long long> live_host;
@@ -318,6 +320,9 @@ bool ions_fused(const md_ctx* c, int ci) {
   return c->d_ion_e && io.rate_model != 0 && io.ionize_every == 1 && io.n_ions > 0;
 }
 
+// Source segments of md_get_fields / md_diagnostics at most.
+constexpr int kFieldMaxSeg = 8;
+
 // Segments per i-block for a requested split S: each segment holds at least
 // one shared-memory tile of sources.
 void segments_for(const md::ClusterDev& cl, int S, int tile, int* nseg, int* seg_len) {
@@ -455,6 +460,9 @@ int default_config(md_ctx* c) {
 
 md_status ensure_scratch(md_ctx* c) {
   if (c->d_e) return MD_OK;
+  MD_CUDA(dev_alloc(&c->d_field_part,
+                    4 * static_cast<size_t>(kFieldMaxSeg) * static_cast<size_t>(c->max_n + md::kPad)));
+  MD_CUDA(md::field_blocks_per_sm(&c->field_bps));
   MD_CUDA(dev_alloc(&c->d_e, 3 * static_cast<size_t>(c->max_n + md::kPad)));
   MD_CUDA(dev_alloc(&c->d_phi, static_cast<size_t>(c->max_n + md::kPad)));
   c->diag_blocks = std::max(1, std::min(4 * c->sm_count,
@@ -636,6 +644,7 @@ void free_ctx(md_ctx* c) {
   cudaFree(c->d_part);
   cudaFree(c->d_diag);
   cudaFree(c->d_units);
+  cudaFree(c->d_field_part);
   cudaFree(c->d_fpart);
   cudaFree(c->d_iblk_cnt);
   cudaFree(c->d_raw);
@@ -1222,6 +1231,18 @@ static md_status run_fields(md_ctx* c, int ci, bool potential) {
   a.src_live = c->d_src_live;
   a.tgt_live = c->d_tgt_live;
   a.gbase = cl.off;
+  // split the sources so that about 4 waves of CTAs run (at most kFieldMaxSeg
+  // segments of at least 4 tiles each)
+  const long long per = md::field_targets_per_cta();
+  const long long blocks = (a.nt + per - 1) / per;
+  const long long want = (4LL * c->field_bps * c->sm_count + blocks - 1) / blocks;
+  const long long nseg = std::max(1LL, std::min({want, static_cast<long long>(kFieldMaxSeg),
+                                                a.ns / 2048}));
+  if (nseg > 1) {
+    a.nseg = static_cast<int>(nseg);
+    a.seg_len = (a.ns + nseg - 1) / nseg;
+    a.part = c->d_field_part;
+  }
   MD_CUDA(md::launch_field(a, potential, c->stream));
   return MD_OK;
 }

@@ -162,6 +162,12 @@ struct FieldArgs {
   const unsigned char* src_live;
   const unsigned char* tgt_live;
   long long gbase;
+  // sources split into nseg segments of seg_len (nseg > 1): CTA (x, y) sums
+  // segment y into part[y][nt][4] = (ex, ey, ez, phi), and a second kernel
+  // adds the segments in order
+  int nseg = 1;
+  long long seg_len = 0;
+  double* part = nullptr;
 };
 
 struct DiagPartial {

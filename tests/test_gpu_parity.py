@@ -5,6 +5,7 @@ with p99 <= 2e-5 for the FP32/Kahan sum.  Trajectories: compared over a few
 steps only (chaotic beyond); long runs by energy and momentum.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -43,16 +44,20 @@ def oracle_params(w, nthreads=1):
 
 # ------------------------------------------------------------------ field --
 
-@pytest.mark.parametrize("n_ions,n_el", [(700, 2100), (1, 1), (5, 0), (1500, 1517)])
+@pytest.mark.parametrize("n_ions,n_el", [(700, 2100), (1, 1), (5, 0), (1500, 1517),
+                                         (5003, 15001)])
 def test_field_parity_small(md, n_ions, n_el):
-    """Several 512-source tiles plus a ragged tail, and degenerate sizes."""
+    """Several 512-source tiles plus a ragged tail, and degenerate sizes.  At
+    20k records the sources are split into segments whose partials are added
+    in order (with the potential's self term removed once)."""
     c = synth.make_cluster(3, n_ions, n_el, synth.nm_to_len(3.0), 3, synth.MASS_XE, kT_e_ev=10)
     w = synth.Workload("t", c, a0=0.07, pol=0, env=1, tau=300.0, eps=synth.nm_to_len(0.1),
                        dt=0.02, nsteps=1)
     with ctx_for(md, w) as ctx:
         e, phi = ctx.fields(0, potential=True)
     kc = oracle.coulomb_constant(0.8)
-    e64, phi64 = oracle.self_field(c.x, c.w * c.z, w.eps, kc, potential=True)
+    e64, phi64 = oracle.self_field(c.x, c.w * c.z, w.eps, kc, potential=True,
+                                   nthreads=os.cpu_count() or 1)
     if c.n == 1:
         assert np.all(e == 0) and np.all(np.abs(phi) < 1e-12)
         return
