@@ -1,19 +1,24 @@
 // md_ionize.cu -- Monte-Carlo ionization pass on the GPU (Holkundkar,
 // arXiv:1307.3711, Sec. II, ionization paragraph).
 //
-// Two kernels per cluster and pass:
-//   k_ion_field   for every ion/atom record: the Coulomb field of all other
-//                 particles (the TMA-staged FP32/Kahan direct sum of the step
-//                 kernel) and the weight, momentum and momentum-square sums of
-//                 the electrons within r_loc (from the FP32 velocity stream,
-//                 landed beside the position tiles);
-//   k_ion_decide  per ion: laser field at t_n, |E|, local density and
-//                 temperature, total rate (static ADK + Lotz, or the learned
-//                 surrogate), P = 1 - exp(-nu dt_ion) and a Philox4x32-10 draw;
-//   k_ion_apply   one CTA per cluster: the ions that fired, in index order,
+// Kernels of one cluster's pass, in launch order:
+//   k_ion_field   for every ion/atom record and source segment: the Coulomb
+//                 field of the live records (the TMA-staged FP32/Kahan direct
+//                 sum of the step kernel) and the weight, momentum and
+//                 momentum-square sums of the electrons within r_loc (from the
+//                 FP32 velocity stream, landed beside the position tiles);
+//   k_ion_inputs  per ion: the segments added in order, laser field at t_n,
+//                 |E|, local density and temperature;
+//   (k_ion_mlp_rates, md_mlp.cu: surrogate rates where the model has them)
+//   k_ion_decide  per ion: total rate (static ADK + Lotz, or the surrogate's),
+//                 P = 1 - exp(-nu dt_ion) and a Philox4x32-10 draw;
+//   k_ion_apply   one CTA per 256 ions: the ions that fired, in index order,
 //                 get charge z + 1 and free their electrons into the next free
-//                 slots (an exclusive scan of the fired flags gives each its
-//                 slot), so the active slots stay one dense block.
+//                 slots (a scan of the fired flags gives each its slot), so
+//                 the active slots stay one dense block;
+//   k_ion_fix     (a pass before every step) the field of the pass's charge
+//                 changes added to each ion's field, which k_push_ions then
+//                 uses to push the ions in place of the step kernel's sum.
 // The decision runs after the whole field pass, so no charge changes while
 // any other ion's field is being summed.  Rates are FP64, as on the host.
 #include <cmath>
