@@ -313,6 +313,10 @@ md_status md_autotune(md_ctx *ctx, int32_t steps, double *times_ms, int32_t cap)
  *         is removed), or -1 if targets are not sources
  *   e:    device double[nt][3] output field; phi: device double[nt] or NULL
  *   stream: cudaStream_t (NULL = legacy default stream).  Asynchronous.
+ * When few targets would leave the GPU mostly idle, the sources are split
+ * into segments whose partial fields are added in order (deterministic); the
+ * partials are allocated and freed in stream order on `stream` (at most
+ * 256 MB), so calls on different streams may overlap.
  * Errors: MD_ERR_ARG for NULL/unaligned pointers, ns < 0, nt < 0. */
 md_status md_coulomb_field_device(const void *src, int64_t ns, const void *tgt,
                                   int64_t nt, float eps2, int64_t self_offset,

@@ -1589,7 +1589,29 @@ md_status md_coulomb_field_device(const void* src, int64_t ns, const void* tgt, 
   a.src_live = nullptr;
   a.tgt_live = nullptr;
   a.gbase = 0;
-  MD_CUDA(md::launch_field(a, phi != nullptr, static_cast<cudaStream_t>(stream)));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // split the sources until about 4 waves of CTAs run (up to 64 segments of
+  // at least 4 tiles, partials of at most 256 MB); the partials live in
+  // stream-ordered memory, so calls on different streams do not share them
+  int bps = 1, sms = 1;
+  MD_CUDA(md::field_blocks_per_sm(&bps));
+  MD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const long long per = md::field_targets_per_cta();
+  const long long nt_ = static_cast<long long>(nt), ns_ = static_cast<long long>(ns);
+  const long long blocks = (nt_ + per - 1) / per;
+  const long long want = (4LL * std::max(1, bps) * sms + blocks - 1) / blocks;
+  const long long by_mem = (256LL << 20) / (32LL * nt_);
+  const long long nseg = std::max(1LL, std::min({want, 64LL, ns_ / 2048, by_mem}));
+  void* part = nullptr;
+  if (nseg > 1) {
+    MD_CUDA(cudaMallocAsync(&part, static_cast<size_t>(32 * nseg * nt_), st));
+    a.nseg = static_cast<int>(nseg);
+    a.seg_len = (ns_ + nseg - 1) / nseg;
+    a.part = static_cast<double*>(part);
+  }
+  const cudaError_t le = md::launch_field(a, phi != nullptr, st);
+  if (part) MD_CUDA(cudaFreeAsync(part, st));
+  MD_CUDA(le);
   return MD_OK;
 }
 

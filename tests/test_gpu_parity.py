@@ -121,6 +121,36 @@ def test_stateless_field_entry_point(md):
                                 e.data_ptr(), 0, stream)
 
 
+def test_stateless_field_few_targets_many_sources(md):
+    """md_coulomb_field_device with 300 targets and 200k sources splits the
+    sources into segments (stream-ordered partials) and adds them in order:
+    the FP64 oracle's field and potential, the self term removed once when
+    the targets are sources; the same call gives the same bits twice."""
+    import torch
+    rng = np.random.default_rng(29)
+    kc = oracle.coulomb_constant(0.8)
+    ns, nt = 200000, 300
+    xs = rng.normal(size=(ns, 3)) * 0.05
+    qs = rng.choice([-1.0, 1.0, 2.0], size=ns)
+    eps = 1e-3
+    src = torch.tensor(np.c_[xs, kc * qs], dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    out = []
+    for _ in range(2):
+        e = torch.zeros((nt, 3), dtype=torch.float64, device="cuda")
+        phi = torch.zeros(nt, dtype=torch.float64, device="cuda")
+        md.coulomb_field_device(src.data_ptr(), ns, src.data_ptr(), nt, eps * eps, 0,
+                                e.data_ptr(), phi.data_ptr(), stream)
+        torch.cuda.synchronize()
+        out.append((e.cpu().numpy(), phi.cpu().numpy()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    idx = np.arange(nt)
+    e64, phi64 = oracle.coulomb_field(xs[:nt], xs, qs, eps, kc, self_idx=idx, potential=True,
+                                      nthreads=os.cpu_count() or 1)
+    assert summary(force_error(out[0][0], e64))["p99"] <= FORCE_P99
+    np.testing.assert_allclose(out[0][1], phi64, rtol=2e-5, atol=2e-5 * np.abs(phi64).max())
+
+
 def test_stateless_fields_on_empty_and_single_inputs(md):
     """Degenerate sizes of the stateless entry points (FP32/Kahan, allocation
     free, FP64 reference): no sources gives a zero field and potential at
