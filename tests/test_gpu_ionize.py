@@ -291,12 +291,14 @@ def test_ionization_pass_full_size_sampled(md):
     np.testing.assert_allclose(info["prob"][idx], p_ref, rtol=1e-12, atol=1e-300)
 
 
-def test_graph_replay_equals_direct_launches_when_ionizing(md):
+@pytest.mark.parametrize("every", [2, 1])
+def test_graph_replay_equals_direct_launches_when_ionizing(md, every):
     """md_step(32) replays a captured graph of 16 steps (ionization pass and
-    step kernel, every 2nd step ionizing); 32 calls of md_step(1) launch
-    directly: the same bits, charges and slots."""
+    step kernel; with a pass before every step also the charge-change
+    correction and the push of the ions with the pass's field); 32 calls of
+    md_step(1) launch directly: the same bits, charges and slots."""
     c, kw = ar_case(n_atoms=1500, a0=0.1)
-    kw["ionize_every"] = 2
+    kw["ionize_every"] = every
     out = []
     for graph in (True, False):
         with md.Context([md.make_config(**kw)], [md.HostParticles.from_cluster(c)]) as ctx:
