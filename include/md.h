@@ -186,6 +186,18 @@ md_status md_sync(md_ctx *ctx);
  * `cluster` at the current step (synchronous; out is caller-owned). */
 md_status md_diagnostics(md_ctx *ctx, int32_t cluster, md_diag *out);
 
+/* md_step_diag: one step of every cluster (as md_step(ctx, 1)) that also
+ * writes out[k], for every cluster k, the diagnostics md_diagnostics would
+ * report at the start of the step (t_n).  The potential is summed inside the
+ * step's Coulomb pass (one more FP32 add per pair) and the kinetic energy at
+ * integer time comes from the step's own kick, so a diagnosed step costs
+ * about one step instead of two N^2 passes.  Contexts with ionization or
+ * detectors and the packed kernel configurations use md_diagnostics and
+ * md_step instead (same results up to the order of the FP32 sums).
+ * out: caller-owned md_diag[n_clusters].  Synchronous.  Errors: MD_ERR_ARG,
+ * MD_ERR_NONFINITE (after the step) as md_diagnostics. */
+md_status md_step_diag(md_ctx *ctx, md_diag *out);
+
 /* md_count_active: the number of records of cluster `cluster` that are not
  * MD_KIND_INACTIVE (md_diag.n_active) without the rest of the diagnostics:
  * an O(n) count, where md_diagnostics also sums the potential over all pairs.

@@ -886,10 +886,15 @@ __device__ __forceinline__ void detect(unsigned long long* hist, unsigned char* 
 
 // Laser + Boris kick (FP32 increment) + FP64 drift + boundary for record i
 // with Coulomb field (ex, ey, ez); writes x, u and the next j-stream entry.
-template <bool DET>
+// DIAG (diagnostic steps): also the record's diagnostics at t_n, as
+// k_diag_partial forms them from the same kick: status (1 active, 2
+// non-finite; inactive records are left at 0), kinetic energy at the
+// integer-time u = u^{n-1/2} + du/2, potential energy w z phi / 2, momentum.
+template <bool DET, bool DIAG = false>
 __device__ __forceinline__ void push_record(const StepArgs& a, const ClusterDev& c, long long i,
                                             double ex, double ey, double ez, const float* las,
-                                            double t_next, const float4* cur, float4* nxt) {
+                                            double t_next, const float4* cur, float4* nxt,
+                                            double phi = 0.0) {
   if (!MD_IN_RANGE(a.err, i, c.off, c.off + c.n_pad)) return;
   double X = a.x[i], Y = a.y[i], Z = a.z[i];
   double Ux = a.ux[i], Uy = a.uy[i], Uz = a.uz[i];
@@ -898,6 +903,25 @@ __device__ __forceinline__ void push_record(const StepArgs& a, const ClusterDev&
   boris_increment(static_cast<float>(Ux), static_cast<float>(Uy), static_cast<float>(Uz),
                   static_cast<float>(ex) + las[0], static_cast<float>(ey) + las[1],
                   static_cast<float>(ez) + las[2], las[3], las[4], las[5], h, dux, duy, duz);
+  if constexpr (DIAG) {
+    if (a.kind[i] != 2) {
+      double* rec = a.diag_rec + 6 * i;
+      if (!(isfinite(X) && isfinite(Y) && isfinite(Z) && isfinite(Ux) && isfinite(Uy) &&
+            isfinite(Uz))) {
+        rec[0] = 2.0;
+      } else {
+        const double mx = Ux + 0.5 * dux, my = Uy + 0.5 * duy, mz = Uz + 0.5 * duz;
+        const double uu = mx * mx + my * my + mz * mz;
+        const double wm = a.w[i] * a.mass[i];
+        rec[0] = 1.0;
+        rec[1] = wm * uu / (sqrt(1.0 + uu) + 1.0);
+        rec[2] = 0.5 * a.w[i] * a.zq[i] * phi;
+        rec[3] = wm * mx;
+        rec[4] = wm * my;
+        rec[5] = wm * mz;
+      }
+    }
+  }
   Ux += static_cast<double>(dux);
   Uy += static_cast<double>(duy);
   Uz += static_cast<double>(duz);
@@ -936,8 +960,14 @@ __device__ __forceinline__ void push_record(const StepArgs& a, const ClusterDev&
 // One full MD step for every work unit (cluster, i-block): field at x^n from
 // all sources of the cluster, laser at t_n, Boris kick, FP64 drift, boundary,
 // new j-stream entry.  Persistent: CTAs take units from an atomic ticket.
-template <int THREADS, int R, int TILE, int STAGES, bool PACK, int MINB, bool DET>
+//
+// POT (scalar path only): a diagnostic step, which also sums the potential
+// phi_i beside the field (split segments add their phi partials in order)
+// and records every record's diagnostics at t_n (push_record's DIAG).
+template <int THREADS, int R, int TILE, int STAGES, bool PACK, int MINB, bool DET,
+          bool POT = false>
 __global__ void __launch_bounds__(THREADS, MINB) k_step(const StepArgs a) {
+  static_assert(!(PACK && POT), "diagnostic steps use the scalar path");
   __shared__ Stage<TILE, STAGES> sm;
   __shared__ DupTile<PACK ? TILE : 1> dup;
   __shared__ KahanSmem<PACK ? R / 2 : 1, PACK ? THREADS : 1, false> ks;
@@ -992,16 +1022,16 @@ __global__ void __launch_bounds__(THREADS, MINB) k_step(const StepArgs a) {
         zi[r] = p.z;
       }
       bool ok;
-      Acc<R, false> acc;
+      Acc<R, POT> acc;
       if constexpr (PACK) {
         ok = sum_sources_packed<THREADS, R, TILE, STAGES, false>(
             sm, dup, ks, it, cur + s_c.off + j0, jn, xi, yi, zi, s_c.eps2, a.err, &s_abort,
             a.src_live, s_c.off + j0);
       } else {
         acc.zero();
-        ok = sum_sources<THREADS, R, TILE, STAGES, false>(sm, it, cur + s_c.off + j0, jn, xi, yi,
-                                                          zi, s_c.eps2, acc, a.err, &s_abort,
-                                                          a.src_live, s_c.off + j0);
+        ok = sum_sources<THREADS, R, TILE, STAGES, POT>(sm, it, cur + s_c.off + j0, jn, xi, yi,
+                                                        zi, s_c.eps2, acc, a.err, &s_abort,
+                                                        a.src_live, s_c.off + j0);
       }
       if (!ok) return;
 
@@ -1043,7 +1073,14 @@ __global__ void __launch_bounds__(THREADS, MINB) k_step(const StepArgs a) {
             if (i >= eend) continue;
             double ex, ey, ez;
             field_of(r, ex, ey, ez);
-            push_record<DET>(a, s_c, i, ex, ey, ez, s_las, t_next, cur2, nxt);
+            if constexpr (POT) {
+              // the potential without the record's own term
+              const double ph = (static_cast<double>(acc.sp[r]) - acc.cp[r]) -
+                                static_cast<double>(cur2[i].w * rsqrt_mufu(s_c.eps2));
+              push_record<DET, true>(a, s_c, i, ex, ey, ez, s_las, t_next, cur2, nxt, ph);
+            } else {
+              push_record<DET>(a, s_c, i, ex, ey, ez, s_las, t_next, cur2, nxt);
+            }
           }
         }
       } else {
@@ -1063,6 +1100,9 @@ __global__ void __launch_bounds__(THREADS, MINB) k_step(const StepArgs a) {
           __stcg(p + 0, ex);
           __stcg(p + 1, ey);
           __stcg(p + 2, ez);
+          if constexpr (POT)
+            __stcg(a.part_phi + static_cast<long long>(seg) * a.n_total + i,
+                   static_cast<double>(acc.sp[r]) - acc.cp[r]);
         }
         __threadfence();
         __syncthreads();
@@ -1086,7 +1126,15 @@ __global__ void __launch_bounds__(THREADS, MINB) k_step(const StepArgs a) {
               ey += __ldcg(p + 1);
               ez += __ldcg(p + 2);
             }
-            push_record<DET>(a, s_c, i, ex, ey, ez, s_las, t_next, cur2, nxt);
+            if constexpr (POT) {
+              double ph = 0.0;
+              for (int sg = 0; sg < nseg; ++sg)
+                ph += __ldcg(a.part_phi + static_cast<long long>(sg) * a.n_total + i);
+              ph -= static_cast<double>(cur2[i].w * rsqrt_mufu(s_c.eps2));
+              push_record<DET, true>(a, s_c, i, ex, ey, ez, s_las, t_next, cur2, nxt, ph);
+            } else {
+              push_record<DET>(a, s_c, i, ex, ey, ez, s_las, t_next, cur2, nxt);
+            }
           }
         }
       }
@@ -1227,29 +1275,44 @@ __global__ void __launch_bounds__(THREADS) k_diag_partial(const DiagArgs a) {
     const unsigned char kd = a.kind[i];
     if (kd == 2) continue;
     ++na;
-    const double X = a.x[i], Y = a.y[i], Z = a.z[i];
-    const double Ux = a.ux[i], Uy = a.uy[i], Uz = a.uz[i];
-    if (!(isfinite(X) && isfinite(Y) && isfinite(Z) && isfinite(Ux) && isfinite(Uy) &&
-          isfinite(Uz))) {
-      ++nbad;
-      continue;
+    if (a.rec) {
+      // recorded by a diagnostic step at t_n (the state here is t_{n+1})
+      const double* rc = a.rec + 6 * i;
+      if (rc[0] != 1.0) {
+        ++nbad;
+        continue;
+      }
+      acc[0] += rc[1];
+      if (kd == 1) acc[2] += rc[1]; else acc[1] += rc[1];
+      acc[3] += rc[2];
+      acc[4] += rc[3];
+      acc[5] += rc[4];
+      acc[6] += rc[5];
+    } else {
+      const double X = a.x[i], Y = a.y[i], Z = a.z[i];
+      const double Ux = a.ux[i], Uy = a.uy[i], Uz = a.uz[i];
+      if (!(isfinite(X) && isfinite(Y) && isfinite(Z) && isfinite(Ux) && isfinite(Uy) &&
+            isfinite(Uz))) {
+        ++nbad;
+        continue;
+      }
+      float dux, duy, duz;
+      boris_increment(static_cast<float>(Ux), static_cast<float>(Uy), static_cast<float>(Uz),
+                      static_cast<float>(a.e[3 * k]) + las[0],
+                      static_cast<float>(a.e[3 * k + 1]) + las[1],
+                      static_cast<float>(a.e[3 * k + 2]) + las[2], las[3], las[4], las[5],
+                      hq * a.qm[i], dux, duy, duz);
+      const double mx = Ux + 0.5 * dux, my = Uy + 0.5 * duy, mz = Uz + 0.5 * duz;
+      const double uu = mx * mx + my * my + mz * mz;
+      const double wm = a.w[i] * a.mass[i];
+      const double ke = wm * uu / (sqrt(1.0 + uu) + 1.0);
+      acc[0] += ke;
+      if (kd == 1) acc[2] += ke; else acc[1] += ke;
+      acc[3] += 0.5 * a.w[i] * a.zq[i] * a.phi[k];
+      acc[4] += wm * mx;
+      acc[5] += wm * my;
+      acc[6] += wm * mz;
     }
-    float dux, duy, duz;
-    boris_increment(static_cast<float>(Ux), static_cast<float>(Uy), static_cast<float>(Uz),
-                    static_cast<float>(a.e[3 * k]) + las[0],
-                    static_cast<float>(a.e[3 * k + 1]) + las[1],
-                    static_cast<float>(a.e[3 * k + 2]) + las[2], las[3], las[4], las[5],
-                    hq * a.qm[i], dux, duy, duz);
-    const double mx = Ux + 0.5 * dux, my = Uy + 0.5 * duy, mz = Uz + 0.5 * duz;
-    const double uu = mx * mx + my * my + mz * mz;
-    const double wm = a.w[i] * a.mass[i];
-    const double ke = wm * uu / (sqrt(1.0 + uu) + 1.0);
-    acc[0] += ke;
-    if (kd == 1) acc[2] += ke; else acc[1] += ke;
-    acc[3] += 0.5 * a.w[i] * a.zq[i] * a.phi[k];
-    acc[4] += wm * mx;
-    acc[5] += wm * my;
-    acc[6] += wm * mz;
     if (kd == 0) {
       int zb = a.zq[i];
       zb = zb < 0 ? 0 : (zb >= kHistBins ? kHistBins - 1 : zb);

@@ -23,6 +23,10 @@ struct KernelConfig {
   // epilogue (used while any cluster of the context has detectors)
   cudaError_t (*launch_step_det)(const StepArgs& a, int grid, cudaStream_t s);
   cudaError_t (*max_blocks_per_sm_det)(int* out);
+  // the diagnostic step (potential and per-record diagnostics at t_n), or
+  // nullptr (packed configurations)
+  cudaError_t (*launch_step_pot)(const StepArgs& a, int grid, cudaStream_t s);
+  cudaError_t (*max_blocks_per_sm_pot)(int* out);
 };
 
 const KernelConfig* step_configs(int* count);

@@ -192,6 +192,19 @@ cudaError_t launch_step_t(const StepArgs& a, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// the diagnostic step (potential summed beside the field), scalar path
+template <int T, int R, int TILE, int ST, int MB>
+cudaError_t launch_step_pot_t(const StepArgs& a, int grid, cudaStream_t s) {
+  k_step<T, R, TILE, ST, false, MB, false, true><<<grid, T, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int T, int R, int TILE, int ST, int MB>
+cudaError_t blocks_per_sm_pot_t(int* out) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      out, k_step<T, R, TILE, ST, false, MB, false, true>, T, 0);
+}
+
 template <int T, int R, int TILE, int ST, bool PK, int MB, bool DET>
 cudaError_t blocks_per_sm_t(int* out) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_step<T, R, TILE, ST, PK, MB, DET>,
@@ -202,15 +215,23 @@ cudaError_t blocks_per_sm_t(int* out) {
 #define MD_STEP_CONFIG(T, R, TILE, ST, PK, MB)                                          \
   {T, R, TILE, ST, PK, MB, &launch_step_t<T, R, TILE, ST, PK, MB, false>,              \
    &blocks_per_sm_t<T, R, TILE, ST, PK, MB, false>,                                      \
-   &launch_step_t<T, R, TILE, ST, PK, MB, true>, &blocks_per_sm_t<T, R, TILE, ST, PK, MB, true>}
+   &launch_step_t<T, R, TILE, ST, PK, MB, true>, &blocks_per_sm_t<T, R, TILE, ST, PK, MB, true>, \
+   nullptr, nullptr}
+// scalar configurations also have the diagnostic step
+#define MD_STEP_CONFIG_POT(T, R, TILE, ST, MB)                                          \
+  {T, R, TILE, ST, false, MB, &launch_step_t<T, R, TILE, ST, false, MB, false>,          \
+   &blocks_per_sm_t<T, R, TILE, ST, false, MB, false>,                                   \
+   &launch_step_t<T, R, TILE, ST, false, MB, true>,                                      \
+   &blocks_per_sm_t<T, R, TILE, ST, false, MB, true>,                                    \
+   &launch_step_pot_t<T, R, TILE, ST, MB>, &blocks_per_sm_pot_t<T, R, TILE, ST, MB>}
 
 // min CTAs per SM = 0 leaves the register budget to ptxas; a positive value
 // caps it at 64K / (threads x value)
 const KernelConfig kConfigs[] = {
     // scalar FP32 pair arithmetic
-    MD_STEP_CONFIG(128, 1, 512, 2, false, 0), MD_STEP_CONFIG(128, 4, 512, 2, false, 0),
-    MD_STEP_CONFIG(256, 2, 512, 2, false, 0), MD_STEP_CONFIG(128, 8, 512, 2, false, 0),
-    MD_STEP_CONFIG(256, 4, 512, 2, false, 0),
+    MD_STEP_CONFIG_POT(128, 1, 512, 2, 0), MD_STEP_CONFIG_POT(128, 4, 512, 2, 0),
+    MD_STEP_CONFIG_POT(256, 2, 512, 2, 0), MD_STEP_CONFIG_POT(128, 8, 512, 2, 0),
+    MD_STEP_CONFIG_POT(256, 4, 512, 2, 0),
     // packed f32x2 pair arithmetic (tile expanded in shared memory, one TMA stage)
     MD_STEP_CONFIG(128, 4, 256, 1, true, 0), MD_STEP_CONFIG(256, 4, 256, 1, true, 0),
     MD_STEP_CONFIG(128, 8, 256, 1, true, 0),

@@ -55,6 +55,9 @@ struct md_ctx {
   int ion_field_bps = 1;   // resident CTAs per SM of the ionization field kernel
   int field_bps = 1;       // resident CTAs per SM of the field kernel (md_get_fields)
   double* d_field_part = nullptr;  // [kFieldMaxSeg][max n_pad][4] split partials
+  double* d_diag_rec = nullptr;    // diagnostic steps: [n_total][6] per-record diagnostics
+  double* d_part_phi = nullptr;    // diagnostic steps: [part_phi_seg][n_total] phi partials
+  int part_phi_seg = 0;
   // per cluster: records live at the last upload (an ionizing cluster: below
   // its next free electron slot), for the choice of the source split
   std::vector<long long> live_host;
@@ -309,6 +312,11 @@ md::StepArgs step_args(md_ctx* c) {
   a.det_hist = c->d_det_hist;
   a.det_crossed = c->d_det_crossed;
   a.mass = c->d_mass;
+  a.diag_rec = nullptr;
+  a.part_phi = nullptr;
+  a.zq = c->d_z;
+  a.kind = c->d_kind;
+  a.w = c->d_w;
   return a;
 }
 
@@ -644,6 +652,8 @@ void free_ctx(md_ctx* c) {
   cudaFree(c->d_part);
   cudaFree(c->d_diag);
   cudaFree(c->d_units);
+  cudaFree(c->d_diag_rec);
+  cudaFree(c->d_part_phi);
   cudaFree(c->d_field_part);
   cudaFree(c->d_fpart);
   cudaFree(c->d_iblk_cnt);
@@ -1274,6 +1284,31 @@ md_status md_count_active(md_ctx* c, int32_t cluster, int64_t* out) {
   return MD_OK;
 }
 
+// md_diag of a cluster from its reduced partials, at step `step`.
+md_status fill_diag(const md::DiagPartial& d, long long step, const md::ClusterDev& cl,
+                    md_diag* out) {
+  std::memset(out, 0, sizeof(*out));
+  out->step = step;
+  out->t = cl.t0 + static_cast<double>(step) * cl.dt;
+  out->ke = d.v[0];
+  out->ke_ions = d.v[1];
+  out->ke_electrons = d.v[2];
+  out->pe = d.v[3];
+  out->total = d.v[0] + d.v[3];
+  out->p[0] = d.v[4];
+  out->p[1] = d.v[5];
+  out->p[2] = d.v[6];
+  out->n_active = d.cnt[0];
+  out->n_nonfinite = d.cnt[1];
+  for (int k = 0; k < md::kHistBins; ++k) {
+    out->charge_count[k] = d.hist[k];
+    out->charge_weight[k] = d.histw[k];
+  }
+  if (out->n_nonfinite > 0)
+    return fail(MD_ERR_NONFINITE, "%lld records hold NaN/Inf", (long long)out->n_nonfinite);
+  return MD_OK;
+}
+
 md_status md_diagnostics(md_ctx* c, int32_t cluster, md_diag* out) {
   if (!c || !out) return fail(MD_ERR_ARG, "NULL argument");
   if (cluster < 0 || cluster >= c->n_clusters) return fail(MD_ERR_ARG, "bad cluster index");
@@ -1304,27 +1339,76 @@ md_status md_diagnostics(md_ctx* c, int32_t cluster, md_diag* out) {
   MD_CUDA(cudaStreamSynchronize(c->stream));
   st = check_device_error(c);
   if (st != MD_OK) return st;
-  const md::DiagPartial& d = *c->h_diag;
-  std::memset(out, 0, sizeof(*out));
-  out->step = step;
-  out->t = a.c.t0 + static_cast<double>(step) * a.c.dt;
-  out->ke = d.v[0];
-  out->ke_ions = d.v[1];
-  out->ke_electrons = d.v[2];
-  out->pe = d.v[3];
-  out->total = d.v[0] + d.v[3];
-  out->p[0] = d.v[4];
-  out->p[1] = d.v[5];
-  out->p[2] = d.v[6];
-  out->n_active = d.cnt[0];
-  out->n_nonfinite = d.cnt[1];
-  for (int k = 0; k < md::kHistBins; ++k) {
-    out->charge_count[k] = d.hist[k];
-    out->charge_weight[k] = d.histw[k];
+  return fill_diag(*c->h_diag, step, a.c, out);
+}
+
+// One step of every cluster that also reports each cluster's diagnostics at
+// the start of the step: the step kernel's POT twin sums the potential beside
+// the field and records every record's diagnostics from its own kick, and an
+// O(N) reduction per cluster adds them in a fixed order.  Contexts with
+// ionization or detectors, and packed configurations, take the diagnostics
+// call and md_step(1) instead.
+md_status md_step_diag(md_ctx* c, md_diag* out) {
+  if (!c || !out) return fail(MD_ERR_ARG, "NULL argument");
+  int ncfg = 0;
+  const md::KernelConfig* cfgs = md::step_configs(&ncfg);
+  const md::KernelConfig& k = cfgs[c->cfg];
+  md_status st = MD_OK, worst = MD_OK;
+  if (c->any_ion || c->det_on || !k.launch_step_pot) {
+    for (int ci = 0; ci < c->n_clusters; ++ci) {
+      st = md_diagnostics(c, ci, &out[ci]);
+      if (st == MD_ERR_NONFINITE) worst = st;
+      else if (st != MD_OK) return st;
+    }
+    st = md_step(c, 1);
+    return st != MD_OK ? st : (worst != MD_OK ? fail(worst, "records hold NaN/Inf") : MD_OK);
   }
-  if (out->n_nonfinite > 0)
-    return fail(MD_ERR_NONFINITE, "%lld records hold NaN/Inf", (long long)out->n_nonfinite);
-  return MD_OK;
+  st = ensure_scratch(c);
+  if (st != MD_OK) return st;
+  const size_t nt = static_cast<size_t>(c->n_total);
+  if (!c->d_diag_rec) MD_CUDA(dev_alloc(&c->d_diag_rec, 6 * nt));
+  if (c->nseg_used > 1 && c->part_phi_seg < c->nseg_used) {
+    cudaFree(c->d_part_phi);
+    c->d_part_phi = nullptr;
+    MD_CUDA(dev_alloc(&c->d_part_phi, static_cast<size_t>(c->nseg_used) * nt));
+    c->part_phi_seg = c->nseg_used;
+  }
+  MD_CUDA(cudaMemsetAsync(c->d_diag_rec, 0, sizeof(double) * 6 * nt, c->stream));
+  long long step = 0;
+  MD_CUDA(cudaMemcpyAsync(&step, c->d_step, sizeof(step), cudaMemcpyDeviceToHost, c->stream));
+  md::StepArgs a = step_args(c);
+  a.diag_rec = c->d_diag_rec;
+  a.part_phi = c->d_part_phi;
+  MD_CUDA(k.launch_step_pot(a, c->grid, c->stream));
+  for (int ci = 0; ci < c->n_clusters; ++ci) {
+    md::DiagArgs d;
+    d.c = c->cl[ci];
+    d.x = c->d_x[0];
+    d.y = c->d_x[1];
+    d.z = c->d_x[2];
+    d.ux = c->d_u[0];
+    d.uy = c->d_u[1];
+    d.uz = c->d_u[2];
+    d.qm = c->d_qm;
+    d.w = c->d_w;
+    d.mass = c->d_mass;
+    d.zq = c->d_z;
+    d.kind = c->d_kind;
+    d.e = nullptr;
+    d.phi = nullptr;
+    d.step = c->d_step;
+    d.part = c->d_part;
+    d.rec = c->d_diag_rec;
+    MD_CUDA(md::launch_diag(d, c->diag_blocks, c->d_diag, c->stream));
+    MD_CUDA(cudaMemcpyAsync(c->h_diag, c->d_diag, sizeof(md::DiagPartial),
+                            cudaMemcpyDeviceToHost, c->stream));
+    MD_CUDA(cudaStreamSynchronize(c->stream));
+    st = check_device_error(c);
+    if (st != MD_OK) return st;
+    st = fill_diag(*c->h_diag, step, c->cl[ci], &out[ci]);
+    if (st == MD_ERR_NONFINITE) worst = st;
+  }
+  return worst != MD_OK ? fail(worst, "records hold NaN/Inf") : MD_OK;
 }
 
 md_status md_get_particles(md_ctx* c, int32_t cluster, md_particles* out) {

@@ -100,6 +100,14 @@ struct StepArgs {
   unsigned long long* det_hist;
   unsigned char* det_crossed;
   const double* mass;
+  // diagnostic steps only (the POT step kernel): per record (status, ke, pe,
+  // px, py, pz) at t_n, [n_total][6], and the potential partials of split
+  // sources, [nseg][n_total]
+  double* diag_rec;
+  double* part_phi;
+  const int* zq;
+  const unsigned char* kind;
+  const double* w;
 };
 
 // Arguments of the ionization kernels of one cluster.
@@ -195,6 +203,9 @@ struct DiagArgs {
   const double* phi;  // potential [n_pad]
   const long long* step;
   DiagPartial* part;  // [gridDim.x]
+  // per-record diagnostics of a diagnostic step ([n_total][6], status, ke,
+  // pe, px, py, pz), used instead of e / phi and the kick; or nullptr
+  const double* rec = nullptr;
 };
 
 struct UploadArgs {

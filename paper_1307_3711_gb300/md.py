@@ -104,6 +104,7 @@ _SIGS = {
     "md_sync": (_st, [_ctx_p]),
     "md_diagnostics": (_st, [_ctx_p, C.c_int32, C.POINTER(Diag)]),
     "md_count_active": (_st, [_ctx_p, C.c_int32, C.POINTER(C.c_int64)]),
+    "md_step_diag": (_st, [_ctx_p, C.POINTER(Diag)]),
     "md_get_particles": (_st, [_ctx_p, C.c_int32, C.POINTER(Particles)]),
     "md_set_particles": (_st, [_ctx_p, C.c_int32, C.POINTER(Particles)]),
     "md_get_fields": (_st, [_ctx_p, C.c_int32, _p, _p]),
@@ -294,14 +295,24 @@ class Context:
         _check(_lib.md_get_step(self._h, C.byref(v)))
         return int(v.value)
 
-    def diagnostics(self, cluster: int = 0) -> dict:
-        d = Diag()
-        _check(_lib.md_diagnostics(self._h, cluster, C.byref(d)))
+    @staticmethod
+    def _diag_dict(d: Diag) -> dict:
         return {"step": d.step, "t": d.t, "ke": d.ke, "ke_ions": d.ke_ions,
                 "ke_electrons": d.ke_electrons, "pe": d.pe, "total": d.total,
                 "p": np.array(d.p[:]), "n_active": d.n_active, "n_nonfinite": d.n_nonfinite,
                 "charge_count": np.array(d.charge_count[:]),
                 "charge_weight": np.array(d.charge_weight[:])}
+
+    def diagnostics(self, cluster: int = 0) -> dict:
+        d = Diag()
+        _check(_lib.md_diagnostics(self._h, cluster, C.byref(d)))
+        return self._diag_dict(d)
+
+    def step_diag(self) -> list:
+        """One step that also returns every cluster's diagnostics at its start."""
+        arr = (Diag * len(self._cfgs))()
+        _check(_lib.md_step_diag(self._h, arr))
+        return [self._diag_dict(d) for d in arr]
 
     def get_particles(self, cluster: int = 0, out: HostParticles | None = None) -> HostParticles:
         out = out or HostParticles.empty(self.sizes[cluster])

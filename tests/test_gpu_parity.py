@@ -237,6 +237,69 @@ def test_diagnostics_parity_and_energy_conservation_2k(md):
     assert d1["charge_count"][1] == 1000
 
 
+@pytest.mark.parametrize("split", [1, 4])
+def test_diagnostic_step_equals_diagnostics_then_step(md, split):
+    """md_step_diag sums the potential inside the step's Coulomb pass and takes
+    the kinetic energy from the step's own kick: its diagnostics are those of
+    md_diagnostics before the step (to FP32 summation order; the oracle's at
+    step 0 for the 2k case), and the step it takes leaves the same state bit
+    for bit, with one or with 4 source segments per i-block, for a context of
+    two clusters."""
+    ws = [synth.plain_fp64_2k(0), synth.xe3_cluster(30000, seed=9)]
+    cfgs = [md.config_from_workload(w) for w in ws]
+    out = []
+    for fused in (False, True):
+        with md.Context(cfgs, [md.HostParticles.from_cluster(w.cluster) for w in ws]) as ctx:
+            ctx.set_tuning(128, 4, 512, 0, split, 0)
+            ctx.step(3)
+            if fused:
+                d = ctx.step_diag()
+            else:
+                d = [ctx.diagnostics(k) for k in range(len(ws))]
+                ctx.step(1)
+            g = [ctx.get_particles(k) for k in range(len(ws))]
+            out.append((d, g, ctx.step_index()))
+    (da, ga, sa), (db, gb, sb) = out
+    assert sa == sb == 4
+    for k in range(len(ws)):
+        for f in ("x", "u"):
+            assert np.array_equal(getattr(ga[k], f), getattr(gb[k], f)), (k, f)
+        assert db[k]["step"] == da[k]["step"] == 3 and db[k]["t"] == da[k]["t"]
+        scale = abs(da[k]["pe"]) + da[k]["ke"]
+        assert abs(db[k]["pe"] - da[k]["pe"]) < 1e-6 * scale, (k, db[k]["pe"], da[k]["pe"])
+        assert abs(db[k]["ke"] - da[k]["ke"]) < 1e-6 * scale, (k, db[k]["ke"], da[k]["ke"])
+        pscale = np.sum(ga[k].w * ga[k].mass * np.linalg.norm(ga[k].u, axis=1))
+        assert np.abs(db[k]["p"] - da[k]["p"]).max() < 1e-8 * pscale
+        assert db[k]["n_active"] == da[k]["n_active"]
+        assert np.array_equal(db[k]["charge_count"], da[k]["charge_count"])
+    # the 2k case at step 0 against the oracle, through the diagnostic step
+    w = ws[0]
+    with ctx_for(md, w) as ctx:
+        d0 = ctx.step_diag()[0]
+    o0 = oracle.diagnostics(oracle_state(w.cluster), oracle_params(w))
+    assert d0["pe"] == pytest.approx(o0["pe"], rel=1e-5)
+    assert abs(d0["ke"] - o0["ke"]) < 1e-5 * abs(o0["pe"])
+
+
+def test_diagnostic_step_falls_back_with_detectors(md):
+    """With detectors set, md_step_diag is md_diagnostics followed by
+    md_step(1): the same numbers and the same state."""
+    w = synth.xe3_cluster(4000, seed=10)
+    out = []
+    for fused in (False, True):
+        with ctx_for(md, w) as ctx:
+            ctx.set_detectors(0, 5 * synth.nm_to_len(2.0))
+            if fused:
+                d = ctx.step_diag()[0]
+            else:
+                d = ctx.diagnostics(0)
+                ctx.step(1)
+            out.append((d, ctx.get_particles(0)))
+    (da, ga), (db, gb) = out
+    assert da["pe"] == db["pe"] and da["ke"] == db["ke"]
+    assert np.array_equal(ga.x, gb.x) and np.array_equal(ga.u, gb.u)
+
+
 @pytest.mark.parametrize("pol", [0, 1])
 def test_free_electron_light_cone_invariant_gpu(md, pol):
     """One electron in the laser of Eqs. 4-9 (b0 = a0): gamma - u_z = 1 and
