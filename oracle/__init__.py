@@ -54,7 +54,7 @@ class Params(C.Structure):
                 ("dt", C.c_double), ("eps", C.c_double), ("kc", C.c_double),
                 ("box", C.c_double), ("t_switch", C.c_double),
                 ("pol", C.c_int), ("env", C.c_int), ("boundary", C.c_int),
-                ("pad", C.c_int)]
+                ("min_image", C.c_int)]
 
 
 def lib():
@@ -79,6 +79,8 @@ def lib():
             L.or_laser_fields.argtypes = [d, d, i, i, d, p, p]
             L.or_coulomb_field.restype = None
             L.or_coulomb_field.argtypes = [i, p, p, i, p, p, d, d, p, p, i]
+            L.or_coulomb_field_mi.restype = None
+            L.or_coulomb_field_mi.argtypes = [i, p, p, i, p, p, d, d, d, p, p, i]
             L.or_boris_kick.restype = None
             L.or_boris_kick.argtypes = [p, p, p, d, d]
             L.or_drift.restype = None
@@ -170,10 +172,11 @@ def laser_fields(t: float, a0: float, pol: int, env: int, tau: float):
 # ------------------------------------------------------------ direct sum ---
 
 def coulomb_field(x_targets, x_sources, q_sources, eps, kc, self_idx=None,
-                  potential=False, nthreads=1):
+                  potential=False, nthreads=1, box=0.0):
     """Softened direct-sum field (and potential) at the targets (Sec. II: the
     Coulomb force of all other charged particles).  ``self_idx[i]`` is the
-    source index of target i, excluded from its sum (-1: none)."""
+    source index of target i, excluded from its sum (-1: none).  box > 0:
+    minimum-image displacements in the periodic cube of that side."""
     xt = _f64(x_targets, (-1, 3))
     xs = _f64(x_sources, (-1, 3))
     qs = _f64(q_sources).ravel()
@@ -185,17 +188,22 @@ def coulomb_field(x_targets, x_sources, q_sources, eps, kc, self_idx=None,
     if self_idx is not None:
         si = np.ascontiguousarray(self_idx, dtype=np.int64)
         assert si.shape[0] == nt
-    lib().or_coulomb_field(nt, _ptr(xt), _ptr(si) if si is not None else None, ns,
-                           _ptr(xs), _ptr(qs), float(eps), float(kc), _ptr(e),
-                           _ptr(phi) if phi is not None else None, int(nthreads))
+    if box > 0.0:
+        lib().or_coulomb_field_mi(nt, _ptr(xt), _ptr(si) if si is not None else None, ns,
+                                  _ptr(xs), _ptr(qs), float(eps), float(kc), float(box), _ptr(e),
+                                  _ptr(phi) if phi is not None else None, int(nthreads))
+    else:
+        lib().or_coulomb_field(nt, _ptr(xt), _ptr(si) if si is not None else None, ns,
+                               _ptr(xs), _ptr(qs), float(eps), float(kc), _ptr(e),
+                               _ptr(phi) if phi is not None else None, int(nthreads))
     return (e, phi) if potential else e
 
 
-def self_field(x, q, eps, kc, potential=False, nthreads=1):
-    """Field of every particle from all the others."""
+def self_field(x, q, eps, kc, potential=False, nthreads=1, box=0.0):
+    """Field of every particle from all the others (box > 0: minimum image)."""
     n = len(q)
     return coulomb_field(x, x, q, eps, kc, np.arange(n, dtype=np.int64),
-                         potential=potential, nthreads=nthreads)
+                         potential=potential, nthreads=nthreads, box=box)
 
 
 # ----------------------------------------------------------------- Boris ---
@@ -247,10 +255,10 @@ class State:
 
 def make_params(a0=0.0, tau=1.0, t0=0.0, dt=0.02, eps=0.0, kc=None, box=0.0,
                 t_switch=0.0, pol=0, env=ENV_SIN2, boundary=BOUNDARY_OPEN,
-                lambda_um=0.8):
+                lambda_um=0.8, min_image=0):
     if kc is None:
         kc = coulomb_constant(lambda_um)
-    return Params(a0, tau, t0, dt, eps, kc, box, t_switch, pol, env, boundary, 0)
+    return Params(a0, tau, t0, dt, eps, kc, box, t_switch, pol, env, boundary, int(min_image))
 
 
 def md_steps(state: State, params: Params, nsteps: int, nthreads: int = 1) -> State:

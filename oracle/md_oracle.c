@@ -154,6 +154,46 @@ void or_coulomb_field(int nt, const double *xt, const int64_t *self_idx,
     }
 }
 
+/* The same sum with minimum-image displacements in a periodic cube of side
+ * box (the "optional minimum-image forces" of a periodic boundary, Sec. II,
+ * boundary paragraph): each component of x_i - x_j is reduced to the nearest
+ * periodic image, d - box * nearbyint(d / box) (ties to even), before the
+ * softened pair term is formed.  box <= 0 gives the open sum. */
+void or_coulomb_field_mi(int nt, const double *xt, const int64_t *self_idx,
+                         int ns, const double *xs, const double *qs,
+                         double eps, double kc, double box, double *e_out,
+                         double *phi_out, int nthreads)
+{
+    double eps2 = eps * eps;
+    int i;
+#ifdef _OPENMP
+    if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads)
+#endif
+    for (i = 0; i < nt; ++i) {
+        double xi = xt[3 * i], yi = xt[3 * i + 1], zi = xt[3 * i + 2];
+        int64_t self = self_idx ? self_idx[i] : -1;
+        double ex = 0.0, ey = 0.0, ez = 0.0, ph = 0.0;
+        for (int j = 0; j < ns; ++j) {
+            if (qs[j] == 0.0 || (int64_t)j == self) continue;
+            double d[3] = {xi - xs[3 * j], yi - xs[3 * j + 1], zi - xs[3 * j + 2]};
+            if (box > 0.0)
+                for (int k = 0; k < 3; ++k) d[k] -= box * nearbyint(d[k] / box);
+            double rm2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + eps2;
+            double rm = sqrt(rm2);
+            double inv_rm3 = 1.0 / (rm2 * rm);
+            ex += qs[j] * d[0] * inv_rm3;
+            ey += qs[j] * d[1] * inv_rm3;
+            ez += qs[j] * d[2] * inv_rm3;
+            ph += qs[j] / rm;
+        }
+        e_out[3 * i] = kc * ex;
+        e_out[3 * i + 1] = kc * ey;
+        e_out[3 * i + 2] = kc * ez;
+        if (phi_out) phi_out[i] = kc * ph;
+    }
+}
+
 /* --------------------------------------------------------------- Boris */
 
 /* One relativistic Boris kick (Sec. II, "standard Boris leap frog"):
@@ -205,8 +245,21 @@ static void or_boundary(double x[3], int mode, double box, double t, double t_sw
 
 typedef struct {
     double a0, tau, t0, dt, eps, kc, box, t_switch;
-    int pol, env, boundary, pad;
+    int pol, env, boundary;
+    int min_image; /* 1: minimum-image forces while the boundary is periodic */
 } or_params;
+
+/* The Coulomb field of a step at time t: minimum-image while the boundary is
+ * periodic (mode 1, or mode 2 before t_switch) and min_image is set. */
+static void or_step_field(int n, const double *x, const int64_t *self_idx, const double *q,
+                          const or_params *p, double t, double *e, double *phi, int nthreads)
+{
+    int periodic = p->boundary == 1 || (p->boundary == 2 && t < p->t_switch);
+    if (p->min_image && periodic)
+        or_coulomb_field_mi(n, x, self_idx, n, x, q, p->eps, p->kc, p->box, e, phi, nthreads);
+    else
+        or_coulomb_field(n, x, self_idx, n, x, q, p->eps, p->kc, e, phi, nthreads);
+}
 
 /* nsteps full MD steps (Sec. II) on n particles, starting at step index
  * step0 (t_n = t0 + n dt).  x, u: [n][3] in/out; qm = z/m; q = w z (macro
@@ -223,7 +276,7 @@ void or_md_steps(int n, double *x, double *u, const double *qm, const double *q,
         double t = p->t0 + (double)step * p->dt;
         double a[3], b[3];
         or_laser_fields(t, p->a0, p->pol, p->env, p->tau, a, b);
-        or_coulomb_field(n, x, self_idx, n, x, q, p->eps, p->kc, e, NULL, nthreads);
+        or_step_field(n, x, self_idx, q, p, t, e, NULL, nthreads);
         for (int i = 0; i < n; ++i) {
             if (!active[i]) continue;
             double et[3] = {e[3 * i] + a[0], e[3 * i + 1] + a[1], e[3 * i + 2] + a[2]};
@@ -250,7 +303,7 @@ void or_diagnostics(int n, const double *x, const double *u, const double *qm,
     double a[3], b[3];
     for (int i = 0; i < n; ++i) self_idx[i] = i;
     or_laser_fields(t, p->a0, p->pol, p->env, p->tau, a, b);
-    or_coulomb_field(n, x, self_idx, n, x, q, p->eps, p->kc, e, phi, nthreads);
+    or_step_field(n, x, self_idx, q, p, t, e, phi, nthreads);
     double ke = 0, kei = 0, kee = 0, pe = 0, px = 0, py = 0, pz = 0, na = 0;
     for (int i = 0; i < n; ++i) {
         if (!active[i]) continue;

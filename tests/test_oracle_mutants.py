@@ -46,6 +46,12 @@ MUTANTS = [
     ("eq1_wrong_power", "return q * q * q;", "return q * q;"),
     ("self_not_excluded", "if ((int64_t)j == self || qs[j] == 0.0) continue;",
      "if (qs[j] == 0.0) continue;"),
+    ("min_image_floor", "d[k] -= box * nearbyint(d[k] / box);", "d[k] -= box * floor(d[k] / box);"),
+    ("min_image_two_axes", "for (int k = 0; k < 3; ++k) d[k] -= box",
+     "for (int k = 0; k < 2; ++k) d[k] -= box"),
+    ("min_image_not_in_steps", "if (p->min_image && periodic)", "if (p->min_image && !periodic)"),
+    ("min_image_softening", "double rm2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + eps2;",
+     "double rm2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];"),
 ]
 
 # (name, file, exact text, replacement, pin file) for the ionization and

@@ -380,3 +380,94 @@ def test_coulomb_explosion_spectrum_of_uniform_ion_sphere():
     assert (s ** 2).mean() == pytest.approx(3 / 7, abs=0.02)
     ks = stats.kstest(np.clip(s, 0, 1), lambda v: np.clip(v, 0, 1) ** 1.5)
     assert ks.pvalue > 1e-3
+
+
+# ---------------------------------------------- minimum-image forces (periodic)
+
+def _wrap(x, box):
+    """Positions into [-box/2, box/2) (the periodic boundary's wrap)."""
+    return x - box * np.floor((x + 0.5 * box) / box)
+
+
+def test_min_image_pair_across_a_face_is_the_open_pair_at_its_image():
+    """Two charges near opposite faces of the cube interact through their
+    nearest images: the field and potential equal the open-boundary ones with
+    the second charge moved by one box length, on every axis."""
+    box, eps = 1.0, 1e-3
+    for ax in range(3):
+        x = np.zeros((2, 3))
+        x[0, ax], x[1, ax] = 0.5 * box - 0.01, -0.5 * box + 0.02
+        x[1, (ax + 1) % 3] = 0.003
+        q = np.array([2.0, -1.0])
+        e_mi, p_mi = oracle.self_field(x, q, eps, KC, potential=True, box=box)
+        xi = x.copy()
+        xi[1, ax] += box
+        e_op, p_op = oracle.self_field(xi, q, eps, KC, potential=True)
+        np.testing.assert_allclose(e_mi, e_op, rtol=1e-12)
+        np.testing.assert_allclose(p_mi, p_op, rtol=1e-12)
+        # the open sum through the box is a different, much weaker force
+        e_far = oracle.self_field(x, q, eps, KC)
+        assert np.linalg.norm(e_far[0]) < 1e-3 * np.linalg.norm(e_mi[0])
+
+
+def test_min_image_field_is_invariant_under_periodic_translation():
+    """Shifting every charge by the same vector and wrapping it back into the
+    cube leaves every minimum-image field and potential unchanged (to FP64
+    rounding); the open-boundary field of the same system changes."""
+    rng = np.random.default_rng(41)
+    box, eps, n = 1.0, 2e-3, 300
+    x = rng.uniform(-0.5, 0.5, size=(n, 3)) * box
+    q = rng.choice([-1.0, 1.0, 3.0], size=n)
+    e0, p0 = oracle.self_field(x, q, eps, KC, potential=True, box=box)
+    for s in ([0.31, -0.17, 0.44], [-0.5, 0.5, 0.25]):
+        xs = _wrap(x + np.array(s) * box, box)
+        e1, p1 = oracle.self_field(xs, q, eps, KC, potential=True, box=box)
+        scale = np.abs(e0).max()
+        assert np.abs(e1 - e0).max() < 1e-9 * scale
+        assert np.abs(p1 - p0).max() < 1e-9 * np.abs(p0).max()
+    e_open = oracle.self_field(xs, q, eps, KC)
+    assert np.abs(e_open - e0).max() > 1e-2 * np.abs(e0).max()
+
+
+def test_min_image_newton_third_law_and_small_systems():
+    """Minimum-image pair forces are antisymmetric (sum q E = 0); a system that
+    fits in a cube of half the box side has exactly its open-boundary field."""
+    rng = np.random.default_rng(42)
+    box, eps, n = 1.0, 2e-3, 200
+    x = rng.uniform(-0.5, 0.5, size=(n, 3)) * box
+    q = rng.choice([-1.0, 2.0], size=n)
+    e = oracle.self_field(x, q, eps, KC, box=box)
+    f = q[:, None] * e
+    assert np.abs(f.sum(axis=0)).max() < 1e-12 * np.abs(f).sum()
+    xs = rng.uniform(-0.2, 0.2, size=(n, 3)) * box
+    assert np.array_equal(oracle.self_field(xs, q, eps, KC, box=box),
+                          oracle.self_field(xs, q, eps, KC))
+
+
+def test_min_image_steps_follow_the_open_pair_at_its_image():
+    """md_steps with a periodic boundary and minimum-image forces: two charges
+    near opposite faces move exactly as the open-boundary pair with the second
+    charge one box length away, up to the wrap.  Without minimum image (or
+    once a mixed boundary has switched to open) they barely feel each other."""
+    box, eps, dt, n_steps = 1.0, 1e-3, 0.05, 40
+    x = np.array([[0.5 * box - 0.01, 0.0, 0.0], [-0.5 * box + 0.02, 0.002, 0.0]])
+    u = np.zeros((2, 3))
+    z, m, w = [1, -1], [5.0, 1.0], [1.0, 1.0]
+    st = oracle.State(x, u, z, m, w)
+    p = oracle.make_params(dt=dt, eps=eps, box=box, boundary=oracle.BOUNDARY_PERIODIC,
+                           env=oracle.ENV_FLAT, min_image=1)
+    oracle.md_steps(st, p, n_steps)
+    xi = x.copy()
+    xi[1, 0] += box
+    so = oracle.State(xi, u, z, m, w)
+    po = oracle.make_params(dt=dt, eps=eps, env=oracle.ENV_FLAT)
+    oracle.md_steps(so, po, n_steps)
+    d = _wrap(st.x - so.x, box)     # equal up to whole boxes
+    assert np.abs(d).max() < 1e-12
+    np.testing.assert_allclose(st.u, so.u, rtol=1e-10, atol=1e-14)
+    assert np.abs(st.u).max() > 1e-5
+    sn = oracle.State(x, u, z, m, w)
+    pn = oracle.make_params(dt=dt, eps=eps, box=box, boundary=oracle.BOUNDARY_MIXED,
+                            t_switch=0.0, env=oracle.ENV_FLAT, min_image=1)
+    oracle.md_steps(sn, pn, n_steps)
+    assert np.abs(sn.u).max() < 1e-3 * np.abs(st.u).max()
