@@ -63,7 +63,8 @@ enum {
 /* Boundary of the simulation box (Sec. II, first paragraph). */
 enum {
     MD_BOUNDARY_OPEN = 0,
-    MD_BOUNDARY_PERIODIC = 1, /* positions wrapped into the cube [-box/2, box/2)^3, no image forces */
+    MD_BOUNDARY_PERIODIC = 1, /* positions wrapped into the cube [-box/2, box/2)^3; image
+                                 forces only with md_config.min_image */
     MD_BOUNDARY_MIXED = 2     /* periodic while t < t_switch, open afterwards */
 };
 
@@ -93,7 +94,11 @@ typedef struct {
                              0: passes only through md_ionize (dt_ion = dt) */
     int32_t zmax;         /* highest charge state, 1..16 */
     int32_t n_ions;       /* records [0, n_ions) are the atoms/ions that can ionize */
-    int32_t reserved;     /* must be 0 */
+    int32_t min_image;    /* 1: while the boundary is periodic (PERIODIC, or MIXED before
+                             t_switch) every pair interacts through its nearest periodic
+                             image (each displacement component reduced to
+                             [-box/2, box/2]); 0: no image forces.  Not with ionization
+                             (rate_model != 0) or detectors: MD_ERR_ARG / MD_ERR_STATE */
     int64_t slot_base;    /* records [slot_base, slot_base + zmax n_ions) are electron
                              slots (INACTIVE until used); freed electrons fill them
                              densely, after the last active one (see md_ionize) */
@@ -192,8 +197,9 @@ md_status md_diagnostics(md_ctx *ctx, int32_t cluster, md_diag *out);
  * step's Coulomb pass (one more FP32 add per pair) and the kinetic energy at
  * integer time comes from the step's own kick, so a diagnosed step costs
  * about one step instead of two N^2 passes.  Contexts with ionization or
- * detectors and the packed kernel configurations use md_diagnostics and
- * md_step instead (same results up to the order of the FP32 sums).
+ * detectors or minimum-image forces, and the packed kernel configurations,
+ * use md_diagnostics and md_step instead (same results up to the order of
+ * the FP32 sums).
  * out: caller-owned md_diag[n_clusters].  Synchronous.  Errors: MD_ERR_ARG,
  * MD_ERR_NONFINITE (after the step) as md_diagnostics. */
 md_status md_step_diag(md_ctx *ctx, md_diag *out);

@@ -317,16 +317,31 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
   s = t;
 }
 
+// Minimum-image reduction of one displacement component in a periodic cube
+// of side L (invL = 1/L): d - L rint(d / L), rounded to nearest even on the
+// FP32 pipe by adding and removing 1.5 * 2^23 (|d / L| < 2^22).
+__device__ __forceinline__ float min_image(float d, float L, float invL) {
+  const float k = __fsub_rn(__fmaf_rn(d, invL, 12582912.0f), 12582912.0f);
+  return __fmaf_rn(-L, k, d);
+}
+
 // One source against R targets: acc += Q_j (x_j - x_i) / (r^2 + eps^2)^{3/2}
-// (and phi += Q_j / sqrt(r^2 + eps^2)); Q_j already carries K_C.
-template <int R, bool POT>
+// (and phi += Q_j / sqrt(r^2 + eps^2)); Q_j already carries K_C.  MI: the
+// displacement is the minimum image in the periodic cube of side L.
+template <int R, bool POT, bool MI = false>
 __device__ __forceinline__ void pair(const float4 p, const float (&xi)[R], const float (&yi)[R],
-                                     const float (&zi)[R], float eps2, Acc<R, POT>& a) {
+                                     const float (&zi)[R], float eps2, Acc<R, POT>& a,
+                                     float L = 0.0f, float invL = 0.0f) {
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    const float dx = p.x - xi[r];
-    const float dy = p.y - yi[r];
-    const float dz = p.z - zi[r];
+    float dx = p.x - xi[r];
+    float dy = p.y - yi[r];
+    float dz = p.z - zi[r];
+    if constexpr (MI) {
+      dx = min_image(dx, L, invL);
+      dy = min_image(dy, L, invL);
+      dz = min_image(dz, L, invL);
+    }
     float r2 = fmaf(dx, dx, eps2);
     r2 = fmaf(dy, dy, r2);
     r2 = fmaf(dz, dz, r2);
@@ -344,14 +359,20 @@ __device__ __forceinline__ void pair(const float4 p, const float (&xi)[R], const
 // The same for a tile whose sources all carry one charge Q: the sum of
 // (x_j - x_i)/(r^2+eps^2)^{3/2} (and 1/sqrt(r^2+eps^2)) without Q, which then
 // multiplies the tile partial once (fold_q).  One FP32 multiply less per pair.
-template <int R, bool POT>
+template <int R, bool POT, bool MI = false>
 __device__ __forceinline__ void pair_u(const float4 p, const float (&xi)[R], const float (&yi)[R],
-                                       const float (&zi)[R], float eps2, Acc<R, POT>& a) {
+                                       const float (&zi)[R], float eps2, Acc<R, POT>& a,
+                                       float L = 0.0f, float invL = 0.0f) {
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    const float dx = p.x - xi[r];
-    const float dy = p.y - yi[r];
-    const float dz = p.z - zi[r];
+    float dx = p.x - xi[r];
+    float dy = p.y - yi[r];
+    float dz = p.z - zi[r];
+    if constexpr (MI) {
+      dx = min_image(dx, L, invL);
+      dy = min_image(dy, L, invL);
+      dz = min_image(dz, L, invL);
+    }
     float r2 = fmaf(dx, dx, eps2);
     r2 = fmaf(dy, dy, r2);
     r2 = fmaf(dz, dz, r2);
@@ -449,14 +470,15 @@ __device__ __forceinline__ int next_live_tile(const unsigned char* live, long lo
 // consumed so far (sets the barrier phases).  Returns false (uniformly across
 // the CTA) if a wait ran out of budget; the error bit is then set and this
 // CTA's copies in flight have been waited for (bounded).
-template <int THREADS, int R, int TILE, int STAGES, bool POT>
+template <int THREADS, int R, int TILE, int STAGES, bool POT, bool MI = false>
 __device__ __forceinline__ bool sum_sources(Stage<TILE, STAGES>& sm, unsigned& it,
                                             const float4* __restrict__ src, long long ns,
                                             const float (&xi)[R], const float (&yi)[R],
                                             const float (&zi)[R], float eps2, Acc<R, POT>& acc,
                                             int* err, int* s_abort,
                                             const unsigned char* live = nullptr,
-                                            long long gbase = 0) {
+                                            long long gbase = 0, float L = 0.0f,
+                                            float invL = 0.0f) {
   const int ntiles = static_cast<int>((ns + TILE - 1) / TILE);
   // consumers and the issuing thread walk the same sequence of live tiles;
   // the k-th live tile goes through ring stage (it + k) % STAGES
@@ -491,7 +513,7 @@ __device__ __forceinline__ bool sum_sources(Stage<TILE, STAGES>& sm, unsigned& i
           for (; j + 8 <= cnt; j += 8) {
 #pragma unroll
             for (int q = 0; q < 8; ++q)
-              pair_u<R, POT>(lds_f4(tile + 16u * (j + q)), xi, yi, zi, eps2, acc);
+              pair_u<R, POT, MI>(lds_f4(tile + 16u * (j + q)), xi, yi, zi, eps2, acc, L, invL);
             if (POT) {
 #pragma unroll
               for (int r = 0; r < R; ++r) {
@@ -500,7 +522,8 @@ __device__ __forceinline__ bool sum_sources(Stage<TILE, STAGES>& sm, unsigned& i
               }
             }
           }
-          for (; j < cnt; ++j) pair_u<R, POT>(lds_f4(tile + 16u * j), xi, yi, zi, eps2, acc);
+          for (; j < cnt; ++j)
+            pair_u<R, POT, MI>(lds_f4(tile + 16u * j), xi, yi, zi, eps2, acc, L, invL);
           fold_q<R, POT>(acc, qt);
         }
       } else {
@@ -508,7 +531,7 @@ __device__ __forceinline__ bool sum_sources(Stage<TILE, STAGES>& sm, unsigned& i
         for (; j + 8 <= cnt; j += 8) {
 #pragma unroll
           for (int q = 0; q < 8; ++q)
-            pair<R, POT>(lds_f4(tile + 16u * (j + q)), xi, yi, zi, eps2, acc);
+            pair<R, POT, MI>(lds_f4(tile + 16u * (j + q)), xi, yi, zi, eps2, acc, L, invL);
           if (POT) {
             // potential terms of one species share a sign: fold them often so
             // the FP32 partial stays small against a cancelling total
@@ -519,7 +542,8 @@ __device__ __forceinline__ bool sum_sources(Stage<TILE, STAGES>& sm, unsigned& i
             }
           }
         }
-        for (; j < cnt; ++j) pair<R, POT>(lds_f4(tile + 16u * j), xi, yi, zi, eps2, acc);
+        for (; j < cnt; ++j)
+          pair<R, POT, MI>(lds_f4(tile + 16u * j), xi, yi, zi, eps2, acc, L, invL);
         fold<R, POT>(acc);
       }
     }
@@ -964,10 +988,14 @@ __device__ __forceinline__ void push_record(const StepArgs& a, const ClusterDev&
 // POT (scalar path only): a diagnostic step, which also sums the potential
 // phi_i beside the field (split segments add their phi partials in order)
 // and records every record's diagnostics at t_n (push_record's DIAG).
+//
+// MI (scalar path only): clusters whose min_image flag is set sum
+// minimum-image displacements while their boundary is periodic.
 template <int THREADS, int R, int TILE, int STAGES, bool PACK, int MINB, bool DET,
-          bool POT = false>
+          bool POT = false, bool MI = false>
 __global__ void __launch_bounds__(THREADS, MINB) k_step(const StepArgs a) {
   static_assert(!(PACK && POT), "diagnostic steps use the scalar path");
+  static_assert(!(PACK && MI), "minimum-image forces use the scalar path");
   __shared__ Stage<TILE, STAGES> sm;
   __shared__ DupTile<PACK ? TILE : 1> dup;
   __shared__ KahanSmem<PACK ? R / 2 : 1, PACK ? THREADS : 1, false> ks;
@@ -1029,9 +1057,23 @@ __global__ void __launch_bounds__(THREADS, MINB) k_step(const StepArgs a) {
             a.src_live, s_c.off + j0);
       } else {
         acc.zero();
-        ok = sum_sources<THREADS, R, TILE, STAGES, POT>(sm, it, cur + s_c.off + j0, jn, xi, yi,
-                                                        zi, s_c.eps2, acc, a.err, &s_abort,
-                                                        a.src_live, s_c.off + j0);
+        bool mi = false;
+        if constexpr (MI) {
+          // minimum-image forces while this cluster's boundary is periodic at t_n
+          const double t_n = s_c.t0 + static_cast<double>(step) * s_c.dt;
+          mi = a.min_image && a.min_image[s_un.cluster] &&
+               (s_c.boundary == 1 || (s_c.boundary == 2 && t_n < s_c.t_switch));
+        }
+        if (mi) {
+          const float L = static_cast<float>(s_c.box);
+          ok = sum_sources<THREADS, R, TILE, STAGES, POT, true>(
+              sm, it, cur + s_c.off + j0, jn, xi, yi, zi, s_c.eps2, acc, a.err, &s_abort,
+              a.src_live, s_c.off + j0, L, 1.0f / L);
+        } else {
+          ok = sum_sources<THREADS, R, TILE, STAGES, POT>(sm, it, cur + s_c.off + j0, jn, xi, yi,
+                                                          zi, s_c.eps2, acc, a.err, &s_abort,
+                                                          a.src_live, s_c.off + j0);
+        }
       }
       if (!ok) return;
 
@@ -1158,7 +1200,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_step(const StepArgs a) {
 // ----------------------------------------------------------- field kernel --
 
 // Field (and potential) at targets from sources; one target block per CTA.
-template <int THREADS, int R, int TILE, int STAGES, bool POT>
+template <int THREADS, int R, int TILE, int STAGES, bool POT, bool MI = false>
 __global__ void __launch_bounds__(THREADS) k_field(const FieldArgs a) {
   __shared__ Stage<TILE, STAGES> sm;
   __shared__ int s_abort;
@@ -1203,9 +1245,10 @@ __global__ void __launch_bounds__(THREADS) k_field(const FieldArgs a) {
   Acc<R, POT> acc;
   acc.zero();
   unsigned it = 0;
-  if (!sum_sources<THREADS, R, TILE, STAGES, POT>(sm, it, a.src + j0, jn, xi, yi, zi, a.eps2,
-                                                   acc, a.err, &s_abort, a.src_live,
-                                                   a.gbase + j0))
+  if (!sum_sources<THREADS, R, TILE, STAGES, POT, MI>(sm, it, a.src + j0, jn, xi, yi, zi, a.eps2,
+                                                       acc, a.err, &s_abort, a.src_live,
+                                                       a.gbase + j0, a.box,
+                                                       MI ? 1.0f / a.box : 0.0f))
     return;
 #pragma unroll
   for (int r = 0; r < R; ++r) {

@@ -27,6 +27,10 @@ struct KernelConfig {
   // nullptr (packed configurations)
   cudaError_t (*launch_step_pot)(const StepArgs& a, int grid, cudaStream_t s);
   cudaError_t (*max_blocks_per_sm_pot)(int* out);
+  // minimum-image forces for periodic clusters that ask for them, or nullptr
+  // (packed configurations)
+  cudaError_t (*launch_step_mi)(const StepArgs& a, int grid, cudaStream_t s);
+  cudaError_t (*max_blocks_per_sm_mi)(int* out);
 };
 
 const KernelConfig* step_configs(int* count);

@@ -205,6 +205,19 @@ cudaError_t blocks_per_sm_pot_t(int* out) {
       out, k_step<T, R, TILE, ST, false, MB, false, true>, T, 0);
 }
 
+// minimum-image forces (periodic clusters with min_image), scalar path
+template <int T, int R, int TILE, int ST, int MB>
+cudaError_t launch_step_mi_t(const StepArgs& a, int grid, cudaStream_t s) {
+  k_step<T, R, TILE, ST, false, MB, false, false, true><<<grid, T, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int T, int R, int TILE, int ST, int MB>
+cudaError_t blocks_per_sm_mi_t(int* out) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      out, k_step<T, R, TILE, ST, false, MB, false, false, true>, T, 0);
+}
+
 template <int T, int R, int TILE, int ST, bool PK, int MB, bool DET>
 cudaError_t blocks_per_sm_t(int* out) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_step<T, R, TILE, ST, PK, MB, DET>,
@@ -216,14 +229,15 @@ cudaError_t blocks_per_sm_t(int* out) {
   {T, R, TILE, ST, PK, MB, &launch_step_t<T, R, TILE, ST, PK, MB, false>,              \
    &blocks_per_sm_t<T, R, TILE, ST, PK, MB, false>,                                      \
    &launch_step_t<T, R, TILE, ST, PK, MB, true>, &blocks_per_sm_t<T, R, TILE, ST, PK, MB, true>, \
-   nullptr, nullptr}
-// scalar configurations also have the diagnostic step
+   nullptr, nullptr, nullptr, nullptr}
+// scalar configurations also have the diagnostic step and minimum-image forces
 #define MD_STEP_CONFIG_POT(T, R, TILE, ST, MB)                                          \
   {T, R, TILE, ST, false, MB, &launch_step_t<T, R, TILE, ST, false, MB, false>,          \
    &blocks_per_sm_t<T, R, TILE, ST, false, MB, false>,                                   \
    &launch_step_t<T, R, TILE, ST, false, MB, true>,                                      \
    &blocks_per_sm_t<T, R, TILE, ST, false, MB, true>,                                    \
-   &launch_step_pot_t<T, R, TILE, ST, MB>, &blocks_per_sm_pot_t<T, R, TILE, ST, MB>}
+   &launch_step_pot_t<T, R, TILE, ST, MB>, &blocks_per_sm_pot_t<T, R, TILE, ST, MB>,        \
+   &launch_step_mi_t<T, R, TILE, ST, MB>, &blocks_per_sm_mi_t<T, R, TILE, ST, MB>}
 
 // min CTAs per SM = 0 leaves the register budget to ptxas; a positive value
 // caps it at 64K / (threads x value)
@@ -280,10 +294,16 @@ cudaError_t launch_field(const FieldArgs& a, bool potential, cudaStream_t s) {
   const long long per = kFieldThreads * kFieldR;
   const dim3 grid(static_cast<unsigned>((a.nt + per - 1) / per),
                   static_cast<unsigned>(a.nseg > 1 ? a.nseg : 1));
-  if (potential)
+  if (a.box > 0.0f) {
+    if (potential)
+      k_field<kFieldThreads, kFieldR, kFieldTile, 2, true, true><<<grid, kFieldThreads, 0, s>>>(a);
+    else
+      k_field<kFieldThreads, kFieldR, kFieldTile, 2, false, true><<<grid, kFieldThreads, 0, s>>>(a);
+  } else if (potential) {
     k_field<kFieldThreads, kFieldR, kFieldTile, 2, true><<<grid, kFieldThreads, 0, s>>>(a);
-  else
+  } else {
     k_field<kFieldThreads, kFieldR, kFieldTile, 2, false><<<grid, kFieldThreads, 0, s>>>(a);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || a.nseg <= 1) return e;
   k_field_combine<<<static_cast<unsigned>((a.nt + 255) / 256), 256, 0, s>>>(a);

@@ -141,6 +141,10 @@ struct md_ctx {
   unsigned long long* d_det_hist = nullptr;  // [clusters][5][kDetMaxBins + 1]
   unsigned char* d_det_crossed = nullptr;    // [n_total]
   bool det_on = false;                       // some cluster has detectors
+  // minimum-image forces: per-cluster flags (host and device), any set
+  std::vector<unsigned char> min_image;
+  unsigned char* d_min_image = nullptr;
+  bool any_mi = false;
   float* d_mlp = nullptr;              // surrogate parameters (device), if set
 };
 
@@ -210,7 +214,13 @@ md_status validate_config(const md_config& c, int idx) {
     return fail(MD_ERR_ARG, "cluster %d: periodic/mixed boundary needs box > 0", idx);
   if (c.envelope != MD_ENV_FLAT && !(c.tau > 0.0))
     return fail(MD_ERR_ARG, "cluster %d: tau must be > 0", idx);
-  if (c.reserved != 0) return fail(MD_ERR_ARG, "cluster %d: reserved must be 0", idx);
+  if (c.min_image != 0 && c.min_image != 1)
+    return fail(MD_ERR_ARG, "cluster %d: min_image must be 0 or 1", idx);
+  if (c.min_image && c.boundary == 0)
+    return fail(MD_ERR_ARG, "cluster %d: min_image needs a periodic or mixed boundary", idx);
+  if (c.min_image && c.rate_model != 0)
+    return fail(MD_ERR_ARG,
+                "cluster %d: minimum-image forces are not built for ionizing clusters", idx);
   if (c.rate_model < 0 || c.rate_model > 2)
     return fail(MD_ERR_ARG, "cluster %d: rate_model must be 0, 1 or 2", idx);
   return MD_OK;
@@ -317,7 +327,22 @@ md::StepArgs step_args(md_ctx* c) {
   a.zq = c->d_z;
   a.kind = c->d_kind;
   a.w = c->d_w;
+  a.min_image = c->d_min_image;
   return a;
+}
+
+// The step kernel a context with configuration k runs: the minimum-image
+// twin when a cluster asks for image forces, the detector twin when a
+// cluster has detectors, else the plain one.
+cudaError_t launch_step_of(const md_ctx* c, const md::KernelConfig& k, const md::StepArgs& a,
+                           cudaStream_t s) {
+  if (c->any_mi) return k.launch_step_mi ? k.launch_step_mi(a, c->grid, s) : cudaErrorInvalidValue;
+  return c->det_on ? k.launch_step_det(a, c->grid, s) : k.launch_step(a, c->grid, s);
+}
+
+cudaError_t blocks_per_sm_of(const md_ctx* c, const md::KernelConfig& k, int* bps) {
+  if (c->any_mi) return k.max_blocks_per_sm_mi ? k.max_blocks_per_sm_mi(bps) : cudaErrorInvalidValue;
+  return c->det_on ? k.max_blocks_per_sm_det(bps) : k.max_blocks_per_sm(bps);
 }
 
 // A cluster whose ionization pass runs before every step: the pass's field at
@@ -383,8 +408,10 @@ md_status configure(md_ctx* c, int cfg, int ctas_per_sm, int jsplit) {
   if (jsplit < 0 || jsplit > 64) return fail(MD_ERR_ARG, "jsplit must be in [0, 64]");
   const md::KernelConfig& k = cfgs[cfg];
   const long long per = static_cast<long long>(k.threads) * k.r;
+  if (c->any_mi && !k.launch_step_mi)
+    return fail(MD_ERR_ARG, "configuration %d (packed) has no minimum-image kernel", cfg);
   int bps = 0;
-  MD_CUDA(c->det_on ? k.max_blocks_per_sm_det(&bps) : k.max_blocks_per_sm(&bps));
+  MD_CUDA(blocks_per_sm_of(c, k, &bps));
   if (bps < 1) return fail(MD_ERR_CUDA, "kernel configuration %d does not fit on an SM", cfg);
   const int cps = ctas_per_sm > 0 ? std::min(ctas_per_sm, bps) : bps;
   const long long slots = static_cast<long long>(cps) * c->sm_count;
@@ -594,8 +621,7 @@ md_status launch_steps_direct(md_ctx* c, int n) {
       if (e == cudaSuccess) e = launch_ion_pushes(c, a, c->stream);
       if (e != cudaSuccess) return cuda_fail(e, "ionization launch");
     }
-    cudaError_t e = c->det_on ? cfgs[c->cfg].launch_step_det(a, c->grid, c->stream)
-                              : cfgs[c->cfg].launch_step(a, c->grid, c->stream);
+    cudaError_t e = launch_step_of(c, cfgs[c->cfg], a, c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
   }
   return MD_OK;
@@ -613,9 +639,7 @@ md_status build_graph(md_ctx* c) {
     for (int s = 0; s < kGraphSteps && e == cudaSuccess; ++s) {
       if (c->any_ion) e = launch_ion_all(c, 0, cs);
       if (c->any_ion && e == cudaSuccess) e = launch_ion_pushes(c, a, cs);
-      if (e == cudaSuccess)
-        e = c->det_on ? cfgs[c->cfg].launch_step_det(a, c->grid, cs)
-                      : cfgs[c->cfg].launch_step(a, c->grid, cs);
+      if (e == cudaSuccess) e = launch_step_of(c, cfgs[c->cfg], a, cs);
     }
     cudaError_t e2 = cudaStreamEndCapture(cs, &g);
     if (e == cudaSuccess) e = e2;
@@ -654,6 +678,7 @@ void free_ctx(md_ctx* c) {
   cudaFree(c->d_units);
   cudaFree(c->d_diag_rec);
   cudaFree(c->d_part_phi);
+  cudaFree(c->d_min_image);
   cudaFree(c->d_field_part);
   cudaFree(c->d_fpart);
   cudaFree(c->d_iblk_cnt);
@@ -907,6 +932,8 @@ md_status md_init(md_ctx** out, const md_config* cfgs, int32_t n_clusters,
     c->ion.push_back(io);
     c->ion_push.push_back(0);
     if (f.rate_model) c->any_ion = true;
+    c->min_image.push_back(static_cast<unsigned char>(f.min_image));
+    if (f.min_image) c->any_mi = true;
     off += d.n_pad;
     c->max_n = std::max<long long>(c->max_n, parts[i].n);
   }
@@ -941,6 +968,13 @@ md_status md_init(md_ctx** out, const md_config* cfgs, int32_t n_clusters,
   if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
   e = cudaMallocHost(reinterpret_cast<void**>(&c->h_raw), c->raw_bytes);
   if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMallocHost"));
+  if (c->any_mi) {
+    if (dev_alloc(&c->d_min_image, static_cast<size_t>(n_clusters)) != cudaSuccess)
+      return bail(fail(MD_ERR_OOM, "minimum-image flags"));
+    e = cudaMemcpy(c->d_min_image, c->min_image.data(), static_cast<size_t>(n_clusters),
+                   cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMemcpy"));
+  }
   if (dev_alloc(&c->d_word, 1) != cudaSuccess ||
       cudaMallocHost(reinterpret_cast<void**>(&c->h_word), sizeof(unsigned long long)) !=
           cudaSuccess)
@@ -1077,6 +1111,8 @@ md_status md_set_rate_mlp(md_ctx* c, const float* params, const md_mlp_train_con
 md_status md_set_detectors(md_ctx* c, int32_t cluster, const md_detector_config* d) {
   if (!c) return fail(MD_ERR_ARG, "ctx is NULL");
   if (cluster < 0 || cluster >= c->n_clusters) return fail(MD_ERR_ARG, "bad cluster index");
+  if (d && c->any_mi)
+    return fail(MD_ERR_STATE, "detectors are not built with minimum-image forces");
   if (d && !(d->radius > 0.0 && d->cone_half_angle_deg >= 0.0 &&
              d->cone_half_angle_deg <= 90.0 && d->e_max_ev > 0.0 && d->n_bins >= 1 &&
              d->n_bins <= kDetMaxBins && d->reserved == 0 && std::isfinite(d->center[0]) &&
@@ -1241,6 +1277,10 @@ static md_status run_fields(md_ctx* c, int ci, bool potential) {
   a.src_live = c->d_src_live;
   a.tgt_live = c->d_tgt_live;
   a.gbase = cl.off;
+  // minimum-image displacements while this cluster's boundary is periodic
+  const double t_n = cl.t0 + static_cast<double>(step) * cl.dt;
+  if (c->min_image[ci] && (cl.boundary == 1 || (cl.boundary == 2 && t_n < cl.t_switch)))
+    a.box = static_cast<float>(cl.box);
   // split the sources so that about 4 waves of CTAs run (at most kFieldMaxSeg
   // segments of at least 4 tiles each)
   const long long per = md::field_targets_per_cta();
@@ -1354,7 +1394,7 @@ md_status md_step_diag(md_ctx* c, md_diag* out) {
   const md::KernelConfig* cfgs = md::step_configs(&ncfg);
   const md::KernelConfig& k = cfgs[c->cfg];
   md_status st = MD_OK, worst = MD_OK;
-  if (c->any_ion || c->det_on || !k.launch_step_pot) {
+  if (c->any_ion || c->det_on || c->any_mi || !k.launch_step_pot) {
     for (int ci = 0; ci < c->n_clusters; ++ci) {
       st = md_diagnostics(c, ci, &out[ci]);
       if (st == MD_ERR_NONFINITE) worst = st;
@@ -1586,10 +1626,8 @@ md_status md_autotune(md_ctx* c, int32_t steps, double* times_ms, int32_t cap) {
   for (int i = 0; i < n && st == MD_OK; ++i) {
     if (times_ms && i < cap) times_ms[i] = -1.0;
     int bps = 0;
-    if ((c->det_on ? cfgs[i].max_blocks_per_sm_det(&bps) : cfgs[i].max_blocks_per_sm(&bps)) !=
-            cudaSuccess ||
-        bps < 1)
-      continue;  // does not fit
+    if (c->any_mi && !cfgs[i].launch_step_mi) continue;  // no minimum-image kernel
+    if (blocks_per_sm_of(c, cfgs[i], &bps) != cudaSuccess || bps < 1) continue;  // does not fit
     st = configure(c, i, 0, 0);
     if (st != MD_OK) break;
     st = launch_steps_direct(c, 1);  // warm-up

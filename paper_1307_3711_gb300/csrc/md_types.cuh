@@ -108,6 +108,8 @@ struct StepArgs {
   const int* zq;
   const unsigned char* kind;
   const double* w;
+  // per cluster: minimum-image forces while periodic (nullptr: no cluster)
+  const unsigned char* min_image;
 };
 
 // Arguments of the ionization kernels of one cluster.
@@ -176,6 +178,8 @@ struct FieldArgs {
   int nseg = 1;
   long long seg_len = 0;
   double* part = nullptr;
+  // > 0: minimum-image displacements in the periodic cube of this side
+  float box = 0.0f;
 };
 
 struct DiagPartial {

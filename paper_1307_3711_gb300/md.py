@@ -40,7 +40,7 @@ class Config(C.Structure):
                 ("polarization", C.c_int32), ("envelope", C.c_int32),
                 ("boundary", C.c_int32), ("rate_model", C.c_int32),
                 ("ionize_every", C.c_int32), ("zmax", C.c_int32), ("n_ions", C.c_int32),
-                ("reserved", C.c_int32), ("slot_base", C.c_int64), ("seed", C.c_uint64),
+                ("min_image", C.c_int32), ("slot_base", C.c_int64), ("seed", C.c_uint64),
                 ("r_loc", C.c_double), ("r_create", C.c_double),
                 ("ip_ev", C.c_double * 16), ("q_outer", C.c_double * 16)]
 
@@ -231,13 +231,14 @@ RATES_NONE, RATES_PLAIN, RATES_MLP = 0, 1, 2
 def make_config(a0=0.0, tau=1.0, t0=0.0, dt=0.02, softening=1e-3, box=0.0, t_switch=0.0,
                 lambda_um=0.8, polarization=0, envelope=ENV_SIN2,
                 boundary=BOUNDARY_OPEN, rate_model=RATES_NONE, ionize_every=0, zmax=0,
-                n_ions=0, slot_base=0, seed=0, r_loc=0.0, r_create=0.0, species=None) -> Config:
+                n_ions=0, slot_base=0, seed=0, r_loc=0.0, r_create=0.0, species=None,
+                min_image=0) -> Config:
     c = Config()
     c.a0, c.tau, c.t0, c.dt, c.softening = a0, tau, t0, dt, softening
     c.box, c.t_switch, c.lambda_um = box, t_switch, lambda_um
     c.polarization, c.envelope, c.boundary = polarization, envelope, boundary
     c.rate_model, c.ionize_every, c.zmax, c.n_ions = rate_model, ionize_every, zmax, n_ions
-    c.reserved, c.slot_base, c.seed = 0, slot_base, seed & (2 ** 64 - 1)
+    c.min_image, c.slot_base, c.seed = int(min_image), slot_base, seed & (2 ** 64 - 1)
     c.r_loc, c.r_create = r_loc, r_create
     if species is not None:
         for k, v in enumerate(species["ip_ev"]):

@@ -513,6 +513,95 @@ def test_periodic_boundary_wraps_into_box(md):
     assert np.percentile(d.max(1), 90) < 1e-5 * L
 
 
+def _box_gas(n_ions, n_el, L, seed):
+    """Ions (Xe3+) and electrons uniform over the whole periodic cube, so that
+    many pairs meet through the faces."""
+    rng = np.random.default_rng(seed)
+    n = n_ions + n_el
+    x = rng.uniform(-0.5 * L, 0.5 * L, size=(n, 3))
+    u = np.r_[np.zeros((n_ions, 3)), rng.normal(size=(n_el, 3)) * 4e-3]
+    z = np.r_[np.full(n_ions, 3), np.full(n_el, -1)].astype(np.int32)
+    mass = np.r_[np.full(n_ions, synth.MASS_XE), np.ones(n_el)]
+    return x, u, z, mass, np.ones(n)
+
+
+@pytest.mark.parametrize("split", [1, 4])
+def test_min_image_field_step_and_diagnostics_follow_oracle(md, split):
+    """Periodic cube with minimum-image forces (the optional image forces of
+    the periodic boundary, Sec. II): the field and potential, one step's kick
+    and drift, and the diagnostics follow the FP64 oracle's minimum-image sums
+    for a gas spread over the whole cube (many pairs meet through the faces),
+    with one or 4 source segments; a periodic translation of the gas leaves
+    the GPU's field unchanged, and the field without image forces differs."""
+    L, eps, kc = 0.05, 1e-3, oracle.coulomb_constant(0.8)
+    x, u, z, mass, w = _box_gas(1000, 3000, L, 31)
+    q = w * z
+
+    def ctx_of(xx, min_image=1, boundary=1, t_switch=0.0):
+        cfg = md.make_config(a0=0.02, tau=1.0, dt=0.05, softening=eps, box=L,
+                             t_switch=t_switch, envelope=synth.ENV_FLAT, boundary=boundary,
+                             min_image=min_image)
+        c = md.Context([cfg], [md.HostParticles(xx, u, z, mass, w)])
+        c.set_tuning(128, 4, 512, 0, split, 0)
+        return c
+
+    e64, p64 = oracle.self_field(x, q, eps, kc, potential=True, box=L,
+                                 nthreads=os.cpu_count() or 1)
+    with ctx_of(x) as ctx:
+        e, phi = ctx.fields(0, potential=True)
+        d = ctx.step_diag()[0]            # falls back to diagnostics + step
+        g1 = ctx.get_particles(0)
+    err = summary(force_error(e, e64))
+    assert err["p99"] <= FORCE_P99, err
+    perr = np.abs(phi - p64) / np.sqrt(np.mean(p64 ** 2))
+    assert np.percentile(perr, 99) < 2e-5
+    e_open = oracle.self_field(x, q, eps, kc)
+    assert summary(force_error(e_open, e64))["median"] > 1e-2   # image forces matter here
+    # one step against the oracle's minimum-image kick and drift
+    a, b = oracle.laser_fields(0.0, 0.02, 0, synth.ENV_FLAT, 1.0)
+    du_ref, dx_ref = [], []
+    for i in range(len(q)):
+        u1 = oracle.boris_kick(u[i], e64[i] + a, b, z[i] / mass[i], 0.05)
+        du_ref.append(u1 - u[i])
+        x1 = oracle.drift(x[i], u1, 0.05)
+        dx_ref.append(x1 - x[i])
+    du_ref, dx_ref = np.array(du_ref), np.array(dx_ref)
+    dx_gpu = g1.x - x
+    dx_gpu -= L * np.round(dx_gpu / L)                 # across the wrap
+    assert summary(force_error(g1.u - u, du_ref))["p99"] <= FORCE_P99
+    assert summary(force_error(dx_gpu, dx_ref))["p99"] <= FORCE_P99
+    # diagnostics against the oracle's minimum-image diagnostics
+    st = oracle.State(x, u, z, mass, w)
+    o = oracle.diagnostics(st, oracle.make_params(a0=0.02, tau=1.0, dt=0.05, eps=eps, box=L,
+                                                  boundary=oracle.BOUNDARY_PERIODIC,
+                                                  env=synth.ENV_FLAT, min_image=1))
+    assert d["pe"] == pytest.approx(o["pe"], rel=1e-5)
+    assert abs(d["ke"] - o["ke"]) < 1e-5 * (abs(o["pe"]) + o["ke"])
+    # periodic translation: the same field (up to FP32)
+    xs = x + np.array([0.37, -0.21, 0.11]) * L
+    xs -= L * np.floor((xs + 0.5 * L) / L)
+    with ctx_of(xs) as ctx:
+        e2 = ctx.fields(0)
+    assert summary(force_error(e2, e64))["p99"] <= FORCE_P99
+    # a mixed boundary already open at t = 0, and a cluster without the flag:
+    # the open field
+    for kw in ({"boundary": 2, "t_switch": -1.0}, {"min_image": 0}):
+        with ctx_of(x, **kw) as ctx:
+            e3 = ctx.fields(0)
+        assert summary(force_error(e3, e_open))["p99"] <= FORCE_P99
+
+
+def test_min_image_with_detectors_is_refused(md):
+    cfg = md.make_config(softening=1e-3, box=0.05, boundary=1, min_image=1)
+    x, u, z, mass, w = _box_gas(10, 30, 0.05, 3)
+    with md.Context([cfg], [md.HostParticles(x, u, z, mass, w)]) as ctx:
+        with pytest.raises(md.MDError) as ei:
+            ctx.set_detectors(0, 0.01)
+        assert ei.value.status == md.MD_ERR_STATE
+        with pytest.raises(md.MDError):
+            ctx.set_tuning(128, 4, 256, 0, 0, 1)      # packed: no minimum-image kernel
+
+
 def test_checkpoint_resume_is_exact(md):
     """A checkpoint (particles + step) restored into a new context continues
     bit-identically, ionization included (Philox is keyed on the step)."""
