@@ -273,7 +273,8 @@ typedef struct {
  * detectors of cluster `cluster`; a new configuration starts with empty
  * histograms and no ion recorded.  The first call allocates the histograms
  * of all clusters (5 x 4097 x 8 B each) and one byte per record.
- * Synchronous. */
+ * Synchronous.  Errors: MD_ERR_ARG (bad index or configuration),
+ * MD_ERR_STATE (a cluster of the context uses minimum-image forces). */
 md_status md_set_detectors(md_ctx *ctx, int32_t cluster, const md_detector_config *d);
 
 /* md_get_iedf: the detector histograms of cluster `cluster` (host
