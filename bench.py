@@ -47,7 +47,8 @@ WORKLOAD_TEXT = {
     "xe3_200k": "{name}: N={n} (Xe3+ ions + electrons, 10 eV), one cluster per GPU",
     "scan256": "parameter scan of {clusters} clusters (N log-uniform 1k-50k, Z 1-8, R0 1-8 nm, "
                "a0 0.01-0.3, 20-200 fs), {n} records in one persistent launch per step",
-    "precision_1m": "{name}: N={n}, laser off",
+    "precision_1m": "{name}: N={n}, laser off (timed), then the same cluster driven at a0 = 0.1 "
+                    "(precision.driven)",
     "ar_ionize": "{name}: {atoms} Ar atoms (neutral at the start) in an 8 nm sphere + 8 "
                  "electron slots each ({n} records), ADK + Lotz ionization before every step "
                  "({rates} rates), from the pulse peak",
@@ -312,6 +313,34 @@ def precision_study(md, ctx, w, n_targets=10000, n_oracle=2000, seed=0):
             "fp64_gpu_vs_oracle_bitwise_equal": f"{int(np.sum(np.all(e_or == e64[:m], axis=1)))}"
                                                 f"/{m} targets",
             "metric": "|E - E_fp64| / max(|E_fp64|, rms|E_fp64|), state after the timed steps"}
+
+
+def driven_precision(md, args, rank, stream, tuning):
+    """The precision case's driven run: the same 1M-particle cluster with the
+    laser on (a0 = 0.1, 100 fs sin^2, from the envelope's peak), the same
+    kernel configuration, as many
+    steps as the timed run; then the FP32/Kahan field against the FP64 GPU
+    reference (and the oracle) on the state the laser has pulled apart, and
+    the energy the laser has put in."""
+    import torch
+    wd = synth.precision_1m(seed=rank, a0=0.1)
+    wd.t0 = 0.5 * wd.tau          # from the peak of the sin^2 envelope
+    with md.Context([md.config_from_workload(wd)], [md.HostParticles.from_cluster(wd.cluster)],
+                    stream=stream.cuda_stream) as cd:
+        cd.set_tuning(tuning[0], tuning[1], tuning[2], 0, tuning[4], tuning[5], tuning[6])
+        d0 = cd.diagnostics(0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cd.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        d1 = cd.diagnostics(0)
+        out = precision_study(md, cd, wd)
+    out.update(a0=wd.a0, steps=args.steps, ms_per_step=ms,
+               energy_gain_m_ec2=d1["total"] - d0["total"], ke_after=d1["ke"],
+               t_end=d1["t"], laser="on, a0 = 0.1, 100 fs sin^2 from its peak")
+    return out
 
 
 def single_thread_rate(w, seconds: float):
@@ -589,6 +618,7 @@ def run_native(args):
             "steps": args.steps, "dt": w.dt, "laser": "off",
             "what": "(E_total after - before) / |PE before| over the timed steps (the cluster "
                     "starts cold: KE = 0), FP64 sums, m_e c^2 units"}
+        precision["driven"] = driven_precision(md, args, rank, stream, tuning)
     ion_state = None
     if ionizing:
         # the state the timed steps reached (the end-to-end leg below repeats
