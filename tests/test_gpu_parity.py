@@ -151,6 +151,36 @@ def test_stateless_field_few_targets_many_sources(md):
     np.testing.assert_allclose(out[0][1], phi64, rtol=2e-5, atol=2e-5 * np.abs(phi64).max())
 
 
+def test_stateless_field_calls_on_two_streams_overlap_safely(md):
+    """Two split md_coulomb_field_device calls with different sources, issued
+    back to back on two streams (their partials in each stream's own
+    stream-ordered memory): each result equals the same call made alone."""
+    import torch
+    rng = np.random.default_rng(30)
+    kc = oracle.coulomb_constant(0.8)
+    ns, nt = 100000, 500
+    srcs = [torch.tensor(np.c_[rng.normal(size=(ns, 3)) * 0.05,
+                               kc * rng.choice([-1.0, 1.0], size=ns)],
+                         dtype=torch.float32, device="cuda") for _ in range(2)]
+    alone = []
+    for src in srcs:
+        e = torch.zeros((nt, 3), dtype=torch.float64, device="cuda")
+        md.coulomb_field_device(src.data_ptr(), ns, src.data_ptr(), nt, 1e-6, 0, e.data_ptr(), 0,
+                                torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        alone.append(e.cpu().numpy())
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    outs = [torch.zeros((nt, 3), dtype=torch.float64, device="cuda") for _ in range(2)]
+    torch.cuda.synchronize()
+    for _ in range(3):
+        for src, st, e in zip(srcs, streams, outs):
+            md.coulomb_field_device(src.data_ptr(), ns, src.data_ptr(), nt, 1e-6, 0,
+                                    e.data_ptr(), 0, st.cuda_stream)
+    torch.cuda.synchronize()
+    for k in range(2):
+        assert np.array_equal(outs[k].cpu().numpy(), alone[k])
+
+
 def test_stateless_fields_on_empty_and_single_inputs(md):
     """Degenerate sizes of the stateless entry points (FP32/Kahan, allocation
     free, FP64 reference): no sources gives a zero field and potential at
