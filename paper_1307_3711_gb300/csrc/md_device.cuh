@@ -470,6 +470,128 @@ __device__ __forceinline__ int next_live_tile(const unsigned char* live, long lo
 // consumed so far (sets the barrier phases).  Returns false (uniformly across
 // the CTA) if a wait ran out of budget; the error bit is then set and this
 // CTA's copies in flight have been waited for (bounded).
+// Bounds of a landed tile's positions (same answer in every warp).
+__device__ __forceinline__ void tile_bounds(uint32_t tile, int cnt, float (&lo)[3],
+                                            float (&hi)[3]) {
+  lo[0] = lo[1] = lo[2] = 3.0e38f;
+  hi[0] = hi[1] = hi[2] = -3.0e38f;
+  for (int k = static_cast<int>(threadIdx.x & 31u); k < cnt; k += 32) {
+    const float4 p = lds_f4(tile + 16u * k);
+    lo[0] = fminf(lo[0], p.x);
+    lo[1] = fminf(lo[1], p.y);
+    lo[2] = fminf(lo[2], p.z);
+    hi[0] = fmaxf(hi[0], p.x);
+    hi[1] = fmaxf(hi[1], p.y);
+    hi[2] = fmaxf(hi[2], p.z);
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      lo[c] = fminf(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], d));
+      hi[c] = fmaxf(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], d));
+    }
+  }
+}
+
+// Whether some (target, source) pair of a tile can be half a box apart on an
+// axis: the tile's bounds joined with the targets' (tb = lo[3], hi[3]) span
+// at least (1 - 1e-6) L / 2.  If not, every displacement is already its own
+// minimum image and the reduction can be skipped (the same bits).
+__device__ __forceinline__ bool tile_needs_image(uint32_t tile, int cnt, const float* tb,
+                                                 float L) {
+  float lo[3], hi[3];
+  tile_bounds(tile, cnt, lo, hi);
+  const float h = 0.4999995f * L;
+  bool need = false;
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+    need = need || (fmaxf(hi[c], tb[3 + c]) - fminf(lo[c], tb[c]) >= h);
+  return need;
+}
+
+// Bounds of a CTA's targets into tb[6] (shared): lo[3], hi[3].  Every thread
+// of the CTA calls it.
+template <int THREADS, int R>
+__device__ __forceinline__ void target_bounds(const float (&xi)[R], const float (&yi)[R],
+                                              const float (&zi)[R], float* tb) {
+  static_assert(THREADS % 32 == 0, "whole warps");
+  __shared__ float red[THREADS / 32][6];
+  float v[6] = {3.0e38f, 3.0e38f, 3.0e38f, -3.0e38f, -3.0e38f, -3.0e38f};
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    v[0] = fminf(v[0], xi[r]);
+    v[1] = fminf(v[1], yi[r]);
+    v[2] = fminf(v[2], zi[r]);
+    v[3] = fmaxf(v[3], xi[r]);
+    v[4] = fmaxf(v[4], yi[r]);
+    v[5] = fmaxf(v[5], zi[r]);
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      v[c] = fminf(v[c], __shfl_xor_sync(0xffffffffu, v[c], d));
+      v[3 + c] = fmaxf(v[3 + c], __shfl_xor_sync(0xffffffffu, v[3 + c], d));
+    }
+  }
+  if ((threadIdx.x & 31u) == 0)
+    for (int c = 0; c < 6; ++c) red[threadIdx.x >> 5][c] = v[c];
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    float a = red[0][threadIdx.x];
+    for (int k = 1; k < THREADS / 32; ++k)
+      a = threadIdx.x < 3 ? fminf(a, red[k][threadIdx.x]) : fmaxf(a, red[k][threadIdx.x]);
+    tb[threadIdx.x] = a;
+  }
+  __syncthreads();
+}
+
+// The pairs of one landed tile (the body of sum_sources' tile loop), for
+// the minimum-image kernels, which pick MI per tile.
+template <int R, bool POT, bool MI>
+__device__ __forceinline__ void sum_tile(uint32_t tile, int cnt, const float (&xi)[R],
+                                         const float (&yi)[R], const float (&zi)[R], float eps2,
+                                         Acc<R, POT>& acc, float L, float invL) {
+  float qt;
+  if (tile_uniform_q(tile, cnt, qt)) {
+    if (qt != 0.0f) {
+      int j = 0;
+      for (; j + 8 <= cnt; j += 8) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          pair_u<R, POT, MI>(lds_f4(tile + 16u * (j + q)), xi, yi, zi, eps2, acc, L, invL);
+        if (POT) {
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            kahan_add(acc.sp[r], acc.cp[r], acc.ap[r] * qt);
+            acc.ap[r] = 0.0f;
+          }
+        }
+      }
+      for (; j < cnt; ++j)
+        pair_u<R, POT, MI>(lds_f4(tile + 16u * j), xi, yi, zi, eps2, acc, L, invL);
+      fold_q<R, POT>(acc, qt);
+    }
+  } else {
+    int j = 0;
+    for (; j + 8 <= cnt; j += 8) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        pair<R, POT, MI>(lds_f4(tile + 16u * (j + q)), xi, yi, zi, eps2, acc, L, invL);
+      if (POT) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          kahan_add(acc.sp[r], acc.cp[r], acc.ap[r]);
+          acc.ap[r] = 0.0f;
+        }
+      }
+    }
+    for (; j < cnt; ++j) pair<R, POT, MI>(lds_f4(tile + 16u * j), xi, yi, zi, eps2, acc, L, invL);
+    fold<R, POT>(acc);
+  }
+}
+
 template <int THREADS, int R, int TILE, int STAGES, bool POT, bool MI = false>
 __device__ __forceinline__ bool sum_sources(Stage<TILE, STAGES>& sm, unsigned& it,
                                             const float4* __restrict__ src, long long ns,
@@ -478,7 +600,7 @@ __device__ __forceinline__ bool sum_sources(Stage<TILE, STAGES>& sm, unsigned& i
                                             int* err, int* s_abort,
                                             const unsigned char* live = nullptr,
                                             long long gbase = 0, float L = 0.0f,
-                                            float invL = 0.0f) {
+                                            float invL = 0.0f, const float* tb = nullptr) {
   const int ntiles = static_cast<int>((ns + TILE - 1) / TILE);
   // consumers and the issuing thread walk the same sequence of live tiles;
   // the k-th live tile goes through ring stage (it + k) % STAGES
@@ -504,6 +626,14 @@ __device__ __forceinline__ bool sum_sources(Stage<TILE, STAGES>& sm, unsigned& i
       const uint32_t tile = smem_u32(&sm.tile[s][0]);
       const long long rem = ns - static_cast<long long>(t) * TILE;
       const int cnt = static_cast<int>(rem < TILE ? rem : TILE);
+      if constexpr (MI) {
+        // a tile whose pairs all lie within half a box needs no image: the
+        // plain sum gives the same bits
+        if (tile_needs_image(tile, cnt, tb, L))
+          sum_tile<R, POT, true>(tile, cnt, xi, yi, zi, eps2, acc, L, invL);
+        else
+          sum_tile<R, POT, false>(tile, cnt, xi, yi, zi, eps2, acc, L, invL);
+      } else {
       float qt;
       if (tile_uniform_q(tile, cnt, qt)) {
         // one charge for the whole tile (records are grouped by species);
@@ -545,6 +675,7 @@ __device__ __forceinline__ bool sum_sources(Stage<TILE, STAGES>& sm, unsigned& i
         for (; j < cnt; ++j)
           pair<R, POT, MI>(lds_f4(tile + 16u * j), xi, yi, zi, eps2, acc, L, invL);
         fold<R, POT>(acc);
+      }
       }
     }
     __syncthreads();
@@ -1057,18 +1188,23 @@ __global__ void __launch_bounds__(THREADS, MINB) k_step(const StepArgs a) {
             a.src_live, s_c.off + j0);
       } else {
         acc.zero();
-        bool mi = false;
         if constexpr (MI) {
           // minimum-image forces while this cluster's boundary is periodic at t_n
           const double t_n = s_c.t0 + static_cast<double>(step) * s_c.dt;
-          mi = a.min_image && a.min_image[s_un.cluster] &&
-               (s_c.boundary == 1 || (s_c.boundary == 2 && t_n < s_c.t_switch));
-        }
-        if (mi) {
-          const float L = static_cast<float>(s_c.box);
-          ok = sum_sources<THREADS, R, TILE, STAGES, POT, true>(
-              sm, it, cur + s_c.off + j0, jn, xi, yi, zi, s_c.eps2, acc, a.err, &s_abort,
-              a.src_live, s_c.off + j0, L, 1.0f / L);
+          const bool mi = a.min_image && a.min_image[s_un.cluster] &&
+                          (s_c.boundary == 1 || (s_c.boundary == 2 && t_n < s_c.t_switch));
+          if (mi) {
+            __shared__ float s_tb[6];  // bounds of this unit's targets
+            target_bounds<THREADS, R>(xi, yi, zi, s_tb);
+            const float L = static_cast<float>(s_c.box);
+            ok = sum_sources<THREADS, R, TILE, STAGES, POT, true>(
+                sm, it, cur + s_c.off + j0, jn, xi, yi, zi, s_c.eps2, acc, a.err, &s_abort,
+                a.src_live, s_c.off + j0, L, 1.0f / L, s_tb);
+          } else {
+            ok = sum_sources<THREADS, R, TILE, STAGES, POT>(
+                sm, it, cur + s_c.off + j0, jn, xi, yi, zi, s_c.eps2, acc, a.err, &s_abort,
+                a.src_live, s_c.off + j0);
+          }
         } else {
           ok = sum_sources<THREADS, R, TILE, STAGES, POT>(sm, it, cur + s_c.off + j0, jn, xi, yi,
                                                           zi, s_c.eps2, acc, a.err, &s_abort,
@@ -1245,11 +1381,20 @@ __global__ void __launch_bounds__(THREADS) k_field(const FieldArgs a) {
   Acc<R, POT> acc;
   acc.zero();
   unsigned it = 0;
-  if (!sum_sources<THREADS, R, TILE, STAGES, POT, MI>(sm, it, a.src + j0, jn, xi, yi, zi, a.eps2,
-                                                       acc, a.err, &s_abort, a.src_live,
-                                                       a.gbase + j0, a.box,
-                                                       MI ? 1.0f / a.box : 0.0f))
-    return;
+  bool ok;
+  if constexpr (MI) {
+    __shared__ float s_tb[6];  // bounds of this CTA's targets
+    target_bounds<THREADS, R>(xi, yi, zi, s_tb);
+    ok = sum_sources<THREADS, R, TILE, STAGES, POT, true>(sm, it, a.src + j0, jn, xi, yi, zi,
+                                                          a.eps2, acc, a.err, &s_abort,
+                                                          a.src_live, a.gbase + j0, a.box,
+                                                          1.0f / a.box, s_tb);
+  } else {
+    ok = sum_sources<THREADS, R, TILE, STAGES, POT>(sm, it, a.src + j0, jn, xi, yi, zi, a.eps2,
+                                                    acc, a.err, &s_abort, a.src_live,
+                                                    a.gbase + j0);
+  }
+  if (!ok) return;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const long long i = i0 + threadIdx.x + r * THREADS;

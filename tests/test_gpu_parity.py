@@ -621,6 +621,26 @@ def test_min_image_field_step_and_diagnostics_follow_oracle(md, split):
         assert summary(force_error(e3, e_open))["p99"] <= FORCE_P99
 
 
+def test_min_image_skips_tiles_within_half_a_box_bit_for_bit(md):
+    """A compact cluster in a large periodic cube (20 R0, as in Sec. II): no
+    pair is half a box apart, so with minimum-image forces every tile takes
+    the plain sum and the run equals the run without image forces bit for
+    bit (fields and 5 steps)."""
+    w = synth.xe3_cluster(20000, seed=12)
+    r0 = float(np.abs(w.cluster.x).max())
+    out = []
+    for mi in (0, 1):
+        cfg = md.config_from_workload(w)
+        cfg.boundary, cfg.box, cfg.min_image = 1, 20.0 * r0, mi
+        with md.Context([cfg], [md.HostParticles.from_cluster(w.cluster)]) as ctx:
+            ctx.set_tuning(128, 4, 512, 0, 2, 0)
+            e = ctx.fields(0)
+            ctx.step(5)
+            out.append((e, ctx.get_particles(0)))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1].x, out[1][1].x) and np.array_equal(out[0][1].u, out[1][1].u)
+
+
 def test_min_image_with_detectors_is_refused(md):
     cfg = md.make_config(softening=1e-3, box=0.05, boundary=1, min_image=1)
     x, u, z, mass, w = _box_gas(10, 30, 0.05, 3)
