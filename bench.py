@@ -265,8 +265,10 @@ def ar_ionize_context(md, args, rank, stream):
               "r_create", "ip_ev", "q_outer"):
         setattr(cfg, f, getattr(ion, f))
     ctx = md.Context([cfg], [md.HostParticles.from_cluster(c)], stream=stream)
-    info = {"rates": args.rates, "t0": t0, "kernels_per_step": 1 + (4 if model == md.RATES_MLP
-                                                                     else 3)}
+    # ion field, inputs, (surrogate rates,) decision, apply, charge-change
+    # correction, ion push, step
+    info = {"rates": args.rates, "t0": t0,
+            "kernels_per_step": 7 + (1 if model == md.RATES_MLP else 0)}
     if model == md.RATES_MLP:
         tc = md.mlp_train_config(synth.ARGON, n_samples=10 << 20, epochs=80, batch=8192,
                                  lr=3e-3, seed=11, lambda_um=0.806)
@@ -532,7 +534,8 @@ def run_iedf(args):
                        "mean_charge": float(zs.mean())},
         "iedf": iedf, "ions_inside": int(inside.sum()),
         "inside_mean_kev": float((hin * centers).sum() / max(hin.sum(), 1.0) / 1e3),
-        "gpu_launches": 5 * nsteps,   # ion field, inputs, decision, apply, step
+        # ion field, inputs, decision, apply, charge-change correction, ion push, step
+        "gpu_launches": 7 * nsteps,
     }
     print(json.dumps(line), flush=True)
 
