@@ -98,7 +98,7 @@ typedef struct {
                              t_switch) every pair interacts through its nearest periodic
                              image (each displacement component reduced to
                              [-box/2, box/2]); 0: no image forces.  Not with ionization
-                             (rate_model != 0) or detectors: MD_ERR_ARG / MD_ERR_STATE */
+                             (rate_model != 0): MD_ERR_ARG */
     int64_t slot_base;    /* records [slot_base, slot_base + zmax n_ions) are electron
                              slots (INACTIVE until used); freed electrons fill them
                              densely, after the last active one (see md_ionize) */
@@ -273,8 +273,7 @@ typedef struct {
  * detectors of cluster `cluster`; a new configuration starts with empty
  * histograms and no ion recorded.  The first call allocates the histograms
  * of all clusters (5 x 4097 x 8 B each) and one byte per record.
- * Synchronous.  Errors: MD_ERR_ARG (bad index or configuration),
- * MD_ERR_STATE (a cluster of the context uses minimum-image forces). */
+ * Synchronous.  Errors: MD_ERR_ARG (bad index or configuration). */
 md_status md_set_detectors(md_ctx *ctx, int32_t cluster, const md_detector_config *d);
 
 /* md_get_iedf: the detector histograms of cluster `cluster` (host

@@ -31,6 +31,9 @@ struct KernelConfig {
   // (packed configurations)
   cudaError_t (*launch_step_mi)(const StepArgs& a, int grid, cudaStream_t s);
   cudaError_t (*max_blocks_per_sm_mi)(int* out);
+  // the same with the detector epilogue
+  cudaError_t (*launch_step_mi_det)(const StepArgs& a, int grid, cudaStream_t s);
+  cudaError_t (*max_blocks_per_sm_mi_det)(int* out);
 };
 
 const KernelConfig* step_configs(int* count);

@@ -212,10 +212,16 @@ cudaError_t launch_step_mi_t(const StepArgs& a, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int T, int R, int TILE, int ST, int MB>
+template <int T, int R, int TILE, int ST, int MB, bool DET = false>
 cudaError_t blocks_per_sm_mi_t(int* out) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      out, k_step<T, R, TILE, ST, false, MB, false, false, true>, T, 0);
+      out, k_step<T, R, TILE, ST, false, MB, DET, false, true>, T, 0);
+}
+
+template <int T, int R, int TILE, int ST, int MB>
+cudaError_t launch_step_mi_det_t(const StepArgs& a, int grid, cudaStream_t s) {
+  k_step<T, R, TILE, ST, false, MB, true, false, true><<<grid, T, 0, s>>>(a);
+  return cudaGetLastError();
 }
 
 template <int T, int R, int TILE, int ST, bool PK, int MB, bool DET>
@@ -229,7 +235,7 @@ cudaError_t blocks_per_sm_t(int* out) {
   {T, R, TILE, ST, PK, MB, &launch_step_t<T, R, TILE, ST, PK, MB, false>,              \
    &blocks_per_sm_t<T, R, TILE, ST, PK, MB, false>,                                      \
    &launch_step_t<T, R, TILE, ST, PK, MB, true>, &blocks_per_sm_t<T, R, TILE, ST, PK, MB, true>, \
-   nullptr, nullptr, nullptr, nullptr}
+   nullptr, nullptr, nullptr, nullptr, nullptr, nullptr}
 // scalar configurations also have the diagnostic step and minimum-image forces
 #define MD_STEP_CONFIG_POT(T, R, TILE, ST, MB)                                          \
   {T, R, TILE, ST, false, MB, &launch_step_t<T, R, TILE, ST, false, MB, false>,          \
@@ -237,7 +243,8 @@ cudaError_t blocks_per_sm_t(int* out) {
    &launch_step_t<T, R, TILE, ST, false, MB, true>,                                      \
    &blocks_per_sm_t<T, R, TILE, ST, false, MB, true>,                                    \
    &launch_step_pot_t<T, R, TILE, ST, MB>, &blocks_per_sm_pot_t<T, R, TILE, ST, MB>,        \
-   &launch_step_mi_t<T, R, TILE, ST, MB>, &blocks_per_sm_mi_t<T, R, TILE, ST, MB>}
+   &launch_step_mi_t<T, R, TILE, ST, MB>, &blocks_per_sm_mi_t<T, R, TILE, ST, MB>,          \
+   &launch_step_mi_det_t<T, R, TILE, ST, MB>, &blocks_per_sm_mi_t<T, R, TILE, ST, MB, true>}
 
 // min CTAs per SM = 0 leaves the register budget to ptxas; a positive value
 // caps it at 64K / (threads x value)

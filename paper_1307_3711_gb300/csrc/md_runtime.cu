@@ -336,12 +336,18 @@ md::StepArgs step_args(md_ctx* c) {
 // cluster has detectors, else the plain one.
 cudaError_t launch_step_of(const md_ctx* c, const md::KernelConfig& k, const md::StepArgs& a,
                            cudaStream_t s) {
-  if (c->any_mi) return k.launch_step_mi ? k.launch_step_mi(a, c->grid, s) : cudaErrorInvalidValue;
+  if (c->any_mi) {
+    if (!k.launch_step_mi) return cudaErrorInvalidValue;
+    return c->det_on ? k.launch_step_mi_det(a, c->grid, s) : k.launch_step_mi(a, c->grid, s);
+  }
   return c->det_on ? k.launch_step_det(a, c->grid, s) : k.launch_step(a, c->grid, s);
 }
 
 cudaError_t blocks_per_sm_of(const md_ctx* c, const md::KernelConfig& k, int* bps) {
-  if (c->any_mi) return k.max_blocks_per_sm_mi ? k.max_blocks_per_sm_mi(bps) : cudaErrorInvalidValue;
+  if (c->any_mi) {
+    if (!k.max_blocks_per_sm_mi) return cudaErrorInvalidValue;
+    return c->det_on ? k.max_blocks_per_sm_mi_det(bps) : k.max_blocks_per_sm_mi(bps);
+  }
   return c->det_on ? k.max_blocks_per_sm_det(bps) : k.max_blocks_per_sm(bps);
 }
 
@@ -1111,8 +1117,6 @@ md_status md_set_rate_mlp(md_ctx* c, const float* params, const md_mlp_train_con
 md_status md_set_detectors(md_ctx* c, int32_t cluster, const md_detector_config* d) {
   if (!c) return fail(MD_ERR_ARG, "ctx is NULL");
   if (cluster < 0 || cluster >= c->n_clusters) return fail(MD_ERR_ARG, "bad cluster index");
-  if (d && c->any_mi)
-    return fail(MD_ERR_STATE, "detectors are not built with minimum-image forces");
   if (d && !(d->radius > 0.0 && d->cone_half_angle_deg >= 0.0 &&
              d->cone_half_angle_deg <= 90.0 && d->e_max_ev > 0.0 && d->n_bins >= 1 &&
              d->n_bins <= kDetMaxBins && d->reserved == 0 && std::isfinite(d->center[0]) &&

@@ -135,3 +135,28 @@ def test_detectors_on_an_ionizing_cluster_match_oracle(md):
     assert np.sum(crossed < 1024) > 5 and np.sum(crossed >= 1024) > 2
     np.testing.assert_array_equal(got, det.hist)
     np.testing.assert_array_equal(inside, det.inside(state_of(g0)))
+
+
+def test_detectors_with_minimum_image_forces_match_oracle(md):
+    """The exploding ion sphere in a periodic cube of 6 R0 with minimum-image
+    forces (the step kernel's image twin with the detector epilogue): every
+    crossing of 2.5 R0 matches the oracle's detectors applied to the GPU's
+    own states, step by step."""
+    n = 600
+    c, r0, e_max, cfg = explosion(md, n, seed=6)
+    cfg.boundary, cfg.box, cfg.min_image = 1, 6.0 * r0, 1
+    nb = 32
+    e_max_ev = 0.4 * e_max * ME_C2_EV
+    det = oracle.Detectors(n, radius=2.5 * r0, cone_deg=30.0, e_max_ev=e_max_ev, nbins=nb)
+    with md.Context([cfg], [md.HostParticles.from_cluster(c)]) as ctx:
+        ctx.set_detectors(0, 2.5 * r0, cone_deg=30.0, e_max_ev=e_max_ev, n_bins=nb)
+        g0 = ctx.get_particles(0)
+        for _ in range(200):
+            ctx.step(1)
+            g1 = ctx.get_particles(0)
+            det.record(g0.x, g1.x, state_of(g1))
+            g0 = g1
+        got, inside = ctx.iedf(0)
+    assert det.hist[4].sum() > 0.5 * n
+    np.testing.assert_array_equal(got, det.hist)
+    np.testing.assert_array_equal(inside, det.inside(state_of(g0)))

@@ -641,15 +641,13 @@ def test_min_image_skips_tiles_within_half_a_box_bit_for_bit(md):
     assert np.array_equal(out[0][1].x, out[1][1].x) and np.array_equal(out[0][1].u, out[1][1].u)
 
 
-def test_min_image_with_detectors_is_refused(md):
+def test_min_image_refuses_packed_tunings(md):
     cfg = md.make_config(softening=1e-3, box=0.05, boundary=1, min_image=1)
     x, u, z, mass, w = _box_gas(10, 30, 0.05, 3)
     with md.Context([cfg], [md.HostParticles(x, u, z, mass, w)]) as ctx:
         with pytest.raises(md.MDError) as ei:
-            ctx.set_detectors(0, 0.01)
-        assert ei.value.status == md.MD_ERR_STATE
-        with pytest.raises(md.MDError):
             ctx.set_tuning(128, 4, 256, 0, 0, 1)      # packed: no minimum-image kernel
+        assert ei.value.status == md.MD_ERR_ARG
 
 
 def test_checkpoint_resume_is_exact(md):
