@@ -108,6 +108,8 @@ def lib():
             L.io_rate_total.argtypes = [d, i, d, d, p, p, d]
             L.io_local_moments.restype = None
             L.io_local_moments.argtypes = [i, p, i, p, p, p, p, p, d, d, p, p]
+            L.io_local_moments_box.restype = None
+            L.io_local_moments_box.argtypes = [i, p, i, p, p, p, p, p, d, d, d, p, p]
             L.mo_nparam.restype = i
             L.mo_nparam.argtypes = []
             L.mo_features.restype = None
@@ -379,14 +381,21 @@ def rate_total(a_mag, z, ne, te, species, lambda_um=0.8):
                                float(lambda_um))
 
 
-def local_moments(x_targets, state: "State", r_loc, lambda_um=0.8):
-    """(ne [cm^-3], Te [eV]) of the active electrons within r_loc of each target."""
+def local_moments(x_targets, state: "State", r_loc, lambda_um=0.8, box=0.0):
+    """(ne [cm^-3], Te [eV]) of the active electrons within r_loc of each target
+    (box > 0: nearest periodic images in the cube of that side)."""
     xt = _f64(x_targets, (-1, 3))
     ne = np.zeros(xt.shape[0])
     te = np.zeros(xt.shape[0])
-    lib().io_local_moments(xt.shape[0], _ptr(xt), state.n, _ptr(state.x), _ptr(state.u),
-                           _ptr(state.w), _ptr(state.z), _ptr(state.active), float(r_loc),
-                           float(lambda_um), _ptr(ne), _ptr(te))
+    if box > 0.0:
+        lib().io_local_moments_box(xt.shape[0], _ptr(xt), state.n, _ptr(state.x),
+                                   _ptr(state.u), _ptr(state.w), _ptr(state.z),
+                                   _ptr(state.active), float(r_loc), float(lambda_um), float(box),
+                                   _ptr(ne), _ptr(te))
+    else:
+        lib().io_local_moments(xt.shape[0], _ptr(xt), state.n, _ptr(state.x), _ptr(state.u),
+                               _ptr(state.w), _ptr(state.z), _ptr(state.active), float(r_loc),
+                               float(lambda_um), _ptr(ne), _ptr(te))
     return ne, te
 
 
@@ -419,21 +428,29 @@ def next_free_slot(state: "State", slot_base, n_ion, zmax):
 
 def ionize_pass(state: "State", params: Params, species, n_ion, slot_base, zmax, seed, dt_ion,
                 r_loc, r_create, lambda_um=0.8, nthreads=1):
+    """Without minimum-image forces; see ionize_pass_box."""
+    return ionize_pass_box(state, params, species, n_ion, slot_base, zmax, seed, dt_ion, r_loc,
+                           r_create, lambda_um, nthreads, box=0.0)
+
+
+def ionize_pass_box(state: "State", params: Params, species, n_ion, slot_base, zmax, seed,
+                    dt_ion, r_loc, r_create, lambda_um=0.8, nthreads=1, box=0.0):
     """One ionization pass at step state.step (Sec. II): for each ion record
     i < n_ion (id = i) of charge z < zmax, the field |E_coulomb + a(t_n)| at
     x_i, the local electron moments, the Philox decision; an ionizing ion gets
     z + 1 and frees an electron at x_i + offset with the ion's u and weight.
     The electrons freed in one pass take the next free slots (next_free_slot)
-    in the order of their ions' indices.  Returns (fired, field_mag, ne, te)
-    of the ions; modifies state."""
+    in the order of their ions' indices.  box > 0: the field and the local
+    moments use minimum-image distances in the periodic cube of that side.
+    Returns (fired, field_mag, ne, te) of the ions; modifies state."""
     ions = np.arange(n_ion, dtype=np.int64)
     q = state.q()
     e = coulomb_field(state.x[:n_ion], state.x, q, params.eps, params.kc, self_idx=ions,
-                      nthreads=nthreads)
+                      nthreads=nthreads, box=box)
     t = params.t0 + state.step * params.dt
     a, _ = laser_fields(t, params.a0, params.pol, params.env, params.tau)
     amag = np.linalg.norm(e + a[None, :], axis=1)
-    ne, te = local_moments(state.x[:n_ion], state, r_loc, lambda_um)
+    ne, te = local_moments(state.x[:n_ion], state, r_loc, lambda_um, box=box)
     z_old = state.z[:n_ion].copy()
     z_new, fired, off, _ = decide(ions, z_old, amag, ne, te, species, zmax, seed, state.step,
                                   dt_ion, r_create, lambda_um)

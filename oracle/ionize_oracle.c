@@ -184,6 +184,44 @@ void io_local_moments(int nt, const double *xt, int ns, const double *xs, const 
     }
 }
 
+/* The same moments with minimum-image distances in a periodic cube of side
+ * box (box <= 0: open): an electron counts if its nearest periodic image is
+ * within r_loc of the ion. */
+void io_local_moments_box(int nt, const double *xt, int ns, const double *xs, const double *us,
+                          const double *ws, const int32_t *zs, const uint8_t *active_s,
+                          double r_loc, double lambda_um, double box, double *ne, double *te)
+{
+    double kw = 2.0 * IO_PI / (lambda_um * 1e-6);
+    double vol = (4.0 / 3.0) * IO_PI * pow(r_loc / kw, 3) * 1e6;
+    double rl2 = r_loc * r_loc;
+    for (int i = 0; i < nt; ++i) {
+        double s_w = 0, s_x = 0, s_y = 0, s_z = 0, s_2 = 0;
+        for (int j = 0; j < ns; ++j) {
+            if (!active_s[j] || zs[j] >= 0) continue;
+            double d[3];
+            for (int c = 0; c < 3; ++c) {
+                d[c] = xs[3 * j + c] - xt[3 * i + c];
+                if (box > 0.0) d[c] -= box * nearbyint(d[c] / box);
+            }
+            if (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] >= rl2) continue;
+            double wj = ws[j];
+            double vx = us[3 * j], vy = us[3 * j + 1], vz = us[3 * j + 2];
+            s_w += wj;
+            s_x += wj * vx; s_y += wj * vy; s_z += wj * vz;
+            s_2 += wj * (vx * vx + vy * vy + vz * vz);
+        }
+        if (s_w > 0.0) {
+            double ax = s_x / s_w, ay = s_y / s_w, az = s_z / s_w;
+            double v2 = s_2 / s_w - (ax * ax + ay * ay + az * az);
+            ne[i] = s_w / vol;
+            te[i] = v2 > 0.0 ? IO_ME_C2_EV * v2 / 3.0 : 0.0;
+        } else {
+            ne[i] = 0.0;
+            te[i] = 0.0;
+        }
+    }
+}
+
 /* ------------------------------------------------------------- decision */
 
 /* Monte-Carlo decision for n ions with ids id[] (Philox counter word 0),

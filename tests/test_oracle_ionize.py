@@ -245,3 +245,35 @@ def test_next_free_slot_follows_the_last_active_slot():
     assert oracle.next_free_slot(st, 4, n_ion, zmax) == 4
     st.active[[4, 7]] = 1
     assert oracle.next_free_slot(st, 4, n_ion, zmax) == 8
+
+
+def test_local_moments_with_minimum_image():
+    """Minimum-image moments: an electron just across a face is within r_loc
+    of an ion near the opposite face through its image; the moments are
+    invariant under a periodic translation of the whole system; a system
+    within half the box has exactly its open moments."""
+    box, r_loc = 1.0, 0.05
+    x = np.array([[0.49, 0.0, 0.0], [-0.48, 0.01, 0.0], [0.47, 0.0, 0.02]])
+    u = np.array([[0.0, 0.0, 0.0], [0.01, 0.0, 0.0], [-0.02, 0.003, 0.0]])
+    st = oracle.State(x, u, [1, -1, -1], [7e4, 1.0, 1.0], [1.0, 1.0, 1.0])
+    ne_b, te_b = oracle.local_moments(x[:1], st, r_loc, box=box)
+    ne_o, te_o = oracle.local_moments(x[:1], st, r_loc)
+    assert ne_b[0] == pytest.approx(2 * ne_o[0]) and te_b[0] > 0.0 and te_o[0] == 0.0
+    rng = np.random.default_rng(5)
+    n = 400
+    xr = rng.uniform(-0.5, 0.5, size=(n, 3))
+    ur = rng.normal(size=(n, 3)) * 0.01
+    z = np.where(np.arange(n) < 100, 2, -1)
+    st = oracle.State(xr, ur, z, np.where(z > 0, 7e4, 1.0), np.ones(n))
+    ne0, te0 = oracle.local_moments(xr[:100], st, 0.2, box=box)
+    xs = xr + np.array([0.3, -0.45, 0.2])
+    xs -= box * np.floor((xs + 0.5 * box) / box)
+    st2 = oracle.State(xs, ur, z, st.mass, st.w)
+    ne1, te1 = oracle.local_moments(xs[:100], st2, 0.2, box=box)
+    np.testing.assert_allclose(ne1, ne0, rtol=1e-12)
+    np.testing.assert_allclose(te1, te0, rtol=1e-9, atol=1e-12)
+    xc = rng.uniform(-0.2, 0.2, size=(n, 3))
+    st3 = oracle.State(xc, ur, z, st.mass, st.w)
+    a = oracle.local_moments(xc[:100], st3, 0.2, box=box)
+    b = oracle.local_moments(xc[:100], st3, 0.2)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])

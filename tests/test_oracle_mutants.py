@@ -77,6 +77,8 @@ MUTANTS_OTHER = [
     ("moments_no_mean_frame", "ionize_oracle.c",
      "double var = su2 / sw - (mx * mx + my * my + mz * mz);", "double var = su2 / sw;",
      "test_oracle_ionize.py"),
+    ("moments_min_image_dropped", "ionize_oracle.c",
+     "if (box > 0.0) d[c] -= box * nearbyint(d[c] / box);", "", "test_oracle_ionize.py"),
     ("decision_le", "ionize_oracle.c", "if (alpha < P) {", "if (alpha > P) {",
      "test_oracle_ionize.py"),
     ("placement_radius", "ionize_oracle.c", "double ph = 2.0 * IO_PI * u2, r = r_create * cbrt(u3);",
