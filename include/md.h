@@ -97,8 +97,9 @@ typedef struct {
     int32_t min_image;    /* 1: while the boundary is periodic (PERIODIC, or MIXED before
                              t_switch) every pair interacts through its nearest periodic
                              image (each displacement component reduced to
-                             [-box/2, box/2]); 0: no image forces.  Not with ionization
-                             (rate_model != 0): MD_ERR_ARG */
+                             [-box/2, box/2]), in the step, the diagnostics and the
+                             ionization pass (field and local moments); 0: no image
+                             forces */
     int64_t slot_base;    /* records [slot_base, slot_base + zmax n_ions) are electron
                              slots (INACTIVE until used); freed electrons fill them
                              densely, after the last active one (see md_ionize) */

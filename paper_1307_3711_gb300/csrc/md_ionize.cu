@@ -119,11 +119,12 @@ __device__ __forceinline__ void tile_class(uint32_t tile, int cnt, float& q, boo
 // rloc2e = r_loc^2 + eps^2 is compared with r^2 + eps^2.  Sources go in
 // groups of 4 with one (rarely taken) branch per group on the nearest of the
 // 4; inside it the electrons within r_loc are added in source order.
-template <int R, bool UNIFORM>
+template <int R, bool UNIFORM, bool MI = false>
 __device__ __forceinline__ void ion_pairs_moments(uint32_t ptile, const float4* vtile, int cnt,
                                                   const float (&xi)[R], const float (&yi)[R],
                                                   const float (&zi)[R], float eps2, float rloc2e,
-                                                  Acc<R, false>& acc, LocalMoments<R>& m) {
+                                                  Acc<R, false>& acc, LocalMoments<R>& m,
+                                                  float L = 0.0f, float invL = 0.0f) {
   constexpr int G = 4;
   int j = 0;
   for (; j + G <= cnt; j += G) {
@@ -135,7 +136,12 @@ __device__ __forceinline__ void ion_pairs_moments(uint32_t ptile, const float4* 
       float near2[G];
 #pragma unroll
       for (int g = 0; g < G; ++g) {
-        const float dx = p[g].x - xi[r], dy = p[g].y - yi[r], dz = p[g].z - zi[r];
+        float dx = p[g].x - xi[r], dy = p[g].y - yi[r], dz = p[g].z - zi[r];
+        if constexpr (MI) {
+          dx = min_image(dx, L, invL);
+          dy = min_image(dy, L, invL);
+          dz = min_image(dz, L, invL);
+        }
         float r2 = fmaf(dx, dx, eps2);
         r2 = fmaf(dy, dy, r2);
         r2 = fmaf(dz, dz, r2);
@@ -159,7 +165,12 @@ __device__ __forceinline__ void ion_pairs_moments(uint32_t ptile, const float4* 
     const float4 p = lds_f4(ptile + 16u * j);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      const float dx = p.x - xi[r], dy = p.y - yi[r], dz = p.z - zi[r];
+      float dx = p.x - xi[r], dy = p.y - yi[r], dz = p.z - zi[r];
+      if constexpr (MI) {
+        dx = min_image(dx, L, invL);
+        dy = min_image(dy, L, invL);
+        dz = min_image(dz, L, invL);
+      }
       float r2 = fmaf(dx, dx, eps2);
       r2 = fmaf(dy, dy, r2);
       r2 = fmaf(dz, dz, r2);
@@ -174,13 +185,47 @@ __device__ __forceinline__ void ion_pairs_moments(uint32_t ptile, const float4* 
   }
 }
 
+// One landed tile of the field pass (the dispatch of k_ion_field by the
+// tile's charge class), for the minimum-image twin, which picks MI per tile.
+template <int R, bool MI>
+__device__ __forceinline__ void ion_tile(uint32_t ptile, const float4* vtile, int cnt,
+                                         const float (&xi)[R], const float (&yi)[R],
+                                         const float (&zi)[R], float eps2, float rloc2e,
+                                         Acc<R, false>& acc, LocalMoments<R>& mom, float L,
+                                         float invL) {
+  float qt;
+  bool uniform, has_e;
+  tile_class(ptile, cnt, qt, uniform, has_e);
+  if (uniform) {
+    if (qt < 0.0f) {
+      ion_pairs_moments<R, true, MI>(ptile, vtile, cnt, xi, yi, zi, eps2, rloc2e, acc, mom, L,
+                                     invL);
+      fold_q<R, false>(acc, qt);
+    } else if (qt > 0.0f) {
+#pragma unroll 4
+      for (int j = 0; j < cnt; ++j)
+        pair_u<R, false, MI>(lds_f4(ptile + 16u * j), xi, yi, zi, eps2, acc, L, invL);
+      fold_q<R, false>(acc, qt);
+    }
+  } else if (has_e) {
+    ion_pairs_moments<R, false, MI>(ptile, vtile, cnt, xi, yi, zi, eps2, rloc2e, acc, mom, L,
+                                    invL);
+    fold<R, false>(acc);
+  } else {
+#pragma unroll 4
+    for (int j = 0; j < cnt; ++j)
+      pair<R, false, MI>(lds_f4(ptile + 16u * j), xi, yi, zi, eps2, acc, L, invL);
+    fold<R, false>(acc);
+  }
+}
+
 // Field (FP32/Kahan) and local electron moments at R ion targets per thread,
 // from source segment blockIdx.y of the cluster's live records.  The live
 // records are the ions and electrons below the next free electron slot (the
 // slots are filled densely), split into gridDim.y equal segments.  Tiles of
 // one charge take the charge out of the pair loop; ion-only tiles skip the
 // moment test; uncharged tiles and dead record groups are skipped.
-template <int THREADS, int R, int TILE, int STAGES>
+template <int THREADS, int R, int TILE, int STAGES, bool MI = false>
 __global__ void __launch_bounds__(THREADS) k_ion_field(const IonArgs a) {
   __shared__ IonStage<TILE, STAGES> sm;
   __shared__ int s_abort;
@@ -219,6 +264,19 @@ __global__ void __launch_bounds__(THREADS) k_ion_field(const IonArgs a) {
     yi[r] = p.y;
     zi[r] = p.z;
   }
+  // minimum-image twin: image distances while the boundary is periodic at t_n
+  bool mi_on = false;
+  float L = 0.0f, invL = 0.0f;
+  [[maybe_unused]] float* s_tb = nullptr;
+  if constexpr (MI) {
+    __shared__ float tb[6];
+    const double t_n = a.c.t0 + static_cast<double>(step) * a.c.dt;
+    mi_on = a.min_image && (a.c.boundary == 1 || (a.c.boundary == 2 && t_n < a.c.t_switch));
+    L = static_cast<float>(a.c.box);
+    invL = 1.0f / L;
+    s_tb = tb;
+    if (mi_on) target_bounds<THREADS, R>(xi, yi, zi, tb);
+  }
   const int ntiles = static_cast<int>((ns + TILE - 1) / TILE);
   // only tiles holding a live group are copied and summed, in the same order
   // for the issuing thread and the consumers
@@ -243,6 +301,15 @@ __global__ void __launch_bounds__(THREADS) k_ion_field(const IonArgs a) {
     const int cnt = static_cast<int>(rem < TILE ? rem : TILE);
     if (!*reinterpret_cast<volatile int*>(&s_abort)) {
       const uint32_t ptile = smem_u32(&sm.pos[s][0]);
+      if constexpr (MI) {
+        // minimum-image distances only for tiles with pairs half a box apart
+        if (mi_on && tile_needs_image(ptile, cnt, s_tb, L))
+          ion_tile<R, true>(ptile, &sm.vel[s][0], cnt, xi, yi, zi, eps2, rloc2e, acc, mom, L,
+                            invL);
+        else
+          ion_tile<R, false>(ptile, &sm.vel[s][0], cnt, xi, yi, zi, eps2, rloc2e, acc, mom, L,
+                             invL);
+      } else {
       float qt;
       bool uniform, has_e;
       tile_class(ptile, cnt, qt, uniform, has_e);
@@ -264,6 +331,7 @@ __global__ void __launch_bounds__(THREADS) k_ion_field(const IonArgs a) {
 #pragma unroll 4
         for (int j = 0; j < cnt; ++j) pair<R, false>(lds_f4(ptile + 16u * j), xi, yi, zi, eps2, acc);
         fold<R, false>(acc);
+      }
       }
     }
     __syncthreads();
@@ -509,6 +577,7 @@ __global__ void __launch_bounds__(256) k_ion_apply(const IonArgs a) {
 constexpr int kFixThreads = 256;
 constexpr int kFixChunk = 256;
 
+template <bool MI = false>
 __global__ void __launch_bounds__(kFixThreads) k_ion_fix(const IonArgs a) {
   __shared__ float4 s_src[2 * kFixChunk];
   const long long step = __ldcg(a.step);
@@ -523,6 +592,19 @@ __global__ void __launch_bounds__(kFixThreads) k_ion_fix(const IonArgs a) {
   Acc<1, false> acc;
   acc.zero();
   const float kc = static_cast<float>(a.ion.kc);
+  // minimum-image twin: image distances while the boundary is periodic at t_n
+  bool mi_on = false;
+  float L = 0.0f, invL = 0.0f;
+  [[maybe_unused]] float* s_tb = nullptr;
+  if constexpr (MI) {
+    __shared__ float tb[6];
+    const double t_n = a.c.t0 + static_cast<double>(step) * a.c.dt;
+    mi_on = a.min_image && (a.c.boundary == 1 || (a.c.boundary == 2 && t_n < a.c.t_switch));
+    L = static_cast<float>(a.c.box);
+    invL = 1.0f / L;
+    s_tb = tb;
+    if (mi_on) target_bounds<kFixThreads, 1>(xi, yi, zi, tb);
+  }
   for (long long k0 = 0; k0 < nf; k0 += kFixChunk) {
     const int cnt = static_cast<int>(nf - k0 < kFixChunk ? nf - k0 : kFixChunk);
     __syncthreads();
@@ -540,9 +622,20 @@ __global__ void __launch_bounds__(kFixThreads) k_ion_fix(const IonArgs a) {
       s_src[kFixChunk + threadIdx.x] = pe;
     }
     __syncthreads();
-    for (int q = 0; q < cnt; ++q) {
-      pair<1, false>(s_src[q], xi, yi, zi, a.c.eps2, acc);
-      pair<1, false>(s_src[kFixChunk + q], xi, yi, zi, a.c.eps2, acc);
+    bool img = false;
+    if constexpr (MI)
+      img = mi_on && (tile_needs_image(smem_u32(&s_src[0]), cnt, s_tb, L) ||
+                      tile_needs_image(smem_u32(&s_src[kFixChunk]), cnt, s_tb, L));
+    if (img) {
+      for (int q = 0; q < cnt; ++q) {
+        pair<1, false, true>(s_src[q], xi, yi, zi, a.c.eps2, acc, L, invL);
+        pair<1, false, true>(s_src[kFixChunk + q], xi, yi, zi, a.c.eps2, acc, L, invL);
+      }
+    } else {
+      for (int q = 0; q < cnt; ++q) {
+        pair<1, false>(s_src[q], xi, yi, zi, a.c.eps2, acc);
+        pair<1, false>(s_src[kFixChunk + q], xi, yi, zi, a.c.eps2, acc);
+      }
     }
     fold<1, false>(acc);
   }
@@ -624,7 +717,10 @@ cudaError_t launch_ion_pass(const IonArgs& a, cudaStream_t s) {
   const long long per = kIonThreads * kIonR;
   const dim3 g1(static_cast<unsigned>((a.ion.n_ions + per - 1) / per),
                 static_cast<unsigned>(a.nseg));
-  k_ion_field<kIonThreads, kIonR, kIonTile, 2><<<g1, kIonThreads, 0, s>>>(a);
+  if (a.min_image)
+    k_ion_field<kIonThreads, kIonR, kIonTile, 2, true><<<g1, kIonThreads, 0, s>>>(a);
+  else
+    k_ion_field<kIonThreads, kIonR, kIonTile, 2><<<g1, kIonThreads, 0, s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const unsigned g2 = static_cast<unsigned>((a.ion.n_ions + 255) / 256);
@@ -638,8 +734,11 @@ cudaError_t launch_ion_pass(const IonArgs& a, cudaStream_t s) {
   k_ion_apply<<<g2, 256, 0, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (a.e_ion && a.fired_list) {
-    k_ion_fix<<<static_cast<unsigned>((a.ion.n_ions + kFixThreads - 1) / kFixThreads), kFixThreads,
-                0, s>>>(a);
+    const unsigned gf = static_cast<unsigned>((a.ion.n_ions + kFixThreads - 1) / kFixThreads);
+    if (a.min_image)
+      k_ion_fix<true><<<gf, kFixThreads, 0, s>>>(a);
+    else
+      k_ion_fix<<<gf, kFixThreads, 0, s>>>(a);
     e = cudaGetLastError();
   }
   return e;

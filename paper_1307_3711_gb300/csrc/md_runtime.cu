@@ -218,9 +218,6 @@ md_status validate_config(const md_config& c, int idx) {
     return fail(MD_ERR_ARG, "cluster %d: min_image must be 0 or 1", idx);
   if (c.min_image && c.boundary == 0)
     return fail(MD_ERR_ARG, "cluster %d: min_image needs a periodic or mixed boundary", idx);
-  if (c.min_image && c.rate_model != 0)
-    return fail(MD_ERR_ARG,
-                "cluster %d: minimum-image forces are not built for ionizing clusters", idx);
   if (c.rate_model < 0 || c.rate_model > 2)
     return fail(MD_ERR_ARG, "cluster %d: rate_model must be 0, 1 or 2", idx);
   return MD_OK;
@@ -588,6 +585,7 @@ md::IonArgs ion_args(md_ctx* c, int ci, int force) {
   a.vel = c->d_vel;
   a.next_slot = c->d_ion_next + ci;
   a.cl_dev = c->d_cl + ci;
+  a.min_image = c->min_image[ci];
   a.e_ion = ions_fused(c, ci) ? c->d_ion_e + 3 * c->ion_out_off[ci] : nullptr;
   a.fired_list = ions_fused(c, ci) ? c->d_ion_list + c->ion_out_off[ci] : nullptr;
   return a;

@@ -155,6 +155,9 @@ struct IonArgs {
   // fired in this pass in slot order, [n_ions]
   double* e_ion;
   int* fired_list;
+  // 1: minimum-image distances while the boundary is periodic (field and
+  // local moments of the pass, charge-change correction)
+  int min_image;
 };
 
 struct FieldArgs {

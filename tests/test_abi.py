@@ -67,8 +67,6 @@ def _one(md, **kw):
     ({"softening": 1e-30}, "softening"), ({"a0": float("nan")}, "finite"),
     ({"t0": float("inf")}, "finite"),
     ({"min_image": 2}, "min_image"), ({"min_image": 1}, "periodic or mixed boundary"),
-    ({"min_image": 1, "boundary": 1, "box": 1.0, "rate_model": 1, "zmax": 1, "n_ions": 1,
-      "slot_base": 2}, "not built for ionizing"),
 ])
 def test_init_rejects_bad_config_on_host(md, kw, what):
     cfg, p = _one(md, **kw)

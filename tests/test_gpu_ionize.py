@@ -492,3 +492,61 @@ def test_ions_pushed_with_the_pass_field_follow_oracle(md):
             assert summary(err_x)["p99"] <= 2e-5, k
             checked += 1
     assert checked >= 2
+
+
+def test_ionization_pass_with_minimum_image_follows_oracle(md):
+    """Atoms spread over a periodic cube of 3 nm with minimum-image forces: a
+    pass sees the FP64 oracle's minimum-image |E| and local electron moments
+    (electrons near one face count for ions near the opposite one), decides as
+    the oracle does from the GPU's inputs, and ionizing steps with image forces
+    (field pass, charge-change correction, ion push, step) conserve charge."""
+    n, zmax = 800, 8
+    L = synth.nm_to_len(3.0)
+    rng = np.random.default_rng(12)
+    c = synth.make_cluster(7, n, 0, synth.nm_to_len(1.0), 0, AR["mass"],
+                           n_electron_slots=zmax * n)
+    c.x[:n] = rng.uniform(-0.5 * L, 0.5 * L, size=(n, 3))
+    rw = synth.nm_to_len(AR["r_w_nm"])
+    eps = synth.nm_to_len(0.1)
+    kw = dict(a0=0.1, tau=1.0, dt=0.05, softening=eps, envelope=synth.ENV_FLAT, rate_model=1,
+              ionize_every=0, zmax=zmax, n_ions=n, slot_base=n, seed=1234567, r_loc=3 * rw,
+              r_create=rw, species=AR, boundary=1, box=L, min_image=1)
+    st = oracle.State(c.x, c.u, c.z, c.mass, c.w, c.active)
+    p = oracle.make_params(a0=0.1, tau=1.0, dt=0.05, eps=eps, env=oracle.ENV_FLAT, box=L,
+                           boundary=oracle.BOUNDARY_PERIODIC, min_image=1)
+    for s_ in range(3):
+        st.step = 40 + s_
+        oracle.ionize_pass_box(st, p, AR, n, n, zmax, kw["seed"], kw["dt"], kw["r_loc"],
+                               kw["r_create"], box=L)
+    kind = np.where(st.active == 0, md.KIND_INACTIVE, np.where(st.z < 0, md.KIND_ELECTRON,
+                                                              md.KIND_ION))
+    hp = md.HostParticles(st.x, st.u, st.z, st.mass, st.w, kind)
+    with md.Context([md.make_config(**kw)], [hp]) as ctx:
+        g0 = ctx.get_particles(0)
+        ctx.ionize()
+        info = ctx.ionization(0)
+    kc = oracle.coulomb_constant(0.8)
+    e64 = oracle.coulomb_field(st.x[:n], st.x, st.q(), eps, kc, self_idx=np.arange(n), box=L)
+    emag64 = np.linalg.norm(e64, axis=1)          # laser: a0 sin(0) = 0 at step 0
+    rel = np.abs(info["emag"] - emag64) / np.sqrt(np.mean(emag64 ** 2))
+    assert np.percentile(rel, 99) < 2e-5
+    e_open = oracle.coulomb_field(st.x[:n], st.x, st.q(), eps, kc, self_idx=np.arange(n))
+    assert np.percentile(np.abs(np.linalg.norm(e_open, axis=1) - emag64) / emag64, 90) > 1e-3
+    ne64, te64 = oracle.local_moments(st.x[:n], st, kw["r_loc"], box=L)
+    both = (ne64 > 0) & (info["ne"] > 0)
+    assert both.sum() > 0.5 * (ne64 > 0).sum()
+    same = np.isclose(info["ne"][both], ne64[both], rtol=1e-12)
+    assert same.mean() > 0.95
+    np.testing.assert_allclose(info["te"][both][same], te64[both][same], rtol=2e-5, atol=1e-6)
+    z_ref, fired_ref, _, _ = oracle.decide(np.arange(n), g0.z[:n], info["emag"], info["ne"],
+                                           info["te"], AR, zmax, kw["seed"], 0, kw["dt"],
+                                           kw["r_create"])
+    assert np.array_equal(info["fired"], fired_ref)
+    kw["ionize_every"] = 1
+    with md.Context([md.make_config(**kw)], [hp]) as ctx:
+        ctx.step(6)
+        g = ctx.get_particles(0)
+        d = ctx.diagnostics(0)
+    live = g.kind != md.KIND_INACTIVE
+    assert int(np.sum((g.w * g.z)[live])) == 0 and d["n_nonfinite"] == 0
+    assert g.z[:n].sum() > st.z[:n].sum()
