@@ -77,6 +77,12 @@ MUTANTS_OTHER = [
     ("moments_no_mean_frame", "ionize_oracle.c",
      "double var = su2 / sw - (mx * mx + my * my + mz * mz);", "double var = su2 / sw;",
      "test_oracle_ionize.py"),
+    ("rate_residual_charge", "ionize_oracle.c",
+     "double w_ofi = io_adk_rate_au(F, ip, (double)(z + 1)) / IO_TIME_AU;",
+     "double w_ofi = io_adk_rate_au(F, ip, (double)z) / IO_TIME_AU;", "test_oracle_ionize.py"),
+    ("rate_lotz_wrong_shell", "ionize_oracle.c",
+     "io_lotz_rate_cgs(ip_ev[z], te, q_outer[z])", "io_lotz_rate_cgs(ip_ev[z], te, q_outer[0])",
+     "test_oracle_ionize.py"),
     ("moments_min_image_dropped", "ionize_oracle.c",
      "if (box > 0.0) d[c] -= box * nearbyint(d[c] / box);", "", "test_oracle_ionize.py"),
     ("decision_le", "ionize_oracle.c", "if (alpha < P) {", "if (alpha > P) {",
