@@ -634,48 +634,48 @@ __device__ __forceinline__ bool sum_sources(Stage<TILE, STAGES>& sm, unsigned& i
         else
           sum_tile<R, POT, false>(tile, cnt, xi, yi, zi, eps2, acc, L, invL);
       } else {
-      float qt;
-      if (tile_uniform_q(tile, cnt, qt)) {
-        // one charge for the whole tile (records are grouped by species);
-        // an uncharged tile adds nothing
-        if (qt != 0.0f) {
+        float qt;
+        if (tile_uniform_q(tile, cnt, qt)) {
+          // one charge for the whole tile (records are grouped by species);
+          // an uncharged tile adds nothing
+          if (qt != 0.0f) {
+            int j = 0;
+            for (; j + 8 <= cnt; j += 8) {
+#pragma unroll
+              for (int q = 0; q < 8; ++q)
+                pair_u<R, POT, MI>(lds_f4(tile + 16u * (j + q)), xi, yi, zi, eps2, acc, L, invL);
+              if (POT) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                  kahan_add(acc.sp[r], acc.cp[r], acc.ap[r] * qt);
+                  acc.ap[r] = 0.0f;
+                }
+              }
+            }
+            for (; j < cnt; ++j)
+              pair_u<R, POT, MI>(lds_f4(tile + 16u * j), xi, yi, zi, eps2, acc, L, invL);
+            fold_q<R, POT>(acc, qt);
+          }
+        } else {
           int j = 0;
           for (; j + 8 <= cnt; j += 8) {
 #pragma unroll
             for (int q = 0; q < 8; ++q)
-              pair_u<R, POT, MI>(lds_f4(tile + 16u * (j + q)), xi, yi, zi, eps2, acc, L, invL);
+              pair<R, POT, MI>(lds_f4(tile + 16u * (j + q)), xi, yi, zi, eps2, acc, L, invL);
             if (POT) {
+              // potential terms of one species share a sign: fold them often so
+              // the FP32 partial stays small against a cancelling total
 #pragma unroll
               for (int r = 0; r < R; ++r) {
-                kahan_add(acc.sp[r], acc.cp[r], acc.ap[r] * qt);
+                kahan_add(acc.sp[r], acc.cp[r], acc.ap[r]);
                 acc.ap[r] = 0.0f;
               }
             }
           }
           for (; j < cnt; ++j)
-            pair_u<R, POT, MI>(lds_f4(tile + 16u * j), xi, yi, zi, eps2, acc, L, invL);
-          fold_q<R, POT>(acc, qt);
+            pair<R, POT, MI>(lds_f4(tile + 16u * j), xi, yi, zi, eps2, acc, L, invL);
+          fold<R, POT>(acc);
         }
-      } else {
-        int j = 0;
-        for (; j + 8 <= cnt; j += 8) {
-#pragma unroll
-          for (int q = 0; q < 8; ++q)
-            pair<R, POT, MI>(lds_f4(tile + 16u * (j + q)), xi, yi, zi, eps2, acc, L, invL);
-          if (POT) {
-            // potential terms of one species share a sign: fold them often so
-            // the FP32 partial stays small against a cancelling total
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-              kahan_add(acc.sp[r], acc.cp[r], acc.ap[r]);
-              acc.ap[r] = 0.0f;
-            }
-          }
-        }
-        for (; j < cnt; ++j)
-          pair<R, POT, MI>(lds_f4(tile + 16u * j), xi, yi, zi, eps2, acc, L, invL);
-        fold<R, POT>(acc);
-      }
       }
     }
     __syncthreads();

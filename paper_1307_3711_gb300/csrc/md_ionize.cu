@@ -310,28 +310,28 @@ __global__ void __launch_bounds__(THREADS) k_ion_field(const IonArgs a) {
           ion_tile<R, false>(ptile, &sm.vel[s][0], cnt, xi, yi, zi, eps2, rloc2e, acc, mom, L,
                              invL);
       } else {
-      float qt;
-      bool uniform, has_e;
-      tile_class(ptile, cnt, qt, uniform, has_e);
-      if (uniform) {
-        if (qt < 0.0f) {
-          ion_pairs_moments<R, true>(ptile, &sm.vel[s][0], cnt, xi, yi, zi, eps2, rloc2e, acc,
-                                     mom);
-          fold_q<R, false>(acc, qt);
-        } else if (qt > 0.0f) {
+        float qt;
+        bool uniform, has_e;
+        tile_class(ptile, cnt, qt, uniform, has_e);
+        if (uniform) {
+          if (qt < 0.0f) {
+            ion_pairs_moments<R, true>(ptile, &sm.vel[s][0], cnt, xi, yi, zi, eps2, rloc2e, acc,
+                                       mom);
+            fold_q<R, false>(acc, qt);
+          } else if (qt > 0.0f) {
 #pragma unroll 4
-          for (int j = 0; j < cnt; ++j) pair_u<R, false>(lds_f4(ptile + 16u * j), xi, yi, zi, eps2, acc);
-          fold_q<R, false>(acc, qt);
+            for (int j = 0; j < cnt; ++j) pair_u<R, false>(lds_f4(ptile + 16u * j), xi, yi, zi, eps2, acc);
+            fold_q<R, false>(acc, qt);
+          }
+        } else if (has_e) {
+          ion_pairs_moments<R, false>(ptile, &sm.vel[s][0], cnt, xi, yi, zi, eps2, rloc2e, acc,
+                                      mom);
+          fold<R, false>(acc);
+        } else {
+#pragma unroll 4
+          for (int j = 0; j < cnt; ++j) pair<R, false>(lds_f4(ptile + 16u * j), xi, yi, zi, eps2, acc);
+          fold<R, false>(acc);
         }
-      } else if (has_e) {
-        ion_pairs_moments<R, false>(ptile, &sm.vel[s][0], cnt, xi, yi, zi, eps2, rloc2e, acc,
-                                    mom);
-        fold<R, false>(acc);
-      } else {
-#pragma unroll 4
-        for (int j = 0; j < cnt; ++j) pair<R, false>(lds_f4(ptile + 16u * j), xi, yi, zi, eps2, acc);
-        fold<R, false>(acc);
-      }
       }
     }
     __syncthreads();
