@@ -49,7 +49,7 @@ typedef enum {
     MD_ERR_TIMEOUT = -4,    /* a device-side wait exceeded its budget */
     MD_ERR_NONFINITE = -5,  /* diagnostics found NaN/Inf in the state */
     MD_ERR_STATE = -6,      /* call not valid in the current state */
-    MD_ERR_UNSUPPORTED = -7 /* feature not available in this build */
+    MD_ERR_UNSUPPORTED = -7 /* device or option this library does not support */
 } md_status;
 
 /* Temporal envelope of the laser (Eq. 3 and its readings). */

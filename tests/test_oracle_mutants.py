@@ -137,3 +137,50 @@ def test_ionization_and_surrogate_pins_catch_planted_mistake(name, fname, old, n
                                                              tmp_path):
     r = _run_mutant(tmp_path, fname, old, new, pins)
     assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
+
+
+# (name, exact text in oracle/__init__.py, replacement, pin file): slips in the
+# oracle's Python layer, which forms each macro's charge and charge-to-mass
+# ratio from its weight (Eq. 1) before calling the C code
+MUTANTS_PY = [
+    ("macro_charge_unweighted", "np.where(self.active > 0, self.w * self.z, 0.0)",
+     "np.where(self.active > 0, 1.0 * self.z, 0.0)", "test_oracle_pins.py"),
+    ("charge_to_mass_of_the_macro", "return (self.z / self.mass)",
+     "return (self.w * self.z / self.mass)", "test_oracle_pins.py"),
+    ("kinetic_energy_unweighted", "wm = (state.w * state.mass)", "wm = (state.mass)",
+     "test_oracle_pins.py"),
+]
+
+_PY_RUNNER = """
+import sys
+sys.path.insert(0, {root!r})
+import pytest
+import oracle
+src = open(oracle.__file__).read()
+assert src.count({old!r}) == 1, "mutation anchor not unique"
+exec(compile(src.replace({old!r}, {new!r}), oracle.__file__, "exec"), oracle.__dict__)
+sys.exit(pytest.main(["-x", "-q", "-p", "no:cacheprovider", {pins!r}]))
+"""
+
+
+@pytest.mark.parametrize("name,old,new,pins", MUTANTS_PY, ids=[m[0] for m in MUTANTS_PY])
+def test_pins_catch_planted_mistake_in_python_layer(name, old, new, pins, tmp_path):
+    runner = tmp_path / "run_mutant.py"
+    runner.write_text(_PY_RUNNER.format(root=ROOT, old=old, new=new,
+                                        pins=os.path.join(ROOT, "tests", pins)))
+    r = subprocess.run([sys.executable, str(runner)], cwd=ROOT, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode not in (0, 5), f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
+    assert "AssertionError" in r.stdout or "assert" in r.stdout, r.stdout[-2000:]
+
+
+def test_python_layer_runner_passes_without_a_mistake(tmp_path):
+    """Control: the same runner with the anchor left as it is passes every pin,
+    so a caught mutant fails because of its slip alone."""
+    old = MUTANTS_PY[0][1]
+    runner = tmp_path / "run_mutant.py"
+    runner.write_text(_PY_RUNNER.format(root=ROOT, old=old, new=old,
+                                        pins=os.path.join(ROOT, "tests", "test_oracle_pins.py")))
+    r = subprocess.run([sys.executable, str(runner)], cwd=ROOT, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stdout[-2000:]

@@ -353,6 +353,15 @@ def _asymptotic_energy(x, u, q, m, kc):
     return ke + kc * q * qin / r
 
 
+def _charge_inside(x, q):
+    """Q_in(r) / r: the charge of the macros nearer the centre, over r."""
+    r = np.linalg.norm(x, axis=1)
+    order = np.argsort(r)
+    qin = np.empty_like(q)
+    qin[order] = np.cumsum(q[order]) - q[order]
+    return qin / r
+
+
 def test_coulomb_explosion_spectrum_of_uniform_ion_sphere():
     """Ions only, uniform ball, from rest, laser off (Sec. III: <E> = 3/5 E_max):
     dN/dE ~ sqrt(E) on [0, E_max], E_max = K q Q / R0; CDF (E/E_max)^{3/2},
@@ -380,6 +389,71 @@ def test_coulomb_explosion_spectrum_of_uniform_ion_sphere():
     assert (s ** 2).mean() == pytest.approx(3 / 7, abs=0.02)
     ks = stats.kstest(np.clip(s, 0, 1), lambda v: np.clip(v, 0, 1) ** 1.5)
     assert ks.pvalue > 1e-3
+
+
+# ------------------------------------------- macro-particle lumping (Eq. 1)
+
+def _split_macros(c, frac):
+    """Every macro k becomes two coincident macros of weights frac_k w_k and
+    (1 - frac_k) w_k, with the same position, momentum, charge number and mass."""
+    idx = np.repeat(np.arange(c.x.shape[0]), 2)
+    w = np.empty(idx.size)
+    w[0::2] = frac * c.w
+    w[1::2] = (1.0 - frac) * c.w
+    return oracle.State(c.x[idx], c.u[idx], c.z[idx], c.mass[idx], w)
+
+
+def test_lumping_split_macros_follow_the_whole():
+    """Eq. 1: a macro of weight w stands for w atoms, so it carries charge w z
+    and mass w m.  Its charge-to-mass ratio is an atom's, whatever w, and its
+    field is w times an atom's.  A macro split into two coincident parts whose
+    weights add up to w therefore moves exactly as the whole did, and so does
+    everything around it (the softened pair at r = 0 exerts no force).
+    Laser on, ions and hot electrons, random weights in [1, 3] and random
+    splits: 40 steps in which the particles move by most of the radius."""
+    rng = np.random.default_rng(11)
+    r0 = synth.nm_to_len(2.0)
+    c = synth.make_cluster(13, 200, 600, r0, 3, synth.MASS_40AMU, kT_e_ev=50.0)
+    c.w[:] = rng.uniform(1.0, 3.0, c.w.shape)
+    frac = rng.uniform(0.2, 0.8, c.w.shape)
+    p = oracle.make_params(a0=0.5, tau=40.0, t0=-40.0, dt=0.05, eps=synth.nm_to_len(0.1),
+                           env=oracle.ENV_GAUSS, pol=0)
+    whole = oracle.State(c.x, c.u, c.z, c.mass, c.w)
+    parts = _split_macros(c, frac)
+    oracle.md_steps(whole, p, 40, nthreads=4)
+    oracle.md_steps(parts, p, 40, nthreads=4)
+    xs, us = np.abs(whole.x).max(), np.abs(whole.u).max()
+    assert np.abs(whole.x - c.x).max() > 0.5 * xs
+    for h in (0, 1):
+        assert np.abs(parts.x[h::2] - whole.x).max() < 1e-11 * xs
+        assert np.abs(parts.u[h::2] - whole.u).max() < 1e-10 * us
+    dw, dp = oracle.diagnostics(whole, p), oracle.diagnostics(parts, p)
+    assert dp["ke"] == pytest.approx(dw["ke"], rel=1e-10)
+    np.testing.assert_allclose(dp["p"], dw["p"], rtol=1e-10, atol=1e-12 * np.abs(dw["p"]).max())
+
+
+def test_lumping_explosion_energy_per_atom_independent_of_n_macro():
+    """The lumping check of Sec. III, on the closed-form case: the same uniform
+    ion ball, from rest, laser off, sampled by 1200 macros of weight 1 and by
+    300 macros of weight 4 (a 75 % cut in N_macro at the same total charge Q).
+    The mean energy per atom after the explosion is 3/5 of E_max = K z Q / R0
+    in both, within the sampling error of 300 macros (std 0.015)."""
+    r0, m, zv = synth.nm_to_len(2.0), synth.MASS_40AMU, 1
+    means = []
+    for n, w in ((1200, 1.0), (300, 4.0)):
+        c = synth.make_cluster(5, n, 0, r0, zv, m, weight=w)
+        q_tot = (c.w * c.z).sum()
+        e_max = KC * zv * q_tot / r0
+        tau = math.sqrt(m * r0 ** 3 / (KC * zv * q_tot))
+        st = oracle.State(c.x, c.u, c.z, c.mass, c.w)
+        p = oracle.make_params(a0=0.0, dt=tau / 40, eps=0.0, env=oracle.ENV_FLAT)
+        oracle.md_steps(st, p, 240, nthreads=4)  # t = 6 tau
+        # per atom: kinetic energy of one atom plus z K Q_in(r) / r (macros inside r)
+        q = c.w * c.z
+        e_atom = _asymptotic_energy(st.x, st.u, q, m, KC) + KC * (c.z - q) * _charge_inside(st.x, q)
+        assert e_atom.mean() / e_max == pytest.approx(3 / 5, abs=0.045)
+        means.append(e_atom.mean() / e_max)
+    assert means[1] == pytest.approx(means[0], rel=0.08)
 
 
 # ---------------------------------------------- minimum-image forces (periodic)
