@@ -236,6 +236,56 @@ def test_ionize_pass_conserves_charge_and_uses_slots():
     assert st.active[n_ion:].sum() == st.z[:n_ion].sum()
 
 
+def test_ionize_pass_field_is_coulomb_plus_laser_at_t_n():
+    """The pass ionizes in the total field at the ion (Sec. II): the softened
+    Coulomb field of the others plus the laser field a(t_n), t_n = t0 + n dt.
+    Two records along the polarization: a neutral atom at the origin and a
+    Z = 2 ion at distance d on +x.  At the atom the two fields are collinear:
+    |a0 sin t_n - K Z d / (d^2 + eps^2)^{3/2}| (flat envelope, linear
+    polarization); at the ion the neutral atom adds nothing: |a0 sin t_n|."""
+    n_ion, zmax = 2, 8
+    d, eps, a0, zq = synth.nm_to_len(1.0), synth.nm_to_len(0.1), 1e-3, 2
+    x = np.zeros((n_ion + n_ion * zmax, 3))
+    x[1, 0] = d
+    z = np.zeros(x.shape[0], np.int32)
+    z[1] = zq
+    active = np.zeros(x.shape[0], np.uint8)
+    active[:n_ion] = 1
+    st = oracle.State(x, np.zeros_like(x), z, np.full(x.shape[0], AR["mass"]),
+                      np.ones(x.shape[0]), active, step=13)
+    p = oracle.make_params(a0=a0, tau=1.0, t0=0.7, dt=0.05, eps=eps, env=oracle.ENV_FLAT)
+    kc = oracle.coulomb_constant(0.8)
+    t_n = 0.7 + 13 * 0.05
+    e_c = kc * zq * d / (d * d + eps * eps) ** 1.5
+    assert 0.2 < e_c / (a0 * abs(math.sin(t_n))) < 5  # both terms matter
+    _, amag, _, _ = oracle.ionize_pass(st, p, AR, n_ion, n_ion, zmax, seed=1, dt_ion=1e-9,
+                                       r_loc=d / 4, r_create=d / 4)
+    assert amag[0] == pytest.approx(abs(a0 * math.sin(t_n) - e_c), rel=1e-12)
+    assert amag[1] == pytest.approx(abs(a0 * math.sin(t_n)), rel=1e-12)
+
+
+def test_ionize_pass_conserves_weighted_charge():
+    """Macro atoms of unequal weight (Eq. 1): a freed electron stands for as
+    many electrons as its atom has atoms, and has the electron mass, so the
+    total charge sum w z stays zero pass after pass."""
+    n_ion, zmax = 200, 8
+    c = synth.make_cluster(6, n_ion, 0, synth.nm_to_len(2.0), 0, AR["mass"],
+                           n_electron_slots=n_ion * zmax)
+    c.w[:n_ion] = np.random.default_rng(2).uniform(0.5, 3.0, n_ion)
+    st = oracle.State(c.x, c.u, c.z, c.mass, c.w, c.active)
+    p = oracle.make_params(a0=0.3, tau=1.0, dt=0.05, eps=synth.nm_to_len(0.1),
+                           env=oracle.ENV_FLAT)
+    for k in range(3):
+        st.step = 20 + k
+        oracle.ionize_pass(st, p, AR, n_ion, n_ion, zmax, seed=8, dt_ion=5.0,
+                           r_loc=3 * synth.nm_to_len(AR["r_w_nm"]),
+                           r_create=synth.nm_to_len(AR["r_w_nm"]))
+        q = st.w * st.z * st.active
+        assert abs(q.sum()) < 1e-12 * np.abs(q).sum()
+    el = np.nonzero(st.active[n_ion:])[0] + n_ion
+    assert el.size > n_ion and np.all(st.mass[el] == 1.0)
+
+
 def test_next_free_slot_follows_the_last_active_slot():
     """A state whose slot region has holes: new electrons go after the last
     active slot, never into a hole."""

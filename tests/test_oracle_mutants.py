@@ -141,7 +141,8 @@ def test_ionization_and_surrogate_pins_catch_planted_mistake(name, fname, old, n
 
 # (name, exact text in oracle/__init__.py, replacement, pin file): slips in the
 # oracle's Python layer, which forms each macro's charge and charge-to-mass
-# ratio from its weight (Eq. 1) before calling the C code
+# ratio from its weight (Eq. 1) before calling the C code, and which adds the
+# laser field to the Coulomb field and places the freed electrons in a pass
 MUTANTS_PY = [
     ("macro_charge_unweighted", "np.where(self.active > 0, self.w * self.z, 0.0)",
      "np.where(self.active > 0, 1.0 * self.z, 0.0)", "test_oracle_pins.py"),
@@ -149,6 +150,16 @@ MUTANTS_PY = [
      "return (self.w * self.z / self.mass)", "test_oracle_pins.py"),
     ("kinetic_energy_unweighted", "wm = (state.w * state.mass)", "wm = (state.mass)",
      "test_oracle_pins.py"),
+    ("pass_field_laser_dropped", "amag = np.linalg.norm(e + a[None, :], axis=1)",
+     "amag = np.linalg.norm(e, axis=1)", "test_oracle_ionize.py"),
+    ("pass_field_laser_subtracted", "amag = np.linalg.norm(e + a[None, :], axis=1)",
+     "amag = np.linalg.norm(e - a[None, :], axis=1)", "test_oracle_ionize.py"),
+    ("pass_time_without_t0", "t = params.t0 + state.step * params.dt",
+     "t = state.step * params.dt", "test_oracle_ionize.py"),
+    ("freed_electron_unit_weight", "state.w[slot] = state.w[i]", "state.w[slot] = 1.0",
+     "test_oracle_ionize.py"),
+    ("freed_electron_ion_mass", "state.mass[slot] = 1.0", "state.mass[slot] = state.mass[i]",
+     "test_oracle_ionize.py"),
 ]
 
 _PY_RUNNER = """
