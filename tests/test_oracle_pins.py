@@ -343,6 +343,41 @@ def test_momentum_and_energy_conservation_laser_off():
     assert errs[0] / errs[1] == pytest.approx(4.0, rel=0.15)
 
 
+@pytest.mark.parametrize("pol", [0, 1])
+def test_momentum_balance_laser_on(pol):
+    """Laser on: the Coulomb forces are internal and cancel in the sum, so the
+    total momentum changes only by the laser's force,
+    dP/dt = (sum w q) a + sum w q beta x b (Eqs. 4-9).  For the Boris kick this
+    holds exactly per step with beta = (u^{n-1/2} + u^{n+1/2}) / (2 gamma^-),
+    gamma^- that of u^- = u^{n-1/2} + (q/m)(dt/2)(E + a): the rotation is
+    u^+ - u^- = (q/m) dt (u^+ + u^-)/(2 gamma^-) x b.  A charged plasma
+    (Z = 2 ions and fewer electrons, random weights) at the peak of the pulse,
+    where the magnetic term is a third to a half of the change."""
+    rng = np.random.default_rng(4)
+    r0, eps, a0, T = synth.nm_to_len(2.0), synth.nm_to_len(0.1), 0.5, 20 * math.pi
+    c = synth.make_cluster(21, 300, 400, r0, 2, synth.MASS_40AMU, kT_e_ev=20.0)
+    c.w[:] = rng.uniform(0.5, 3.0, c.w.shape)
+    st = oracle.State(c.x, c.u, c.z, c.mass, c.w)
+    p = oracle.make_params(a0=a0, tau=T, t0=0.5 * T - 1.0, dt=0.02, eps=eps,
+                           env=oracle.ENV_SIN2, pol=pol)
+    wm, wq, qm = c.w * c.mass, c.w * c.z, c.z / c.mass
+    mag_share = 0.0
+    for n in range(60):
+        u_prev = st.u.copy()
+        e = oracle.self_field(st.x, wq, eps, KC, nthreads=4)
+        a, b = oracle.laser_fields(p.t0 + n * p.dt, a0, pol, oracle.ENV_SIN2, T)
+        oracle.md_steps(st, p, 1, nthreads=4)
+        dp = (wm[:, None] * (st.u - u_prev)).sum(0)
+        um = u_prev + (0.5 * p.dt * qm)[:, None] * (e + a)
+        beta = 0.5 * (u_prev + st.u) / np.sqrt(1.0 + (um * um).sum(1))[:, None]
+        magnetic = p.dt * (wq[:, None] * np.cross(beta, b)).sum(0)
+        expect = p.dt * wq.sum() * a + magnetic
+        scale = p.dt * a0 * (np.abs(wq) * (1.0 + np.linalg.norm(beta, axis=1))).sum()
+        assert np.abs(dp - expect).max() < 1e-12 * scale
+        mag_share = max(mag_share, np.abs(magnetic).max() / np.abs(expect).max())
+    assert mag_share > 0.25  # the v x b term is tested, not only the electric one
+
+
 def _asymptotic_energy(x, u, q, m, kc):
     """Spherical symmetry with no shell crossing: E_inf = KE + K q Q_in(r)/r."""
     r = np.linalg.norm(x, axis=1)
