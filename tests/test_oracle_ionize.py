@@ -191,6 +191,27 @@ def test_decision_statistics_constant_rate():
     assert np.all(f2 == 0) and np.all(z2 == 8) and np.all(p2 == 0)
 
 
+def test_survival_after_n_passes_is_exponential():
+    """Sec. II: at a constant rate nu each pass ionizes with P = 1 - exp(-nu dt),
+    independently of the earlier passes, so the fraction of atoms not yet
+    ionized after n passes is exp(-nu n dt) (memoryless decay); nu is the rate
+    function's, pinned above.  nu dt = 0.35: a first-order P = nu dt would
+    leave (0.65)^n instead."""
+    n = 40000
+    ids = np.arange(n)
+    z = np.zeros(n, np.int32)
+    amag = np.full(n, 0.012)
+    nu = oracle.rate_total(0.012, 0, 0.0, 0.0, AR)
+    dt_ion = 0.35 / nu
+    alive = np.ones(n, bool)
+    for k in range(6):
+        _, fired, _, _ = oracle.decide(ids, z, amag, np.zeros(n), np.zeros(n), AR, 8, seed=12,
+                                       step=100 + k, dt_ion=dt_ion, r_create=0.001)
+        alive &= fired == 0
+        s_exp = math.exp(-nu * dt_ion * (k + 1))
+        assert abs(alive.mean() - s_exp) < 4 * math.sqrt(s_exp * (1 - s_exp) / n)
+
+
 def test_electron_placement_uniform_in_ball():
     n = 20000
     rc = 0.004

@@ -87,6 +87,8 @@ MUTANTS_OTHER = [
      "if (box > 0.0) d[c] -= box * nearbyint(d[c] / box);", "", "test_oracle_ionize.py"),
     ("decision_le", "ionize_oracle.c", "if (alpha < P) {", "if (alpha > P) {",
      "test_oracle_ionize.py"),
+    ("probability_first_order", "ionize_oracle.c", "double P = -expm1(-nu * dt_ion);",
+     "double P = nu * dt_ion;", "test_oracle_ionize.py"),
     ("placement_radius", "ionize_oracle.c", "double ph = 2.0 * IO_PI * u2, r = r_create * cbrt(u3);",
      "double ph = 2.0 * IO_PI * u2, r = r_create * u3;", "test_oracle_ionize.py"),
     ("mlp_dsilu", "mlp_oracle.c", "return s * (1.0 + a * (1.0 - s));", "return s * (1.0 + a * s);",
