@@ -71,6 +71,22 @@ def test_energy_bins_and_relativistic_energy():
     assert det.hist[0].tolist() == [1, 1, 0, 0, 1]   # all moved along +x
 
 
+def test_energy_bins_are_equal_widths_of_e_max():
+    """The IEDF bins split [0, e_max) into nbins equal widths: ions with
+    E = (k + 1/2) e_max / nbins, k = 0..nbins-1, fill one bin each, and one
+    at 1.001 e_max goes to the overflow bin (E = (gamma - 1) m c^2 set by u)."""
+    mass, nbins, e_max = synth.MASS_40AMU, 10, 2.0e4
+    energies = np.concatenate([(np.arange(nbins) + 0.5) * e_max / nbins, [1.001 * e_max]])
+    n = energies.size
+    st = one_ion_state(n, mass=mass)
+    g = 1.0 + energies / (mass * ME_C2_EV)
+    st.u[:, 1] = np.sqrt(g * g - 1.0)
+    det = oracle.Detectors(n, radius=1.0, e_max_ev=e_max, nbins=nbins)
+    det.record(np.tile([0.0, 0.9, 0.0], (n, 1)), np.tile([0.0, 1.1, 0.0], (n, 1)), st)
+    assert det.hist[4].tolist() == [1] * (nbins + 1)
+    assert det.hist[2].tolist() == [1] * (nbins + 1)   # all along +y
+
+
 def test_coulomb_explosion_seen_at_nine_radii():
     """Uniform ion sphere from rest, laser off: an ion starting at s = r0/R0
     keeps its enclosed charge Q s^3 and crosses 9 R0 with

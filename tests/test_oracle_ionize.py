@@ -136,7 +136,8 @@ def test_local_moments_constructed_case():
     """Six electrons at 0.5 r_loc along +-x, +-y, +-z with u = drift +- v
     along the same axis (spread about the mean: <|u - <u>|^2> = v^2):
     ne = 6 w / volume, Te = m c^2 v^2 / 3 in the local mean frame; an ion,
-    an inactive slot and a far electron do not count."""
+    a neutral atom, an inactive slot and a far electron do not count.  The
+    periodic version in a box much larger than r_loc gives the same."""
     r_loc, v, w = 0.01, 0.003, 2.0
     drift = np.array([0.002, -0.001, 0.0005])
     pos = []
@@ -146,16 +147,17 @@ def test_local_moments_constructed_case():
             p = np.zeros(3); p[ax] = 0.5 * s * r_loc
             q = drift.copy(); q[ax] += s * v
             pos.append(p); vel.append(q)
-    x = np.array(pos + [[0.001, 0, 0], [0, 0.002, 0], [2 * r_loc, 0, 0]])
-    u = np.array(vel + [[0, 0, 0], [0, 0, 0], [0.5, 0, 0]])
-    z = np.array([-1] * 6 + [3, 0, -1])
-    active = np.array([1] * 6 + [1, 0, 1], np.uint8)
-    st = oracle.State(x, u, z, np.ones(9), np.full(9, w), active)
-    ne, te = oracle.local_moments(np.zeros((1, 3)), st, r_loc)
+    x = np.array(pos + [[0.001, 0, 0], [0, 0.002, 0], [2 * r_loc, 0, 0], [0, 0, -0.003]])
+    u = np.array(vel + [[0, 0, 0], [0, 0, 0], [0.5, 0, 0], [0.4, 0, 0]])
+    z = np.array([-1] * 6 + [3, 0, -1, 0])
+    active = np.array([1] * 6 + [1, 0, 1, 1], np.uint8)
+    st = oracle.State(x, u, z, np.ones(10), np.full(10, w), active)
     k = 2 * math.pi / 0.8e-6
     vol_cm3 = 4 / 3 * math.pi * (r_loc / k) ** 3 * 1e6
-    assert ne[0] == pytest.approx(6 * w / vol_cm3, rel=1e-12)
-    assert te[0] == pytest.approx(510998.95 * v * v / 3, rel=1e-9)
+    for box in (0.0, 1.0):
+        ne, te = oracle.local_moments(np.zeros((1, 3)), st, r_loc, box=box)
+        assert ne[0] == pytest.approx(6 * w / vol_cm3, rel=1e-12)
+        assert te[0] == pytest.approx(510998.95 * v * v / 3, rel=1e-9)
     ne, te = oracle.local_moments(np.array([[10.0, 0, 0]]), st, r_loc)
     assert ne[0] == 0 and te[0] == 0
 
@@ -210,6 +212,27 @@ def test_survival_after_n_passes_is_exponential():
         alive &= fired == 0
         s_exp = math.exp(-nu * dt_ion * (k + 1))
         assert abs(alive.mean() - s_exp) < 4 * math.sqrt(s_exp * (1 - s_exp) / n)
+
+
+def test_decision_uses_all_64_bits_of_seed_and_step():
+    """The Philox key is the whole 64-bit seed and the counter holds the whole
+    64-bit step (with the ion index), so seeds or steps that differ only in
+    their high 32 bits draw independent numbers."""
+    n = 4000
+    ids = np.arange(n)
+    z = np.zeros(n, np.int32)
+    amag = np.full(n, 0.012)
+    args = (np.zeros(n), np.zeros(n), AR, 8)
+
+    def fired(seed, step):
+        return oracle.decide(ids, z, amag, *args, seed=seed, step=step, dt_ion=2.0,
+                             r_create=0.001)[1]
+
+    base = fired(5, 3)
+    for seed, step in ((5 + 2 ** 32, 3), (5, 3 + 2 ** 32)):
+        other = fired(seed, step)
+        # independent Bernoulli draws agree on about P^2 + (1-P)^2 of the ions
+        assert 0.05 < (base != other).mean() < 0.95
 
 
 def test_electron_placement_uniform_in_ball():

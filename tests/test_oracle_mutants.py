@@ -52,6 +52,20 @@ MUTANTS = [
     ("min_image_not_in_steps", "if (p->min_image && periodic)", "if (p->min_image && !periodic)"),
     ("min_image_softening", "double rm2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + eps2;",
      "double rm2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];"),
+    ("wrap_box_not_centred", "x[k] = x[k] - box * floor((x[k] + h) / box);",
+     "x[k] = x[k] - box * floor(x[k] / box);"),
+    ("mixed_switch_inverted", "if (mode == 2 && t >= t_switch) return;",
+     "if (mode == 2 && t < t_switch) return;"),
+    ("mixed_switch_at_step_start",
+     "or_boundary(&x[3 * i], p->boundary, p->box, t + p->dt, p->t_switch);",
+     "or_boundary(&x[3 * i], p->boundary, p->box, t, p->t_switch);"),
+    ("diag_time_without_t0",
+     "double t = p->t0 + (double)step * p->dt;\n    double a[3], b[3];\n    for",
+     "double t = (double)step * p->dt;\n    double a[3], b[3];\n    for"),
+    ("ke_neutral_atoms_as_electrons", "if (z[i] < 0) kee += k; else kei += k;",
+     "if (z[i] <= 0) kee += k; else kei += k;"),
+    ("inactive_records_pushed", "            if (!active[i]) continue;\n            double et",
+     "            double et"),
 ]
 
 # (name, file, exact text, replacement, pin file) for the ionization and
@@ -87,6 +101,15 @@ MUTANTS_OTHER = [
      "if (box > 0.0) d[c] -= box * nearbyint(d[c] / box);", "", "test_oracle_ionize.py"),
     ("decision_le", "ionize_oracle.c", "if (alpha < P) {", "if (alpha > P) {",
      "test_oracle_ionize.py"),
+    ("moments_count_neutral_atoms", "ionize_oracle.c",
+     "if (!active_s[j] || zs[j] >= 0) continue;\n            double dx",
+     "if (!active_s[j] || zs[j] > 0) continue;\n            double dx", "test_oracle_ionize.py"),
+    ("counter_step_high_word", "ionize_oracle.c",
+     "uint32_t ctr[4] = {(uint32_t)id[i], (uint32_t)step, (uint32_t)((uint64_t)step >> 32), 0u};",
+     "uint32_t ctr[4] = {(uint32_t)id[i], (uint32_t)step, 0u, 0u};", "test_oracle_ionize.py"),
+    ("key_seed_high_word", "ionize_oracle.c",
+     "uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};",
+     "uint32_t key[2] = {(uint32_t)seed, 0u};", "test_oracle_ionize.py"),
     ("probability_first_order", "ionize_oracle.c", "double P = -expm1(-nu * dt_ion);",
      "double P = nu * dt_ion;", "test_oracle_ionize.py"),
     ("placement_radius", "ionize_oracle.c", "double ph = 2.0 * IO_PI * u2, r = r_create * cbrt(u3);",
@@ -106,6 +129,8 @@ MUTANTS_OTHER = [
      "return sqrt(1.0 + uu) * mass * OR_ME_C2_EV;", "test_oracle_detectors.py"),
     ("detector_no_once", "md_oracle.c", "        crossed[i] = 1;\n", "\n",
      "test_oracle_detectors.py"),
+    ("detector_bin_width", "md_oracle.c", "int b = (int)floor(ke * (double)nbins / e_max);",
+     "int b = (int)floor(ke * (double)(nbins - 1) / e_max);", "test_oracle_detectors.py"),
 ]
 
 

@@ -343,6 +343,57 @@ def test_momentum_and_energy_conservation_laser_off():
     assert errs[0] / errs[1] == pytest.approx(4.0, rel=0.15)
 
 
+def test_diagnostics_use_the_half_step_mean_of_the_step_taken():
+    """Integer-time diagnostics: u^n = (u^{n-1/2} + u^{n+1/2}) / 2, where
+    u^{n+1/2} is the momentum the step from t_n actually produces (laser at
+    t_n = t0 + n dt).  So the diagnostic momentum and kinetic energy at step n
+    equal the mean of the momenta before and after md_steps advances one step
+    (laser on near its peak, t0 != 0, random weights)."""
+    rng = np.random.default_rng(9)
+    c = synth.make_cluster(17, 150, 300, synth.nm_to_len(2.0), 2, synth.MASS_40AMU,
+                           kT_e_ev=30.0)
+    c.w[:] = rng.uniform(0.5, 3.0, c.w.shape)
+    T = 20 * math.pi
+    p = oracle.make_params(a0=0.5, tau=T, t0=0.5 * T - 0.2, dt=0.02, eps=synth.nm_to_len(0.1),
+                           env=oracle.ENV_SIN2, pol=1)
+    st = oracle.State(c.x, c.u, c.z, c.mass, c.w, step=7)
+    oracle.md_steps(st, p, 3)
+    d = oracle.diagnostics(st, p)
+    u_prev = st.u.copy()
+    oracle.md_steps(st, p, 1)
+    un = 0.5 * (u_prev + st.u)
+    wm = c.w * c.mass
+    uu = (un * un).sum(1)
+    ke = (wm * uu / (np.sqrt(1.0 + uu) + 1.0))
+    np.testing.assert_allclose(d["p"], (wm[:, None] * un).sum(0), rtol=1e-12,
+                               atol=1e-14 * np.abs(wm[:, None] * un).sum())
+    assert d["ke"] == pytest.approx(ke.sum(), rel=1e-12)
+    assert d["ke_electrons"] == pytest.approx(ke[c.z < 0].sum(), rel=1e-12)
+
+
+def test_inactive_records_and_neutral_atoms_in_steps_and_diagnostics():
+    """A neutral atom (z = 0) feels no force and moves in a straight line; it
+    is counted with the ions (z >= 0) in the kinetic energy.  An inactive
+    record (an unused electron slot) neither moves nor counts.  With a lone
+    electron as the only charge and the laser off nothing accelerates, so the
+    energies are the closed forms w m (gamma(u) - 1)."""
+    x = np.array([[0.01, 0.0, 0.0], [-0.02, 0.005, 0.0], [0.0, 0.0, 0.03]])
+    u = np.array([[0.02, -0.01, 0.005], [0.3, 0.1, -0.2], [0.5, 0.5, 0.5]])
+    z, m, w = [0, -1, -1], [72916.0, 1.0, 1.0], [2.5, 1.5, 1.0]
+    st = oracle.State(x, u, z, m, w, active=[1, 1, 0])
+    p = oracle.make_params(dt=0.05, eps=1e-3, env=oracle.ENV_FLAT)
+    d = oracle.diagnostics(st, p)
+    g = np.sqrt(1.0 + (u * u).sum(1))
+    assert d["n_active"] == 2
+    assert d["ke_ions"] == pytest.approx(w[0] * m[0] * (g[0] - 1.0), rel=1e-12)
+    assert d["ke_electrons"] == pytest.approx(w[1] * m[1] * (g[1] - 1.0), rel=1e-12)
+    assert d["pe"] == 0.0
+    oracle.md_steps(st, p, 20)
+    np.testing.assert_array_equal(st.x[2], x[2])
+    np.testing.assert_array_equal(st.u, u)
+    np.testing.assert_allclose(st.x[:2], x[:2] + 20 * 0.05 * u[:2] / g[:2, None], rtol=1e-13)
+
+
 @pytest.mark.parametrize("pol", [0, 1])
 def test_momentum_balance_laser_on(pol):
     """Laser on: the Coulomb forces are internal and cancel in the sum, so the
@@ -551,6 +602,53 @@ def test_min_image_newton_third_law_and_small_systems():
     xs = rng.uniform(-0.2, 0.2, size=(n, 3)) * box
     assert np.array_equal(oracle.self_field(xs, q, eps, KC, box=box),
                           oracle.self_field(xs, q, eps, KC))
+
+
+def _free_flight(x0, u, dt, n):
+    """Straight-line positions x0 + k dt u / gamma, k = 0..n (no force)."""
+    v = np.asarray(u) / math.sqrt(1.0 + float(np.dot(u, u)))
+    return np.asarray(x0)[None, :] + dt * np.arange(n + 1)[:, None] * v[None, :]
+
+
+def test_periodic_wrap_is_the_box_centred_on_the_cluster():
+    """Sec. II periodic boundary: the box [-L/2, L/2)^3 is centred on the
+    cluster; a particle that leaves through a face comes back through the
+    opposite one with its momentum unchanged.  A free relativistic particle
+    (z = 0: no force, laser off) crosses faces on all three axes: after every
+    step it sits at the wrapped straight-line position."""
+    box, dt, n = 1.0, 0.05, 120
+    x0, u0 = np.array([0.45, -0.42, 0.3]), np.array([0.6, -0.35, 0.25])
+    st = oracle.State(x0[None, :], u0[None, :], [0], [3.0], [1.0])
+    p = oracle.make_params(dt=dt, box=box, boundary=oracle.BOUNDARY_PERIODIC, env=oracle.ENV_FLAT)
+    line = _free_flight(x0, u0, dt, n)
+    assert np.all(np.abs(line[-1] - x0) > box)  # every axis crossed at least once
+    for k in range(1, n + 1):
+        oracle.md_steps(st, p, 1)
+        assert np.all(st.x[0] >= -0.5 * box) and np.all(st.x[0] < 0.5 * box)
+        np.testing.assert_allclose(st.x[0], _wrap(line[k], box), rtol=0, atol=1e-12)
+    np.testing.assert_array_equal(st.u[0], u0)
+
+
+def test_mixed_boundary_switches_to_open_at_t_switch():
+    """Sec. II mixed boundary: periodic while t < t_switch, open from then on;
+    the wrap of x^{n+1} is the one in force at t_{n+1}.  A free particle
+    (0.19 box per step) crosses an x face before the switch (wrapped) and
+    again during the step from t_9 to t_10, with t_switch = 9.5 dt in between
+    (not wrapped), then flies on out of the box."""
+    box, dt, n = 1.0, 0.2, 16
+    u0 = np.array([4.0, 0.0, 0.0])
+    s = dt * 4.0 / math.sqrt(17.0)
+    x0 = np.array([_wrap(0.5 * box - 9.5 * s, box), 0.1, 0.0])
+    st = oracle.State(x0[None, :], u0[None, :], [0], [3.0], [1.0])
+    p = oracle.make_params(dt=dt, box=box, boundary=oracle.BOUNDARY_MIXED, t_switch=9.5 * dt,
+                           env=oracle.ENV_FLAT)
+    line = _free_flight(x0, u0, dt, n)
+    assert line[9, 0] > 0.5 * box and line[10, 0] > 1.5 * box > line[9, 0]
+    for k in range(1, n + 1):
+        oracle.md_steps(st, p, 1)
+        want = _wrap(line[k], box) if k < 10 else _wrap(line[9], box) + (line[k] - line[9])
+        np.testing.assert_allclose(st.x[0], want, rtol=0, atol=1e-12)
+    assert st.x[0, 0] > 0.5 * box  # outside the box after the switch
 
 
 def test_min_image_steps_follow_the_open_pair_at_its_image():
