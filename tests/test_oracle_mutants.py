@@ -1,10 +1,13 @@
 """Planted mistakes in the oracle, on the CPU: each plausible slip (dropped
-term, wrong sign, wrong power, transposed operand, missing factor) compiled
-into a mutant of the oracle's C sources must make at least one pin fail.  This
-shows that the pins constrain every part of the FP64 oracle."""
+term, wrong sign, wrong power, transposed operand, missing factor), compiled
+into a mutant of the oracle's C sources or re-executed in its Python layer,
+must make at least one pin fail.  The mutants run side by side, each in its
+own process and directory.  Not constrained: the l* and Gamma terms of the
+ADK prefactor away from n* = 1, where no independent value is at hand."""
 import os
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 import pytest
 
@@ -152,20 +155,6 @@ def _run_mutant(tmp_path, fname, old, new, pin_file):
                           cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
 
 
-@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
-def test_pins_catch_planted_mistake(name, old, new, tmp_path):
-    r = _run_mutant(tmp_path, "md_oracle.c", old, new, "test_oracle_pins.py")
-    assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
-
-
-@pytest.mark.parametrize("name,fname,old,new,pins", MUTANTS_OTHER,
-                         ids=[m[0] for m in MUTANTS_OTHER])
-def test_ionization_and_surrogate_pins_catch_planted_mistake(name, fname, old, new, pins,
-                                                             tmp_path):
-    r = _run_mutant(tmp_path, fname, old, new, pins)
-    assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
-
-
 # (name, exact text in oracle/__init__.py, replacement, pin file): slips in the
 # oracle's Python layer, which forms each macro's charge and charge-to-mass
 # ratio from its weight (Eq. 1) before calling the C code, and which adds the
@@ -201,24 +190,80 @@ sys.exit(pytest.main(["-x", "-q", "-p", "no:cacheprovider", {pins!r}]))
 """
 
 
-@pytest.mark.parametrize("name,old,new,pins", MUTANTS_PY, ids=[m[0] for m in MUTANTS_PY])
-def test_pins_catch_planted_mistake_in_python_layer(name, old, new, pins, tmp_path):
+
+
+def _run_py_mutant(tmp_path, old, new, pin_file):
     runner = tmp_path / "run_mutant.py"
     runner.write_text(_PY_RUNNER.format(root=ROOT, old=old, new=new,
-                                        pins=os.path.join(ROOT, "tests", pins)))
-    r = subprocess.run([sys.executable, str(runner)], cwd=ROOT, capture_output=True, text=True,
-                       timeout=600)
+                                        pins=os.path.join(ROOT, "tests", pin_file)))
+    return subprocess.run([sys.executable, str(runner)], cwd=ROOT, capture_output=True,
+                          text=True, timeout=600)
+
+
+# every mutant by name: (runner, file, anchor, replacement, pin file)
+ALL = {}
+for _n, _old, _new in MUTANTS:
+    ALL[_n] = ("c", "md_oracle.c", _old, _new, "test_oracle_pins.py")
+for _n, _f, _old, _new, _pins in MUTANTS_OTHER:
+    ALL[_n] = ("c", _f, _old, _new, _pins)
+for _n, _old, _new, _pins in MUTANTS_PY:
+    ALL[_n] = ("py", None, _old, _new, _pins)
+ALL["control_no_mistake"] = ("py", None, MUTANTS_PY[0][1], MUTANTS_PY[0][1],
+                             "test_oracle_pins.py")
+assert len(ALL) == len(MUTANTS) + len(MUTANTS_OTHER) + len(MUTANTS_PY) + 1, "names collide"
+
+
+@pytest.fixture(scope="module")
+def mutant_runs(request, tmp_path_factory):
+    """Runs the selected mutants' pin files side by side (each in its own
+    process and directory) and returns {name: CompletedProcess or exception}."""
+    wanted = [it.callspec.params["name"] for it in request.session.items
+              if getattr(it, "module", None) is not None and it.module.__file__ == __file__
+              and hasattr(it, "callspec") and "name" in it.callspec.params]
+
+    def one(name):
+        kind, fname, old, new, pins = ALL[name]
+        d = tmp_path_factory.mktemp(name)
+        try:
+            if kind == "c":
+                return name, _run_mutant(d, fname, old, new, pins)
+            return name, _run_py_mutant(d, old, new, pins)
+        except Exception as exc:  # reported by the mutant's own test
+            return name, exc
+
+    with ThreadPoolExecutor(max_workers=max(2, (os.cpu_count() or 2) // 2)) as ex:
+        return dict(ex.map(one, wanted))
+
+
+def _result(runs, name):
+    r = runs[name]
+    if isinstance(r, Exception):
+        raise r
+    return r
+
+
+@pytest.mark.parametrize("name", [m[0] for m in MUTANTS])
+def test_pins_catch_planted_mistake(name, mutant_runs):
+    r = _result(mutant_runs, name)
+    assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
+
+
+@pytest.mark.parametrize("name", [m[0] for m in MUTANTS_OTHER])
+def test_ionization_and_surrogate_pins_catch_planted_mistake(name, mutant_runs):
+    r = _result(mutant_runs, name)
+    assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
+
+
+@pytest.mark.parametrize("name", [m[0] for m in MUTANTS_PY])
+def test_pins_catch_planted_mistake_in_python_layer(name, mutant_runs):
+    r = _result(mutant_runs, name)
     assert r.returncode not in (0, 5), f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
     assert "AssertionError" in r.stdout or "assert" in r.stdout, r.stdout[-2000:]
 
 
-def test_python_layer_runner_passes_without_a_mistake(tmp_path):
+@pytest.mark.parametrize("name", ["control_no_mistake"])
+def test_python_layer_runner_passes_without_a_mistake(name, mutant_runs):
     """Control: the same runner with the anchor left as it is passes every pin,
     so a caught mutant fails because of its slip alone."""
-    old = MUTANTS_PY[0][1]
-    runner = tmp_path / "run_mutant.py"
-    runner.write_text(_PY_RUNNER.format(root=ROOT, old=old, new=old,
-                                        pins=os.path.join(ROOT, "tests", "test_oracle_pins.py")))
-    r = subprocess.run([sys.executable, str(runner)], cwd=ROOT, capture_output=True, text=True,
-                       timeout=600)
+    r = _result(mutant_runs, name)
     assert r.returncode == 0, r.stdout[-2000:]
