@@ -371,6 +371,43 @@ def single_thread_rate(w, seconds: float):
             "sample": f"FP64 field at {nt} sampled targets from all {c.n} sources ({dt:.1f} s)"}
 
 
+def oracle_step_scaling(ns=(20000, 50000, 100000), sweep_n=20000):
+    """The paper's Fig. 7 on the host cores, with the FP64 oracle as it stands:
+    one full step (field of every particle from all the others, laser, Boris
+    push, drift; OpenMP over targets, the paper's own decomposition) of the
+    same cluster family at several N on all cores (Fig. 7b: time ~ N^2), and
+    at N = sweep_n on 1, 2, 4, ... cores (Fig. 7a)."""
+    import oracle
+    threads = os.cpu_count() or 1
+
+    def one_step(n, nthreads):
+        w = workload(n, seed=0)
+        c = w.cluster
+        st = oracle.State(c.x, c.u, c.z, c.mass, c.w, c.active)
+        p = oracle.make_params(a0=w.a0, tau=w.tau, t0=w.t0, dt=w.dt, eps=w.eps, pol=w.pol,
+                               env=w.env, boundary=w.boundary, box=w.box, t_switch=w.t_switch,
+                               lambda_um=w.lambda_um)
+        t0 = time.perf_counter()
+        oracle.md_steps(st, p, 1, nthreads=nthreads)
+        return time.perf_counter() - t0
+
+    rows = []
+    for n in ns:
+        s = one_step(n, threads)
+        rows.append({"n": n, "s_per_step": s, "pairs_per_s": float(n) ** 2 / s,
+                     "ns_per_pair": 1e9 * s / float(n) ** 2})
+    counts = sorted({k for k in (1, 2, 4, 8, 16, 32, 64, 128) if k < threads} | {threads})
+    cores = []
+    for k in counts:
+        s = one_step(sweep_n, k)
+        cores.append({"cores": k, "s_per_step": s})
+    for r in cores:
+        r["speedup"] = cores[0]["s_per_step"] / r["s_per_step"]
+    return {"kind": "oracle", "cores": threads, "unit": UNIT,
+            "what": "one full FP64 oracle step (all targets, OpenMP over targets) per row",
+            "n_rows": rows, "n_for_core_rows": sweep_n, "core_rows": cores}
+
+
 def run_nscale(args):
     """Step time against N for the headline cluster family (Xe3+ + 3 e per
     ion at the density of the 400k case), one autotuned context per N: the
@@ -407,9 +444,10 @@ def run_nscale(args):
             rows.append({"n": n, "ms_per_step": t, "pairs_per_s": pairs / (t / 1e3),
                          "frac_at_max_clock": pairs / (t / 1e3) / peak,
                          "tuning": list(ctx.tuning())})
+    cpu = None if args.no_cpu_baseline else oracle_step_scaling()
     print(json.dumps({"workload": "nscale: xe3 clusters at the density of the 400k case",
                       "device": gpu_name, "l2": "flushed between timed steps",
-                      "rows": rows}), flush=True)
+                      "rows": rows, "cpu_baseline": cpu}), flush=True)
 
 
 def build_contexts(md, args, rank, stream):

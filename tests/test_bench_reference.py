@@ -23,3 +23,17 @@ def test_reference_arm_prints_json_line():
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
     assert d["gpu_launches"] == 0
+
+
+def test_oracle_step_scaling_rows():
+    """The host leg of the N sweep (the paper's Fig. 7 with the oracle): one
+    full oracle step per N on all cores and one per core count."""
+    sys.path.insert(0, ROOT)
+    import bench
+    d = bench.oracle_step_scaling(ns=(400, 800), sweep_n=400)
+    assert d["kind"] == "oracle" and d["cores"] >= 1
+    assert [r["n"] for r in d["n_rows"]] == [400, 800]
+    assert all(r["s_per_step"] > 0 and r["pairs_per_s"] > 0 for r in d["n_rows"])
+    counts = [r["cores"] for r in d["core_rows"]]
+    assert counts[0] == 1 and counts[-1] == d["cores"] and counts == sorted(set(counts))
+    assert d["core_rows"][0]["speedup"] == 1.0
