@@ -93,6 +93,31 @@ def test_ionization_decisions_bit_exact_with_oracle(md):
         assert total_fired > 0.2 * n
 
 
+@pytest.mark.parametrize("seed,step", [(1234567 + (5 << 32), 40), (99, (1 << 32) + 40)])
+def test_decisions_with_64_bit_seed_and_step_follow_oracle(md, seed, step):
+    """The Philox key is the whole 64-bit seed and the counter holds the whole
+    64-bit step: with a seed or a step beyond 2^32 the GPU's decisions equal
+    the oracle's from the same inputs, and differ from those that the low 32
+    bits alone would draw."""
+    c, kw = ar_case()
+    kw["seed"] = seed
+    n = c.n_ions
+    with md.Context([md.make_config(**kw)], [md.HostParticles.from_cluster(c)]) as ctx:
+        ctx.set_step(step)
+        assert ctx.step_index() == step
+        g0 = ctx.get_particles(0)
+        ctx.ionize()
+        info = ctx.ionization(0)
+        g1 = ctx.get_particles(0)
+    args = (np.arange(n), g0.z[:n], info["emag"], info["ne"], info["te"], AR, kw["zmax"])
+    z_ref, fired_ref, _, _ = oracle.decide(*args, seed, step, kw["dt"], kw["r_create"])
+    assert np.array_equal(info["fired"], fired_ref)
+    assert np.array_equal(g1.z[:n], z_ref)
+    assert fired_ref.sum() > 20
+    low = oracle.decide(*args, seed & 0xFFFFFFFF, step & 0xFFFFFFFF, kw["dt"], kw["r_create"])[1]
+    assert (low != fired_ref).any()
+
+
 def test_ionization_inputs_match_oracle(md):
     """The GPU's field magnitude at the ions agrees with the FP64 oracle to the
     FP32 field tolerance, the local electron density exactly and the local

@@ -705,6 +705,41 @@ def test_mixed_boundary_periodic_then_open(md):
     assert np.percentile(np.abs(g2.x - st.x).max(1), 90) < 1e-4 * L
 
 
+@pytest.mark.parametrize("boundary", [1, 2])
+def test_free_flight_through_the_faces_closed_form(md, boundary):
+    """Sec. II boundaries on free particles (neutral atoms: no force, laser
+    off), against the straight line, not the oracle.  Periodic: after every
+    step each particle sits at its wrapped line position in [-L/2, L/2).
+    Mixed with t_switch = 9.5 dt: wrapped up to x^9; from x^10 on (the wrap of
+    x^{n+1} is the one in force at t_{n+1}) the particles fly on unwrapped."""
+    rng = np.random.default_rng(21)
+    n, L, dt, steps = 64, 1.0, 0.2, 16
+    x0 = rng.uniform(-0.5 * L, 0.5 * L, size=(n, 3))
+    u0 = rng.normal(size=(n, 3)) * 2.0
+    c = synth.Cluster(x0, u0, np.zeros(n, np.int32), np.full(n, 3.0), np.ones(n),
+                      np.ones(n, np.uint8), n_ions=n)
+    cfg = md.make_config(dt=dt, envelope=synth.ENV_FLAT, boundary=boundary, box=L,
+                         t_switch=9.5 * dt)
+    line = x0[None] + dt * np.arange(steps + 1)[:, None, None] * (
+        u0 / np.sqrt(1.0 + (u0 * u0).sum(1, keepdims=True)))[None]
+    wrap = lambda x: x - L * np.floor((x + 0.5 * L) / L)
+    with md.Context([cfg], [md.HostParticles.from_cluster(c)]) as ctx:
+        for k in range(1, steps + 1):
+            ctx.step(1)
+            g = ctx.get_particles(0)
+            if boundary == 1 or k < 10:
+                want = wrap(line[k])
+                assert g.x.min() >= -0.5 * L and g.x.max() < 0.5 * L
+            else:
+                want = wrap(line[9]) + (line[k] - line[9])
+            np.testing.assert_allclose(g.x, want, rtol=0, atol=1e-12)
+        np.testing.assert_array_equal(g.u, u0)
+    if boundary == 2:
+        assert np.abs(g.x).max() > 0.5 * L  # some left the box after the switch
+        # and some crossed a face during the step that ends after t_switch
+        assert (np.floor((line[10] + 0.5 * L) / L) != np.floor((line[9] + 0.5 * L) / L)).any()
+
+
 def test_fp64_reference_field_matches_oracle_bitwise(md):
     """The FP64 reference direct sum evaluates the oracle's formula in the
     oracle's order with every operation rounded to nearest: the same bits
