@@ -170,7 +170,9 @@ typedef struct {
 /* ---- context life cycle -------------------------------------------------
  * md_init: creates a context holding n_clusters independent clusters (a
  * batched parameter scan when > 1), uploads their particles and returns it
- * in *out.  cfgs[c] and parts[c] describe cluster c.  stream: a cudaStream_t
+ * in *out.  A cluster is the system of Sec. II: macro-ions and macro-electrons
+ * (weight w = N_atoms / N_macro, Eq. 1) in a sphere of radius R0, with the
+ * laser, boundary and ionization settings of its md_config.  cfgs[c] and parts[c] describe cluster c.  stream: a cudaStream_t
  * to launch on (NULL: the library creates its own).  The device must be an
  * sm_103 GPU.  Errors: MD_ERR_ARG (n_clusters < 1, n < 1, dt/softening/
  * lambda <= 0, bad enum, kind/z mismatch), MD_ERR_OOM, MD_ERR_CUDA. */
@@ -185,11 +187,15 @@ const char *md_last_error(void);
  * captured CUDA graph.  Asynchronous.  nsteps >= 0. */
 md_status md_step(md_ctx *ctx, int32_t nsteps);
 
-/* md_sync: waits for the context's stream and reports device-side errors. */
+/* md_sync: waits for the context's stream and reports device-side errors
+ * (runtime control; no counterpart in the paper). */
 md_status md_sync(md_ctx *ctx);
 
 /* md_diagnostics: FP64 energies, momentum and charge-state counts of cluster
- * `cluster` at the current step (synchronous; out is caller-owned). */
+ * `cluster` at the current step (synchronous; out is caller-owned): the
+ * energy balance and the charge-state distribution that Sec. III reports, at
+ * integer time as md_diag states.  Errors: MD_ERR_ARG (NULL, bad index),
+ * MD_ERR_NONFINITE (a record with NaN/Inf; out is still filled). */
 md_status md_diagnostics(md_ctx *ctx, int32_t cluster, md_diag *out);
 
 /* md_step_diag: one step of every cluster (as md_step(ctx, 1)) that also
@@ -206,7 +212,9 @@ md_status md_diagnostics(md_ctx *ctx, int32_t cluster, md_diag *out);
 md_status md_step_diag(md_ctx *ctx, md_diag *out);
 
 /* md_count_active: the number of records of cluster `cluster` that are not
- * MD_KIND_INACTIVE (md_diag.n_active) without the rest of the diagnostics:
+ * MD_KIND_INACTIVE (md_diag.n_active; the macro-particles in play once the
+ * ionization pass of Sec. II has freed electrons) without the rest of the
+ * diagnostics:
  * an O(n) count, where md_diagnostics also sums the potential over all pairs.
  * Synchronous; *out is caller-owned.  Errors: MD_ERR_ARG (NULL, bad index). */
 md_status md_count_active(md_ctx *ctx, int32_t cluster, int64_t *out);
@@ -223,7 +231,8 @@ md_status md_count_active(md_ctx *ctx, int32_t cluster, int64_t *out);
 md_status md_get_particles(md_ctx *ctx, int32_t cluster, md_particles *out);
 md_status md_set_particles(md_ctx *ctx, int32_t cluster, const md_particles *in);
 
-/* md_get_fields: the Coulomb field (without the laser) and, if phi != NULL,
+/* md_get_fields: the Coulomb field of Sec. II's particle mover (without the
+ * laser) and, if phi != NULL,
  * the potential K_C sum_{j!=i} Q_j / sqrt(r^2+eps^2) at the current positions
  * of cluster `cluster`, computed by the same FP32/Kahan sum as md_step.
  * In clusters with ionization, records in a block of 256 targets with no
@@ -285,7 +294,8 @@ md_status md_set_detectors(md_ctx *ctx, int32_t cluster, const md_detector_confi
  * for `inside` during the call.  Synchronous. */
 md_status md_get_iedf(md_ctx *ctx, int32_t cluster, uint64_t *detected, uint64_t *inside);
 
-/* md_get_ionization: per-ion results of the last pass of cluster `cluster`
+/* md_get_ionization: per-ion inputs and outcome of the last ionization pass
+ * (Sec. II, ionization paragraph) of cluster `cluster`
  * (host arrays of n_ions entries, any may be NULL): field magnitude |E| (paper
  * units), local electron density (cm^-3) and temperature (eV), probability P
  * and whether the ion ionized.  Synchronous. */
@@ -293,21 +303,23 @@ md_status md_get_ionization(md_ctx *ctx, int32_t cluster, double *emag, double *
                             double *prob, uint8_t *fired);
 
 /* md_set_step: sets the step counter (with md_set_particles, a checkpoint is
- * restored exactly: the laser time and the Philox counters derive from the
- * step).  Synchronous. */
+ * restored exactly: the laser time t_n = t0 + n dt of Eqs. 3-9 and the Philox
+ * counters derive from the step).  Synchronous.  Errors: MD_ERR_ARG (step < 0). */
 md_status md_set_step(md_ctx *ctx, int64_t step);
 
-/* md_wait_selftest: exercises the bounded device waits.  One CTA waits on an
+/* md_wait_selftest (runtime check; no counterpart in the paper): exercises
+ * the bounded device waits.  One CTA waits on an
  * mbarrier phase that nothing completes; after budget_ms (0 < budget_ms <=
  * 5000, converted with the nominal SM clock) the wait gives up, the kernel
  * sets the context's error word and returns.  Returns MD_ERR_TIMEOUT (the
  * expected outcome) and leaves the context usable. */
 md_status md_wait_selftest(md_ctx *ctx, double budget_ms);
 
-/* Step counter of the context (steps taken since md_init). Synchronous. */
+/* Step counter of the context (steps taken since md_init, or as set by
+ * md_set_step): step n is at time t0 + n dt.  Synchronous. */
 md_status md_get_step(md_ctx *ctx, int64_t *step);
 
-/* ---- tuning -------------------------------------------------------------
+/* ---- tuning (runtime control; no counterpart in the paper) ---------------
  * md_tuning_list: writes up to cap entries of the compiled kernel
  * configurations into list (may be NULL) and returns their number.
  * md_set_tuning: uses the given configuration from now on.
@@ -362,8 +374,8 @@ md_status md_coulomb_field_device_noalloc(const void *src, int64_t ns, const voi
                                           int64_t nt, float eps2, int64_t self_offset,
                                           double *e, double *phi, void *stream);
 
-/* md_coulomb_field_fp64_device: the FP64 reference of the direct sum (the
- * precision study's reference, not on the hot path).  For each target i:
+/* md_coulomb_field_fp64_device: the FP64 reference of the direct sum of
+ * Sec. II (the precision study's reference, not on the hot path).  For each target i:
  *   E_i   = kc sum_j Q_j (x_i - x_j) / (|x_i - x_j|^2 + eps^2)^{3/2}
  *   phi_i = kc sum_j Q_j / sqrt(|x_i - x_j|^2 + eps^2)
  * over sources j in index order, skipping j == self_idx[i] and Q_j == 0, every
@@ -462,14 +474,15 @@ double md_coulomb_constant(double lambda_um);                  /* K_C = 2 pi r_e
 double md_a0_from_intensity(double intensity_wcm2, double lambda_um); /* Eq. 2 */
 double md_n_atoms(double r0, double r_wigner_seitz);           /* Eq. 1 */
 
-/* Measurement helper: FP32 fused multiply-adds per second (lane operations)
+/* Measurement helper (no counterpart in the paper): FP32 fused multiply-adds per second (lane operations)
  * of the current device, from kernels of 8 independent FMA chains per thread
  * on 8 x SMs CTAs of 256 threads: *ffma_per_s with scalar fma.rn.f32,
  * *packed_fma_per_s (may be NULL) with packed fma.rn.f32x2.  Synchronous on
  * `stream`.  The denominators of the FP32 roofline fraction. */
 md_status md_measure_fp32_peak(double *ffma_per_s, double *packed_fma_per_s, void *stream);
 
-/* Number of SMs and the device name of the current device (for reports). */
+/* Number of SMs and the device name of the current device (for reports; no
+ * counterpart in the paper).  name: host buffer of name_cap bytes. */
 md_status md_device_info(int32_t *sm_count, char *name, int32_t name_cap);
 
 #ifdef __cplusplus
