@@ -158,6 +158,10 @@ def test_local_moments_constructed_case():
         ne, te = oracle.local_moments(np.zeros((1, 3)), st, r_loc, box=box)
         assert ne[0] == pytest.approx(6 * w / vol_cm3, rel=1e-12)
         assert te[0] == pytest.approx(510998.95 * v * v / 3, rel=1e-9)
+        # at 0.4 micron the same r_loc (in 1/k) is half as long in cm: 8 times the density
+        ne4, te4 = oracle.local_moments(np.zeros((1, 3)), st, r_loc, lambda_um=0.4, box=box)
+        assert ne4[0] == pytest.approx(8 * 6 * w / vol_cm3, rel=1e-12)
+        assert te4[0] == pytest.approx(te[0], rel=1e-12)
     ne, te = oracle.local_moments(np.array([[10.0, 0, 0]]), st, r_loc)
     assert ne[0] == 0 and te[0] == 0
 
@@ -306,6 +310,36 @@ def test_ionize_pass_field_is_coulomb_plus_laser_at_t_n():
                                        r_loc=d / 4, r_create=d / 4)
     assert amag[0] == pytest.approx(abs(a0 * math.sin(t_n) - e_c), rel=1e-12)
     assert amag[1] == pytest.approx(abs(a0 * math.sin(t_n)), rel=1e-12)
+
+
+def test_ionize_pass_takes_the_moments_at_each_ion():
+    """The pass measures n_e and T_e around each ion (Sec. II): two neutral
+    atoms 10 r_loc apart, three electrons within r_loc of the second only,
+    with u = (+v, 0, 0), (-v, 0, 0), 0: n_e = 3 w / (4/3 pi r_loc^3) and
+    T_e = m c^2 (2 v^2 / 3) / 3 there, nothing at the first atom."""
+    n_ion, zmax, w = 2, 8, 1.5
+    r_loc, v = 0.01, 0.004
+    n = n_ion + n_ion * zmax
+    x = np.zeros((n, 3))
+    x[1, 0] = 10 * r_loc
+    x[2:5] = x[1] + np.array([[0, 0.3 * r_loc, 0], [0, -0.3 * r_loc, 0], [0, 0, 0.5 * r_loc]])
+    u = np.zeros((n, 3))
+    u[2, 0], u[3, 0] = v, -v
+    z = np.zeros(n, np.int32)
+    z[2:5] = -1
+    mass = np.ones(n)
+    mass[:n_ion] = AR["mass"]
+    active = np.zeros(n, np.uint8)
+    active[:5] = 1
+    st = oracle.State(x, u, z, mass, np.full(n, w), active)
+    p = oracle.make_params(a0=0.0, tau=1.0, dt=0.05, eps=1e-3, env=oracle.ENV_FLAT)
+    _, _, ne, te = oracle.ionize_pass(st, p, AR, n_ion, n_ion, zmax, seed=1, dt_ion=1e-9,
+                                      r_loc=r_loc, r_create=1e-4)
+    k = 2 * math.pi / 0.8e-6
+    vol_cm3 = 4 / 3 * math.pi * (r_loc / k) ** 3 * 1e6
+    assert ne[0] == 0.0 and te[0] == 0.0
+    assert ne[1] == pytest.approx(3 * w / vol_cm3, rel=1e-12)
+    assert te[1] == pytest.approx(510998.95 * (2 * v * v / 3) / 3, rel=1e-9)
 
 
 def test_ionize_pass_conserves_weighted_charge():

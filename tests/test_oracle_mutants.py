@@ -176,6 +176,13 @@ MUTANTS_PY = [
      "test_oracle_ionize.py"),
     ("freed_electron_ion_mass", "state.mass[slot] = 1.0", "state.mass[slot] = state.mass[i]",
      "test_oracle_ionize.py"),
+    ("pass_moments_not_at_the_ions",
+     "ne, te = local_moments(state.x[:n_ion], state, r_loc, lambda_um, box=box)",
+     "ne, te = local_moments(state.x[:n_ion] * 0.0, state, r_loc, lambda_um, box=box)",
+     "test_oracle_ionize.py"),
+    ("box_moments_fixed_wavelength",
+     "_ptr(state.active), float(r_loc), float(lambda_um), float(box),",
+     "_ptr(state.active), float(r_loc), 0.8, float(box),", "test_oracle_ionize.py"),
 ]
 
 _PY_RUNNER = """
