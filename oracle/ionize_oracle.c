@@ -18,12 +18,13 @@
  *   alpha in (0, 1] from Philox4x32-10 keyed on (seed) with counter
  *   (ion id, step lo, step hi, 0); the ion ionizes if alpha < P.
  *
- * Parity unpinned: the ADK rate away from n* = 1.  The tests fix it where it
- * reduces to Landau's exact hydrogen rate (n* = 1, where l* = 0 and both
- * Gamma factors of C^2 are 1); nothing in reach fixes the l* and Gamma terms
- * of C^2 for n* != 1 (planted slips there pass every test), and the species
- * data are unpinned as well, so the absolute rates of multi-electron ions rest
- * on the formula as written above.
+ * Parity unpinned: the ADK rate away from n* = 1.  The tests fix it where
+ * n* = 1 (l* = 0, both Gamma factors of C^2 equal 1): Landau's exact hydrogen
+ * rate, and its Coulomb scaling to hydrogen-like ions of any nuclear charge
+ * (Ip = Z^2/2), which fixes the Ip and F0 dependence.  Nothing in reach fixes
+ * the l* and Gamma terms of C^2 for n* != 1 (planted slips there pass every
+ * test), and the species data are unpinned as well, so the absolute rates of
+ * multi-electron ions rest on the formula as written above.
  */
 #include <math.h>
 #include <stdint.h>

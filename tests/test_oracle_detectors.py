@@ -71,20 +71,55 @@ def test_energy_bins_and_relativistic_energy():
     assert det.hist[0].tolist() == [1, 1, 0, 0, 1]   # all moved along +x
 
 
-def test_energy_bins_are_equal_widths_of_e_max():
+@pytest.mark.parametrize("axis,sign,row", [(0, 1, 0), (0, -1, 1), (1, 1, 2), (1, -1, 3)])
+def test_energy_bins_are_equal_widths_of_e_max(axis, sign, row):
     """The IEDF bins split [0, e_max) into nbins equal widths: ions with
-    E = (k + 1/2) e_max / nbins, k = 0..nbins-1, fill one bin each, and one
-    at 1.001 e_max goes to the overflow bin (E = (gamma - 1) m c^2 set by u)."""
+    E = (k + 1/2) e_max / nbins, k = 0..nbins-1, fill one bin each of their
+    cone's histogram and of the all-directions one, and one at 1.001 e_max goes
+    to the overflow bin (E = (gamma - 1) m c^2 set by u).  The detector sphere
+    is centred off the origin; the crossing is along the cone's axis."""
     mass, nbins, e_max = synth.MASS_40AMU, 10, 2.0e4
+    center = np.array([0.3, -0.2, 0.1])
     energies = np.concatenate([(np.arange(nbins) + 0.5) * e_max / nbins, [1.001 * e_max]])
     n = energies.size
     st = one_ion_state(n, mass=mass)
     g = 1.0 + energies / (mass * ME_C2_EV)
-    st.u[:, 1] = np.sqrt(g * g - 1.0)
-    det = oracle.Detectors(n, radius=1.0, e_max_ev=e_max, nbins=nbins)
-    det.record(np.tile([0.0, 0.9, 0.0], (n, 1)), np.tile([0.0, 1.1, 0.0], (n, 1)), st)
-    assert det.hist[4].tolist() == [1] * (nbins + 1)
-    assert det.hist[2].tolist() == [1] * (nbins + 1)   # all along +y
+    st.u[:, axis] = sign * np.sqrt(g * g - 1.0)
+    d = np.zeros(3)
+    d[axis] = sign
+    det = oracle.Detectors(n, radius=1.0, e_max_ev=e_max, nbins=nbins, center=center)
+    det.record(np.tile(center + 0.9 * d, (n, 1)), np.tile(center + 1.1 * d, (n, 1)), st)
+    for k in range(5):
+        want = [1] * (nbins + 1) if k in (row, 4) else [0] * (nbins + 1)
+        assert det.hist[k].tolist() == want, k
+    # the ions not yet recorded are binned at their own energies
+    st2 = one_ion_state(n, mass=mass)
+    st2.u[:] = st.u
+    fresh = oracle.Detectors(n, radius=1.0, e_max_ev=e_max, nbins=nbins, center=center)
+    assert fresh.inside(st2).tolist() == [1] * (nbins + 1)
+    assert det.inside(st).tolist() == [0] * (nbins + 1)   # all recorded already
+
+
+def test_only_crossings_from_inside_count():
+    """An ion that is already outside the sphere and moves further out (along
+    each axis and a diagonal), or one that stays inside, is not recorded; the
+    sphere is centred off the origin, so positions are taken relative to it."""
+    center = np.array([0.5, 0.4, -0.3])
+    dirs = np.array([[1, 0, 0], [0, 1, 0], [0, 0, 1], [0, -1, 0], [1, 1, 1] / np.sqrt(3)])
+    n = 2 * len(dirs)
+    st = one_ion_state(n)
+    st.u[:, 0] = 1e-3
+    x0 = np.concatenate([center + 1.05 * dirs, center + 0.5 * dirs])
+    x1 = np.concatenate([center + 1.2 * dirs, center + 0.9 * dirs])
+    det = oracle.Detectors(n, radius=1.0, nbins=10, center=center)
+    det.record(x0, x1, st)
+    assert det.hist.sum() == 0 and not det.crossed.any()
+    # the same moves seen from a sphere at the origin do cross it
+    det0 = oracle.Detectors(n, radius=1.0, nbins=10)
+    det0.record(x0 - center, x1 - center, st)
+    assert det0.hist[4].sum() == 0
+    det0.record(x1 - center, 1.1 * (x1 - center) / np.linalg.norm(x1 - center, axis=1)[:, None], st)
+    assert det0.hist[4].sum() == len(dirs)   # the inner ones now cross, the outer ones do not
 
 
 def test_coulomb_explosion_seen_at_nine_radii():

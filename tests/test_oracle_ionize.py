@@ -56,6 +56,22 @@ def test_adk_reduces_to_landau_hydrogen_rate(F):
                                                             rel=1e-12)
 
 
+@pytest.mark.parametrize("Z", [2, 3, 5])
+@pytest.mark.parametrize("f", [0.02, 0.05, 0.1])
+def test_adk_for_hydrogen_like_ions_follows_coulomb_scaling(Z, f):
+    """A hydrogen-like ion of nuclear charge Z (Ip = Z^2/2, residual charge Z,
+    so n* = 1 again) is hydrogen rescaled: lengths 1/Z, energies Z^2, fields
+    Z^3, rates Z^2.  Its exact weak-field rate is therefore Landau's rate at
+    F / Z^3 times Z^2: w = (4 Z^5 / F) exp(-2 Z^3 / (3F)).  This fixes the
+    Ip and F0 = (2 Ip)^{3/2} dependence of the ADK expression away from
+    Ip = 1/2 (f = F / Z^3)."""
+    F = f * Z ** 3
+    landau = Z ** 2 * (4.0 / f) * math.exp(-2.0 / (3.0 * f))
+    assert oracle.adk_rate_au(F, Z * Z / 2.0, float(Z)) == pytest.approx(landau, rel=1e-12)
+    assert landau == pytest.approx(4.0 * Z ** 5 / F * math.exp(-2.0 * Z ** 3 / (3.0 * F)),
+                                   rel=1e-12)
+
+
 def test_adk_structure():
     """Monotone in the field, vanishing as F -> 0, and suppressed for higher
     potentials at the same field."""

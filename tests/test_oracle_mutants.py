@@ -69,6 +69,7 @@ MUTANTS = [
      "if (z[i] <= 0) kee += k; else kei += k;"),
     ("inactive_records_pushed", "            if (!active[i]) continue;\n            double et",
      "            double et"),
+    ("wrap_half_box", "double h = 0.5 * box;", "double h = 0.5 / box;"),
 ]
 
 # (name, file, exact text, replacement, pin file) for the ionization and
@@ -84,6 +85,9 @@ MUTANTS_OTHER = [
      "return ((double)w) * (1.0 / 4294967296.0);", "test_oracle_ionize.py"),
     ("e1_series_sign", "ionize_oracle.c", "return -IO_EULER_GAMMA - log(x) + sum;",
      "return -IO_EULER_GAMMA - log(x) - sum;", "test_oracle_ionize.py"),
+    ("adk_field_scale", "ionize_oracle.c",
+     "return c2 * ip * pow(2.0 * F0 / F, 2.0 * ns - 1.0)",
+     "return c2 * ip * pow(2.0 / F0 / F, 2.0 * ns - 1.0)", "test_oracle_ionize.py"),
     ("adk_exponent", "ionize_oracle.c",
      "return c2 * ip * pow(2.0 * F0 / F, 2.0 * ns - 1.0) * exp(-2.0 * F0 / (3.0 * F));",
      "return c2 * ip * pow(2.0 * F0 / F, 2.0 * ns) * exp(-2.0 * F0 / (3.0 * F));",
@@ -134,6 +138,16 @@ MUTANTS_OTHER = [
      "test_oracle_detectors.py"),
     ("detector_bin_width", "md_oracle.c", "int b = (int)floor(ke * (double)nbins / e_max);",
      "int b = (int)floor(ke * (double)(nbins - 1) / e_max);", "test_oracle_detectors.py"),
+    ("detector_centre_sign", "md_oracle.c", "double a0 = x_prev[3 * i] - center[0]",
+     "double a0 = x_prev[3 * i] + center[0]", "test_oracle_detectors.py"),
+    ("detector_radius_sign", "md_oracle.c", "double rp2 = (a0 * a0 + a1 * a1) + a2 * a2;",
+     "double rp2 = (a0 * a0 - a1 * a1) + a2 * a2;", "test_oracle_detectors.py"),
+    ("detector_row_offset", "md_oracle.c", "if (-b0 >= c) hist[1 * (nbins + 1) + bin] += 1;",
+     "if (-b0 >= c) hist[1 * (nbins - 1) + bin] += 1;", "test_oracle_detectors.py"),
+    ("iedf_inside_wrong_record", "md_oracle.c",
+     "hist[or_energy_bin(or_ke_ev(&u[3 * i], mass[i]), e_max_ev, nbins)] += 1;",
+     "hist[or_energy_bin(or_ke_ev(&u[3 / (i + 1)], mass[i]), e_max_ev, nbins)] += 1;",
+     "test_oracle_detectors.py"),
 ]
 
 
