@@ -37,14 +37,21 @@ def state_of(g):
     return oracle.State(g.x, g.u, g.z, g.mass, g.w, (g.kind != 2).astype(np.uint8))
 
 
-def test_detector_counts_match_oracle_on_gpu_states(md):
+@pytest.mark.parametrize("offset", [(0.0, 0.0, 0.0), (0.3, -0.2, 0.1)])
+def test_detector_counts_match_oracle_on_gpu_states(md, offset):
+    """Exact counts against the oracle's detectors on the GPU's states, with
+    the detector sphere centred on the cluster and off it (centre offset in
+    units of R0)."""
     n = 600
     c, r0, e_max, cfg = explosion(md, n)
     nb = 64
     e_max_ev = 0.4 * e_max * ME_C2_EV   # at 2.5 R0 energies reach 0.6 E_max: some overflow
-    det = oracle.Detectors(n, radius=2.5 * r0, cone_deg=30.0, e_max_ev=e_max_ev, nbins=nb)
+    center = tuple(r0 * v for v in offset)
+    det = oracle.Detectors(n, radius=2.5 * r0, cone_deg=30.0, e_max_ev=e_max_ev, nbins=nb,
+                           center=center)
     with md.Context([cfg], [md.HostParticles.from_cluster(c)]) as ctx:
-        ctx.set_detectors(0, 2.5 * r0, cone_deg=30.0, e_max_ev=e_max_ev, n_bins=nb)
+        ctx.set_detectors(0, 2.5 * r0, cone_deg=30.0, e_max_ev=e_max_ev, n_bins=nb,
+                          center=center)
         g0 = ctx.get_particles(0)
         for _ in range(200):
             ctx.step(1)
