@@ -74,3 +74,8 @@ def test_features_definition_points():
     g = oracle.mlp_features(1e-6, 0, 1e15, 0.1, 15.0)
     np.testing.assert_allclose(f, g, atol=1e-15)
     assert f[2] == pytest.approx((15 - 19.5) / 4.5) and f[1] == 0.0
+    # the other ends of the normalised ranges: F = 10^0.1 F0, n_e = 1e24 cm^-3 and
+    # T_e = 10^2.8 Ip each map to +1
+    f = oracle.mlp_features(e_au_paper * 10 ** 0.1, 8, 1e24, 0.5 * hartree * 10 ** 2.8,
+                            0.5 * hartree)
+    np.testing.assert_allclose(f, [1.0, 1.0, 1.0, 1.0], atol=1e-9)

@@ -127,6 +127,9 @@ MUTANTS_OTHER = [
      "grad[OFF_W2 + k * NH + j] += da2[j] * h1[k];", "test_oracle_mlp.py"),
     ("mlp_loss_scale", "mlp_oracle.c", "dy[zs] = 2.0 * r / n;", "dy[zs] = r / n;",
      "test_oracle_mlp.py"),
+    ("mlp_temperature_scale", "mlp_oracle.c",
+     "f[3] = (log10(fmax(te, 0.1) / ip_ev) + 0.2) / 3.0;",
+     "f[3] = (log10(fmax(te, 0.1) / ip_ev) + 0.2) / 2.0;", "test_oracle_mlp.py"),
     ("detector_no_cone", "md_oracle.c", "if (b0 >= c) hist[0 * (nbins + 1) + bin] += 1;",
      "if (b0 >= 0.0) hist[0 * (nbins + 1) + bin] += 1;", "test_oracle_detectors.py"),
     ("detector_inward", "md_oracle.c", "if (!(rp2 < R2 && rn2 >= R2)) continue;",
