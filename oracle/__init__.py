@@ -4,8 +4,9 @@ TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
 ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` load it; the product
 library never does.  It shares no code with the CUDA path.
 
-The arithmetic lives in plain C (``md_oracle.c`` and, for ionization and the MLP
-surrogate, ``ionize_oracle.c``); this module only compiles it with gcc and
+The arithmetic lives in plain C (``md_oracle.c``; ``ionize_oracle.c`` for
+ionization, ``mlp_oracle.c`` for the MLP surrogate, ``generate_oracle.c`` for the
+seeded placement of a cluster's records); this module only compiles it with gcc and
 marshals numpy arrays through ctypes.  Every function states the passage of the
 paper it follows; the readings of silent points are stated in the C sources.
 """
@@ -23,7 +24,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libmd_oracle.so")
 # a planted-mistake test compiles a mutant elsewhere and points here
 _LIB_OVERRIDE = os.environ.get("MD_ORACLE_LIB")
-_SOURCES = ["md_oracle.c", "ionize_oracle.c", "mlp_oracle.c"]
+_SOURCES = ["md_oracle.c", "ionize_oracle.c", "mlp_oracle.c", "generate_oracle.c"]
 _lock = threading.Lock()
 _lib = None
 
@@ -122,6 +123,9 @@ def lib():
             L.mo_forward.argtypes = [p, i, p, p]
             L.mo_loss_grad.restype = d
             L.mo_loss_grad.argtypes = [p, i, p, p, p, p]
+            L.or_generate_cluster.restype = None
+            L.or_generate_cluster.argtypes = [d, p, d, d, d, d, i64, i64, i64, C.c_int32,
+                                              C.c_uint64, p, p, p, p, p, p]
             L.io_decide.restype = None
             L.io_decide.argtypes = [i, p, p, p, p, p, p, p, i, d, d, C.c_uint64, i64, d, p, p,
                                     p]
@@ -169,6 +173,27 @@ def laser_fields(t: float, a0: float, pol: int, env: int, tau: float):
     b = np.zeros(3)
     lib().or_laser_fields(t, a0, pol, env, tau, _ptr(a), _ptr(b))
     return a, b
+
+
+# ------------------------------------------------------------ generation ---
+
+def generate_cluster(r0, n_ions, n_electrons, n_slots=0, ion_charge=1, ion_mass=1.0,
+                     weight=1.0, kt_e_ev=0.0, kt_i_ev=0.0, seed=0, center=(0.0, 0.0, 0.0)):
+    """Seeded records of one cluster (Sec. II: atoms at random in the sphere
+    of radius r0; Eq. 1: macro weight w): ions, electrons, then inactive
+    electron slots; positions uniform in the ball by rejection from the cube,
+    Maxwellian momenta (generate_oracle.c states the draws).  Returns a dict
+    of x, u, z, mass, w, kind."""
+    n = int(n_ions) + int(n_electrons) + int(n_slots)
+    out = {"x": np.zeros((n, 3)), "u": np.zeros((n, 3)), "z": np.zeros(n, np.int32),
+           "mass": np.zeros(n), "w": np.zeros(n), "kind": np.zeros(n, np.uint8)}
+    c = _f64(center)
+    lib().or_generate_cluster(float(r0), _ptr(c), float(ion_mass), float(weight),
+                              float(kt_e_ev), float(kt_i_ev), int(n_ions), int(n_electrons),
+                              int(n_slots), int(ion_charge), int(seed) & (2 ** 64 - 1),
+                              _ptr(out["x"]), _ptr(out["u"]), _ptr(out["z"]), _ptr(out["mass"]),
+                              _ptr(out["w"]), _ptr(out["kind"]))
+    return out
 
 
 # ------------------------------------------------------------ direct sum ---

@@ -13,7 +13,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 ORACLE = os.path.join(ROOT, "oracle")
-SOURCES = ["md_oracle.c", "ionize_oracle.c", "mlp_oracle.c"]
+SOURCES = ["md_oracle.c", "ionize_oracle.c", "mlp_oracle.c", "generate_oracle.c"]
 
 # (name, exact text in md_oracle.c, replacement)
 MUTANTS = [
@@ -147,6 +147,40 @@ MUTANTS_OTHER = [
      "double rp2 = (a0 * a0 - a1 * a1) + a2 * a2;", "test_oracle_detectors.py"),
     ("detector_row_offset", "md_oracle.c", "if (-b0 >= c) hist[1 * (nbins + 1) + bin] += 1;",
      "if (-b0 >= c) hist[1 * (nbins - 1) + bin] += 1;", "test_oracle_detectors.py"),
+    ("gen_cube_not_centred", "generate_oracle.c",
+     "c[k] = ((double)w[k] + 0.5) * (1.0 / 2147483648.0) - 1.0;",
+     "c[k] = ((double)w[k] + 0.5) * (1.0 / 4294967296.0);", "test_oracle_generate.py"),
+    ("gen_no_rejection", "generate_oracle.c", "if (r2 < 1.0) {", "if (r2 < 3.0) {",
+     "test_oracle_generate.py"),
+    ("gen_radius_misses_an_axis", "generate_oracle.c", "r2 = r2 + c[2] * c[2];",
+     "r2 = r2 + c[1] * c[1];", "test_oracle_generate.py"),
+    ("gen_attempts_share_a_counter", "generate_oracle.c",
+     "(uint32_t)((uint64_t)rec >> 32), a, GO_TAG_POSITION};",
+     "(uint32_t)((uint64_t)rec >> 32), 0u, GO_TAG_POSITION};", "test_oracle_generate.py"),
+    ("gen_position_unscaled", "generate_oracle.c", "x[3 * i + c] = center[c] + r0 * s[c];",
+     "x[3 * i + c] = center[c] + s[c];", "test_oracle_generate.py"),
+    ("gen_sigma_without_sqrt", "generate_oracle.c",
+     "sqrt(kt_e_ev / (1.0 * GO_ME_C2_EV))", "(kt_e_ev / (1.0 * GO_ME_C2_EV))",
+     "test_oracle_generate.py"),
+    ("gen_sigma_without_ion_mass", "generate_oracle.c",
+     "sqrt(kt_i_ev / (ion_mass * GO_ME_C2_EV))", "sqrt(kt_i_ev / GO_ME_C2_EV)",
+     "test_oracle_generate.py"),
+    ("gen_box_muller_cos_twice", "generate_oracle.c", "n[1] = rho * sin(2.0 * GO_PI * v1);",
+     "n[1] = rho * cos(2.0 * GO_PI * v1);", "test_oracle_generate.py"),
+    ("gen_box_muller_radius", "generate_oracle.c", "double rho = sqrt(-2.0 * log(v0));",
+     "double rho = sqrt(-log(v0));", "test_oracle_generate.py"),
+    ("gen_momentum_draws_reuse_positions", "generate_oracle.c",
+     "(uint32_t)((uint64_t)rec >> 32), 0u, GO_TAG_MOMENTUM};",
+     "(uint32_t)((uint64_t)rec >> 32), 0u, GO_TAG_POSITION};", "test_oracle_generate.py"),
+    ("gen_electron_charge_sign", "generate_oracle.c",
+     "z[i] = k == 0 ? ion_charge : (k == 1 ? -1 : 0);",
+     "z[i] = k == 0 ? ion_charge : (k == 1 ? 1 : 0);", "test_oracle_generate.py"),
+    ("gen_slots_not_at_rest", "generate_oracle.c",
+     "const double sig = k == 0 ? sig_i : (k == 1 ? sig_e : 0.0);",
+     "const double sig = k == 0 ? sig_i : sig_e;", "test_oracle_generate.py"),
+    ("gen_seed_high_word", "generate_oracle.c",
+     "uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};\n    for",
+     "uint32_t key[2] = {(uint32_t)seed, 0u};\n    for", "test_oracle_generate.py"),
     ("iedf_inside_wrong_record", "md_oracle.c",
      "hist[or_energy_bin(or_ke_ev(&u[3 * i], mass[i]), e_max_ev, nbins)] += 1;",
      "hist[or_energy_bin(or_ke_ev(&u[3 / (i + 1)], mass[i]), e_max_ev, nbins)] += 1;",
