@@ -37,10 +37,10 @@ METRIC = "Coulomb pair interactions/s & steps/s at N=200k on 1 GB300; force err 
 UNIT = "pair/s"
 RECORD_BYTES = 3 * 8 + 3 * 8 + 4 + 8 + 8 + 1   # x, u, z, mass, w, kind per record
 FP32_INSTR_PER_PAIR = 12
-# DRAM bytes (read + write) per launch of the step kernel, from one ncu capture
-# of the named workload in the named kernel configuration
-# (profiles/k_step_traffic_xe3_200k.md); reported only when the timed run uses
-# that configuration.
+# DRAM bytes (read + write) per launch of the step kernel, from one 1-pass ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum) of the named workload
+# at full size in the named kernel configuration; reported only when the timed
+# run uses that configuration.
 STEP_TRAFFIC_BYTES = {("xe3_200k", 200000, 128, 4, 512, False): 34.02e6}
 L2_FLUSH_BYTES = 512 << 20
 WORKLOAD_TEXT = {
@@ -68,6 +68,9 @@ def parse_args():
                     help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the secondary measurements (scan256, ar_ionize plain/mlp, "
+                         "precision_1m) that follow the headline at N = 1")
     ap.add_argument("--tuning", default=None,
                     help="force a kernel configuration: threads,r,tile,packed[,jsplit[,min_blocks]]")
     ap.add_argument("--workload", default="xe3_200k",
@@ -246,36 +249,41 @@ def ar_ionize_context(md, args, rank, stream):
     """Neutral argon cluster at the density of 200k atoms in an 8 nm sphere, 8
     inactive electron slots per atom, 806 nm pulse of 8e15 W/cm^2 (a0 = 0.0617)
     with a 100 fs sin^2 envelope, started just before a field crest at the
-    envelope peak so that the timed steps ionize."""
-    n = args.n
-    c = synth.make_cluster(rank, n, 0, synth.nm_to_len(8.0 * (n / 200000) ** (1 / 3), 0.806), 0,
-                           synth.ARGON["mass"], n_electron_slots=8 * n)
-    rw = synth.nm_to_len(synth.ARGON["r_w_nm"], 0.806)
-    tau = synth.sin2_length_from_fwhm(synth.fs_to_time(100.0, 0.806))
-    # a_x = a0 env(t) sin(t): the crest nearest the envelope peak, less 0.3 rad
-    t0 = math.floor(tau / 2 / math.pi) * math.pi + 0.5 * math.pi - 0.3
-    w = synth.Workload(f"ar{n // 1000}k_ionize", c, a0=0.0617, pol=0, env=synth.ENV_SIN2,
-                       tau=tau, eps=synth.nm_to_len(0.1, 0.806), dt=0.02, nsteps=0, t0=t0,
-                       lambda_um=0.806)
+    envelope peak so that the timed steps ionize (synth.ar_ionize)."""
+    return ionizing_context(md, args.n, args.rates, rank, stream)
+
+
+def ionizing_context(md, n, rates, rank, stream, train=None):
+    """The ar_ionize context with `rates` ("plain" or "mlp").  train: a
+    previously trained (params, train_config) to install instead of training
+    the surrogate again."""
+    w = synth.ar_ionize(seed=rank, n_atoms=n)
+    c = w.cluster
     cfg = md.config_from_workload(w)
-    model = md.RATES_MLP if args.rates == "mlp" else md.RATES_PLAIN
-    ion = md.make_config(rate_model=model, ionize_every=1, zmax=8, n_ions=n, slot_base=n,
-                         seed=rank + 1, r_loc=3 * rw, r_create=rw, species=synth.ARGON)
+    model = md.RATES_MLP if rates == "mlp" else md.RATES_PLAIN
+    ion = md.make_config(rate_model=model, ionize_every=1, zmax=w.extra["zmax"], n_ions=n,
+                         slot_base=n, seed=rank + 1, r_loc=w.extra["r_loc"],
+                         r_create=w.extra["r_create"], species=synth.ARGON)
     for f in ("rate_model", "ionize_every", "zmax", "n_ions", "slot_base", "seed", "r_loc",
               "r_create", "ip_ev", "q_outer"):
         setattr(cfg, f, getattr(ion, f))
     ctx = md.Context([cfg], [md.HostParticles.from_cluster(c)], stream=stream)
     # ion field, inputs, (surrogate rates,) decision, apply, charge-change
     # correction, ion push, step
-    info = {"rates": args.rates, "t0": t0,
+    info = {"rates": rates, "t0": w.t0,
             "kernels_per_step": 7 + (1 if model == md.RATES_MLP else 0)}
     if model == md.RATES_MLP:
-        tc = md.mlp_train_config(synth.ARGON, n_samples=10 << 20, epochs=80, batch=8192,
-                                 lr=3e-3, seed=11, lambda_um=0.806)
-        t_train = time.perf_counter()
-        params, rep = md.mlp_train(tc, stream)
-        info["surrogate_training"] = dict(rep, wall_s=time.perf_counter() - t_train,
-                                          samples=tc.n_samples, epochs=tc.epochs)
+        if train is None:
+            tc = md.mlp_train_config(synth.ARGON, n_samples=10 << 20, epochs=80, batch=8192,
+                                     lr=3e-3, seed=11, lambda_um=w.lambda_um)
+            t_train = time.perf_counter()
+            params, rep = md.mlp_train(tc, stream)
+            info["surrogate_training"] = dict(rep, wall_s=time.perf_counter() - t_train,
+                                              samples=tc.n_samples, epochs=tc.epochs,
+                                              ms_per_epoch=rep["train_ms"] / tc.epochs)
+            info["trained"] = (params, tc)
+        else:
+            params, tc = train
         ctx.set_rate_mlp(params, tc)
     return ctx, [w], None, info
 
@@ -342,6 +350,137 @@ def driven_precision(md, args, rank, stream, tuning):
     out.update(a0=wd.a0, steps=args.steps, ms_per_step=ms,
                energy_gain_m_ec2=d1["total"] - d0["total"], ke_after=d1["ke"],
                t_end=d1["t"], laser="on, a0 = 0.1, 100 fs sin^2 from its peak")
+    return out
+
+
+def event_steps(ctx, stream, flush, steps, after=None):
+    """Times `steps` single steps with CUDA events on `stream`, the L2 flushed
+    before each outside the events; after(ctx) runs after each step (outside
+    the events) and its results are returned beside the step times (ms)."""
+    import torch
+    ms, extra = [], []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.step(1)
+        e1.record(stream)
+        if after is not None:
+            extra.append(after(ctx))
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return ms, extra
+
+
+def alu_frac(pairs_per_s: float, sms: int, clocks: dict) -> dict:
+    """Fraction of the FP32 roofline (128 lanes x SMs x clock / 12) at the
+    median SM clock sampled during the run and at the maximum clock."""
+    clk = clocks.get("sm_mhz") or 2070.0
+    peak = 128.0 * sms * clk * 1e6 / FP32_INSTR_PER_PAIR
+    return {"frac": pairs_per_s / peak, "peak_gpair_s": peak / 1e9, "sm_mhz": clk,
+            "frac_at_max_clock": pairs_per_s / (128.0 * sms * 2070e6 / FP32_INSTR_PER_PAIR)}
+
+
+def secondary_measurements(md, stream, flush, sms, gpu_id, steps=3, warmup=2):
+    """Driver-visible numbers of the other configurations, each timed with
+    CUDA events (L2 flushed between steps, outside the events) and its own
+    nvidia-smi clock record:
+      scan256      -- 256 uneven clusters in one persistent launch (autotuned);
+      ar_ionize    -- 200k neutral Ar atoms ionizing before every step, plain
+                      ADK + Lotz rates and the BF16 surrogate (trained here;
+                      its training time per epoch), charge-state fractions of
+                      both on the same seed;
+      precision_1m -- 500k Ar+ + 500k e: the step time, and the FP32/Kahan
+                      field against the FP64 GPU reference and the oracle."""
+    import torch
+    out = {}
+    cs = stream.cuda_stream
+
+    # scan256
+    t_wall = time.perf_counter()
+    scan = synth.batched_scan(256, seed=0)
+    cfgs, parts = [], []
+    pairs = 0.0
+    for e in scan:
+        cl = synth.scan_cluster(e)
+        w = synth.Workload(f"scan_{e.seed}", cl, a0=e.a0, pol=0, env=synth.ENV_SIN2, tau=e.tau,
+                           eps=synth.nm_to_len(0.1), dt=0.02, nsteps=0)
+        cfgs.append(md.config_from_workload(w))
+        parts.append(md.HostParticles.from_cluster(cl))
+        pairs += float(cl.n) ** 2
+    with md.Context(cfgs, parts, stream=cs) as ctx:
+        ctx.autotune(2)
+        for _ in range(warmup):
+            ctx.step(1)
+        sampler = ClockSampler(gpu_id)
+        time.sleep(0.3)
+        ms, _ = event_steps(ctx, stream, flush, 2 * steps)
+        clocks = sampler.stop()
+        tun = ctx.tuning()
+    rate = pairs / (statistics.mean(ms) / 1e3)
+    out["scan256"] = dict({"clusters": 256, "records": int(sum(p.n for p in parts)),
+                           "pairs_per_step": pairs, "steps": len(ms),
+                           "ms_per_step": statistics.mean(ms), "pairs_per_s": rate,
+                           "tuning": list(tun), "clocks": clocks, "gpu_launches": len(ms),
+                           "wall_s": time.perf_counter() - t_wall}, **alu_frac(rate, sms, clocks))
+
+    # ar_ionize, plain rates then the surrogate, same seed
+    n_atoms = 200000
+    trained = None
+    for rates in ("plain", "mlp"):
+        t_wall = time.perf_counter()
+        ctx, ws, _, info = ionizing_context(md, n_atoms, rates, 0, cs)
+        if rates == "mlp":
+            trained = info.get("trained")
+        with ctx:
+            for _ in range(warmup):
+                ctx.step(1)
+            sampler = ClockSampler(gpu_id)
+            time.sleep(0.3)
+            ms, act = event_steps(ctx, stream, flush, steps, after=lambda c: c.count_active(0))
+            clocks = sampler.stop()
+            d = ctx.diagnostics(0)
+        pairs = float(np.mean([float(a) ** 2 for a in act]))
+        rate = pairs / (statistics.mean(ms) / 1e3)
+        ent = dict({"atoms": n_atoms, "records": ws[0].cluster.n, "steps": steps,
+                    "warmup": warmup, "ms_per_step": statistics.mean(ms),
+                    "ms_per_timed_step": ms, "active_records_per_timed_step": act,
+                    "pairs_per_s": rate,
+                    "pairs_counted": "(active records after each step's ionization pass)^2",
+                    "charge_fractions": (d["charge_count"][:9] / n_atoms).tolist(),
+                    "clocks": clocks, "gpu_launches": steps * info["kernels_per_step"],
+                    "wall_s": time.perf_counter() - t_wall},
+                   **alu_frac(rate, sms, clocks))
+        if "surrogate_training" in info:
+            ent["surrogate_training"] = info["surrogate_training"]
+        out[f"ar_ionize_{rates}"] = ent
+    fp, fm = (np.array(out[f"ar_ionize_{r}"]["charge_fractions"]) for r in ("plain", "mlp"))
+    out["ar_ionize_mlp"]["max_abs_fraction_diff_vs_plain"] = float(np.abs(fp - fm).max())
+    out["ar_ionize_mlp"]["step_speedup_vs_plain"] = (out["ar_ionize_plain"]["ms_per_step"] /
+                                                     out["ar_ionize_mlp"]["ms_per_step"])
+    del trained
+
+    # precision_1m: a short run of the 1M case, laser off
+    t_wall = time.perf_counter()
+    w = synth.precision_1m(seed=0, a0=0.0)
+    with md.Context([md.config_from_workload(w)], [md.HostParticles.from_cluster(w.cluster)],
+                    stream=cs) as ctx:
+        ctx.step(1)
+        sampler = ClockSampler(gpu_id)
+        time.sleep(0.3)
+        ms, _ = event_steps(ctx, stream, flush, 2)
+        clocks = sampler.stop()
+        tun = ctx.tuning()
+        prec = precision_study(md, ctx, w, n_targets=10000, n_oracle=1000)
+    pairs = float(w.cluster.n) ** 2
+    rate = pairs / (statistics.mean(ms) / 1e3)
+    out["precision_1m"] = dict({"n_particles": w.cluster.n, "steps": len(ms),
+                                "ms_per_step": statistics.mean(ms), "pairs_per_s": rate,
+                                "tuning": list(tun), "clocks": clocks,
+                                "gpu_launches": len(ms), "precision": prec,
+                                "wall_s": time.perf_counter() - t_wall},
+                               **alu_frac(rate, sms, clocks))
+    torch.cuda.synchronize()
     return out
 
 
@@ -665,7 +804,7 @@ def run_native(args):
         # the state the timed steps reached (the end-to-end leg below repeats
         # one step from it)
         d = ctx.diagnostics(0)
-        ion_state = dict(info, charge_fractions=(d["charge_count"][:9] / w.cluster.n_ions).tolist(),
+        ion_state = dict({k: v for k, v in info.items() if k != "trained"}, charge_fractions=(d["charge_count"][:9] / w.cluster.n_ions).tolist(),
                          active_records_after_timed_steps=int(d["n_active"]),
                          active_records_per_timed_step=[int(round(math.sqrt(p)))
                                                         for p in step_pairs],
@@ -731,6 +870,11 @@ def run_native(args):
 
     launches_per_step = info.get("kernels_per_step", 1)
     ctx.close()
+    secondary = None
+    if (rank == 0 and world == 1 and args.workload == "xe3_200k" and not args.no_secondary):
+        t_sec = time.perf_counter()
+        secondary = secondary_measurements(md, stream, flush, sms, gpu_id_for(local))
+        secondary["wall_s"] = time.perf_counter() - t_sec
     dist.close()
     if rank != 0:
         return
@@ -789,6 +933,7 @@ def run_native(args):
         "cpu_baseline": cpu,
         "force_err_vs_fp64": force_err,
         "precision_study": precision,
+        "secondary": secondary,
     }
     print(json.dumps(line), flush=True)
 

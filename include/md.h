@@ -181,6 +181,45 @@ md_status md_init(md_ctx **out, const md_config *cfgs, int32_t n_clusters,
 void md_destroy(md_ctx *ctx);
 const char *md_last_error(void);
 
+/* Seeded placement of one cluster's records (Sec. II: the atoms of a cluster
+ * of radius R0 sit at random inside the sphere; Eq. 1: a macro-particle of
+ * weight w stands for w atoms, w = N_atoms / N_macro).  Records in the order
+ * ions [0, n_ions), electrons [n_ions, n_ions + n_electrons), then n_slots
+ * INACTIVE electron slots (at the centre, at rest, z = 0, mass 1) for the
+ * ionization pass.  Every ion and electron is uniform in the ball of radius
+ * r0 about `center` (rejection from the cube, Philox4x32-10 keyed on seed,
+ * counter (record, attempt, 0x67656E01)); its u is a non-relativistic
+ * Maxwellian of temperature kt (eV): each component normal with variance
+ * kt / (m m_e c^2), from Box-Muller on counter (record, 0, 0x67656E02).
+ * Charges: ion_charge (ions), -1 (electrons); masses ion_mass and 1; weight w
+ * for every record.  Positions are bit-identical to any IEEE FP64 evaluation
+ * of these draws in the stated order; momenta go through the device's log,
+ * sin and cos. */
+typedef struct {
+    double r0;            /* sphere radius (paper units), > 0 */
+    double center[3];     /* sphere centre (paper units) */
+    double ion_mass;      /* m_e, > 0 */
+    double weight;        /* macro weight w, > 0 */
+    double kt_e_ev;       /* electron temperature (eV), >= 0; 0: at rest */
+    double kt_i_ev;       /* ion temperature (eV), >= 0; 0: at rest */
+    int64_t n_ions;       /* >= 0 */
+    int64_t n_electrons;  /* >= 0 */
+    int64_t n_slots;      /* >= 0; n_ions + n_electrons + n_slots >= 1 */
+    int32_t ion_charge;   /* z of every ion, >= 0 (0: neutral atoms) */
+    int32_t reserved;     /* must be 0 */
+    uint64_t seed;        /* Philox key */
+} md_generate;
+
+/* md_init_generate: as md_init, with cluster c's records generated on the
+ * device from gens[c] (md_generate) instead of copied from host arrays;
+ * cfgs[c] as in md_init (its ionization settings refer to the generated
+ * record order, e.g. n_ions = gens[c].n_ions, slot_base = n_ions +
+ * n_electrons).  md_get_particles reads the records back.  Errors: as md_init,
+ * and MD_ERR_ARG for a bad md_generate (message says which field) or an
+ * ionization setting the generated records do not fit. */
+md_status md_init_generate(md_ctx **out, const md_config *cfgs, const md_generate *gens,
+                           int32_t n_clusters, void *stream);
+
 /* md_step: advances every cluster by nsteps full steps (Sec. II): softened
  * Coulomb field at x^n + laser at t_n, relativistic Boris kick, FP64 drift,
  * boundary.  One fused kernel per step; runs of steps are replayed from a
@@ -348,7 +387,10 @@ md_status md_autotune(md_ctx *ctx, int32_t steps, double *times_ms, int32_t cap)
  * into segments whose partial fields are added in order (deterministic); the
  * partials are allocated and freed in stream order on `stream` (at most
  * 256 MB), so calls on different streams may overlap.
- * Errors: MD_ERR_ARG for NULL/unaligned pointers, ns < 0, nt < 0. */
+ * Errors: MD_ERR_ARG for NULL/unaligned pointers, ns < 0, nt < 0.  A
+ * device-side wait that runs out of its budget (about 2 s) leaves e/phi not
+ * (completely) written and is recorded in the device's sticky field error
+ * word: md_field_device_status reports it. */
 md_status md_coulomb_field_device(const void *src, int64_t ns, const void *tgt,
                                   int64_t nt, float eps2, int64_t self_offset,
                                   double *e, double *phi, void *stream);
@@ -373,6 +415,30 @@ md_status md_coulomb_field_device(const void *src, int64_t ns, const void *tgt,
 md_status md_coulomb_field_device_noalloc(const void *src, int64_t ns, const void *tgt,
                                           int64_t nt, float eps2, int64_t self_offset,
                                           double *e, double *phi, void *stream);
+
+/* md_field_device_status (runtime control; no counterpart in the paper): the
+ * outcome of the stateless field calls (md_coulomb_field_device and
+ * md_coulomb_field_device_noalloc) on the current device.  Those calls are
+ * asynchronous and return MD_OK once their kernels are launched; a device-side
+ * wait that later runs out of its budget sets a per-device error word (a fixed
+ * device array, no allocation) and the call's output is then not (completely)
+ * written.  The word is sticky: it collects every such call on the device,
+ * from any stream, until this call reads it.  md_field_device_status
+ * synchronises `stream` (issue it on the stream of the calls to check, or
+ * synchronise their streams first), reads the word and clears it.
+ * Returns MD_ERR_TIMEOUT if a wait ran out, MD_ERR_STATE if a bounds check of
+ * the checked build failed, else MD_OK.
+ * The device addresses of the library's device arrays are looked up once per
+ * device ordinal and kept for the life of the process: calling the stateless
+ * entry points after cudaDeviceReset on that device is not supported. */
+md_status md_field_device_status(void *stream);
+
+/* md_field_wait_selftest (runtime check; no counterpart in the paper): one CTA
+ * on `stream` waits on an mbarrier phase that nothing completes; after
+ * budget_ms (0 < budget_ms <= 5000, converted with the nominal SM clock) it
+ * gives up and sets the field error word of the current device, which the
+ * next md_field_device_status reports as MD_ERR_TIMEOUT.  Asynchronous. */
+md_status md_field_wait_selftest(double budget_ms, void *stream);
 
 /* md_coulomb_field_fp64_device: the FP64 reference of the direct sum of
  * Sec. II (the precision study's reference, not on the hot path).  For each target i:

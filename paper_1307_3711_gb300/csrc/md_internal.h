@@ -56,6 +56,9 @@ cudaError_t launch_ffma_probe(int blocks, int iters, bool packed, float* sink, c
 // record first and a rejected block is not applied.
 cudaError_t launch_upload(const UploadArgs& a, cudaStream_t s);
 
+// Seeded records of one cluster into the host-layout staging buffer.
+cudaError_t launch_generate(const GenerateArgs& g, cudaStream_t s);
+
 // Count of the records [off, off + n) that are not INACTIVE, into *out.
 cudaError_t launch_count_active(const unsigned char* kind, long long off, long long n,
                                 unsigned long long* out, cudaStream_t s);
@@ -85,6 +88,10 @@ cudaError_t launch_live_init(const float4* posq0, const float4* posq1, const uns
 
 // Surrogate rates of the ions inside its domain (rate_model 2).
 cudaError_t launch_ion_mlp(const IonArgs& a, cudaStream_t s);
+
+// Device address of the current device's error word of the stateless field
+// calls (a file-scope device array, looked up once per device).
+md_status field_error_word(int** out);
 
 // Records the thread-local message returned by md_last_error() and returns
 // the status (implemented in md_runtime.cu).

@@ -422,6 +422,75 @@ cudaError_t launch_count_active(const unsigned char* kind, long long off, long l
   return cudaGetLastError();
 }
 
+// Records of a generated cluster (Sec. II: atoms at random inside the sphere
+// of radius R0; Eq. 1: macro weight w).  Record k is an ion (k < n_ions), an
+// electron (k < n_ions + n_electrons) or an inactive slot.
+//   Position: uniform in the ball by rejection from the cube [-1, 1]^3.
+//     Attempt a draws Philox4x32-10 (key = seed, counter = (k lo, k hi, a,
+//     0x67656E01)); s_i = (w_i + 1/2) 2^-31 - 1 (exact), accepted when
+//     (s0 s0 + s1 s1) + s2 s2 < 1 with every operation rounded to nearest, so
+//     the decision and x = c + r0 s are the same bits as any IEEE FP64
+//     evaluation in that order.  64 rejected attempts (2e-21 per record)
+//     leave the record at the centre.
+//   Momentum: u_i = sigma n_i, Box-Muller normals from the words of counter
+//     (k lo, k hi, 0, 0x67656E02): n0, n1 = sqrt(-2 ln v0) (cos, sin)(2 pi v1),
+//     n2 = sqrt(-2 ln v2) cos(2 pi v3), v0, v2 = (w + 1) 2^-32,
+//     v1, v3 = (w + 1/2) 2^-32.
+//   Slots sit at the centre, at rest, z = 0, mass 1.
+__global__ void __launch_bounds__(256) k_generate(const GenerateArgs g) {
+  const long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= g.n) return;
+  const int kd = k < g.n_ions ? 0 : (k < g.n_ions + g.n_electrons ? 1 : 2);
+  const uint2 key = make_uint2(static_cast<uint32_t>(g.seed), static_cast<uint32_t>(g.seed >> 32));
+  const uint32_t klo = static_cast<uint32_t>(k), khi = static_cast<uint32_t>(k >> 32);
+  double s[3] = {0.0, 0.0, 0.0};
+  if (kd != 2) {
+    for (uint32_t a = 0; a < 64u; ++a) {
+      const uint4 w = philox4x32_10(make_uint4(klo, khi, a, 0x67656E01u), key);
+      const double c0 = __dadd_rn(__dmul_rn(__dadd_rn(static_cast<double>(w.x), 0.5), 0x1p-31), -1.0);
+      const double c1 = __dadd_rn(__dmul_rn(__dadd_rn(static_cast<double>(w.y), 0.5), 0x1p-31), -1.0);
+      const double c2 = __dadd_rn(__dmul_rn(__dadd_rn(static_cast<double>(w.z), 0.5), 0x1p-31), -1.0);
+      const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(c0, c0), __dmul_rn(c1, c1)), __dmul_rn(c2, c2));
+      if (r2 < 1.0) {
+        s[0] = c0;
+        s[1] = c1;
+        s[2] = c2;
+        break;
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) g.x[3 * k + c] = __dadd_rn(g.c[c], __dmul_rn(g.r0, s[c]));
+  const double sig = kd == 0 ? g.sig_i : (kd == 1 ? g.sig_e : 0.0);
+  double n[3] = {0.0, 0.0, 0.0};
+  if (sig > 0.0) {
+    const uint4 w = philox4x32_10(make_uint4(klo, khi, 0u, 0x67656E02u), key);
+    const double two_pi = 2.0 * 3.14159265358979323846;
+    const double v0 = __dmul_rn(__dadd_rn(static_cast<double>(w.x), 1.0), 0x1p-32);
+    const double v1 = __dmul_rn(__dadd_rn(static_cast<double>(w.y), 0.5), 0x1p-32);
+    const double v2 = __dmul_rn(__dadd_rn(static_cast<double>(w.z), 1.0), 0x1p-32);
+    const double v3 = __dmul_rn(__dadd_rn(static_cast<double>(w.w), 0.5), 0x1p-32);
+    const double rho = __dsqrt_rn(__dmul_rn(-2.0, log(v0)));
+    double sn, cs;
+    sincos(__dmul_rn(two_pi, v1), &sn, &cs);
+    n[0] = __dmul_rn(rho, cs);
+    n[1] = __dmul_rn(rho, sn);
+    n[2] = __dmul_rn(__dsqrt_rn(__dmul_rn(-2.0, log(v2))), cos(__dmul_rn(two_pi, v3)));
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) g.u[3 * k + c] = __dmul_rn(sig, n[c]);
+  g.kind[k] = static_cast<unsigned char>(kd);
+  g.z[k] = kd == 0 ? g.ion_charge : (kd == 1 ? -1 : 0);
+  g.mass[k] = kd == 0 ? g.ion_mass : 1.0;
+  g.w[k] = g.weight;
+}
+
+cudaError_t launch_generate(const GenerateArgs& g, cudaStream_t s) {
+  if (g.n <= 0) return cudaSuccess;
+  k_generate<<<static_cast<unsigned>((g.n + 255) / 256), 256, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_upload(const UploadArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
   const unsigned grid = static_cast<unsigned>((a.n + 255) / 256);
@@ -461,6 +530,11 @@ cudaError_t launch_download(const DownloadArgs& a, cudaStream_t s) {
 // them, so calls that overlap on the GPU (two streams, two host threads) race
 // and give wrong fields: serialise them.  Each call clears the counters it
 // needs before its kernel runs; the partial sums are overwritten before use.
+//
+// Both stateless field calls (this one and md_coulomb_field_device) record a
+// bounded wait that ran out in one error word per device, also a file-scope
+// device array.  The word is sticky: md_field_device_status reads and clears
+// it.
 
 namespace md {
 
@@ -472,10 +546,11 @@ constexpr int kNoAllocTile = 512;
 constexpr int kNoAllocBlocks = kNoAllocMaxTargets / (kNoAllocThreads * kNoAllocR);
 
 // partial (ex, ey, ez, phi) per segment and target, completion counters per
-// target block, and the wait-timeout error word
+// target block, and the error word of the stateless field calls (kErrTimeout:
+// a bounded wait ran out; kErrBounds: a bounds check of the checked build)
 static __device__ __align__(256) double g_noalloc_part[kNoAllocMaxSeg * kNoAllocMaxTargets * 4];
 static __device__ __align__(256) unsigned g_noalloc_cnt[kNoAllocBlocks];
-static __device__ __align__(256) int g_noalloc_err[1];
+static __device__ __align__(256) int g_field_err[1];
 
 struct NoAllocScratch {
   double* part;
@@ -581,7 +656,7 @@ md_status noalloc_scratch(NoAllocScratch* out) {
     if (e != cudaSuccess) return report_cuda_error(e, "cudaGetSymbolAddress(partials)");
     e = cudaGetSymbolAddress(reinterpret_cast<void**>(&s.cnt), g_noalloc_cnt);
     if (e != cudaSuccess) return report_cuda_error(e, "cudaGetSymbolAddress(counters)");
-    e = cudaGetSymbolAddress(reinterpret_cast<void**>(&s.err), g_noalloc_err);
+    e = cudaGetSymbolAddress(reinterpret_cast<void**>(&s.err), g_field_err);
     if (e != cudaSuccess) return report_cuda_error(e, "cudaGetSymbolAddress(error word)");
     g_noalloc_ptr[dev] = s;
     g_noalloc_ready[dev] = true;
@@ -591,7 +666,55 @@ md_status noalloc_scratch(NoAllocScratch* out) {
 }
 
 }  // namespace
+
+md_status field_error_word(int** out) {
+  NoAllocScratch sc;
+  const md_status st = noalloc_scratch(&sc);
+  if (st == MD_OK) *out = sc.err;
+  return st;
+}
+
 }  // namespace md
+
+extern "C" md_status md_field_device_status(void* stream) {
+  using namespace md;
+  int* word = nullptr;
+  md_status st = field_error_word(&word);
+  if (st != MD_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t ce = cudaStreamSynchronize(s);
+  if (ce != cudaSuccess) return report_cuda_error(ce, "cudaStreamSynchronize");
+  int v = 0;
+  ce = cudaMemcpyAsync(&v, word, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  if (ce == cudaSuccess && v != 0) ce = cudaMemsetAsync(word, 0, sizeof(int), s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  if (ce != cudaSuccess) return report_cuda_error(ce, "reading the field error word");
+  if (v & kErrTimeout)
+    return report_error(MD_ERR_TIMEOUT,
+                        "a stateless field call hit a device-side wait that exceeded its budget; "
+                        "its output was not (completely) written");
+  if (v & kErrBounds)
+    return report_error(MD_ERR_STATE, "a device-side bounds check failed (checked build)");
+  return MD_OK;
+}
+
+extern "C" md_status md_field_wait_selftest(double budget_ms, void* stream) {
+  using namespace md;
+  if (!(budget_ms > 0.0) || budget_ms > 5000.0)
+    return report_error(MD_ERR_ARG, "budget_ms must be in (0, 5000]");
+  int* word = nullptr;
+  md_status st = field_error_word(&word);
+  if (st != MD_OK) return st;
+  int dev = 0, clk_khz = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, dev);
+  if (ce != cudaSuccess) return report_cuda_error(ce, "cudaDeviceGetAttribute");
+  const long long budget = static_cast<long long>(budget_ms * clk_khz);
+  ce = launch_wait_selftest(budget, word, static_cast<cudaStream_t>(stream));
+  if (ce != cudaSuccess) return report_cuda_error(ce, "wait self-test launch");
+  return MD_OK;
+}
 
 extern "C" md_status md_coulomb_field_device_noalloc(const void* src, int64_t ns, const void* tgt,
                                                      int64_t nt, float eps2, int64_t self_offset,

@@ -41,6 +41,7 @@ md_status cuda_fail(cudaError_t e, const char* what) {
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kClassicalElectronRadius = 2.8179403262e-15;  // m, CODATA 2018
 constexpr int kGraphSteps = 16;
+constexpr double kMeC2Ev = 510998.95;  // electron rest energy, eV
 
 template <class T>
 cudaError_t dev_alloc(T** p, size_t count) {
@@ -223,13 +224,13 @@ md_status validate_config(const md_config& c, int idx) {
   return MD_OK;
 }
 
-md_status validate_ionization(const md_config& c, const md_particles& p, int idx) {
-  if (c.rate_model == 0) return MD_OK;
+// The ionization settings of a cluster of n records (rate_model != 0).
+md_status validate_ionization_params(const md_config& c, long long n, int idx) {
   if (c.zmax < 1 || c.zmax > md::kMaxZ)
     return fail(MD_ERR_ARG, "cluster %d: zmax must be in [1, 16]", idx);
-  if (c.n_ions < 1 || c.n_ions > p.n) return fail(MD_ERR_ARG, "cluster %d: bad n_ions", idx);
+  if (c.n_ions < 1 || c.n_ions > n) return fail(MD_ERR_ARG, "cluster %d: bad n_ions", idx);
   if (c.slot_base < c.n_ions ||
-      c.slot_base + static_cast<long long>(c.zmax) * c.n_ions > p.n)
+      c.slot_base + static_cast<long long>(c.zmax) * c.n_ions > n)
     return fail(MD_ERR_ARG,
                 "cluster %d: electron slots [slot_base, slot_base + zmax n_ions) must lie "
                 "after the ions and inside the records", idx);
@@ -239,10 +240,47 @@ md_status validate_ionization(const md_config& c, const md_particles& p, int idx
   for (int z = 0; z < c.zmax; ++z)
     if (!(c.ip_ev[z] > 0.0) || !(c.q_outer[z] >= 0.0))
       return fail(MD_ERR_ARG, "cluster %d: ip_ev[%d] must be > 0, q_outer >= 0", idx, z);
+  return MD_OK;
+}
+
+md_status validate_ionization(const md_config& c, const md_particles& p, int idx) {
+  if (c.rate_model == 0) return MD_OK;
+  const md_status st = validate_ionization_params(c, p.n, idx);
+  if (st != MD_OK) return st;
   for (long long i = 0; i < c.n_ions; ++i) {
     const int kd = p.kind ? p.kind[i] : (p.z[i] < 0 ? MD_KIND_ELECTRON : MD_KIND_ION);
     if (kd != MD_KIND_ION) return fail(MD_ERR_ARG, "cluster %d: record %lld < n_ions is not an ion", idx, i);
   }
+  return MD_OK;
+}
+
+// The checks of one cluster's generation parameters and of its ionization
+// settings against the generated record order.
+md_status validate_generate(const md_config& c, const md_generate& g, int idx) {
+  const bool fin = std::isfinite(g.r0) && std::isfinite(g.center[0]) &&
+                   std::isfinite(g.center[1]) && std::isfinite(g.center[2]) &&
+                   std::isfinite(g.ion_mass) && std::isfinite(g.weight) &&
+                   std::isfinite(g.kt_e_ev) && std::isfinite(g.kt_i_ev);
+  if (!fin) return fail(MD_ERR_ARG, "cluster %d: md_generate fields must be finite", idx);
+  if (!(g.r0 > 0.0)) return fail(MD_ERR_ARG, "cluster %d: md_generate.r0 must be > 0", idx);
+  if (!(g.ion_mass > 0.0))
+    return fail(MD_ERR_ARG, "cluster %d: md_generate.ion_mass must be > 0", idx);
+  if (!(g.weight > 0.0)) return fail(MD_ERR_ARG, "cluster %d: md_generate.weight must be > 0", idx);
+  if (!(g.kt_e_ev >= 0.0) || !(g.kt_i_ev >= 0.0))
+    return fail(MD_ERR_ARG, "cluster %d: md_generate temperatures must be >= 0", idx);
+  if (g.n_ions < 0 || g.n_electrons < 0 || g.n_slots < 0)
+    return fail(MD_ERR_ARG, "cluster %d: md_generate counts must be >= 0", idx);
+  const long long n = static_cast<long long>(g.n_ions) + g.n_electrons + g.n_slots;
+  if (n < 1 || n > (1LL << 30))
+    return fail(MD_ERR_ARG, "cluster %d: md_generate record count must be in [1, 2^30]", idx);
+  if (g.ion_charge < 0) return fail(MD_ERR_ARG, "cluster %d: md_generate.ion_charge < 0", idx);
+  if (g.reserved != 0) return fail(MD_ERR_ARG, "cluster %d: md_generate.reserved must be 0", idx);
+  if (c.rate_model == 0) return MD_OK;
+  const md_status st = validate_ionization_params(c, n, idx);
+  if (st != MD_OK) return st;
+  if (c.n_ions > g.n_ions)
+    return fail(MD_ERR_ARG, "cluster %d: n_ions = %d but only %lld records are ions", idx,
+                c.n_ions, static_cast<long long>(g.n_ions));
   return MD_OK;
 }
 
@@ -710,6 +748,45 @@ void free_ctx(md_ctx* c) {
   delete c;
 }
 
+#define MD_STATUS(call)              \
+  do {                               \
+    const md_status s_ = (call);     \
+    if (s_ != MD_OK) return s_;      \
+  } while (0)
+
+// Arguments of k_upload for n staged records (view d) of cluster ci.
+md::UploadArgs upload_args(md_ctx* c, int ci, const RawView& d, long long n) {
+  md::UploadArgs a;
+  a.hx = d.x;
+  a.hu = d.u;
+  a.hz = d.z;
+  a.hmass = d.mass;
+  a.hw = d.w;
+  a.hkind = d.kind;
+  a.n = n;
+  a.off = c->cl[ci].off;
+  a.kc = c->kc[ci];
+  a.posq0 = c->d_posq[0];
+  a.posq1 = c->d_posq[1];
+  a.x = c->d_x[0];
+  a.y = c->d_x[1];
+  a.z = c->d_x[2];
+  a.ux = c->d_u[0];
+  a.uy = c->d_u[1];
+  a.uz = c->d_u[2];
+  a.qm = c->d_qm;
+  a.w = c->d_w;
+  a.mass = c->d_mass;
+  a.zq = c->d_z;
+  a.kind = c->d_kind;
+  a.step = c->d_step;
+  a.vel = c->d_vel;
+  a.first_bad = nullptr;
+  return a;
+}
+
+md_status finish_upload(md_ctx* c, int ci, long long next_slot);
+
 // Records of cluster ci from the caller's host arrays.  device_check: the
 // records have not been checked on the host; k_validate checks the staged
 // copy and a rejected block is not applied (clusters without ionization,
@@ -757,36 +834,27 @@ md_status upload_cluster(md_ctx* c, int ci, const md_particles& p, bool device_c
       h.kind[i] = static_cast<unsigned char>(p.z[i] < 0 ? MD_KIND_ELECTRON : MD_KIND_ION);
     MD_CUDA(cudaMemcpyAsync(d.kind, h.kind, n, cudaMemcpyHostToDevice, c->stream));
   }
-  md::UploadArgs a;
-  a.hx = d.x;
-  a.hu = d.u;
-  a.hz = d.z;
-  a.hmass = d.mass;
-  a.hw = d.w;
-  a.hkind = d.kind;
-  a.n = n;
-  a.off = c->cl[ci].off;
-  a.kc = c->kc[ci];
-  a.posq0 = c->d_posq[0];
-  a.posq1 = c->d_posq[1];
-  a.x = c->d_x[0];
-  a.y = c->d_x[1];
-  a.z = c->d_x[2];
-  a.ux = c->d_u[0];
-  a.uy = c->d_u[1];
-  a.uz = c->d_u[2];
-  a.qm = c->d_qm;
-  a.w = c->d_w;
-  a.mass = c->d_mass;
-  a.zq = c->d_z;
-  a.kind = c->d_kind;
-  a.step = c->d_step;
-  a.vel = c->d_vel;
+  md::UploadArgs a = upload_args(c, ci, d, n);
   a.first_bad = device_check ? c->d_word : nullptr;
   MD_CUDA(md::launch_upload(a, c->stream));
   if (device_check)
     MD_CUDA(cudaMemcpyAsync(c->h_word, c->d_word, sizeof(unsigned long long),
                             cudaMemcpyDeviceToHost, c->stream));
+  MD_STATUS(finish_upload(c, ci, next_slot));
+  if (device_check && *c->h_word != md::kNoBadRecord) {
+    // the message of the host check, for the first record the device rejected
+    const md_status st = check_record(p, ci, static_cast<long long>(*c->h_word));
+    return st != MD_OK ? st : fail(MD_ERR_ARG, "cluster %d: record %llu rejected", ci,
+                                   *c->h_word);
+  }
+  return MD_OK;
+}
+
+// The state updates that follow an upload of cluster ci's records: its next
+// free electron slot, the live records of the source split, the device
+// descriptor's segment length and the liveness flags; then waits for the
+// copies (the pinned staging buffer is reused by the next call).
+md_status finish_upload(md_ctx* c, int ci, long long next_slot) {
   if (c->d_ion_next && c->ion[ci].rate_model)
     MD_CUDA(cudaMemcpyAsync(c->d_ion_next + ci, &next_slot, sizeof(long long),
                             cudaMemcpyHostToDevice, c->stream));
@@ -806,13 +874,54 @@ md_status upload_cluster(md_ctx* c, int ci, const md_particles& p, bool device_c
                                  c->d_src_live, c->d_tgt_live, c->stream));
   // the pinned staging buffer is reused by the next call: wait for the copy
   MD_CUDA(cudaStreamSynchronize(c->stream));
-  if (device_check && *c->h_word != md::kNoBadRecord) {
-    // the message of the host check, for the first record the device rejected
-    const md_status st = check_record(p, ci, static_cast<long long>(*c->h_word));
-    return st != MD_OK ? st : fail(MD_ERR_ARG, "cluster %d: record %llu rejected", ci,
-                                   *c->h_word);
-  }
   return MD_OK;
+}
+
+// Records of cluster ci generated on the device (md_generate) into the
+// staging buffer, then scattered into the state as an upload.
+md_status generate_cluster(md_ctx* c, int ci, const md_generate& g) {
+  const long long n = static_cast<long long>(g.n_ions) + g.n_electrons + g.n_slots;
+  long long next_slot = 0;
+  if (c->d_ion_next && c->ion[ci].rate_model) {
+    // the active records are [0, n_ions + n_electrons); electrons are freed
+    // into the slots after the last active one, and all the ionizations still
+    // possible must fit before the end of the slot region
+    const md::IonDev& io = c->ion[ci];
+    const long long end = io.slot_base + static_cast<long long>(io.zmax) * io.n_ions;
+    const long long n_act = static_cast<long long>(g.n_ions) + g.n_electrons;
+    const long long last = io.slot_base < n_act ? std::min(end, n_act) - 1 : -1;
+    const long long remaining =
+        static_cast<long long>(io.n_ions) * std::max(0, io.zmax - g.ion_charge);
+    next_slot = last >= 0 ? last + 1 : io.slot_base;
+    if (next_slot + remaining > end)
+      return fail(MD_ERR_ARG,
+                  "cluster %d: %lld more ionizations possible but only %lld free electron slots "
+                  "after the last active one", ci, remaining, end - next_slot);
+  }
+  RawView d = raw_view(c->d_raw, n);
+  md::GenerateArgs ga;
+  ga.r0 = g.r0;
+  for (int k = 0; k < 3; ++k) ga.c[k] = g.center[k];
+  ga.ion_mass = g.ion_mass;
+  ga.weight = g.weight;
+  ga.sig_i = g.kt_i_ev > 0.0 ? std::sqrt(g.kt_i_ev / (g.ion_mass * kMeC2Ev)) : 0.0;
+  ga.sig_e = g.kt_e_ev > 0.0 ? std::sqrt(g.kt_e_ev / (1.0 * kMeC2Ev)) : 0.0;
+  ga.n_ions = g.n_ions;
+  ga.n_electrons = g.n_electrons;
+  ga.n = n;
+  ga.ion_charge = g.ion_charge;
+  ga.seed = g.seed;
+  ga.x = d.x;
+  ga.u = d.u;
+  ga.mass = d.mass;
+  ga.w = d.w;
+  ga.z = d.z;
+  ga.kind = d.kind;
+  MD_CUDA(md::launch_generate(ga, c->stream));
+  md::UploadArgs a = upload_args(c, ci, d, n);
+  a.first_bad = nullptr;
+  MD_CUDA(md::launch_upload(a, c->stream));
+  return finish_upload(c, ci, next_slot);
 }
 
 }  // namespace
@@ -857,19 +966,15 @@ md_status md_device_info(int32_t* sm_count, char* name, int32_t name_cap) {
   return MD_OK;
 }
 
-md_status md_init(md_ctx** out, const md_config* cfgs, int32_t n_clusters,
-                  const md_particles* parts, void* stream) {
-  if (!out) return fail(MD_ERR_ARG, "out is NULL");
-  *out = nullptr;
-  if (n_clusters < 1 || !cfgs || !parts) return fail(MD_ERR_ARG, "need >= 1 cluster");
-  for (int i = 0; i < n_clusters; ++i) {
-    md_status st = validate_config(cfgs[i], i);
-    if (st != MD_OK) return st;
-    st = validate_particles(parts[i], i, -1);
-    if (st != MD_OK) return st;
-    st = validate_ionization(cfgs[i], parts[i], i);
-    if (st != MD_OK) return st;
-  }
+}  // extern "C"
+
+namespace {
+
+// A context for n_clusters clusters of nrec[i] records: device state
+// allocated and zeroed (padding records INACTIVE at the origin), no records
+// uploaded yet.  On failure nothing is left allocated.
+md_status create_context(const md_config* cfgs, int32_t n_clusters, const long long* nrec,
+                         void* stream, md_ctx** out) {
   md_ctx* c = new md_ctx();
   auto bail = [&](md_status st) {
     free_ctx(c);
@@ -901,8 +1006,8 @@ md_status md_init(md_ctx** out, const md_config* cfgs, int32_t n_clusters,
     md::ClusterDev d;
     std::memset(&d, 0, sizeof(d));  // detectors off
     d.off = off;
-    d.n = static_cast<int>(parts[i].n);
-    d.n_pad = static_cast<int>((parts[i].n + md::kPad - 1) / md::kPad * md::kPad);
+    d.n = static_cast<int>(nrec[i]);
+    d.n_pad = static_cast<int>((nrec[i] + md::kPad - 1) / md::kPad * md::kPad);
     d.a0 = f.a0;
     d.tau = f.tau;
     d.t0 = f.t0;
@@ -939,7 +1044,7 @@ md_status md_init(md_ctx** out, const md_config* cfgs, int32_t n_clusters,
     c->min_image.push_back(static_cast<unsigned char>(f.min_image));
     if (f.min_image) c->any_mi = true;
     off += d.n_pad;
-    c->max_n = std::max<long long>(c->max_n, parts[i].n);
+    c->max_n = std::max<long long>(c->max_n, nrec[i]);
   }
   c->n_total = off;
   const size_t N = static_cast<size_t>(c->n_total);
@@ -1032,15 +1137,77 @@ md_status md_init(md_ctx** out, const md_config* cfgs, int32_t n_clusters,
   ok &= cudaMemsetAsync(c->d_done, 0, sizeof(unsigned), s) == cudaSuccess;
   ok &= cudaMemsetAsync(c->d_err, 0, sizeof(int), s) == cudaSuccess;
   if (!ok) return bail(cuda_fail(cudaGetLastError(), "initialising device state"));
-  for (int i = 0; i < n_clusters; ++i) {
-    st = upload_cluster(c, i, parts[i]);
-    if (st != MD_OK) return bail(st);
-  }
-  st = configure(c, default_config(c), 0, 0);
-  if (st != MD_OK) return bail(st);
+  (void)st;
   *out = c;
   return MD_OK;
 }
+
+// Records of every cluster in place (fill(c, i) uploads or generates cluster
+// i), then the default kernel configuration.
+template <class Fill>
+md_status populate(md_ctx* c, int32_t n_clusters, Fill fill, md_ctx** out) {
+  for (int i = 0; i < n_clusters; ++i) {
+    const md_status st = fill(c, i);
+    if (st != MD_OK) {
+      free_ctx(c);
+      return st;
+    }
+  }
+  const md_status st = configure(c, default_config(c), 0, 0);
+  if (st != MD_OK) {
+    free_ctx(c);
+    return st;
+  }
+  *out = c;
+  return MD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+md_status md_init(md_ctx** out, const md_config* cfgs, int32_t n_clusters,
+                  const md_particles* parts, void* stream) {
+  if (!out) return fail(MD_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (n_clusters < 1 || !cfgs || !parts) return fail(MD_ERR_ARG, "need >= 1 cluster");
+  std::vector<long long> nrec(static_cast<size_t>(n_clusters));
+  for (int i = 0; i < n_clusters; ++i) {
+    md_status st = validate_config(cfgs[i], i);
+    if (st != MD_OK) return st;
+    st = validate_particles(parts[i], i, -1);
+    if (st != MD_OK) return st;
+    st = validate_ionization(cfgs[i], parts[i], i);
+    if (st != MD_OK) return st;
+    nrec[i] = parts[i].n;
+  }
+  md_ctx* c = nullptr;
+  const md_status st = create_context(cfgs, n_clusters, nrec.data(), stream, &c);
+  if (st != MD_OK) return st;
+  return populate(c, n_clusters, [&](md_ctx* x, int i) { return upload_cluster(x, i, parts[i]); },
+                  out);
+}
+
+md_status md_init_generate(md_ctx** out, const md_config* cfgs, const md_generate* gens,
+                           int32_t n_clusters, void* stream) {
+  if (!out) return fail(MD_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (n_clusters < 1 || !cfgs || !gens) return fail(MD_ERR_ARG, "need >= 1 cluster");
+  std::vector<long long> nrec(static_cast<size_t>(n_clusters));
+  for (int i = 0; i < n_clusters; ++i) {
+    md_status st = validate_config(cfgs[i], i);
+    if (st != MD_OK) return st;
+    st = validate_generate(cfgs[i], gens[i], i);
+    if (st != MD_OK) return st;
+    nrec[i] = static_cast<long long>(gens[i].n_ions) + gens[i].n_electrons + gens[i].n_slots;
+  }
+  md_ctx* c = nullptr;
+  const md_status st = create_context(cfgs, n_clusters, nrec.data(), stream, &c);
+  if (st != MD_OK) return st;
+  return populate(c, n_clusters, [&](md_ctx* x, int i) { return generate_cluster(x, i, gens[i]); },
+                  out);
+}
+
 
 void md_destroy(md_ctx* ctx) { free_ctx(ctx); }
 
@@ -1683,22 +1850,14 @@ md_status md_coulomb_field_device(const void* src, int64_t ns, const void* tgt, 
   if ((reinterpret_cast<uintptr_t>(src) & 15) || (reinterpret_cast<uintptr_t>(tgt) & 15))
     return fail(MD_ERR_ARG, "src and tgt must be 16-byte aligned");
   if (!(eps2 > 0.0f)) return fail(MD_ERR_ARG, "eps2 must be > 0");
-  // one error word per device of the process, allocated on first use there
-  static std::mutex mu;
-  static std::vector<int*> words;
+  // the sticky error word of the stateless field calls on this device, read
+  // and cleared by md_field_device_status
   int dev = 0;
   MD_CUDA(cudaGetDevice(&dev));
   int* d_err = nullptr;
   {
-    std::lock_guard<std::mutex> lock(mu);
-    if (static_cast<int>(words.size()) <= dev) words.resize(dev + 1, nullptr);
-    if (!words[dev]) {
-      cudaError_t ce = cudaMalloc(reinterpret_cast<void**>(&words[dev]), sizeof(int));
-      if (ce != cudaSuccess) return cuda_fail(ce, "cudaMalloc");
-      ce = cudaMemset(words[dev], 0, sizeof(int));
-      if (ce != cudaSuccess) return cuda_fail(ce, "cudaMemset");
-    }
-    d_err = words[dev];
+    const md_status es = md::field_error_word(&d_err);
+    if (es != MD_OK) return es;
   }
   md::FieldArgs a;
   a.src = static_cast<const float4*>(src);

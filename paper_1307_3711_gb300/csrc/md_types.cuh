@@ -248,6 +248,25 @@ struct UploadArgs {
 
 constexpr unsigned long long kNoBadRecord = ~0ull;
 
+// Seeded generation of one cluster's records into the host-layout staging
+// buffer (x[n][3], u[n][3], mass, w, z, kind), which k_upload then scatters.
+struct GenerateArgs {
+  double r0;
+  double c[3];          // sphere centre
+  double ion_mass;
+  double weight;
+  double sig_i, sig_e;  // per-component spread of u of ions / electrons (0: at rest)
+  long long n_ions, n_electrons, n;  // n = n_ions + n_electrons + slots
+  int ion_charge;
+  unsigned long long seed;
+  double* x;
+  double* u;
+  double* mass;
+  double* w;
+  int* z;
+  unsigned char* kind;
+};
+
 struct DownloadArgs {
   double* hx;
   double* hu;

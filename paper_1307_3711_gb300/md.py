@@ -86,6 +86,25 @@ class DetectorConfig(C.Structure):
 DETECTORS = ("+x", "-x", "+y", "-y", "all")
 
 
+class Generate(C.Structure):
+    """Mirror of md_generate: seeded records of one cluster (see md.h)."""
+    _fields_ = [("r0", C.c_double), ("center", C.c_double * 3), ("ion_mass", C.c_double),
+                ("weight", C.c_double), ("kt_e_ev", C.c_double), ("kt_i_ev", C.c_double),
+                ("n_ions", C.c_int64), ("n_electrons", C.c_int64), ("n_slots", C.c_int64),
+                ("ion_charge", C.c_int32), ("reserved", C.c_int32), ("seed", C.c_uint64)]
+
+
+def make_generate(r0, n_ions, n_electrons, n_slots=0, ion_charge=1, ion_mass=1.0, weight=1.0,
+                  kt_e_ev=0.0, kt_i_ev=0.0, seed=0, center=(0.0, 0.0, 0.0)) -> Generate:
+    g = Generate()
+    g.r0, g.ion_mass, g.weight, g.kt_e_ev, g.kt_i_ev = r0, ion_mass, weight, kt_e_ev, kt_i_ev
+    for k in range(3):
+        g.center[k] = center[k]
+    g.n_ions, g.n_electrons, g.n_slots = int(n_ions), int(n_electrons), int(n_slots)
+    g.ion_charge, g.reserved, g.seed = int(ion_charge), 0, int(seed) & (2 ** 64 - 1)
+    return g
+
+
 class MlpReport(C.Structure):
     _fields_ = [("loss_first", C.c_double), ("loss_last", C.c_double),
                 ("holdout_median_dlog10", C.c_double), ("holdout_p99_dlog10", C.c_double),
@@ -98,6 +117,8 @@ _st = C.c_int
 _p = C.c_void_p
 _SIGS = {
     "md_init": (_st, [C.POINTER(_ctx_p), C.POINTER(Config), C.c_int32, C.POINTER(Particles), _p]),
+    "md_init_generate": (_st, [C.POINTER(_ctx_p), C.POINTER(Config), C.POINTER(Generate),
+                               C.c_int32, _p]),
     "md_destroy": (None, [_ctx_p]),
     "md_last_error": (C.c_char_p, []),
     "md_step": (_st, [_ctx_p, C.c_int32]),
@@ -125,6 +146,8 @@ _SIGS = {
                                       _p, _p]),
     "md_coulomb_field_device_noalloc": (_st, [_p, C.c_int64, _p, C.c_int64, C.c_float, C.c_int64,
                                               _p, _p, _p]),
+    "md_field_device_status": (_st, [_p]),
+    "md_field_wait_selftest": (_st, [C.c_double, _p]),
     "md_mlp_train": (_st, [C.POINTER(MlpTrainConfig), _p, C.POINTER(MlpReport), _p]),
     "md_set_rate_mlp": (_st, [_ctx_p, _p, C.POINTER(MlpTrainConfig)]),
     "md_mlp_forward_device": (_st, [_p, _p, C.c_int64, _p, _p]),
@@ -270,6 +293,23 @@ class Context:
         _check(_lib.md_init(C.byref(h), self._cfgs, len(configs), self._parts,
                             C.c_void_p(stream) if stream else None))
         self._h = h
+
+    @classmethod
+    def generate(cls, configs, gens, stream=None) -> "Context":
+        """A context whose clusters' records are generated on the device
+        (md_init_generate) from `gens` (Generate structures)."""
+        configs, gens = list(configs), list(gens)
+        assert len(configs) == len(gens) and configs
+        self = cls.__new__(cls)
+        self._cfgs = (Config * len(configs))(*configs)
+        self._gens = (Generate * len(gens))(*gens)
+        self._keep = []
+        self.sizes = [g.n_ions + g.n_electrons + g.n_slots for g in gens]
+        h = _ctx_p()
+        _check(_lib.md_init_generate(C.byref(h), self._cfgs, self._gens, len(configs),
+                                     C.c_void_p(stream) if stream else None))
+        self._h = h
+        return self
 
     def close(self):
         if getattr(self, "_h", None):
@@ -430,6 +470,19 @@ def coulomb_field_device_noalloc(src_ptr: int, ns: int, tgt_ptr: int, nt: int, e
         C.c_void_p(src_ptr), int(ns), C.c_void_p(tgt_ptr), int(nt), float(eps2),
         int(self_offset), C.c_void_p(e_ptr), C.c_void_p(phi_ptr) if phi_ptr else None,
         C.c_void_p(stream) if stream else None))
+
+
+def field_device_status(stream=None) -> int:
+    """Status of the stateless field calls on the current device since the
+    last query (synchronises `stream`; the sticky error word is cleared).
+    Returns MD_OK, MD_ERR_TIMEOUT or MD_ERR_STATE (no exception)."""
+    return int(_lib.md_field_device_status(_vp(stream)))
+
+
+def field_wait_selftest(budget_ms: float, stream=None):
+    """Launches a wait that runs out after budget_ms and records it in the
+    stateless field calls' error word (see md.h)."""
+    _check(_lib.md_field_wait_selftest(float(budget_ms), _vp(stream)))
 
 
 # ---------------------------------------------------------- rate surrogate --

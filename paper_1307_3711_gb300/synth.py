@@ -226,3 +226,23 @@ def neutral_ar_200k(seed: int = 0, n_atoms: int = 200000, zmax: int = 8,
     ionization (zmax per atom)."""
     return make_cluster(seed, n_atoms, 0, nm_to_len(r0_nm), 0, MASS_AR,
                         n_electron_slots=n_atoms * zmax)
+
+
+def ar_ionize(seed: int = 0, n_atoms: int = 200000) -> Workload:
+    """Neutral argon cluster at the density of 200k atoms in an 8 nm sphere
+    (R0 = 8 nm (n_atoms / 200000)^(1/3)), 8 inactive electron slots per atom,
+    806 nm pulse of 8e15 W/cm^2 (a0 = 0.0617) with a 100 fs sin^2 envelope.
+    The run starts 0.3 rad before the field crest nearest the envelope peak
+    (a_x = a0 env(t) sin t), so its first steps ionize.  extra holds the
+    ionization settings in paper units: zmax, the radius r_loc = 3 R_W of the
+    local electron moments and the radius r_create = R_W of the ball a freed
+    electron is placed in."""
+    lam = 0.806
+    c = make_cluster(seed, n_atoms, 0, nm_to_len(8.0 * (n_atoms / 200000) ** (1 / 3), lam), 0,
+                     ARGON["mass"], n_electron_slots=8 * n_atoms)
+    rw = nm_to_len(ARGON["r_w_nm"], lam)
+    tau = sin2_length_from_fwhm(fs_to_time(100.0, lam))
+    t0 = math.floor(tau / 2 / math.pi) * math.pi + 0.5 * math.pi - 0.3
+    return Workload(f"ar{n_atoms // 1000}k_ionize", c, a0=0.0617, pol=0, env=ENV_SIN2, tau=tau,
+                    eps=nm_to_len(0.1, lam), dt=0.02, nsteps=0, t0=t0, lambda_um=lam,
+                    extra={"zmax": 8, "r_loc": 3 * rw, "r_create": rw})

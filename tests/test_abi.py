@@ -114,3 +114,23 @@ def test_init_without_gpu_fails_cleanly(md):
     with pytest.raises(md.MDError) as ei:
         md.Context([cfg], [p])
     assert ei.value.status in (md.MD_ERR_CUDA, md.MD_ERR_UNSUPPORTED)
+
+
+def test_generate_rejects_bad_parameters(md):
+    """md_init_generate checks its md_generate and the ionization settings
+    against the generated record order on the host, before any GPU work."""
+    from tests.test_gpu_generate import GENS, _configs
+    cfg = _configs(md)[:1]
+    bad = [dict(GENS[0], r0=0.0), dict(GENS[0], ion_mass=-1.0), dict(GENS[0], weight=0.0),
+           dict(GENS[0], kt_e_ev=-1.0), dict(GENS[0], n_ions=0, n_electrons=0, n_slots=0),
+           dict(GENS[0], ion_charge=-1)]
+    for b in bad:
+        with pytest.raises(md.MDError) as ei:
+            md.Context.generate(cfg, [md.make_generate(**b)])
+        assert ei.value.status == md.MD_ERR_ARG
+    # ionization settings the generated records cannot hold: 1500 atoms need
+    # 12000 slots for zmax = 8
+    ion = _configs(md, True)[1]
+    with pytest.raises(md.MDError) as ei:
+        md.Context.generate([ion], [md.make_generate(**dict(GENS[1], n_slots=11999))])
+    assert ei.value.status == md.MD_ERR_ARG

@@ -168,6 +168,43 @@ def test_surrogate_charge_states_match_plain_rates(md, trained):
     assert np.abs(fracs[0] - fracs[1]).max() <= 0.01
 
 
+def test_surrogate_charge_states_at_full_size(md):
+    """The full-size ionizing workload: 200k neutral Ar atoms in an 8 nm
+    sphere (1.8M records with the electron slots), 806 nm, 8e15 W/cm^2,
+    100 fs sin^2 pulse, started at the field crest nearest the envelope peak,
+    ionization before every step.  The surrogate is trained for argon at
+    806 nm; after 10 ionizing steps the charge-state fractions of the
+    surrogate run are within 0.01 of the plain-rate run on the same seed.
+    At 200k atoms the binomial noise of a fraction is below 0.0012; a plain
+    run with another seed shows it."""
+    cfg = md.mlp_train_config(AR, n_samples=8 << 20, epochs=80, batch=8192, lr=3e-3, seed=11,
+                              lambda_um=0.806)
+    params, rep = md.mlp_train(cfg)
+    assert rep["holdout_median_dlog10"] < 0.05
+    n = 200000
+    w = synth.ar_ionize(seed=0, n_atoms=n)
+    fracs = []
+    for model, seed in ((1, 1), (2, 1), (1, 2)):
+        c = md.config_from_workload(w)
+        ion = md.make_config(rate_model=model, ionize_every=1, zmax=w.extra["zmax"], n_ions=n,
+                             slot_base=n, seed=seed, r_loc=w.extra["r_loc"],
+                             r_create=w.extra["r_create"], species=AR)
+        for f in ("rate_model", "ionize_every", "zmax", "n_ions", "slot_base", "seed", "r_loc",
+                  "r_create", "ip_ev", "q_outer"):
+            setattr(c, f, getattr(ion, f))
+        with md.Context([c], [md.HostParticles.from_cluster(w.cluster)]) as ctx:
+            if model == 2:
+                ctx.set_rate_mlp(params, cfg)
+            ctx.step(10)
+            d = ctx.diagnostics(0)
+        fracs.append(d["charge_count"][:9] / n)
+    print("charge fractions plain", np.round(fracs[0], 4), "surrogate", np.round(fracs[1], 4),
+          "plain, other seed", np.round(fracs[2], 4))
+    assert fracs[0][1:].sum() > 0.5   # the run ionized
+    assert np.abs(fracs[0] - fracs[2]).max() <= 0.005   # seed-to-seed noise
+    assert np.abs(fracs[0] - fracs[1]).max() <= 0.01
+
+
 def test_surrogate_gain_in_rate_evaluation(md, trained):
     """What the network buys: the rate evaluation of 200k ions with the
     surrogate (BF16 tensor cores) against the FP64 transcendental plain rate."""

@@ -121,6 +121,24 @@ def test_stateless_field_entry_point(md):
                                 e.data_ptr(), 0, stream)
 
 
+def test_stateless_field_status_reports_a_timeout(md):
+    """The stateless field calls return once launched; a device-side wait that
+    runs out is recorded in a sticky per-device word.  A wait that nothing
+    completes (50 ms budget) sets it: md_field_device_status reports
+    MD_ERR_TIMEOUT once, clears it, and a field call afterwards is clean."""
+    import torch
+    stream = torch.cuda.current_stream().cuda_stream
+    assert md.field_device_status(stream) == md.MD_OK
+    md.field_wait_selftest(50.0, stream)
+    assert md.field_device_status(stream) == md.MD_ERR_TIMEOUT
+    assert md.field_device_status(stream) == md.MD_OK
+    src = torch.zeros((64, 4), dtype=torch.float32, device="cuda")
+    e = torch.zeros((64, 3), dtype=torch.float64, device="cuda")
+    md.coulomb_field_device(src.data_ptr(), 64, src.data_ptr(), 64, 1e-6, 0, e.data_ptr(), 0,
+                            stream)
+    assert md.field_device_status(stream) == md.MD_OK
+
+
 def test_stateless_field_few_targets_many_sources(md):
     """md_coulomb_field_device with 300 targets and 200k sources splits the
     sources into segments (stream-ordered partials) and adds them in order:

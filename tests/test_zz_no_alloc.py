@@ -5,10 +5,14 @@ framework's memory pool, a CUDA-graph builder that must not see cudaMalloc, a
 plugin whose host forbids allocation.  For them the library offers a field
 evaluation whose scratch memory is a fixed array compiled into the library.
 This test calls it through the C ABI twice in a row and checks each result
-against the allocating entry point md_coulomb_field_device, within the same
-tolerance as the other field tests.  It sits in a file of its own, collected
-last, and works both alone in a fresh process and after the other tests.
+against the allocating entry point md_coulomb_field_device and against the
+FP64 oracle's direct sum, within the same tolerance as the other field tests;
+a third case fills the scratch array to its 32768-target limit.  The file sits
+on its own, collected last, and works both alone in a fresh process and after
+the other tests.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -19,6 +23,7 @@ pytestmark = pytest.mark.gpu
 
 FORCE_P99 = 2e-5
 MAX_TARGETS = 32768
+NTHREADS = os.cpu_count() or 1
 
 
 @pytest.fixture(scope="module")
@@ -54,15 +59,47 @@ def test_noalloc_field_matches_allocating_entry_point_twice(md):
     tgt = torch.tensor(np.c_[xt, np.zeros(nt)], dtype=torch.float32, device="cuda")
     ref = _field(md, md.coulomb_field_device, src, ns, tgt, nt, eps * eps, -1, stream)
     got = _field(md, md.coulomb_field_device_noalloc, src, ns, tgt, nt, eps * eps, -1, stream)
+    assert md.field_device_status(stream) == md.MD_OK
     assert summary(force_error(got[0], ref[0]))["p99"] <= FORCE_P99
     np.testing.assert_allclose(got[1], ref[1], rtol=1e-5, atol=1e-5 * np.abs(ref[1]).max())
+    e64, phi64 = oracle.coulomb_field(xt, xs, qs, eps, kc, potential=True, nthreads=NTHREADS)
+    assert summary(force_error(got[0], e64))["p99"] <= FORCE_P99
+    np.testing.assert_allclose(got[1], phi64, rtol=1e-5, atol=1e-5 * np.abs(phi64).max())
     # second call in a row: targets are the sources (self term removed)
     ns2 = 9000
     src2 = src[:ns2].clone()
     ref = _field(md, md.coulomb_field_device, src2, ns2, src2, ns2, eps * eps, 0, stream)
     got = _field(md, md.coulomb_field_device_noalloc, src2, ns2, src2, ns2, eps * eps, 0, stream)
+    assert md.field_device_status(stream) == md.MD_OK
     assert summary(force_error(got[0], ref[0]))["p99"] <= FORCE_P99
     np.testing.assert_allclose(got[1], ref[1], rtol=1e-5, atol=1e-5 * np.abs(ref[1]).max())
+    e64, phi64 = oracle.self_field(xs[:ns2], qs[:ns2], eps, kc, potential=True, nthreads=NTHREADS)
+    assert summary(force_error(got[0], e64))["p99"] <= FORCE_P99
+    np.testing.assert_allclose(got[1], phi64, rtol=1e-4, atol=2e-5 * np.abs(phi64).max())
+
+
+def test_noalloc_field_at_its_target_limit(md):
+    """nt = 32768 uses every completion counter and the top rows of each
+    segment's partials; 8192 sources make 4 segments."""
+    import torch
+    kc = oracle.coulomb_constant(0.8)
+    stream = torch.cuda.current_stream().cuda_stream
+    eps = 1e-3
+    rng = np.random.default_rng(22)
+    ns, nt = 8192, MAX_TARGETS
+    xs = rng.uniform(-0.02, 0.02, size=(ns, 3))
+    qs = rng.choice([-1.0, 2.0], size=ns)
+    xt = rng.uniform(-0.02, 0.02, size=(nt, 3))
+    src = torch.tensor(np.c_[xs, kc * qs], dtype=torch.float32, device="cuda")
+    tgt = torch.tensor(np.c_[xt, np.zeros(nt)], dtype=torch.float32, device="cuda")
+    ref = _field(md, md.coulomb_field_device, src, ns, tgt, nt, eps * eps, -1, stream)
+    got = _field(md, md.coulomb_field_device_noalloc, src, ns, tgt, nt, eps * eps, -1, stream)
+    assert md.field_device_status(stream) == md.MD_OK
+    assert np.isfinite(got[0]).all() and np.isfinite(got[1]).all()
+    assert summary(force_error(got[0], ref[0]))["p99"] <= FORCE_P99
+    e64, phi64 = oracle.coulomb_field(xt, xs, qs, eps, kc, potential=True, nthreads=NTHREADS)
+    assert summary(force_error(got[0], e64))["p99"] <= FORCE_P99
+    np.testing.assert_allclose(got[1], phi64, rtol=1e-5, atol=1e-5 * np.abs(phi64).max())
 
 
 def test_noalloc_rejects_too_many_targets(md):
