@@ -45,6 +45,8 @@ STEP_TRAFFIC_BYTES = {("xe3_200k", 200000, 128, 4, 512, False): 34.02e6}
 L2_FLUSH_BYTES = 512 << 20
 WORKLOAD_TEXT = {
     "xe3_200k": "{name}: N={n} (Xe3+ ions + electrons, 10 eV), one cluster per GPU",
+    "xe3_200k_shard": "{name}: N={n} (Xe3+ ions + electrons, 10 eV), one cluster split over "
+                      "{ranks} GPU(s) by target records, j-stream all-gathered every step",
     "scan256": "parameter scan of {clusters} clusters (N log-uniform 1k-50k, Z 1-8, R0 1-8 nm, "
                "a0 0.01-0.3, 20-200 fs), {n} records in one persistent launch per step",
     "precision_1m": "{name}: N={n}, laser off (timed), then the same cluster driven at a0 = 0.1 "
@@ -68,6 +70,10 @@ def parse_args():
                     help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--shard", action="store_true",
+                    help="xe3_200k under torchrun: one cluster split over the ranks by target "
+                         "records, its j-stream all-gathered (NCCL) after every step (strong "
+                         "scaling); without it every rank runs its own cluster (weak scaling)")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the secondary measurements (scan256, ar_ionize plain/mlp, "
                          "precision_1m) that follow the headline at N = 1")
@@ -607,6 +613,16 @@ def build_contexts(md, args, rank, stream):
         w = synth.precision_1m(seed=rank, a0=0.0)
     elif args.workload == "ar_ionize":
         return ar_ionize_context(md, args, rank, stream)
+    elif args.shard:
+        # the same cluster on every rank, each pushing its slice of targets
+        from paper_1307_3711_gb300 import shard
+        world = dist_env()[0]
+        w = workload(args.n, seed=0)
+        ctx = md.Context([md.config_from_workload(w)], [md.HostParticles.from_cluster(w.cluster)],
+                         stream=stream)
+        b, e, per = shard.slice_bounds(w.cluster.n, world, rank)
+        ctx.set_slice(0, b, e)
+        return ctx, [w], float(w.cluster.n) ** 2, {"slice": (b, e, per)}
     else:
         w = workload(args.n, seed=rank)
     return (md.Context([md.config_from_workload(w)], [md.HostParticles.from_cluster(w.cluster)],
@@ -750,10 +766,20 @@ def run_native(args):
         tune_ms = ctx.autotune(3).tolist()
     tuning = ctx.tuning()
 
+    sliced = info.get("slice")
+
+    def step_once():
+        """One step of the workload: with --shard under several ranks, the
+        rank's slice pushed, then the j-stream all-gathered."""
+        ctx.step(1)
+        if sliced and world > 1:
+            from paper_1307_3711_gb300 import shard
+            shard.exchange(shard.jstream_tensor(ctx), sliced[2], world, rank)
+
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     for _ in range(max(args.warmup, 3)):
         flush.zero_()
-        ctx.step(1)
+        step_once()
     torch.cuda.synchronize()
 
     d_before = ctx.diagnostics(0) if args.workload == "precision_1m" else None
@@ -768,7 +794,7 @@ def run_native(args):
     for e0, e1 in evs:
         flush.zero_()                # L2 flushed between timed steps, outside the events
         e0.record(stream)
-        ctx.step(1)
+        step_once()
         e1.record(stream)
         if ionizing:
             # records active after the step's ionization pass (the pairs its
@@ -785,7 +811,11 @@ def run_native(args):
     t_local = sum(step_ms) / 1e3
     t_max = dist.max(t_local)
     ms_per_step = t_max * 1e3 / args.steps
-    value = whole_job_value(world, pairs_per_step, args.steps, t_max)
+    # a split cluster's ranks share its N^2 pairs; replicas each add theirs
+    value = (pairs_per_step * args.steps / t_max if sliced
+             else whole_job_value(world, pairs_per_step, args.steps, t_max))
+    # pairs this GPU's kernel summed per step (its slice of targets x all sources)
+    pairs_local = (float(sliced[1] - sliced[0]) * w.cluster.n if sliced else pairs_per_step)
 
     precision = None
     if args.workload == "precision_1m":
@@ -817,7 +847,7 @@ def run_native(args):
 
     # FP32 roofline of the step kernel (the only kernel of a step)
     ffma_per_s, ffma2_per_s = md.measure_fp32_peak(stream.cuda_stream)
-    achieved = pairs_per_step / (statistics.mean(step_ms) / 1e3)
+    achieved = pairs_local / (statistics.mean(step_ms) / 1e3)
     peak_probe = max(ffma_per_s, ffma2_per_s) / FP32_INSTR_PER_PAIR
     clk = clocks.get("sm_mhz") or None
     peak_clock = 128.0 * sms * clk * 1e6 / FP32_INSTR_PER_PAIR if clk else None
@@ -843,7 +873,7 @@ def run_native(args):
         t0 = time.perf_counter()
         for k, hp in enumerate(hps):
             ctx.set_particles(k, hp)
-        ctx.step(1)
+        step_once()
         for k, hp in enumerate(hps):
             ctx.get_particles(k, out=hp)
         t1 = time.perf_counter()
@@ -856,7 +886,7 @@ def run_native(args):
                 getattr(hps[0], k)[...] = getattr(reached, k)
     e2e_local = float(np.mean(e2e_t))
     e2e_max = dist.max(e2e_local)
-    e2e_value = world * float(np.mean(e2e_pairs)) / e2e_max
+    e2e_value = (1 if sliced else world) * float(np.mean(e2e_pairs)) / e2e_max
 
     cpu = None
     force_err = None
@@ -888,14 +918,15 @@ def run_native(args):
         "ms_per_step": ms_per_step,
         "steps_per_s": 1e3 / ms_per_step,
         "higher_is_better": True,
-        "scaling": "weak",
+        "scaling": "strong" if sliced else "weak",
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
         "config": {
-            "workload": WORKLOAD_TEXT[args.workload].format(name=w.name, n=n,
-                                                            clusters=len(ws), atoms=args.n,
-                                                            rates=args.rates),
+            "workload": (WORKLOAD_TEXT["xe3_200k_shard"] if sliced else
+                         WORKLOAD_TEXT[args.workload]).format(name=w.name, n=n,
+                                                              clusters=len(ws), atoms=args.n,
+                                                              rates=args.rates, ranks=world),
             "n_particles": n, "pairs_per_step": pairs_per_step, "ionization": ion_state,
             "softening_nm": 0.1, "dt": w.dt, "a0": w.a0, "envelope": "sin2, 100 fs FWHM",
             "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write outside the "

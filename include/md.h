@@ -346,6 +346,40 @@ md_status md_get_ionization(md_ctx *ctx, int32_t cluster, double *emag, double *
  * counters derive from the step).  Synchronous.  Errors: MD_ERR_ARG (step < 0). */
 md_status md_set_step(md_ctx *ctx, int64_t step);
 
+/* ---- target slices: one cluster split over several GPUs ---------------------
+ * The step's cost is the direct sum over all pairs (Sec. II, particle mover
+ * paragraph; Sec. III: time grows as N_part^2).  The paper parallelises the
+ * force and mover loops over target particles on the cores of one node; here
+ * the same split spreads one cluster over GPUs.  Every GPU holds the whole
+ * cluster, sums the field of all sources at its own slice of target records
+ * and pushes only those; between steps the slices' new positions (the j-stream,
+ * 16 bytes per record) are exchanged, e.g. by an all-gather, so every GPU
+ * again holds every source.
+ *
+ * md_set_slice: from now on cluster `cluster` of this context pushes only its
+ * records [i_begin, i_end).  i_begin and i_end are multiples of 1024 (a whole
+ * number of i-blocks of every kernel configuration) or the record count n;
+ * [0, n) undoes the slice, i_begin == i_end pushes nothing.
+ * Records outside the slice keep their state (md_get_particles returns it as
+ * it was: stale on this GPU); their j-stream entries are whatever the caller
+ * writes through md_get_jstream.  md_get_fields writes e and phi for the
+ * slice's records only; md_diagnostics and md_step_diag sum over the slice's
+ * records (the field and potential at them from all sources), so the
+ * cluster's totals are the sums over the GPUs' slices.
+ * Errors: MD_ERR_ARG (bounds), MD_ERR_STATE (a context with ionization or
+ * detectors).  Synchronous. */
+md_status md_set_slice(md_ctx *ctx, int32_t cluster, int64_t i_begin, int64_t i_end);
+
+/* md_get_jstream: device address of cluster `cluster`'s current j-stream,
+ * the float4[n_pad] records (x, y, z, K_C w z) that the next step reads as
+ * its sources (n_pad: the record count rounded up to a multiple of 16; the
+ * padding records carry no charge).  After a step each GPU's slice of it holds
+ * that GPU's new positions; the caller writes the other slices there (ordered
+ * before the next md_step on the context's stream) from the GPUs that own
+ * them.  The address changes from step to step (two buffers alternate).
+ * Synchronises the context's stream. */
+md_status md_get_jstream(md_ctx *ctx, int32_t cluster, void **posq, int64_t *n_pad);
+
 /* md_wait_selftest (runtime check; no counterpart in the paper): exercises
  * the bounded device waits.  One CTA waits on an
  * mbarrier phase that nothing completes; after budget_ms (0 < budget_ms <=

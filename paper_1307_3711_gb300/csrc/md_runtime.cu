@@ -42,6 +42,10 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr double kClassicalElectronRadius = 2.8179403262e-15;  // m, CODATA 2018
 constexpr int kGraphSteps = 16;
 constexpr double kMeC2Ev = 510998.95;  // electron rest energy, eV
+// target slices start (and end, unless at the record count) on multiples of
+// this, a multiple of every compiled i-block size, so that a slice is a whole
+// number of i-blocks
+constexpr int kSliceAlign = 1024;
 
 template <class T>
 cudaError_t dev_alloc(T** p, size_t count) {
@@ -62,6 +66,10 @@ struct md_ctx {
   // per cluster: records live at the last upload (an ionizing cluster: below
   // its next free electron slot), for the choice of the source split
   std::vector<long long> live_host;
+  // per cluster: the targets this context pushes, [slice_b, slice_e) of the
+  // cluster's padded records (md_set_slice; default all of them)
+  std::vector<long long> slice_b, slice_e;
+  bool any_slice = false;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
 
@@ -394,6 +402,15 @@ bool ions_fused(const md_ctx* c, int ci) {
   return c->d_ion_e && io.rate_model != 0 && io.ionize_every == 1 && io.n_ions > 0;
 }
 
+// Cluster ci restricted to its target slice (the records md_diagnostics sums).
+md::ClusterDev slice_view(const md_ctx* c, int ci) {
+  md::ClusterDev v = c->cl[ci];
+  const long long b = c->slice_b[ci], e = std::min<long long>(c->slice_e[ci], v.n);
+  v.off += b;
+  v.n = static_cast<int>(std::max(0LL, e - b));
+  return v;
+}
+
 // Source segments of md_get_fields / md_diagnostics at most.
 constexpr int kFieldMaxSeg = 8;
 
@@ -407,6 +424,13 @@ void segments_for(const md::ClusterDev& cl, int S, int tile, int* nseg, int* seg
   *nseg = (cl.n_pad + len - 1) / len;
 }
 
+// Whether i-block b (of `per` targets) of cluster ci lies in the cluster's
+// target slice (slice bounds are multiples of every i-block size).
+bool block_in_slice(const md_ctx* c, int ci, long long b, long long per) {
+  const long long i0 = b * per;
+  return i0 >= c->slice_b[ci] && i0 < c->slice_e[ci];
+}
+
 long long units_for(const md_ctx* c, long long per, int S, int tile) {
   long long u = 0;
   for (int ci = 0; ci < c->n_clusters; ++ci) {
@@ -416,9 +440,16 @@ long long units_for(const md_ctx* c, long long per, int S, int tile) {
     // i-blocks past the live records finish at once: count the live ones
     const long long live = ci < static_cast<int>(c->live_host.size()) ? c->live_host[ci] : cl.n_pad;
     const long long skip = ions_fused(c, ci) ? c->ion[ci].n_ions / per : 0;
-    u += std::max(1LL, (std::max(1LL, live) + per - 1) / per - skip) * ns;
+    long long blocks = std::max(1LL, (std::max(1LL, live) + per - 1) / per - skip);
+    if (c->slice_b[ci] > 0 || c->slice_e[ci] < cl.n_pad) {
+      // a target slice: only its i-blocks
+      const long long b0 = c->slice_b[ci] / per;
+      const long long b1 = (std::min<long long>(c->slice_e[ci], cl.n_pad) + per - 1) / per;
+      blocks = std::max(0LL, b1 - b0);
+    }
+    u += blocks * ns;
   }
-  return u;
+  return std::max(1LL, u);
 }
 
 // Source split chosen for balance: equal units handed out by the ticket finish
@@ -474,7 +505,7 @@ md_status configure(md_ctx* c, int cfg, int ctas_per_sm, int jsplit) {
     const long long skip = ions_fused(c, ci) ? c->ion[ci].n_ions / per : 0;
     c->ion_push[ci] = skip * per;
     for (long long b = 0; b < nb; ++b, ++ib) {
-      if (b < skip) continue;
+      if (b < skip || !block_in_slice(c, ci, b, per)) continue;
       for (int sg = 0; sg < cl.nseg; ++sg) {
         const long long len = std::min<long long>(cl.seg_len, cl.n_pad - static_cast<long long>(sg) * cl.seg_len);
         work.push_back({per * len, {ci, static_cast<int>(b), sg, ib}});
@@ -1043,6 +1074,8 @@ md_status create_context(const md_config* cfgs, int32_t n_clusters, const long l
     if (f.rate_model) c->any_ion = true;
     c->min_image.push_back(static_cast<unsigned char>(f.min_image));
     if (f.min_image) c->any_mi = true;
+    c->slice_b.push_back(0);
+    c->slice_e.push_back(d.n_pad);
     off += d.n_pad;
     c->max_n = std::max<long long>(c->max_n, nrec[i]);
   }
@@ -1288,6 +1321,8 @@ md_status md_set_detectors(md_ctx* c, int32_t cluster, const md_detector_config*
              std::isfinite(d->center[1]) && std::isfinite(d->center[2])))
     return fail(MD_ERR_ARG, "detectors: radius > 0, cone in [0, 90] degrees, e_max_ev > 0, "
                 "1 <= n_bins <= %d, reserved = 0, finite centre", kDetMaxBins);
+  if (d && c->any_slice)
+    return fail(MD_ERR_STATE, "detectors are not available in a context with target slices");
   MD_CUDA(cudaStreamSynchronize(c->stream));
   const size_t per = 5 * static_cast<size_t>(kDetMaxBins + 1);
   if (d && !c->d_det_hist) {
@@ -1416,6 +1451,40 @@ md_status md_wait_selftest(md_ctx* c, double budget_ms) {
   return check_device_error(c);
 }
 
+md_status md_set_slice(md_ctx* c, int32_t cluster, int64_t i_begin, int64_t i_end) {
+  if (!c) return fail(MD_ERR_ARG, "ctx is NULL");
+  if (cluster < 0 || cluster >= c->n_clusters) return fail(MD_ERR_ARG, "bad cluster index");
+  const md::ClusterDev& cl = c->cl[cluster];
+  if (i_begin < 0 || i_end < i_begin || i_end > cl.n)
+    return fail(MD_ERR_ARG, "slice [%lld, %lld) must lie in [0, %d]", (long long)i_begin,
+                (long long)i_end, cl.n);
+  if ((i_begin % kSliceAlign != 0 && i_begin != cl.n) ||
+      (i_end % kSliceAlign != 0 && i_end != cl.n))
+    return fail(MD_ERR_ARG, "slice bounds must be multiples of %d (or the record count)",
+                kSliceAlign);
+  if (c->any_ion || c->det_on)
+    return fail(MD_ERR_STATE, "target slices need a context without ionization or detectors");
+  MD_CUDA(cudaStreamSynchronize(c->stream));
+  c->slice_b[cluster] = i_begin;
+  c->slice_e[cluster] = i_end == cl.n ? cl.n_pad : i_end;
+  bool any = false;
+  for (int ci = 0; ci < c->n_clusters; ++ci)
+    any = any || c->slice_b[ci] > 0 || c->slice_e[ci] < c->cl[ci].n_pad;
+  c->any_slice = any;
+  return configure(c, c->cfg, c->ctas_per_sm, c->jsplit);
+}
+
+md_status md_get_jstream(md_ctx* c, int32_t cluster, void** posq, int64_t* n_pad) {
+  if (!c || !posq || !n_pad) return fail(MD_ERR_ARG, "NULL argument");
+  if (cluster < 0 || cluster >= c->n_clusters) return fail(MD_ERR_ARG, "bad cluster index");
+  long long step = 0;
+  MD_CUDA(cudaMemcpyAsync(&step, c->d_step, sizeof(step), cudaMemcpyDeviceToHost, c->stream));
+  MD_CUDA(cudaStreamSynchronize(c->stream));
+  *posq = static_cast<void*>(c->d_posq[step & 1] + c->cl[cluster].off);
+  *n_pad = c->cl[cluster].n_pad;
+  return check_device_error(c);
+}
+
 md_status md_get_step(md_ctx* c, int64_t* step) {
   if (!c || !step) return fail(MD_ERR_ARG, "NULL argument");
   long long v = 0;
@@ -1433,13 +1502,15 @@ static md_status run_fields(md_ctx* c, int ci, bool potential) {
   MD_CUDA(cudaStreamSynchronize(c->stream));
   const md::ClusterDev& cl = c->cl[ci];
   const float4* cur = c->d_posq[step & 1] + cl.off;
+  // targets: the cluster's slice (all its records unless md_set_slice)
+  const long long sb = c->slice_b[ci], se = std::min<long long>(c->slice_e[ci], cl.n_pad);
   md::FieldArgs a;
   a.src = cur;
   a.ns = cl.n_pad;
-  a.tgt = cur;
-  a.nt = cl.n_pad;
+  a.tgt = cur + sb;
+  a.nt = std::max(0LL, se - sb);
   a.eps2 = cl.eps2;
-  a.self_offset = 0;
+  a.self_offset = sb;
   a.e = c->d_e;
   a.phi = potential ? c->d_phi : nullptr;
   a.err = c->d_err;
@@ -1471,10 +1542,14 @@ md_status md_get_fields(md_ctx* c, int32_t cluster, double* e, double* phi) {
   if (cluster < 0 || cluster >= c->n_clusters) return fail(MD_ERR_ARG, "bad cluster index");
   md_status st = run_fields(c, cluster, phi != nullptr);
   if (st != MD_OK) return st;
-  const long long n = c->cl[cluster].n;
-  MD_CUDA(cudaMemcpyAsync(e, c->d_e, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
+  // the records of the cluster's target slice (all of them unless md_set_slice)
+  const long long sb = c->slice_b[cluster];
+  const long long n = std::max(0LL, std::min<long long>(c->slice_e[cluster], c->cl[cluster].n) - sb);
+  MD_CUDA(cudaMemcpyAsync(e + 3 * sb, c->d_e, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost,
+                          c->stream));
   if (phi)
-    MD_CUDA(cudaMemcpyAsync(phi, c->d_phi, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+    MD_CUDA(cudaMemcpyAsync(phi + sb, c->d_phi, sizeof(double) * n, cudaMemcpyDeviceToHost,
+                            c->stream));
   MD_CUDA(cudaStreamSynchronize(c->stream));
   return check_device_error(c);
 }
@@ -1524,7 +1599,7 @@ md_status md_diagnostics(md_ctx* c, int32_t cluster, md_diag* out) {
   md_status st = run_fields(c, cluster, true);
   if (st != MD_OK) return st;
   md::DiagArgs a;
-  a.c = c->cl[cluster];
+  a.c = slice_view(c, cluster);
   a.x = c->d_x[0];
   a.y = c->d_x[1];
   a.z = c->d_x[2];
@@ -1591,7 +1666,7 @@ md_status md_step_diag(md_ctx* c, md_diag* out) {
   MD_CUDA(k.launch_step_pot(a, c->grid, c->stream));
   for (int ci = 0; ci < c->n_clusters; ++ci) {
     md::DiagArgs d;
-    d.c = c->cl[ci];
+    d.c = slice_view(c, ci);
     d.x = c->d_x[0];
     d.y = c->d_x[1];
     d.z = c->d_x[2];

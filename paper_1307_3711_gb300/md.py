@@ -132,6 +132,8 @@ _SIGS = {
     "md_get_step": (_st, [_ctx_p, C.POINTER(C.c_int64)]),
     "md_set_step": (_st, [_ctx_p, C.c_int64]),
     "md_wait_selftest": (_st, [_ctx_p, C.c_double]),
+    "md_set_slice": (_st, [_ctx_p, C.c_int32, C.c_int64, C.c_int64]),
+    "md_get_jstream": (_st, [_ctx_p, C.c_int32, C.POINTER(C.c_void_p), C.POINTER(C.c_int64)]),
     "md_ionize": (_st, [_ctx_p]),
     "md_get_ionization": (_st, [_ctx_p, C.c_int32, _p, _p, _p, _p, _p]),
     "md_set_detectors": (_st, [_ctx_p, C.c_int32, C.POINTER(DetectorConfig)]),
@@ -330,6 +332,17 @@ class Context:
 
     def sync(self):
         _check(_lib.md_sync(self._h))
+
+    def set_slice(self, cluster: int, i_begin: int, i_end: int):
+        """Push only the records [i_begin, i_end) of the cluster (see md.h)."""
+        _check(_lib.md_set_slice(self._h, int(cluster), int(i_begin), int(i_end)))
+
+    def jstream(self, cluster: int = 0):
+        """(device address, n_pad) of the cluster's current j-stream, float4
+        records (x, y, z, K_C w z) read by the next step."""
+        ptr, n = C.c_void_p(), C.c_int64()
+        _check(_lib.md_get_jstream(self._h, int(cluster), C.byref(ptr), C.byref(n)))
+        return int(ptr.value or 0), int(n.value)
 
     def step_index(self) -> int:
         v = C.c_int64(0)
