@@ -387,7 +387,7 @@ def alu_frac(pairs_per_s: float, sms: int, clocks: dict) -> dict:
             "frac_at_max_clock": pairs_per_s / (128.0 * sms * 2070e6 / FP32_INSTR_PER_PAIR)}
 
 
-def secondary_measurements(md, stream, flush, sms, gpu_id, steps=3, warmup=2):
+def secondary_measurements(md, stream, flush, sms, gpu_id, tuning, steps=3, warmup=2):
     """Driver-visible numbers of the other configurations, each timed with
     CUDA events (L2 flushed between steps, outside the events) and its own
     nvidia-smi clock record:
@@ -397,7 +397,9 @@ def secondary_measurements(md, stream, flush, sms, gpu_id, steps=3, warmup=2):
                       its training time per epoch), charge-state fractions of
                       both on the same seed;
       precision_1m -- 500k Ar+ + 500k e: the step time, and the FP32/Kahan
-                      field against the FP64 GPU reference and the oracle."""
+                      field against the FP64 GPU reference and the oracle.
+    The ionizing and 1M contexts run the step kernel configuration that the
+    headline's autotuner chose (`tuning`), each with its own source split."""
     import torch
     out = {}
     cs = stream.cuda_stream
@@ -438,6 +440,7 @@ def secondary_measurements(md, stream, flush, sms, gpu_id, steps=3, warmup=2):
         ctx, ws, _, info = ionizing_context(md, n_atoms, rates, 0, cs)
         if rates == "mlp":
             trained = info.get("trained")
+        ctx.set_tuning(tuning[0], tuning[1], tuning[2], 0, 0, tuning[5], tuning[6])
         with ctx:
             for _ in range(warmup):
                 ctx.step(1)
@@ -471,6 +474,7 @@ def secondary_measurements(md, stream, flush, sms, gpu_id, steps=3, warmup=2):
     w = synth.precision_1m(seed=0, a0=0.0)
     with md.Context([md.config_from_workload(w)], [md.HostParticles.from_cluster(w.cluster)],
                     stream=cs) as ctx:
+        ctx.set_tuning(tuning[0], tuning[1], tuning[2], 0, 0, tuning[5], tuning[6])
         ctx.step(1)
         sampler = ClockSampler(gpu_id)
         time.sleep(0.3)
@@ -903,7 +907,7 @@ def run_native(args):
     secondary = None
     if (rank == 0 and world == 1 and args.workload == "xe3_200k" and not args.no_secondary):
         t_sec = time.perf_counter()
-        secondary = secondary_measurements(md, stream, flush, sms, gpu_id_for(local))
+        secondary = secondary_measurements(md, stream, flush, sms, gpu_id_for(local), tuning)
         secondary["wall_s"] = time.perf_counter() - t_sec
     dist.close()
     if rank != 0:

@@ -411,19 +411,23 @@ __device__ __forceinline__ void fold(Acc<R, POT>& a) {
   }
 }
 
-// Shared-memory staging of the j-stream.
+// The tile partial of a charge-uniform tile times its charge, then folded.
+// The products are rounded on their own (__fmul_rn), not fused into the
+// Kahan subtraction that follows, so the scalar and packed paths (whose
+// packed multiply is never fused) give the same bits.
 template <int R, bool POT>
 __device__ __forceinline__ void fold_q(Acc<R, POT>& a, float q) {
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    a.ax[r] *= q;
-    a.ay[r] *= q;
-    a.az[r] *= q;
-    if (POT) a.ap[r] *= q;
+    a.ax[r] = __fmul_rn(a.ax[r], q);
+    a.ay[r] = __fmul_rn(a.ay[r], q);
+    a.az[r] = __fmul_rn(a.az[r], q);
+    if (POT) a.ap[r] = __fmul_rn(a.ap[r], q);
   }
   fold<R, POT>(a);
 }
 
+// Shared-memory staging of the j-stream.
 template <int TILE, int STAGES>
 struct Stage {
   alignas(128) float4 tile[STAGES][TILE];
@@ -564,7 +568,7 @@ __device__ __forceinline__ void sum_tile(uint32_t tile, int cnt, const float (&x
         if (POT) {
 #pragma unroll
           for (int r = 0; r < R; ++r) {
-            kahan_add(acc.sp[r], acc.cp[r], acc.ap[r] * qt);
+            kahan_add(acc.sp[r], acc.cp[r], __fmul_rn(acc.ap[r], qt));
             acc.ap[r] = 0.0f;
           }
         }
@@ -647,7 +651,7 @@ __device__ __forceinline__ bool sum_sources(Stage<TILE, STAGES>& sm, unsigned& i
               if (POT) {
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                  kahan_add(acc.sp[r], acc.cp[r], acc.ap[r] * qt);
+                  kahan_add(acc.sp[r], acc.cp[r], __fmul_rn(acc.ap[r], qt));
                   acc.ap[r] = 0.0f;
                 }
               }
@@ -761,11 +765,24 @@ struct AccP {
 // Kahan sums and compensations of the packed path, one slot per thread, kept
 // in shared memory (folded once per tile) so the registers hold only the
 // targets and the tile partials: [component][pair][thread], component =
-// sx, sy, sz, cx, cy, cz (, sp, cp with the potential).
+// sx, sy, sz, cx, cy, cz (, sp, cp with the potential).  t holds each
+// thread's packed targets (x, y, z of its target pairs) and, in e2, the
+// packed softening: the source loop reads them back once per unit, so ptxas
+// keeps them as loaded register pairs instead of rebuilding each pair from
+// its two scalar halves at every use (two ALU moves per use, measured as ~3
+// ALU instructions per pair).
 template <int P, int THREADS, bool POT>
 struct KahanSmem {
   u64 v[POT ? 8 : 6][P][THREADS];
+  u64 t[3][P][THREADS];
+  u64 e2[THREADS];
 };
+
+__device__ __forceinline__ u64 lds_u64(uint32_t addr) {
+  u64 v;
+  asm volatile("ld.shared.u64 %0, [%1];" : "=l"(v) : "r"(addr));
+  return v;
+}
 
 // Component k (0..5: sx, sy, sz, cx, cy, cz) of target r of this thread.
 template <int P, int THREADS, bool POT>
@@ -846,14 +863,18 @@ __device__ __forceinline__ bool sum_sources_packed(Stage<TILE, STAGES>& sm, DupT
   AccP<P, POT> a;
 #pragma unroll
   for (int p = 0; p < P; ++p) {
-    xi2[p] = f2_pack(xi[2 * p], xi[2 * p + 1]);
-    yi2[p] = f2_pack(yi[2 * p], yi[2 * p + 1]);
-    zi2[p] = f2_pack(zi[2 * p], zi[2 * p + 1]);
+    ks.t[0][p][tid] = f2_pack(xi[2 * p], xi[2 * p + 1]);
+    ks.t[1][p][tid] = f2_pack(yi[2 * p], yi[2 * p + 1]);
+    ks.t[2][p][tid] = f2_pack(zi[2 * p], zi[2 * p + 1]);
+    xi2[p] = lds_u64(smem_u32(&ks.t[0][p][tid]));
+    yi2[p] = lds_u64(smem_u32(&ks.t[1][p][tid]));
+    zi2[p] = lds_u64(smem_u32(&ks.t[2][p][tid]));
     a.ax[p] = a.ay[p] = a.az[p] = a.ap[p] = 0ull;
 #pragma unroll
     for (int k = 0; k < (POT ? 8 : 6); ++k) ks.v[k][p][tid] = 0ull;
   }
-  const u64 e2 = f2_pack(eps2, eps2);
+  ks.e2[tid] = f2_pack(eps2, eps2);
+  const u64 e2 = lds_u64(smem_u32(&ks.e2[tid]));
   const int ntiles = static_cast<int>((ns + TILE - 1) / TILE);
   // live tiles only, in the same order for the issuing thread and the consumers
   int t = next_live_tile(live, gbase, ns, 0, ntiles, TILE);
