@@ -41,7 +41,7 @@ FP32_INSTR_PER_PAIR = 12
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the named workload
 # at full size in the named kernel configuration; reported only when the timed
 # run uses that configuration.
-STEP_TRAFFIC_BYTES = {("xe3_200k", 200000, 128, 4, 512, False): 34.02e6}
+STEP_TRAFFIC_BYTES = {("xe3_200k", 200000, 128, 8, 512, True): 15.77e6}
 L2_FLUSH_BYTES = 512 << 20
 WORKLOAD_TEXT = {
     "xe3_200k": "{name}: N={n} (Xe3+ ions + electrons, 10 eV), one cluster per GPU",
