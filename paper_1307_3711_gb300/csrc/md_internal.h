@@ -80,6 +80,10 @@ cudaError_t launch_ion_push(const StepArgs& a, int ci, const double* e_ion, long
 // per SM (for the choice of the source split).
 int ion_field_targets_per_cta();
 cudaError_t ion_field_blocks_per_sm(int* out);
+// Shape of the charge-change field kernel (k_ion_fix): ion targets per CTA and
+// resident CTAs per SM.
+int ion_fix_targets_per_cta();
+cudaError_t ion_fix_blocks_per_sm(int* out);
 
 // Liveness flags of all records (contexts with ionization).
 cudaError_t launch_live_init(const float4* posq0, const float4* posq1, const unsigned char* kind,

@@ -17,8 +17,10 @@
 //                 slots (a scan of the fired flags gives each its slot), so
 //                 the active slots stay one dense block;
 //   k_ion_fix     (a pass before every step) the field of the pass's charge
-//                 changes added to each ion's field, which k_push_ions then
-//                 uses to push the ions in place of the step kernel's sum.
+//                 changes at every ion, by segments of the changes;
+//   k_ion_fix_combine  the segments added in order to each ion's field, which
+//                 k_push_ions then uses to push the ions in place of the step
+//                 kernel's sum.
 // The decision runs after the whole field pass, so no charge changes while
 // any other ion's field is being summed.  Rates are FP64, as on the host.
 #include <cmath>
@@ -551,9 +553,16 @@ __global__ void __launch_bounds__(256) k_ion_apply(const IonArgs a) {
                     a.ion.slot_base + static_cast<long long>(a.ion.zmax) * a.ion.n_ions) &&
         MD_IN_RANGE(a.err, slot, 0, a.c.n)) {
       apply_one(a, step, t, slot);
-      // ions fired in this pass, in slot order (the charge changes of k_ion_fix)
-      if (a.fired_list && MD_IN_RANGE(a.err, slot - *a.pass_slot, 0, a.ion.n_ions))
-        a.fired_list[slot - *a.pass_slot] = static_cast<int>(t);
+      // the pass's charge changes in slot order, the sources of k_ion_fix: the
+      // ion's extra charge at its position and its freed electron's record
+      const long long k = slot - *a.pass_slot;
+      if (a.fix_src && MD_IN_RANGE(a.err, k, 0, a.ion.n_ions)) {
+        const float4* cur = (step & 1) ? a.posq1 : a.posq0;
+        const float4 pi = cur[a.c.off + t];
+        a.fix_src[k] = make_float4(pi.x, pi.y, pi.z,
+                                   static_cast<float>(a.ion.kc) * static_cast<float>(a.w[a.c.off + t]));
+        a.fix_src[a.ion.n_ions + k] = cur[a.c.off + slot];
+      }
     }
   }
   if (blockIdx.x == gridDim.x - 1 && tid == 0) {
@@ -569,80 +578,98 @@ __global__ void __launch_bounds__(256) k_ion_apply(const IonArgs a) {
 
 // Field at the ions after the pass's charge changes, for the step (clusters
 // with a pass before every step).  The pass summed the field with the charges
-// before its decisions; each ion j it fired gained one charge (kc w_j) at x_j
-// and freed an electron (charge -kc w_j) at x_e.  By superposition the field
-// the step would sum at ion t is e_ion[t] + sum over the fired of
-// dQ (x_t - x_s) / (|x_t - x_s|^2 + eps^2)^{3/2}, summed here in FP32 with a
-// Kahan fold per chunk of kFixChunk fired ions.
-constexpr int kFixThreads = 256;
-constexpr int kFixChunk = 256;
-
-template <bool MI = false>
-__global__ void __launch_bounds__(kFixThreads) k_ion_fix(const IonArgs a) {
-  __shared__ float4 s_src[2 * kFixChunk];
+// before its decisions; each ion j it fired gained one charge (K_C w_j) at x_j
+// and freed an electron (charge -K_C w_j) at x_e.  By superposition the field
+// the step would sum at ion t is e_ion[t] plus the field of those changes.
+// k_ion_apply lists them as two source streams in slot order (fix_src: the
+// ions' extra charges, then at n_ions the freed electrons), and k_ion_fix sums
+// them at every ion with the step kernel's TMA-staged FP32/Kahan source loop:
+// CTA (x, y) takes R x THREADS ions and segment y of the nf charge changes of
+// each stream, and writes its partial field to scratch [seg][n_ions][3];
+// k_ion_fix_combine adds the segments in order to e_ion (deterministic).
+template <int THREADS, int R, int TILE, int STAGES, bool MI = false>
+__global__ void __launch_bounds__(THREADS) k_ion_fix(const IonArgs a) {
+  __shared__ Stage<TILE, STAGES> sm;
+  __shared__ int s_abort;
   const long long step = __ldcg(a.step);
   if (!pass_active(a, step)) return;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) mbar_init(&sm.full[s], 1);
+    fence_mbar_init();
+    s_abort = 0;
+  }
+  __syncthreads();
   const long long base = __ldcg(a.pass_slot);
-  const long long nf = __ldcg(a.next_slot) - base;
-  if (nf <= 0) return;
+  long long nf = __ldcg(a.next_slot) - base;
+  nf = nf < 0 ? 0 : (nf > a.ion.n_ions ? a.ion.n_ions : nf);
+  const long long per_seg = (nf + gridDim.y - 1) / gridDim.y;
+  const long long j0 = static_cast<long long>(blockIdx.y) * per_seg;
+  const long long jn = j0 >= nf ? 0 : (nf - j0 < per_seg ? nf - j0 : per_seg);
   const float4* __restrict__ cur = (step & 1) ? a.posq1 : a.posq0;
-  const long long t = static_cast<long long>(blockIdx.x) * kFixThreads + threadIdx.x;
-  const float4 pt = (t < a.ion.n_ions) ? cur[a.c.off + t] : make_float4(0.f, 0.f, 0.f, 0.f);
-  const float xi[1] = {pt.x}, yi[1] = {pt.y}, zi[1] = {pt.z};
-  Acc<1, false> acc;
+  const long long t0 = static_cast<long long>(blockIdx.x) * (THREADS * R);
+  float xi[R], yi[R], zi[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const long long t = t0 + threadIdx.x + r * THREADS;
+    const float4 p = (t < a.ion.n_ions) ? cur[a.c.off + t] : make_float4(0.f, 0.f, 0.f, 0.f);
+    xi[r] = p.x;
+    yi[r] = p.y;
+    zi[r] = p.z;
+  }
+  Acc<R, false> acc;
   acc.zero();
-  const float kc = static_cast<float>(a.ion.kc);
-  // minimum-image twin: image distances while the boundary is periodic at t_n
-  bool mi_on = false;
-  float L = 0.0f, invL = 0.0f;
-  [[maybe_unused]] float* s_tb = nullptr;
-  if constexpr (MI) {
-    __shared__ float tb[6];
-    const double t_n = a.c.t0 + static_cast<double>(step) * a.c.dt;
-    mi_on = a.min_image && (a.c.boundary == 1 || (a.c.boundary == 2 && t_n < a.c.t_switch));
-    L = static_cast<float>(a.c.box);
-    invL = 1.0f / L;
-    s_tb = tb;
-    if (mi_on) target_bounds<kFixThreads, 1>(xi, yi, zi, tb);
-  }
-  for (long long k0 = 0; k0 < nf; k0 += kFixChunk) {
-    const int cnt = static_cast<int>(nf - k0 < kFixChunk ? nf - k0 : kFixChunk);
-    __syncthreads();
-    if (threadIdx.x < cnt) {
-      const long long k = k0 + threadIdx.x;
-      const int j = a.fired_list[k];
-      float4 pj = make_float4(0.f, 0.f, 0.f, 0.f), pe = pj;
-      if (MD_IN_RANGE(a.err, j, 0, a.ion.n_ions) &&
-          MD_IN_RANGE(a.err, base + k, 0, a.c.n)) {
-        pj = cur[a.c.off + j];
-        pj.w = kc * static_cast<float>(a.w[a.c.off + j]);
-        pe = cur[a.c.off + base + k];
-      }
-      s_src[threadIdx.x] = pj;
-      s_src[kFixChunk + threadIdx.x] = pe;
+  if (jn > 0) {
+    unsigned it = 0;
+    bool ok = true;
+    bool mi_on = false;
+    if constexpr (MI) {
+      const double t_n = a.c.t0 + static_cast<double>(step) * a.c.dt;
+      mi_on = a.min_image && (a.c.boundary == 1 || (a.c.boundary == 2 && t_n < a.c.t_switch));
     }
-    __syncthreads();
-    bool img = false;
-    if constexpr (MI)
-      img = mi_on && (tile_needs_image(smem_u32(&s_src[0]), cnt, s_tb, L) ||
-                      tile_needs_image(smem_u32(&s_src[kFixChunk]), cnt, s_tb, L));
-    if (img) {
-      for (int q = 0; q < cnt; ++q) {
-        pair<1, false, true>(s_src[q], xi, yi, zi, a.c.eps2, acc, L, invL);
-        pair<1, false, true>(s_src[kFixChunk + q], xi, yi, zi, a.c.eps2, acc, L, invL);
-      }
+    if (mi_on) {
+      __shared__ float s_tb[6];
+      target_bounds<THREADS, R>(xi, yi, zi, s_tb);
+      const float L = static_cast<float>(a.c.box);
+      for (int half = 0; half < 2 && ok; ++half)
+        ok = sum_sources<THREADS, R, TILE, STAGES, false, true>(
+            sm, it, a.fix_src + half * a.ion.n_ions + j0, jn, xi, yi, zi, a.c.eps2, acc, a.err,
+            &s_abort, nullptr, 0, L, 1.0f / L, s_tb);
     } else {
-      for (int q = 0; q < cnt; ++q) {
-        pair<1, false>(s_src[q], xi, yi, zi, a.c.eps2, acc);
-        pair<1, false>(s_src[kFixChunk + q], xi, yi, zi, a.c.eps2, acc);
-      }
+      for (int half = 0; half < 2 && ok; ++half)
+        ok = sum_sources<THREADS, R, TILE, STAGES, false>(
+            sm, it, a.fix_src + half * a.ion.n_ions + j0, jn, xi, yi, zi, a.c.eps2, acc, a.err,
+            &s_abort);
     }
-    fold<1, false>(acc);
+    if (!ok) return;
   }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const long long t = t0 + threadIdx.x + r * THREADS;
+    if (t >= a.ion.n_ions) continue;
+    if (!MD_IN_RANGE(a.err, blockIdx.y, 0, kIonMaxSeg)) continue;
+    double* o = a.scratch + 3 * (static_cast<long long>(blockIdx.y) * a.ion.n_ions + t);
+    o[0] = -(static_cast<double>(acc.sx[r]) - acc.cx[r]);
+    o[1] = -(static_cast<double>(acc.sy[r]) - acc.cy[r]);
+    o[2] = -(static_cast<double>(acc.sz[r]) - acc.cz[r]);
+  }
+}
+
+// e_ion[t] += the charge-change field of k_ion_fix, its segments in order.
+__global__ void __launch_bounds__(256) k_ion_fix_combine(const IonArgs a) {
+  const long long step = __ldcg(a.step);
+  if (!pass_active(a, step)) return;
+  const long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= a.ion.n_ions) return;
-  a.e_ion[3 * t + 0] -= static_cast<double>(acc.sx[0]) - acc.cx[0];
-  a.e_ion[3 * t + 1] -= static_cast<double>(acc.sy[0]) - acc.cy[0];
-  a.e_ion[3 * t + 2] -= static_cast<double>(acc.sz[0]) - acc.cz[0];
+  double ex = 0.0, ey = 0.0, ez = 0.0;
+  for (int sg = 0; sg < a.fix_nseg; ++sg) {
+    const double* o = a.scratch + 3 * (static_cast<long long>(sg) * a.ion.n_ions + t);
+    ex += o[0];
+    ey += o[1];
+    ez += o[2];
+  }
+  a.e_ion[3 * t + 0] += ex;
+  a.e_ion[3 * t + 1] += ey;
+  a.e_ion[3 * t + 2] += ez;
 }
 
 // Push of the first n_push ion records of cluster ci with the field of the
@@ -692,6 +719,10 @@ __global__ void k_live_init(const float4* posq0, const float4* posq1, const unsi
 constexpr int kIonThreads = 128;
 constexpr int kIonR = 2;
 constexpr int kIonTile = 512;
+// the charge-change field (no moments: four targets per thread)
+constexpr int kFixThreads = kIonThreads;
+constexpr int kFixR = 4;
+constexpr int kFixTile = 512;
 
 }  // namespace
 
@@ -706,9 +737,16 @@ cudaError_t launch_live_init(const float4* posq0, const float4* posq1, const uns
 
 int ion_field_targets_per_cta() { return kIonThreads * kIonR; }
 
+int ion_fix_targets_per_cta() { return kFixThreads * kFixR; }
+
 cudaError_t ion_field_blocks_per_sm(int* out) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
       out, k_ion_field<kIonThreads, kIonR, kIonTile, 2>, kIonThreads, 0);
+}
+
+cudaError_t ion_fix_blocks_per_sm(int* out) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      out, k_ion_fix<kFixThreads, kFixR, kFixTile, 2>, kFixThreads, 0);
 }
 
 cudaError_t launch_ion_pass(const IonArgs& a, cudaStream_t s) {
@@ -733,12 +771,17 @@ cudaError_t launch_ion_pass(const IonArgs& a, cudaStream_t s) {
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_ion_apply<<<g2, 256, 0, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if (a.e_ion && a.fired_list) {
-    const unsigned gf = static_cast<unsigned>((a.ion.n_ions + kFixThreads - 1) / kFixThreads);
+  if (a.e_ion && a.fix_src) {
+    if (a.fix_nseg < 1 || a.fix_nseg > kIonMaxSeg) return cudaErrorInvalidValue;
+    const long long per_fix = kFixThreads * kFixR;
+    const dim3 gf(static_cast<unsigned>((a.ion.n_ions + per_fix - 1) / per_fix),
+                  static_cast<unsigned>(a.fix_nseg));
     if (a.min_image)
-      k_ion_fix<true><<<gf, kFixThreads, 0, s>>>(a);
+      k_ion_fix<kFixThreads, kFixR, kFixTile, 2, true><<<gf, kFixThreads, 0, s>>>(a);
     else
-      k_ion_fix<<<gf, kFixThreads, 0, s>>>(a);
+      k_ion_fix<kFixThreads, kFixR, kFixTile, 2><<<gf, kFixThreads, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_ion_fix_combine<<<g2, 256, 0, s>>>(a);
     e = cudaGetLastError();
   }
   return e;

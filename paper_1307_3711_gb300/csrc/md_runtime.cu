@@ -58,6 +58,7 @@ struct md_ctx {
   int device = 0;
   int sm_count = 0;
   int ion_field_bps = 1;   // resident CTAs per SM of the ionization field kernel
+  int ion_fix_bps = 1;     // resident CTAs per SM of the charge-change field kernel
   int field_bps = 1;       // resident CTAs per SM of the field kernel (md_get_fields)
   double* d_field_part = nullptr;  // [kFieldMaxSeg][max n_pad][4] split partials
   double* d_diag_rec = nullptr;    // diagnostic steps: [n_total][6] per-record diagnostics
@@ -139,7 +140,7 @@ struct md_ctx {
   // clusters with a pass before every step: the field at each ion after the
   // pass (the step pushes those ions with it) and the ions fired per pass
   double* d_ion_e = nullptr;           // [sum n_ions][3]
-  int* d_ion_list = nullptr;           // [sum n_ions]
+  float4* d_ion_fix = nullptr;         // [2 sum n_ions] charge changes of a pass (fix_src)
   std::vector<long long> ion_push;     // per cluster: ion records pushed with d_ion_e
   unsigned char* d_src_live = nullptr; // liveness flags per kLiveGroup records
   unsigned char* d_tgt_live = nullptr;
@@ -656,7 +657,15 @@ md::IonArgs ion_args(md_ctx* c, int ci, int force) {
   a.cl_dev = c->d_cl + ci;
   a.min_image = c->min_image[ci];
   a.e_ion = ions_fused(c, ci) ? c->d_ion_e + 3 * c->ion_out_off[ci] : nullptr;
-  a.fired_list = ions_fused(c, ci) ? c->d_ion_list + c->ion_out_off[ci] : nullptr;
+  a.fix_src = ions_fused(c, ci) ? c->d_ion_fix + 2 * c->ion_out_off[ci] : nullptr;
+  // segments of the charge-change field: about 3 waves of (ion block, segment) CTAs
+  {
+    const long long per = md::ion_fix_targets_per_cta();
+    const long long blocks = std::max(1LL, (static_cast<long long>(a.ion.n_ions) + per - 1) / per);
+    const long long cap = std::max(1LL, static_cast<long long>(c->ion_fix_bps) * c->sm_count);
+    a.fix_nseg = static_cast<int>(std::max(1LL, std::min<long long>(
+        md::kIonMaxSeg, (3 * cap + blocks - 1) / blocks)));
+  }
   return a;
 }
 
@@ -763,7 +772,7 @@ void free_ctx(md_ctx* c) {
   cudaFree(c->d_ion_fired);
   cudaFree(c->d_ion_nu);
   cudaFree(c->d_ion_e);
-  cudaFree(c->d_ion_list);
+  cudaFree(c->d_ion_fix);
   cudaFree(c->d_src_live);
   cudaFree(c->d_tgt_live);
   cudaFree(c->d_vel);
@@ -1021,6 +1030,7 @@ md_status create_context(const md_config* cfgs, int32_t n_clusters, const long l
                      prop.name, prop.major, prop.minor));
   c->sm_count = prop.multiProcessorCount;
   e = md::ion_field_blocks_per_sm(&c->ion_field_bps);
+  if (e == cudaSuccess) e = md::ion_fix_blocks_per_sm(&c->ion_fix_bps);
   if (e != cudaSuccess) return bail(cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor"));
   if (stream) {
     c->stream = static_cast<cudaStream_t>(stream);
@@ -1135,7 +1145,7 @@ md_status create_context(const md_config* cfgs, int32_t n_clusters, const long l
         dev_alloc(&c->d_ion_fired, static_cast<size_t>(sum_ion)) != cudaSuccess ||
         dev_alloc(&c->d_ion_nu, static_cast<size_t>(sum_ion)) != cudaSuccess ||
         dev_alloc(&c->d_ion_e, 3 * static_cast<size_t>(sum_ion)) != cudaSuccess ||
-        dev_alloc(&c->d_ion_list, static_cast<size_t>(sum_ion)) != cudaSuccess)
+        dev_alloc(&c->d_ion_fix, 2 * static_cast<size_t>(sum_ion)) != cudaSuccess)
       return bail(fail(MD_ERR_OOM, "ionization buffers"));
     const size_t groups = static_cast<size_t>((c->n_total + md::kLiveGroup - 1) / md::kLiveGroup);
     if (dev_alloc(&c->d_src_live, groups) != cudaSuccess ||

@@ -151,10 +151,13 @@ struct IonArgs {
   ClusterDev* cl_dev;
   // clusters with a pass before every step (nullptr otherwise): the Coulomb
   // field at each ion after the pass's charge changes, [n_ions][3], which the
-  // step uses for the ions instead of summing their field again, and the ions
-  // fired in this pass in slot order, [n_ions]
+  // step uses for the ions instead of summing their field again; and the
+  // pass's charge changes as two source streams in slot order, [2 n_ions]:
+  // fix_src[k] = (x, y, z, +K_C w) of the k-th fired ion (its extra charge),
+  // fix_src[n_ions + k] = its freed electron's j-stream record
   double* e_ion;
-  int* fired_list;
+  float4* fix_src;
+  int fix_nseg;       // source segments of the charge-change field (k_ion_fix)
   // 1: minimum-image distances while the boundary is periodic (field and
   // local moments of the pass, charge-change correction)
   int min_image;
