@@ -771,7 +771,10 @@ md_status md_mlp_train(const md_mlp_train_config* cfg, float* params_out, md_mlp
   MLP_CUDA(md::train_smem_attr());
   const long long n = cfg->n_samples;
   const long long nh = std::max<long long>(4096, n / 20);  // held-out set
-  const int grid = md::train_grid();
+  // one CTA per tile of the minibatch (up to two per SM): more CTAs would only
+  // add zero partials for the Adam kernel to sum
+  const int grid = static_cast<int>(std::max<long long>(1, std::min<long long>(
+      md::train_grid(), (cfg->batch + md::kTileSamples - 1) / md::kTileSamples)));
   float *feats = nullptr, *target = nullptr, *hfeats = nullptr, *htarget = nullptr, *hy = nullptr;
   int *zs = nullptr, *hz = nullptr;
   float *p = nullptr, *m = nullptr, *v = nullptr, *part = nullptr, *lpart = nullptr,

@@ -54,9 +54,22 @@ def test_forward_matches_oracle(md):
     md.mlp_forward_device(pd.data_ptr(), fd.data_ptr(), n, yd.data_ptr())
     torch.cuda.synchronize()
     y = yd.cpu().numpy()
-    y64 = oracle.mlp_forward(bf16_round(p), bf16_round(f))
+    pb = bf16_round(p)
+    y64 = oracle.mlp_forward(pb, bf16_round(f))
     err = np.abs(y - y64)
-    assert err.max() < 0.03 * np.abs(y64).max()
+    # Error budget of the one rounding the oracle does not make: the GPU feeds
+    # layer 2 with the layer-1 activations h1 rounded to BF16 (relative
+    # 2^-9), so a2_j moves by at most 2^-9 sum_k |W2_jk| |h1_k|, h2 = silu(a2)
+    # by at most max|silu'| (< 1.1) times that, and output i by
+    # sum_j |W3_ij| times the h2 error; FP32 accumulation adds ~1e-6.
+    w1, b1 = pb[0:256].reshape(64, 4), pb[256:320]
+    w2, w3 = pb[320:4416].reshape(64, 64), pb[4480:4992].reshape(8, 64)
+    a1 = bf16_round(f) @ w1.T + b1
+    h1 = a1 / (1.0 + np.exp(-a1))
+    bound = 1.1 * 2.0 ** -9 * (np.abs(h1) @ np.abs(w2).T) @ np.abs(w3).T + 1e-5
+    print(f"forward: max |y - y64| {err.max():.3g} (max/bound {(err / bound).max():.3g}), "
+          f"median {np.median(err):.3g}, scale {np.abs(y64).max():.3g}")
+    assert np.all(err <= bound)
     assert np.median(err) < 0.003 * np.abs(y64).max()
 
 
