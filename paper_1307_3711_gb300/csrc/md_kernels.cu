@@ -255,8 +255,8 @@ const KernelConfig kConfigs[] = {
     MD_STEP_CONFIG_POT(256, 4, 512, 2, 0),
     // packed f32x2 pair arithmetic (tile expanded in shared memory, one TMA stage)
     MD_STEP_CONFIG(128, 4, 256, 1, true, 0), MD_STEP_CONFIG(256, 4, 256, 1, true, 0),
-    MD_STEP_CONFIG(128, 8, 256, 1, true, 0), MD_STEP_CONFIG(128, 6, 256, 1, true, 0),
-    MD_STEP_CONFIG(128, 8, 512, 1, true, 0), MD_STEP_CONFIG(64, 8, 256, 1, true, 0),
+    MD_STEP_CONFIG(128, 8, 256, 1, true, 0), MD_STEP_CONFIG(128, 4, 512, 1, true, 0),
+    MD_STEP_CONFIG(256, 4, 512, 1, true, 0), MD_STEP_CONFIG(128, 8, 512, 1, true, 0),
 };
 
 constexpr int kFieldThreads = 128;
