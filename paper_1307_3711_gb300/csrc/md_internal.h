@@ -84,6 +84,10 @@ cudaError_t ion_field_blocks_per_sm(int* out);
 // resident CTAs per SM.
 int ion_fix_targets_per_cta();
 cudaError_t ion_fix_blocks_per_sm(int* out);
+// Shape of the field-only pass kernel (clusters whose moments come from the
+// cell list).
+int ion_sum_targets_per_cta();
+cudaError_t ion_sum_blocks_per_sm(int* out);
 
 // Liveness flags of all records (contexts with ionization).
 cudaError_t launch_live_init(const float4* posq0, const float4* posq1, const unsigned char* kind,

@@ -23,6 +23,7 @@
 //                 kernel's sum.
 // The decision runs after the whole field pass, so no charge changes while
 // any other ion's field is being summed.  Rates are FP64, as on the host.
+#include <algorithm>
 #include <cmath>
 
 #include "md_device.cuh"
@@ -369,6 +370,326 @@ __global__ void __launch_bounds__(THREADS) k_ion_field(const IonArgs a) {
     o[9] = mom.ry[r];
     o[10] = mom.rz[r];
   }
+}
+
+// ------------------------------------------- field and moments, separately --
+//
+// Clusters without minimum-image forces take the field and the local moments
+// of the pass in two parts: k_ion_field_sum sums the field of the live records
+// at the ions (the step kernel's TMA source loop, no moment test in the pair
+// loop), and the moments come from a cell list of the electrons near the ions,
+// so each ion tests only the electrons of its own and the 26 neighbouring
+// cells.  The moments are summed about the ion's own velocity: each
+// electron's terms are rounded to FP32, then to 64-bit fixed point (units of
+// 2^-40), and integer sums do not depend on the order in which the cells
+// list their electrons, so the result is deterministic although the listing
+// uses atomic counters.  The near test is the field pass's: the FP32
+// r^2 + eps^2 of the j-stream positions against r_loc^2 + eps^2.
+
+// Field of the live records at the ions: CTA (x, y) sums segment y of the
+// live records for R x THREADS ions and writes its field to the scratch
+// slots of segment y (slots 0-2; slot 3, the weight of the local electrons,
+// is 0 here and filled for segment 0 by k_ion_moments).
+template <int THREADS, int R, int TILE, int STAGES, bool PACK>
+__global__ void __launch_bounds__(THREADS) k_ion_field_sum(const IonArgs a) {
+  __shared__ Stage<TILE, STAGES> sm;
+  __shared__ DupTile<PACK ? TILE : 1> dup;
+  __shared__ KahanSmem<PACK ? R / 2 : 1, PACK ? THREADS : 1, false> ks;
+  __shared__ int s_abort;
+  const long long step = __ldcg(a.step);
+  if (!pass_active(a, step)) return;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) mbar_init(&sm.full[s], 1);
+    fence_mbar_init();
+    s_abort = 0;
+  }
+  __syncthreads();
+  const float4* __restrict__ cur = (step & 1) ? a.posq1 : a.posq0;
+  long long n_live = __ldcg(a.next_slot);
+  n_live = n_live > a.ion.slot_base ? n_live : a.ion.slot_base;
+  n_live = n_live < a.c.n_pad ? (n_live > 0 ? n_live : 0) : a.c.n_pad;
+  const long long per_seg = (n_live + gridDim.y - 1) / gridDim.y;
+  const long long seg_len = (per_seg + TILE - 1) / TILE * TILE;
+  const long long j0 = static_cast<long long>(blockIdx.y) * seg_len;
+  const long long ns = (j0 >= n_live) ? 0 : ((n_live - j0 < seg_len) ? n_live - j0 : seg_len);
+  const long long t0 = static_cast<long long>(blockIdx.x) * (THREADS * R);
+  float xi[R], yi[R], zi[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const long long t = t0 + threadIdx.x + r * THREADS;
+    const float4 p = (t < a.ion.n_ions) ? cur[a.c.off + t] : make_float4(0.f, 0.f, 0.f, 0.f);
+    xi[r] = p.x;
+    yi[r] = p.y;
+    zi[r] = p.z;
+  }
+  Acc<R, false> acc;
+  acc.zero();
+  unsigned it = 0;
+  if constexpr (PACK) {
+    // (an empty segment still clears the Kahan sums and returns at once)
+    if (!sum_sources_packed<THREADS, R, TILE, STAGES, false>(
+            sm, dup, ks, it, cur + a.c.off + j0, ns, xi, yi, zi, a.c.eps2, a.err, &s_abort,
+            a.src_live, a.c.off + j0))
+      return;
+  } else if (ns > 0) {
+    if (!sum_sources<THREADS, R, TILE, STAGES, false>(sm, it, cur + a.c.off + j0, ns, xi, yi, zi,
+                                                      a.c.eps2, acc, a.err, &s_abort, a.src_live,
+                                                      a.c.off + j0))
+      return;
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const long long tt = t0 + threadIdx.x + r * THREADS;
+    if (tt >= a.ion.n_ions) continue;
+    if (!MD_IN_RANGE(a.err, blockIdx.y, 0, kIonMaxSeg)) continue;
+    double* o = a.scratch + kIonScratch * (static_cast<long long>(blockIdx.y) * a.ion.n_ions + tt);
+    if constexpr (PACK) {
+      o[0] = -(static_cast<double>(kahan_part(ks, 0, r)) - kahan_part(ks, 3, r));
+      o[1] = -(static_cast<double>(kahan_part(ks, 1, r)) - kahan_part(ks, 4, r));
+      o[2] = -(static_cast<double>(kahan_part(ks, 2, r)) - kahan_part(ks, 5, r));
+    } else {
+      o[0] = -(static_cast<double>(acc.sx[r]) - acc.cx[r]);
+      o[1] = -(static_cast<double>(acc.sy[r]) - acc.cy[r]);
+      o[2] = -(static_cast<double>(acc.sz[r]) - acc.cz[r]);
+    }
+    o[3] = 0.0;
+  }
+}
+
+// Spatial hash of the cell list: cells of side h = 1.01 r_loc, so an electron
+// within r_loc of an ion lies in the ion's cell or one of the 26 around it;
+// the integer cell coordinates are hashed into kCellBuckets buckets (distant
+// cells may share a bucket; the near test rejects their electrons).
+__device__ __forceinline__ bool cell_coords(float x, float y, float z, float inv_h, int* cc) {
+  const float p[3] = {x * inv_h, y * inv_h, z * inv_h};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float f = floorf(p[c]);
+    if (!(f > -1.0e9f && f < 1.0e9f)) return false;  // far away or not finite
+    cc[c] = static_cast<int>(f);
+  }
+  return true;
+}
+
+__device__ __forceinline__ int cell_bucket(int x, int y, int z) {
+  const unsigned h = (static_cast<unsigned>(x) * 73856093u) ^
+                     (static_cast<unsigned>(y) * 19349663u) ^
+                     (static_cast<unsigned>(z) * 83492791u);
+  return static_cast<int>(h & static_cast<unsigned>(kCellBuckets - 1));
+}
+
+__device__ __forceinline__ int bucket_of(float x, float y, float z, float inv_h) {
+  int cc[3];
+  if (!cell_coords(x, y, z, inv_h, cc)) return -1;
+  return cell_bucket(cc[0], cc[1], cc[2]);
+}
+
+__device__ __forceinline__ float cell_inv_h(const IonArgs& a) {
+  return 1.0f / (1.01f * static_cast<float>(a.ion.r_loc));
+}
+
+// FILL = false: count the electrons (negative charge) of the live records per
+// cell; FILL = true: list each at its cell's start + an atomic fill counter.
+template <bool FILL>
+__global__ void __launch_bounds__(256) k_cell_list(const IonArgs a) {
+  const long long step = __ldcg(a.step);
+  if (!pass_active(a, step)) return;
+  const float4* __restrict__ cur = (step & 1) ? a.posq1 : a.posq0;
+  long long n_live = __ldcg(a.next_slot);
+  n_live = n_live > a.ion.slot_base ? n_live : a.ion.slot_base;
+  n_live = n_live < a.c.n_pad ? (n_live > 0 ? n_live : 0) : a.c.n_pad;
+  const CellBuf cb = a.cells;
+  const float inv_h = cell_inv_h(a);
+  for (long long j = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; j < n_live;
+       j += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const float4 p = cur[a.c.off + j];
+    if (!(p.w < 0.0f)) continue;
+    const int cell = bucket_of(p.x, p.y, p.z, inv_h);
+    if (cell < 0) continue;
+    if (!FILL) {
+      atomicAdd(cb.count + cell, 1);
+    } else {
+      const long long k = cb.start[cell] + atomicAdd(cb.fill + cell, 1);
+      if (!MD_IN_RANGE(a.err, k, 0, cb.capacity)) continue;
+      cb.rec[2 * k] = p;
+      cb.rec[2 * k + 1] = a.vel[a.c.off + j];
+    }
+  }
+}
+
+// FILL = false: count the ions per cell; FILL = true: list them in cell order.
+template <bool FILL>
+__global__ void __launch_bounds__(256) k_ion_cell_list(const IonArgs a) {
+  const long long step = __ldcg(a.step);
+  if (!pass_active(a, step)) return;
+  const float4* __restrict__ cur = (step & 1) ? a.posq1 : a.posq0;
+  const CellBuf cb = a.cells;
+  const float inv_h = cell_inv_h(a);
+  for (long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+       t < a.ion.n_ions; t += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const float4 p = cur[a.c.off + t];
+    int cell = bucket_of(p.x, p.y, p.z, inv_h);
+    if (cell < 0) cell = 0;  // a position too far away to have a cell: its moments stay 0
+    if (!FILL) {
+      atomicAdd(cb.ion_count + cell, 1);
+    } else {
+      const long long k = cb.ion_start[cell] + atomicAdd(cb.ion_fill + cell, 1);
+      if (!MD_IN_RANGE(a.err, k, 0, a.ion.n_ions)) continue;
+      cb.ion_list[k] = static_cast<int>(t);
+    }
+  }
+}
+
+// Exclusive scan of the kCellBuckets bucket counts into starts, in three
+// launches: each of kScanBlocks CTAs scans its 1024 buckets and records their
+// total; one CTA scans the totals; each CTA adds its offset.
+constexpr int kScanBlocks = kCellBuckets / 1024;
+
+__device__ __forceinline__ int block_excl_scan_1024(int v, int* s_warp, int* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int w = s_warp[lane];
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, d);
+      if (lane >= d) w += y;
+    }
+    s_warp[lane] = w;  // inclusive scan of the warp totals
+  }
+  __syncthreads();
+  const int before = (warp > 0 ? s_warp[warp - 1] : 0) + x - v;
+  if (total) *total = s_warp[31];
+  return before;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_blocks(const IonArgs a, const int* count,
+                                                      int* start, int* totals) {
+  __shared__ int s_warp[32];
+  const long long step = __ldcg(a.step);
+  if (!pass_active(a, step)) return;
+  const int k = blockIdx.x * 1024 + threadIdx.x;
+  int tot = 0;
+  start[k] = block_excl_scan_1024(count[k], s_warp, &tot);
+  if (threadIdx.x == 0) totals[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_totals(const IonArgs a, int* totals, int* start) {
+  __shared__ int s_warp[32];
+  const long long step = __ldcg(a.step);
+  if (!pass_active(a, step)) return;
+  const int v = threadIdx.x < kScanBlocks ? totals[threadIdx.x] : 0;
+  int tot = 0;
+  const int before = block_excl_scan_1024(v, s_warp, &tot);
+  __syncthreads();
+  if (threadIdx.x < kScanBlocks) totals[threadIdx.x] = before;
+  if (threadIdx.x == 0) start[kCellBuckets] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_add(const IonArgs a, const int* totals,
+                                                   int* start) {
+  const long long step = __ldcg(a.step);
+  if (!pass_active(a, step)) return;
+  start[blockIdx.x * 1024 + threadIdx.x] += totals[blockIdx.x];
+}
+
+cudaError_t launch_cell_scan(const IonArgs& a, const int* count, int* start, cudaStream_t s) {
+  k_scan_blocks<<<kScanBlocks, 1024, 0, s>>>(a, count, start, a.cells.scan_tmp);
+  k_scan_totals<<<1, 1024, 0, s>>>(a, a.cells.scan_tmp, start);
+  k_scan_add<<<kScanBlocks, 1024, 0, s>>>(a, a.cells.scan_tmp, start);
+  return cudaGetLastError();
+}
+
+// Local moments of every ion from the electrons of its 27 cells (R14): weight
+// W, and about u_ref = the ion's own velocity the sums S = sum w du and
+// Q = sum w |du|^2, in fixed point; written as segment 0 of the scratch.
+__global__ void __launch_bounds__(128) k_ion_moments(const IonArgs a) {
+  const long long step = __ldcg(a.step);
+  if (!pass_active(a, step)) return;
+  const long long k_ion = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k_ion >= a.ion.n_ions) return;
+  const CellBuf cb = a.cells;
+  // ions in cell order: the threads of a warp mostly share their 27 cells
+  const long long t = cb.ion_list[k_ion];
+  if (!MD_IN_RANGE(a.err, t, 0, a.ion.n_ions)) return;
+  const float4* __restrict__ cur = (step & 1) ? a.posq1 : a.posq0;
+  const float4 pi = cur[a.c.off + t];
+  const float4 ui = a.vel[a.c.off + t];
+  const float eps2 = a.c.eps2;
+  const float rloc2e = static_cast<float>(a.ion.r_loc * a.ion.r_loc) + eps2;
+  constexpr float kScaleF = 1099511627776.0f;  // 2^40
+  long long W = 0, S[3] = {0, 0, 0}, Q = 0;
+  // one electron's terms, rounded to FP32 and then exactly to 2^-40 units
+  auto add = [&](const float4 v) {
+    const float ux = v.x - ui.x, uy = v.y - ui.y, uz = v.z - ui.z;
+    const float ws = v.w * kScaleF;
+    W += __float2ll_rn(ws);
+    S[0] += __float2ll_rn(ws * ux);
+    S[1] += __float2ll_rn(ws * uy);
+    S[2] += __float2ll_rn(ws * uz);
+    Q += __float2ll_rn(ws * fmaf(ux, ux, fmaf(uy, uy, uz * uz)));
+  };
+  int cc[3];
+  if (cell_coords(pi.x, pi.y, pi.z, cell_inv_h(a), cc)) {
+    // the 27 cells' buckets, each visited once (cells may share a bucket)
+    int bk[27];
+    int nb = 0;
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int b = cell_bucket(cc[0] + dx, cc[1] + dy, cc[2] + dz);
+          bool seen = false;
+          for (int q = 0; q < nb; ++q) seen = seen || (bk[q] == b);
+          if (!seen) bk[nb++] = b;
+        }
+    for (int q = 0; q < nb; ++q) {
+      const int cell = bk[q];
+      const int k1 = cb.start[cell + 1];
+      int k = cb.start[cell];
+      // four candidates per round: independent loads, one branch on the nearest
+      for (; k + 4 <= k1; k += 4) {
+        float r2[4];
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          const float4 p = cb.rec[2 * (k + g)];
+          const float ddx = p.x - pi.x, ddy = p.y - pi.y, ddz = p.z - pi.z;
+          r2[g] = fmaf(ddx, ddx, eps2);
+          r2[g] = fmaf(ddy, ddy, r2[g]);
+          r2[g] = fmaf(ddz, ddz, r2[g]);
+        }
+        if (fminf(fminf(r2[0], r2[1]), fminf(r2[2], r2[3])) < rloc2e) {
+#pragma unroll
+          for (int g = 0; g < 4; ++g)
+            if (r2[g] < rloc2e) add(cb.rec[2 * (k + g) + 1]);
+        }
+      }
+      for (; k < k1; ++k) {
+        const float4 p = cb.rec[2 * k];
+        const float ddx = p.x - pi.x, ddy = p.y - pi.y, ddz = p.z - pi.z;
+        float r2 = fmaf(ddx, ddx, eps2);
+        r2 = fmaf(ddy, ddy, r2);
+        r2 = fmaf(ddz, ddz, r2);
+        if (r2 < rloc2e) add(cb.rec[2 * k + 1]);
+      }
+    }
+  }
+  constexpr double kScale = 1099511627776.0;  // 2^40
+  double* o = a.scratch + kIonScratch * t;  // segment 0
+  o[3] = static_cast<double>(W) / kScale;
+  o[4] = static_cast<double>(S[0]) / kScale;
+  o[5] = static_cast<double>(S[1]) / kScale;
+  o[6] = static_cast<double>(S[2]) / kScale;
+  o[7] = static_cast<double>(Q) / kScale;
+  o[8] = ui.x;
+  o[9] = ui.y;
+  o[10] = ui.z;
 }
 
 // ------------------------------------------------------------- decision --
@@ -719,6 +1040,12 @@ __global__ void k_live_init(const float4* posq0, const float4* posq1, const unsi
 constexpr int kIonThreads = 128;
 constexpr int kIonR = 2;
 constexpr int kIonTile = 512;
+// the field pass without moments (cell-list moments): the step kernel's
+// packed source loop
+constexpr int kSumThreads = 128;
+constexpr int kSumR = 8;
+constexpr int kSumTile = 512;
+constexpr bool kSumPacked = true;
 // the charge-change field (no moments: four targets per thread)
 constexpr int kFixThreads = kIonThreads;
 constexpr int kFixR = 4;
@@ -739,6 +1066,13 @@ int ion_field_targets_per_cta() { return kIonThreads * kIonR; }
 
 int ion_fix_targets_per_cta() { return kFixThreads * kFixR; }
 
+int ion_sum_targets_per_cta() { return kSumThreads * kSumR; }
+
+cudaError_t ion_sum_blocks_per_sm(int* out) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      out, k_ion_field_sum<kSumThreads, kSumR, kSumTile, 1, kSumPacked>, kSumThreads, 0);
+}
+
 cudaError_t ion_field_blocks_per_sm(int* out) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
       out, k_ion_field<kIonThreads, kIonR, kIonTile, 2>, kIonThreads, 0);
@@ -752,15 +1086,44 @@ cudaError_t ion_fix_blocks_per_sm(int* out) {
 cudaError_t launch_ion_pass(const IonArgs& a, cudaStream_t s) {
   if (a.ion.n_ions <= 0) return cudaSuccess;
   if (a.nseg < 1 || a.nseg > kIonMaxSeg) return cudaErrorInvalidValue;
-  const long long per = kIonThreads * kIonR;
-  const dim3 g1(static_cast<unsigned>((a.ion.n_ions + per - 1) / per),
-                static_cast<unsigned>(a.nseg));
-  if (a.min_image)
-    k_ion_field<kIonThreads, kIonR, kIonTile, 2, true><<<g1, kIonThreads, 0, s>>>(a);
-  else
-    k_ion_field<kIonThreads, kIonR, kIonTile, 2><<<g1, kIonThreads, 0, s>>>(a);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  cudaError_t e = cudaSuccess;
+  if (a.min_image || !a.cells.count) {
+    // field and moments in one source loop
+    const long long per = kIonThreads * kIonR;
+    const dim3 g1(static_cast<unsigned>((a.ion.n_ions + per - 1) / per),
+                  static_cast<unsigned>(a.nseg));
+    if (a.min_image)
+      k_ion_field<kIonThreads, kIonR, kIonTile, 2, true><<<g1, kIonThreads, 0, s>>>(a);
+    else
+      k_ion_field<kIonThreads, kIonR, kIonTile, 2><<<g1, kIonThreads, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  } else {
+    // the field of the live records, then the moments from the cell list
+    const long long per = kSumThreads * kSumR;
+    const dim3 g1(static_cast<unsigned>((a.ion.n_ions + per - 1) / per),
+                  static_cast<unsigned>(a.nseg));
+    k_ion_field_sum<kSumThreads, kSumR, kSumTile, 1, kSumPacked><<<g1, kSumThreads, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int cells = kCellBuckets;
+    if ((e = cudaMemsetAsync(a.cells.count, 0, sizeof(int) * cells, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(a.cells.fill, 0, sizeof(int) * cells, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(a.cells.ion_count, 0, sizeof(int) * cells, s)) != cudaSuccess)
+      return e;
+    if ((e = cudaMemsetAsync(a.cells.ion_fill, 0, sizeof(int) * cells, s)) != cudaSuccess)
+      return e;
+    const unsigned gl = static_cast<unsigned>(std::min<long long>(4096, (a.c.n_pad + 255) / 256));
+    const unsigned gi = static_cast<unsigned>(
+        std::min<long long>(4096, (a.ion.n_ions + 255) / 256));
+    k_cell_list<false><<<gl, 256, 0, s>>>(a);
+    k_ion_cell_list<false><<<gi, 256, 0, s>>>(a);
+    if ((e = launch_cell_scan(a, a.cells.count, a.cells.start, s)) != cudaSuccess) return e;
+    if ((e = launch_cell_scan(a, a.cells.ion_count, a.cells.ion_start, s)) != cudaSuccess)
+      return e;
+    k_cell_list<true><<<gl, 256, 0, s>>>(a);
+    k_ion_cell_list<true><<<gi, 256, 0, s>>>(a);
+    k_ion_moments<<<static_cast<unsigned>((a.ion.n_ions + 127) / 128), 128, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   const unsigned g2 = static_cast<unsigned>((a.ion.n_ions + 255) / 256);
   k_ion_inputs<<<g2, 256, 0, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

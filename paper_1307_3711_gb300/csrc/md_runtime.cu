@@ -59,6 +59,7 @@ struct md_ctx {
   int sm_count = 0;
   int ion_field_bps = 1;   // resident CTAs per SM of the ionization field kernel
   int ion_fix_bps = 1;     // resident CTAs per SM of the charge-change field kernel
+  int ion_sum_bps = 1;     // resident CTAs per SM of the field-only pass kernel
   int field_bps = 1;       // resident CTAs per SM of the field kernel (md_get_fields)
   double* d_field_part = nullptr;  // [kFieldMaxSeg][max n_pad][4] split partials
   double* d_diag_rec = nullptr;    // diagnostic steps: [n_total][6] per-record diagnostics
@@ -141,6 +142,12 @@ struct md_ctx {
   // pass (the step pushes those ions with it) and the ions fired per pass
   double* d_ion_e = nullptr;           // [sum n_ions][3]
   float4* d_ion_fix = nullptr;         // [2 sum n_ions] charge changes of a pass (fix_src)
+  // cell list of the local moments: ints (bounds, dims, grid, counts, starts,
+  // fill counters) and the listed electrons' records, for the largest cluster
+  int* d_cell_int = nullptr;
+  float4* d_cell_rec = nullptr;
+  long long cell_cap = 0;
+  long long cell_ion_cap = 0;
   std::vector<long long> ion_push;     // per cluster: ion records pushed with d_ion_e
   unsigned char* d_src_live = nullptr; // liveness flags per kLiveGroup records
   unsigned char* d_tgt_live = nullptr;
@@ -629,9 +636,12 @@ md::IonArgs ion_args(md_ctx* c, int ci, int force) {
   // well as possible, with a small cost per extra segment; each segment keeps
   // at least 4 tiles of the cluster's records
   {
-    const long long per = md::ion_field_targets_per_cta();
+    // the field-only kernel when the moments come from the cell list
+    const bool sum_only = !c->min_image[ci] && c->d_cell_int;
+    const long long per = sum_only ? md::ion_sum_targets_per_cta() : md::ion_field_targets_per_cta();
     const long long ion_blocks = (a.ion.n_ions + per - 1) / per;
-    const long long cap = std::max(1LL, static_cast<long long>(c->ion_field_bps) * c->sm_count);
+    const long long cap = std::max(1LL, static_cast<long long>(
+        sum_only ? c->ion_sum_bps : c->ion_field_bps) * c->sm_count);
     const long long by_len = std::max(1LL, static_cast<long long>(a.c.n_pad) / 2048);
     const int smax = static_cast<int>(std::min<long long>(md::kIonMaxSeg, by_len));
     double best = -1.0;
@@ -658,6 +668,20 @@ md::IonArgs ion_args(md_ctx* c, int ci, int force) {
   a.min_image = c->min_image[ci];
   a.e_ion = ions_fused(c, ci) ? c->d_ion_e + 3 * c->ion_out_off[ci] : nullptr;
   a.fix_src = ions_fused(c, ci) ? c->d_ion_fix + 2 * c->ion_out_off[ci] : nullptr;
+  std::memset(&a.cells, 0, sizeof(a.cells));
+  if (!a.min_image && c->d_cell_int) {
+    constexpr long long C = md::kCellBuckets;
+    a.cells.count = c->d_cell_int + 16;
+    a.cells.start = c->d_cell_int + 16 + C;
+    a.cells.fill = c->d_cell_int + 16 + 2 * C + 1;
+    a.cells.rec = c->d_cell_rec;
+    a.cells.capacity = c->cell_cap;
+    a.cells.ion_count = c->d_cell_int + 16 + 3 * C + 1;
+    a.cells.ion_start = c->d_cell_int + 16 + 4 * C + 1;
+    a.cells.ion_fill = c->d_cell_int + 16 + 5 * C + 2;
+    a.cells.ion_list = c->d_cell_int + 16 + 6 * C + 2;
+    a.cells.scan_tmp = c->d_cell_int + 16 + 6 * C + 2 + c->cell_ion_cap;
+  }
   // segments of the charge-change field: about 3 waves of (ion block, segment) CTAs
   {
     const long long per = md::ion_fix_targets_per_cta();
@@ -773,6 +797,8 @@ void free_ctx(md_ctx* c) {
   cudaFree(c->d_ion_nu);
   cudaFree(c->d_ion_e);
   cudaFree(c->d_ion_fix);
+  cudaFree(c->d_cell_int);
+  cudaFree(c->d_cell_rec);
   cudaFree(c->d_src_live);
   cudaFree(c->d_tgt_live);
   cudaFree(c->d_vel);
@@ -1031,6 +1057,7 @@ md_status create_context(const md_config* cfgs, int32_t n_clusters, const long l
   c->sm_count = prop.multiProcessorCount;
   e = md::ion_field_blocks_per_sm(&c->ion_field_bps);
   if (e == cudaSuccess) e = md::ion_fix_blocks_per_sm(&c->ion_fix_bps);
+  if (e == cudaSuccess) e = md::ion_sum_blocks_per_sm(&c->ion_sum_bps);
   if (e != cudaSuccess) return bail(cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor"));
   if (stream) {
     c->stream = static_cast<cudaStream_t>(stream);
@@ -1154,6 +1181,18 @@ md_status create_context(const md_config* cfgs, int32_t n_clusters, const long l
     if (dev_alloc(&c->d_vel, N) != cudaSuccess ||
         dev_alloc(&c->d_ion_next, static_cast<size_t>(n_clusters)) != cudaSuccess)
       return bail(fail(MD_ERR_OOM, "velocity stream"));
+    {
+      // cell list of the local moments, sized for the largest cluster
+      constexpr size_t C = md::kCellBuckets;
+      long long cap = 0;
+      for (const auto& d : c->cl) cap = std::max<long long>(cap, d.n_pad);
+      if (dev_alloc(&c->d_cell_int, 16 + 6 * C + 2 + static_cast<size_t>(max_ion) + C / 1024) !=
+              cudaSuccess ||
+          dev_alloc(&c->d_cell_rec, 2 * static_cast<size_t>(cap)) != cudaSuccess)
+        return bail(fail(MD_ERR_OOM, "cell list"));
+      c->cell_cap = cap;
+      c->cell_ion_cap = max_ion;
+    }
     cudaMemsetAsync(c->d_ion_next, 0, sizeof(long long) * n_clusters, c->stream);
     cudaMemsetAsync(c->d_vel, 0, N * sizeof(float4), c->stream);
     cudaMemsetAsync(c->d_ion_out, 0, sizeof(double) * 4 * sum_ion, c->stream);

@@ -112,6 +112,27 @@ struct StepArgs {
   const unsigned char* min_image;
 };
 
+// Cell list of the electrons near the ions, for the local moments of the
+// ionization pass (clusters without minimum-image forces): cells of side
+// 1.01 r_loc, hashed into kCellBuckets buckets, the electrons of each bucket
+// listed contiguously as (position record, velocity record) pairs, and the
+// ions listed by bucket too.
+constexpr int kCellBuckets = 1 << 18;
+struct CellBuf {
+  int* count;    // [kCellBuckets] electrons per bucket
+  int* start;    // [kCellBuckets + 1] first listed electron of each bucket
+  int* fill;     // [kCellBuckets] fill counters of the listing
+  float4* rec;   // [2 capacity] the listed electrons' position and velocity records
+  long long capacity;
+  // the ions listed by bucket, so that neighbouring threads of the moment
+  // kernel take ions of one cell and read the same electron lists
+  int* ion_count;  // [kCellBuckets]
+  int* ion_start;  // [kCellBuckets + 1]
+  int* ion_fill;   // [kCellBuckets]
+  int* ion_list;   // [n_ions capacity] ion records in bucket order
+  int* scan_tmp;   // [kCellBuckets / 1024] block totals of the bucket scans
+};
+
 // Arguments of the ionization kernels of one cluster.
 struct IonArgs {
   ClusterDev c;
@@ -158,6 +179,9 @@ struct IonArgs {
   double* e_ion;
   float4* fix_src;
   int fix_nseg;       // source segments of the charge-change field (k_ion_fix)
+  // local moments from a cell list (cells.count non-null) instead of beside
+  // the field sum
+  CellBuf cells;
   // 1: minimum-image distances while the boundary is periodic (field and
   // local moments of the pass, charge-change correction)
   int min_image;
