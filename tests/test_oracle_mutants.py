@@ -279,9 +279,12 @@ def mutant_runs(request, tmp_path_factory):
               if getattr(it, "module", None) is not None and it.module.__file__ == __file__
               and hasattr(it, "callspec") and "name" in it.callspec.params]
 
+    # the directories are made here, one by one: mktemp is not thread-safe
+    dirs = {name: tmp_path_factory.mktemp(name) for name in wanted}
+
     def one(name):
         kind, fname, old, new, pins = ALL[name]
-        d = tmp_path_factory.mktemp(name)
+        d = dirs[name]
         try:
             if kind == "c":
                 return name, _run_mutant(d, fname, old, new, pins)
