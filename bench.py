@@ -39,10 +39,16 @@ RECORD_BYTES = 3 * 8 + 3 * 8 + 4 + 8 + 8 + 1   # x, u, z, mass, w, kind per reco
 FP32_INSTR_PER_PAIR = 12
 # DRAM bytes (read + write) per launch of the step kernel, from one 1-pass ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the named workload
-# at full size in the named kernel configuration; reported only when the timed
-# run uses that configuration.
-STEP_TRAFFIC_BYTES = {("xe3_200k", 200000, 128, 8, 512, True): 15.77e6}
+# at full size in the named kernel configuration (threads, r, tile, packed,
+# jsplit); reported only when the timed run uses that configuration.
+STEP_TRAFFIC_BYTES = {("xe3_200k", 200000, 128, 8, 512, True, 9): 15.77e6,
+                      ("xe3_200k", 200000, 128, 8, 256, True, -4): 19.49e6}
 L2_FLUSH_BYTES = 512 << 20
+# step kernel configuration of the ionizing 200k-atom contexts (threads, r,
+# tile, CTAs per SM, jsplit, packed, min_blocks): the fastest of the packed
+# configurations on that workload with tile 512 (the ionizing step skips dead
+# source tiles and takes the charge per pair on the ions' mixed tiles)
+IONIZING_TUNING = (128, 8, 512, 0, 0, 1, 0)
 WORKLOAD_TEXT = {
     "xe3_200k": "{name}: N={n} (Xe3+ ions + electrons, 10 eV), one cluster per GPU",
     "xe3_200k_shard": "{name}: N={n} (Xe3+ ions + electrons, 10 eV), one cluster split over "
@@ -398,8 +404,9 @@ def secondary_measurements(md, stream, flush, sms, gpu_id, tuning, steps=3, warm
                       both on the same seed;
       precision_1m -- 500k Ar+ + 500k e: the step time, and the FP32/Kahan
                       field against the FP64 GPU reference and the oracle.
-    The ionizing and 1M contexts run the step kernel configuration that the
-    headline's autotuner chose (`tuning`), each with its own source split."""
+    The 1M context runs the step kernel configuration and source split that
+    the headline's autotuner chose (`tuning`); the ionizing contexts run
+    IONIZING_TUNING with a segment count chosen for balance."""
     import torch
     out = {}
     cs = stream.cuda_stream
@@ -440,7 +447,7 @@ def secondary_measurements(md, stream, flush, sms, gpu_id, tuning, steps=3, warm
         ctx, ws, _, info = ionizing_context(md, n_atoms, rates, 0, cs)
         if rates == "mlp":
             trained = info.get("trained")
-        ctx.set_tuning(tuning[0], tuning[1], tuning[2], 0, 0, tuning[5], tuning[6])
+        ctx.set_tuning(*IONIZING_TUNING)
         with ctx:
             for _ in range(warmup):
                 ctx.step(1)
@@ -474,7 +481,7 @@ def secondary_measurements(md, stream, flush, sms, gpu_id, tuning, steps=3, warm
     w = synth.precision_1m(seed=0, a0=0.0)
     with md.Context([md.config_from_workload(w)], [md.HostParticles.from_cluster(w.cluster)],
                     stream=cs) as ctx:
-        ctx.set_tuning(tuning[0], tuning[1], tuning[2], 0, 0, tuning[5], tuning[6])
+        ctx.set_tuning(tuning[0], tuning[1], tuning[2], 0, tuning[4], tuning[5], tuning[6])
         ctx.step(1)
         sampler = ClockSampler(gpu_id)
         time.sleep(0.3)
@@ -936,7 +943,10 @@ def run_native(args):
             "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write outside the "
                   "timed events)",
             "tuning": {"threads": tuning[0], "r": tuning[1], "tile": tuning[2],
-                       "source_segments": tuning[4], "packed_f32x2": bool(tuning[5]),
+                       "source_split": (f"equal shares, {-tuning[4]} per resident CTA"
+                                        if tuning[4] < 0 else
+                                        f"{tuning[4]} segments per i-block"),
+                       "jsplit": tuning[4], "packed_f32x2": bool(tuning[5]),
                        "min_blocks": tuning[6]},
             "autotune_configs": [list(t) for t in md.tuning_list()],
             "autotune_ms_per_step": tune_ms,
@@ -956,7 +966,7 @@ def run_native(args):
             "measured_ffma_tflops": 2 * ffma_per_s / 1e12,
             "measured_packed_f32x2_fma_tflops": 2 * ffma2_per_s / 1e12,
             "traffic": STEP_TRAFFIC_BYTES.get((args.workload, n, tuning[0], tuning[1],
-                                                tuning[2], bool(tuning[5]))),
+                                                tuning[2], bool(tuning[5]), tuning[4])),
             "traffic_unit": "B per launch (dram read + write, ncu)",
         },
         "clocks": clocks,

@@ -158,9 +158,20 @@ typedef struct {
     int32_t r;          /* i-particles per thread (register blocking) */
     int32_t tile;       /* sources per shared-memory stage */
     int32_t ctas_per_sm;/* persistent CTAs per SM (0: as many as fit) */
-    int32_t jsplit;     /* source segments per i-block (0: chosen for load balance); the
-                           partial fields of the segments go to a library scratch buffer
-                           and the last segment to finish sums them and pushes */
+    int32_t jsplit;     /* how the sources of an i-block are split into pieces:
+                           1..64: that many equal segments per i-block;
+                           0: a segment count chosen for load balance;
+                           -k (1 <= k <= 8): equal shares, the sources of all i-blocks
+                           laid end to end in tiles and cut into k x the resident CTAs
+                           equal shares of one or more pieces each (contexts with
+                           ionizing clusters take 0 instead).
+                           The partial fields of the pieces go to a library scratch
+                           buffer and the last piece to finish adds them in source
+                           order and pushes.  With jsplit > 0 a cluster's results do
+                           not depend on the other clusters of the context; with 0 or
+                           equal shares they may.  md_get_tuning reports -k for equal shares,
+                           else the largest segment count of any cluster; md_autotune
+                           tries 0 for every configuration and -4 for the two fastest. */
     int32_t packed;     /* 1: pair arithmetic in packed f32x2 (two i-particles per
                            instruction, bit-identical results), 0: scalar FP32 */
     int32_t min_blocks; /* register budget: 64K / (threads x min_blocks); 0 = left to the
@@ -398,9 +409,10 @@ md_status md_get_step(md_ctx *ctx, int64_t *step);
  * md_set_tuning: uses the given configuration from now on.
  * md_get_tuning: the configuration in use.
  * md_autotune: times every configuration over `steps` steps on the
- * context's own state (restored afterwards) and keeps the fastest; the
- * per-configuration mean step times in ms go to times_ms (cap entries, may be
- * NULL). */
+ * context's own state (restored afterwards), with jsplit 0 and, for the two
+ * fastest, jsplit -4 (no ionizing cluster), and keeps the fastest; the
+ * per-configuration best mean step times in ms go to times_ms (cap entries,
+ * may be NULL; -1 for a configuration not timed). */
 int32_t md_tuning_list(md_tuning *list, int32_t cap);
 md_status md_set_tuning(md_ctx *ctx, const md_tuning *t);
 md_status md_get_tuning(md_ctx *ctx, md_tuning *t);

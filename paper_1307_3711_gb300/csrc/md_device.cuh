@@ -1133,6 +1133,37 @@ __device__ __forceinline__ void push_record(const StepArgs& a, const ClusterDev&
   }
 }
 
+// Sum of the n partials p[k stride] (C components each, k = 0 .. n - 1) of
+// one target, added in index order; the loads of eight partials are issued
+// before their adds, so the sum costs n / 8 round trips to L2, not n.
+template <int C>
+__device__ __forceinline__ void sum_partials(const double* p, long long stride, int n, double& x,
+                                             double& y, double& z) {
+  constexpr int kInFlight = 8;
+  x = 0.0;
+  y = 0.0;
+  z = 0.0;
+#pragma unroll 1
+  for (int k0 = 0; k0 < n; k0 += kInFlight) {
+    double v[kInFlight][C];
+#pragma unroll
+    for (int k = 0; k < kInFlight; ++k)
+      if (k0 + k < n) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) v[k][c] = __ldcg(p + (k0 + k) * stride + c);
+      }
+#pragma unroll
+    for (int k = 0; k < kInFlight; ++k)
+      if (k0 + k < n) {
+        x += v[k][0];
+        if constexpr (C > 1) {
+          y += v[k][1];
+          z += v[k][2];
+        }
+      }
+  }
+}
+
 // One full MD step for every work unit (cluster, i-block): field at x^n from
 // all sources of the cluster, laser at t_n, Boris kick, FP64 drift, boundary,
 // new j-stream entry.  Persistent: CTAs take units from an atomic ticket.
@@ -1170,175 +1201,180 @@ __global__ void __launch_bounds__(THREADS, MINB) k_step(const StepArgs a) {
 
   unsigned it = 0;
   for (;;) {
-    if (threadIdx.x == 0) {
-      const int u = static_cast<int>(atomicAdd(a.ticket, 1u));
-      s_unit = u;
-      if (u < a.n_units) {
+    if (threadIdx.x == 0) s_unit = static_cast<int>(atomicAdd(a.ticket, 1u));
+    __syncthreads();
+    const int share = s_unit;
+    __syncthreads();  // s_unit is rewritten by the next share's ticket
+    if (share >= a.n_shares) break;
+    const int u_end = a.share_first[share + 1];
+#pragma unroll 1
+    for (int u = a.share_first[share]; u < u_end; ++u) {
+      if (threadIdx.x == 0) {
         s_un = a.units[u];
         s_c = a.cl[s_un.cluster];
         laser_field(s_c, s_c.t0 + static_cast<double>(step) * s_c.dt, s_las);
       }
-    }
-    __syncthreads();
-    if (s_unit >= a.n_units) break;
-    if (any_live(a.tgt_live, s_c.off + static_cast<long long>(s_un.block) * (THREADS * R),
-                 (s_c.off + static_cast<long long>(s_un.block + 1) * (THREADS * R) <
-                          s_c.off + s_c.n_pad
-                      ? s_c.off + static_cast<long long>(s_un.block + 1) * (THREADS * R)
-                      : s_c.off + s_c.n_pad) - 1)) {
-      const float4* __restrict__ cur = (step & 1) ? a.posq1 : a.posq0;
-      const long long i0 = s_c.off + static_cast<long long>(s_un.block) * (THREADS * R);
-      const long long iend = s_c.off + s_c.n_pad;
-      const long long j0 = static_cast<long long>(s_un.seg) * s_c.seg_len;
-      const long long jrem = s_c.n_pad - j0;
-      const long long jn = jrem < s_c.seg_len ? jrem : s_c.seg_len;
-      float xi[R], yi[R], zi[R];
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const long long i = i0 + threadIdx.x + r * THREADS;
-        const float4 p = (i < iend) ? cur[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-        xi[r] = p.x;
-        yi[r] = p.y;
-        zi[r] = p.z;
-      }
-      bool ok;
-      Acc<R, POT> acc;
-      if constexpr (PACK) {
-        ok = sum_sources_packed<THREADS, R, TILE, STAGES, false>(
-            sm, dup, ks, it, cur + s_c.off + j0, jn, xi, yi, zi, s_c.eps2, a.err, &s_abort,
-            a.src_live, s_c.off + j0);
-      } else {
-        acc.zero();
-        if constexpr (MI) {
-          // minimum-image forces while this cluster's boundary is periodic at t_n
-          const double t_n = s_c.t0 + static_cast<double>(step) * s_c.dt;
-          const bool mi = a.min_image && a.min_image[s_un.cluster] &&
-                          (s_c.boundary == 1 || (s_c.boundary == 2 && t_n < s_c.t_switch));
-          if (mi) {
-            __shared__ float s_tb[6];  // bounds of this unit's targets
-            target_bounds<THREADS, R>(xi, yi, zi, s_tb);
-            const float L = static_cast<float>(s_c.box);
-            ok = sum_sources<THREADS, R, TILE, STAGES, POT, true>(
-                sm, it, cur + s_c.off + j0, jn, xi, yi, zi, s_c.eps2, acc, a.err, &s_abort,
-                a.src_live, s_c.off + j0, L, 1.0f / L, s_tb);
-          } else {
-            ok = sum_sources<THREADS, R, TILE, STAGES, POT>(
-                sm, it, cur + s_c.off + j0, jn, xi, yi, zi, s_c.eps2, acc, a.err, &s_abort,
-                a.src_live, s_c.off + j0);
-          }
+      __syncthreads();
+      if (any_live(a.tgt_live, s_c.off + static_cast<long long>(s_un.block) * (THREADS * R),
+                   (s_c.off + static_cast<long long>(s_un.block + 1) * (THREADS * R) <
+                            s_c.off + s_c.n_pad
+                        ? s_c.off + static_cast<long long>(s_un.block + 1) * (THREADS * R)
+                        : s_c.off + s_c.n_pad) - 1)) {
+        const float4* __restrict__ cur = (step & 1) ? a.posq1 : a.posq0;
+        const long long i0 = s_c.off + static_cast<long long>(s_un.block) * (THREADS * R);
+        const long long iend = s_c.off + s_c.n_pad;
+        long long j0, jn;
+        if (s_un.jn >= 0) {
+          j0 = s_un.j0;
+          jn = s_un.jn;
         } else {
-          ok = sum_sources<THREADS, R, TILE, STAGES, POT>(sm, it, cur + s_c.off + j0, jn, xi, yi,
-                                                          zi, s_c.eps2, acc, a.err, &s_abort,
-                                                          a.src_live, s_c.off + j0);
+          j0 = static_cast<long long>(s_un.seg) * s_c.seg_len;
+          const long long jrem = s_c.n_pad - j0;
+          jn = jrem < s_c.seg_len ? jrem : s_c.seg_len;
         }
-      }
-      if (!ok) return;
-
-      // field at target r: -(Kahan total s - c) of sum Q (x_j - x_i)/r^3
-      auto field_of = [&](int r, double& ex, double& ey, double& ez) {
-        if constexpr (PACK) {
-          ex = -(static_cast<double>(kahan_part(ks, 0, r)) - kahan_part(ks, 3, r));
-          ey = -(static_cast<double>(kahan_part(ks, 1, r)) - kahan_part(ks, 4, r));
-          ez = -(static_cast<double>(kahan_part(ks, 2, r)) - kahan_part(ks, 5, r));
-        } else {
-          ex = -(static_cast<double>(acc.sx[r]) - acc.cx[r]);
-          ey = -(static_cast<double>(acc.sy[r]) - acc.cy[r]);
-          ez = -(static_cast<double>(acc.sz[r]) - acc.cz[r]);
-        }
-      };
-
-      // the unit's ranges are re-read from shared memory after the loop
-      const float4* __restrict__ cur2 = (step & 1) ? a.posq1 : a.posq0;
-      float4* __restrict__ nxt = (step & 1) ? a.posq0 : a.posq1;
-      const long long e0 = s_c.off + static_cast<long long>(s_un.block) * (THREADS * R);
-      const long long eend = s_c.off + s_c.n_pad;
-      const double t_next = s_c.t0 + static_cast<double>(step + 1) * s_c.dt;
-      if (s_c.nseg == 1) {
-        // the packed path reads its sums from shared memory, so its epilogue
-        // stays rolled (one FP64 push at a time)
-        if constexpr (PACK) {
-#pragma unroll 1
-          for (int r = 0; r < R; ++r) {
-            const long long i = e0 + threadIdx.x + r * THREADS;
-            if (i >= eend) continue;
-            double ex, ey, ez;
-            field_of(r, ex, ey, ez);
-            push_record<DET>(a, s_c, i, ex, ey, ez, s_las, t_next, cur2, nxt);
-          }
-        } else {
-#pragma unroll
-          for (int r = 0; r < R; ++r) {
-            const long long i = e0 + threadIdx.x + r * THREADS;
-            if (i >= eend) continue;
-            double ex, ey, ez;
-            field_of(r, ex, ey, ez);
-            if constexpr (POT) {
-              // the potential without the record's own term
-              const double ph = (static_cast<double>(acc.sp[r]) - acc.cp[r]) -
-                                static_cast<double>(cur2[i].w * rsqrt_mufu(s_c.eps2));
-              push_record<DET, true>(a, s_c, i, ex, ey, ez, s_las, t_next, cur2, nxt, ph);
-            } else {
-              push_record<DET>(a, s_c, i, ex, ey, ez, s_las, t_next, cur2, nxt);
-            }
-          }
-        }
-      } else {
-        // this unit covers one segment of the sources: publish the partial
-        // field; the last of the nseg units of this i-block sums the partials
-        // in segment order (deterministic) and pushes
-        const int seg = s_un.seg;
+        float xi[R], yi[R], zi[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-          const long long i = e0 + threadIdx.x + r * THREADS;
-          if (i >= eend) continue;
-          double ex, ey, ez;
-          field_of(r, ex, ey, ez);
-          if (!MD_IN_RANGE(a.err, seg, 0, s_c.nseg) || !MD_IN_RANGE(a.err, i, 0, a.n_total))
-            continue;
-          double* p = a.part + 3 * (static_cast<long long>(seg) * a.n_total + i);
-          __stcg(p + 0, ex);
-          __stcg(p + 1, ey);
-          __stcg(p + 2, ez);
-          if constexpr (POT)
-            __stcg(a.part_phi + static_cast<long long>(seg) * a.n_total + i,
-                   static_cast<double>(acc.sp[r]) - acc.cp[r]);
+          const long long i = i0 + threadIdx.x + r * THREADS;
+          const float4 p = (i < iend) ? cur[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+          xi[r] = p.x;
+          yi[r] = p.y;
+          zi[r] = p.z;
         }
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) {
-          const unsigned prev = atomicAdd(a.iblk_cnt + s_un.ib, 1u);
-          s_last = (prev == static_cast<unsigned>(s_c.nseg - 1));
-          if (s_last) atomicExch(a.iblk_cnt + s_un.ib, 0u);
+        bool ok;
+        Acc<R, POT> acc;
+        if constexpr (PACK) {
+          ok = sum_sources_packed<THREADS, R, TILE, STAGES, false>(
+              sm, dup, ks, it, cur + s_c.off + j0, jn, xi, yi, zi, s_c.eps2, a.err, &s_abort,
+              a.src_live, s_c.off + j0);
+        } else {
+          acc.zero();
+          if constexpr (MI) {
+            // minimum-image forces while this cluster's boundary is periodic at t_n
+            const double t_n = s_c.t0 + static_cast<double>(step) * s_c.dt;
+            const bool mi = a.min_image && a.min_image[s_un.cluster] &&
+                            (s_c.boundary == 1 || (s_c.boundary == 2 && t_n < s_c.t_switch));
+            if (mi) {
+              __shared__ float s_tb[6];  // bounds of this unit's targets
+              target_bounds<THREADS, R>(xi, yi, zi, s_tb);
+              const float L = static_cast<float>(s_c.box);
+              ok = sum_sources<THREADS, R, TILE, STAGES, POT, true>(
+                  sm, it, cur + s_c.off + j0, jn, xi, yi, zi, s_c.eps2, acc, a.err, &s_abort,
+                  a.src_live, s_c.off + j0, L, 1.0f / L, s_tb);
+            } else {
+              ok = sum_sources<THREADS, R, TILE, STAGES, POT>(
+                  sm, it, cur + s_c.off + j0, jn, xi, yi, zi, s_c.eps2, acc, a.err, &s_abort,
+                  a.src_live, s_c.off + j0);
+            }
+          } else {
+            ok = sum_sources<THREADS, R, TILE, STAGES, POT>(sm, it, cur + s_c.off + j0, jn, xi, yi,
+                                                            zi, s_c.eps2, acc, a.err, &s_abort,
+                                                            a.src_live, s_c.off + j0);
+          }
         }
-        __syncthreads();
-        if (s_last) {
-          __threadfence();
-          const int nseg = s_c.nseg;
+        if (!ok) return;
+
+        // field at target r: -(Kahan total s - c) of sum Q (x_j - x_i)/r^3
+        auto field_of = [&](int r, double& ex, double& ey, double& ez) {
+          if constexpr (PACK) {
+            ex = -(static_cast<double>(kahan_part(ks, 0, r)) - kahan_part(ks, 3, r));
+            ey = -(static_cast<double>(kahan_part(ks, 1, r)) - kahan_part(ks, 4, r));
+            ez = -(static_cast<double>(kahan_part(ks, 2, r)) - kahan_part(ks, 5, r));
+          } else {
+            ex = -(static_cast<double>(acc.sx[r]) - acc.cx[r]);
+            ey = -(static_cast<double>(acc.sy[r]) - acc.cy[r]);
+            ez = -(static_cast<double>(acc.sz[r]) - acc.cz[r]);
+          }
+        };
+
+        // the unit's ranges are re-read from shared memory after the loop
+        const float4* __restrict__ cur2 = (step & 1) ? a.posq1 : a.posq0;
+        float4* __restrict__ nxt = (step & 1) ? a.posq0 : a.posq1;
+        const long long e0 = s_c.off + static_cast<long long>(s_un.block) * (THREADS * R);
+        const long long eend = s_c.off + s_c.n_pad;
+        const double t_next = s_c.t0 + static_cast<double>(step + 1) * s_c.dt;
+        const int nparts = s_un.jn >= 0 ? s_un.nparts : s_c.nseg;
+        if (nparts == 1) {
+          // the packed path reads its sums from shared memory, so its epilogue
+          // stays rolled (one FP64 push at a time)
+          if constexpr (PACK) {
 #pragma unroll 1
+            for (int r = 0; r < R; ++r) {
+              const long long i = e0 + threadIdx.x + r * THREADS;
+              if (i >= eend) continue;
+              double ex, ey, ez;
+              field_of(r, ex, ey, ez);
+              push_record<DET>(a, s_c, i, ex, ey, ez, s_las, t_next, cur2, nxt);
+            }
+          } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              const long long i = e0 + threadIdx.x + r * THREADS;
+              if (i >= eend) continue;
+              double ex, ey, ez;
+              field_of(r, ex, ey, ez);
+              if constexpr (POT) {
+                // the potential without the record's own term
+                const double ph = (static_cast<double>(acc.sp[r]) - acc.cp[r]) -
+                                  static_cast<double>(cur2[i].w * rsqrt_mufu(s_c.eps2));
+                push_record<DET, true>(a, s_c, i, ex, ey, ez, s_las, t_next, cur2, nxt, ph);
+              } else {
+                push_record<DET>(a, s_c, i, ex, ey, ez, s_las, t_next, cur2, nxt);
+              }
+            }
+          }
+        } else {
+          // this unit covers one piece of the sources: publish the partial
+          // field; the last of the nparts units of this i-block sums the
+          // partials in piece order (deterministic) and pushes
+          const int seg = s_un.seg;
+#pragma unroll
           for (int r = 0; r < R; ++r) {
             const long long i = e0 + threadIdx.x + r * THREADS;
             if (i >= eend) continue;
-            double ex = 0.0, ey = 0.0, ez = 0.0;
-            for (int sg = 0; sg < nseg; ++sg) {
-              const double* p = a.part + 3 * (static_cast<long long>(sg) * a.n_total + i);
-              ex += __ldcg(p + 0);
-              ey += __ldcg(p + 1);
-              ez += __ldcg(p + 2);
-            }
-            if constexpr (POT) {
-              double ph = 0.0;
-              for (int sg = 0; sg < nseg; ++sg)
-                ph += __ldcg(a.part_phi + static_cast<long long>(sg) * a.n_total + i);
-              ph -= static_cast<double>(cur2[i].w * rsqrt_mufu(s_c.eps2));
-              push_record<DET, true>(a, s_c, i, ex, ey, ez, s_las, t_next, cur2, nxt, ph);
-            } else {
-              push_record<DET>(a, s_c, i, ex, ey, ez, s_las, t_next, cur2, nxt);
+            double ex, ey, ez;
+            field_of(r, ex, ey, ez);
+            if (!MD_IN_RANGE(a.err, seg, 0, nparts) || !MD_IN_RANGE(a.err, i, 0, a.n_total))
+              continue;
+            double* p = a.part + 3 * (static_cast<long long>(seg) * a.n_total + i);
+            __stcg(p + 0, ex);
+            __stcg(p + 1, ey);
+            __stcg(p + 2, ez);
+            if constexpr (POT)
+              __stcg(a.part_phi + static_cast<long long>(seg) * a.n_total + i,
+                     static_cast<double>(acc.sp[r]) - acc.cp[r]);
+          }
+          __threadfence();
+          __syncthreads();
+          if (threadIdx.x == 0) {
+            const unsigned prev = atomicAdd(a.iblk_cnt + s_un.ib, 1u);
+            s_last = (prev == static_cast<unsigned>(nparts - 1));
+            if (s_last) atomicExch(a.iblk_cnt + s_un.ib, 0u);
+          }
+          __syncthreads();
+          if (s_last) {
+            __threadfence();
+            const int nseg = nparts;
+#pragma unroll 1
+            for (int r = 0; r < R; ++r) {
+              const long long i = e0 + threadIdx.x + r * THREADS;
+              if (i >= eend) continue;
+              double ex, ey, ez;
+              sum_partials<3>(a.part + 3 * i, 3 * a.n_total, nseg, ex, ey, ez);
+              if constexpr (POT) {
+                double ph, d1, d2;
+                sum_partials<1>(a.part_phi + i, a.n_total, nseg, ph, d1, d2);
+                ph -= static_cast<double>(cur2[i].w * rsqrt_mufu(s_c.eps2));
+                push_record<DET, true>(a, s_c, i, ex, ey, ez, s_las, t_next, cur2, nxt, ph);
+              } else {
+                push_record<DET>(a, s_c, i, ex, ey, ez, s_las, t_next, cur2, nxt);
+              }
             }
           }
         }
       }
+      __syncthreads();
     }
-    __syncthreads();
   }
 
   // last CTA out: reset the ticket, advance the step counter

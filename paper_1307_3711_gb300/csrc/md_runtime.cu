@@ -120,6 +120,8 @@ struct md_ctx {
   int nseg_used = 1;       // largest segment count of any cluster
   md::Unit* d_units = nullptr;
   int n_units = 0;
+  int* d_share_first = nullptr;  // first unit of every share, n_shares + 1
+  int n_shares = 0;
   int grid = 0;
   double* d_fpart = nullptr;       // partial fields [nseg][n_total][3]
   size_t part_cap = 0;             // doubles allocated
@@ -350,7 +352,8 @@ md::StepArgs step_args(md_ctx* c) {
   md::StepArgs a;
   a.cl = c->d_cl;
   a.units = c->d_units;
-  a.n_units = c->n_units;
+  a.share_first = c->d_share_first;
+  a.n_shares = c->n_shares;
   a.posq0 = c->d_posq[0];
   a.posq1 = c->d_posq[1];
   a.x = c->d_x[0];
@@ -419,6 +422,9 @@ md::ClusterDev slice_view(const md_ctx* c, int ci) {
   return v;
 }
 
+// Equal shares per resident CTA that md_autotune tries (jsplit = -kAutoShares).
+constexpr int kAutoShares = 4;
+
 // Source segments of md_get_fields / md_diagnostics at most.
 constexpr int kFieldMaxSeg = 8;
 
@@ -479,13 +485,82 @@ int choose_split(const md_ctx* c, long long per, int tile, long long slots) {
   return best;
 }
 
-// Work units (cluster, i-block, source segment) ordered by decreasing cost,
-// so the ticket hands the largest blocks out first.
+// Whether the step's source split must follow the live records, which only
+// the device knows after each ionization pass (R16).
+bool any_ionizing(const md_ctx* c) {
+  for (int ci = 0; ci < c->n_clusters; ++ci)
+    if (ci < static_cast<int>(c->ion.size()) && c->ion[ci].rate_model != 0) return true;
+  return false;
+}
+
+// Equal shares: the sources of every pushed i-block, laid end to end in
+// tiles, are cut into G shares of equal tile counts (G = the resident CTAs
+// times `per_slot`), so the ticket's last round leaves no CTA idle.  A share
+// is one or more pieces, each a tile range of one i-block's sources; the
+// pieces of an i-block are numbered in source order.  Appends the units in
+// share order and the first unit of every share (G + 1 entries).
+void equal_shares(md_ctx* c, long long per, int tile, long long G, std::vector<md::Unit>* units,
+                  std::vector<int>* first, int* max_parts) {
+  struct Blk {
+    int ci, b, ib;
+    long long tiles;
+  };
+  std::vector<Blk> blks;
+  long long T = 0;
+  int ib = 0;
+  for (int ci = 0; ci < c->n_clusters; ++ci) {
+    md::ClusterDev& cl = c->cl[ci];
+    cl.nseg = 1;
+    cl.seg_len = cl.n_pad;
+    c->ion_push[ci] = 0;
+    const long long nb = (cl.n_pad + per - 1) / per;
+    const long long tiles = std::max(1LL, (static_cast<long long>(cl.n_pad) + tile - 1) / tile);
+    for (long long b = 0; b < nb; ++b, ++ib) {
+      if (!block_in_slice(c, ci, b, per)) continue;
+      blks.push_back({ci, static_cast<int>(b), ib, tiles});
+      T += tiles;
+    }
+  }
+  G = std::max(1LL, std::min(G, T));
+  auto bound = [&](long long k) { return k * T / G; };  // first tile of share k
+  std::vector<int> share_of;
+  long long F = 0, k = 0;
+  *max_parts = 1;
+  for (const Blk& bk : blks) {
+    const md::ClusterDev& cl = c->cl[bk.ci];
+    const size_t u0 = units->size();
+    for (long long p = F; p < F + bk.tiles;) {
+      while (bound(k + 1) <= p) ++k;
+      const long long q = std::min(F + bk.tiles, bound(k + 1));
+      const long long j0 = (p - F) * tile;
+      const long long j1 = std::min<long long>((q - F) * tile, cl.n_pad);
+      md::Unit u{bk.ci, bk.b, static_cast<int>(units->size() - u0), bk.ib,
+                 static_cast<int>(j0), static_cast<int>(j1 - j0), 0, 0};
+      units->push_back(u);
+      share_of.push_back(static_cast<int>(k));
+      p = q;
+    }
+    const int np = static_cast<int>(units->size() - u0);
+    for (size_t i = u0; i < units->size(); ++i) (*units)[i].nparts = np;
+    *max_parts = std::max(*max_parts, np);
+    F += bk.tiles;
+  }
+  first->assign(static_cast<size_t>(G) + 1, 0);
+  for (int s : share_of) ++(*first)[static_cast<size_t>(s) + 1];
+  for (size_t i = 1; i < first->size(); ++i) (*first)[i] += (*first)[i - 1];
+}
+
+// Work units (cluster, i-block, source piece) and their shares.  jsplit < 0
+// without ionizing clusters: equal shares, -jsplit per resident CTA.
+// Otherwise every i-block's sources are split into segments (jsplit of them,
+// or for 0 (and jsplit < 0 with ionizing clusters) a count chosen for
+// balance) and the units, ordered by decreasing cost so the ticket hands the
+// largest out first, are one share each.
 md_status configure(md_ctx* c, int cfg, int ctas_per_sm, int jsplit) {
   int ncfg = 0;
   const md::KernelConfig* cfgs = md::step_configs(&ncfg);
   if (cfg < 0 || cfg >= ncfg) return fail(MD_ERR_ARG, "tuning index %d out of range", cfg);
-  if (jsplit < 0 || jsplit > 64) return fail(MD_ERR_ARG, "jsplit must be in [0, 64]");
+  if (jsplit < -8 || jsplit > 64) return fail(MD_ERR_ARG, "jsplit must be in [-8, 64]");
   const md::KernelConfig& k = cfgs[cfg];
   const long long per = static_cast<long long>(k.threads) * k.r;
   if (c->any_mi && !k.launch_step_mi)
@@ -495,42 +570,59 @@ md_status configure(md_ctx* c, int cfg, int ctas_per_sm, int jsplit) {
   if (bps < 1) return fail(MD_ERR_CUDA, "kernel configuration %d does not fit on an SM", cfg);
   const int cps = ctas_per_sm > 0 ? std::min(ctas_per_sm, bps) : bps;
   const long long slots = static_cast<long long>(cps) * c->sm_count;
-  const int S = jsplit > 0 ? jsplit : choose_split(c, per, k.tile, slots);
 
-  struct Work {
-    long long cost;
-    md::Unit u;
-  };
-  std::vector<Work> work;
+  std::vector<md::Unit> units;
+  std::vector<int> first;
   int ib = 0, max_seg = 1;
-  for (int ci = 0; ci < c->n_clusters; ++ci) {
-    md::ClusterDev& cl = c->cl[ci];
-    segments_for(cl, S, k.tile, &cl.nseg, &cl.seg_len);
-    max_seg = std::max(max_seg, cl.nseg);
-    const long long nb = (cl.n_pad + per - 1) / per;
-    // a cluster with a pass before every step: the i-blocks holding only ions
-    // are pushed with the pass's field (launch_ion_push), not summed again
-    const long long skip = ions_fused(c, ci) ? c->ion[ci].n_ions / per : 0;
-    c->ion_push[ci] = skip * per;
-    for (long long b = 0; b < nb; ++b, ++ib) {
-      if (b < skip || !block_in_slice(c, ci, b, per)) continue;
-      for (int sg = 0; sg < cl.nseg; ++sg) {
-        const long long len = std::min<long long>(cl.seg_len, cl.n_pad - static_cast<long long>(sg) * cl.seg_len);
-        work.push_back({per * len, {ci, static_cast<int>(b), sg, ib}});
+  const bool shares = jsplit < 0 && !any_ionizing(c);
+  if (shares) {
+    equal_shares(c, per, k.tile, slots * -jsplit, &units, &first, &max_seg);
+    for (int ci = 0; ci < c->n_clusters; ++ci)
+      ib += static_cast<int>((c->cl[ci].n_pad + per - 1) / per);
+  } else {
+    const int S = jsplit > 0 ? jsplit : choose_split(c, per, k.tile, slots);
+    jsplit = std::max(jsplit, 0);
+    struct Work {
+      long long cost;
+      md::Unit u;
+    };
+    std::vector<Work> work;
+    for (int ci = 0; ci < c->n_clusters; ++ci) {
+      md::ClusterDev& cl = c->cl[ci];
+      segments_for(cl, S, k.tile, &cl.nseg, &cl.seg_len);
+      max_seg = std::max(max_seg, cl.nseg);
+      const long long nb = (cl.n_pad + per - 1) / per;
+      // a cluster with a pass before every step: the i-blocks holding only
+      // ions are pushed with the pass's field (launch_ion_push), not summed
+      // again
+      const long long skip = ions_fused(c, ci) ? c->ion[ci].n_ions / per : 0;
+      c->ion_push[ci] = skip * per;
+      for (long long b = 0; b < nb; ++b, ++ib) {
+        if (b < skip || !block_in_slice(c, ci, b, per)) continue;
+        for (int sg = 0; sg < cl.nseg; ++sg) {
+          const long long len = std::min<long long>(cl.seg_len, cl.n_pad - static_cast<long long>(sg) * cl.seg_len);
+          work.push_back({per * len, {ci, static_cast<int>(b), sg, ib, 0, -1, cl.nseg, 0}});
+        }
       }
     }
+    std::stable_sort(work.begin(), work.end(),
+                     [](const Work& a, const Work& b) { return a.cost > b.cost; });
+    units.reserve(work.size());
+    for (auto& w : work) units.push_back(w.u);
+    first.resize(units.size() + 1);
+    for (size_t i = 0; i < first.size(); ++i) first[i] = static_cast<int>(i);
   }
-  std::stable_sort(work.begin(), work.end(),
-                   [](const Work& a, const Work& b) { return a.cost > b.cost; });
-  std::vector<md::Unit> units;
-  units.reserve(work.size());
-  for (auto& w : work) units.push_back(w.u);
 
   MD_CUDA(cudaStreamSynchronize(c->stream));
   if (c->d_units) cudaFree(c->d_units);
   c->d_units = nullptr;
+  if (c->d_share_first) cudaFree(c->d_share_first);
+  c->d_share_first = nullptr;
   MD_CUDA(dev_alloc(&c->d_units, units.size()));
+  MD_CUDA(dev_alloc(&c->d_share_first, first.size()));
   MD_CUDA(cudaMemcpyAsync(c->d_units, units.data(), units.size() * sizeof(md::Unit),
+                          cudaMemcpyHostToDevice, c->stream));
+  MD_CUDA(cudaMemcpyAsync(c->d_share_first, first.data(), first.size() * sizeof(int),
                           cudaMemcpyHostToDevice, c->stream));
   MD_CUDA(cudaMemcpyAsync(c->d_cl, c->cl.data(), sizeof(md::ClusterDev) * c->n_clusters,
                           cudaMemcpyHostToDevice, c->stream));
@@ -554,7 +646,8 @@ md_status configure(md_ctx* c, int cfg, int ctas_per_sm, int jsplit) {
   }
   MD_CUDA(cudaStreamSynchronize(c->stream));
   c->n_units = static_cast<int>(units.size());
-  c->grid = static_cast<int>(std::max<long long>(1, std::min<long long>(c->n_units, slots)));
+  c->n_shares = static_cast<int>(first.size() - 1);
+  c->grid = static_cast<int>(std::max<long long>(1, std::min<long long>(c->n_shares, slots)));
   c->cfg = cfg;
   c->ctas_per_sm = ctas_per_sm;
   c->jsplit = jsplit;
@@ -782,6 +875,7 @@ void free_ctx(md_ctx* c) {
   cudaFree(c->d_part);
   cudaFree(c->d_diag);
   cudaFree(c->d_units);
+  cudaFree(c->d_share_first);
   cudaFree(c->d_diag_rec);
   cudaFree(c->d_part_phi);
   cudaFree(c->d_min_image);
@@ -1852,7 +1946,7 @@ md_status md_get_tuning(md_ctx* c, md_tuning* t) {
   t->r = cfgs[c->cfg].r;
   t->tile = cfgs[c->cfg].tile;
   t->ctas_per_sm = c->ctas_per_sm;
-  t->jsplit = c->nseg_used;
+  t->jsplit = c->jsplit < 0 ? c->jsplit : c->nseg_used;
   t->packed = cfgs[c->cfg].packed;
   t->min_blocks = cfgs[c->cfg].min_blocks;
   return MD_OK;
@@ -1914,17 +2008,16 @@ md_status md_autotune(md_ctx* c, int32_t steps, double* times_ms, int32_t cap) {
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   double best = 1e300;
-  int best_cfg = cfg0;
+  int best_cfg = cfg0, best_js = 0;
   md_status st = MD_OK;
-  for (int i = 0; i < n && st == MD_OK; ++i) {
-    if (times_ms && i < cap) times_ms[i] = -1.0;
-    int bps = 0;
-    if (c->any_mi && !cfgs[i].launch_step_mi) continue;  // no minimum-image kernel
-    if (blocks_per_sm_of(c, cfgs[i], &bps) != cudaSuccess || bps < 1) continue;  // does not fit
-    st = configure(c, i, 0, 0);
-    if (st != MD_OK) break;
+  std::vector<double> by_cfg(static_cast<size_t>(n), -1.0);
+  // one trial: configuration i with source split js, timed over `steps`
+  // steps from the saved state (restored afterwards)
+  auto trial = [&](int i, int js) {
+    st = configure(c, i, 0, js);
+    if (st != MD_OK) return;
     st = launch_steps_direct(c, 1);  // warm-up
-    if (st != MD_OK) break;
+    if (st != MD_OK) return;
     cudaEventRecord(e0, s);
     st = launch_steps_direct(c, steps);
     cudaEventRecord(e1, s);
@@ -1932,16 +2025,36 @@ md_status md_autotune(md_ctx* c, int32_t steps, double* times_ms, int32_t cap) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     const double per = ms / steps;
-    if (times_ms && i < cap) times_ms[i] = per;
+    if (by_cfg[i] < 0.0 || per < by_cfg[i]) by_cfg[i] = per;
     if (per < best) {
       best = per;
       best_cfg = i;
+      best_js = js;
     }
     if (st == MD_OK) st = check_device_error(c);
     for (auto& b : bufs) cudaMemcpyAsync(b.dev, b.copy, b.bytes, cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(c->d_step, &step0, sizeof(step0), cudaMemcpyHostToDevice, s);
     cudaStreamSynchronize(s);
+  };
+  // every configuration with its segments chosen for balance, then the two
+  // fastest with equal shares (kAutoShares per resident CTA), which fill the
+  // last round of a large step but add pieces that cross i-blocks
+  for (int i = 0; i < n && st == MD_OK; ++i) {
+    int bps = 0;
+    if (c->any_mi && !cfgs[i].launch_step_mi) continue;  // no minimum-image kernel
+    if (blocks_per_sm_of(c, cfgs[i], &bps) != cudaSuccess || bps < 1) continue;  // does not fit
+    trial(i, 0);
   }
+  if (st == MD_OK && !any_ionizing(c)) {
+    std::vector<int> order;
+    for (int i = 0; i < n; ++i)
+      if (by_cfg[i] >= 0.0) order.push_back(i);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return by_cfg[x] < by_cfg[y]; });
+    for (size_t k = 0; k < order.size() && k < 2 && st == MD_OK; ++k) trial(order[k], -kAutoShares);
+  }
+  if (times_ms)
+    for (int i = 0; i < n && i < cap; ++i) times_ms[i] = by_cfg[i];
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   release();
@@ -1949,7 +2062,7 @@ md_status md_autotune(md_ctx* c, int32_t steps, double* times_ms, int32_t cap) {
     configure(c, cfg0, cps0, js0);
     return st;
   }
-  return configure(c, best_cfg, 0, 0);
+  return configure(c, best_cfg, 0, best_js);
 }
 
 md_status md_coulomb_field_fp64_device(const double* xs, const double* qs, int64_t ns,

@@ -61,17 +61,28 @@ struct IonDev {
   double dom[6];      // surrogate domain: |E| min/max, n_e min/max, T_e min/max
 };
 
+// One unit of the step kernel: the field at one i-block of targets from one
+// piece of its cluster's sources.  The pieces of an i-block publish partial
+// fields that the last of them adds up in piece order.
 struct Unit {
   int cluster;
-  int block;  // i-block within the cluster
-  int seg;    // source segment
-  int ib;     // i-block index over all clusters (completion counter)
+  int block;   // i-block within the cluster
+  int seg;     // piece of the i-block's sources
+  int ib;      // i-block index over all clusters (completion counter)
+  int j0;      // first source record of the piece, and
+  int jn;      // its length; jn < 0: piece seg of the cluster's nseg segments
+               // of seg_len records (a split the device may reset, R16)
+  int nparts;  // pieces of this i-block (jn >= 0)
+  int pad_;
 };
 
 struct StepArgs {
   const ClusterDev* cl;
   const Unit* units;
-  int n_units;
+  // shares of the work handed out by the ticket: share k runs the units
+  // [share_first[k], share_first[k + 1]) in order
+  const int* share_first;
+  int n_shares;
   float4* posq0;
   float4* posq1;
   double* x;

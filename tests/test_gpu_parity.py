@@ -449,16 +449,21 @@ def test_graph_replay_equals_direct_launches_and_tunings_agree(md):
             assert np.abs(g.x - first.x).max() < 1e-6 * r0
 
 
-def test_split_sources_parity_and_determinism(md):
-    """Splitting the sources into segments (partial fields in scratch, summed
-    by the last segment's CTA) matches the oracle after a few steps and is
-    bitwise reproducible."""
+@pytest.mark.parametrize("jsplit", [5, 0, -4])
+def test_split_sources_parity_and_determinism(md, jsplit):
+    """Splitting the sources into pieces (partial fields in scratch, summed
+    by the last piece's CTA) matches the oracle after a few steps and is
+    bitwise reproducible: 5 equal segments per i-block, a segment count chosen
+    for balance, or equal shares of all tiles (four per resident CTA), which
+    at 20k records cut every i-block into several pieces, some of them
+    sharing a CTA's share with a piece of the next i-block."""
     w = synth.xe3_cluster(20000, seed=7)
     outs = []
     for _ in range(2):
         with ctx_for(md, w) as c:
-            c.set_tuning(256, 4, 256, 0, 5, 1)
-            assert c.tuning()[4] == 5
+            c.set_tuning(256, 4, 256, 0, jsplit, 1)
+            t = c.tuning()[4]
+            assert t == jsplit if jsplit != 0 else t >= 1
             c.step(6)
             outs.append(c.get_particles(0))
     assert np.array_equal(outs[0].x, outs[1].x) and np.array_equal(outs[0].u, outs[1].u)
@@ -886,8 +891,10 @@ def test_step_parity_batched_scan_sampled(md):
 def test_heterogeneous_context_equals_single_runs_bitwise(md):
     """One context with an ionizing argon cluster and a plain cluster with
     detectors (so the step kernel with the detector epilogue runs for both):
-    every record, charge state and detector count equals the single-cluster
-    runs of the same clusters."""
+    with one source segment per i-block, every record, charge state and
+    detector count equals the single-cluster runs of the same clusters.
+    (Equal shares cut the sources by the whole context's work, so there a
+    cluster's bits depend on the others.)"""
     AR = synth.ARGON
     n = 1200
     ca = synth.make_cluster(2, n, 0, synth.nm_to_len(2.5), 0, AR["mass"],
@@ -908,7 +915,7 @@ def test_heterogeneous_context_equals_single_runs_bitwise(md):
 
     def run(cfgs, parts, det_on):
         with md.Context(cfgs, parts) as ctx:
-            ctx.set_tuning(128, 4, 512)
+            ctx.set_tuning(128, 4, 512, 0, 1)
             if det_on is not None:
                 ctx.set_detectors(det_on, 1.1 * r0, e_max_ev=500.0, n_bins=32)
             ctx.step(40)
