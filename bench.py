@@ -45,10 +45,10 @@ STEP_TRAFFIC_BYTES = {("xe3_200k", 200000, 128, 8, 512, True, 9): 15.77e6,
                       ("xe3_200k", 200000, 128, 8, 256, True, -4): 19.49e6}
 L2_FLUSH_BYTES = 512 << 20
 # step kernel configuration of the ionizing 200k-atom contexts (threads, r,
-# tile, CTAs per SM, jsplit, packed, min_blocks): the fastest of the packed
-# configurations on that workload with tile 512 (the ionizing step skips dead
-# source tiles and takes the charge per pair on the ions' mixed tiles)
-IONIZING_TUNING = (128, 8, 512, 0, 0, 1, 0)
+# tile, CTAs per SM, jsplit, packed, min_blocks): the fastest of four packed
+# configurations timed on that workload (193.4 ms per step against 205.9 to
+# 207.5 ms for 128 x 8 targets with 256- or 512-source tiles)
+IONIZING_TUNING = (256, 4, 512, 0, 0, 1, 0)
 WORKLOAD_TEXT = {
     "xe3_200k": "{name}: N={n} (Xe3+ ions + electrons, 10 eV), one cluster per GPU",
     "xe3_200k_shard": "{name}: N={n} (Xe3+ ions + electrons, 10 eV), one cluster split over "

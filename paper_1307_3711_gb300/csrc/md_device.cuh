@@ -1134,12 +1134,11 @@ __device__ __forceinline__ void push_record(const StepArgs& a, const ClusterDev&
 }
 
 // Sum of the n partials p[k stride] (C components each, k = 0 .. n - 1) of
-// one target, added in index order; the loads of eight partials are issued
-// before their adds, so the sum costs n / 8 round trips to L2, not n.
-template <int C>
+// one target, added in index order; the loads of kInFlight partials are
+// issued before their adds, so the sum costs n / kInFlight round trips to L2.
+template <int C, int kInFlight>
 __device__ __forceinline__ void sum_partials(const double* p, long long stride, int n, double& x,
                                              double& y, double& z) {
-  constexpr int kInFlight = 8;
   x = 0.0;
   y = 0.0;
   z = 0.0;
@@ -1359,11 +1358,14 @@ __global__ void __launch_bounds__(THREADS, MINB) k_step(const StepArgs a) {
             for (int r = 0; r < R; ++r) {
               const long long i = e0 + threadIdx.x + r * THREADS;
               if (i >= eend) continue;
+              // eight partials in flight on the packed path (measured 2-3 %
+              // faster at 100k-400k records with 4 equal shares per CTA, the
+              // ptxas register budget rising with it), one on the scalar path
               double ex, ey, ez;
-              sum_partials<3>(a.part + 3 * i, 3 * a.n_total, nseg, ex, ey, ez);
+              sum_partials<3, PACK ? 8 : 1>(a.part + 3 * i, 3 * a.n_total, nseg, ex, ey, ez);
               if constexpr (POT) {
                 double ph, d1, d2;
-                sum_partials<1>(a.part_phi + i, a.n_total, nseg, ph, d1, d2);
+                sum_partials<1, 1>(a.part_phi + i, a.n_total, nseg, ph, d1, d2);
                 ph -= static_cast<double>(cur2[i].w * rsqrt_mufu(s_c.eps2));
                 push_record<DET, true>(a, s_c, i, ex, ey, ez, s_las, t_next, cur2, nxt, ph);
               } else {

@@ -257,6 +257,8 @@ const KernelConfig kConfigs[] = {
     MD_STEP_CONFIG(128, 4, 256, 1, true, 0), MD_STEP_CONFIG(256, 4, 256, 1, true, 0),
     MD_STEP_CONFIG(128, 8, 256, 1, true, 0), MD_STEP_CONFIG(128, 4, 512, 1, true, 0),
     MD_STEP_CONFIG(256, 4, 512, 1, true, 0), MD_STEP_CONFIG(128, 8, 512, 1, true, 0),
+    // the same with the registers capped for 3 CTAs per SM
+    MD_STEP_CONFIG(128, 8, 512, 1, true, 3),
 };
 
 constexpr int kFieldThreads = 128;
