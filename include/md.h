@@ -418,6 +418,27 @@ md_status md_set_tuning(md_ctx *ctx, const md_tuning *t);
 md_status md_get_tuning(md_ctx *ctx, md_tuning *t);
 md_status md_autotune(md_ctx *ctx, int32_t steps, double *times_ms, int32_t cap);
 
+/* md_plan_shares: the work units that equal shares (jsplit < 0) give the step
+ * kernel, for clusters of n_pad[c] records (records with their zero-charge
+ * padding, c < n_clusters) pushed in i-blocks of `per` targets (threads x r
+ * of a configuration) with `tile`-record source tiles, when `shares` shares
+ * are handed out (k x the resident CTAs).  The source tiles of every i-block,
+ * laid end to end in cluster and i-block order (T tiles), are cut into
+ * S = min(shares, T) shares of floor or ceil of T / S tiles; a share is one
+ * or more pieces, a piece one i-block's tile range.  Host only: no device is
+ * touched and the library's state is not changed.
+ * units (may be NULL): caller-owned int32[6 x cap], per unit in share order
+ * (cluster, i-block, piece of the i-block numbered in source order, pieces of
+ * the i-block, first source record, source records); first (may be NULL):
+ * caller-owned int32[shares + 1], the first unit of share s at first[s] and
+ * the unit count at first[S].  *n_units and *n_shares receive the counts;
+ * with units and first NULL the call only sizes them.  Errors: MD_ERR_ARG
+ * (NULL n_pad/n_units/n_shares, n_clusters, per, tile or shares < 1, an
+ * n_pad < 1, cap below the unit count). */
+md_status md_plan_shares(const int32_t *n_pad, int32_t n_clusters, int32_t per, int32_t tile,
+                         int64_t shares, int32_t *units, int64_t cap, int32_t *first,
+                         int64_t *n_units, int64_t *n_shares);
+
 /* ---- stateless field evaluation on caller device buffers -----------------
  * md_coulomb_field_device: field (and potential) at nt targets from ns
  * sources, the FP32/Kahan direct sum of Sec. II on device memory the caller

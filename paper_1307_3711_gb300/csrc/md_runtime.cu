@@ -493,47 +493,36 @@ bool any_ionizing(const md_ctx* c) {
   return false;
 }
 
-// Equal shares: the sources of every pushed i-block, laid end to end in
-// tiles, are cut into G shares of equal tile counts (G = the resident CTAs
-// times `per_slot`), so the ticket's last round leaves no CTA idle.  A share
-// is one or more pieces, each a tile range of one i-block's sources; the
-// pieces of an i-block are numbered in source order.  Appends the units in
-// share order and the first unit of every share (G + 1 entries).
-void equal_shares(md_ctx* c, long long per, int tile, long long G, std::vector<md::Unit>* units,
-                  std::vector<int>* first, int* max_parts) {
-  struct Blk {
-    int ci, b, ib;
-    long long tiles;
-  };
-  std::vector<Blk> blks;
+// One pushed i-block for the share planner: its cluster, index in the
+// cluster, index over all clusters, source tiles and the cluster's records.
+struct BlockSpan {
+  int ci, b, ib;
+  long long tiles;
+  int n_pad;
+};
+
+// Equal shares: the source tiles of the i-blocks `blks`, laid end to end (T
+// tiles in all), are cut into G' = min(G, T) shares of floor or ceil of T / G'
+// tiles, so the ticket's last round leaves no CTA idle.  A share is one or
+// more pieces, each a tile range of one i-block's sources; the pieces of an
+// i-block are numbered in source order.  Appends the units in share order and
+// sets the first unit of every share (G' + 1 entries); returns G'.
+long long plan_shares(const std::vector<BlockSpan>& blks, int tile, long long G,
+                      std::vector<md::Unit>* units, std::vector<int>* first, int* max_parts) {
   long long T = 0;
-  int ib = 0;
-  for (int ci = 0; ci < c->n_clusters; ++ci) {
-    md::ClusterDev& cl = c->cl[ci];
-    cl.nseg = 1;
-    cl.seg_len = cl.n_pad;
-    c->ion_push[ci] = 0;
-    const long long nb = (cl.n_pad + per - 1) / per;
-    const long long tiles = std::max(1LL, (static_cast<long long>(cl.n_pad) + tile - 1) / tile);
-    for (long long b = 0; b < nb; ++b, ++ib) {
-      if (!block_in_slice(c, ci, b, per)) continue;
-      blks.push_back({ci, static_cast<int>(b), ib, tiles});
-      T += tiles;
-    }
-  }
+  for (const BlockSpan& bk : blks) T += bk.tiles;
   G = std::max(1LL, std::min(G, T));
   auto bound = [&](long long k) { return k * T / G; };  // first tile of share k
   std::vector<int> share_of;
   long long F = 0, k = 0;
   *max_parts = 1;
-  for (const Blk& bk : blks) {
-    const md::ClusterDev& cl = c->cl[bk.ci];
+  for (const BlockSpan& bk : blks) {
     const size_t u0 = units->size();
     for (long long p = F; p < F + bk.tiles;) {
       while (bound(k + 1) <= p) ++k;
       const long long q = std::min(F + bk.tiles, bound(k + 1));
       const long long j0 = (p - F) * tile;
-      const long long j1 = std::min<long long>((q - F) * tile, cl.n_pad);
+      const long long j1 = std::min<long long>((q - F) * tile, bk.n_pad);
       md::Unit u{bk.ci, bk.b, static_cast<int>(units->size() - u0), bk.ib,
                  static_cast<int>(j0), static_cast<int>(j1 - j0), 0, 0};
       units->push_back(u);
@@ -546,8 +535,28 @@ void equal_shares(md_ctx* c, long long per, int tile, long long G, std::vector<m
     F += bk.tiles;
   }
   first->assign(static_cast<size_t>(G) + 1, 0);
-  for (int s : share_of) ++(*first)[static_cast<size_t>(s) + 1];
+  for (int sh : share_of) ++(*first)[static_cast<size_t>(sh) + 1];
   for (size_t i = 1; i < first->size(); ++i) (*first)[i] += (*first)[i - 1];
+  return G;
+}
+
+// Equal shares of a context's pushed i-blocks (those of its target slices)
+// with G shares; the clusters' descriptors get one segment of all records.
+void equal_shares(md_ctx* c, long long per, int tile, long long G, std::vector<md::Unit>* units,
+                  std::vector<int>* first, int* max_parts) {
+  std::vector<BlockSpan> blks;
+  int ib = 0;
+  for (int ci = 0; ci < c->n_clusters; ++ci) {
+    md::ClusterDev& cl = c->cl[ci];
+    cl.nseg = 1;
+    cl.seg_len = cl.n_pad;
+    c->ion_push[ci] = 0;
+    const long long nb = (cl.n_pad + per - 1) / per;
+    const long long tiles = std::max(1LL, (static_cast<long long>(cl.n_pad) + tile - 1) / tile);
+    for (long long b = 0; b < nb; ++b, ++ib)
+      if (block_in_slice(c, ci, b, per)) blks.push_back({ci, static_cast<int>(b), ib, tiles, cl.n_pad});
+  }
+  plan_shares(blks, tile, G, units, first, max_parts);
 }
 
 // Work units (cluster, i-block, source piece) and their shares.  jsplit < 0
@@ -1949,6 +1958,44 @@ md_status md_get_tuning(md_ctx* c, md_tuning* t) {
   t->jsplit = c->jsplit < 0 ? c->jsplit : c->nseg_used;
   t->packed = cfgs[c->cfg].packed;
   t->min_blocks = cfgs[c->cfg].min_blocks;
+  return MD_OK;
+}
+
+md_status md_plan_shares(const int32_t* n_pad, int32_t n_clusters, int32_t per, int32_t tile,
+                         int64_t shares, int32_t* units, int64_t cap, int32_t* first,
+                         int64_t* n_units, int64_t* n_shares) {
+  if (!n_pad || !n_units || !n_shares) return fail(MD_ERR_ARG, "NULL argument");
+  if (n_clusters < 1 || per < 1 || tile < 1 || shares < 1 || cap < 0)
+    return fail(MD_ERR_ARG, "need n_clusters, per, tile, shares >= 1 and cap >= 0");
+  std::vector<BlockSpan> blks;
+  int ib = 0;
+  for (int ci = 0; ci < n_clusters; ++ci) {
+    if (n_pad[ci] < 1) return fail(MD_ERR_ARG, "cluster %d: n_pad < 1", ci);
+    const long long nb = (static_cast<long long>(n_pad[ci]) + per - 1) / per;
+    const long long tiles = (static_cast<long long>(n_pad[ci]) + tile - 1) / tile;
+    for (long long b = 0; b < nb; ++b, ++ib) blks.push_back({ci, static_cast<int>(b), ib, tiles, n_pad[ci]});
+  }
+  std::vector<md::Unit> us;
+  std::vector<int> fs;
+  int max_parts = 1;
+  const long long G = plan_shares(blks, tile, shares, &us, &fs, &max_parts);
+  *n_units = static_cast<int64_t>(us.size());
+  *n_shares = G;
+  if (!units && !first) return MD_OK;  // a query of the sizes
+  if (cap < static_cast<int64_t>(us.size()))
+    return fail(MD_ERR_ARG, "cap %lld below the %zu units", static_cast<long long>(cap), us.size());
+  if (units)
+    for (size_t i = 0; i < us.size(); ++i) {
+      int32_t* o = units + 6 * i;
+      o[0] = us[i].cluster;
+      o[1] = us[i].block;
+      o[2] = us[i].seg;
+      o[3] = us[i].nparts;
+      o[4] = us[i].j0;
+      o[5] = us[i].jn;
+    }
+  if (first)
+    for (size_t i = 0; i < fs.size(); ++i) first[i] = fs[i];
   return MD_OK;
 }
 

@@ -141,6 +141,10 @@ _SIGS = {
                                            C.c_double, _p, _p, _p]),
     "md_get_iedf": (_st, [_ctx_p, C.c_int32, _p, _p]),
     "md_tuning_list": (C.c_int32, [C.POINTER(Tuning), C.c_int32]),
+    "md_plan_shares": (C.c_int, [C.POINTER(C.c_int32), C.c_int32, C.c_int32, C.c_int32,
+                                 C.c_int64, C.POINTER(C.c_int32), C.c_int64,
+                                 C.POINTER(C.c_int32), C.POINTER(C.c_int64),
+                                 C.POINTER(C.c_int64)]),
     "md_set_tuning": (_st, [_ctx_p, C.POINTER(Tuning)]),
     "md_get_tuning": (_st, [_ctx_p, C.POINTER(Tuning)]),
     "md_autotune": (_st, [_ctx_p, C.c_int32, _p, C.c_int32]),
@@ -215,6 +219,24 @@ def tuning_list():
     arr = (Tuning * n)()
     _lib.md_tuning_list(arr, n)
     return [t.as_tuple() for t in arr]
+
+
+def plan_shares(n_pad, per, tile, shares):
+    """md_plan_shares (host only): the step kernel's units under equal shares
+    for clusters of n_pad records each.  Returns (units [n, 6] int32: cluster,
+    i-block, piece, pieces of the i-block, first source, sources; first
+    [S + 1] int32: each share's first unit)."""
+    n_pad = np.ascontiguousarray(n_pad, dtype=np.int32).ravel()
+    nu, ns = C.c_int64(0), C.c_int64(0)
+    ip = C.POINTER(C.c_int32)
+    _check(_lib.md_plan_shares(n_pad.ctypes.data_as(ip), len(n_pad), per, tile, shares, None, 0,
+                               None, C.byref(nu), C.byref(ns)))
+    units = np.zeros((nu.value, 6), np.int32)
+    first = np.zeros(shares + 1, np.int32)
+    _check(_lib.md_plan_shares(n_pad.ctypes.data_as(ip), len(n_pad), per, tile, shares,
+                               units.ctypes.data_as(ip), nu.value, first.ctypes.data_as(ip),
+                               C.byref(nu), C.byref(ns)))
+    return units, first[: ns.value + 1]
 
 
 class HostParticles:
