@@ -471,11 +471,19 @@ __device__ __forceinline__ bool cell_coords(float x, float y, float z, float inv
   return true;
 }
 
+// The three coordinates (mod 2^21) packed into one 63-bit key, hashed by
+// Knuth's multiplicative method: the top bits of the key times 2^64 / phi.
+// (An XOR of the coordinates times three odd constants, the first version,
+// put the mirror cells (0, y, z) and (0, -y, -z) of a cluster centred on the
+// origin into one bucket whenever y and z have the same power of 2.)
 __device__ __forceinline__ int cell_bucket(int x, int y, int z) {
-  const unsigned h = (static_cast<unsigned>(x) * 73856093u) ^
-                     (static_cast<unsigned>(y) * 19349663u) ^
-                     (static_cast<unsigned>(z) * 83492791u);
-  return static_cast<int>(h & static_cast<unsigned>(kCellBuckets - 1));
+  constexpr unsigned long long kMask = (1ull << 21) - 1;
+  const unsigned long long key = (static_cast<unsigned long long>(x) & kMask) |
+                                 ((static_cast<unsigned long long>(y) & kMask) << 21) |
+                                 ((static_cast<unsigned long long>(z) & kMask) << 42);
+  constexpr int kBits = 18;
+  static_assert(kCellBuckets == 1 << kBits, "bucket count");
+  return static_cast<int>((key * 0x9E3779B97F4A7C15ull) >> (64 - kBits));
 }
 
 __device__ __forceinline__ int bucket_of(float x, float y, float z, float inv_h) {
@@ -610,86 +618,236 @@ cudaError_t launch_cell_scan(const IonArgs& a, const int* count, int* start, cud
 // Local moments of every ion from the electrons of its 27 cells (R14): weight
 // W, and about u_ref = the ion's own velocity the sums S = sum w du and
 // Q = sum w |du|^2, in fixed point; written as segment 0 of the scratch.
-__global__ void __launch_bounds__(128) k_ion_moments(const IonArgs a) {
-  const long long step = __ldcg(a.step);
-  if (!pass_active(a, step)) return;
-  const long long k_ion = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (k_ion >= a.ion.n_ions) return;
-  const CellBuf cb = a.cells;
-  // ions in cell order: the threads of a warp mostly share their 27 cells
-  const long long t = cb.ion_list[k_ion];
-  if (!MD_IN_RANGE(a.err, t, 0, a.ion.n_ions)) return;
-  const float4* __restrict__ cur = (step & 1) ? a.posq1 : a.posq0;
-  const float4 pi = cur[a.c.off + t];
-  const float4 ui = a.vel[a.c.off + t];
-  const float eps2 = a.c.eps2;
-  const float rloc2e = static_cast<float>(a.ion.r_loc * a.ion.r_loc) + eps2;
-  constexpr float kScaleF = 1099511627776.0f;  // 2^40
-  long long W = 0, S[3] = {0, 0, 0}, Q = 0;
-  // one electron's terms, rounded to FP32 and then exactly to 2^-40 units
-  auto add = [&](const float4 v) {
+// Each electron's terms are rounded to FP32 and then exactly to 2^-40 units
+// and added to 64-bit integer sums, so a total does not depend on which lane
+// took which electron, nor on the order of the listing.
+//
+// The ions are taken in bucket order, kMomIons per CTA.  The ions of one
+// bucket mostly share one cell and so one set of 27 neighbour cells: for each
+// run of ions with the same bucket, the positions of the electrons listed in
+// those cells' buckets (a few thousand) are staged once in shared memory, and
+// each warp tests them against one ion at a time, 32 electrons per step.  An
+// ion of the run in another cell (two cells hashed to one bucket, or a
+// position without a cell) and a run whose electrons do not fit the stage
+// walk their own 27 buckets from global memory instead.
+constexpr int kMomThreads = 256;
+constexpr int kMomWarps = kMomThreads / 32;
+constexpr int kMomIons = 64;     // ions per CTA
+constexpr int kMomCap = 3072;    // staged electrons per run
+
+// v rounded to the nearest integer, ties to even, as a 64-bit integer, on
+// the integer pipe (for |v| < 2^62).  From the binary32 layout: v = m 2^s
+// with the 24-bit significand m and s = exponent - 150; for s >= 0 the value
+// is m shifted left, else m / 2^-s rounded by its remainder (every |v| < 1/2
+// rounds to 0, so the shift stops at 25).  GB300 runs the F2I.S64 conversion
+// on its narrow FP64 pipe, which held it 85 % busy in this kernel.
+__device__ __forceinline__ long long rint_ll(float v) {
+  const unsigned b = __float_as_uint(v);
+  const int e = static_cast<int>((b >> 23) & 0xffu);
+  const unsigned long long m = (b & 0x7fffffu) | (e ? 0x800000u : 0u);
+  const int s = e - 150;
+  unsigned long long r;
+  if (s >= 0) {
+    r = m << (s < 62 ? s : 62);
+  } else {
+    const int k = -s < 25 ? -s : 25;
+    const unsigned long long q = m >> k, rem = m & ((1ull << k) - 1), half = 1ull << (k - 1);
+    r = q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
+  }
+  const long long x = static_cast<long long>(r);
+  return (b >> 31) ? -x : x;
+}
+
+struct MomSums {
+  long long W = 0, S0 = 0, S1 = 0, S2 = 0, Q = 0;
+
+  // one electron of velocity record v (w in .w) against an ion of velocity ui
+  __device__ __forceinline__ void add(const float4 v, const float4 ui) {
+    constexpr float kScaleF = 1099511627776.0f;  // 2^40
     const float ux = v.x - ui.x, uy = v.y - ui.y, uz = v.z - ui.z;
     const float ws = v.w * kScaleF;
-    W += __float2ll_rn(ws);
-    S[0] += __float2ll_rn(ws * ux);
-    S[1] += __float2ll_rn(ws * uy);
-    S[2] += __float2ll_rn(ws * uz);
-    Q += __float2ll_rn(ws * fmaf(ux, ux, fmaf(uy, uy, uz * uz)));
-  };
-  int cc[3];
-  if (cell_coords(pi.x, pi.y, pi.z, cell_inv_h(a), cc)) {
-    // the 27 cells' buckets, each visited once (cells may share a bucket)
-    int bk[27];
-    int nb = 0;
-    for (int dz = -1; dz <= 1; ++dz)
-      for (int dy = -1; dy <= 1; ++dy)
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int b = cell_bucket(cc[0] + dx, cc[1] + dy, cc[2] + dz);
-          bool seen = false;
-          for (int q = 0; q < nb; ++q) seen = seen || (bk[q] == b);
-          if (!seen) bk[nb++] = b;
-        }
-    for (int q = 0; q < nb; ++q) {
-      const int cell = bk[q];
-      const int k1 = cb.start[cell + 1];
-      int k = cb.start[cell];
-      // four candidates per round: independent loads, one branch on the nearest
-      for (; k + 4 <= k1; k += 4) {
-        float r2[4];
+    W += rint_ll(ws);
+    S0 += rint_ll(ws * ux);
+    S1 += rint_ll(ws * uy);
+    S2 += rint_ll(ws * uz);
+    Q += rint_ll(ws * fmaf(ux, ux, fmaf(uy, uy, uz * uz)));
+  }
+
+  __device__ __forceinline__ void warp_sum() {
 #pragma unroll
-        for (int g = 0; g < 4; ++g) {
-          const float4 p = cb.rec[2 * (k + g)];
-          const float ddx = p.x - pi.x, ddy = p.y - pi.y, ddz = p.z - pi.z;
-          r2[g] = fmaf(ddx, ddx, eps2);
-          r2[g] = fmaf(ddy, ddy, r2[g]);
-          r2[g] = fmaf(ddz, ddz, r2[g]);
-        }
-        if (fminf(fminf(r2[0], r2[1]), fminf(r2[2], r2[3])) < rloc2e) {
-#pragma unroll
-          for (int g = 0; g < 4; ++g)
-            if (r2[g] < rloc2e) add(cb.rec[2 * (k + g) + 1]);
-        }
-      }
-      for (; k < k1; ++k) {
-        const float4 p = cb.rec[2 * k];
-        const float ddx = p.x - pi.x, ddy = p.y - pi.y, ddz = p.z - pi.z;
-        float r2 = fmaf(ddx, ddx, eps2);
-        r2 = fmaf(ddy, ddy, r2);
-        r2 = fmaf(ddz, ddz, r2);
-        if (r2 < rloc2e) add(cb.rec[2 * k + 1]);
-      }
+    for (int d = 16; d > 0; d >>= 1) {
+      W += __shfl_xor_sync(0xffffffffu, W, d);
+      S0 += __shfl_xor_sync(0xffffffffu, S0, d);
+      S1 += __shfl_xor_sync(0xffffffffu, S1, d);
+      S2 += __shfl_xor_sync(0xffffffffu, S2, d);
+      Q += __shfl_xor_sync(0xffffffffu, Q, d);
     }
   }
-  constexpr double kScale = 1099511627776.0;  // 2^40
-  double* o = a.scratch + kIonScratch * t;  // segment 0
-  o[3] = static_cast<double>(W) / kScale;
-  o[4] = static_cast<double>(S[0]) / kScale;
-  o[5] = static_cast<double>(S[1]) / kScale;
-  o[6] = static_cast<double>(S[2]) / kScale;
-  o[7] = static_cast<double>(Q) / kScale;
-  o[8] = ui.x;
-  o[9] = ui.y;
-  o[10] = ui.z;
+};
+
+__device__ __forceinline__ bool near_loc(const float4 p, const float4 pi, float eps2,
+                                         float rloc2e) {
+  const float ddx = p.x - pi.x, ddy = p.y - pi.y, ddz = p.z - pi.z;
+  float r2 = fmaf(ddx, ddx, eps2);
+  r2 = fmaf(ddy, ddy, r2);
+  r2 = fmaf(ddz, ddz, r2);
+  return r2 < rloc2e;
+}
+
+// Lane l < 27 of a warp: the bucket of neighbour cell l of cc (offsets
+// l % 3 - 1, l / 3 % 3 - 1, l / 9 - 1), or -1 for a repeat of a lower lane's
+// bucket (cells may share one) and for lanes 27..31.
+__device__ __forceinline__ int neighbour_bucket(const int (&cc)[3], int lane) {
+  int bk = -1;
+  if (lane < 27)
+    bk = cell_bucket(cc[0] + lane % 3 - 1, cc[1] + (lane / 3) % 3 - 1, cc[2] + lane / 9 - 1);
+  bool first = lane < 27;
+  for (int m = 0; m < 27; ++m) {
+    const int bm = __shfl_sync(0xffffffffu, bk, m);
+    if (m < lane && bm == bk) first = false;
+  }
+  return first ? bk : -1;
+}
+
+// One warp: the sums of one ion over its 27 cells' buckets, read from global
+// memory (lane-strided over each bucket's electrons).
+__device__ __forceinline__ void moments_global(const CellBuf& cb, const float4 pi,
+                                               const float4 ui, const int (&cc)[3], float eps2,
+                                               float rloc2e, int lane, MomSums& m) {
+  const int bk = neighbour_bucket(cc, lane);
+  unsigned todo = __ballot_sync(0xffffffffu, bk >= 0);
+  while (todo) {
+    const int src = __ffs(todo) - 1;
+    todo &= todo - 1;
+    const int cell = __shfl_sync(0xffffffffu, bk, src);
+    const int k1 = cb.start[cell + 1];
+    for (int k = cb.start[cell] + lane; k < k1; k += 32)
+      if (near_loc(cb.rec[2 * k], pi, eps2, rloc2e)) m.add(cb.rec[2 * k + 1], ui);
+  }
+}
+
+__global__ void __launch_bounds__(kMomThreads) k_ion_moments(const IonArgs a) {
+  __shared__ float4 s_pos[kMomCap];
+  __shared__ int s_idx[kMomCap];
+  // per warp: the electrons found within r_loc and not yet added, so that
+  // the terms are added 32 at a time with every lane busy
+  __shared__ int s_near[kMomWarps][64];
+  __shared__ int s_bucket[kMomIons];
+  __shared__ int s_bk[32], s_beg[32], s_cnt[32];
+  __shared__ int s_total;
+  const long long step = __ldcg(a.step);
+  if (!pass_active(a, step)) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const CellBuf cb = a.cells;
+  const float4* __restrict__ cur = (step & 1) ? a.posq1 : a.posq0;
+  const float eps2 = a.c.eps2;
+  const float rloc2e = static_cast<float>(a.ion.r_loc * a.ion.r_loc) + eps2;
+  const float inv_h = cell_inv_h(a);
+  const long long c0 = static_cast<long long>(blockIdx.x) * kMomIons;
+  const int nloc = static_cast<int>(a.ion.n_ions - c0 < kMomIons ? a.ion.n_ions - c0 : kMomIons);
+  // each ion's bucket, as the ion listing computed it (no cell: bucket 0)
+  if (tid < nloc) {
+    const long long t = cb.ion_list[c0 + tid];
+    int b = 0;
+    if (MD_IN_RANGE(a.err, t, 0, a.ion.n_ions)) {
+      const float4 p = cur[a.c.off + t];
+      b = bucket_of(p.x, p.y, p.z, inv_h);
+      b = b < 0 ? 0 : b;
+    }
+    s_bucket[tid] = b;
+  }
+  __syncthreads();
+  for (int r0 = 0; r0 < nloc;) {
+    int r1 = r0 + 1;
+    while (r1 < nloc && s_bucket[r1] == s_bucket[r0]) ++r1;
+    // the run's first ion sets the staged cell
+    const long long t0 = cb.ion_list[c0 + r0];
+    int cc0[3] = {0, 0, 0};
+    bool staged = MD_IN_RANGE(a.err, t0, 0, a.ion.n_ions);
+    if (staged) {
+      const float4 p0 = cur[a.c.off + t0];
+      staged = cell_coords(p0.x, p0.y, p0.z, inv_h, cc0);
+    }
+    if (staged && warp == 0) {
+      const int bk = neighbour_bucket(cc0, lane);
+      const int cnt = bk >= 0 ? cb.start[bk + 1] - cb.start[bk] : 0;
+      int inc = cnt;  // inclusive scan of the counts over the lanes
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += y;
+      }
+      s_bk[lane] = bk;
+      s_cnt[lane] = cnt;
+      s_beg[lane] = inc - cnt;
+      if (lane == 31) s_total = inc;
+    }
+    __syncthreads();
+    staged = staged && s_total <= kMomCap;
+    if (staged) {
+      for (int l = 0; l < 27; ++l) {
+        const int cnt = s_cnt[l];
+        if (cnt == 0) continue;
+        const int k0 = cb.start[s_bk[l]], beg = s_beg[l];
+        for (int k = tid; k < cnt; k += kMomThreads) {
+          s_pos[beg + k] = cb.rec[2 * (k0 + k)];
+          s_idx[beg + k] = k0 + k;
+        }
+      }
+    }
+    __syncthreads();
+    const int total = staged ? s_total : 0;
+    for (int q = r0 + warp; q < r1; q += kMomWarps) {
+      const long long t = cb.ion_list[c0 + q];
+      if (!MD_IN_RANGE(a.err, t, 0, a.ion.n_ions)) continue;  // warp-uniform
+      const float4 pi = cur[a.c.off + t];
+      const float4 ui = a.vel[a.c.off + t];
+      MomSums m;
+      int cc[3];
+      if (cell_coords(pi.x, pi.y, pi.z, inv_h, cc)) {
+        if (staged && cc[0] == cc0[0] && cc[1] == cc0[1] && cc[2] == cc0[2]) {
+          int* q = s_near[warp];
+          int qn = 0;  // queued electrons (warp-uniform)
+          for (int k0 = 0; k0 < total; k0 += 32) {
+            const int k = k0 + lane;
+            const bool nr = k < total && near_loc(s_pos[k], pi, eps2, rloc2e);
+            const unsigned mask = __ballot_sync(0xffffffffu, nr);
+            if (nr) q[qn + __popc(mask & ((1u << lane) - 1u))] = s_idx[k];
+            qn += __popc(mask);
+            if (qn >= 32) {
+              __syncwarp();
+              m.add(cb.rec[2 * q[lane] + 1], ui);
+              const int rest = qn - 32 > lane ? q[32 + lane] : 0;
+              __syncwarp();
+              if (lane < qn - 32) q[lane] = rest;
+              __syncwarp();
+              qn -= 32;
+            }
+          }
+          __syncwarp();
+          if (lane < qn) m.add(cb.rec[2 * q[lane] + 1], ui);
+          __syncwarp();
+        } else {
+          moments_global(cb, pi, ui, cc, eps2, rloc2e, lane, m);
+        }
+        m.warp_sum();
+      }
+      if (lane == 0) {
+        constexpr double kScale = 1099511627776.0;  // 2^40
+        double* o = a.scratch + kIonScratch * t;  // segment 0
+        o[3] = static_cast<double>(m.W) / kScale;
+        o[4] = static_cast<double>(m.S0) / kScale;
+        o[5] = static_cast<double>(m.S1) / kScale;
+        o[6] = static_cast<double>(m.S2) / kScale;
+        o[7] = static_cast<double>(m.Q) / kScale;
+        o[8] = ui.x;
+        o[9] = ui.y;
+        o[10] = ui.z;
+      }
+    }
+    __syncthreads();  // the stage is rewritten by the next run
+    r0 = r1;
+  }
 }
 
 // ------------------------------------------------------------- decision --
@@ -1121,7 +1279,8 @@ cudaError_t launch_ion_pass(const IonArgs& a, cudaStream_t s) {
       return e;
     k_cell_list<true><<<gl, 256, 0, s>>>(a);
     k_ion_cell_list<true><<<gi, 256, 0, s>>>(a);
-    k_ion_moments<<<static_cast<unsigned>((a.ion.n_ions + 127) / 128), 128, 0, s>>>(a);
+    k_ion_moments<<<static_cast<unsigned>((a.ion.n_ions + kMomIons - 1) / kMomIons),
+                    kMomThreads, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   const unsigned g2 = static_cast<unsigned>((a.ion.n_ions + 255) / 256);
