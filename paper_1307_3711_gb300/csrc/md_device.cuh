@@ -845,8 +845,9 @@ __device__ __forceinline__ void pair2_u(const ulonglong2 xy, const ulonglong2 zq
 // As sum_sources, with the pair arithmetic in packed f32x2.  Each landed
 // tile is first expanded into `dup` (which frees its TMA stage at once, so a
 // single stage suffices), then the R targets of this thread are summed two at
-// a time.  The Kahan sums live in `ks` and are returned unpacked in `out`
-// (bit-identical to the scalar path).
+// a time.  The Kahan sums live in `ks` (bit-identical to the scalar path's);
+// reset = false continues the sums of an earlier call instead of clearing
+// them.
 template <int THREADS, int R, int TILE, int STAGES, bool POT>
 __device__ __forceinline__ bool sum_sources_packed(Stage<TILE, STAGES>& sm, DupTile<TILE>& dup,
                                                    KahanSmem<R / 2, THREADS, POT>& ks, unsigned& it,
@@ -855,7 +856,7 @@ __device__ __forceinline__ bool sum_sources_packed(Stage<TILE, STAGES>& sm, DupT
                                                    const float (&zi)[R], float eps2, int* err,
                                                    int* s_abort,
                                                    const unsigned char* live = nullptr,
-                                                   long long gbase = 0) {
+                                                   long long gbase = 0, bool reset = true) {
   static_assert(R % 2 == 0, "packed path needs an even number of i-particles per thread");
   constexpr int P = R / 2;
   const int tid = threadIdx.x;
@@ -870,8 +871,10 @@ __device__ __forceinline__ bool sum_sources_packed(Stage<TILE, STAGES>& sm, DupT
     yi2[p] = lds_u64(smem_u32(&ks.t[1][p][tid]));
     zi2[p] = lds_u64(smem_u32(&ks.t[2][p][tid]));
     a.ax[p] = a.ay[p] = a.az[p] = a.ap[p] = 0ull;
+    if (reset) {
 #pragma unroll
-    for (int k = 0; k < (POT ? 8 : 6); ++k) ks.v[k][p][tid] = 0ull;
+      for (int k = 0; k < (POT ? 8 : 6); ++k) ks.v[k][p][tid] = 0ull;
+    }
   }
   ks.e2[tid] = f2_pack(eps2, eps2);
   const u64 e2 = lds_u64(smem_u32(&ks.e2[tid]));

@@ -1066,9 +1066,12 @@ __global__ void __launch_bounds__(256) k_ion_apply(const IonArgs a) {
 // CTA (x, y) takes R x THREADS ions and segment y of the nf charge changes of
 // each stream, and writes its partial field to scratch [seg][n_ions][3];
 // k_ion_fix_combine adds the segments in order to e_ion (deterministic).
-template <int THREADS, int R, int TILE, int STAGES, bool MI = false>
+template <int THREADS, int R, int TILE, int STAGES, bool MI = false, bool PACK = false>
 __global__ void __launch_bounds__(THREADS) k_ion_fix(const IonArgs a) {
+  static_assert(!(PACK && MI), "minimum-image forces use the scalar path");
   __shared__ Stage<TILE, STAGES> sm;
+  __shared__ DupTile<PACK ? TILE : 1> dup;
+  __shared__ KahanSmem<PACK ? R / 2 : 1, PACK ? THREADS : 1, false> ks;
   __shared__ int s_abort;
   const long long step = __ldcg(a.step);
   if (!pass_active(a, step)) return;
@@ -1097,7 +1100,17 @@ __global__ void __launch_bounds__(THREADS) k_ion_fix(const IonArgs a) {
   }
   Acc<R, false> acc;
   acc.zero();
-  if (jn > 0) {
+  if constexpr (PACK) {
+    // both halves of the changes into one set of Kahan sums (an empty
+    // segment only clears them)
+    unsigned it = 0;
+    bool ok = true;
+    for (int half = 0; half < 2 && ok; ++half)
+      ok = sum_sources_packed<THREADS, R, TILE, STAGES, false>(
+          sm, dup, ks, it, a.fix_src + half * a.ion.n_ions + j0, jn, xi, yi, zi, a.c.eps2, a.err,
+          &s_abort, nullptr, 0, half == 0);
+    if (!ok) return;
+  } else if (jn > 0) {
     unsigned it = 0;
     bool ok = true;
     bool mi_on = false;
@@ -1127,9 +1140,15 @@ __global__ void __launch_bounds__(THREADS) k_ion_fix(const IonArgs a) {
     if (t >= a.ion.n_ions) continue;
     if (!MD_IN_RANGE(a.err, blockIdx.y, 0, kIonMaxSeg)) continue;
     double* o = a.scratch + 3 * (static_cast<long long>(blockIdx.y) * a.ion.n_ions + t);
-    o[0] = -(static_cast<double>(acc.sx[r]) - acc.cx[r]);
-    o[1] = -(static_cast<double>(acc.sy[r]) - acc.cy[r]);
-    o[2] = -(static_cast<double>(acc.sz[r]) - acc.cz[r]);
+    if constexpr (PACK) {
+      o[0] = -(static_cast<double>(kahan_part(ks, 0, r)) - kahan_part(ks, 3, r));
+      o[1] = -(static_cast<double>(kahan_part(ks, 1, r)) - kahan_part(ks, 4, r));
+      o[2] = -(static_cast<double>(kahan_part(ks, 2, r)) - kahan_part(ks, 5, r));
+    } else {
+      o[0] = -(static_cast<double>(acc.sx[r]) - acc.cx[r]);
+      o[1] = -(static_cast<double>(acc.sy[r]) - acc.cy[r]);
+      o[2] = -(static_cast<double>(acc.sz[r]) - acc.cz[r]);
+    }
   }
 }
 
@@ -1204,10 +1223,12 @@ constexpr int kSumThreads = 128;
 constexpr int kSumR = 8;
 constexpr int kSumTile = 512;
 constexpr bool kSumPacked = true;
-// the charge-change field (no moments: four targets per thread)
+// the charge-change field: the step kernel's packed source loop (eight
+// targets per thread); the minimum-image twin is scalar (four per thread)
 constexpr int kFixThreads = kIonThreads;
-constexpr int kFixR = 4;
+constexpr int kFixR = 8;
 constexpr int kFixTile = 512;
+constexpr int kFixMiR = 4;
 
 }  // namespace
 
@@ -1238,7 +1259,7 @@ cudaError_t ion_field_blocks_per_sm(int* out) {
 
 cudaError_t ion_fix_blocks_per_sm(int* out) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      out, k_ion_fix<kFixThreads, kFixR, kFixTile, 2>, kFixThreads, 0);
+      out, k_ion_fix<kFixThreads, kFixR, kFixTile, 1, false, true>, kFixThreads, 0);
 }
 
 cudaError_t launch_ion_pass(const IonArgs& a, cudaStream_t s) {
@@ -1295,13 +1316,13 @@ cudaError_t launch_ion_pass(const IonArgs& a, cudaStream_t s) {
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (a.e_ion && a.fix_src) {
     if (a.fix_nseg < 1 || a.fix_nseg > kIonMaxSeg) return cudaErrorInvalidValue;
-    const long long per_fix = kFixThreads * kFixR;
+    const long long per_fix = kFixThreads * (a.min_image ? kFixMiR : kFixR);
     const dim3 gf(static_cast<unsigned>((a.ion.n_ions + per_fix - 1) / per_fix),
                   static_cast<unsigned>(a.fix_nseg));
     if (a.min_image)
-      k_ion_fix<kFixThreads, kFixR, kFixTile, 2, true><<<gf, kFixThreads, 0, s>>>(a);
+      k_ion_fix<kFixThreads, kFixMiR, kFixTile, 2, true><<<gf, kFixThreads, 0, s>>>(a);
     else
-      k_ion_fix<kFixThreads, kFixR, kFixTile, 2><<<gf, kFixThreads, 0, s>>>(a);
+      k_ion_fix<kFixThreads, kFixR, kFixTile, 1, false, true><<<gf, kFixThreads, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_ion_fix_combine<<<g2, 256, 0, s>>>(a);
     e = cudaGetLastError();
