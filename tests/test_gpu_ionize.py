@@ -156,6 +156,51 @@ def test_ionization_inputs_match_oracle(md):
     np.testing.assert_allclose(info["te"][both][same], te64[both][same], rtol=2e-5, atol=1e-6)
 
 
+@pytest.mark.parametrize("n_el", [2000, 6000])
+def test_local_moments_of_dense_electron_clouds_follow_oracle(md, n_el):
+    """1000 ions in a ball of radius r_loc inside a cloud of electrons of radius
+    2 r_loc: with 2000 electrons the 27 cells of an ion hold fewer than the
+    moment kernel stages at once, and a few hundred lie within r_loc (their
+    terms are queued and added 32 at a time); with 6000 they overflow the
+    stage and the ions walk their cells in global memory.  Either way n_e
+    equals the oracle's where both count the same electrons and T_e agrees to
+    FP32 rounding."""
+    n, zmax = 1000, 8
+    z_ion = n_el // n            # each ion has freed its electrons: the slots suffice
+    rw = synth.nm_to_len(AR["r_w_nm"])
+    r_loc = 3 * rw
+    rng = np.random.default_rng(17 + n_el)
+    nt = n + zmax * n
+    x = np.zeros((nt, 3))
+    u = np.zeros((nt, 3))
+    x[:n] = synth.uniform_sphere(rng, n, r_loc)
+    x[n:n + n_el] = synth.uniform_sphere(rng, n_el, 2 * r_loc)
+    x[n + n_el:] = synth.uniform_sphere(rng, nt - n - n_el, 2 * r_loc)
+    u[n:n + n_el] = rng.normal(size=(n_el, 3)) * synth.thermal_sigma_u(50.0, 1.0)
+    z = np.zeros(nt, np.int32)
+    z[:n] = z_ion
+    z[n:] = -1
+    mass = np.where(np.arange(nt) < n, AR["mass"], 1.0)
+    w = np.ones(nt)
+    active = (np.arange(nt) < n + n_el).astype(np.uint8)
+    kind = np.where(active == 0, md.KIND_INACTIVE, np.where(z < 0, md.KIND_ELECTRON,
+                                                            md.KIND_ION))
+    kw = dict(a0=0.0, tau=1.0, dt=0.05, softening=synth.nm_to_len(0.1), envelope=3,
+              rate_model=1, ionize_every=0, zmax=zmax, n_ions=n, slot_base=n, seed=99,
+              r_loc=r_loc, r_create=rw, species=AR)
+    with md.Context([md.make_config(**kw)], [md.HostParticles(x, u, z, mass, w, kind)]) as ctx:
+        ctx.ionize()
+        info = ctx.ionization(0)
+    st = oracle.State(x, u, z, mass, w, active)
+    ne64, te64 = oracle.local_moments(st.x[:n], st, r_loc)
+    assert (ne64 > 0).all()
+    both = info["ne"] > 0
+    assert both.mean() > 0.99
+    same = np.isclose(info["ne"][both], ne64[both], rtol=1e-12)
+    assert same.mean() > 0.95
+    np.testing.assert_allclose(info["te"][both][same], te64[both][same], rtol=2e-5, atol=1e-6)
+
+
 def test_ionization_in_steps_conserves_charge(md):
     """md_step with a pass before every 2nd step: total charge stays zero
     exactly, and the active electrons equal the sum of ion charges."""
