@@ -171,7 +171,8 @@ typedef struct {
                            not depend on the other clusters of the context; with 0 or
                            equal shares they may.  md_get_tuning reports -k for equal shares,
                            else the largest segment count of any cluster; md_autotune
-                           tries 0 for every configuration and -4 for the two fastest. */
+                           tries 0 for every configuration and -2, -4 for the two
+                           fastest. */
     int32_t packed;     /* 1: pair arithmetic in packed f32x2 (two i-particles per
                            instruction, bit-identical results), 0: scalar FP32 */
     int32_t min_blocks; /* register budget: 64K / (threads x min_blocks); 0 = left to the
@@ -410,7 +411,7 @@ md_status md_get_step(md_ctx *ctx, int64_t *step);
  * md_get_tuning: the configuration in use.
  * md_autotune: times every configuration over `steps` steps on the
  * context's own state (restored afterwards), with jsplit 0 and, for the two
- * fastest, jsplit -4 (no ionizing cluster), and keeps the fastest; the
+ * fastest, jsplit -2 and -4 (no ionizing cluster), and keeps the fastest; the
  * per-configuration best mean step times in ms go to times_ms (cap entries,
  * may be NULL; -1 for a configuration not timed). */
 int32_t md_tuning_list(md_tuning *list, int32_t cap);

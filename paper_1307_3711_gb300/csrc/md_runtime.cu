@@ -422,8 +422,8 @@ md::ClusterDev slice_view(const md_ctx* c, int ci) {
   return v;
 }
 
-// Equal shares per resident CTA that md_autotune tries (jsplit = -kAutoShares).
-constexpr int kAutoShares = 4;
+// Equal shares per resident CTA that md_autotune tries (jsplit = -k).
+constexpr int kAutoShares[] = {2, 4};
 
 // Source segments of md_get_fields / md_diagnostics at most.
 constexpr int kFieldMaxSeg = 8;
@@ -2084,8 +2084,9 @@ md_status md_autotune(md_ctx* c, int32_t steps, double* times_ms, int32_t cap) {
     cudaStreamSynchronize(s);
   };
   // every configuration with its segments chosen for balance, then the two
-  // fastest with equal shares (kAutoShares per resident CTA), which fill the
-  // last round of a large step but add pieces that cross i-blocks
+  // fastest with equal shares (each count of kAutoShares per resident CTA),
+  // which fill the last round of a large step but add pieces that cross
+  // i-blocks
   for (int i = 0; i < n && st == MD_OK; ++i) {
     int bps = 0;
     if (c->any_mi && !cfgs[i].launch_step_mi) continue;  // no minimum-image kernel
@@ -2098,7 +2099,9 @@ md_status md_autotune(md_ctx* c, int32_t steps, double* times_ms, int32_t cap) {
       if (by_cfg[i] >= 0.0) order.push_back(i);
     std::stable_sort(order.begin(), order.end(),
                      [&](int x, int y) { return by_cfg[x] < by_cfg[y]; });
-    for (size_t k = 0; k < order.size() && k < 2 && st == MD_OK; ++k) trial(order[k], -kAutoShares);
+    for (size_t k = 0; k < order.size() && k < 2 && st == MD_OK; ++k)
+      for (int sh : kAutoShares)
+        if (st == MD_OK) trial(order[k], -sh);
   }
   if (times_ms)
     for (int i = 0; i < n && i < cap; ++i) times_ms[i] = by_cfg[i];
