@@ -69,6 +69,42 @@ def test_two_slices_step_like_the_whole_cluster(md, jsplit):
         c.close()
 
 
+def test_slices_with_equal_shares_step_like_the_whole_cluster(md):
+    """With equal shares (jsplit -4, the autotuner's usual pick) each slice cuts
+    its own i-blocks' sources into shares, so its pieces, and the order of its
+    sums, differ from the unsplit context's: after 5 steps the slices' records
+    agree with the whole cluster's to FP32 summation order."""
+    import torch
+    from paper_1307_3711_gb300 import shard
+    w = synth.xe3_cluster(20000, seed=5)
+    n = w.cluster.n
+    b1 = shard.slice_bounds(n, 2, 1)[0]
+    whole, lo, hi = _ctx(md, w, -4), _ctx(md, w, -4), _ctx(md, w, -4)
+    assert whole.tuning()[4] == -4
+    lo.set_slice(0, 0, b1)
+    hi.set_slice(0, b1, n)
+    for _ in range(5):
+        for c in (whole, lo, hi):
+            c.step(1)
+        jl, jh = shard.jstream_tensor(lo), shard.jstream_tensor(hi)
+        jl[b1:] = jh[b1:]
+        jh[:b1] = jl[:b1]
+        torch.cuda.synchronize()
+    ref = whole.get_particles(0)
+    pl, ph = lo.get_particles(0), hi.get_particles(0)
+    x = np.r_[pl.x[:b1], ph.x[b1:]]
+    u = np.r_[pl.u[:b1], ph.u[b1:]]
+    r0 = np.abs(ref.x).max()
+    assert np.abs(x - ref.x).max() < 1e-6 * r0
+    du = np.abs(u - ref.u).max(1)
+    assert np.percentile(du, 99) < 1e-4 * np.abs(ref.u).max()
+    e_w = whole.fields(0)
+    e_l, e_h = lo.fields(0), hi.fields(0)
+    assert summary(force_error(np.r_[e_l[:b1], e_h[b1:]], e_w))["p99"] <= 2e-5
+    for c in (whole, lo, hi):
+        c.close()
+
+
 def test_slice_arguments_and_states(md):
     w = synth.xe3_cluster(4000, seed=1)
     with _ctx(md, w, 0) as c:
