@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 
+#include <new>
+
 #include "md.h"
 #include "md_types.cuh"
 
@@ -104,6 +106,19 @@ md_status field_error_word(int** out);
 // Records the thread-local message returned by md_last_error() and returns
 // the status (implemented in md_runtime.cu).
 md_status report_error(md_status status, const char* msg);
+
+// Runs an entry point's body: the C ABI returns a status and lets no C++
+// exception out (a host allocation that fails becomes MD_ERR_OOM).
+template <class F>
+md_status guarded(F&& body) noexcept {
+  try {
+    return body();
+  } catch (const std::bad_alloc&) {
+    return report_error(MD_ERR_OOM, "host memory allocation failed");
+  } catch (...) {
+    return report_error(MD_ERR_STATE, "unexpected host exception");
+  }
+}
 md_status report_cuda_error(cudaError_t e, const char* what);
 cudaError_t launch_download(const DownloadArgs& a, cudaStream_t s);
 

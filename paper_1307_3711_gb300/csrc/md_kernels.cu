@@ -679,7 +679,7 @@ md_status field_error_word(int** out) {
 
 }  // namespace md
 
-extern "C" md_status md_field_device_status(void* stream) {
+static md_status md_field_device_status_body(void* stream) {
   using namespace md;
   int* word = nullptr;
   md_status st = field_error_word(&word);
@@ -702,7 +702,11 @@ extern "C" md_status md_field_device_status(void* stream) {
   return MD_OK;
 }
 
-extern "C" md_status md_field_wait_selftest(double budget_ms, void* stream) {
+extern "C" md_status md_field_device_status(void* stream) {
+  return md::guarded([&] { return md_field_device_status_body(stream); });
+}
+
+static md_status md_field_wait_selftest_body(double budget_ms, void* stream) {
   using namespace md;
   if (!(budget_ms > 0.0) || budget_ms > 5000.0)
     return report_error(MD_ERR_ARG, "budget_ms must be in (0, 5000]");
@@ -719,9 +723,13 @@ extern "C" md_status md_field_wait_selftest(double budget_ms, void* stream) {
   return MD_OK;
 }
 
-extern "C" md_status md_coulomb_field_device_noalloc(const void* src, int64_t ns, const void* tgt,
-                                                     int64_t nt, float eps2, int64_t self_offset,
-                                                     double* e, double* phi, void* stream) {
+extern "C" md_status md_field_wait_selftest(double budget_ms, void* stream) {
+  return md::guarded([&] { return md_field_wait_selftest_body(budget_ms, stream); });
+}
+
+static md_status md_coulomb_field_device_noalloc_body(const void* src, int64_t ns, const void* tgt,
+                                                      int64_t nt, float eps2, int64_t self_offset,
+                                                      double* e, double* phi, void* stream) {
   using namespace md;
   if (ns < 0 || nt < 0) return report_error(MD_ERR_ARG, "negative size");
   if (nt > kNoAllocMaxTargets)
@@ -768,4 +776,10 @@ extern "C" md_status md_coulomb_field_device_noalloc(const void* src, int64_t ns
   ce = cudaGetLastError();
   if (ce != cudaSuccess) return report_cuda_error(ce, "allocation-free field launch");
   return MD_OK;
+}
+
+extern "C" md_status md_coulomb_field_device_noalloc(const void* src, int64_t ns, const void* tgt,
+                                                     int64_t nt, float eps2, int64_t self_offset,
+                                                     double* e, double* phi, void* stream) {
+  return md::guarded([&] { return md_coulomb_field_device_noalloc_body(src, ns, tgt, nt, eps2, self_offset, e, phi, stream); });
 }

@@ -675,8 +675,8 @@ using md::report_error;
 
 extern "C" {
 
-md_status md_mlp_forward_device(const float* params, const float* feats, int64_t n, float* y,
-                                void* stream) {
+static md_status md_mlp_forward_device_body(const float* params, const float* feats, int64_t n, float* y,
+                                            void* stream) {
   if (n < 0) return report_error(MD_ERR_ARG, "n < 0");
   if (n == 0) return MD_OK;
   if (!params || !feats || !y) return report_error(MD_ERR_ARG, "NULL pointer");
@@ -689,9 +689,14 @@ md_status md_mlp_forward_device(const float* params, const float* feats, int64_t
   return MD_OK;
 }
 
-md_status md_mlp_loss_grad_device(const float* params, const float* feats, const int32_t* z,
-                                  const float* target, int64_t n, float* grad, float* loss,
-                                  void* stream) {
+md_status md_mlp_forward_device(const float* params, const float* feats, int64_t n, float* y,
+                                void* stream) {
+  return md::guarded([&] { return md_mlp_forward_device_body(params, feats, n, y, stream); });
+}
+
+static md_status md_mlp_loss_grad_device_body(const float* params, const float* feats, const int32_t* z,
+                                              const float* target, int64_t n, float* grad, float* loss,
+                                              void* stream) {
   if (n <= 0) return report_error(MD_ERR_ARG, "n must be > 0");
   if (!params || !feats || !z || !target || !grad) return report_error(MD_ERR_ARG, "NULL pointer");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -722,9 +727,15 @@ md_status md_mlp_loss_grad_device(const float* params, const float* feats, const
   return MD_OK;
 }
 
-md_status md_mlp_samples_device(const md_mlp_train_config* cfg, int64_t n, uint64_t seed,
-                                float* feats, int32_t* z, float* target, double* raw,
-                                void* stream) {
+md_status md_mlp_loss_grad_device(const float* params, const float* feats, const int32_t* z,
+                                  const float* target, int64_t n, float* grad, float* loss,
+                                  void* stream) {
+  return md::guarded([&] { return md_mlp_loss_grad_device_body(params, feats, z, target, n, grad, loss, stream); });
+}
+
+static md_status md_mlp_samples_device_body(const md_mlp_train_config* cfg, int64_t n, uint64_t seed,
+                                            float* feats, int32_t* z, float* target, double* raw,
+                                            void* stream) {
   md_status st = md::check_train_config(cfg);
   if (st != MD_OK) return st;
   if (n <= 0 || !feats || !z || !target) return report_error(MD_ERR_ARG, "bad sample buffers");
@@ -735,9 +746,15 @@ md_status md_mlp_samples_device(const md_mlp_train_config* cfg, int64_t n, uint6
   return MD_OK;
 }
 
-md_status md_ion_rates_device(const md_mlp_train_config* cfg, int32_t model, const float* params,
-                              const double* emag, const int32_t* z, const double* ne,
-                              const double* te, int64_t n, double* nu, void* stream) {
+md_status md_mlp_samples_device(const md_mlp_train_config* cfg, int64_t n, uint64_t seed,
+                                float* feats, int32_t* z, float* target, double* raw,
+                                void* stream) {
+  return md::guarded([&] { return md_mlp_samples_device_body(cfg, n, seed, feats, z, target, raw, stream); });
+}
+
+static md_status md_ion_rates_device_body(const md_mlp_train_config* cfg, int32_t model, const float* params,
+                                          const double* emag, const int32_t* z, const double* ne,
+                                          const double* te, int64_t n, double* nu, void* stream) {
   md_status st = md::check_train_config(cfg);
   if (st != MD_OK) return st;
   if (model != 1 && model != 2) return report_error(MD_ERR_ARG, "model must be 1 or 2");
@@ -760,8 +777,14 @@ md_status md_ion_rates_device(const md_mlp_train_config* cfg, int32_t model, con
   return MD_OK;
 }
 
-md_status md_mlp_train(const md_mlp_train_config* cfg, float* params_out, md_mlp_report* rep,
-                       void* stream) {
+md_status md_ion_rates_device(const md_mlp_train_config* cfg, int32_t model, const float* params,
+                              const double* emag, const int32_t* z, const double* ne,
+                              const double* te, int64_t n, double* nu, void* stream) {
+  return md::guarded([&] { return md_ion_rates_device_body(cfg, model, params, emag, z, ne, te, n, nu, stream); });
+}
+
+static md_status md_mlp_train_body(const md_mlp_train_config* cfg, float* params_out, md_mlp_report* rep,
+                                   void* stream) {
   md_status st = md::check_train_config(cfg);
   if (st != MD_OK) return st;
   if (!params_out) return report_error(MD_ERR_ARG, "params_out is NULL");
@@ -876,6 +899,11 @@ md_status md_mlp_train(const md_mlp_train_config* cfg, float* params_out, md_mlp
     rep->steps = step;
   }
   return MD_OK;
+}
+
+md_status md_mlp_train(const md_mlp_train_config* cfg, float* params_out, md_mlp_report* rep,
+                       void* stream) {
+  return md::guarded([&] { return md_mlp_train_body(cfg, params_out, rep, stream); });
 }
 
 }  // extern "C"

@@ -1122,7 +1122,7 @@ double md_n_atoms(double r0, double r_wigner_seitz) {
   return q * q * q;
 }
 
-md_status md_device_info(int32_t* sm_count, char* name, int32_t name_cap) {
+static md_status md_device_info_body(int32_t* sm_count, char* name, int32_t name_cap) {
   int dev = 0;
   MD_CUDA(cudaGetDevice(&dev));
   cudaDeviceProp prop;
@@ -1133,6 +1133,10 @@ md_status md_device_info(int32_t* sm_count, char* name, int32_t name_cap) {
     name[name_cap - 1] = 0;
   }
   return MD_OK;
+}
+
+md_status md_device_info(int32_t* sm_count, char* name, int32_t name_cap) {
+  return md::guarded([&] { return md_device_info_body(sm_count, name, name_cap); });
 }
 
 }  // extern "C"
@@ -1351,8 +1355,8 @@ md_status populate(md_ctx* c, int32_t n_clusters, Fill fill, md_ctx** out) {
 
 extern "C" {
 
-md_status md_init(md_ctx** out, const md_config* cfgs, int32_t n_clusters,
-                  const md_particles* parts, void* stream) {
+static md_status md_init_body(md_ctx** out, const md_config* cfgs, int32_t n_clusters,
+                              const md_particles* parts, void* stream) {
   if (!out) return fail(MD_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (n_clusters < 1 || !cfgs || !parts) return fail(MD_ERR_ARG, "need >= 1 cluster");
@@ -1373,8 +1377,13 @@ md_status md_init(md_ctx** out, const md_config* cfgs, int32_t n_clusters,
                   out);
 }
 
-md_status md_init_generate(md_ctx** out, const md_config* cfgs, const md_generate* gens,
-                           int32_t n_clusters, void* stream) {
+md_status md_init(md_ctx** out, const md_config* cfgs, int32_t n_clusters,
+                  const md_particles* parts, void* stream) {
+  return md::guarded([&] { return md_init_body(out, cfgs, n_clusters, parts, stream); });
+}
+
+static md_status md_init_generate_body(md_ctx** out, const md_config* cfgs, const md_generate* gens,
+                                       int32_t n_clusters, void* stream) {
   if (!out) return fail(MD_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (n_clusters < 1 || !cfgs || !gens) return fail(MD_ERR_ARG, "need >= 1 cluster");
@@ -1393,10 +1402,15 @@ md_status md_init_generate(md_ctx** out, const md_config* cfgs, const md_generat
                   out);
 }
 
+md_status md_init_generate(md_ctx** out, const md_config* cfgs, const md_generate* gens,
+                           int32_t n_clusters, void* stream) {
+  return md::guarded([&] { return md_init_generate_body(out, cfgs, gens, n_clusters, stream); });
+}
+
 
 void md_destroy(md_ctx* ctx) { free_ctx(ctx); }
 
-md_status md_step(md_ctx* c, int32_t nsteps) {
+static md_status md_step_body(md_ctx* c, int32_t nsteps) {
   if (!c) return fail(MD_ERR_ARG, "ctx is NULL");
   if (nsteps < 0) return fail(MD_ERR_ARG, "nsteps < 0");
   if (nsteps == 0) return MD_OK;
@@ -1413,13 +1427,21 @@ md_status md_step(md_ctx* c, int32_t nsteps) {
   return launch_steps_direct(c, nsteps % kGraphSteps);
 }
 
-md_status md_sync(md_ctx* c) {
+md_status md_step(md_ctx* c, int32_t nsteps) {
+  return md::guarded([&] { return md_step_body(c, nsteps); });
+}
+
+static md_status md_sync_body(md_ctx* c) {
   if (!c) return fail(MD_ERR_ARG, "ctx is NULL");
   MD_CUDA(cudaStreamSynchronize(c->stream));
   return check_device_error(c);
 }
 
-md_status md_ionize(md_ctx* c) {
+md_status md_sync(md_ctx* c) {
+  return md::guarded([&] { return md_sync_body(c); });
+}
+
+static md_status md_ionize_body(md_ctx* c) {
   if (!c) return fail(MD_ERR_ARG, "ctx is NULL");
   if (!c->any_ion) return MD_OK;
   cudaError_t e = launch_ion_all(c, 1, c->stream);
@@ -1427,7 +1449,11 @@ md_status md_ionize(md_ctx* c) {
   return MD_OK;
 }
 
-md_status md_set_rate_mlp(md_ctx* c, const float* params, const md_mlp_train_config* domain) {
+md_status md_ionize(md_ctx* c) {
+  return md::guarded([&] { return md_ionize_body(c); });
+}
+
+static md_status md_set_rate_mlp_body(md_ctx* c, const float* params, const md_mlp_train_config* domain) {
   if (!c || !params || !domain) return fail(MD_ERR_ARG, "NULL argument");
   if (!(domain->e_min > 0.0 && domain->e_max > domain->e_min && domain->ne_min > 0.0 &&
         domain->ne_max > domain->ne_min && domain->te_min > 0.0 &&
@@ -1464,7 +1490,11 @@ md_status md_set_rate_mlp(md_ctx* c, const float* params, const md_mlp_train_con
   return MD_OK;
 }
 
-md_status md_set_detectors(md_ctx* c, int32_t cluster, const md_detector_config* d) {
+md_status md_set_rate_mlp(md_ctx* c, const float* params, const md_mlp_train_config* domain) {
+  return md::guarded([&] { return md_set_rate_mlp_body(c, params, domain); });
+}
+
+static md_status md_set_detectors_body(md_ctx* c, int32_t cluster, const md_detector_config* d) {
   if (!c) return fail(MD_ERR_ARG, "ctx is NULL");
   if (cluster < 0 || cluster >= c->n_clusters) return fail(MD_ERR_ARG, "bad cluster index");
   if (d && !(d->radius > 0.0 && d->cone_half_angle_deg >= 0.0 &&
@@ -1516,7 +1546,11 @@ md_status md_set_detectors(md_ctx* c, int32_t cluster, const md_detector_config*
   return check_device_error(c);
 }
 
-md_status md_get_iedf(md_ctx* c, int32_t cluster, uint64_t* detected, uint64_t* inside) {
+md_status md_set_detectors(md_ctx* c, int32_t cluster, const md_detector_config* d) {
+  return md::guarded([&] { return md_set_detectors_body(c, cluster, d); });
+}
+
+static md_status md_get_iedf_body(md_ctx* c, int32_t cluster, uint64_t* detected, uint64_t* inside) {
   if (!c) return fail(MD_ERR_ARG, "ctx is NULL");
   if (cluster < 0 || cluster >= c->n_clusters) return fail(MD_ERR_ARG, "bad cluster index");
   const md::ClusterDev& cl = c->cl[cluster];
@@ -1551,8 +1585,12 @@ md_status md_get_iedf(md_ctx* c, int32_t cluster, uint64_t* detected, uint64_t* 
   return check_device_error(c);
 }
 
-md_status md_get_ionization(md_ctx* c, int32_t cluster, double* emag, double* ne, double* te,
-                            double* prob, uint8_t* fired) {
+md_status md_get_iedf(md_ctx* c, int32_t cluster, uint64_t* detected, uint64_t* inside) {
+  return md::guarded([&] { return md_get_iedf_body(c, cluster, detected, inside); });
+}
+
+static md_status md_get_ionization_body(md_ctx* c, int32_t cluster, double* emag, double* ne, double* te,
+                                        double* prob, uint8_t* fired) {
   if (!c) return fail(MD_ERR_ARG, "ctx is NULL");
   if (cluster < 0 || cluster >= c->n_clusters) return fail(MD_ERR_ARG, "bad cluster index");
   const long long n = c->ion[cluster].n_ions;
@@ -1573,7 +1611,12 @@ md_status md_get_ionization(md_ctx* c, int32_t cluster, double* emag, double* ne
   return check_device_error(c);
 }
 
-md_status md_set_step(md_ctx* c, int64_t step) {
+md_status md_get_ionization(md_ctx* c, int32_t cluster, double* emag, double* ne, double* te,
+                            double* prob, uint8_t* fired) {
+  return md::guarded([&] { return md_get_ionization_body(c, cluster, emag, ne, te, prob, fired); });
+}
+
+static md_status md_set_step_body(md_ctx* c, int64_t step) {
   if (!c) return fail(MD_ERR_ARG, "ctx is NULL");
   if (step < 0) return fail(MD_ERR_ARG, "step < 0");
   // the j-stream buffer in use is selected by the parity of the step: move
@@ -1591,7 +1634,11 @@ md_status md_set_step(md_ctx* c, int64_t step) {
   return MD_OK;
 }
 
-md_status md_wait_selftest(md_ctx* c, double budget_ms) {
+md_status md_set_step(md_ctx* c, int64_t step) {
+  return md::guarded([&] { return md_set_step_body(c, step); });
+}
+
+static md_status md_wait_selftest_body(md_ctx* c, double budget_ms) {
   if (!c) return fail(MD_ERR_ARG, "ctx is NULL");
   if (!(budget_ms > 0.0) || budget_ms > 5000.0)
     return fail(MD_ERR_ARG, "budget_ms must be in (0, 5000]");
@@ -1603,7 +1650,11 @@ md_status md_wait_selftest(md_ctx* c, double budget_ms) {
   return check_device_error(c);
 }
 
-md_status md_set_slice(md_ctx* c, int32_t cluster, int64_t i_begin, int64_t i_end) {
+md_status md_wait_selftest(md_ctx* c, double budget_ms) {
+  return md::guarded([&] { return md_wait_selftest_body(c, budget_ms); });
+}
+
+static md_status md_set_slice_body(md_ctx* c, int32_t cluster, int64_t i_begin, int64_t i_end) {
   if (!c) return fail(MD_ERR_ARG, "ctx is NULL");
   if (cluster < 0 || cluster >= c->n_clusters) return fail(MD_ERR_ARG, "bad cluster index");
   const md::ClusterDev& cl = c->cl[cluster];
@@ -1626,7 +1677,11 @@ md_status md_set_slice(md_ctx* c, int32_t cluster, int64_t i_begin, int64_t i_en
   return configure(c, c->cfg, c->ctas_per_sm, c->jsplit);
 }
 
-md_status md_get_jstream(md_ctx* c, int32_t cluster, void** posq, int64_t* n_pad) {
+md_status md_set_slice(md_ctx* c, int32_t cluster, int64_t i_begin, int64_t i_end) {
+  return md::guarded([&] { return md_set_slice_body(c, cluster, i_begin, i_end); });
+}
+
+static md_status md_get_jstream_body(md_ctx* c, int32_t cluster, void** posq, int64_t* n_pad) {
   if (!c || !posq || !n_pad) return fail(MD_ERR_ARG, "NULL argument");
   if (cluster < 0 || cluster >= c->n_clusters) return fail(MD_ERR_ARG, "bad cluster index");
   long long step = 0;
@@ -1637,13 +1692,21 @@ md_status md_get_jstream(md_ctx* c, int32_t cluster, void** posq, int64_t* n_pad
   return check_device_error(c);
 }
 
-md_status md_get_step(md_ctx* c, int64_t* step) {
+md_status md_get_jstream(md_ctx* c, int32_t cluster, void** posq, int64_t* n_pad) {
+  return md::guarded([&] { return md_get_jstream_body(c, cluster, posq, n_pad); });
+}
+
+static md_status md_get_step_body(md_ctx* c, int64_t* step) {
   if (!c || !step) return fail(MD_ERR_ARG, "NULL argument");
   long long v = 0;
   MD_CUDA(cudaMemcpyAsync(&v, c->d_step, sizeof(v), cudaMemcpyDeviceToHost, c->stream));
   MD_CUDA(cudaStreamSynchronize(c->stream));
   *step = v;
   return MD_OK;
+}
+
+md_status md_get_step(md_ctx* c, int64_t* step) {
+  return md::guarded([&] { return md_get_step_body(c, step); });
 }
 
 static md_status run_fields(md_ctx* c, int ci, bool potential) {
@@ -1689,7 +1752,7 @@ static md_status run_fields(md_ctx* c, int ci, bool potential) {
   return MD_OK;
 }
 
-md_status md_get_fields(md_ctx* c, int32_t cluster, double* e, double* phi) {
+static md_status md_get_fields_body(md_ctx* c, int32_t cluster, double* e, double* phi) {
   if (!c || !e) return fail(MD_ERR_ARG, "NULL argument");
   if (cluster < 0 || cluster >= c->n_clusters) return fail(MD_ERR_ARG, "bad cluster index");
   md_status st = run_fields(c, cluster, phi != nullptr);
@@ -1706,7 +1769,11 @@ md_status md_get_fields(md_ctx* c, int32_t cluster, double* e, double* phi) {
   return check_device_error(c);
 }
 
-md_status md_count_active(md_ctx* c, int32_t cluster, int64_t* out) {
+md_status md_get_fields(md_ctx* c, int32_t cluster, double* e, double* phi) {
+  return md::guarded([&] { return md_get_fields_body(c, cluster, e, phi); });
+}
+
+static md_status md_count_active_body(md_ctx* c, int32_t cluster, int64_t* out) {
   if (!c || !out) return fail(MD_ERR_ARG, "NULL argument");
   if (cluster < 0 || cluster >= c->n_clusters) return fail(MD_ERR_ARG, "bad cluster index");
   MD_CUDA(md::launch_count_active(c->d_kind, c->cl[cluster].off, c->cl[cluster].n,
@@ -1718,6 +1785,10 @@ md_status md_count_active(md_ctx* c, int32_t cluster, int64_t* out) {
   if (st != MD_OK) return st;
   *out = static_cast<int64_t>(*c->h_word);
   return MD_OK;
+}
+
+md_status md_count_active(md_ctx* c, int32_t cluster, int64_t* out) {
+  return md::guarded([&] { return md_count_active_body(c, cluster, out); });
 }
 
 // md_diag of a cluster from its reduced partials, at step `step`.
@@ -1745,7 +1816,7 @@ md_status fill_diag(const md::DiagPartial& d, long long step, const md::ClusterD
   return MD_OK;
 }
 
-md_status md_diagnostics(md_ctx* c, int32_t cluster, md_diag* out) {
+static md_status md_diagnostics_body(md_ctx* c, int32_t cluster, md_diag* out) {
   if (!c || !out) return fail(MD_ERR_ARG, "NULL argument");
   if (cluster < 0 || cluster >= c->n_clusters) return fail(MD_ERR_ARG, "bad cluster index");
   md_status st = run_fields(c, cluster, true);
@@ -1778,13 +1849,17 @@ md_status md_diagnostics(md_ctx* c, int32_t cluster, md_diag* out) {
   return fill_diag(*c->h_diag, step, a.c, out);
 }
 
+md_status md_diagnostics(md_ctx* c, int32_t cluster, md_diag* out) {
+  return md::guarded([&] { return md_diagnostics_body(c, cluster, out); });
+}
+
 // One step of every cluster that also reports each cluster's diagnostics at
 // the start of the step: the step kernel's POT twin sums the potential beside
 // the field and records every record's diagnostics from its own kick, and an
 // O(N) reduction per cluster adds them in a fixed order.  Contexts with
 // ionization or detectors, and packed configurations, take the diagnostics
 // call and md_step(1) instead.
-md_status md_step_diag(md_ctx* c, md_diag* out) {
+static md_status md_step_diag_body(md_ctx* c, md_diag* out) {
   if (!c || !out) return fail(MD_ERR_ARG, "NULL argument");
   int ncfg = 0;
   const md::KernelConfig* cfgs = md::step_configs(&ncfg);
@@ -1847,7 +1922,11 @@ md_status md_step_diag(md_ctx* c, md_diag* out) {
   return worst != MD_OK ? fail(worst, "records hold NaN/Inf") : MD_OK;
 }
 
-md_status md_get_particles(md_ctx* c, int32_t cluster, md_particles* out) {
+md_status md_step_diag(md_ctx* c, md_diag* out) {
+  return md::guarded([&] { return md_step_diag_body(c, out); });
+}
+
+static md_status md_get_particles_body(md_ctx* c, int32_t cluster, md_particles* out) {
   if (!c || !out) return fail(MD_ERR_ARG, "NULL argument");
   if (cluster < 0 || cluster >= c->n_clusters) return fail(MD_ERR_ARG, "bad cluster index");
   const long long n = c->cl[cluster].n;
@@ -1901,7 +1980,11 @@ md_status md_get_particles(md_ctx* c, int32_t cluster, md_particles* out) {
   return check_device_error(c);
 }
 
-md_status md_set_particles(md_ctx* c, int32_t cluster, const md_particles* in) {
+md_status md_get_particles(md_ctx* c, int32_t cluster, md_particles* out) {
+  return md::guarded([&] { return md_get_particles_body(c, cluster, out); });
+}
+
+static md_status md_set_particles_body(md_ctx* c, int32_t cluster, const md_particles* in) {
   if (!c || !in) return fail(MD_ERR_ARG, "NULL argument");
   if (cluster < 0 || cluster >= c->n_clusters) return fail(MD_ERR_ARG, "bad cluster index");
   if (!c->ion[cluster].rate_model) {
@@ -1913,6 +1996,10 @@ md_status md_set_particles(md_ctx* c, int32_t cluster, const md_particles* in) {
   md_status st = validate_particles(*in, cluster, c->cl[cluster].n);
   if (st != MD_OK) return st;
   return upload_cluster(c, cluster, *in);
+}
+
+md_status md_set_particles(md_ctx* c, int32_t cluster, const md_particles* in) {
+  return md::guarded([&] { return md_set_particles_body(c, cluster, in); });
 }
 
 int32_t md_tuning_list(md_tuning* list, int32_t cap) {
@@ -1930,7 +2017,7 @@ int32_t md_tuning_list(md_tuning* list, int32_t cap) {
   return n;
 }
 
-md_status md_set_tuning(md_ctx* c, const md_tuning* t) {
+static md_status md_set_tuning_body(md_ctx* c, const md_tuning* t) {
   if (!c || !t) return fail(MD_ERR_ARG, "NULL argument");
   int n = 0;
   const md::KernelConfig* cfgs = md::step_configs(&n);
@@ -1947,7 +2034,11 @@ md_status md_set_tuning(md_ctx* c, const md_tuning* t) {
               t->threads, t->r, t->tile, t->packed);
 }
 
-md_status md_get_tuning(md_ctx* c, md_tuning* t) {
+md_status md_set_tuning(md_ctx* c, const md_tuning* t) {
+  return md::guarded([&] { return md_set_tuning_body(c, t); });
+}
+
+static md_status md_get_tuning_body(md_ctx* c, md_tuning* t) {
   if (!c || !t) return fail(MD_ERR_ARG, "NULL argument");
   int n = 0;
   const md::KernelConfig* cfgs = md::step_configs(&n);
@@ -1961,16 +2052,27 @@ md_status md_get_tuning(md_ctx* c, md_tuning* t) {
   return MD_OK;
 }
 
-md_status md_plan_shares(const int32_t* n_pad, int32_t n_clusters, int32_t per, int32_t tile,
-                         int64_t shares, int32_t* units, int64_t cap, int32_t* first,
-                         int64_t* n_units, int64_t* n_shares) {
+md_status md_get_tuning(md_ctx* c, md_tuning* t) {
+  return md::guarded([&] { return md_get_tuning_body(c, t); });
+}
+
+static md_status md_plan_shares_body(const int32_t* n_pad, int32_t n_clusters, int32_t per, int32_t tile,
+                                     int64_t shares, int32_t* units, int64_t cap, int32_t* first,
+                                     int64_t* n_units, int64_t* n_shares) {
   if (!n_pad || !n_units || !n_shares) return fail(MD_ERR_ARG, "NULL argument");
   if (n_clusters < 1 || per < 1 || tile < 1 || shares < 1 || cap < 0)
     return fail(MD_ERR_ARG, "need n_clusters, per, tile, shares >= 1 and cap >= 0");
+  if (shares > INT32_MAX) return fail(MD_ERR_ARG, "shares must be below 2^31");
+  long long T = 0;
+  for (int ci = 0; ci < n_clusters; ++ci) {
+    if (n_pad[ci] < 1) return fail(MD_ERR_ARG, "cluster %d: n_pad < 1", ci);
+    T += ((static_cast<long long>(n_pad[ci]) + per - 1) / per) *
+         ((static_cast<long long>(n_pad[ci]) + tile - 1) / tile);
+    if (T > INT32_MAX) return fail(MD_ERR_ARG, "more than 2^31 source tiles in all");
+  }
   std::vector<BlockSpan> blks;
   int ib = 0;
   for (int ci = 0; ci < n_clusters; ++ci) {
-    if (n_pad[ci] < 1) return fail(MD_ERR_ARG, "cluster %d: n_pad < 1", ci);
     const long long nb = (static_cast<long long>(n_pad[ci]) + per - 1) / per;
     const long long tiles = (static_cast<long long>(n_pad[ci]) + tile - 1) / tile;
     for (long long b = 0; b < nb; ++b, ++ib) blks.push_back({ci, static_cast<int>(b), ib, tiles, n_pad[ci]});
@@ -1999,7 +2101,13 @@ md_status md_plan_shares(const int32_t* n_pad, int32_t n_clusters, int32_t per, 
   return MD_OK;
 }
 
-md_status md_autotune(md_ctx* c, int32_t steps, double* times_ms, int32_t cap) {
+md_status md_plan_shares(const int32_t* n_pad, int32_t n_clusters, int32_t per, int32_t tile,
+                         int64_t shares, int32_t* units, int64_t cap, int32_t* first,
+                         int64_t* n_units, int64_t* n_shares) {
+  return md::guarded([&] { return md_plan_shares_body(n_pad, n_clusters, per, tile, shares, units, cap, first, n_units, n_shares); });
+}
+
+static md_status md_autotune_body(md_ctx* c, int32_t steps, double* times_ms, int32_t cap) {
   if (!c) return fail(MD_ERR_ARG, "ctx is NULL");
   if (steps < 1) return fail(MD_ERR_ARG, "steps < 1");
   const size_t N = static_cast<size_t>(c->n_total);
@@ -2115,10 +2223,14 @@ md_status md_autotune(md_ctx* c, int32_t steps, double* times_ms, int32_t cap) {
   return configure(c, best_cfg, 0, best_js);
 }
 
-md_status md_coulomb_field_fp64_device(const double* xs, const double* qs, int64_t ns,
-                                       const double* xt, const int64_t* self_idx, int64_t nt,
-                                       double eps, double kc, double* e, double* phi,
-                                       void* stream) {
+md_status md_autotune(md_ctx* c, int32_t steps, double* times_ms, int32_t cap) {
+  return md::guarded([&] { return md_autotune_body(c, steps, times_ms, cap); });
+}
+
+static md_status md_coulomb_field_fp64_device_body(const double* xs, const double* qs, int64_t ns,
+                                                   const double* xt, const int64_t* self_idx, int64_t nt,
+                                                   double eps, double kc, double* e, double* phi,
+                                                   void* stream) {
   if (ns < 0 || nt < 0) return fail(MD_ERR_ARG, "negative size");
   if (nt == 0) return MD_OK;
   if (!xs || !qs || !xt || !e) return fail(MD_ERR_ARG, "NULL pointer");
@@ -2128,9 +2240,16 @@ md_status md_coulomb_field_fp64_device(const double* xs, const double* qs, int64
   return MD_OK;
 }
 
-md_status md_coulomb_field_device(const void* src, int64_t ns, const void* tgt, int64_t nt,
-                                  float eps2, int64_t self_offset, double* e, double* phi,
-                                  void* stream) {
+md_status md_coulomb_field_fp64_device(const double* xs, const double* qs, int64_t ns,
+                                       const double* xt, const int64_t* self_idx, int64_t nt,
+                                       double eps, double kc, double* e, double* phi,
+                                       void* stream) {
+  return md::guarded([&] { return md_coulomb_field_fp64_device_body(xs, qs, ns, xt, self_idx, nt, eps, kc, e, phi, stream); });
+}
+
+static md_status md_coulomb_field_device_body(const void* src, int64_t ns, const void* tgt, int64_t nt,
+                                              float eps2, int64_t self_offset, double* e, double* phi,
+                                              void* stream) {
   if (ns < 0 || nt < 0) return fail(MD_ERR_ARG, "negative size");
   if (nt == 0) return MD_OK;
   if (!src || !tgt || !e) return fail(MD_ERR_ARG, "NULL pointer");
@@ -2185,7 +2304,13 @@ md_status md_coulomb_field_device(const void* src, int64_t ns, const void* tgt, 
   return MD_OK;
 }
 
-md_status md_measure_fp32_peak(double* ffma_per_s, double* packed_fma_per_s, void* stream) {
+md_status md_coulomb_field_device(const void* src, int64_t ns, const void* tgt, int64_t nt,
+                                  float eps2, int64_t self_offset, double* e, double* phi,
+                                  void* stream) {
+  return md::guarded([&] { return md_coulomb_field_device_body(src, ns, tgt, nt, eps2, self_offset, e, phi, stream); });
+}
+
+static md_status md_measure_fp32_peak_body(double* ffma_per_s, double* packed_fma_per_s, void* stream) {
   if (!ffma_per_s) return fail(MD_ERR_ARG, "NULL argument");
   int dev = 0, sms = 0;
   MD_CUDA(cudaGetDevice(&dev));
@@ -2218,6 +2343,10 @@ md_status md_measure_fp32_peak(double* ffma_per_s, double* packed_fma_per_s, voi
   *ffma_per_s = rate[0];
   if (packed_fma_per_s) *packed_fma_per_s = rate[1];
   return MD_OK;
+}
+
+md_status md_measure_fp32_peak(double* ffma_per_s, double* packed_fma_per_s, void* stream) {
+  return md::guarded([&] { return md_measure_fp32_peak_body(ffma_per_s, packed_fma_per_s, stream); });
 }
 
 }  // extern "C"

@@ -88,6 +88,8 @@ def test_small_plan_by_hand(md):
     ([100], 0, 256, 8),         # per < 1
     ([100], 128, 0, 8),         # tile < 1
     ([100], 128, 256, 0),       # shares < 1
+    ([100], 128, 256, 1 << 31),  # shares beyond int32
+    ([1 << 30, 1 << 30], 128, 256, 10),  # 2^31 or more source tiles in all
 ])
 def test_bad_arguments(md, args):
     with pytest.raises(md.MDError) as ei:
