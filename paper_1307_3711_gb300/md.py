@@ -466,6 +466,9 @@ class Context:
         return t.as_tuple()
 
     def set_tuning(self, threads, r, tile, ctas_per_sm=0, jsplit=0, packed=0, min_blocks=-1):
+        """md_set_tuning: one of tuning_list()'s configurations; jsplit > 0 that
+        many source segments per i-block, 0 a count chosen for balance, -k equal
+        shares, k per resident CTA (md_tuning in md.h)."""
         t = Tuning(threads, r, tile, ctas_per_sm, jsplit, packed, min_blocks)
         _check(_lib.md_set_tuning(self._h, C.byref(t)))
 
