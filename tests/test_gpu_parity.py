@@ -285,14 +285,14 @@ def test_diagnostics_parity_and_energy_conservation_2k(md):
     assert d1["charge_count"][1] == 1000
 
 
-@pytest.mark.parametrize("split", [1, 4])
+@pytest.mark.parametrize("split", [1, 4, -4])
 def test_diagnostic_step_equals_diagnostics_then_step(md, split):
     """md_step_diag sums the potential inside the step's Coulomb pass and takes
     the kinetic energy from the step's own kick: its diagnostics are those of
     md_diagnostics before the step (to FP32 summation order; the oracle's at
     step 0 for the 2k case), and the step it takes leaves the same state bit
-    for bit, with one or with 4 source segments per i-block, for a context of
-    two clusters."""
+    for bit, with one or with 4 source segments per i-block or with 4 equal
+    shares per CTA, for a context of two clusters."""
     ws = [synth.plain_fp64_2k(0), synth.xe3_cluster(30000, seed=9)]
     cfgs = [md.config_from_workload(w) for w in ws]
     out = []
@@ -578,7 +578,7 @@ def _box_gas(n_ions, n_el, L, seed):
     return x, u, z, mass, np.ones(n)
 
 
-@pytest.mark.parametrize("split", [1, 4])
+@pytest.mark.parametrize("split", [1, 4, -4])
 def test_min_image_field_step_and_diagnostics_follow_oracle(md, split):
     """Periodic cube with minimum-image forces (the optional image forces of
     the periodic boundary, Sec. II): the field and potential, one step's kick
