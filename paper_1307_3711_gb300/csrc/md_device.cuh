@@ -1230,6 +1230,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_step(const StepArgs a) {
         if (s_un.jn >= 0) {
           j0 = s_un.j0;
           jn = s_un.jn;
+          if (!MD_IN_RANGE(a.err, j0 + jn, 1, s_c.n_pad + 1)) jn = 0;  // a piece in the cluster
         } else {
           j0 = static_cast<long long>(s_un.seg) * s_c.seg_len;
           const long long jrem = s_c.n_pad - j0;

@@ -713,7 +713,7 @@ __device__ __forceinline__ int neighbour_bucket(const int (&cc)[3], int lane) {
 // memory (lane-strided over each bucket's electrons).
 __device__ __forceinline__ void moments_global(const CellBuf& cb, const float4 pi,
                                                const float4 ui, const int (&cc)[3], float eps2,
-                                               float rloc2e, int lane, MomSums& m) {
+                                               float rloc2e, int lane, MomSums& m, int* err) {
   const int bk = neighbour_bucket(cc, lane);
   unsigned todo = __ballot_sync(0xffffffffu, bk >= 0);
   while (todo) {
@@ -722,7 +722,8 @@ __device__ __forceinline__ void moments_global(const CellBuf& cb, const float4 p
     const int cell = __shfl_sync(0xffffffffu, bk, src);
     const int k1 = cb.start[cell + 1];
     for (int k = cb.start[cell] + lane; k < k1; k += 32)
-      if (near_loc(cb.rec[2 * k], pi, eps2, rloc2e)) m.add(cb.rec[2 * k + 1], ui);
+      if (MD_IN_RANGE(err, k, 0, cb.capacity) && near_loc(cb.rec[2 * k], pi, eps2, rloc2e))
+        m.add(cb.rec[2 * k + 1], ui);
   }
 }
 
@@ -790,8 +791,10 @@ __global__ void __launch_bounds__(kMomThreads) k_ion_moments(const IonArgs a) {
         if (cnt == 0) continue;
         const int k0 = cb.start[s_bk[l]], beg = s_beg[l];
         for (int k = tid; k < cnt; k += kMomThreads) {
-          s_pos[beg + k] = cb.rec[2 * (k0 + k)];
-          s_idx[beg + k] = k0 + k;
+          const bool ok = MD_IN_RANGE(a.err, k0 + k, 0, cb.capacity);
+          // (an index out of range stages a position no ion is near)
+          s_pos[beg + k] = ok ? cb.rec[2 * (k0 + k)] : make_float4(3e38f, 3e38f, 3e38f, 0.f);
+          s_idx[beg + k] = ok ? k0 + k : 0;
         }
       }
     }
@@ -828,7 +831,7 @@ __global__ void __launch_bounds__(kMomThreads) k_ion_moments(const IonArgs a) {
           if (lane < qn) m.add(cb.rec[2 * q[lane] + 1], ui);
           __syncwarp();
         } else {
-          moments_global(cb, pi, ui, cc, eps2, rloc2e, lane, m);
+          moments_global(cb, pi, ui, cc, eps2, rloc2e, lane, m, a.err);
         }
         m.warp_sum();
       }

@@ -1,7 +1,8 @@
 """The checked build (-DMD_CHECKED: device-side bounds checks that record an
 error instead of accessing memory out of range) on scenarios that exercise
-every checked access: split sources, ionization with slot assignment,
-detectors, a multi-cluster scan and graph replay.  It must report no bounds
+every checked access: split sources, ionization with slot assignment and the
+local moments' cell list, detectors, a multi-cluster scan with segments and
+with equal shares, and graph replay.  It must report no bounds
 error and give the same bits as the normal build."""
 import os
 import subprocess
@@ -53,6 +54,11 @@ for e in synth.batched_scan(24, seed=3, n_max=8000):
 with md.Context([md.config_from_workload(w) for w in ws],
                 [md.HostParticles.from_cluster(w.cluster) for w in ws]) as ctx:
     ctx.set_tuning(128, 4, 256, 0, 0, 1)
+    ctx.step(3)
+    for k in range(len(ws)):
+        feed(ctx.get_particles(k))
+    # the same scan with equal shares (pieces that cross i-blocks and clusters)
+    ctx.set_tuning(128, 8, 256, 0, -4, 1)
     ctx.step(3)
     for k in range(len(ws)):
         feed(ctx.get_particles(k))
