@@ -17,10 +17,11 @@
 //   * the laser field and the Boris kick are fused into the epilogue: the
 //     kick increment is evaluated in FP32, the integrator state (x, u) and the
 //     drift are FP64;
-//   * work units (cluster, i-block) are handed out by an atomic ticket to a
-//     persistent grid, so uneven clusters of a parameter scan share one launch;
-//     the last CTA to finish resets the ticket and advances the step counter,
-//     so a captured CUDA graph of many steps replays without host work.
+//   * shares of work units (cluster, i-block, piece of the sources) are
+//     handed out by an atomic ticket to a persistent grid, so uneven clusters
+//     of a parameter scan share one launch; the last CTA to finish resets the
+//     ticket and advances the step counter, so a captured CUDA graph of many
+//     steps replays without host work.
 // Every mbarrier wait is bounded by a clock64 budget; on expiry the kernel sets
 // an error bit, drains its own copies (again bounded) and returns.
 #pragma once
@@ -1167,9 +1168,10 @@ __device__ __forceinline__ void sum_partials(const double* p, long long stride, 
   }
 }
 
-// One full MD step for every work unit (cluster, i-block): field at x^n from
-// all sources of the cluster, laser at t_n, Boris kick, FP64 drift, boundary,
-// new j-stream entry.  Persistent: CTAs take units from an atomic ticket.
+// One full MD step for every work unit (cluster, i-block, piece): field at x^n
+// from the piece's sources, and once all pieces of an i-block are summed,
+// laser at t_n, Boris kick, FP64 drift, boundary, new j-stream entry.
+// Persistent: CTAs take shares (runs of units) from an atomic ticket.
 //
 // POT (scalar path only): a diagnostic step, which also sums the potential
 // phi_i beside the field (split segments add their phi partials in order)
