@@ -256,9 +256,8 @@ md_status md_diagnostics(md_ctx *ctx, int32_t cluster, md_diag *out);
  * step's Coulomb pass (one more FP32 add per pair) and the kinetic energy at
  * integer time comes from the step's own kick, so a diagnosed step costs
  * about one step instead of two N^2 passes.  Contexts with ionization or
- * detectors or minimum-image forces, and the packed kernel configurations,
- * use md_diagnostics and md_step instead (same results up to the order of
- * the FP32 sums).
+ * detectors or minimum-image forces use md_diagnostics and md_step instead
+ * (same results up to the order of the FP32 sums).
  * out: caller-owned md_diag[n_clusters].  Synchronous.  Errors: MD_ERR_ARG,
  * MD_ERR_NONFINITE (after the step) as md_diagnostics. */
 md_status md_step_diag(md_ctx *ctx, md_diag *out);

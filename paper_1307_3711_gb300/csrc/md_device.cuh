@@ -943,7 +943,7 @@ __device__ __forceinline__ bool sum_sources_packed(Stage<TILE, STAGES>& sm, DupT
         for (int k = 0; k < 4; ++k)
           pair2_u<P, POT>(lds_u64x2(dbase + 32u * (j + k)),
                           lds_u64x2(dbase + 32u * (j + k) + 16u), xi2, yi2, zi2, e2, a);
-        if (POT) {
+        if (POT && (j & 4)) {  // the potential is folded every 8 sources
 #pragma unroll
           for (int p = 0; p < P; ++p) {
             u64 sp = ks.v[6][p][tid], cp = ks.v[7][p][tid];
@@ -970,7 +970,7 @@ __device__ __forceinline__ bool sum_sources_packed(Stage<TILE, STAGES>& sm, DupT
         for (int k = 0; k < 4; ++k)
           pair2<P, POT>(lds_u64x2(dbase + 32u * (j + k)), lds_u64x2(dbase + 32u * (j + k) + 16u),
                         xi2, yi2, zi2, e2, a);
-        if (POT) {
+        if (POT && (j & 4)) {  // the potential is folded every 8 sources
 #pragma unroll
           for (int p = 0; p < P; ++p) {
             u64 sp = ks.v[6][p][tid], cp = ks.v[7][p][tid];
@@ -1173,20 +1173,19 @@ __device__ __forceinline__ void sum_partials(const double* p, long long stride, 
 // laser at t_n, Boris kick, FP64 drift, boundary, new j-stream entry.
 // Persistent: CTAs take shares (runs of units) from an atomic ticket.
 //
-// POT (scalar path only): a diagnostic step, which also sums the potential
-// phi_i beside the field (split segments add their phi partials in order)
-// and records every record's diagnostics at t_n (push_record's DIAG).
+// POT: a diagnostic step, which also sums the potential phi_i beside the
+// field (split pieces add their phi partials in order) and records every
+// record's diagnostics at t_n (push_record's DIAG).
 //
 // MI (scalar path only): clusters whose min_image flag is set sum
 // minimum-image displacements while their boundary is periodic.
 template <int THREADS, int R, int TILE, int STAGES, bool PACK, int MINB, bool DET,
           bool POT = false, bool MI = false>
 __global__ void __launch_bounds__(THREADS, MINB) k_step(const StepArgs a) {
-  static_assert(!(PACK && POT), "diagnostic steps use the scalar path");
   static_assert(!(PACK && MI), "minimum-image forces use the scalar path");
   __shared__ Stage<TILE, STAGES> sm;
   __shared__ DupTile<PACK ? TILE : 1> dup;
-  __shared__ KahanSmem<PACK ? R / 2 : 1, PACK ? THREADS : 1, false> ks;
+  __shared__ KahanSmem<PACK ? R / 2 : 1, PACK ? THREADS : 1, POT> ks;
   __shared__ int s_unit, s_abort, s_last;
   __shared__ float s_las[6];
   // the current unit's cluster and ranges live in shared memory, not in
@@ -1250,7 +1249,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_step(const StepArgs a) {
         bool ok;
         Acc<R, POT> acc;
         if constexpr (PACK) {
-          ok = sum_sources_packed<THREADS, R, TILE, STAGES, false>(
+          ok = sum_sources_packed<THREADS, R, TILE, STAGES, POT>(
               sm, dup, ks, it, cur + s_c.off + j0, jn, xi, yi, zi, s_c.eps2, a.err, &s_abort,
               a.src_live, s_c.off + j0);
         } else {
@@ -1292,6 +1291,15 @@ __global__ void __launch_bounds__(THREADS, MINB) k_step(const StepArgs a) {
             ez = -(static_cast<double>(acc.sz[r]) - acc.cz[r]);
           }
         };
+        // POT: the potential's Kahan total (s - c) at target r
+        auto phi_of = [&](int r) -> double {
+          if constexpr (PACK && POT)
+            return static_cast<double>(kahan_part(ks, 6, r)) - kahan_part(ks, 7, r);
+          else if constexpr (POT)
+            return static_cast<double>(acc.sp[r]) - acc.cp[r];
+          else
+            return 0.0;
+        };
 
         // the unit's ranges are re-read from shared memory after the loop
         const float4* __restrict__ cur2 = (step & 1) ? a.posq1 : a.posq0;
@@ -1310,7 +1318,13 @@ __global__ void __launch_bounds__(THREADS, MINB) k_step(const StepArgs a) {
               if (i >= eend) continue;
               double ex, ey, ez;
               field_of(r, ex, ey, ez);
-              push_record<DET>(a, s_c, i, ex, ey, ez, s_las, t_next, cur2, nxt);
+              if constexpr (POT) {
+                const double ph =
+                    phi_of(r) - static_cast<double>(cur2[i].w * rsqrt_mufu(s_c.eps2));
+                push_record<DET, true>(a, s_c, i, ex, ey, ez, s_las, t_next, cur2, nxt, ph);
+              } else {
+                push_record<DET>(a, s_c, i, ex, ey, ez, s_las, t_next, cur2, nxt);
+              }
             }
           } else {
 #pragma unroll
@@ -1321,8 +1335,8 @@ __global__ void __launch_bounds__(THREADS, MINB) k_step(const StepArgs a) {
               field_of(r, ex, ey, ez);
               if constexpr (POT) {
                 // the potential without the record's own term
-                const double ph = (static_cast<double>(acc.sp[r]) - acc.cp[r]) -
-                                  static_cast<double>(cur2[i].w * rsqrt_mufu(s_c.eps2));
+                const double ph =
+                    phi_of(r) - static_cast<double>(cur2[i].w * rsqrt_mufu(s_c.eps2));
                 push_record<DET, true>(a, s_c, i, ex, ey, ez, s_las, t_next, cur2, nxt, ph);
               } else {
                 push_record<DET>(a, s_c, i, ex, ey, ez, s_las, t_next, cur2, nxt);
@@ -1347,8 +1361,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_step(const StepArgs a) {
             __stcg(p + 1, ey);
             __stcg(p + 2, ez);
             if constexpr (POT)
-              __stcg(a.part_phi + static_cast<long long>(seg) * a.n_total + i,
-                     static_cast<double>(acc.sp[r]) - acc.cp[r]);
+              __stcg(a.part_phi + static_cast<long long>(seg) * a.n_total + i, phi_of(r));
           }
           __threadfence();
           __syncthreads();

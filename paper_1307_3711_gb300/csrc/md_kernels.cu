@@ -192,17 +192,17 @@ cudaError_t launch_step_t(const StepArgs& a, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// the diagnostic step (potential summed beside the field), scalar path
-template <int T, int R, int TILE, int ST, int MB>
+// the diagnostic step (potential summed beside the field)
+template <int T, int R, int TILE, int ST, bool PK, int MB>
 cudaError_t launch_step_pot_t(const StepArgs& a, int grid, cudaStream_t s) {
-  k_step<T, R, TILE, ST, false, MB, false, true><<<grid, T, 0, s>>>(a);
+  k_step<T, R, TILE, ST, PK, MB, false, true><<<grid, T, 0, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int T, int R, int TILE, int ST, int MB>
+template <int T, int R, int TILE, int ST, bool PK, int MB>
 cudaError_t blocks_per_sm_pot_t(int* out) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      out, k_step<T, R, TILE, ST, false, MB, false, true>, T, 0);
+      out, k_step<T, R, TILE, ST, PK, MB, false, true>, T, 0);
 }
 
 // minimum-image forces (periodic clusters with min_image), scalar path
@@ -235,14 +235,15 @@ cudaError_t blocks_per_sm_t(int* out) {
   {T, R, TILE, ST, PK, MB, &launch_step_t<T, R, TILE, ST, PK, MB, false>,              \
    &blocks_per_sm_t<T, R, TILE, ST, PK, MB, false>,                                      \
    &launch_step_t<T, R, TILE, ST, PK, MB, true>, &blocks_per_sm_t<T, R, TILE, ST, PK, MB, true>, \
-   nullptr, nullptr, nullptr, nullptr, nullptr, nullptr}
-// scalar configurations also have the diagnostic step and minimum-image forces
+   &launch_step_pot_t<T, R, TILE, ST, PK, MB>, &blocks_per_sm_pot_t<T, R, TILE, ST, PK, MB>,    \
+   nullptr, nullptr, nullptr, nullptr}
+// scalar configurations also have minimum-image forces
 #define MD_STEP_CONFIG_POT(T, R, TILE, ST, MB)                                          \
   {T, R, TILE, ST, false, MB, &launch_step_t<T, R, TILE, ST, false, MB, false>,          \
    &blocks_per_sm_t<T, R, TILE, ST, false, MB, false>,                                   \
    &launch_step_t<T, R, TILE, ST, false, MB, true>,                                      \
    &blocks_per_sm_t<T, R, TILE, ST, false, MB, true>,                                    \
-   &launch_step_pot_t<T, R, TILE, ST, MB>, &blocks_per_sm_pot_t<T, R, TILE, ST, MB>,        \
+   &launch_step_pot_t<T, R, TILE, ST, false, MB>, &blocks_per_sm_pot_t<T, R, TILE, ST, false, MB>, \
    &launch_step_mi_t<T, R, TILE, ST, MB>, &blocks_per_sm_mi_t<T, R, TILE, ST, MB>,          \
    &launch_step_mi_det_t<T, R, TILE, ST, MB>, &blocks_per_sm_mi_t<T, R, TILE, ST, MB, true>}
 

@@ -1857,8 +1857,8 @@ md_status md_diagnostics(md_ctx* c, int32_t cluster, md_diag* out) {
 // the start of the step: the step kernel's POT twin sums the potential beside
 // the field and records every record's diagnostics from its own kick, and an
 // O(N) reduction per cluster adds them in a fixed order.  Contexts with
-// ionization or detectors, and packed configurations, take the diagnostics
-// call and md_step(1) instead.
+// ionization, detectors or minimum-image forces take the diagnostics call
+// and md_step(1) instead.
 static md_status md_step_diag_body(md_ctx* c, md_diag* out) {
   if (!c || !out) return fail(MD_ERR_ARG, "NULL argument");
   int ncfg = 0;

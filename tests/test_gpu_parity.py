@@ -285,20 +285,21 @@ def test_diagnostics_parity_and_energy_conservation_2k(md):
     assert d1["charge_count"][1] == 1000
 
 
-@pytest.mark.parametrize("split", [1, 4, -4])
-def test_diagnostic_step_equals_diagnostics_then_step(md, split):
+@pytest.mark.parametrize("split,packed", [(1, 0), (4, 0), (-4, 0), (1, 1), (-4, 1)])
+def test_diagnostic_step_equals_diagnostics_then_step(md, split, packed):
     """md_step_diag sums the potential inside the step's Coulomb pass and takes
     the kinetic energy from the step's own kick: its diagnostics are those of
     md_diagnostics before the step (to FP32 summation order; the oracle's at
     step 0 for the 2k case), and the step it takes leaves the same state bit
     for bit, with one or with 4 source segments per i-block or with 4 equal
-    shares per CTA, for a context of two clusters."""
+    shares per CTA, on the scalar and the packed path, for a context of two
+    clusters."""
     ws = [synth.plain_fp64_2k(0), synth.xe3_cluster(30000, seed=9)]
     cfgs = [md.config_from_workload(w) for w in ws]
     out = []
     for fused in (False, True):
         with md.Context(cfgs, [md.HostParticles.from_cluster(w.cluster) for w in ws]) as ctx:
-            ctx.set_tuning(128, 4, 512, 0, split, 0)
+            ctx.set_tuning(128, 4, 512, 0, split, packed)
             ctx.step(3)
             if fused:
                 d = ctx.step_diag()
