@@ -27,6 +27,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "md_types.cuh"
@@ -751,6 +752,13 @@ __device__ __forceinline__ void kahan_add2(u64& s, u64& c, u64 v) {
   s = t;
 }
 
+// min_image of both lanes: mi = (-L, 1/L, 1.5 2^23) packed; the same three
+// rounded operations per lane as the scalar min_image.
+__device__ __forceinline__ u64 f2_min_image(u64 d, const u64 (&mi)[3]) {
+  const u64 k = f2_sub(f2_fma(d, mi[1], mi[2]), mi[2]);
+  return f2_fma(mi[0], k, d);
+}
+
 // A tile of sources expanded for packed use: per source (x,x | y,y) and
 // (z,z | q,q), so one LDS.128 yields two ready register pairs.
 template <int TILE>
@@ -793,15 +801,20 @@ __device__ __forceinline__ float kahan_part(const KahanSmem<P, THREADS, POT>& ks
   return (r & 1) ? hi : lo;
 }
 
-template <int P, bool POT>
+template <int P, bool POT, bool IMG = false>
 __device__ __forceinline__ void pair2(const ulonglong2 xy, const ulonglong2 zq, const u64 (&xi)[P],
                                       const u64 (&yi)[P], const u64 (&zi)[P], u64 e2,
-                                      AccP<P, POT>& a) {
+                                      AccP<P, POT>& a, const u64 (&mi)[3]) {
 #pragma unroll
   for (int p = 0; p < P; ++p) {
-    const u64 dx = f2_sub(xy.x, xi[p]);
-    const u64 dy = f2_sub(xy.y, yi[p]);
-    const u64 dz = f2_sub(zq.x, zi[p]);
+    u64 dx = f2_sub(xy.x, xi[p]);
+    u64 dy = f2_sub(xy.y, yi[p]);
+    u64 dz = f2_sub(zq.x, zi[p]);
+    if constexpr (IMG) {
+      dx = f2_min_image(dx, mi);
+      dy = f2_min_image(dy, mi);
+      dz = f2_min_image(dz, mi);
+    }
     u64 r2 = f2_fma(dx, dx, e2);
     r2 = f2_fma(dy, dy, r2);
     r2 = f2_fma(dz, dz, r2);
@@ -819,15 +832,21 @@ __device__ __forceinline__ void pair2(const ulonglong2 xy, const ulonglong2 zq, 
 }
 
 // pair2 for a tile of one charge (see pair_u): no charge multiply per pair.
-template <int P, bool POT>
+template <int P, bool POT, bool IMG = false>
 __device__ __forceinline__ void pair2_u(const ulonglong2 xy, const ulonglong2 zq,
                                         const u64 (&xi)[P], const u64 (&yi)[P],
-                                        const u64 (&zi)[P], u64 e2, AccP<P, POT>& a) {
+                                        const u64 (&zi)[P], u64 e2, AccP<P, POT>& a,
+                                        const u64 (&mi)[3]) {
 #pragma unroll
   for (int p = 0; p < P; ++p) {
-    const u64 dx = f2_sub(xy.x, xi[p]);
-    const u64 dy = f2_sub(xy.y, yi[p]);
-    const u64 dz = f2_sub(zq.x, zi[p]);
+    u64 dx = f2_sub(xy.x, xi[p]);
+    u64 dy = f2_sub(xy.y, yi[p]);
+    u64 dz = f2_sub(zq.x, zi[p]);
+    if constexpr (IMG) {
+      dx = f2_min_image(dx, mi);
+      dy = f2_min_image(dy, mi);
+      dz = f2_min_image(dz, mi);
+    }
     u64 r2 = f2_fma(dx, dx, e2);
     r2 = f2_fma(dy, dy, r2);
     r2 = f2_fma(dz, dz, r2);
@@ -847,10 +866,12 @@ __device__ __forceinline__ void pair2_u(const ulonglong2 xy, const ulonglong2 zq
 // tile is first expanded into `dup` (which frees its TMA stage at once, so a
 // single stage suffices), then the R targets of this thread are summed two at
 // a time, four sources per unrolled step (eight were 0.2 % slower and sixteen
-// 11 %: the loop's code outgrows the instruction cache).  The Kahan sums live in `ks` (bit-identical to the scalar path's);
-// reset = false continues the sums of an earlier call instead of clearing
-// them.
-template <int THREADS, int R, int TILE, int STAGES, bool POT>
+// 11 %: the loop's code outgrows the instruction cache).  The Kahan sums live
+// in `ks` (bit-identical to the scalar path's); reset = false continues the
+// sums of an earlier call instead of clearing them.  MI: as sum_sources, a
+// tile some of whose pairs may lie half a box apart (targets' bounds tb)
+// takes minimum-image displacements in the cube of side L.
+template <int THREADS, int R, int TILE, int STAGES, bool POT, bool MI = false>
 __device__ __forceinline__ bool sum_sources_packed(Stage<TILE, STAGES>& sm, DupTile<TILE>& dup,
                                                    KahanSmem<R / 2, THREADS, POT>& ks, unsigned& it,
                                                    const float4* __restrict__ src, long long ns,
@@ -858,7 +879,9 @@ __device__ __forceinline__ bool sum_sources_packed(Stage<TILE, STAGES>& sm, DupT
                                                    const float (&zi)[R], float eps2, int* err,
                                                    int* s_abort,
                                                    const unsigned char* live = nullptr,
-                                                   long long gbase = 0, bool reset = true) {
+                                                   long long gbase = 0, bool reset = true,
+                                                   float L = 0.0f, float invL = 0.0f,
+                                                   const float* tb = nullptr) {
   static_assert(R % 2 == 0, "packed path needs an even number of i-particles per thread");
   constexpr int P = R / 2;
   const int tid = threadIdx.x;
@@ -880,6 +903,16 @@ __device__ __forceinline__ bool sum_sources_packed(Stage<TILE, STAGES>& sm, DupT
   }
   ks.e2[tid] = f2_pack(eps2, eps2);
   const u64 e2 = lds_u64(smem_u32(&ks.e2[tid]));
+  // MI: the packed minimum-image constants, loaded as register pairs
+  u64 mi[3] = {0ull, 0ull, 0ull};
+  if constexpr (MI) {
+    __shared__ u64 s_mi[3][THREADS];
+    s_mi[0][tid] = f2_pack(-L, -L);
+    s_mi[1][tid] = f2_pack(invL, invL);
+    s_mi[2][tid] = f2_pack(12582912.0f, 12582912.0f);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) mi[k] = lds_u64(smem_u32(&s_mi[k][tid]));
+  }
   const int ntiles = static_cast<int>((ns + TILE - 1) / TILE);
   // live tiles only, in the same order for the issuing thread and the consumers
   int t = next_live_tile(live, gbase, ns, 0, ntiles, TILE);
@@ -904,8 +937,10 @@ __device__ __forceinline__ bool sum_sources_packed(Stage<TILE, STAGES>& sm, DupT
     const int cnt = static_cast<int>(rem < TILE ? rem : TILE);
     float qt = 0.0f;
     bool uni = false;
+    bool img = false;  // MI: some pair of this tile may be half a box apart
     if (!*reinterpret_cast<volatile int*>(s_abort)) {
       uni = tile_uniform_q(smem_u32(&sm.tile[s][0]), cnt, qt);
+      if constexpr (MI) img = tile_needs_image(smem_u32(&sm.tile[s][0]), cnt, tb, L);
       for (int k = tid; k < cnt; k += THREADS) {
         const float4 p = sm.tile[s][k];
         dup.v[k][0] = make_ulonglong2(f2_pack(p.x, p.x), f2_pack(p.y, p.y));
@@ -936,55 +971,65 @@ __device__ __forceinline__ bool sum_sources_packed(Stage<TILE, STAGES>& sm, DupT
       continue;
     }
     const u64 qq = f2_pack(qt, qt);
-    int j = 0;
-    if (uni) {
-      for (; j + 4 <= cnt; j += 4) {
+    // the tile's pairs; IMG: with minimum-image displacements
+    auto sum_tile2 = [&](auto img_tag) {
+      constexpr bool IMG = decltype(img_tag)::value;
+      int j = 0;
+      if (uni) {
+        for (; j + 4 <= cnt; j += 4) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-          pair2_u<P, POT>(lds_u64x2(dbase + 32u * (j + k)),
-                          lds_u64x2(dbase + 32u * (j + k) + 16u), xi2, yi2, zi2, e2, a);
-        if (POT && (j & 4)) {  // the potential is folded every 8 sources
+          for (int k = 0; k < 4; ++k)
+            pair2_u<P, POT, IMG>(lds_u64x2(dbase + 32u * (j + k)),
+                                 lds_u64x2(dbase + 32u * (j + k) + 16u), xi2, yi2, zi2, e2, a,
+                                 mi);
+          if (POT && (j & 4)) {  // the potential is folded every 8 sources
 #pragma unroll
-          for (int p = 0; p < P; ++p) {
-            u64 sp = ks.v[6][p][tid], cp = ks.v[7][p][tid];
-            kahan_add2(sp, cp, f2_mul(a.ap[p], qq));
-            ks.v[6][p][tid] = sp;
-            ks.v[7][p][tid] = cp;
-            a.ap[p] = 0ull;
+            for (int p = 0; p < P; ++p) {
+              u64 sp = ks.v[6][p][tid], cp = ks.v[7][p][tid];
+              kahan_add2(sp, cp, f2_mul(a.ap[p], qq));
+              ks.v[6][p][tid] = sp;
+              ks.v[7][p][tid] = cp;
+              a.ap[p] = 0ull;
+            }
           }
         }
-      }
-      for (; j < cnt; ++j)
-        pair2_u<P, POT>(lds_u64x2(dbase + 32u * j), lds_u64x2(dbase + 32u * j + 16u), xi2, yi2,
-                        zi2, e2, a);
+        for (; j < cnt; ++j)
+          pair2_u<P, POT, IMG>(lds_u64x2(dbase + 32u * j), lds_u64x2(dbase + 32u * j + 16u), xi2,
+                               yi2, zi2, e2, a, mi);
 #pragma unroll
-      for (int p = 0; p < P; ++p) {
-        a.ax[p] = f2_mul(a.ax[p], qq);
-        a.ay[p] = f2_mul(a.ay[p], qq);
-        a.az[p] = f2_mul(a.az[p], qq);
-        if (POT) a.ap[p] = f2_mul(a.ap[p], qq);
-      }
-    } else {
-      for (; j + 4 <= cnt; j += 4) {
+        for (int p = 0; p < P; ++p) {
+          a.ax[p] = f2_mul(a.ax[p], qq);
+          a.ay[p] = f2_mul(a.ay[p], qq);
+          a.az[p] = f2_mul(a.az[p], qq);
+          if (POT) a.ap[p] = f2_mul(a.ap[p], qq);
+        }
+      } else {
+        for (; j + 4 <= cnt; j += 4) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-          pair2<P, POT>(lds_u64x2(dbase + 32u * (j + k)), lds_u64x2(dbase + 32u * (j + k) + 16u),
-                        xi2, yi2, zi2, e2, a);
-        if (POT && (j & 4)) {  // the potential is folded every 8 sources
+          for (int k = 0; k < 4; ++k)
+            pair2<P, POT, IMG>(lds_u64x2(dbase + 32u * (j + k)),
+                               lds_u64x2(dbase + 32u * (j + k) + 16u), xi2, yi2, zi2, e2, a,
+                               mi);
+          if (POT && (j & 4)) {  // the potential is folded every 8 sources
 #pragma unroll
-          for (int p = 0; p < P; ++p) {
-            u64 sp = ks.v[6][p][tid], cp = ks.v[7][p][tid];
-            kahan_add2(sp, cp, a.ap[p]);
-            ks.v[6][p][tid] = sp;
-            ks.v[7][p][tid] = cp;
-            a.ap[p] = 0ull;
+            for (int p = 0; p < P; ++p) {
+              u64 sp = ks.v[6][p][tid], cp = ks.v[7][p][tid];
+              kahan_add2(sp, cp, a.ap[p]);
+              ks.v[6][p][tid] = sp;
+              ks.v[7][p][tid] = cp;
+              a.ap[p] = 0ull;
+            }
           }
         }
+        for (; j < cnt; ++j)
+          pair2<P, POT, IMG>(lds_u64x2(dbase + 32u * j), lds_u64x2(dbase + 32u * j + 16u), xi2, yi2,
+                             zi2, e2, a, mi);
       }
-      for (; j < cnt; ++j)
-        pair2<P, POT>(lds_u64x2(dbase + 32u * j), lds_u64x2(dbase + 32u * j + 16u), xi2, yi2,
-                      zi2, e2, a);
-    }
+    };
+    if (MI && img)
+      sum_tile2(std::integral_constant<bool, MI>{});
+    else
+      sum_tile2(std::false_type{});
 #pragma unroll
     for (int p = 0; p < P; ++p) {
       u64 sv, cv;
@@ -1177,12 +1222,11 @@ __device__ __forceinline__ void sum_partials(const double* p, long long stride, 
 // field (split pieces add their phi partials in order) and records every
 // record's diagnostics at t_n (push_record's DIAG).
 //
-// MI (scalar path only): clusters whose min_image flag is set sum
-// minimum-image displacements while their boundary is periodic.
+// MI: clusters whose min_image flag is set sum minimum-image displacements
+// while their boundary is periodic.
 template <int THREADS, int R, int TILE, int STAGES, bool PACK, int MINB, bool DET,
           bool POT = false, bool MI = false>
 __global__ void __launch_bounds__(THREADS, MINB) k_step(const StepArgs a) {
-  static_assert(!(PACK && MI), "minimum-image forces use the scalar path");
   __shared__ Stage<TILE, STAGES> sm;
   __shared__ DupTile<PACK ? TILE : 1> dup;
   __shared__ KahanSmem<PACK ? R / 2 : 1, PACK ? THREADS : 1, POT> ks;
@@ -1248,17 +1292,29 @@ __global__ void __launch_bounds__(THREADS, MINB) k_step(const StepArgs a) {
         }
         bool ok;
         Acc<R, POT> acc;
+        // MI: minimum-image forces while this cluster's boundary is periodic at t_n
+        bool mi = false;
+        if constexpr (MI) {
+          const double t_n = s_c.t0 + static_cast<double>(step) * s_c.dt;
+          mi = a.min_image && a.min_image[s_un.cluster] &&
+               (s_c.boundary == 1 || (s_c.boundary == 2 && t_n < s_c.t_switch));
+        }
         if constexpr (PACK) {
-          ok = sum_sources_packed<THREADS, R, TILE, STAGES, POT>(
-              sm, dup, ks, it, cur + s_c.off + j0, jn, xi, yi, zi, s_c.eps2, a.err, &s_abort,
-              a.src_live, s_c.off + j0);
+          if (MI && mi) {
+            __shared__ float s_tb2[6];  // bounds of this unit's targets
+            target_bounds<THREADS, R>(xi, yi, zi, s_tb2);
+            const float L = static_cast<float>(s_c.box);
+            ok = sum_sources_packed<THREADS, R, TILE, STAGES, POT, MI>(
+                sm, dup, ks, it, cur + s_c.off + j0, jn, xi, yi, zi, s_c.eps2, a.err, &s_abort,
+                a.src_live, s_c.off + j0, true, L, 1.0f / L, s_tb2);
+          } else {
+            ok = sum_sources_packed<THREADS, R, TILE, STAGES, POT>(
+                sm, dup, ks, it, cur + s_c.off + j0, jn, xi, yi, zi, s_c.eps2, a.err, &s_abort,
+                a.src_live, s_c.off + j0);
+          }
         } else {
           acc.zero();
           if constexpr (MI) {
-            // minimum-image forces while this cluster's boundary is periodic at t_n
-            const double t_n = s_c.t0 + static_cast<double>(step) * s_c.dt;
-            const bool mi = a.min_image && a.min_image[s_un.cluster] &&
-                            (s_c.boundary == 1 || (s_c.boundary == 2 && t_n < s_c.t_switch));
             if (mi) {
               __shared__ float s_tb[6];  // bounds of this unit's targets
               target_bounds<THREADS, R>(xi, yi, zi, s_tb);

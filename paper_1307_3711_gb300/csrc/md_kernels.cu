@@ -205,22 +205,22 @@ cudaError_t blocks_per_sm_pot_t(int* out) {
       out, k_step<T, R, TILE, ST, PK, MB, false, true>, T, 0);
 }
 
-// minimum-image forces (periodic clusters with min_image), scalar path
-template <int T, int R, int TILE, int ST, int MB>
+// minimum-image forces (periodic clusters with min_image)
+template <int T, int R, int TILE, int ST, bool PK, int MB>
 cudaError_t launch_step_mi_t(const StepArgs& a, int grid, cudaStream_t s) {
-  k_step<T, R, TILE, ST, false, MB, false, false, true><<<grid, T, 0, s>>>(a);
+  k_step<T, R, TILE, ST, PK, MB, false, false, true><<<grid, T, 0, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int T, int R, int TILE, int ST, int MB, bool DET = false>
+template <int T, int R, int TILE, int ST, bool PK, int MB, bool DET = false>
 cudaError_t blocks_per_sm_mi_t(int* out) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      out, k_step<T, R, TILE, ST, false, MB, DET, false, true>, T, 0);
+      out, k_step<T, R, TILE, ST, PK, MB, DET, false, true>, T, 0);
 }
 
-template <int T, int R, int TILE, int ST, int MB>
+template <int T, int R, int TILE, int ST, bool PK, int MB>
 cudaError_t launch_step_mi_det_t(const StepArgs& a, int grid, cudaStream_t s) {
-  k_step<T, R, TILE, ST, false, MB, true, false, true><<<grid, T, 0, s>>>(a);
+  k_step<T, R, TILE, ST, PK, MB, true, false, true><<<grid, T, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -237,15 +237,25 @@ cudaError_t blocks_per_sm_t(int* out) {
    &launch_step_t<T, R, TILE, ST, PK, MB, true>, &blocks_per_sm_t<T, R, TILE, ST, PK, MB, true>, \
    &launch_step_pot_t<T, R, TILE, ST, PK, MB>, &blocks_per_sm_pot_t<T, R, TILE, ST, PK, MB>,    \
    nullptr, nullptr, nullptr, nullptr}
-// scalar configurations also have minimum-image forces
+// ... and with minimum-image forces
+#define MD_STEP_CONFIG_MI(T, R, TILE, ST, PK, MB)                                       \
+  {T, R, TILE, ST, PK, MB, &launch_step_t<T, R, TILE, ST, PK, MB, false>,              \
+   &blocks_per_sm_t<T, R, TILE, ST, PK, MB, false>,                                      \
+   &launch_step_t<T, R, TILE, ST, PK, MB, true>, &blocks_per_sm_t<T, R, TILE, ST, PK, MB, true>, \
+   &launch_step_pot_t<T, R, TILE, ST, PK, MB>, &blocks_per_sm_pot_t<T, R, TILE, ST, PK, MB>,    \
+   &launch_step_mi_t<T, R, TILE, ST, PK, MB>, &blocks_per_sm_mi_t<T, R, TILE, ST, PK, MB>,      \
+   &launch_step_mi_det_t<T, R, TILE, ST, PK, MB>,                                        \
+   &blocks_per_sm_mi_t<T, R, TILE, ST, PK, MB, true>}
+// scalar configurations (all with minimum-image forces)
 #define MD_STEP_CONFIG_POT(T, R, TILE, ST, MB)                                          \
   {T, R, TILE, ST, false, MB, &launch_step_t<T, R, TILE, ST, false, MB, false>,          \
    &blocks_per_sm_t<T, R, TILE, ST, false, MB, false>,                                   \
    &launch_step_t<T, R, TILE, ST, false, MB, true>,                                      \
    &blocks_per_sm_t<T, R, TILE, ST, false, MB, true>,                                    \
    &launch_step_pot_t<T, R, TILE, ST, false, MB>, &blocks_per_sm_pot_t<T, R, TILE, ST, false, MB>, \
-   &launch_step_mi_t<T, R, TILE, ST, MB>, &blocks_per_sm_mi_t<T, R, TILE, ST, MB>,          \
-   &launch_step_mi_det_t<T, R, TILE, ST, MB>, &blocks_per_sm_mi_t<T, R, TILE, ST, MB, true>}
+   &launch_step_mi_t<T, R, TILE, ST, false, MB>, &blocks_per_sm_mi_t<T, R, TILE, ST, false, MB>, \
+   &launch_step_mi_det_t<T, R, TILE, ST, false, MB>,                                     \
+   &blocks_per_sm_mi_t<T, R, TILE, ST, false, MB, true>}
 
 // min CTAs per SM = 0 leaves the register budget to ptxas; a positive value
 // caps it at 64K / (threads x value)
@@ -256,8 +266,8 @@ const KernelConfig kConfigs[] = {
     MD_STEP_CONFIG_POT(256, 4, 512, 2, 0),
     // packed f32x2 pair arithmetic (tile expanded in shared memory, one TMA stage)
     MD_STEP_CONFIG(128, 4, 256, 1, true, 0), MD_STEP_CONFIG(256, 4, 256, 1, true, 0),
-    MD_STEP_CONFIG(128, 8, 256, 1, true, 0), MD_STEP_CONFIG(128, 4, 512, 1, true, 0),
-    MD_STEP_CONFIG(256, 4, 512, 1, true, 0), MD_STEP_CONFIG(128, 8, 512, 1, true, 0),
+    MD_STEP_CONFIG_MI(128, 8, 256, 1, true, 0), MD_STEP_CONFIG(128, 4, 512, 1, true, 0),
+    MD_STEP_CONFIG_MI(256, 4, 512, 1, true, 0), MD_STEP_CONFIG(128, 8, 512, 1, true, 0),
     // the same with the registers capped for 3 CTAs per SM
     MD_STEP_CONFIG(128, 8, 512, 1, true, 3),
 };

@@ -579,14 +579,17 @@ def _box_gas(n_ions, n_el, L, seed):
     return x, u, z, mass, np.ones(n)
 
 
-@pytest.mark.parametrize("split", [1, 4, -4])
-def test_min_image_field_step_and_diagnostics_follow_oracle(md, split):
+@pytest.mark.parametrize("split,tuning", [(1, (128, 4, 512, 0)), (4, (128, 4, 512, 0)),
+                                          (-4, (128, 4, 512, 0)), (1, (128, 8, 256, 1)),
+                                          (-4, (128, 8, 256, 1))])
+def test_min_image_field_step_and_diagnostics_follow_oracle(md, split, tuning):
     """Periodic cube with minimum-image forces (the optional image forces of
     the periodic boundary, Sec. II): the field and potential, one step's kick
     and drift, and the diagnostics follow the FP64 oracle's minimum-image sums
     for a gas spread over the whole cube (many pairs meet through the faces),
-    with one or 4 source segments; a periodic translation of the gas leaves
-    the GPU's field unchanged, and the field without image forces differs."""
+    with one or 4 source segments or equal shares, on the scalar and the
+    packed path; a periodic translation of the gas leaves the GPU's field
+    unchanged, and the field without image forces differs."""
     L, eps, kc = 0.05, 1e-3, oracle.coulomb_constant(0.8)
     x, u, z, mass, w = _box_gas(1000, 3000, L, 31)
     q = w * z
@@ -596,7 +599,7 @@ def test_min_image_field_step_and_diagnostics_follow_oracle(md, split):
                              t_switch=t_switch, envelope=synth.ENV_FLAT, boundary=boundary,
                              min_image=min_image)
         c = md.Context([cfg], [md.HostParticles(xx, u, z, mass, w)])
-        c.set_tuning(128, 4, 512, 0, split, 0)
+        c.set_tuning(tuning[0], tuning[1], tuning[2], 0, split, tuning[3])
         return c
 
     e64, p64 = oracle.self_field(x, q, eps, kc, potential=True, box=L,
@@ -645,11 +648,12 @@ def test_min_image_field_step_and_diagnostics_follow_oracle(md, split):
         assert summary(force_error(e3, e_open))["p99"] <= FORCE_P99
 
 
-def test_min_image_skips_tiles_within_half_a_box_bit_for_bit(md):
+@pytest.mark.parametrize("tuning", [(128, 4, 512, 0), (128, 8, 256, 1)])
+def test_min_image_skips_tiles_within_half_a_box_bit_for_bit(md, tuning):
     """A compact cluster in a large periodic cube (20 R0, as in Sec. II): no
     pair is half a box apart, so with minimum-image forces every tile takes
     the plain sum and the run equals the run without image forces bit for
-    bit (fields and 5 steps)."""
+    bit (fields and 5 steps), on the scalar and the packed path."""
     w = synth.xe3_cluster(20000, seed=12)
     r0 = float(np.abs(w.cluster.x).max())
     out = []
@@ -657,7 +661,7 @@ def test_min_image_skips_tiles_within_half_a_box_bit_for_bit(md):
         cfg = md.config_from_workload(w)
         cfg.boundary, cfg.box, cfg.min_image = 1, 20.0 * r0, mi
         with md.Context([cfg], [md.HostParticles.from_cluster(w.cluster)]) as ctx:
-            ctx.set_tuning(128, 4, 512, 0, 2, 0)
+            ctx.set_tuning(tuning[0], tuning[1], tuning[2], 0, 2, tuning[3])
             e = ctx.fields(0)
             ctx.step(5)
             out.append((e, ctx.get_particles(0)))
@@ -665,13 +669,33 @@ def test_min_image_skips_tiles_within_half_a_box_bit_for_bit(md):
     assert np.array_equal(out[0][1].x, out[1][1].x) and np.array_equal(out[0][1].u, out[1][1].u)
 
 
-def test_min_image_refuses_packed_tunings(md):
+def test_min_image_refuses_tunings_without_its_kernel(md):
     cfg = md.make_config(softening=1e-3, box=0.05, boundary=1, min_image=1)
     x, u, z, mass, w = _box_gas(10, 30, 0.05, 3)
     with md.Context([cfg], [md.HostParticles(x, u, z, mass, w)]) as ctx:
         with pytest.raises(md.MDError) as ei:
-            ctx.set_tuning(128, 4, 256, 0, 0, 1)      # packed: no minimum-image kernel
+            ctx.set_tuning(128, 4, 256, 0, 0, 1)      # packed 128x4: no minimum-image kernel
         assert ei.value.status == md.MD_ERR_ARG
+        ctx.set_tuning(128, 8, 256, 0, 0, 1)          # packed 128x8 has one
+        ctx.set_tuning(256, 4, 512, 0, 0, 1)
+
+
+def test_min_image_scalar_and_packed_give_the_same_bits(md):
+    """The packed minimum-image reduction takes the scalar one's three rounded
+    operations lane by lane: with one tile size (512) and source split, the
+    scalar and the packed 256 x 4 configurations step a gas that fills the
+    periodic cube identically."""
+    L = 0.05
+    x, u, z, mass, w = _box_gas(1000, 3000, L, 41)
+    cfg = md.make_config(a0=0.02, tau=1.0, dt=0.05, softening=1e-3, box=L,
+                         envelope=synth.ENV_FLAT, boundary=1, min_image=1)
+    out = []
+    for packed in (0, 1):
+        with md.Context([cfg], [md.HostParticles(x, u, z, mass, w)]) as ctx:
+            ctx.set_tuning(256, 4, 512, 0, 1, packed)
+            ctx.step(4)
+            out.append(ctx.get_particles(0))
+    assert np.array_equal(out[0].x, out[1].x) and np.array_equal(out[0].u, out[1].u)
 
 
 def test_checkpoint_resume_is_exact(md):
