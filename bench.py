@@ -42,7 +42,7 @@ FP32_INSTR_PER_PAIR = 12
 # at full size in the named kernel configuration (threads, r, tile, packed,
 # jsplit); reported only when the timed run uses that configuration.
 STEP_TRAFFIC_BYTES = {("xe3_200k", 200000, 128, 8, 512, True, 9): 15.77e6,
-                      ("xe3_200k", 200000, 128, 8, 256, True, -4): 20.27e6}
+                      ("xe3_200k", 200000, 128, 8, 256, True, -4): 20.16e6}
 L2_FLUSH_BYTES = 512 << 20
 # step kernel configuration of the ionizing 200k-atom contexts (threads, r,
 # tile, CTAs per SM, jsplit, packed, min_blocks): the fastest of four packed
