@@ -18,7 +18,8 @@ struct ClusterDev {
   int n;           // real records
   int n_pad;       // records incl. zero-charge padding (multiple of kPad)
   int nseg;        // sources split into nseg segments (work units) per i-block
-  int seg_len;     // sources per segment (last one shorter)
+  int seg_len;     // sources per segment (last one shorter); with equal shares
+                   // the units carry their own source pieces and nseg is 1
   double a0, tau, t0, dt, box, t_switch;
   float eps2;
   int pol, env, boundary;
