@@ -1471,9 +1471,11 @@ __global__ void __launch_bounds__(THREADS, MINB) k_step(const StepArgs a) {
 // ----------------------------------------------------------- field kernel --
 
 // Field (and potential) at targets from sources; one target block per CTA.
-template <int THREADS, int R, int TILE, int STAGES, bool POT, bool MI = false>
+template <int THREADS, int R, int TILE, int STAGES, bool POT, bool MI = false, bool PACK = false>
 __global__ void __launch_bounds__(THREADS) k_field(const FieldArgs a) {
   __shared__ Stage<TILE, STAGES> sm;
+  __shared__ DupTile<PACK ? TILE : 1> dup;
+  __shared__ KahanSmem<PACK ? R / 2 : 1, PACK ? THREADS : 1, POT> ks;
   __shared__ int s_abort;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) mbar_init(&sm.full[s], 1);
@@ -1517,7 +1519,13 @@ __global__ void __launch_bounds__(THREADS) k_field(const FieldArgs a) {
   acc.zero();
   unsigned it = 0;
   bool ok;
-  if constexpr (MI) {
+  if constexpr (PACK) {
+    __shared__ float s_tb[6];  // bounds of this CTA's targets
+    if constexpr (MI) target_bounds<THREADS, R>(xi, yi, zi, s_tb);
+    ok = sum_sources_packed<THREADS, R, TILE, STAGES, POT, MI>(
+        sm, dup, ks, it, a.src + j0, jn, xi, yi, zi, a.eps2, a.err, &s_abort, a.src_live,
+        a.gbase + j0, true, a.box, MI ? 1.0f / a.box : 0.0f, s_tb);
+  } else if constexpr (MI) {
     __shared__ float s_tb[6];  // bounds of this CTA's targets
     target_bounds<THREADS, R>(xi, yi, zi, s_tb);
     ok = sum_sources<THREADS, R, TILE, STAGES, POT, true>(sm, it, a.src + j0, jn, xi, yi, zi,
@@ -1534,10 +1542,18 @@ __global__ void __launch_bounds__(THREADS) k_field(const FieldArgs a) {
   for (int r = 0; r < R; ++r) {
     const long long i = i0 + threadIdx.x + r * THREADS;
     if (i >= a.nt) continue;
-    const double ex = -(static_cast<double>(acc.sx[r]) - acc.cx[r]);
-    const double ey = -(static_cast<double>(acc.sy[r]) - acc.cy[r]);
-    const double ez = -(static_cast<double>(acc.sz[r]) - acc.cz[r]);
-    double ph = POT ? static_cast<double>(acc.sp[r]) - acc.cp[r] : 0.0;
+    double ex, ey, ez, ph = 0.0;
+    if constexpr (PACK) {
+      ex = -(static_cast<double>(kahan_part(ks, 0, r)) - kahan_part(ks, 3, r));
+      ey = -(static_cast<double>(kahan_part(ks, 1, r)) - kahan_part(ks, 4, r));
+      ez = -(static_cast<double>(kahan_part(ks, 2, r)) - kahan_part(ks, 5, r));
+      if constexpr (POT) ph = static_cast<double>(kahan_part(ks, 6, r)) - kahan_part(ks, 7, r);
+    } else {
+      ex = -(static_cast<double>(acc.sx[r]) - acc.cx[r]);
+      ey = -(static_cast<double>(acc.sy[r]) - acc.cy[r]);
+      ez = -(static_cast<double>(acc.sz[r]) - acc.cz[r]);
+      if constexpr (POT) ph = static_cast<double>(acc.sp[r]) - acc.cp[r];
+    }
     if (split) {
       part[4 * i + 0] = ex;
       part[4 * i + 1] = ey;

@@ -272,8 +272,10 @@ const KernelConfig kConfigs[] = {
     MD_STEP_CONFIG(128, 8, 512, 1, true, 3),
 };
 
+// the field kernel: the step kernel's packed source loop (128 threads x 8
+// targets, 512-source tiles, one stage)
 constexpr int kFieldThreads = 128;
-constexpr int kFieldR = 2;
+constexpr int kFieldR = 8;
 constexpr int kFieldTile = 512;
 
 }  // namespace
@@ -315,15 +317,16 @@ cudaError_t launch_field(const FieldArgs& a, bool potential, cudaStream_t s) {
   const long long per = kFieldThreads * kFieldR;
   const dim3 grid(static_cast<unsigned>((a.nt + per - 1) / per),
                   static_cast<unsigned>(a.nseg > 1 ? a.nseg : 1));
+  constexpr int T = kFieldThreads, R = kFieldR, TL = kFieldTile;
   if (a.box > 0.0f) {
     if (potential)
-      k_field<kFieldThreads, kFieldR, kFieldTile, 2, true, true><<<grid, kFieldThreads, 0, s>>>(a);
+      k_field<T, R, TL, 1, true, true, true><<<grid, T, 0, s>>>(a);
     else
-      k_field<kFieldThreads, kFieldR, kFieldTile, 2, false, true><<<grid, kFieldThreads, 0, s>>>(a);
+      k_field<T, R, TL, 1, false, true, true><<<grid, T, 0, s>>>(a);
   } else if (potential) {
-    k_field<kFieldThreads, kFieldR, kFieldTile, 2, true><<<grid, kFieldThreads, 0, s>>>(a);
+    k_field<T, R, TL, 1, true, false, true><<<grid, T, 0, s>>>(a);
   } else {
-    k_field<kFieldThreads, kFieldR, kFieldTile, 2, false><<<grid, kFieldThreads, 0, s>>>(a);
+    k_field<T, R, TL, 1, false, false, true><<<grid, T, 0, s>>>(a);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || a.nseg <= 1) return e;
@@ -335,7 +338,7 @@ int field_targets_per_cta() { return kFieldThreads * kFieldR; }
 
 cudaError_t field_blocks_per_sm(int* out) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      out, k_field<kFieldThreads, kFieldR, kFieldTile, 2, true>, kFieldThreads, 0);
+      out, k_field<kFieldThreads, kFieldR, kFieldTile, 1, true, false, true>, kFieldThreads, 0);
 }
 
 cudaError_t launch_diag(const DiagArgs& a, int blocks, DiagPartial* out, cudaStream_t s) {
