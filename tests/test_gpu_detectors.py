@@ -144,11 +144,12 @@ def test_detectors_on_an_ionizing_cluster_match_oracle(md):
     np.testing.assert_array_equal(inside, det.inside(state_of(g0)))
 
 
-def test_detectors_with_minimum_image_forces_match_oracle(md):
+@pytest.mark.parametrize("packed", [0, 1])
+def test_detectors_with_minimum_image_forces_match_oracle(md, packed):
     """The exploding ion sphere in a periodic cube of 6 R0 with minimum-image
-    forces (the step kernel's image twin with the detector epilogue): every
-    crossing of 2.5 R0 matches the oracle's detectors applied to the GPU's
-    own states, step by step."""
+    forces (the step kernel's image twin with the detector epilogue, scalar
+    and packed): every crossing of 2.5 R0 matches the oracle's detectors
+    applied to the GPU's own states, step by step."""
     n = 600
     c, r0, e_max, cfg = explosion(md, n, seed=6)
     cfg.boundary, cfg.box, cfg.min_image = 1, 6.0 * r0, 1
@@ -156,6 +157,8 @@ def test_detectors_with_minimum_image_forces_match_oracle(md):
     e_max_ev = 0.4 * e_max * ME_C2_EV
     det = oracle.Detectors(n, radius=2.5 * r0, cone_deg=30.0, e_max_ev=e_max_ev, nbins=nb)
     with md.Context([cfg], [md.HostParticles.from_cluster(c)]) as ctx:
+        if packed:
+            ctx.set_tuning(128, 8, 256, 0, 0, 1)
         ctx.set_detectors(0, 2.5 * r0, cone_deg=30.0, e_max_ev=e_max_ev, n_bins=nb)
         g0 = ctx.get_particles(0)
         for _ in range(200):
