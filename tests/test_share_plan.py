@@ -67,6 +67,47 @@ def test_pieces_cover_every_iblock_once_in_order(md, n_pad, per, tile, shares):
     assert min(per_share) == T // S
 
 
+def _plan_by_definition(n_pad, per, tile, shares):
+    """The partition as md.h states it, written out: the tiles of every
+    i-block end to end (cluster, then i-block order), share s = tiles
+    [s T / S, (s + 1) T / S) (integer division), pieces = the non-empty
+    intersections of shares and i-blocks in order."""
+    blocks = []
+    for c, n in enumerate(n_pad):
+        tiles = -(-n // tile)
+        blocks += [(c, b, tiles, n) for b in range(-(-n // per))]
+    T = sum(b[2] for b in blocks)
+    S = min(shares, T)
+    bounds = [k * T // S for k in range(S + 1)]
+    units, share_of, F = [], [], 0
+    for c, b, tiles, n in blocks:
+        pcs = []
+        for s_ in range(S):
+            lo, hi = max(F, bounds[s_]), min(F + tiles, bounds[s_ + 1])
+            if lo < hi:
+                j0 = (lo - F) * tile
+                pcs.append([c, b, len(pcs), 0, j0, min((hi - F) * tile, n) - j0])
+                share_of.append(s_)
+        for p_ in pcs:
+            p_[3] = len(pcs)
+        units += pcs
+        F += tiles
+    first = [0] * (S + 1)
+    for s_ in share_of:
+        first[s_ + 1] += 1
+    for k in range(1, S + 1):
+        first[k] += first[k - 1]
+    return units, first
+
+
+@pytest.mark.parametrize("n_pad,per,tile,shares", CASES[:5] + CASES[6:])
+def test_plan_equals_the_stated_definition(md, n_pad, per, tile, shares):
+    units, first = md.plan_shares(n_pad, per, tile, shares)
+    ref_units, ref_first = _plan_by_definition(n_pad, per, tile, shares)
+    assert units.tolist() == ref_units
+    assert first.tolist() == ref_first
+
+
 def test_small_plan_by_hand(md):
     """2 clusters of 2048 records, i-blocks of 1024 targets, 512-record tiles:
     4 i-blocks of 4 tiles (T = 16) in 3 shares of tiles [0,5) [5,10) [10,16).
