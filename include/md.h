@@ -435,7 +435,8 @@ md_status md_autotune(md_ctx *ctx, int32_t steps, double *times_ms, int32_t cap)
  * the unit count at first[S].  *n_units and *n_shares receive the counts;
  * with units and first NULL the call only sizes them.  Errors: MD_ERR_ARG
  * (NULL n_pad/n_units/n_shares, n_clusters, per, tile or shares < 1, an
- * n_pad < 1, shares or T of 2^31 or more, cap below the unit count),
+ * n_pad < 1, shares or T of 2^31 or more, units given with cap below the
+ * unit count),
  * MD_ERR_OOM (host memory). */
 md_status md_plan_shares(const int32_t *n_pad, int32_t n_clusters, int32_t per, int32_t tile,
                          int64_t shares, int32_t *units, int64_t cap, int32_t *first,

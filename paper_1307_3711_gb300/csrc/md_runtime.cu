@@ -2084,7 +2084,7 @@ static md_status md_plan_shares_body(const int32_t* n_pad, int32_t n_clusters, i
   *n_units = static_cast<int64_t>(us.size());
   *n_shares = G;
   if (!units && !first) return MD_OK;  // a query of the sizes
-  if (cap < static_cast<int64_t>(us.size()))
+  if (units && cap < static_cast<int64_t>(us.size()))
     return fail(MD_ERR_ARG, "cap %lld below the %zu units", static_cast<long long>(cap), us.size());
   if (units)
     for (size_t i = 0; i < us.size(); ++i) {

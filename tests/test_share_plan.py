@@ -150,3 +150,7 @@ def test_cap_below_the_unit_count(md):
                                 C.byref(nu), C.byref(ns))
     assert st == md.MD_ERR_ARG and nu.value == 2016 and ns.value == 1824
     assert not units.any()
+    # the shares' first units alone need no unit capacity
+    st = md._lib.md_plan_shares(n_pad.ctypes.data_as(ip), 1, 1024, 256, 1824, None, 0,
+                                first.ctypes.data_as(ip), C.byref(nu), C.byref(ns))
+    assert st == md.MD_OK and first[-1] == 2016 and np.all(np.diff(first) >= 1)
