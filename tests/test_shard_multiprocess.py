@@ -1,5 +1,5 @@
-"""The multi-GPU split of one cluster by target records, on CPU: two gloo ranks
-(world size 2) each push their slice of a 3000-record Xe3+ cluster with the
+"""The multi-GPU split of one cluster by target records, on CPU: two or three
+gloo ranks each push their slice of a 3000-record Xe3+ cluster with the
 FP64 oracle's pieces (field of all sources at the slice's targets, laser,
 Boris kick, drift) and exchange their slices of the j-stream with
 shard.exchange after every step.  After three steps each rank's slice equals
@@ -73,7 +73,8 @@ def _rank(rank, world, port, q):
     dist.destroy_process_group()
 
 
-def test_two_gloo_ranks_split_one_cluster():
+@pytest.mark.parametrize("world", [2, 3])
+def test_gloo_ranks_split_one_cluster(world):
     import torch.multiprocessing as mp
     sys.path.insert(0, ROOT)
     import oracle
@@ -81,7 +82,7 @@ def test_two_gloo_ranks_split_one_cluster():
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = free_port()
-    ps = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    ps = [ctx.Process(target=_rank, args=(r, world, port, q)) for r in range(world)]
     for p in ps:
         p.start()
     out = sorted((q.get(timeout=300) for _ in ps), key=lambda o: o[0])
@@ -94,7 +95,8 @@ def test_two_gloo_ranks_split_one_cluster():
     p = oracle.make_params(a0=w.a0, tau=w.tau, t0=w.t0, dt=w.dt, eps=w.eps, pol=w.pol,
                            env=w.env, lambda_um=w.lambda_um)
     oracle.md_steps(ref, p, STEPS)
-    assert out[0][1] == 0 and out[0][2] == out[1][1] and out[1][2] == N
+    assert out[0][1] == 0 and out[-1][2] == N
+    assert all(out[k][2] == out[k + 1][1] for k in range(world - 1))
     scale = np.abs(ref.x).max()
     for _, b, e, x, u, jx in out:
         np.testing.assert_allclose(x, ref.x[b:e], rtol=0, atol=1e-12 * scale)
